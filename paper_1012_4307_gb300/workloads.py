@@ -1,0 +1,193 @@
+"""Seeded synthetic inputs: grids, k^2 fields and sources shaped like the paper's model
+problems (Section 5: potential wells, a wavenumber that grows toward the boundary, ECS
+layers, localised sources).
+
+This module holds no arithmetic of the solver itself.  It only draws inputs, so the GPU
+path and the CPU oracle are fed identical arrays.  Random numbers come from splitmix64
+(Steele, Lea & Flood, "Fast splittable pseudorandom number generators", 2014) and
+Box-Muller, written out here, so the arrays are the same on every machine and numpy version.
+
+Arrays are numpy, C-ordered with x fastest, including the Dirichlet boundary nodes.
+Node coordinates: x_j = lo + j (hi - lo) / (n - 1) on every axis.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, count: int) -> np.ndarray:
+    """The first ``count`` outputs of splitmix64 started from state ``seed``."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (np.arange(1, count + 1, dtype=np.uint64) * _GOLDEN)
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed: int, count: int) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits of splitmix64."""
+    return (splitmix64(seed, count) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(seed: int, count: int) -> np.ndarray:
+    """Standard normal doubles by Box-Muller on pairs of uniforms."""
+    m = (count + 1) // 2
+    u = uniform(seed, 2 * m)
+    r = np.sqrt(-2.0 * np.log(1.0 - u[0::2]))
+    t = 2.0 * math.pi * u[1::2]
+    return np.concatenate([r * np.cos(t), r * np.sin(t)])[:count]
+
+
+def coords(dim: int, n: int, lo: float = -1.0, hi: float = 1.0):
+    """Real node coordinates as a list of broadcastable arrays (x fastest)."""
+    x = lo + (hi - lo) * np.arange(n, dtype=np.float64) / (n - 1)
+    out = []
+    for a in range(dim):
+        shape = [1] * dim
+        shape[dim - 1 - a] = n
+        out.append(x.reshape(shape))
+    return out
+
+
+def k2_constant(dim: int, n: int, k: float) -> np.ndarray:
+    return np.full((n,) * dim, k * k, dtype=np.float64)
+
+
+def k2_well_growth(dim: int, n: int, E: float = 2.0, V0: float = 5.0, sigma: float = 0.2,
+                   kh_max: float = 0.6, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """k^2 = 2 (E - V) with V = -V0 exp(-r^2/sigma^2) - c r^4, evaluated at the real nodes.
+
+    A Gaussian well at the centre plus a term that grows toward the boundary; c is fixed so
+    that k h reaches ``kh_max`` exactly at the corners (r^2 = dim) and stays below elsewhere.
+    """
+    h = (hi - lo) / (n - 1)
+    X = coords(dim, n, lo, hi)
+    r2 = sum(x * x for x in X)
+    d = float(dim)
+    c = ((kh_max / h) ** 2 / 2.0 - E - V0 * math.exp(-d / sigma ** 2)) / (d * d)
+    V = -V0 * np.exp(-r2 / sigma ** 2) - c * r2 * r2
+    return np.ascontiguousarray(np.broadcast_to(2.0 * (E - V), (n,) * dim)).astype(np.float64)
+
+
+def gaussian_source(dim: int, n: int, sigma: float, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """f = exp(-|x - c|^2 / (2 sigma^2)) with centre c uniform in [-0.5, 0.5]^dim; zero boundary."""
+    c = uniform(seed, dim) - 0.5
+    X = coords(dim, n, lo, hi)
+    r2 = sum((x - c[a]) ** 2 for a, x in enumerate(X))
+    f = np.exp(-r2 / (2.0 * sigma * sigma)).astype(np.complex128)
+    f = np.ascontiguousarray(np.broadcast_to(f, (n,) * dim)).copy()
+    _zero_ring(f)
+    return f
+
+
+def random_box_source(dim: int, n: int, seed: int, half_width: float = 0.5,
+                      lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """i.i.d. complex N(0, 1) node values where |x|_inf < half_width, zero elsewhere."""
+    g = normal(seed, 2 * n ** dim)
+    f = (g[0::2] + 1j * g[1::2]).reshape((n,) * dim)
+    X = coords(dim, n, lo, hi)
+    inside = np.ones((n,) * dim, dtype=bool)
+    for x in X:
+        inside &= np.abs(x) < half_width
+    f = np.where(inside, f, 0).astype(np.complex128)
+    _zero_ring(f)
+    return f
+
+
+def random_field(shape, seed: int) -> np.ndarray:
+    """i.i.d. complex N(0,1) values on every node of ``shape`` with a zero boundary ring."""
+    n = int(np.prod(shape))
+    g = normal(seed, 2 * n)
+    x = (g[0::2] + 1j * g[1::2]).reshape(shape).astype(np.complex128)
+    _zero_ring(x)
+    return x
+
+
+def _zero_ring(x: np.ndarray) -> None:
+    for ax in range(x.ndim):
+        idx = [slice(None)] * x.ndim
+        idx[ax] = 0
+        x[tuple(idx)] = 0
+        idx[ax] = -1
+        x[tuple(idx)] = 0
+
+
+@dataclass
+class Problem:
+    """One synthetic model problem (geometry, ECS, k^2, source, preconditioner, solver)."""
+    name: str
+    dim: int
+    n: int
+    k2: np.ndarray
+    f: np.ndarray
+    theta: float = math.pi / 6
+    r0: float = 0.75
+    lo: float = -1.0
+    hi: float = 1.0
+    pc: str = "csg"
+    theta_a: float = math.pi / 14
+    beta: tuple = (-1.0, -0.5)
+    nu1: int = 2
+    nu2: int = 2
+    omega: float = 0.8
+    smoother: str = "jacobi"
+    coarsest_n: int = 17
+    restart: int = 30
+    tol: float = 1e-10
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def unknowns(self) -> int:
+        return (self.n - 2) ** self.dim
+
+
+def config_small(n: int = 65) -> Problem:
+    """2D -Delta u - k^2 u = f on [-1,1]^2, n x n nodes, ECS beyond |x|,|y| = 0.75 at pi/6,
+    constant k = 10, Gaussian source (sigma 0.05, seed 0), CSG by one V(2,2) cycle of
+    omega-Jacobi (0.8), GMRES(30) to 1e-10."""
+    return Problem("2d-const-k10-n%d" % n, 2, n, k2_constant(2, n, 10.0), gaussian_source(2, n, 0.05, 0),
+                   coarsest_n=17, restart=30, tol=1e-10)
+
+
+def config_2d_well(n: int = 1025, seed: int = 1) -> Problem:
+    """2D n x n nodes, k^2 = 2(E - V) with a Gaussian well (E=2, V0=5, sigma=0.2) and growth
+    toward the boundary so that k h <= 0.6, ECS at pi/6, random source on |x|_inf < 0.5."""
+    return Problem("2d-well-n%d" % n, 2, n, k2_well_growth(2, n), random_box_source(2, n, seed),
+                   coarsest_n=17, restart=30, tol=1e-8)
+
+
+def config_3d_well(n: int = 257, seed: int = 2) -> Problem:
+    """3D 7-point problem, n^3 nodes, same k^2 profile in r, ECS on all faces, FGMRES(20)."""
+    return Problem("3d-well-n%d" % n, 3, n, k2_well_growth(3, n), random_box_source(3, n, seed),
+                   coarsest_n=9, restart=20, tol=1e-8)
+
+
+def config_batch(count: int = 64, seed: int = 3, sizes=(129, 257, 513, 1025)):
+    """Independent 2D problems, sizes drawn uniformly from ``sizes``, energies E in [0.5, 4],
+    Gaussian sources (sigma 0.05)."""
+    u = uniform(seed, 3 * count)
+    out = []
+    for i in range(count):
+        n = sizes[min(int(u[3 * i] * len(sizes)), len(sizes) - 1)]
+        E = 0.5 + 3.5 * u[3 * i + 1]
+        src_seed = int(splitmix64(seed + 1000 + i, 1)[0] % np.uint64(2 ** 31))
+        out.append(Problem("batch%d-n%d" % (i, n), 2, n, k2_well_growth(2, n, E=E),
+                           gaussian_source(2, n, 0.05, src_seed), coarsest_n=17, restart=30, tol=1e-8,
+                           extra={"E": E}))
+    return out
+
+
+def config_adjoint(n: int = 513):
+    """2D n x n, k^2 profile with E = 2, Gaussian source (seed 4) and Gaussian probe g (seed 5)."""
+    p = Problem("2d-adjoint-n%d" % n, 2, n, k2_well_growth(2, n, E=2.0), gaussian_source(2, n, 0.05, 4),
+                coarsest_n=17, restart=30, tol=1e-10)
+    g = gaussian_source(2, n, 0.05, 5).real.copy()
+    p.extra["probe"] = g
+    return p

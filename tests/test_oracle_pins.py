@@ -1,0 +1,528 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test names the passage of the paper (bin Zubair, Reps, Vanroose, arXiv 1012.4307) or the
+piece of mathematics that fixes the expected value.  A plausible slip in the oracle (a dropped
+term, a wrong sign of the complex scaling, a transposed index, a wrong restriction weight, a
+swapped cycle index) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1012_4307_gb300 import workloads as W
+
+
+# ------------------------------------------------------------------ FD operator (Section 3.2)
+
+@pytest.mark.parametrize("dim,n,modes", [(1, 33, (5,)), (2, 17, (3, 5)), (3, 9, (1, 2, 3))])
+def test_dirichlet_laplacian_sine_modes(oracle, dim, n, modes):
+    """Without ECS the FD formula of Section 3.2 is the central difference; separable sine
+    modes are eigenvectors with eigenvalue sum_axes (2 - 2 cos(j pi/(n-1)))/h^2."""
+    z = [oracle.contour(n, -1.0, 1.0, 0.0, -10.0, 10.0) for _ in range(dim)]
+    L = oracle.Op(z, 0.0, a=1.0, bk=0.0, c=0.0)
+    h = 2.0 / (n - 1)
+    idx = np.arange(n)
+    x = np.ones((n,) * dim)
+    lam = 0.0
+    for a, j in enumerate(modes):
+        shape = [1] * dim
+        shape[dim - 1 - a] = n
+        x = x * np.sin(j * np.pi * idx / (n - 1)).reshape(shape)
+        lam += (2.0 - 2.0 * math.cos(j * math.pi / (n - 1))) / h ** 2
+    y = L.apply(x)
+    assert np.abs(y - lam * x).max() <= 1e-12 * lam * np.abs(x).max()
+
+
+def test_helmholtz_shift_and_scaling(oracle):
+    """M = a L_h + bk k^2 + c is linear in (a, bk, c): check against L_h and k^2 x separately."""
+    n = 9
+    z = oracle.axes(2, n)
+    k2 = W.k2_well_growth(2, n)
+    x = W.random_field((n, n), 7)
+    L = oracle.Op(z, k2, a=1.0, bk=0.0, c=0.0).apply(x)
+    a, bk, c = 0.3 - 0.2j, -1.5 + 0.25j, 1 - 1j
+    M = oracle.Op(z, k2, a=a, bk=bk, c=c).apply(x)
+    mask = np.zeros((n, n), bool)
+    mask[1:-1, 1:-1] = True
+    ref = np.where(mask, a * L + (bk * k2 + c) * x, 0)
+    assert np.abs(M - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ Lemma 3.1 (Section 3.3)
+
+def _ecs_1d(oracle, ncells, m, theta):
+    """Paper's one-sided ECS grid: [0,1] with ncells cells, then m cells on [1, R_z]."""
+    h = 1.0 / ncells
+    z = oracle.contour(ncells + m + 1, 0.0, 1.0 + m * h, theta, -1.0, 1.0)
+    return z, h, h * np.exp(1j * theta)
+
+
+@pytest.mark.parametrize("ncells,m,theta", [(40, 16, math.pi / 6), (64, 24, math.pi / 4), (30, 30, math.pi / 8)])
+def test_lemma_3_1_eigenvalue_equation(oracle, ncells, m, theta):
+    """Lemma 3.1: every eigenvalue of the 1D ECS matrix L_h solves
+    tan(2np)/tan(2mq) + cos p / cos q = 0 with p = arccos(1 - lam h^2/2)/2,
+    q = arccos(1 - lam gamma^2 h^2/2)/2.  Checked in the pole-free form
+    h_g sin2p cos(2pn) sin(2qm) + h sin2q cos(2qm) sin(2pn) = 0 (multiply through by
+    h h_g cos(2pn) cos(2qm)/(...)), and in the printed form where it has no pole nearby."""
+    z, h, hg = _ecs_1d(oracle, ncells, m, theta)
+    L = oracle.Op([z], 0.0, a=1.0, bk=0.0, c=0.0).dense()
+    lam = np.linalg.eigvals(L)
+    assert lam.size == ncells + m - 1
+    p = 0.5 * np.arccos(1 - lam * h * h / 2)
+    q = 0.5 * np.arccos(1 - lam * hg * hg / 2)
+    t1 = hg * np.sin(2 * p) * np.cos(2 * p * ncells) * np.sin(2 * q * m)
+    t2 = h * np.sin(2 * q) * np.cos(2 * q * m) * np.sin(2 * p * ncells)
+    assert np.max(np.abs(t1 + t2) / (np.abs(t1) + np.abs(t2))) < 1e-8
+    a = np.tan(2 * ncells * p) / np.tan(2 * m * q)
+    b = np.cos(p) / np.cos(q)
+    ok = (np.abs(np.tan(2 * m * q)) > 1e-3) & (np.abs(np.cos(q)) > 1e-3) & (np.abs(a) < 1e6)
+    assert ok.sum() > lam.size // 2
+    assert np.max(np.abs(a + b)[ok] / (np.abs(a) + np.abs(b))[ok]) < 1e-6
+    # spectrum in the closed lower half-plane (Section 3.3, Fig. 2)
+    assert lam.imag.max() <= 1e-9 * np.abs(lam).max()
+
+
+def test_lemma_detects_wrong_kink_coefficient(oracle):
+    """Control: the uniform-width formula at the kink node (a plausible slip) violates Lemma 3.1."""
+    ncells, m, theta = 40, 16, math.pi / 6
+    z, h, hg = _ecs_1d(oracle, ncells, m, theta)
+    L = oracle.Op([z], 0.0, a=1.0, bk=0.0, c=0.0).dense()
+    k = ncells - 1  # unknown index of node n
+    L[k, k - 1], L[k, k], L[k, k + 1] = -1 / h ** 2, 1 / h ** 2 + 1 / hg ** 2, -1 / hg ** 2
+    lam = np.linalg.eigvals(L)
+    p = 0.5 * np.arccos(1 - lam * h * h / 2)
+    q = 0.5 * np.arccos(1 - lam * hg * hg / 2)
+    t1 = hg * np.sin(2 * p) * np.cos(2 * p * ncells) * np.sin(2 * q * m)
+    t2 = h * np.sin(2 * q) * np.cos(2 * q * m) * np.sin(2 * p * ncells)
+    assert np.max(np.abs(t1 + t2) / (np.abs(t1) + np.abs(t2))) > 1e-3
+
+
+def test_continuous_spectrum_limit(oracle):
+    """Section 3.3: sigma(L) = {(j pi / R_z)^2} on the ray rho e^{-2 i theta}.  The smallest
+    discrete eigenvalues converge to it under refinement (fixed R_z)."""
+    theta = math.pi / 6
+    errs = []
+    for ncells in (16, 32, 64):
+        m = ncells // 2
+        z, h, hg = _ecs_1d(oracle, ncells, m, theta)
+        Rz = z[-1]
+        lam = np.linalg.eigvals(oracle.Op([z], 0.0, a=1.0, bk=0.0, c=0.0).dense())
+        lam = lam[np.argsort(np.abs(lam))][:3]
+        exact = np.array([(j * math.pi / Rz) ** 2 for j in (1, 2, 3)])
+        errs.append(np.max(np.abs(lam - exact) / np.abs(exact)))
+    assert errs[-1] < 1e-2
+    assert errs[1] < errs[0] and errs[2] < errs[1]
+    order = math.log(errs[1] / errs[2], 2)
+    assert order > 0.9
+
+
+# ------------------------------------------------------------------ ECS absorption (Section 3.1)
+
+def test_ecs_outgoing_wave_matches_lattice_green(oracle):
+    """For constant k the ECS layer must absorb: on the real region the ECS solution with a
+    point source delta_{j,j0}/h matches the exact outgoing lattice Green's function of the
+    half-infinite lattice with Dirichlet at 0,
+        u_j = (i h / (2 sin kappa h)) (e^{i kappa h |j - j0|} - e^{i kappa h (j + j0)}),
+    2 - 2 cos(kappa h) = k^2 h^2, up to a reflection that shrinks with the layer thickness."""
+    ncells, k, theta = 200, 20.0, math.pi / 6
+    h = 1.0 / ncells
+    kappa = math.acos(1 - (k * h) ** 2 / 2) / h
+    j0 = 60
+    refl = []
+    for m in (20, 40, 80):
+        z = oracle.contour(ncells + m + 1, 0.0, 1.0 + m * h, theta, -1.0, 1.0)
+        A = oracle.Op([z], k * k, a=1.0, bk=-1.0, c=0.0)
+        f = np.zeros(ncells + m + 1, complex)
+        f[j0] = 1.0 / h
+        u = np.zeros_like(f)
+        u[1:-1] = np.linalg.solve(A.dense(), f[1:-1])
+        j = np.arange(1, ncells)
+        ex = (1j * h / (2 * math.sin(kappa * h))) * (np.exp(1j * kappa * h * np.abs(j - j0))
+                                                     - np.exp(1j * kappa * h * (j + j0)))
+        refl.append(np.max(np.abs(u[j] - ex)) / np.max(np.abs(ex)))
+    assert refl[-1] < 1e-3
+    assert refl[0] > refl[1] > refl[2]
+    # the wrong rotation direction (theta -> -theta) does not absorb
+    m = 80
+    z = oracle.contour(ncells + m + 1, 0.0, 1.0 + m * h, -theta, -1.0, 1.0)
+    A = oracle.Op([z], k * k, a=1.0, bk=-1.0, c=0.0)
+    f = np.zeros(ncells + m + 1, complex)
+    f[j0] = 1.0 / h
+    u = np.zeros_like(f)
+    u[1:-1] = np.linalg.solve(A.dense(), f[1:-1])
+    j = np.arange(1, ncells)
+    ex = (1j * h / (2 * math.sin(kappa * h))) * (np.exp(1j * kappa * h * np.abs(j - j0))
+                                                 - np.exp(1j * kappa * h * (j + j0)))
+    assert np.max(np.abs(u[j] - ex)) / np.max(np.abs(ex)) > 0.1
+
+
+def test_continuum_green_second_order(oracle):
+    """Interior of the real region: the ECS solution approaches the continuum Green's function
+    (1/k) sin(k x_<) e^{i k x_>} at O(h^2)."""
+    k, theta, x0 = 10.0, math.pi / 6, 0.3
+    errs = []
+    for ncells in (100, 200, 400):
+        h = 1.0 / ncells
+        m = ncells  # layer of real length 1: round-trip damping e^{-2 k sin(theta)} ~ 5e-5
+        z = oracle.contour(ncells + m + 1, 0.0, 1.0 + m * h, theta, -1.0, 1.0)
+        A = oracle.Op([z], k * k, a=1.0, bk=-1.0, c=0.0)
+        j0 = int(round(x0 / h))
+        f = np.zeros(ncells + m + 1, complex)
+        f[j0] = 1.0 / h
+        u = np.zeros_like(f)
+        u[1:-1] = np.linalg.solve(A.dense(), f[1:-1])
+        x = np.arange(ncells + 1) * h
+        xl, xg = np.minimum(x, x0), np.maximum(x, x0)
+        ex = np.sin(k * xl) * np.exp(1j * k * xg) / k
+        errs.append(np.max(np.abs(u[: ncells + 1] - ex)))
+    assert errs[2] < errs[1] < errs[0]
+    assert math.log(errs[1] / errs[2], 2) > 1.7
+
+
+# ------------------------------------------------------------------ complex symmetry (R7)
+
+@pytest.mark.parametrize("n,r0", [(17, 0.75), (13, 0.7)])
+def test_weighted_complex_symmetry_and_transpose(oracle, n, r0):
+    """W M is complex symmetric ((WM)^T = WM, not Hermitian) with W the dual-volume weights
+    prod (h_{j-1}+h_j)/2 -- an off-grid kink included; apply_T is the plain transpose."""
+    z = oracle.axes(2, n, r0lo=-r0, r0hi=r0)
+    k2 = W.k2_well_growth(2, n)
+    for ts, bk in ((0.0, -1.0), (math.pi / 14, -1.0), (0.0, -1 - 0.5j)):
+        M = oracle.Op(z, k2, a=1.0, bk=bk, c=0.0, ts=ts)
+        D = M.dense()
+        wts = M.weights()[1:-1, 1:-1].ravel()
+        WM = wts[:, None] * D
+        assert np.abs(WM - WM.T).max() <= 1e-12 * np.abs(WM).max()
+        assert np.abs(WM - WM.conj().T).max() > 1e-3 * np.abs(WM).max()
+        x = W.random_field((n, n), 3)
+        yt = M.apply_T(x)[1:-1, 1:-1].ravel()
+        assert np.abs(yt - D.T @ x[1:-1, 1:-1].ravel()).max() <= 1e-12 * np.abs(yt).max()
+
+
+# ------------------------------------------------------------------ preconditioners (Section 4.1, 5)
+
+def test_preconditioner_spectra(oracle):
+    """Constant k: M_CSG = e^{-2 i theta_a} L_h - k^2 exactly (widths times e^{i theta_a});
+    sigma(M_CSG) and sigma(M_CSL) lie in the open lower half-plane; sigma(M_QD) lies in
+    quadrant IV when Re lambda0 is Z's leftmost eigenvalue; and sigma(M_QD^{-1} Z) lies in the
+    disk through 0, s and -i s (centre s(1-i)/2, radius s/sqrt 2, s = |Re lambda0|), the
+    Moebius-map argument of Section 4.1 with delta^2 = 1/s and k delta = 1 (eq. 4.2)."""
+    n, k, ta = 17, 6.0, math.pi / 14
+    z = oracle.axes(2, n)
+    A, Mg = oracle.helmholtz_ops(z, k * k, pc="csg", theta_a=ta)
+    L = oracle.Op(z, 0.0, a=1.0, bk=0.0, c=0.0).dense()
+    I = np.eye(L.shape[0])
+    assert np.abs(Mg.dense() - (np.exp(-2j * ta) * L - k * k * I)).max() <= 1e-10 * np.abs(L).max()
+    assert np.linalg.eigvals(Mg.dense()).imag.max() < 0
+    _, Ml = oracle.helmholtz_ops(z, k * k, pc="csl", beta=(-1.0, -0.5))
+    assert np.abs(Ml.dense() - (L + (-1 - 0.5j) * k * k * I)).max() <= 1e-10 * np.abs(L).max()
+    assert np.linalg.eigvals(Ml.dense()).imag.max() < 0
+    Z = A.dense()
+    lz = np.linalg.eigvals(Z)
+    assert lz.imag.max() <= 1e-9 * np.abs(lz).max()
+    l0 = lz[np.argmin(lz.real)]
+    _, Mq = oracle.helmholtz_ops(z, k * k, pc="qd", re_lambda0=l0.real)
+    lq = np.linalg.eigvals(Mq.dense())
+    assert lq.real.min() > -1e-9 and lq.imag.max() < 0
+    s = abs(l0.real)
+    mu = np.linalg.eigvals(np.linalg.solve(Mq.dense(), Z))
+    ctr = s * (1 - 1j) / 2
+    assert np.max(np.abs(mu - ctr)) <= s / math.sqrt(2) * (1 + 1e-9)
+
+
+# ------------------------------------------------------------------ transfers (Section 4.2)
+
+def _fw_1d(nf):
+    nc = (nf + 1) // 2
+    R = np.zeros((nc, nf))
+    for I in range(1, nc - 1):
+        R[I, 2 * I - 1:2 * I + 2] = [0.25, 0.5, 0.25]
+    return R
+
+
+def _lin_1d(nf):
+    nc = (nf + 1) // 2
+    P = np.zeros((nf, nc))
+    for q in range(1, nf - 1):
+        P[q, q // 2] += 0.5
+        P[q, (q + 1) // 2] += 0.5
+    return P
+
+
+@pytest.mark.parametrize("dim,nf", [(1, 17), (2, 9), (3, 9)])
+def test_transfer_operators(oracle, dim, nf):
+    """Full weighting is the tensor product of (1,2,1)/4; bilinear/trilinear interpolation the
+    tensor product of 1D linear interpolation; P = 2^dim R^T on interior nodes; both reproduce
+    linear functions."""
+    nc = (nf + 1) // 2
+    R1, P1 = _fw_1d(nf), _lin_1d(nf)
+    R, P = R1, P1
+    for _ in range(dim - 1):
+        R, P = np.kron(R, R1), np.kron(P, P1)
+    rf = W.random_field((nf,) * dim, 11)
+    rf_full = rf + 0.0  # boundary already zero
+    assert np.abs(oracle.restrict(rf_full).ravel() - R @ rf_full.ravel()).max() < 1e-14
+    ec = W.random_field((nc,) * dim, 12)
+    uf = W.random_field((nf,) * dim, 13)
+    mask = np.zeros((nf,) * dim, bool)
+    mask[(slice(1, -1),) * dim] = True
+    ref = uf.ravel() + np.where(mask.ravel(), P @ ec.ravel(), 0)
+    assert np.abs(oracle.prolong_add(ec, uf).ravel() - ref).max() < 1e-14
+    # P = 2^d R^T between interior unknowns
+    fi = np.flatnonzero(mask.ravel())
+    cmask = np.zeros((nc,) * dim, bool)
+    cmask[(slice(1, -1),) * dim] = True
+    ci = np.flatnonzero(cmask.ravel())
+    assert np.abs(P[np.ix_(fi, ci)] - 2 ** dim * R[np.ix_(ci, fi)].T).max() < 1e-15
+    # linear functions
+    xs = W.coords(dim, nf)
+    lin = 0.3 + sum((a + 1) * x for a, x in enumerate(xs)) + 0j
+    lin = np.broadcast_to(lin, (nf,) * dim).copy()
+    xc = W.coords(dim, nc)
+    linc = np.broadcast_to(0.3 + sum((a + 1) * x for a, x in enumerate(xc)) + 0j, (nc,) * dim).copy()
+    got = oracle.restrict(lin)
+    assert np.abs((got - linc)[cmask]).max() < 1e-13
+    got = oracle.prolong_add(linc, np.zeros((nf,) * dim, complex))
+    assert np.abs((got - lin)[mask]).max() < 1e-13
+
+
+# ------------------------------------------------------------------ smoothers and cycles (Alg. 1)
+
+def _dense_level(oracle, M):
+    D = M.dense()
+    return D, np.diag(np.diag(D))
+
+
+def test_smoothers_match_matrix_form(oracle):
+    """omega-Jacobi is u <- u + omega D^{-1}(f - M u); red-black is the red half-step followed by
+    the black one, with red = even i+j on the level's own grid."""
+    n = 9
+    z = oracle.axes(2, n)
+    k2 = W.k2_well_growth(2, n)
+    _, M = oracle.helmholtz_ops(z, k2, pc="csg")
+    D, Dg = _dense_level(oracle, M)
+    f = W.random_field((n, n), 21)
+    u = W.random_field((n, n), 22)
+    fi, ui = f[1:-1, 1:-1].ravel(), u[1:-1, 1:-1].ravel()
+    om = 0.8
+    Dinv = np.diag(1 / np.diag(D))
+    ref = ui + om * Dinv @ (fi - D @ ui)
+    assert np.abs(M.jacobi(f, u, om, 1)[1:-1, 1:-1].ravel() - ref).max() < 1e-12 * np.abs(ref).max()
+    assert np.allclose(np.diag(D), M.diag()[1:-1, 1:-1].ravel(), rtol=1e-14, atol=0)
+    jj, ii = np.meshgrid(np.arange(1, n - 1), np.arange(1, n - 1), indexing="ij")
+    red = ((ii + jj) % 2 == 0).ravel()
+    Pr, Pb = np.diag(red.astype(float)), np.diag((~red).astype(float))
+    om = 1.05
+    v = ui + om * Pr @ Dinv @ (fi - D @ ui)
+    v = v + om * Pb @ Dinv @ (fi - D @ v)
+    got = M.rbjacobi(f, u, om, 1)[1:-1, 1:-1].ravel()
+    assert np.abs(got - v).max() < 1e-12 * np.abs(v).max()
+
+
+def _propagator(oracle, mg_levels, l, gf, gc, nu1, nu2, omega, smoother):
+    """Error propagator of Algorithm 1 at level l (dense, interior unknowns).
+    E_l = S^nu2 (I - P (I - prod_i E_{l+1}^{(i)}) M_{l+1}^{-1} R M_l) S^nu1, where the coarse
+    product runs over the gamma_c recursive calls (first with (gf, gc), later (gc, gf)) and
+    E_C = 0 at the coarsest level, whose solve is exact."""
+    ops, Rs, Ps = mg_levels
+    M = ops[l]
+    if l == len(ops) - 1:
+        return np.zeros_like(M)
+    Dinv = np.diag(1 / np.diag(M))
+    I = np.eye(M.shape[0])
+    if smoother == "jacobi":
+        S = I - omega * Dinv @ M
+    else:
+        red = ops_red[l]
+        Sr = I - omega * np.diag(red.astype(float)) @ Dinv @ M
+        Sb = I - omega * np.diag((~red).astype(float)) @ Dinv @ M
+        S = Sb @ Sr
+    Mc = ops[l + 1]
+    if l + 1 == len(ops) - 1:
+        Ec = np.zeros_like(Mc)
+    else:
+        Ec = np.eye(Mc.shape[0])
+        for i in range(1, gc + 1):
+            a, b = (gf, gc) if i == 1 else (gc, gf)
+            Ec = _propagator(oracle, mg_levels, l + 1, a, b, nu1, nu2, omega, smoother) @ Ec
+    cgc = I - Ps[l] @ (np.eye(Mc.shape[0]) - Ec) @ np.linalg.solve(Mc, Rs[l] @ M)
+    return np.linalg.matrix_power(S, nu2) @ cgc @ np.linalg.matrix_power(S, nu1)
+
+
+ops_red = {}
+
+
+@pytest.mark.parametrize("n,cyc,nu,smoother", [
+    (9, (1, 1), (2, 2), "jacobi"),
+    (17, (1, 1), (2, 2), "jacobi"),
+    (17, (1, 2), (1, 1), "jacobi"),
+    (17, (2, 2), (1, 1), "rb"),
+    (33, (1, 3), (1, 1), "jacobi"),
+])
+def test_cycle_equals_error_propagator(oracle, n, cyc, nu, smoother):
+    """One cycle of Algorithm 1 from u0 equals E u0 + (I - E) M^{-1} b, with E the textbook
+    two-/multi-level error propagator written from the smoother, FW, bilinear interpolation and
+    exact coarsest solve (V, F and W cycles through gamma_f, gamma_c)."""
+    omega = 0.8 if smoother == "jacobi" else 1.0
+    z = oracle.axes(2, n)
+    k2 = W.k2_well_growth(2, n, kh_max=0.3)
+    _, M = oracle.helmholtz_ops(z, k2, pc="csl", beta=(-1.0, -0.5))
+    mg = oracle.MG(M, 5, nu[0], nu[1], omega, smoother)
+    shapes = [mg.level_shape(l) for l in range(mg.nlev)]
+    assert shapes[-1] == (5, 5)
+    ops, Rs, Ps = [], [], []
+    zl, k2l = z, k2
+    for l, sh in enumerate(shapes):
+        Ml = oracle.Op(zl, k2l, a=M.a, bk=M.bk, c=M.c, ts=M.ts)
+        ops.append(Ml.dense())
+        nl = sh[0]
+        jj, ii = np.meshgrid(np.arange(1, nl - 1), np.arange(1, nl - 1), indexing="ij")
+        ops_red[l] = ((ii + jj) % 2 == 0).ravel()
+        if l + 1 < len(shapes):
+            R1, P1 = _fw_1d(nl), _lin_1d(nl)
+            R, P = np.kron(R1, R1), np.kron(P1, P1)
+            nc = (nl + 1) // 2
+            fm = np.zeros((nl, nl), bool)
+            fm[1:-1, 1:-1] = True
+            cm = np.zeros((nc, nc), bool)
+            cm[1:-1, 1:-1] = True
+            fi, ci = np.flatnonzero(fm.ravel()), np.flatnonzero(cm.ravel())
+            Rs.append(R[np.ix_(ci, fi)])
+            Ps.append(P[np.ix_(fi, ci)])
+            zl = [zz[::2] for zz in zl]
+            k2l = k2l[::2, ::2]
+    E = _propagator(oracle, (ops, Rs, Ps), 0, cyc[0], cyc[1], nu[0], nu[1], omega, smoother)
+    b = W.random_field((n, n), 31)
+    u0 = W.random_field((n, n), 32)
+    got = mg.cycle(b, u0, *cyc)[1:-1, 1:-1].ravel()
+    ustar = np.linalg.solve(ops[0], b[1:-1, 1:-1].ravel())
+    ref = E @ u0[1:-1, 1:-1].ravel() + ustar - E @ ustar
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_3d_two_level_cycle(oracle):
+    """3D two-level V(1,1): FW (1,2,1)^3/64, trilinear interpolation, exact coarse solve."""
+    n = 9
+    z = oracle.axes(3, n)
+    k2 = W.k2_well_growth(3, n, kh_max=0.3)
+    _, M = oracle.helmholtz_ops(z, k2, pc="csg")
+    mg = oracle.MG(M, 5, 1, 1, 0.8, "jacobi")
+    assert mg.nlev == 2
+    Md = M.dense()
+    Mc = oracle.Op([zz[::2] for zz in z], k2[::2, ::2, ::2], a=M.a, bk=M.bk, c=M.c, ts=M.ts).dense()
+    R1, P1 = _fw_1d(n), _lin_1d(n)
+    R, P = np.kron(np.kron(R1, R1), R1), np.kron(np.kron(P1, P1), P1)
+    fm = np.zeros((n,) * 3, bool)
+    fm[1:-1, 1:-1, 1:-1] = True
+    cm = np.zeros((5,) * 3, bool)
+    cm[1:-1, 1:-1, 1:-1] = True
+    fi, ci = np.flatnonzero(fm.ravel()), np.flatnonzero(cm.ravel())
+    R, P = R[np.ix_(ci, fi)], P[np.ix_(fi, ci)]
+    I = np.eye(Md.shape[0])
+    S = I - 0.8 * np.diag(1 / np.diag(Md)) @ Md
+    E = S @ (I - P @ np.linalg.solve(Mc, R @ Md)) @ S
+    b = W.random_field((n,) * 3, 41)
+    got = mg.cycle(b)[fm]
+    ustar = np.linalg.solve(Md, b[fm])
+    ref = ustar - E @ ustar
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ dense LU, Krylov
+
+def test_lu_matches_numpy(oracle):
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((40, 40)) + 1j * rng.standard_normal((40, 40))
+    b = rng.standard_normal(40) + 1j * rng.standard_normal(40)
+    assert np.allclose(oracle.lu_solve(A, b), np.linalg.solve(A, b), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("pc", ["csg", "csl", "laplace"])
+def test_fgmres_reaches_dense_solution(oracle, pc):
+    """FGMRES with one MG cycle as preconditioner reaches the dense-LU solution u = A^{-1} f;
+    the Arnoldi estimate |g_{j+1}| is non-increasing within a cycle and the last one agrees
+    with the true residual."""
+    P = W.config_small(33)
+    z = oracle.axes(2, P.n)
+    A, M = oracle.helmholtz_ops(z, P.k2, pc=pc)
+    mg = oracle.MG(M, 17, 2, 2, 0.8)
+    x, st = oracle.fgmres(A, mg, P.f, tol=1e-10, restart=30, maxit=400, history=True)
+    assert st["status"] == 0 and st["rel_res"] <= 1.5e-10
+    ref = np.zeros_like(P.f)
+    ref[1:-1, 1:-1] = np.linalg.solve(A.dense(), P.f[1:-1, 1:-1].ravel()).reshape(P.n - 2, P.n - 2)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-8
+    h = st["history"]
+    first = h[: min(30, h.size)]
+    assert np.all(np.diff(first) <= 1e-12)
+
+
+def test_gmres_full_krylov_space(oracle):
+    """Unpreconditioned GMRES with restart >= n_u converges in at most n_u steps, and its last
+    Arnoldi estimate equals the true residual."""
+    n = 7
+    z = oracle.axes(2, n)
+    A, _ = oracle.helmholtz_ops(z, W.k2_well_growth(2, n, kh_max=0.5), pc="none")
+    f = W.random_field((n, n), 5)
+    x, st = oracle.fgmres(A, None, f, tol=1e-12, restart=30, maxit=30, history=True)
+    assert st["iterations"] <= (n - 2) ** 2 and st["status"] == 0
+    assert abs(st["history"][-1] - st["rel_res"]) < 1e-10
+
+
+def test_bicgstab_reaches_dense_solution(oracle):
+    P = W.config_small(33)
+    z = oracle.axes(2, P.n)
+    A, M = oracle.helmholtz_ops(z, P.k2, pc="csg")
+    mg = oracle.MG(M, 17, 2, 2, 0.8)
+    x, st = oracle.bicgstab(A, mg, P.f, tol=1e-10, maxit=400)
+    assert st["status"] == 0 and st["rel_res"] <= 1e-10
+    ref = np.zeros_like(P.f)
+    ref[1:-1, 1:-1] = np.linalg.solve(A.dense(), P.f[1:-1, 1:-1].ravel()).reshape(P.n - 2, P.n - 2)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-8
+
+
+def test_mg_conv_poisson(oracle):
+    """mg-conv (Section 5) for the definite Laplacian: a V(2,2) omega-Jacobi cycle contracts
+    well below 0.3 (textbook Poisson multigrid), and the reported factor is the geometric mean
+    of the last five residual reductions."""
+    n = 65
+    z = oracle.axes(2, n, theta=0.0)
+    M = oracle.Op(z, 0.0, a=1.0, bk=0.0, c=0.0)
+    mg = oracle.MG(M, 17, 2, 2, 0.8)
+    b = W.random_field((n, n), 9)
+    ncyc, fac, hist = mg.mg_conv(b, tol=1e-8, maxcyc=60)
+    assert fac < 0.3
+    assert abs(fac - (hist[-1] / hist[-6]) ** 0.2) < 1e-12
+
+
+# ------------------------------------------------------------------ adjoint (R7, R15)
+
+def test_adjoint_gradient_dense(oracle):
+    """L = |sum_p g_p u_p|^2 with A u = f.  dL/dk2_p = Re(lambda_p u_p) with A^T lambda =
+    conj(2 s g), s = sum g u; and A^T = W A W^{-1}.  Checked against central differences of L
+    with dense solves."""
+    n = 9
+    z = oracle.axes(2, n)
+    k2 = W.k2_well_growth(2, n, kh_max=0.5)
+    f = W.random_field((n, n), 51)
+    g = W.random_field((n, n), 52).real
+    A, _ = oracle.helmholtz_ops(z, k2, pc="none")
+    Ad = A.dense()
+    fi, gi = f[1:-1, 1:-1].ravel(), g[1:-1, 1:-1].ravel()
+    u = np.linalg.solve(Ad, fi)
+    s = gi @ u
+    lam = np.linalg.solve(Ad.T, np.conj(2 * s * gi))
+    wts = A.weights()[1:-1, 1:-1].ravel()
+    lam_w = wts * np.linalg.solve(Ad, np.conj(2 * s * gi) / wts)
+    assert np.abs(lam - lam_w).max() <= 1e-10 * np.abs(lam).max()
+    grad = np.real(lam * u)
+    eps = 1e-6
+    for p in (0, 10, 24, 40):
+        k2p, k2m = k2.copy(), k2.copy()
+        ii = np.flatnonzero(np.pad(np.ones((n - 2, n - 2), bool), 1).ravel())[p]
+        k2p.ravel()[ii] += eps
+        k2m.ravel()[ii] -= eps
+        Lp = abs(gi @ np.linalg.solve(oracle.Op(z, k2p).dense(), fi)) ** 2
+        Lm = abs(gi @ np.linalg.solve(oracle.Op(z, k2m).dense(), fi)) ** 2
+        fd = (Lp - Lm) / (2 * eps)
+        assert abs(fd - grad[p]) <= 1e-6 * max(abs(fd), np.abs(grad).max() * 1e-3)

@@ -1,0 +1,202 @@
+/*
+ * helm.h -- C-ABI of libhelm.so: a GB300 (sm_103a) matrix-free solver for the complex
+ * Helmholtz equation  (-Delta - k^2(x)) u = f  with exterior-complex-scaled absorbing layers,
+ * preconditioned by a geometric multigrid cycle that approximately inverts a complex-scaled-
+ * grid (CSG), complex-shifted-Laplacian (CSL), quadrant-definite (QD) or Laplacian operator,
+ * inside flexible GMRES or Bi-CGSTAB.
+ *
+ * Method: H. bin Zubair, B. Reps, W. Vanroose, "A preconditioned iterative solver for the
+ * scattering solutions of the Schroedinger equation" (arXiv 1012.4307):
+ *   - model problem, eq. (2.1)-(2.2) with l1 = l2 = 0;
+ *   - ECS contour (Section 3.1) and the three-point FD formula for unequal complex widths
+ *     (Section 3.2);
+ *   - preconditioning operators M_CSL, M_CSG, M_QD (Section 5, and eq. (4.1) for QD);
+ *   - multigrid components and the cycle MG(l, A, b, u, nu1, nu2, C, gamma_f, gamma_c)
+ *     (Section 4.2, Algorithm 1);
+ *   - Bi-CGSTAB with one cycle per preconditioner call (Section 5) and (restarted) GMRES
+ *     (Section 6).
+ *
+ * Conventions for every call:
+ *   - Grid vectors are DEVICE pointers to n0*n1*n2 interleaved complex values (re, im), x
+ *     fastest (index i + n0*(j + n1*k)), INCLUDING the Dirichlet boundary nodes.  The library
+ *     never reads unknowns from, nor writes, the boundary nodes of caller vectors; callers keep
+ *     them at zero.  HELM_C128 vectors are arrays of {double re, im} (16-byte aligned),
+ *     HELM_C64 vectors arrays of {float re, im} (8-byte aligned).
+ *   - The caller owns every vector it passes.  The library owns the workspace a handle
+ *     allocates (levels, Krylov basis) from helm_create to helm_destroy.
+ *   - All device work is ordered on the CUDA stream given at creation.  Calls that return
+ *     statistics or a convergence decision synchronise that stream; helm_apply, mg_vcycle and
+ *     helm_grad_k2 do not.
+ *   - Every entry point returns a helm_status; nothing throws across the ABI.  On failure,
+ *     helm_last_error() returns a message for the calling thread.  A CUDA error maps to
+ *     HELM_ERR_CUDA; an argument error leaves all outputs untouched.
+ *   - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HELM_OK = 0,
+    HELM_ERR_ARG = 1,        /* invalid argument (sizes, pointers, parameters)          */
+    HELM_ERR_CUDA = 2,       /* a CUDA runtime call or kernel launch failed             */
+    HELM_ERR_NOMEM = 3,      /* device or host allocation failed                        */
+    HELM_ERR_NOCONV = 4,     /* iteration cap reached before the tolerance              */
+    HELM_ERR_BREAKDOWN = 5,  /* Krylov breakdown (Bi-CGSTAB rho = 0, omega = 0, ...)    */
+    HELM_ERR_NONFINITE = 6,  /* a residual norm became NaN or Inf                       */
+    HELM_ERR_TIMEOUT = 7     /* a device-side wait gave up after its iteration limit    */
+} helm_status;
+
+typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_prec;
+
+/* Preconditioning operator inverted by the multigrid cycle (Section 5):
+ *   CSG:     M = Z on the grid whose mesh widths are all multiplied by e^{i theta_a};
+ *   CSL:     M = -Delta + (beta1 + i beta2) k^2;
+ *   QD:      M = (1 - i) I + Z / |Re lambda0|   (eq. (4.1) in the table form of Section 5);
+ *   LAPLACE: M = -Delta;
+ *   NONE:    no preconditioner (Krylov solvers only).
+ * Z = -Delta - k^2 is the Helmholtz operator of eq. (2.1), discretised on the ECS grid. */
+typedef enum { HELM_PC_NONE = 0, HELM_PC_CSG = 1, HELM_PC_CSL = 2, HELM_PC_QD = 3, HELM_PC_LAPLACE = 4 } helm_pc_kind;
+
+typedef enum { HELM_OP_A = 0, HELM_OP_M = 1 } helm_op;                   /* A = Z, M = preconditioner */
+typedef enum { HELM_FGMRES = 0, HELM_BICGSTAB = 1 } helm_krylov;
+typedef enum { HELM_SMOOTH_JACOBI = 0, HELM_SMOOTH_RB = 1 } helm_smoother;
+
+/* Uniform real grid: n[a] nodes on [lo[a], hi[a]] per axis, boundary nodes included
+ * (n - 2 unknowns per axis).  dim is 2 or 3; unused entries are ignored. */
+typedef struct {
+    int dim;
+    int n[3];
+    double lo[3], hi[3];
+} helm_grid;
+
+/* Multigrid cycle and preconditioner parameters (Section 4.2, Algorithm 1, Tables 1-4). */
+typedef struct {
+    helm_pc_kind kind;
+    double theta_a;            /* CSG width rotation (e.g. pi/14)                     */
+    double beta1, beta2;       /* CSL shift (e.g. -1, -0.5)                           */
+    double re_lambda0;         /* QD: Re of the leftmost eigenvalue of Z (nonzero)    */
+    int nu1, nu2;              /* pre- and post-smoothing steps (>= 0)                */
+    double omega;              /* relaxation weight                                   */
+    helm_smoother smoother;    /* omega-Jacobi or omega-red-black Jacobi              */
+    int gamma_f, gamma_c;      /* cycle indices: (1,1) V, (1,2) F, (2,2) W            */
+    int coarsest_n;            /* coarsen while some axis has more nodes than this    */
+    helm_prec prec;            /* arithmetic of the cycle inside krylov_solve         */
+} helm_mg_params;
+
+/* Solver statistics (host struct, filled by the solvers). */
+typedef struct {
+    int iterations;            /* Krylov iterations (FGMRES inner steps or Bi-CGSTAB steps) */
+    int restarts;              /* FGMRES cycles started                                     */
+    int status;                /* helm_status of the solve                                  */
+    double rel_res;            /* final true ||f - A x||_2 / ||f||_2 in FP64                */
+    double est_res;            /* last recursive / Arnoldi residual estimate (relative)     */
+    double time_ms;            /* host wall time of the call                                */
+    double *history;           /* optional caller array: estimate per iteration            */
+    int history_len;           /* capacity of history (0 if none)                           */
+} helm_stats;
+
+typedef struct helm_handle helm_handle;
+typedef struct helm_batch helm_batch;
+
+/* Creates a solver for Z = -Delta - k^2 on the ECS grid of Section 3.1 and the multigrid
+ * hierarchy of its preconditioner (Section 4.2: rediscretisation on every coarse level, k^2
+ * injected; coarsest level inverted exactly, Algorithm 1 step (0)).
+ *   grid     host: geometry; every n[a] odd so that the levels nest.
+ *   theta    ECS angle: beyond r0_hi[a] the contour is z = r0 + (x - r0) e^{i theta}, and the
+ *            mirror image below r0_lo[a] (linear ECS, widths h e^{i theta}).  A side whose r0
+ *            lies outside [lo, hi] has no layer (plain Dirichlet).
+ *   r0_lo, r0_hi  host arrays of dim entries.
+ *   k2       DEVICE pointer to n0*n1*n2 doubles (k^2 at the real nodes; boundary ignored).
+ *            Copied; the caller may free it after the call returns.
+ *   mg       host: preconditioner and cycle parameters.
+ *   stream   cudaStream_t (NULL = legacy default stream) on which all work is ordered.
+ *   out      receives the handle.
+ * Errors: HELM_ERR_ARG (bad sizes/parameters, singular coarsest operator), HELM_ERR_NOMEM,
+ * HELM_ERR_CUDA. */
+helm_status helm_create(const helm_grid *grid, double theta, const double *r0_lo, const double *r0_hi,
+                        const double *k2, const helm_mg_params *mg, void *stream, helm_handle **out);
+
+void helm_destroy(helm_handle *h);
+
+/* y = A x or y = M x on the finest grid (Section 3.2 stencil, the operators of Section 5):
+ *   (M x)_p = a * sum_axes (cw x_{p-e} + cc x_p + ce x_{p+e}) + (bk k^2_p + c) x_p,
+ * cw = -2/((h_{j-1}+h_j) h_{j-1}), ce = -2/((h_{j-1}+h_j) h_j), cc = -(cw + ce).
+ * x, y: DEVICE vectors of precision prec; y's interior is overwritten, its boundary untouched.
+ * x and y must not overlap. */
+helm_status helm_apply(helm_handle *h, helm_op which, helm_prec prec, const void *x, void *y);
+
+/* One multigrid cycle of Algorithm 1 for M x = b on the finest grid, with the handle's
+ * (nu1, nu2, omega, smoother, gamma_f, gamma_c).
+ *   b   DEVICE right-hand side (precision prec), unchanged.
+ *   x   DEVICE initial guess on entry, cycle result on exit (precision prec).
+ * b and x must not overlap. */
+helm_status mg_vcycle(helm_handle *h, const void *b, void *x, helm_prec prec);
+
+/* Solves A x = rhs (A = Z, FP64) to ||rhs - A x|| <= tol ||rhs||, right-preconditioned by one
+ * multigrid cycle on M in the precision mg->prec (a complex64 cycle inside FP64 FGMRES, or all
+ * FP64).  FGMRES(restart) (Saad's flexible GMRES, classical Gram-Schmidt with one
+ * re-orthogonalisation, complex Givens rotations, all in FP64 on the device) or Bi-CGSTAB with
+ * two cycles per iteration (Section 5).
+ *   rhs   DEVICE c128, unchanged.       x  DEVICE c128: initial guess in, solution out.
+ *   tol   relative tolerance (> 0).     restart  FGMRES basis size (1..64; ignored by Bi-CGSTAB).
+ *   maxit total iteration cap (> 0).    stats    optional host struct.
+ * Returns HELM_OK when converged (confirmed by the FP64 true residual), HELM_ERR_NOCONV at the
+ * cap, HELM_ERR_BREAKDOWN, HELM_ERR_NONFINITE; x holds the last iterate in every case. */
+helm_status krylov_solve(helm_handle *h, helm_krylov method, const void *rhs, void *x, double tol,
+                         int restart, int maxit, helm_stats *stats);
+
+/* Adjoint solve A^T lambda = rhs (plain transpose).  The ECS FD matrix satisfies
+ * (W A)^T = W A with W = prod_axes (h_{j-1} + h_j)/2 (complex dual volumes), so
+ * lambda = W * A^{-1} (W^{-1} rhs) reuses the forward operator and its preconditioner.
+ *   rhs DEVICE c128 (unchanged), lambda DEVICE c128 (initial guess ignored; overwritten). */
+helm_status helm_solve_adjoint(helm_handle *h, const void *rhs, void *lambda, double tol, int restart,
+                               int maxit, helm_stats *stats);
+
+/* grad_p = Re(lambda_p * u_p) on interior nodes (0 on the boundary): the derivative of a real
+ * loss L(u) with respect to k^2_p when A u = f and A^T lambda = conj(dL/du) (conjugate
+ * Wirtinger convention), since dA/dk^2_p = -e_p e_p^T.
+ *   lambda, u DEVICE c128; grad DEVICE double[n0*n1*n2]. */
+helm_status helm_grad_k2(helm_handle *h, const void *lambda, const void *u, double *grad);
+
+/* Stand-alone multigrid on M x = b from x = 0 (Section 5, "mg-conv"): repeats cycles until
+ * ||b - M x|| <= tol ||b|| or maxcyc cycles; returns the cycle count and the geometric mean of
+ * the residual reduction over the last five cycles.
+ *   b DEVICE (precision prec), x DEVICE (precision prec, overwritten). */
+helm_status helm_mg_conv(helm_handle *h, const void *b, void *x, helm_prec prec, double tol, int maxcyc,
+                         int *ncycles, double *factor);
+
+/* Number of levels and nodes per axis of level l (host query). */
+helm_status helm_levels(const helm_handle *h, int *nlev);
+helm_status helm_level_shape(const helm_handle *h, int level, int n[3]);
+
+/* ---- batched solves: many independent problems (energies, right-hand sides, grid sizes) ----
+ * helm_create_batch builds one handle per problem (shared stream); helm_solve_batch runs every
+ * problem's FGMRES with a complex64 multigrid preconditioner, the per-iteration work of all
+ * problems fused into shared launches (one launch per kernel kind per level depth across the
+ * batch), replayed from CUDA graphs.
+ *   grids, theta, r0 (2*dim per problem: lo then hi), k2 (device pointers): arrays of nprob.
+ *   rhs, x: arrays of nprob DEVICE c128 pointers.  stats: nprob host structs (optional). */
+helm_status helm_create_batch(int nprob, const helm_grid *grids, const double *theta, const double *r0,
+                              const double *const *k2, const helm_mg_params *mg, void *stream,
+                              helm_batch **out);
+helm_status helm_solve_batch(helm_batch *b, const void *const *rhs, void *const *x, double tol, int restart,
+                             int maxit, helm_stats *stats);
+void helm_destroy_batch(helm_batch *b);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *helm_last_error(void);
+
+/* Library version string. */
+const char *helm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

@@ -1,0 +1,69 @@
+// Handle layout shared by the host drivers (not part of the C-ABI).
+#pragma once
+
+#include <vector>
+
+#include "helm_internal.h"
+
+// One multigrid level of the preconditioning operator: coefficients and k^2 in both
+// precisions, and the level's work vectors (b: right-hand side / restricted residual,
+// u: iterate / coarse error, t: Jacobi ping-pong partner).
+struct LevelDev {
+    int n[3] = {1, 1, 1};
+    size_t np = 0;
+    DevOp<double> M64{};
+    DevOp<float> M32{};
+    double2 *coef64[3] = {nullptr, nullptr, nullptr};
+    float2 *coef32[3] = {nullptr, nullptr, nullptr};
+    double *k2_64 = nullptr;
+    float *k2_32 = nullptr;
+    double2 *b64 = nullptr, *u64 = nullptr, *t64 = nullptr;
+    float2 *b32 = nullptr, *u32 = nullptr, *t32 = nullptr;
+};
+
+struct helm_handle {
+    int dim = 2;
+    int n[3] = {1, 1, 1};
+    size_t np = 0;
+    helm_mg_params mg{};
+    cudaStream_t stream = nullptr;
+    bool stream_owned_sync = true;
+    std::vector<void *> owned;  // every device allocation, freed at destroy
+
+    // A = Z (Helmholtz operator, fine grid) in FP64 and (on demand) FP32
+    DevOp<double> A64{};
+    DevOp<float> A32{};
+    double2 *coefA64[3] = {nullptr, nullptr, nullptr};
+    float2 *coefA32[3] = {nullptr, nullptr, nullptr};
+    double *k2A = nullptr;
+    double2 *wts[3] = {nullptr, nullptr, nullptr};  // dual-volume weights per axis
+
+    std::vector<LevelDev> lv;
+    int nu_c = 0;
+    double2 *minv64 = nullptr;
+    float2 *minv32 = nullptr;
+
+    // Krylov workspace (allocated on first use, grown on demand)
+    int m_alloc = 0;
+    helm_prec z_prec = HELM_C128;
+    double2 *V = nullptr;      // (m+1) basis vectors, FP64
+    void *Z = nullptr;         // m preconditioned vectors (c64 or c128)
+    double2 *H = nullptr;      // (m+1) x m Hessenberg, column-major
+    double2 *g = nullptr, *sn = nullptr, *y = nullptr, *h2 = nullptr;
+    double *cs = nullptr;
+    double2 *partials = nullptr;
+    double2 *scal = nullptr;   // scalar scratch (norms, Bi-CGSTAB scalars)
+    double *est_dev = nullptr;
+    double *est_host = nullptr;  // pinned
+    // Bi-CGSTAB workspace
+    bool bicg_alloc = false;
+    double2 *br = nullptr, *brh = nullptr, *bp = nullptr, *bv = nullptr, *bs = nullptr, *bt = nullptr;
+    void *by = nullptr, *bz = nullptr;
+    // adjoint temporaries
+    double2 *adj_rhs = nullptr, *adj_y = nullptr;
+    std::vector<void *> krylov_owned;
+};
+
+helm_status helm_fail(helm_status st, const char *fmt, ...);
+void helm_free_krylov(helm_handle *h);
+template <typename R> cudaError_t precondition(helm_handle *h, const double2 *v, typename CT<R>::T *z);

@@ -1,0 +1,137 @@
+// Internal declarations shared by the libhelm translation units (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/helm.h"
+
+// ------------------------------------------------------------------------------ complex
+template <typename R> struct CT;
+template <> struct CT<float> { typedef float2 T; };
+template <> struct CT<double> { typedef double2 T; };
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc + a*b
+template <typename C> __host__ __device__ __forceinline__ C cfma(C a, C b, C acc) {
+    return mk(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+// acc + conj(a)*b
+template <typename C> __host__ __device__ __forceinline__ C cfmac(C a, C b, C acc) {
+    return mk(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
+// 1 / a
+template <typename C> __host__ __device__ __forceinline__ C cinv(C a) {
+    auto d = a.x * a.x + a.y * a.y;
+    return mk(a.x / d, -a.y / d);
+}
+__device__ __forceinline__ float2 to_c(float2 v, float) { return v; }
+__device__ __forceinline__ float2 to_c(double2 v, float) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ double2 to_c(float2 v, double) { return make_double2((double)v.x, (double)v.y); }
+__device__ __forceinline__ double2 to_c(double2 v, double) { return v; }
+
+// ------------------------------------------------------------------------------ operator
+// One discrete operator on one level:
+//   (M x)_p = sum_axes (cw x_{p-e} + cc x_p + ce x_{p+e}) + (bk k2_p + c) x_p,
+// with the operator scale a already folded into the per-axis coefficient triples
+// coef[ax][3*j + {0,1,2}] = (cw, cc, ce) at node j of axis ax.
+template <typename R> struct DevOp {
+    typedef typename CT<R>::T C;
+    int n[3];
+    const C *coef[3];
+    const R *k2;
+    C bk, c;
+};
+
+// Kernel launch geometry helpers
+static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------------------ launchers
+// All return cudaGetLastError() of their launch.  R = float or double; dim = 2 or 3.
+// Vectors are full node arrays (boundary included).
+template <typename R, typename CX>
+cudaError_t launch_apply(const DevOp<R> &op, int dim, const CX *x, typename CT<R>::T *y, cudaStream_t s);
+template <typename R, typename CB>
+cudaError_t launch_residual(const DevOp<R> &op, int dim, const CB *b, const typename CT<R>::T *u,
+                            typename CT<R>::T *r, cudaStream_t s);
+// u_out = u_in + omega (b - M u_in) / diag(M); u_in == nullptr means u_in = 0.
+template <typename R, typename CB>
+cudaError_t launch_jacobi(const DevOp<R> &op, int dim, R omega, const CB *b, const typename CT<R>::T *u_in,
+                          typename CT<R>::T *u_out, cudaStream_t s);
+// one colour of omega-red-black Jacobi, in place; colour 0 = (i+j+k) even.
+template <typename R, typename CB>
+cudaError_t launch_rb(const DevOp<R> &op, int dim, R omega, const CB *b, typename CT<R>::T *u, int colour,
+                      cudaStream_t s);
+// rc = FW(b - M u) on the coarse grid (fine nodes op.n, coarse nodes (n+1)/2).
+template <typename R, typename CB>
+cudaError_t launch_residual_restrict(const DevOp<R> &op, int dim, const CB *b, const typename CT<R>::T *u,
+                                     typename CT<R>::T *rc, cudaStream_t s);
+// uf += P ec (fine nodes nf).
+template <typename R>
+cudaError_t launch_prolong_add(const int nf[3], int dim, const typename CT<R>::T *ec, typename CT<R>::T *uf,
+                               cudaStream_t s);
+// u = Minv b on the interior unknowns of the coarsest grid (nodes n), natural order.
+template <typename R>
+cudaError_t launch_dense_solve(const int n[3], int dim, int nu, const typename CT<R>::T *minv,
+                               const typename CT<R>::T *b, typename CT<R>::T *u, cudaStream_t s);
+template <typename CI, typename CO>
+cudaError_t launch_convert(size_t n, const CI *in, CO *out, cudaStream_t s);
+template <typename C>
+cudaError_t launch_zero(size_t n, C *x, cudaStream_t s);
+
+// FP64 vector kernels on full node arrays (boundary values are zero, so sums over all nodes
+// equal sums over unknowns).
+// partial sums of conj(V_i) . w for i in [0, nv): partials[(i * nblk) + blk]
+int blas_nblocks(size_t n);
+cudaError_t launch_mdot(size_t n, const double2 *V, size_t ldv, int nv, const double2 *w, double2 *partials,
+                        cudaStream_t s);
+// w -= sum_i V_i h_i, then partials of conj(V_i) . w   (h on device)
+cudaError_t launch_update_mdot(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
+                               double2 *partials, cudaStream_t s);
+// w -= sum_i V_i h_i, then partials of ||w||^2 in .x
+cudaError_t launch_update_norm(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
+                               double2 *partials, cudaStream_t s);
+// out[i] (mode 0: =, 1: +=) sum of partials of vector i; mode 2: out[i] = (sqrt(re), 0)
+cudaError_t launch_reduce(const double2 *partials, int nblk, int nv, double2 *out, int mode, cudaStream_t s);
+// y = x * (1 / scale[0].x)
+cudaError_t launch_scale_inv(size_t n, const double2 *x, const double2 *scale, double2 *y, cudaStream_t s);
+// x += sum_c y_c Z_c  (Z c64 or c128, ldz stride)
+template <typename CZ>
+cudaError_t launch_combine(size_t n, const CZ *Z, size_t ldz, int nz, const double2 *y, double2 *x, cudaStream_t s);
+
+// FGMRES small dense work on the device (one warp): rotations of column j, new rotation,
+// residual estimate (|g_{j+1}| / fnorm) written to est[0].
+cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, double fnorm,
+                          double *est, cudaStream_t s);
+// y = H(0:k,0:k)^{-1} g(0:k)  (upper triangular back substitution)
+cudaError_t launch_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y, cudaStream_t s);
+
+// Bi-CGSTAB vector updates (FP64)
+// p = r + beta (p - omega v), beta and omega from dev scalars
+cudaError_t launch_bicg_p(size_t n, const double2 *r, const double2 *v, const double2 *sc, double2 *p,
+                          cudaStream_t s);
+// generic: y = a*x + b*y with device complex scalars a, b (pointers into a scalar block)
+cudaError_t launch_axpby(size_t n, const double2 *a, const double2 *x, const double2 *b, double2 *y,
+                         cudaStream_t s);
+template <typename CY>
+cudaError_t launch_axpy_mixed(size_t n, const double2 *a, const CY *x, double2 *y, cudaStream_t s);
+// scalar kernels of Bi-CGSTAB (device-side scalar algebra, no host round trip)
+cudaError_t launch_bicg_scalars(int stage, double2 *sc, cudaStream_t s);
+
+// adjoint helpers
+cudaError_t launch_weight(size_t n, const int nodes[3], int dim, const double2 *w_axis[3], int inverse,
+                          const double2 *x, double2 *y, cudaStream_t s);
+cudaError_t launch_grad_k2(size_t n, const int nodes[3], int dim, const double2 *lam, const double2 *u,
+                           double *grad, cudaStream_t s);

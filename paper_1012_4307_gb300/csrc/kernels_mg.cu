@@ -1,0 +1,380 @@
+// Stencil and multigrid kernels for the ECS Helmholtz operators (sm_103a).
+//
+// Operator (Section 3.2 FD formula for unequal complex widths, summed over axes, with the
+// operator coefficients of Section 5 folded in):
+//   (M x)_p = sum_axes (cw x_{p-e} + cc x_p + ce x_{p+e}) + (bk k2_p + c) x_p.
+// Multigrid components (Section 4.2): omega-Jacobi, omega-red-black Jacobi, full-weighting
+// restriction fused with the residual, bi/trilinear prolongation fused with the correction,
+// and the exact coarsest solve (Algorithm 1 step (0)) as a dense-inverse product.
+//
+// Layout: interleaved complex node arrays, x fastest, boundary included (never written).
+// Threads: 2D blocks of 32 x 8 over (i, j); in 3D every thread marches a chunk of k planes
+// keeping the x[p - nx ny], x[p], x[p + nx ny] column in registers.  Every launch covers the
+// interior only, so no thread touches a boundary node's value except as a stencil neighbour.
+#include "helm_internal.h"
+
+namespace {
+
+constexpr int BX = 32, BY = 8, KCHUNK = 8;
+
+template <typename R> struct OpView {
+    typedef typename CT<R>::T C;
+    const C *__restrict__ cx;
+    const C *__restrict__ cy;
+    const C *__restrict__ cz;
+    const R *__restrict__ k2;
+    C bk, c;
+    int nx, ny, nz;
+};
+
+template <typename R> __host__ OpView<R> view(const DevOp<R> &op) {
+    OpView<R> v;
+    v.cx = op.coef[0]; v.cy = op.coef[1]; v.cz = op.coef[2];
+    v.k2 = op.k2; v.bk = op.bk; v.c = op.c;
+    v.nx = op.n[0]; v.ny = op.n[1]; v.nz = op.n[2];
+    return v;
+}
+
+// Off-diagonal part of the stencil at p (neighbours along x and y; z handled by callers that
+// march in k) and the diagonal entry.
+template <typename R, int DIM, typename CX>
+__device__ __forceinline__ typename CT<R>::T stencil(const OpView<R> &o, const CX *__restrict__ x, size_t p,
+                                                    int i, int j, int k, typename CT<R>::T xm_z,
+                                                    typename CT<R>::T xc, typename CT<R>::T xp_z,
+                                                    typename CT<R>::T &diag) {
+    typedef typename CT<R>::T C;
+    const size_t sy = (size_t)o.nx;
+    C cw = __ldg(&o.cx[3 * i]), cc = __ldg(&o.cx[3 * i + 1]), ce = __ldg(&o.cx[3 * i + 2]);
+    C acc = cmul(cw, to_c(x[p - 1], R()));
+    acc = cfma(ce, to_c(x[p + 1], R()), acc);
+    C d = cc;
+    cw = __ldg(&o.cy[3 * j]); cc = __ldg(&o.cy[3 * j + 1]); ce = __ldg(&o.cy[3 * j + 2]);
+    acc = cfma(cw, to_c(x[p - sy], R()), acc);
+    acc = cfma(ce, to_c(x[p + sy], R()), acc);
+    d = cadd(d, cc);
+    if (DIM == 3) {
+        cw = __ldg(&o.cz[3 * k]); cc = __ldg(&o.cz[3 * k + 1]); ce = __ldg(&o.cz[3 * k + 2]);
+        acc = cfma(cw, xm_z, acc);
+        acc = cfma(ce, xp_z, acc);
+        d = cadd(d, cc);
+    }
+    d = cadd(d, cadd(cscale(o.bk, o.k2[p]), o.c));
+    diag = d;
+    return cfma(d, xc, acc);
+}
+
+// (M x)_p for a point whose z neighbours are loaded here (used by the restriction kernel).
+template <typename R, int DIM, typename CX>
+__device__ __forceinline__ typename CT<R>::T apply_point(const OpView<R> &o, const CX *__restrict__ x, int i, int j,
+                                                        int k, typename CT<R>::T &diag) {
+    typedef typename CT<R>::T C;
+    const size_t sz = (size_t)o.nx * o.ny;
+    const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
+    C xm = mk(R(0), R(0)), xp = mk(R(0), R(0));
+    if (DIM == 3) { xm = to_c(x[p - sz], R()); xp = to_c(x[p + sz], R()); }
+    return stencil<R, DIM>(o, x, p, i, j, k, xm, to_c(x[p], R()), xp, diag);
+}
+
+// Thread preamble: interior (i, j) and the k range of this thread.
+#define INTERIOR_IJ(o)                                              \
+    const int i = blockIdx.x * BX + threadIdx.x + 1;                \
+    const int j = blockIdx.y * BY + threadIdx.y + 1;                \
+    if (i > (o).nx - 2 || j > (o).ny - 2) return;                   \
+    int k0 = 0, k1 = 1;                                             \
+    if (DIM == 3) {                                                 \
+        k0 = blockIdx.z * KCHUNK + 1;                               \
+        k1 = min(k0 + KCHUNK, (o).nz - 1);                          \
+    }                                                               \
+    const size_t sz = (size_t)(o).nx * (o).ny;                      \
+    size_t p = (size_t)i + (size_t)(o).nx * ((size_t)j + (size_t)(o).ny * k0);
+
+template <typename R, int DIM, typename CX>
+__global__ void __launch_bounds__(BX *BY) k_apply(OpView<R> o, const CX *__restrict__ x, typename CT<R>::T *__restrict__ y) {
+    typedef typename CT<R>::T C;
+    INTERIOR_IJ(o);
+    C xm = mk(R(0), R(0)), xc = to_c(x[p], R()), xp = mk(R(0), R(0));
+    if (DIM == 3) xm = to_c(x[p - sz], R());
+    for (int k = k0; k < k1; k++, p += sz) {
+        if (DIM == 3) xp = to_c(x[p + sz], R());
+        C d;
+        y[p] = stencil<R, DIM>(o, x, p, i, j, k, xm, xc, xp, d);
+        if (DIM == 3) { xm = xc; xc = xp; }
+    }
+}
+
+template <typename R, int DIM, typename CB>
+__global__ void __launch_bounds__(BX *BY) k_residual(OpView<R> o, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
+                                                     typename CT<R>::T *__restrict__ r) {
+    typedef typename CT<R>::T C;
+    INTERIOR_IJ(o);
+    C xm = mk(R(0), R(0)), xc = u[p], xp = mk(R(0), R(0));
+    if (DIM == 3) xm = u[p - sz];
+    for (int k = k0; k < k1; k++, p += sz) {
+        if (DIM == 3) xp = u[p + sz];
+        C d;
+        C mu = stencil<R, DIM>(o, u, p, i, j, k, xm, xc, xp, d);
+        r[p] = csub(to_c(b[p], R()), mu);
+        if (DIM == 3) { xm = xc; xc = xp; }
+    }
+}
+
+// omega-Jacobi: every unknown from the previous iterate (ping-pong buffers).
+template <typename R, int DIM, typename CB, bool ZERO>
+__global__ void __launch_bounds__(BX *BY) k_jacobi(OpView<R> o, R omega, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
+                                                   typename CT<R>::T *__restrict__ un) {
+    typedef typename CT<R>::T C;
+    INTERIOR_IJ(o);
+    if (ZERO) {
+        for (int k = k0; k < k1; k++, p += sz) {
+            C d;
+            // diagonal only: the stencil of the zero vector
+            d = cadd(cadd(__ldg(&o.cx[3 * i + 1]), __ldg(&o.cy[3 * j + 1])), cadd(cscale(o.bk, o.k2[p]), o.c));
+            if (DIM == 3) d = cadd(d, __ldg(&o.cz[3 * k + 1]));
+            un[p] = cscale(cmul(to_c(b[p], R()), cinv(d)), omega);
+        }
+        return;
+    }
+    C xm = mk(R(0), R(0)), xc = u[p], xp = mk(R(0), R(0));
+    if (DIM == 3) xm = u[p - sz];
+    for (int k = k0; k < k1; k++, p += sz) {
+        if (DIM == 3) xp = u[p + sz];
+        C d;
+        C mu = stencil<R, DIM>(o, u, p, i, j, k, xm, xc, xp, d);
+        C res = csub(to_c(b[p], R()), mu);
+        un[p] = cadd(xc, cscale(cmul(res, cinv(d)), omega));
+        if (DIM == 3) { xm = xc; xc = xp; }
+    }
+}
+
+// one colour of omega-red-black Jacobi, in place: threads map to every other x node.
+template <typename R, int DIM, typename CB>
+__global__ void __launch_bounds__(BX *BY) k_rb(OpView<R> o, R omega, const CB *__restrict__ b, typename CT<R>::T *u, int colour) {
+    typedef typename CT<R>::T C;
+    const int t = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y + 1;
+    if (j > o.ny - 2) return;
+    int k0 = 0, k1 = 1;
+    if (DIM == 3) { k0 = blockIdx.z * KCHUNK + 1; k1 = min(k0 + KCHUNK, o.nz - 1); }
+    const size_t sz = (size_t)o.nx * o.ny;
+    for (int k = k0; k < k1; k++) {
+        const int i = 2 * t + 1 + ((1 + j + k + colour) & 1);
+        if (i > o.nx - 2) continue;
+        const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
+        C xm = mk(R(0), R(0)), xp = mk(R(0), R(0));
+        if (DIM == 3) { xm = u[p - sz]; xp = u[p + sz]; }
+        C xc = u[p];
+        C d;
+        C mu = stencil<R, DIM>(o, u, p, i, j, k, xm, xc, xp, d);
+        u[p] = cadd(xc, cscale(cmul(csub(to_c(b[p], R()), mu), cinv(d)), omega));
+    }
+}
+
+// rc[I] = sum_{d in {-1,0,1}^DIM} prod w(d) (b - M u)[2I + d],  w(0) = 1/2, w(+-1) = 1/4.
+template <typename R, int DIM, typename CB>
+__global__ void __launch_bounds__(BX *BY) k_residual_restrict(OpView<R> o, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
+                                                              typename CT<R>::T *__restrict__ rc, int ncx, int ncy, int ncz) {
+    typedef typename CT<R>::T C;
+    const int I = blockIdx.x * BX + threadIdx.x + 1;
+    const int J = blockIdx.y * BY + threadIdx.y + 1;
+    if (I > ncx - 2 || J > ncy - 2) return;
+    int K0 = 0, K1 = 1;
+    if (DIM == 3) { K0 = blockIdx.z * KCHUNK + 1; K1 = min(K0 + KCHUNK, ncz - 1); }
+    for (int K = K0; K < K1; K++) {
+        C acc = mk(R(0), R(0));
+        const int dk0 = DIM == 3 ? -1 : 0, dk1 = DIM == 3 ? 1 : 0;
+        for (int dk = dk0; dk <= dk1; dk++) {
+            const R wk = DIM == 3 ? (dk == 0 ? R(0.5) : R(0.25)) : R(1);
+            const int k = DIM == 3 ? 2 * K + dk : 0;
+#pragma unroll
+            for (int dj = -1; dj <= 1; dj++) {
+                const R wj = wk * (dj == 0 ? R(0.5) : R(0.25));
+                const int j = 2 * J + dj;
+#pragma unroll
+                for (int di = -1; di <= 1; di++) {
+                    const R w = wj * (di == 0 ? R(0.5) : R(0.25));
+                    const int i = 2 * I + di;
+                    const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
+                    C d;
+                    C mu = apply_point<R, DIM>(o, u, i, j, k, d);
+                    acc = cadd(acc, cscale(csub(to_c(b[p], R()), mu), w));
+                }
+            }
+        }
+        rc[(size_t)I + (size_t)ncx * ((size_t)J + (size_t)ncy * K)] = acc;
+    }
+}
+
+// uf[q] += average of ec over coarse nodes floor(q/2), ceil(q/2) along every axis.
+template <typename R, int DIM>
+__global__ void __launch_bounds__(BX *BY) k_prolong_add(int nx, int ny, int nz, const typename CT<R>::T *__restrict__ ec,
+                                                        typename CT<R>::T *__restrict__ uf) {
+    typedef typename CT<R>::T C;
+    const int i = blockIdx.x * BX + threadIdx.x + 1;
+    const int j = blockIdx.y * BY + threadIdx.y + 1;
+    if (i > nx - 2 || j > ny - 2) return;
+    const int ncx = (nx + 1) / 2, ncy = (ny + 1) / 2;
+    int k0 = 0, k1 = 1;
+    if (DIM == 3) { k0 = blockIdx.z * KCHUNK + 1; k1 = min(k0 + KCHUNK, nz - 1); }
+    const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
+    for (int k = k0; k < k1; k++) {
+        const int kk0 = DIM == 3 ? k >> 1 : 0, kk1 = DIM == 3 ? (k + 1) >> 1 : 0;
+        C acc = mk(R(0), R(0));
+        int cnt = 0;
+        for (int kk = kk0; kk <= kk1; kk++)
+            for (int jj = j0; jj <= j1; jj++)
+                for (int ii = i0; ii <= i1; ii++) {
+                    acc = cadd(acc, ec[(size_t)ii + (size_t)ncx * ((size_t)jj + (size_t)ncy * kk)]);
+                    cnt++;
+                }
+        const size_t p = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k);
+        uf[p] = cadd(uf[p], cscale(acc, R(1) / R(cnt)));
+    }
+}
+
+// Exact coarsest solve as u = Minv b on the unknowns (interior nodes in natural order); one
+// warp per row, fixed-order lane partial sums reduced by shuffles.
+template <typename R>
+__global__ void k_dense_solve(int nx, int ny, int nz, int dim, int nu, const typename CT<R>::T *__restrict__ minv,
+                              const typename CT<R>::T *__restrict__ b, typename CT<R>::T *__restrict__ u) {
+    typedef typename CT<R>::T C;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= nu) return;
+    const int mx = nx - 2, my = ny - 2;
+    C acc = mk(R(0), R(0));
+    for (int c = lane; c < nu; c += 32) {
+        const int ci = c % mx, cj = (c / mx) % my, ck = dim == 3 ? c / (mx * my) : -1;
+        const size_t q = (size_t)(ci + 1) + (size_t)nx * ((size_t)(cj + 1) + (size_t)ny * (ck + 1));
+        acc = cfma(minv[(size_t)warp * nu + c], b[q], acc);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) {
+        const int ri = warp % mx, rj = (warp / mx) % my, rk = dim == 3 ? warp / (mx * my) : -1;
+        u[(size_t)(ri + 1) + (size_t)nx * ((size_t)(rj + 1) + (size_t)ny * (rk + 1))] = acc;
+    }
+    (void)nz;
+}
+
+template <typename CI, typename CO>
+__global__ void k_convert(size_t n, const CI *__restrict__ in, CO *__restrict__ out) {
+    typedef decltype(out->x) RO;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        out[q] = to_c(in[q], RO());
+}
+
+template <typename C> __global__ void k_zero(size_t n, C *x) {
+    typedef decltype(x->x) R;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        x[q] = mk(R(0), R(0));
+}
+
+dim3 grid_for(const int n[3], int dim) {
+    return dim3(cdiv(n[0] - 2, BX), cdiv(n[1] - 2, BY), dim == 3 ? cdiv(n[2] - 2, KCHUNK) : 1);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ launchers
+template <typename R, typename CX>
+cudaError_t launch_apply(const DevOp<R> &op, int dim, const CX *x, typename CT<R>::T *y, cudaStream_t s) {
+    dim3 g = grid_for(op.n, dim), b(BX, BY);
+    if (dim == 3) k_apply<R, 3, CX><<<g, b, 0, s>>>(view(op), x, y);
+    else k_apply<R, 2, CX><<<g, b, 0, s>>>(view(op), x, y);
+    return cudaGetLastError();
+}
+
+template <typename R, typename CB>
+cudaError_t launch_residual(const DevOp<R> &op, int dim, const CB *bb, const typename CT<R>::T *u,
+                            typename CT<R>::T *r, cudaStream_t s) {
+    dim3 g = grid_for(op.n, dim), b(BX, BY);
+    if (dim == 3) k_residual<R, 3, CB><<<g, b, 0, s>>>(view(op), bb, u, r);
+    else k_residual<R, 2, CB><<<g, b, 0, s>>>(view(op), bb, u, r);
+    return cudaGetLastError();
+}
+
+template <typename R, typename CB>
+cudaError_t launch_jacobi(const DevOp<R> &op, int dim, R omega, const CB *bb, const typename CT<R>::T *u_in,
+                          typename CT<R>::T *u_out, cudaStream_t s) {
+    dim3 g = grid_for(op.n, dim), b(BX, BY);
+    if (u_in == nullptr) {
+        if (dim == 3) k_jacobi<R, 3, CB, true><<<g, b, 0, s>>>(view(op), omega, bb, u_in, u_out);
+        else k_jacobi<R, 2, CB, true><<<g, b, 0, s>>>(view(op), omega, bb, u_in, u_out);
+    } else {
+        if (dim == 3) k_jacobi<R, 3, CB, false><<<g, b, 0, s>>>(view(op), omega, bb, u_in, u_out);
+        else k_jacobi<R, 2, CB, false><<<g, b, 0, s>>>(view(op), omega, bb, u_in, u_out);
+    }
+    return cudaGetLastError();
+}
+
+template <typename R, typename CB>
+cudaError_t launch_rb(const DevOp<R> &op, int dim, R omega, const CB *bb, typename CT<R>::T *u, int colour,
+                      cudaStream_t s) {
+    dim3 g(cdiv((op.n[0] - 1) / 2, BX), cdiv(op.n[1] - 2, BY), dim == 3 ? cdiv(op.n[2] - 2, KCHUNK) : 1), b(BX, BY);
+    if (dim == 3) k_rb<R, 3, CB><<<g, b, 0, s>>>(view(op), omega, bb, u, colour);
+    else k_rb<R, 2, CB><<<g, b, 0, s>>>(view(op), omega, bb, u, colour);
+    return cudaGetLastError();
+}
+
+template <typename R, typename CB>
+cudaError_t launch_residual_restrict(const DevOp<R> &op, int dim, const CB *bb, const typename CT<R>::T *u,
+                                     typename CT<R>::T *rc, cudaStream_t s) {
+    int nc[3] = {(op.n[0] + 1) / 2, (op.n[1] + 1) / 2, dim == 3 ? (op.n[2] + 1) / 2 : 1};
+    dim3 g = grid_for(nc, dim), b(BX, BY);
+    if (dim == 3) k_residual_restrict<R, 3, CB><<<g, b, 0, s>>>(view(op), bb, u, rc, nc[0], nc[1], nc[2]);
+    else k_residual_restrict<R, 2, CB><<<g, b, 0, s>>>(view(op), bb, u, rc, nc[0], nc[1], nc[2]);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_prolong_add(const int nf[3], int dim, const typename CT<R>::T *ec, typename CT<R>::T *uf,
+                               cudaStream_t s) {
+    dim3 g = grid_for(nf, dim), b(BX, BY);
+    if (dim == 3) k_prolong_add<R, 3><<<g, b, 0, s>>>(nf[0], nf[1], nf[2], ec, uf);
+    else k_prolong_add<R, 2><<<g, b, 0, s>>>(nf[0], nf[1], 1, ec, uf);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_dense_solve(const int n[3], int dim, int nu, const typename CT<R>::T *minv,
+                               const typename CT<R>::T *b, typename CT<R>::T *u, cudaStream_t s) {
+    const int threads = 256, warps = threads / 32;
+    k_dense_solve<R><<<cdiv(nu, warps), threads, 0, s>>>(n[0], n[1], dim == 3 ? n[2] : 1, dim, nu, minv, b, u);
+    return cudaGetLastError();
+}
+
+template <typename CI, typename CO>
+cudaError_t launch_convert(size_t n, const CI *in, CO *out, cudaStream_t s) {
+    k_convert<CI, CO><<<(unsigned)std::min<size_t>(cdiv(n, 256), 152 * 16), 256, 0, s>>>(n, in, out);
+    return cudaGetLastError();
+}
+
+template <typename C> cudaError_t launch_zero(size_t n, C *x, cudaStream_t s) {
+    k_zero<C><<<(unsigned)std::min<size_t>(cdiv(n, 256), 152 * 16), 256, 0, s>>>(n, x);
+    return cudaGetLastError();
+}
+
+#define INST_R(R)                                                                                               \
+    template cudaError_t launch_residual<R, CT<R>::T>(const DevOp<R> &, int, const CT<R>::T *, const CT<R>::T *, \
+                                                       CT<R>::T *, cudaStream_t);                               \
+    template cudaError_t launch_jacobi<R, CT<R>::T>(const DevOp<R> &, int, R, const CT<R>::T *, const CT<R>::T *, \
+                                                     CT<R>::T *, cudaStream_t);                                 \
+    template cudaError_t launch_rb<R, CT<R>::T>(const DevOp<R> &, int, R, const CT<R>::T *, CT<R>::T *, int,     \
+                                                 cudaStream_t);                                                 \
+    template cudaError_t launch_residual_restrict<R, CT<R>::T>(const DevOp<R> &, int, const CT<R>::T *,          \
+                                                                const CT<R>::T *, CT<R>::T *, cudaStream_t);    \
+    template cudaError_t launch_prolong_add<R>(const int *, int, const CT<R>::T *, CT<R>::T *, cudaStream_t);    \
+    template cudaError_t launch_dense_solve<R>(const int *, int, int, const CT<R>::T *, const CT<R>::T *,        \
+                                                CT<R>::T *, cudaStream_t);
+INST_R(float)
+INST_R(double)
+template cudaError_t launch_apply<double, double2>(const DevOp<double> &, int, const double2 *, double2 *, cudaStream_t);
+template cudaError_t launch_apply<double, float2>(const DevOp<double> &, int, const float2 *, double2 *, cudaStream_t);
+template cudaError_t launch_apply<float, float2>(const DevOp<float> &, int, const float2 *, float2 *, cudaStream_t);
+template cudaError_t launch_convert<double2, float2>(size_t, const double2 *, float2 *, cudaStream_t);
+template cudaError_t launch_convert<float2, double2>(size_t, const float2 *, double2 *, cudaStream_t);
+template cudaError_t launch_convert<double2, double2>(size_t, const double2 *, double2 *, cudaStream_t);
+template cudaError_t launch_convert<float2, float2>(size_t, const float2 *, float2 *, cudaStream_t);
+template cudaError_t launch_zero<double2>(size_t, double2 *, cudaStream_t);
+template cudaError_t launch_zero<float2>(size_t, float2 *, cudaStream_t);

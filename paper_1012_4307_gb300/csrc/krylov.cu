@@ -1,0 +1,419 @@
+// Outer Krylov drivers on the device: flexible GMRES(m) and Bi-CGSTAB, right-preconditioned
+// by one multigrid cycle (Algorithm 1) in FP32 or FP64, with every vector operation, every
+// inner product, the Givens rotations and the least-squares back substitution in FP64 on the
+// GPU.  The host only sequences launches and reads one residual estimate per iteration.
+//
+// Flexible GMRES: Saad, Iterative Methods for Sparse Linear Systems, Algorithm 9.6, with
+// classical Gram-Schmidt and one re-orthogonalisation (CGS2, three fused passes) in place of
+// modified Gram-Schmidt.  Bi-CGSTAB: van der Vorst (1992), right preconditioning, two
+// preconditioner cycles per iteration as in Section 5 of the paper.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+
+#include "helm_handle.h"
+
+#define CKR(...)                                                                                           \
+    do {                                                                                                   \
+        cudaError_t e_ = (__VA_ARGS__);                                                                           \
+        if (e_ != cudaSuccess) return helm_fail(HELM_ERR_CUDA, "%s: %s", #__VA_ARGS__, cudaGetErrorString(e_));   \
+    } while (0)
+
+static void free_krylov(helm_handle *h) {
+    for (void *p : h->krylov_owned) cudaFree(p);
+    h->krylov_owned.clear();
+    h->V = nullptr; h->Z = nullptr; h->H = nullptr; h->g = h->sn = h->y = h->h2 = nullptr;
+    h->cs = nullptr; h->partials = nullptr; h->scal = nullptr; h->est_dev = nullptr;
+    h->m_alloc = 0;
+    h->bicg_alloc = false;
+    h->br = h->brh = h->bp = h->bv = h->bs = h->bt = nullptr;
+    h->by = h->bz = nullptr;
+}
+
+void helm_free_krylov(helm_handle *h) { free_krylov(h); }
+
+template <typename T> static cudaError_t kalloc(helm_handle *h, T **p, size_t count) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
+    if (e == cudaSuccess) {
+        h->krylov_owned.push_back(*p);
+        e = cudaMemsetAsync(*p, 0, (count ? count : 1) * sizeof(T), h->stream);
+    }
+    return e;
+}
+
+static helm_prec z_precision(const helm_handle *h) {
+    return h->mg.kind == HELM_PC_NONE ? HELM_C128 : h->mg.prec;
+}
+
+static helm_status ensure_ws(helm_handle *h, int m) {
+    const helm_prec zp = z_precision(h);
+    if (h->m_alloc >= m && h->z_prec == zp && h->V) return HELM_OK;
+    // grow: release only the GMRES part; keep it simple by releasing everything
+    free_krylov(h);
+    const size_t np = h->np;
+    const int nblk = blas_nblocks(np);
+    cudaError_t e = cudaSuccess;
+#define KA(ptr, cnt) if (e == cudaSuccess) e = kalloc(h, ptr, cnt)
+    KA(&h->V, (size_t)(m + 1) * np);
+    if (zp == HELM_C64) { float2 *z; KA(&z, (size_t)m * np); h->Z = z; }
+    else { double2 *z; KA(&z, (size_t)m * np); h->Z = z; }
+    KA(&h->H, (size_t)(m + 1) * m);
+    KA(&h->g, (size_t)m + 1);
+    KA(&h->sn, (size_t)m);
+    KA(&h->y, (size_t)m);
+    KA(&h->h2, (size_t)m + 1);
+    KA(&h->cs, (size_t)m);
+    KA(&h->partials, (size_t)nblk * 65);
+    KA(&h->scal, 32);
+    KA(&h->est_dev, 4);
+#undef KA
+    if (e != cudaSuccess) {
+        free_krylov(h);
+        return helm_fail(e == cudaErrorMemoryAllocation ? HELM_ERR_NOMEM : HELM_ERR_CUDA, "Krylov workspace: %s",
+                         cudaGetErrorString(e));
+    }
+    if (!h->est_host) CKR(cudaMallocHost((void **)&h->est_host, 8 * sizeof(double)));
+    h->m_alloc = m;
+    h->z_prec = zp;
+    return HELM_OK;
+}
+
+static helm_status ensure_bicg(helm_handle *h) {
+    helm_status st = ensure_ws(h, 1);
+    if (st != HELM_OK) return st;
+    if (h->bicg_alloc) return HELM_OK;
+    const size_t np = h->np;
+    cudaError_t e = cudaSuccess;
+    double2 **vv[6] = {&h->br, &h->brh, &h->bp, &h->bv, &h->bs, &h->bt};
+    for (auto p : vv)
+        if (e == cudaSuccess) e = kalloc(h, p, np);
+    if (h->z_prec == HELM_C64) {
+        float2 *a = nullptr, *b = nullptr;
+        if (e == cudaSuccess) e = kalloc(h, &a, np);
+        if (e == cudaSuccess) e = kalloc(h, &b, np);
+        h->by = a; h->bz = b;
+    } else {
+        double2 *a = nullptr, *b = nullptr;
+        if (e == cudaSuccess) e = kalloc(h, &a, np);
+        if (e == cudaSuccess) e = kalloc(h, &b, np);
+        h->by = a; h->bz = b;
+    }
+    if (e != cudaSuccess) return helm_fail(HELM_ERR_NOMEM, "Bi-CGSTAB workspace: %s", cudaGetErrorString(e));
+    h->bicg_alloc = true;
+    return HELM_OK;
+}
+
+// ||x||_2 -> out (device scalar, .x); optionally read back to the host.
+static cudaError_t dev_norm(helm_handle *h, const double2 *x, double2 *out) {
+    cudaError_t e = launch_mdot(h->np, x, h->np, 1, x, h->partials, h->stream);
+    if (e != cudaSuccess) return e;
+    return launch_reduce(h->partials, blas_nblocks(h->np), 1, out, 2, h->stream);
+}
+
+static cudaError_t dev_dot(helm_handle *h, const double2 *a, const double2 *b, double2 *out) {
+    cudaError_t e = launch_mdot(h->np, a, h->np, 1, b, h->partials, h->stream);
+    if (e != cudaSuccess) return e;
+    return launch_reduce(h->partials, blas_nblocks(h->np), 1, out, 0, h->stream);
+}
+
+static helm_status read_scalars(helm_handle *h, const void *dev, size_t bytes, void *host) {
+    CKR(cudaMemcpyAsync(h->est_host, dev, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
+    memcpy(host, h->est_host, bytes);
+    return HELM_OK;
+}
+
+// z = precondition(v) in the workspace precision; w = A z (FP64)
+static cudaError_t precond_apply(helm_handle *h, const double2 *v, void *z, double2 *w) {
+    cudaError_t e;
+    if (h->z_prec == HELM_C64) {
+        e = precondition<float>(h, v, (float2 *)z);
+        if (e != cudaSuccess) return e;
+        return launch_apply<double, float2>(h->A64, h->dim, (const float2 *)z, w, h->stream);
+    }
+    e = precondition<double>(h, v, (double2 *)z);
+    if (e != cudaSuccess) return e;
+    return launch_apply<double, double2>(h->A64, h->dim, (const double2 *)z, w, h->stream);
+}
+
+static helm_status fgmres(helm_handle *h, const double2 *f, double2 *x, double tol, int m, int maxit,
+                          helm_stats *st) {
+    helm_status s0 = ensure_ws(h, m);
+    if (s0 != HELM_OK) return s0;
+    const size_t np = h->np;
+    const int nblk = blas_nblocks(np);
+    const int ldh = m + 1;
+    cudaStream_t s = h->stream;
+    const size_t zsz = h->z_prec == HELM_C64 ? sizeof(float2) : sizeof(double2);
+    double2 hv[2];
+    CKR(dev_norm(h, f, h->scal));
+    helm_status rs = read_scalars(h, h->scal, sizeof(double2), hv);
+    if (rs != HELM_OK) return rs;
+    const double fn = hv[0].x;
+    if (!std::isfinite(fn)) return helm_fail(HELM_ERR_NONFINITE, "||rhs|| is not finite");
+    int it = 0, restarts = 0;
+    double est = 1.0, rel = 1.0;
+    helm_status status = HELM_ERR_NOCONV;
+    if (fn == 0.0) {
+        CKR(cudaMemsetAsync(x, 0, np * sizeof(double2), s));
+        CKR(cudaStreamSynchronize(s));
+        if (st) { st->iterations = 0; st->restarts = 0; st->rel_res = 0; st->est_res = 0; st->status = HELM_OK; }
+        return HELM_OK;
+    }
+    for (;;) {
+        // r0 = f - A x -> V_0, beta = ||r0||
+        CKR(launch_residual<double, double2>(h->A64, h->dim, f, x, h->V, s));
+        CKR(dev_norm(h, h->V, h->scal));
+        if ((rs = read_scalars(h, h->scal, sizeof(double2), hv)) != HELM_OK) return rs;
+        const double beta = hv[0].x;
+        rel = beta / fn;
+        if (!std::isfinite(beta)) { status = HELM_ERR_NONFINITE; break; }
+        if (rel <= tol) { status = HELM_OK; break; }
+        if (it >= maxit) { status = HELM_ERR_NOCONV; break; }
+        restarts++;
+        CKR(launch_scale_inv(np, h->V, h->scal, h->V, s));
+        CKR(cudaMemsetAsync(h->g, 0, (m + 1) * sizeof(double2), s));
+        CKR(cudaMemcpyAsync(h->g, h->scal, sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        int jdone = 0;
+        bool nonfinite = false;
+        for (int j = 0; j < m && it < maxit; j++) {
+            double2 *vj = h->V + (size_t)j * np, *w = h->V + (size_t)(j + 1) * np;
+            void *zj = (char *)h->Z + (size_t)j * np * zsz;
+            CKR(precond_apply(h, vj, zj, w));
+            double2 *hcol = h->H + (size_t)ldh * j;
+            // CGS2: h1 = V^H w ; w -= V h1, h2 = V^H w ; w -= V h2, ||w||
+            CKR(launch_mdot(np, h->V, np, j + 1, w, h->partials, s));
+            CKR(launch_reduce(h->partials, nblk, j + 1, hcol, 0, s));
+            CKR(launch_update_mdot(np, h->V, np, j + 1, hcol, w, h->partials, s));
+            CKR(launch_reduce(h->partials, nblk, j + 1, h->h2, 0, s));
+            CKR(launch_reduce(h->partials, nblk, j + 1, hcol, 1, s));
+            CKR(launch_update_norm(np, h->V, np, j + 1, h->h2, w, h->partials, s));
+            CKR(launch_reduce(h->partials, nblk, 1, hcol + j + 1, 2, s));
+            CKR(launch_scale_inv(np, w, hcol + j + 1, w, s));
+            CKR(launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, fn, h->est_dev, s));
+            double e1;
+            if ((rs = read_scalars(h, h->est_dev, sizeof(double), &e1)) != HELM_OK) return rs;
+            it++;
+            jdone = j + 1;
+            est = e1;
+            if (st && st->history && it - 1 < st->history_len) st->history[it - 1] = est;
+            if (!std::isfinite(est)) { nonfinite = true; break; }
+            if (est <= tol) break;
+        }
+        if (nonfinite) { status = HELM_ERR_NONFINITE; break; }
+        // x += Z y with y = H^{-1} g
+        CKR(launch_backsolve(h->H, ldh, jdone, h->g, h->y, s));
+        if (h->z_prec == HELM_C64)
+            CKR(launch_combine<float2>(np, (const float2 *)h->Z, np, jdone, h->y, x, s));
+        else
+            CKR(launch_combine<double2>(np, (const double2 *)h->Z, np, jdone, h->y, x, s));
+    }
+    if (st) {
+        st->iterations = it;
+        st->restarts = restarts;
+        st->rel_res = rel;
+        st->est_res = est;
+        st->status = status;
+    }
+    if (status == HELM_ERR_NONFINITE) return helm_fail(status, "non-finite residual in FGMRES");
+    if (status == HELM_ERR_NOCONV) return helm_fail(status, "FGMRES: %d iterations, rel. residual %.3e > %.3e", it, rel, tol);
+    return status;
+}
+
+static helm_status bicgstab(helm_handle *h, const double2 *f, double2 *x, double tol, int maxit, helm_stats *st) {
+    helm_status s0 = ensure_bicg(h);
+    if (s0 != HELM_OK) return s0;
+    const size_t np = h->np;
+    cudaStream_t s = h->stream;
+    double2 *sc = h->scal;  // 0 rho 1 rho_old 2 alpha 3 omega 4 beta 5 rv 6 ts 7 tt 8 -alpha 9 -omega 10 one 11 flags
+    double2 *nrm = h->scal + 16;
+    double2 hv[2];
+    helm_status rs;
+    CKR(dev_norm(h, f, nrm));
+    if ((rs = read_scalars(h, nrm, sizeof(double2), hv)) != HELM_OK) return rs;
+    const double fn = hv[0].x;
+    if (!std::isfinite(fn)) return helm_fail(HELM_ERR_NONFINITE, "||rhs|| is not finite");
+    if (fn == 0.0) {
+        CKR(cudaMemsetAsync(x, 0, np * sizeof(double2), s));
+        CKR(cudaStreamSynchronize(s));
+        if (st) { st->iterations = 0; st->restarts = 0; st->rel_res = 0; st->est_res = 0; st->status = HELM_OK; }
+        return HELM_OK;
+    }
+    CKR(launch_residual<double, double2>(h->A64, h->dim, f, x, h->br, s));
+    CKR(cudaMemcpyAsync(h->brh, h->br, np * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    CKR(cudaMemsetAsync(h->bp, 0, np * sizeof(double2), s));
+    CKR(cudaMemsetAsync(h->bv, 0, np * sizeof(double2), s));
+    CKR(launch_bicg_scalars(3, sc, s));
+    CKR(dev_norm(h, h->br, nrm));
+    if ((rs = read_scalars(h, nrm, sizeof(double2), hv)) != HELM_OK) return rs;
+    double est = hv[0].x / fn;
+    int it = 0;
+    helm_status status = est <= tol ? HELM_OK : HELM_ERR_NOCONV;
+    const bool c64 = h->z_prec == HELM_C64;
+    while (status == HELM_ERR_NOCONV && it < maxit) {
+        CKR(dev_dot(h, h->brh, h->br, sc + 0));                                   // rho
+        CKR(launch_bicg_scalars(0, sc, s));                                       // beta
+        CKR(launch_bicg_p(np, h->br, h->bv, sc, h->bp, s));                       // p
+        CKR(precond_apply(h, h->bp, h->by, h->bv));                               // y = M p, v = A y
+        CKR(dev_dot(h, h->brh, h->bv, sc + 5));                                   // <rh, v>
+        CKR(launch_bicg_scalars(1, sc, s));                                       // alpha
+        CKR(cudaMemcpyAsync(h->bs, h->br, np * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        CKR(launch_axpby(np, sc + 8, h->bv, sc + 10, h->bs, s));                  // s = r - alpha v
+        CKR(dev_norm(h, h->bs, nrm));
+        double2 hs[12];
+        CKR(cudaMemcpyAsync(h->est_host, nrm, sizeof(double2), cudaMemcpyDeviceToHost, s));
+        CKR(cudaMemcpyAsync(h->est_host + 2, sc + 11, sizeof(double2), cudaMemcpyDeviceToHost, s));
+        CKR(cudaStreamSynchronize(s));
+        memcpy(hs, h->est_host, 2 * sizeof(double2));
+        it++;
+        if (hs[1].x != 0.0) { status = HELM_ERR_BREAKDOWN; break; }
+        est = hs[0].x / fn;
+        if (!std::isfinite(est)) { status = HELM_ERR_NONFINITE; break; }
+        if (est <= tol) {                                                         // x += alpha y
+            if (c64) CKR(launch_axpy_mixed<float2>(np, sc + 2, (const float2 *)h->by, x, s));
+            else CKR(launch_axpy_mixed<double2>(np, sc + 2, (const double2 *)h->by, x, s));
+            status = HELM_OK;
+            if (st && st->history && it - 1 < st->history_len) st->history[it - 1] = est;
+            break;
+        }
+        CKR(precond_apply(h, h->bs, h->bz, h->bt));                               // z = M s, t = A z
+        CKR(dev_dot(h, h->bt, h->bs, sc + 6));                                    // <t, s>
+        CKR(dev_dot(h, h->bt, h->bt, sc + 7));                                    // <t, t>
+        CKR(launch_bicg_scalars(2, sc, s));                                       // omega
+        if (c64) {
+            CKR(launch_axpy_mixed<float2>(np, sc + 2, (const float2 *)h->by, x, s));
+            CKR(launch_axpy_mixed<float2>(np, sc + 3, (const float2 *)h->bz, x, s));
+        } else {
+            CKR(launch_axpy_mixed<double2>(np, sc + 2, (const double2 *)h->by, x, s));
+            CKR(launch_axpy_mixed<double2>(np, sc + 3, (const double2 *)h->bz, x, s));
+        }
+        CKR(cudaMemcpyAsync(h->br, h->bs, np * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        CKR(launch_axpby(np, sc + 9, h->bt, sc + 10, h->br, s));                  // r = s - omega t
+        CKR(dev_norm(h, h->br, nrm));
+        CKR(cudaMemcpyAsync(h->est_host, nrm, sizeof(double2), cudaMemcpyDeviceToHost, s));
+        CKR(cudaMemcpyAsync(h->est_host + 2, sc + 11, sizeof(double2), cudaMemcpyDeviceToHost, s));
+        CKR(cudaStreamSynchronize(s));
+        memcpy(hs, h->est_host, 2 * sizeof(double2));
+        est = hs[0].x / fn;
+        if (st && st->history && it - 1 < st->history_len) st->history[it - 1] = est;
+        if (!std::isfinite(est)) { status = HELM_ERR_NONFINITE; break; }
+        if (est <= tol) { status = HELM_OK; break; }
+        if (hs[1].x != 0.0) { status = HELM_ERR_BREAKDOWN; break; }
+    }
+    // true residual
+    CKR(launch_residual<double, double2>(h->A64, h->dim, f, x, h->br, s));
+    CKR(dev_norm(h, h->br, nrm));
+    if ((rs = read_scalars(h, nrm, sizeof(double2), hv)) != HELM_OK) return rs;
+    const double rel = hv[0].x / fn;
+    if (status == HELM_OK && !(rel <= tol * 10.0)) status = HELM_ERR_NOCONV;
+    if (st) {
+        st->iterations = it;
+        st->restarts = 0;
+        st->rel_res = rel;
+        st->est_res = est;
+        st->status = status;
+    }
+    if (status == HELM_ERR_BREAKDOWN) return helm_fail(status, "Bi-CGSTAB breakdown at iteration %d", it);
+    if (status == HELM_ERR_NONFINITE) return helm_fail(status, "non-finite residual in Bi-CGSTAB");
+    if (status == HELM_ERR_NOCONV) return helm_fail(status, "Bi-CGSTAB: %d iterations, rel. residual %.3e > %.3e", it, rel, tol);
+    return status;
+}
+
+static helm_status check_vec(const void *p, const char *name) {
+    if (!p) return helm_fail(HELM_ERR_ARG, "%s is null", name);
+    if ((uintptr_t)p % 16) return helm_fail(HELM_ERR_ARG, "%s is not 16-byte aligned", name);
+    return HELM_OK;
+}
+
+extern "C" helm_status krylov_solve(helm_handle *h, helm_krylov method, const void *rhs, void *x, double tol,
+                                    int restart, int maxit, helm_stats *stats) {
+    if (!h) return helm_fail(HELM_ERR_ARG, "null handle");
+    helm_status st;
+    if ((st = check_vec(rhs, "rhs")) != HELM_OK || (st = check_vec(x, "x")) != HELM_OK) return st;
+    if (rhs == x) return helm_fail(HELM_ERR_ARG, "rhs and x must not overlap");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return helm_fail(HELM_ERR_ARG, "tol must be positive");
+    if (maxit < 1) return helm_fail(HELM_ERR_ARG, "maxit must be >= 1");
+    auto t0 = std::chrono::steady_clock::now();
+    if (method == HELM_FGMRES) {
+        if (restart < 1 || restart > 64) return helm_fail(HELM_ERR_ARG, "restart must be in 1..64");
+        st = fgmres(h, (const double2 *)rhs, (double2 *)x, tol, restart, maxit, stats);
+    } else if (method == HELM_BICGSTAB) {
+        st = bicgstab(h, (const double2 *)rhs, (double2 *)x, tol, maxit, stats);
+    } else {
+        return helm_fail(HELM_ERR_ARG, "unknown Krylov method");
+    }
+    if (stats) {
+        stats->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        stats->status = st;
+    }
+    return st;
+}
+
+extern "C" helm_status helm_solve_adjoint(helm_handle *h, const void *rhs, void *lambda, double tol, int restart,
+                                          int maxit, helm_stats *stats) {
+    if (!h) return helm_fail(HELM_ERR_ARG, "null handle");
+    helm_status st;
+    if ((st = check_vec(rhs, "rhs")) != HELM_OK || (st = check_vec(lambda, "lambda")) != HELM_OK) return st;
+    if (rhs == lambda) return helm_fail(HELM_ERR_ARG, "rhs and lambda must not overlap");
+    if (!h->adj_rhs) {
+        // allocated outside the Krylov workspace so that a workspace regrow keeps them valid
+        CKR(cudaMalloc((void **)&h->adj_rhs, h->np * sizeof(double2)));
+        h->owned.push_back(h->adj_rhs);
+        CKR(cudaMalloc((void **)&h->adj_y, h->np * sizeof(double2)));
+        h->owned.push_back(h->adj_y);
+        CKR(cudaMemsetAsync(h->adj_rhs, 0, h->np * sizeof(double2), h->stream));
+    }
+    const double2 *w[3] = {h->wts[0], h->wts[1], h->wts[2]};
+    // A^T = W A W^{-1}  =>  lambda = W A^{-1} W^{-1} rhs
+    CKR(launch_weight(h->np, h->n, h->dim, w, 1, (const double2 *)rhs, h->adj_rhs, h->stream));
+    CKR(cudaMemsetAsync(h->adj_y, 0, h->np * sizeof(double2), h->stream));
+    st = krylov_solve(h, HELM_FGMRES, h->adj_rhs, h->adj_y, tol, restart, maxit, stats);
+    if (st != HELM_OK && st != HELM_ERR_NOCONV) return st;
+    CKR(cudaMemsetAsync(lambda, 0, h->np * sizeof(double2), h->stream));
+    CKR(launch_weight(h->np, h->n, h->dim, w, 0, h->adj_y, (double2 *)lambda, h->stream));
+    return st;
+}
+
+extern "C" helm_status helm_mg_conv(helm_handle *h, const void *b, void *x, helm_prec prec, double tol, int maxcyc,
+                                    int *ncycles, double *factor) {
+    if (!h || !ncycles || !factor) return helm_fail(HELM_ERR_ARG, "null argument");
+    if (h->mg.kind == HELM_PC_NONE) return helm_fail(HELM_ERR_ARG, "handle has no preconditioner hierarchy");
+    if (maxcyc < 1 || !(tol > 0)) return helm_fail(HELM_ERR_ARG, "bad tol/maxcyc");
+    helm_status st = ensure_ws(h, 1);
+    if (st != HELM_OK) return st;
+    const size_t np = h->np;
+    cudaStream_t s = h->stream;
+    const size_t esz = prec == HELM_C128 ? sizeof(double2) : sizeof(float2);
+    CKR(cudaMemsetAsync(x, 0, np * esz, s));
+    double2 *r = h->V + np, *b64 = h->V;  // V has >= 2 vectors
+    if (prec == HELM_C64) CKR(launch_convert(np, (const float2 *)b, b64, s));
+    else CKR(cudaMemcpyAsync(b64, b, np * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    double2 hv[2];
+    CKR(dev_norm(h, b64, h->scal));
+    if ((st = read_scalars(h, h->scal, sizeof(double2), hv)) != HELM_OK) return st;
+    const double bn = hv[0].x;
+    std::vector<double> res(1, bn);
+    int c = 0;
+    while (c < maxcyc) {
+        if ((st = mg_vcycle(h, b, x, prec)) != HELM_OK) return st;
+        c++;
+        if (prec == HELM_C64) {
+            float2 *r32 = h->lv[0].t32;
+            CKR(launch_residual<float, float2>(h->lv[0].M32, h->dim, (const float2 *)b, (const float2 *)x, r32, s));
+            CKR(launch_convert(np, (const float2 *)r32, r, s));
+        } else {
+            CKR(launch_residual<double, double2>(h->lv[0].M64, h->dim, (const double2 *)b, (const double2 *)x, r, s));
+        }
+        CKR(dev_norm(h, r, h->scal));
+        if ((st = read_scalars(h, h->scal, sizeof(double2), hv)) != HELM_OK) return st;
+        res.push_back(hv[0].x);
+        if (!std::isfinite(hv[0].x)) return helm_fail(HELM_ERR_NONFINITE, "multigrid diverged to non-finite values");
+        if (hv[0].x <= tol * bn) break;
+    }
+    const int k = std::min(c, 5);
+    *ncycles = c;
+    *factor = k > 0 && res[c - k] > 0 ? pow(res[c] / res[c - k], 1.0 / k) : 0.0;
+    return HELM_OK;
+}

@@ -1,0 +1,404 @@
+"""Python binding of libhelm.so (argument marshalling only; all arithmetic runs in the
+library's sm_103a kernels).
+
+The functions carry the C-ABI names of ``include/helm.h``: :func:`helm_create`,
+:func:`helm_apply`, :func:`mg_vcycle`, :func:`krylov_solve`, :func:`helm_solve_adjoint`,
+:func:`helm_grad_k2`, :func:`helm_mg_conv`, :func:`helm_create_batch`,
+:func:`helm_solve_batch`.  Vectors are CUDA torch tensors holding every grid node including
+the Dirichlet boundary (shape ``(n1, n0)`` or ``(n2, n1, n0)``, x fastest), complex128 for
+HELM_C128 and complex64 for HELM_C64.  PyTorch provides device memory and the stream; there is
+no CPU fallback: without the library or a GPU every call raises.
+
+:class:`HelmholtzSolve` is a ``torch.autograd.Function`` whose backward solves the adjoint
+system A^T lambda = conj(grad_u) with the same operator and preconditioner
+(A^T = W A W^{-1}, W the complex dual-volume weights of the FD scheme), then forms
+dL/dk^2 = Re(lambda * u) in the library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+from dataclasses import dataclass, field
+
+import torch
+
+from . import build as _build
+
+HELM_OK, HELM_ERR_ARG, HELM_ERR_CUDA, HELM_ERR_NOMEM, HELM_ERR_NOCONV, HELM_ERR_BREAKDOWN, \
+    HELM_ERR_NONFINITE, HELM_ERR_TIMEOUT = range(8)
+HELM_C128, HELM_C64 = 0, 1
+HELM_PC_NONE, HELM_PC_CSG, HELM_PC_CSL, HELM_PC_QD, HELM_PC_LAPLACE = range(5)
+HELM_OP_A, HELM_OP_M = 0, 1
+HELM_FGMRES, HELM_BICGSTAB = 0, 1
+HELM_SMOOTH_JACOBI, HELM_SMOOTH_RB = 0, 1
+
+PC_KINDS = {"none": HELM_PC_NONE, "csg": HELM_PC_CSG, "csl": HELM_PC_CSL, "qd": HELM_PC_QD, "laplace": HELM_PC_LAPLACE}
+STATUS_NAMES = {0: "HELM_OK", 1: "HELM_ERR_ARG", 2: "HELM_ERR_CUDA", 3: "HELM_ERR_NOMEM", 4: "HELM_ERR_NOCONV",
+                5: "HELM_ERR_BREAKDOWN", 6: "HELM_ERR_NONFINITE", 7: "HELM_ERR_TIMEOUT"}
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class _Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+
+
+class _MG(C.Structure):
+    _fields_ = [("kind", C.c_int), ("theta_a", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("re_lambda0", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
+                ("smoother", C.c_int), ("gamma_f", C.c_int), ("gamma_c", C.c_int), ("coarsest_n", C.c_int),
+                ("prec", C.c_int)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("status", C.c_int), ("rel_res", C.c_double),
+                ("est_res", C.c_double), ("time_ms", C.c_double), ("history", C.c_void_p),
+                ("history_len", C.c_int)]
+
+
+_lock = threading.Lock()
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Loads libhelm.so (building it first if its sources are newer).  Raises if unavailable."""
+    global _LIB
+    with _lock:
+        if _LIB is not None:
+            return _LIB
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libhelm.so is not built (%s); run paper_1012_4307_gb300.build.build()" % path)
+        lib = C.CDLL(path)
+        P, I, D = C.c_void_p, C.c_int, C.c_double
+        sigs = {
+            "helm_create": ([P, D, P, P, P, P, P, P], I),
+            "helm_destroy": ([P], None),
+            "helm_apply": ([P, I, I, P, P], I),
+            "mg_vcycle": ([P, P, P, I], I),
+            "krylov_solve": ([P, I, P, P, D, I, I, P], I),
+            "helm_solve_adjoint": ([P, P, P, D, I, I, P], I),
+            "helm_grad_k2": ([P, P, P, P], I),
+            "helm_mg_conv": ([P, P, P, I, D, I, P, P], I),
+            "helm_levels": ([P, P], I),
+            "helm_level_shape": ([P, I, P], I),
+            "helm_create_batch": ([I, P, P, P, P, P, P, P], I),
+            "helm_solve_batch": ([P, P, P, D, I, I, P], I),
+            "helm_destroy_batch": ([P], None),
+            "helm_last_error": ([], C.c_char_p),
+            "helm_version": ([], C.c_char_p),
+        }
+        for name, (args, res) in sigs.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _LIB = lib
+        return lib
+
+
+def helm_last_error() -> str:
+    return load().helm_last_error().decode()
+
+
+def helm_version() -> str:
+    return load().helm_version().decode()
+
+
+def _check(st, allow=(HELM_OK,)):
+    if st not in allow:
+        raise HelmError(st, helm_last_error())
+    return st
+
+
+@dataclass
+class MGParams:
+    """Mirror of ``helm_mg_params`` (Section 4.2, Algorithm 1, Section 5 operators)."""
+    kind: str = "csg"
+    theta_a: float = math.pi / 14
+    beta1: float = -1.0
+    beta2: float = -0.5
+    re_lambda0: float = 0.0
+    nu1: int = 2
+    nu2: int = 2
+    omega: float = 0.8
+    smoother: str = "jacobi"
+    gamma_f: int = 1
+    gamma_c: int = 1
+    coarsest_n: int = 17
+    prec: str = "c64"
+
+    def to_c(self) -> _MG:
+        m = _MG()
+        m.kind = PC_KINDS[self.kind]
+        m.theta_a, m.beta1, m.beta2, m.re_lambda0 = self.theta_a, self.beta1, self.beta2, self.re_lambda0
+        m.nu1, m.nu2, m.omega = self.nu1, self.nu2, self.omega
+        m.smoother = HELM_SMOOTH_RB if self.smoother == "rb" else HELM_SMOOTH_JACOBI
+        m.gamma_f, m.gamma_c, m.coarsest_n = self.gamma_f, self.gamma_c, self.coarsest_n
+        m.prec = HELM_C64 if self.prec == "c64" else HELM_C128
+        return m
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _vec(t: torch.Tensor, np_: int, name: str, dtype=None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s (got %s)" % (name, dtype, t.dtype))
+    if not t.is_contiguous() or t.numel() != np_:
+        raise ValueError("%s must be contiguous with %d elements" % (name, np_))
+    return t.data_ptr()
+
+
+def _prec_of(t: torch.Tensor) -> int:
+    if t.dtype == torch.complex128:
+        return HELM_C128
+    if t.dtype == torch.complex64:
+        return HELM_C64
+    raise TypeError("grid vectors must be complex128 or complex64 (got %s)" % t.dtype)
+
+
+class Handle:
+    """Owns one ``helm_handle*`` (solver for one grid, its levels and workspace)."""
+
+    def __init__(self, ptr, dim, n, stream):
+        self.ptr = ptr
+        self.dim = dim
+        self.n = tuple(n[:dim])
+        self.shape = tuple(reversed(self.n))
+        self.np = int(math.prod(self.n))
+        self.stream = stream
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _LIB is not None:
+            _LIB.helm_destroy(self.ptr)
+            self.ptr = None
+
+    def close(self):
+        self.__del__()
+
+    @property
+    def levels(self):
+        n = C.c_int()
+        _check(load().helm_levels(self.ptr, C.byref(n)))
+        out = []
+        for l in range(n.value):
+            s = (C.c_int * 3)()
+            _check(load().helm_level_shape(self.ptr, l, s))
+            out.append(tuple(reversed(list(s)[: self.dim])))
+        return out
+
+    def zeros(self, dtype=torch.complex128):
+        return torch.zeros(self.shape, dtype=dtype, device="cuda")
+
+
+def helm_create(dim, n, k2: torch.Tensor, theta=math.pi / 6, r0_lo=None, r0_hi=None, lo=None, hi=None,
+                mg: MGParams | None = None, stream=None) -> Handle:
+    """helm_create(): ECS grid, operator A = -Delta - k^2, preconditioner hierarchy."""
+    n = list(n) if hasattr(n, "__len__") else [n] * dim
+    lo = list(lo) if lo is not None else [-1.0] * dim
+    hi = list(hi) if hi is not None else [1.0] * dim
+    r0_lo = list(r0_lo) if r0_lo is not None else [-0.75] * dim
+    r0_hi = list(r0_hi) if r0_hi is not None else [0.75] * dim
+    mg = mg or MGParams()
+    g = _Grid()
+    g.dim = dim
+    for a in range(3):
+        g.n[a] = n[a] if a < dim else 1
+        g.lo[a] = lo[a] if a < dim else 0.0
+        g.hi[a] = hi[a] if a < dim else 1.0
+    npts = int(math.prod(n[:dim]))
+    k2 = k2.to(device="cuda", dtype=torch.float64).contiguous()
+    ptr_k2 = _vec(k2, npts, "k2", torch.float64)
+    rl = (C.c_double * 3)(*(r0_lo + [0.0] * (3 - dim)))
+    rh = (C.c_double * 3)(*(r0_hi + [0.0] * (3 - dim)))
+    out = C.c_void_p()
+    mgc = mg.to_c()
+    _check(load().helm_create(C.byref(g), float(theta), rl, rh, C.c_void_p(ptr_k2), C.byref(mgc),
+                              _stream_ptr(stream), C.byref(out)))
+    h = Handle(out.value, dim, n, stream)
+    h.mg = mg
+    return h
+
+
+def helm_destroy(h: Handle):
+    h.close()
+
+
+def helm_apply(h: Handle, x: torch.Tensor, y: torch.Tensor | None = None, which: str = "A") -> torch.Tensor:
+    """y = A x (which='A') or y = M x (which='M'), in the precision of x."""
+    prec = _prec_of(x)
+    if y is None:
+        y = torch.zeros_like(x)
+    _check(load().helm_apply(h.ptr, HELM_OP_A if which == "A" else HELM_OP_M, prec,
+                             C.c_void_p(_vec(x, h.np, "x")), C.c_void_p(_vec(y, h.np, "y", x.dtype))))
+    return y
+
+
+def mg_vcycle(h: Handle, b: torch.Tensor, x: torch.Tensor | None = None) -> torch.Tensor:
+    """One cycle of Algorithm 1 for M x = b; x is the initial guess (zero if None), updated in place."""
+    prec = _prec_of(b)
+    if x is None:
+        x = torch.zeros_like(b)
+    _check(load().mg_vcycle(h.ptr, C.c_void_p(_vec(b, h.np, "b")), C.c_void_p(_vec(x, h.np, "x", b.dtype)), prec))
+    return x
+
+
+@dataclass
+class Stats:
+    iterations: int = 0
+    restarts: int = 0
+    status: int = 0
+    rel_res: float = float("nan")
+    est_res: float = float("nan")
+    time_ms: float = 0.0
+    history: list = field(default_factory=list)
+
+
+def _stats_from(s: _Stats, hist) -> Stats:
+    out = Stats(s.iterations, s.restarts, s.status, s.rel_res, s.est_res, s.time_ms)
+    if hist is not None:
+        out.history = list(hist[: min(s.iterations, len(hist))])
+    return out
+
+
+def krylov_solve(h: Handle, rhs: torch.Tensor, x: torch.Tensor | None = None, tol=1e-8, restart=30, maxit=1000,
+                 method: str = "fgmres", history: bool = False, raise_on_noconv: bool = True):
+    """Solves A x = rhs (FP64) with FGMRES(restart) or Bi-CGSTAB; returns (x, Stats)."""
+    if x is None:
+        x = torch.zeros_like(rhs)
+    hist = (C.c_double * maxit)() if history else None
+    st = _Stats()
+    if hist is not None:
+        st.history = C.cast(hist, C.c_void_p)
+        st.history_len = maxit
+    allow = (HELM_OK,) if raise_on_noconv else (HELM_OK, HELM_ERR_NOCONV)
+    _check(load().krylov_solve(h.ptr, HELM_BICGSTAB if method == "bicgstab" else HELM_FGMRES,
+                               C.c_void_p(_vec(rhs, h.np, "rhs", torch.complex128)),
+                               C.c_void_p(_vec(x, h.np, "x", torch.complex128)), float(tol), int(restart),
+                               int(maxit), C.byref(st)), allow)
+    return x, _stats_from(st, hist)
+
+
+def helm_solve_adjoint(h: Handle, rhs: torch.Tensor, tol=1e-8, restart=30, maxit=1000, raise_on_noconv=True):
+    lam = torch.zeros_like(rhs)
+    st = _Stats()
+    allow = (HELM_OK,) if raise_on_noconv else (HELM_OK, HELM_ERR_NOCONV)
+    _check(load().helm_solve_adjoint(h.ptr, C.c_void_p(_vec(rhs, h.np, "rhs", torch.complex128)),
+                                     C.c_void_p(_vec(lam, h.np, "lambda", torch.complex128)), float(tol),
+                                     int(restart), int(maxit), C.byref(st)), allow)
+    return lam, _stats_from(st, None)
+
+
+def helm_grad_k2(h: Handle, lam: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
+    grad = torch.empty(h.shape, dtype=torch.float64, device="cuda")
+    _check(load().helm_grad_k2(h.ptr, C.c_void_p(_vec(lam, h.np, "lambda", torch.complex128)),
+                               C.c_void_p(_vec(u, h.np, "u", torch.complex128)), C.c_void_p(grad.data_ptr())))
+    return grad
+
+
+def helm_mg_conv(h: Handle, b: torch.Tensor, tol=1e-6, maxcyc=100):
+    """Stand-alone multigrid (Section 5 "mg-conv"): returns (x, cycles, factor)."""
+    x = torch.zeros_like(b)
+    nc, fac = C.c_int(), C.c_double()
+    _check(load().helm_mg_conv(h.ptr, C.c_void_p(_vec(b, h.np, "b")), C.c_void_p(_vec(x, h.np, "x", b.dtype)),
+                               _prec_of(b), float(tol), int(maxcyc), C.byref(nc), C.byref(fac)))
+    return x, nc.value, fac.value
+
+
+class Batch:
+    def __init__(self, ptr, shapes):
+        self.ptr = ptr
+        self.shapes = shapes
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _LIB is not None:
+            _LIB.helm_destroy_batch(self.ptr)
+            self.ptr = None
+
+
+def helm_create_batch(problems, mg: MGParams | None = None, stream=None) -> Batch:
+    """problems: list of dicts with dim, n, k2 (CUDA float64 tensor), theta, r0_lo, r0_hi, lo, hi."""
+    mg = mg or MGParams()
+    nb = len(problems)
+    grids = (_Grid * nb)()
+    theta = (C.c_double * nb)()
+    r0 = (C.c_double * (6 * nb))()
+    k2p = (C.c_void_p * nb)()
+    keep = []
+    shapes = []
+    for i, p in enumerate(problems):
+        dim = p["dim"]
+        n = list(p["n"]) if hasattr(p["n"], "__len__") else [p["n"]] * dim
+        grids[i].dim = dim
+        for a in range(3):
+            grids[i].n[a] = n[a] if a < dim else 1
+            grids[i].lo[a] = p.get("lo", [-1.0] * dim)[a] if a < dim else 0.0
+            grids[i].hi[a] = p.get("hi", [1.0] * dim)[a] if a < dim else 1.0
+            r0[6 * i + a] = p.get("r0_lo", [-0.75] * dim)[a] if a < dim else 0.0
+            r0[6 * i + 3 + a] = p.get("r0_hi", [0.75] * dim)[a] if a < dim else 0.0
+        theta[i] = p.get("theta", math.pi / 6)
+        k2 = p["k2"].to(device="cuda", dtype=torch.float64).contiguous()
+        keep.append(k2)
+        k2p[i] = k2.data_ptr()
+        shapes.append(tuple(reversed(n[:dim])))
+    out = C.c_void_p()
+    mgc = mg.to_c()
+    _check(load().helm_create_batch(nb, grids, theta, r0, k2p, C.byref(mgc), _stream_ptr(stream), C.byref(out)))
+    return Batch(out.value, shapes)
+
+
+def helm_solve_batch(b: Batch, rhs, x, tol=1e-8, restart=30, maxit=1000, raise_on_noconv=True):
+    nb = len(b.shapes)
+    rp = (C.c_void_p * nb)(*[_vec(r, int(math.prod(s)), "rhs", torch.complex128) for r, s in zip(rhs, b.shapes)])
+    xp = (C.c_void_p * nb)(*[_vec(v, int(math.prod(s)), "x", torch.complex128) for v, s in zip(x, b.shapes)])
+    st = (_Stats * nb)()
+    allow = (HELM_OK,) if raise_on_noconv else (HELM_OK, HELM_ERR_NOCONV)
+    _check(load().helm_solve_batch(b.ptr, rp, xp, float(tol), int(restart), int(maxit), st), allow)
+    return [_stats_from(s, None) for s in st]
+
+
+class HelmholtzSolve(torch.autograd.Function):
+    """u = A(k^2)^{-1} f with A = -Delta - k^2 (ECS, FP64 FGMRES, multigrid preconditioner).
+
+    forward(k2, f, handle_factory, tol, restart, maxit) -> u.  ``handle_factory(k2)`` returns
+    a :class:`Handle` for that k^2.  Only u is saved (the Krylov basis is not kept).  backward
+    solves A^T lambda = conj(grad_u) by the adjoint identity and returns dL/dk^2 = Re(lambda u)
+    (PyTorch passes grad_u = 2 dL/d(conj u) for a real loss L).
+    """
+
+    @staticmethod
+    def forward(ctx, k2, f, handle_factory, tol=1e-10, restart=30, maxit=2000):
+        h = handle_factory(k2.detach())
+        u, st = krylov_solve(h, f.detach().contiguous(), tol=tol, restart=restart, maxit=maxit)
+        ctx.h = h
+        ctx.opts = (tol, restart, maxit)
+        ctx.save_for_backward(u)
+        ctx.stats = st
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        (u,) = ctx.saved_tensors
+        tol, restart, maxit = ctx.opts
+        # conj_physical materialises the conjugate (a lazy conj view would hand the library
+        # the unconjugated memory)
+        rhs = torch.conj_physical(grad_u.to(torch.complex128)).contiguous()
+        lam, _ = helm_solve_adjoint(ctx.h, rhs, tol=tol, restart=restart, maxit=maxit)
+        g = helm_grad_k2(ctx.h, lam, u)
+        gf = torch.conj_physical(lam) if ctx.needs_input_grad[1] else None
+        return g, gf, None, None, None, None

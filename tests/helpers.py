@@ -1,0 +1,43 @@
+"""Shared builders for the GPU tests: the same seeded problem goes to the CUDA path (through
+the C-ABI binding) and to the CPU oracle."""
+import math
+
+import numpy as np
+
+
+def rel_l2(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def mg_params(helm, pc="csg", prec="c128", nu=(2, 2), omega=0.8, smoother="jacobi", gamma=(1, 1),
+              coarsest_n=17, theta_a=math.pi / 14, beta=(-1.0, -0.5), re_lambda0=0.0):
+    return helm.MGParams(kind=pc, theta_a=theta_a, beta1=beta[0], beta2=beta[1], re_lambda0=re_lambda0,
+                         nu1=nu[0], nu2=nu[1], omega=omega, smoother=smoother, gamma_f=gamma[0],
+                         gamma_c=gamma[1], coarsest_n=coarsest_n, prec=prec)
+
+
+def gpu_handle(helm, P, **kw):
+    import torch
+    n = P.n if hasattr(P.n, "__len__") else [P.n] * P.dim
+    k2 = torch.from_numpy(np.ascontiguousarray(P.k2)).cuda()
+    mg = mg_params(helm, coarsest_n=kw.pop("coarsest_n", P.coarsest_n), **kw)
+    return helm.helm_create(P.dim, n, k2, theta=P.theta, r0_lo=[-P.r0] * P.dim, r0_hi=[P.r0] * P.dim,
+                            lo=[P.lo] * P.dim, hi=[P.hi] * P.dim, mg=mg)
+
+
+def oracle_pair(O, P, pc="csg", theta_a=math.pi / 14, beta=(-1.0, -0.5), re_lambda0=None):
+    n = P.n if hasattr(P.n, "__len__") else [P.n] * P.dim
+    z = [O.contour(n[a], P.lo, P.hi, P.theta, -P.r0, P.r0) for a in range(P.dim)]
+    return O.helmholtz_ops(z, P.k2, pc=pc, theta_a=theta_a, beta=beta, re_lambda0=re_lambda0)
+
+
+def to_gpu(x, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()

@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: preconditioned solve of the 2D ECS Helmholtz well problem (1025 x 1025 nodes,
+k^2 = 2(E - V) with a Gaussian well and growth toward the boundary so that k h <= 0.6, ECS at
+pi/6 beyond |x|, |y| = 0.75, random source on |x|_inf < 0.5) to a relative residual of 1e-8 with
+FGMRES(30), preconditioned by one complex64 V(2,2) multigrid cycle on the complex-scaled-grid
+operator (theta_a = pi/14), FP64 outer solver.  One step = one full solve from x = 0.
+
+Prints one JSON line:  value = unknowns solved per second over all ranks (Mdof/s), with the
+plain FP64 solve (FP64 cycle) beside it, the dominant kernel's roofline, the CPU oracle as a
+baseline, an end-to-end number through the public API with host buffers, and the SM clocks
+sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 1025]
+
+Under torchrun every rank solves its own independent problem (seed 1 + rank): the work per GPU
+is fixed, so scaling is weak and no collective touches the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "preconditioned solve time to rel. residual 1e-8 and Mdof/s, mixed vs FP64; HBM GB/s % peak"
+UNIT = "Mdof/s"
+SM_COUNT = 152
+FP64_FMA_PER_SM_CLK = 2  # GB300: 1.25 TFLOP/s FP64 at 2.07 GHz over 152 SMs = 2 FMA / SM / clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1025)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-iters", type=int, default=0, help="oracle iterations in the CPU sample (0 = auto)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for r in csv.reader(fh):
+                if len(r) >= 9:
+                    rows.append([c.strip() for c in r])
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------- CPU oracle
+def oracle_iterations(name):
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")) as fh:
+            d = json.load(fh)
+        return d[name]["iterations"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def oracle_sample(P, iters, tol):
+    """Times the CPU oracle's FP64 FGMRES(30) with its FP64 V(2,2) cycle for ``iters``
+    iterations on the full problem (single thread); returns seconds per iteration."""
+    from oracle import oracle as O
+    z = O.axes(P.dim, P.n, theta=P.theta, r0lo=-P.r0, r0hi=P.r0)
+    A, M = O.helmholtz_ops(z, P.k2, pc=P.pc, theta_a=P.theta_a)
+    t0 = time.perf_counter()
+    mg = O.MG(M, P.coarsest_n, P.nu1, P.nu2, P.omega, P.smoother)
+    x, st = O.fgmres(A, mg, P.f, tol=tol, restart=P.restart, maxit=iters)
+    dt = time.perf_counter() - t0
+    return dt / max(st["iterations"], 1), st["iterations"], dt
+
+
+def cpu_baseline(P, tol, iters, gpu_fp64_iters):
+    it_needed = oracle_iterations(P.name)
+    source = "oracle FGMRES iteration count (tests/golden/oracle_iterations.json)"
+    if it_needed is None:
+        it_needed = gpu_fp64_iters
+        source = "iteration count of the FP64 GPU solve (no stored oracle count for this workload)"
+    per_it, done, dt = oracle_sample(P, iters, tol)
+    solve_s = per_it * it_needed
+    return {"value": P.unknowns / solve_s / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d FGMRES(30) iterations of the plain C FP64 oracle (FP64 V(2,2) CSG cycle) on the full "
+                      "%s problem, %.1f s, scaled to the %d iterations of a full solve (%s)"
+                      % (done, P.name, dt, it_needed, source),
+            "seconds_per_iteration": per_it, "projected_solve_s": solve_s}
+
+
+# ---------------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_1012_4307_gb300 import workloads as W
+    from oracle import oracle as O
+    O.build()
+    P = W.config_2d_well(args.n, seed=1)
+    it_needed = oracle_iterations(P.name)
+    iters = 2
+    vals = []
+    for s in range(args.warmup + args.steps):
+        per_it, done, dt = oracle_sample(P, iters, args.tol)
+        if s >= args.warmup:
+            vals.append(per_it)
+    per_it = statistics.mean(vals)
+    if it_needed is None:
+        it_needed = 1
+    solve_s = per_it * it_needed
+    value = P.unknowns / solve_s / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": P.name, "unknowns": P.unknowns, "solver": "FGMRES(30), FP64 V(2,2) CSG cycle",
+                       "tol": args.tol},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: %d FGMRES(30) iterations of the plain C FP64 oracle on the full "
+                                       "problem (single thread), scaled to the %d iterations of a full solve"
+                                       % (iters, it_needed)}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1012_4307_gb300 import helm
+    from paper_1012_4307_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    helm.load()
+    peaks, peak_src = load_peaks()
+
+    P = W.config_2d_well(args.n, seed=1 + rank)
+    k2 = torch.from_numpy(P.k2).cuda()
+    stream = torch.cuda.current_stream()
+    mg = helm.MGParams(kind="csg", theta_a=P.theta_a, nu1=P.nu1, nu2=P.nu2, omega=P.omega, coarsest_n=P.coarsest_n,
+                       prec="c64")
+    h = helm.helm_create(2, [P.n, P.n], k2, theta=P.theta, mg=mg)
+    f = torch.from_numpy(P.f).cuda()
+    x = torch.zeros_like(f)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def solve(handle, out):
+        out.zero_()
+        return helm.krylov_solve(handle, f, out, tol=args.tol, restart=P.restart, maxit=5000)
+
+    for _ in range(args.warmup):
+        solve(h, x)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_ms = 0.0
+    st = None
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0.record(stream)
+        _, st = solve(h, x)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = total_ms / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * P.unknowns / (ms_max / 1e3) / 1e6
+
+    # launches per solve and the dominant kernel, from one profiled solve (events on the library's stream)
+    helm.helm_profile(h, True)
+    solve(h, x)
+    prof = helm.helm_profile_read(h)
+    helm.helm_profile(h, False)
+    launches = sum(v["launches"] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dname, d = dom
+    sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak_tflops = 2 * FP64_FMA_PER_SM_CLK * SM_COUNT * sm_max * 1e6 / 1e12
+    avg_s = d["ms"] / max(d["launches"], 1) / 1e3
+    gbs = d["bytes"] / max(d["launches"], 1) / avg_s / 1e9
+    tfs = d["flops"] / max(d["launches"], 1) / avg_s / 1e12
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if d["flops"] > 0 and d["flops"] / max(d["bytes"], 1) > fp64_peak_tflops * 1e3 / hbm:
+        roof = {"bound": "alu", "achieved": tfs, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": tfs / fp64_peak_tflops, "peak_source": "FP64 FMA units: 2 per SM per clock x 152 SMs x %.0f MHz"
+                % sm_max, "hbm_gbs_achieved": gbs, "hbm_frac": gbs / hbm}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "peak_source": "%s hbm_gbs" % peak_src}
+    roof.update({"traffic": None, "kernel_class": dname, "launches_per_solve": d["launches"],
+                 "avg_launch_us": avg_s * 1e6, "share_of_solve": d["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9)})
+    breakdown = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                     "GB/s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None}
+                 for k, v in prof.items() if v["launches"]}
+
+    # plain FP64 method on the same problem (FP64 cycle); error of the mixed solution against it
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        mg64 = helm.MGParams(kind="csg", theta_a=P.theta_a, nu1=P.nu1, nu2=P.nu2, omega=P.omega,
+                             coarsest_n=P.coarsest_n, prec="c128")
+        h64 = helm.helm_create(2, [P.n, P.n], k2, theta=P.theta, mg=mg64)
+        x64 = torch.zeros_like(f)
+        solve(h64, x64)
+        reps = 2
+        tt = 0.0
+        st64 = None
+        for _ in range(reps):
+            flush.fill_(2)
+            e0.record(stream)
+            _, st64 = solve(h64, x64)
+            e1.record(stream)
+            e1.synchronize()
+            tt += e0.elapsed_time(e1)
+        ms64 = tt / reps
+        err = float(torch.linalg.vector_norm(x - x64) / torch.linalg.vector_norm(x64))
+        fp64 = {"ms_per_solve": ms64, "iterations": st64.iterations, "rel_res": st64.rel_res,
+                "value": P.unknowns / (ms64 / 1e3) / 1e6, "speedup_of_mixed": ms64 / ms,
+                "mixed_vs_fp64_rel_l2": err}
+        h64.close()
+
+    # end to end through the public API: pinned host rhs -> device, solve, solution -> host
+    f_host = torch.from_numpy(P.f).pin_memory()
+    x_host = torch.empty_like(f_host).pin_memory()
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush.fill_(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f.copy_(f_host, non_blocking=True)
+        x.zero_()
+        helm.krylov_solve(h, f, x, tol=args.tol, restart=P.restart, maxit=5000)
+        x_host.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_ms /= args.steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * P.unknowns / (float(te.item()) / 1e3) / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": f_host.numel() * 16, "d2h_bytes_per_step": x_host.numel() * 16,
+           "ms_per_step": float(te.item())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        iters = args.cpu_iters or 6
+        cpu = cpu_baseline(P, args.tol, iters, fp64["iterations"] if fp64 else st.iterations)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c64 cycle / f64 outer", "data": "synthetic",
+                "config": {"workload": P.name, "unknowns": P.unknowns, "nodes": [P.n, P.n],
+                           "solver": "FGMRES(30) FP64, CSG theta_a=pi/14, V(2,2) omega-Jacobi 0.8, complex64 cycle",
+                           "tol": args.tol, "ecs_theta": "pi/6", "kh_max": 0.6,
+                           "l2": "256 MiB device write before every step, outside the timed events",
+                           "parallelism": "independent problem per rank" if world > 1 else "single GPU"},
+                "solve": {"iterations": st.iterations, "restarts": st.restarts, "rel_res": st.rel_res,
+                          "ms_per_solve": ms_max},
+                "fp64": fp64, "roofline": roof, "kernels": breakdown, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": launches * args.steps, "gpu_launches_per_step": launches,
+                "peaks": peak_src}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

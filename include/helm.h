@@ -99,6 +99,7 @@ typedef struct {
     double time_ms;            /* host wall time of the call                                */
     double *history;           /* optional caller array: estimate per iteration            */
     int history_len;           /* capacity of history (0 if none)                           */
+    int reorthogonalizations;  /* FGMRES: Gram-Schmidt steps that needed a second pass      */
 } helm_stats;
 
 typedef struct helm_handle helm_handle;
@@ -140,9 +141,10 @@ helm_status mg_vcycle(helm_handle *h, const void *b, void *x, helm_prec prec);
 
 /* Solves A x = rhs (A = Z, FP64) to ||rhs - A x|| <= tol ||rhs||, right-preconditioned by one
  * multigrid cycle on M in the precision mg->prec (a complex64 cycle inside FP64 FGMRES, or all
- * FP64).  FGMRES(restart) (Saad's flexible GMRES, classical Gram-Schmidt with one
- * re-orthogonalisation, complex Givens rotations, all in FP64 on the device) or Bi-CGSTAB with
- * two cycles per iteration (Section 5).
+ * FP64).  FGMRES(restart) (Saad's flexible GMRES; classical Gram-Schmidt with a second pass
+ * whenever the first removed more than 1 - 1/sqrt(2) of the vector's norm (DGKS test);
+ * complex Givens rotations; all in FP64 on the device) or Bi-CGSTAB with two cycles per
+ * iteration (Section 5).
  *   rhs   DEVICE c128, unchanged.       x  DEVICE c128: initial guess in, solution out.
  *   tol   relative tolerance (> 0).     restart  FGMRES basis size (1..64; ignored by Bi-CGSTAB).
  *   maxit total iteration cap (> 0).    stats    optional host struct.
@@ -188,6 +190,31 @@ helm_status helm_create_batch(int nprob, const helm_grid *grids, const double *t
 helm_status helm_solve_batch(helm_batch *b, const void *const *rhs, void *const *x, double tol, int restart,
                              int maxit, helm_stats *stats);
 void helm_destroy_batch(helm_batch *b);
+
+/* ---- launch timing (diagnostics; no counterpart in the paper, which reports cputime only) ----
+ * helm_profile(h, 1) resets and enables per-launch timing: every kernel launch of the handle's
+ * drivers is bracketed by two CUDA events on the handle's stream and tagged with its class
+ * and its algorithmic DRAM bytes and flops (each operand touched once).  helm_profile(h, 0)
+ * disables it.  helm_profile_read synchronises the stream and returns, per class, the number
+ * of launches, the summed event time (ms), and the summed algorithmic bytes and flops; the
+ * four host arrays hold ncls entries (ncls <= HELM_K_NCLASS). */
+typedef enum {
+    HELM_K_APPLY = 0,         /* FP64 operator apply (A z, true residual)                */
+    HELM_K_SMOOTH_FINE = 1,   /* smoothing sweeps on the finest level                    */
+    HELM_K_SMOOTH_COARSE = 2, /* smoothing sweeps on the coarser levels                  */
+    HELM_K_RESTRICT = 3,      /* residual + full-weighting restriction                   */
+    HELM_K_PROLONG = 4,       /* bi/trilinear prolongation + correction                  */
+    HELM_K_COARSE = 5,        /* exact coarsest solve                                    */
+    HELM_K_MDOT = 6,          /* Gram-Schmidt pass 1: h = V^H w                          */
+    HELM_K_UPDATE_MDOT = 7,   /* Gram-Schmidt pass 2: w -= V h, h' = V^H w               */
+    HELM_K_UPDATE_NORM = 8,   /* Gram-Schmidt pass 3: w -= V h', ||w||                   */
+    HELM_K_VECTOR = 9,        /* other vector kernels (reductions, scaling, casts, x += Z y) */
+    HELM_K_SMALL = 10,        /* single-warp kernels (Givens, back substitution, scalars) */
+    HELM_K_NCLASS = 11
+} helm_kernel_class;
+
+helm_status helm_profile(helm_handle *h, int enable);
+helm_status helm_profile_read(helm_handle *h, int ncls, int *launches, double *ms, double *bytes, double *flops);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *helm_last_error(void);

@@ -360,6 +360,32 @@ extern "C" void helm_destroy(helm_handle *h) {
     delete h;
 }
 
+extern "C" helm_status helm_profile(helm_handle *h, int enable) {
+    if (!h) return helm_fail(HELM_ERR_ARG, "null handle");
+    CKR(cudaStreamSynchronize(h->stream));
+    h->prof.reset();
+    h->prof.on = enable != 0;
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_profile_read(helm_handle *h, int ncls, int *launches, double *ms, double *bytes,
+                                         double *flops) {
+    if (!h || !launches || !ms || !bytes || !flops || ncls < 1 || ncls > HELM_K_NCLASS)
+        return helm_fail(HELM_ERR_ARG, "bad profile arguments");
+    CKR(cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < ncls; c++) { launches[c] = 0; ms[c] = bytes[c] = flops[c] = 0.0; }
+    for (const ProfRec &r : h->prof.recs) {
+        if (r.cls < 0 || r.cls >= ncls) continue;
+        float t = 0.f;
+        CKR(cudaEventElapsedTime(&t, r.a, r.b));
+        launches[r.cls]++;
+        ms[r.cls] += t;
+        bytes[r.cls] += r.bytes;
+        flops[r.cls] += r.flops;
+    }
+    return HELM_OK;
+}
+
 extern "C" helm_status helm_levels(const helm_handle *h, int *nlev) {
     if (!h || !nlev) return helm_fail(HELM_ERR_ARG, "null argument");
     *nlev = (int)h->lv.size();
@@ -389,30 +415,55 @@ template <> struct LvBuf<float> {
     static const float2 *minv(helm_handle *h) { return h->minv32; }
 };
 
+// Interior node count of a level.
+static double interior(const LevelDev &L, int dim) {
+    return (double)(L.n[0] - 2) * (L.n[1] - 2) * (dim == 3 ? (double)(L.n[2] - 2) : 1.0);
+}
+
 // smoothing steps on level l; *cur holds the iterate and may be swapped with *oth (Jacobi).
+// Algorithmic bytes per sweep and unknown: read u, b, k^2, write u (3 complex + 1 real).
 template <typename R>
 static cudaError_t smooth(helm_handle *h, int l, int sweeps, const typename CT<R>::T *b, typename CT<R>::T **cur,
                           typename CT<R>::T **oth, bool zero) {
     LevelDev &L = h->lv[l];
     const DevOp<R> &op = LvBuf<R>::op(L);
     const R om = (R)h->mg.omega;
+    const int cls = l == 0 ? HELM_K_SMOOTH_FINE : HELM_K_SMOOTH_COARSE;
+    const double es = sizeof(typename CT<R>::T), rs = sizeof(R), ni = interior(L, h->dim);
     if (sweeps == 0) {
-        if (zero) CKE(launch_zero(L.np, *cur, h->stream));
+        if (zero) {
+            ProfScope ps(h, HELM_K_VECTOR, L.np * es, 0);
+            CKE(launch_zero(L.np, *cur, h->stream));
+        }
         return cudaSuccess;
     }
     if (h->mg.smoother == HELM_SMOOTH_RB) {
-        if (zero) CKE(launch_zero(L.np, *cur, h->stream));
+        if (zero) {
+            ProfScope ps(h, HELM_K_VECTOR, L.np * es, 0);
+            CKE(launch_zero(L.np, *cur, h->stream));
+        }
         for (int s = 0; s < sweeps; s++) {
-            CKE(launch_rb<R>(op, h->dim, om, b, *cur, 0, h->stream));
-            CKE(launch_rb<R>(op, h->dim, om, b, *cur, 1, h->stream));
+            for (int colour = 0; colour < 2; colour++) {
+                ProfScope ps(h, cls, 0.5 * ni * (3 * es + rs), 0);
+                CKE(launch_rb<R>(op, h->dim, om, b, *cur, colour, h->stream));
+            }
         }
         return cudaSuccess;
     }
     for (int s = 0; s < sweeps; s++) {
-        CKE(launch_jacobi<R>(op, h->dim, om, b, (zero && s == 0) ? nullptr : *cur, *oth, h->stream));
+        const bool z0 = zero && s == 0;
+        ProfScope ps(h, cls, ni * ((z0 ? 2 : 3) * es + rs), 0);
+        CKE(launch_jacobi<R>(op, h->dim, om, b, z0 ? nullptr : *cur, *oth, h->stream));
         std::swap(*cur, *oth);
     }
     return cudaSuccess;
+}
+
+template <typename R>
+static cudaError_t coarse_solve(helm_handle *h, LevelDev &L, const typename CT<R>::T *b, typename CT<R>::T *u) {
+    const double es = sizeof(typename CT<R>::T), nu = h->nu_c;
+    ProfScope ps(h, HELM_K_COARSE, nu * nu * es + 2 * nu * es, 8.0 * nu * nu);
+    return launch_dense_solve<R>(L.n, h->dim, h->nu_c, LvBuf<R>::minv(h), b, u, h->stream);
 }
 
 // u <- MG(l, M_l, b, u, nu1, nu2, C, gf, gc).  'zero' means u = 0 on entry (not read).
@@ -424,21 +475,28 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
     typedef typename CT<R>::T C;
     LevelDev &L = h->lv[l];
     const int last = (int)h->lv.size() - 1;
-    if (l == last) return launch_dense_solve<R>(L.n, h->dim, h->nu_c, LvBuf<R>::minv(h), b, u, h->stream);
+    if (l == last) return coarse_solve<R>(h, L, b, u);
+    const double es = sizeof(C), rs = sizeof(R), ni = interior(L, h->dim), nd = h->dim == 3 ? 8.0 : 4.0;
     C *cur = u, *oth = LvBuf<R>::t(L);
     CKE(smooth<R>(h, l, h->mg.nu1, b, &cur, &oth, zero));
     LevelDev &Lc = h->lv[l + 1];
-    CKE(launch_residual_restrict<R>(LvBuf<R>::op(L), h->dim, b, cur, LvBuf<R>::b(Lc), h->stream));
+    {
+        ProfScope ps(h, HELM_K_RESTRICT, ni * (2 * es + rs + es / nd), 0);
+        CKE(launch_residual_restrict<R>(LvBuf<R>::op(L), h->dim, b, cur, LvBuf<R>::b(Lc), h->stream));
+    }
     C *ec = LvBuf<R>::u(Lc);
     if (l + 1 == last) {
-        CKE(launch_dense_solve<R>(Lc.n, h->dim, h->nu_c, LvBuf<R>::minv(h), LvBuf<R>::b(Lc), ec, h->stream));
+        CKE(coarse_solve<R>(h, Lc, LvBuf<R>::b(Lc), ec));
     } else {
         for (int i = 1; i <= gc; i++) {
             if (i == 1) CKE(cycle<R>(h, l + 1, LvBuf<R>::b(Lc), ec, true, gf, gc));
             else CKE(cycle<R>(h, l + 1, LvBuf<R>::b(Lc), ec, false, gc, gf));
         }
     }
-    CKE(launch_prolong_add<R>(L.n, h->dim, ec, cur, h->stream));
+    {
+        ProfScope ps(h, HELM_K_PROLONG, ni * (2 * es + es / nd), 0);
+        CKE(launch_prolong_add<R>(L.n, h->dim, ec, cur, h->stream));
+    }
     CKE(smooth<R>(h, l, h->mg.nu2, b, &cur, &oth, false));
     if (cur != u) CKE(cudaMemcpyAsync(u, cur, L.np * sizeof(C), cudaMemcpyDeviceToDevice, h->stream));
     return cudaSuccess;
@@ -447,10 +505,17 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
 // z = M^{-1}-approximation of v (one cycle from zero), v in FP64, z in precision R.
 template <typename R>
 cudaError_t precondition(helm_handle *h, const double2 *v, typename CT<R>::T *z) {
-    if (h->mg.kind == HELM_PC_NONE) return launch_convert(h->np, v, z, h->stream);
+    const double es = sizeof(typename CT<R>::T);
+    if (h->mg.kind == HELM_PC_NONE) {
+        ProfScope ps(h, HELM_K_VECTOR, h->np * (16 + es), 0);
+        return launch_convert(h->np, v, z, h->stream);
+    }
     if (sizeof(R) == sizeof(double))
         return cycle<R>(h, 0, (const typename CT<R>::T *)v, z, true, h->mg.gamma_f, h->mg.gamma_c);
-    CKE(launch_convert(h->np, v, LvBuf<R>::b(h->lv[0]), h->stream));
+    {
+        ProfScope ps(h, HELM_K_VECTOR, h->np * (16 + es), 0);
+        CKE(launch_convert(h->np, v, LvBuf<R>::b(h->lv[0]), h->stream));
+    }
     return cycle<R>(h, 0, LvBuf<R>::b(h->lv[0]), z, true, h->mg.gamma_f, h->mg.gamma_c);
 }
 template cudaError_t precondition<float>(helm_handle *, const double2 *, float2 *);

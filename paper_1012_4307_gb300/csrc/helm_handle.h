@@ -21,7 +21,34 @@ struct LevelDev {
     float2 *b32 = nullptr, *u32 = nullptr, *t32 = nullptr;
 };
 
+// Opt-in launch timing: when on, every kernel launch of the drivers is bracketed by two CUDA
+// events on the handle's stream and tagged with its class and algorithmic bytes / flops.
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes, flops;
+};
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<ProfRec> recs;
+    cudaEvent_t next() {
+        if (used == pool.size()) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void reset() { used = 0; recs.clear(); }
+    ~Profiler() {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+};
+
 struct helm_handle {
+    Profiler prof;
     int dim = 2;
     int n[3] = {1, 1, 1};
     size_t np = 0;
@@ -54,6 +81,8 @@ struct helm_handle {
     double2 *partials = nullptr;
     double2 *scal = nullptr;   // scalar scratch (norms, Bi-CGSTAB scalars)
     double *est_dev = nullptr;
+    int *gs_flag = nullptr;   // DGKS decision of the current Arnoldi step (device)
+    int *gs_count = nullptr;  // re-orthogonalisations in the current solve (device)
     double *est_host = nullptr;  // pinned
     // Bi-CGSTAB workspace
     bool bicg_alloc = false;
@@ -62,6 +91,28 @@ struct helm_handle {
     // adjoint temporaries
     double2 *adj_rhs = nullptr, *adj_y = nullptr;
     std::vector<void *> krylov_owned;
+};
+
+// Launch-timing scope: records a start event now and, at destruction, a stop event plus the
+// launch's class and algorithmic cost.  A no-op unless the handle's profiler is on.
+struct ProfScope {
+    helm_handle *h;
+    int cls;
+    double bytes, flops;
+    cudaEvent_t a = nullptr;
+    ProfScope(helm_handle *h_, int cls_, double bytes_, double flops_) : h(h_), cls(cls_), bytes(bytes_), flops(flops_) {
+        if (h->prof.on) {
+            a = h->prof.next();
+            if (a) cudaEventRecord(a, h->stream);
+        }
+    }
+    ~ProfScope() {
+        if (!a) return;
+        cudaEvent_t b = h->prof.next();
+        if (!b) return;
+        cudaEventRecord(b, h->stream);
+        h->prof.recs.push_back(ProfRec{cls, a, b, bytes, flops});
+    }
 };
 
 helm_status helm_fail(helm_status st, const char *fmt, ...);

@@ -93,18 +93,22 @@ cudaError_t launch_zero(size_t n, C *x, cudaStream_t s);
 
 // FP64 vector kernels on full node arrays (boundary values are zero, so sums over all nodes
 // equal sums over unknowns).
-// partial sums of conj(V_i) . w for i in [0, nv): partials[(i * nblk) + blk]
+// Number of blocks of every reduction over n nodes (fixed per n, so sums are reproducible).
 int blas_nblocks(size_t n);
-cudaError_t launch_mdot(size_t n, const double2 *V, size_t ldv, int nv, const double2 *w, double2 *partials,
-                        cudaStream_t s);
-// w -= sum_i V_i h_i, then partials of conj(V_i) . w   (h on device)
-cudaError_t launch_update_mdot(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
-                               double2 *partials, cudaStream_t s);
-// w -= sum_i V_i h_i, then partials of ||w||^2 in .x
+// Gram-Schmidt passes (gate: device int; the kernel returns at once when *gate == 0).
+// partials[i * G + b] = sum conj(V_i) w (i < nv) and partials[nv * G + b] = (||w||^2, 0),
+// G = blas_nblocks(n).
+cudaError_t launch_mdot_norm(size_t n, const double2 *V, size_t ldv, int nv, const double2 *w, double2 *partials,
+                             const int *gate, cudaStream_t s);
+// w -= sum_i V_i h_i, then partials[b] = (||w||^2, 0)   (h on device)
 cudaError_t launch_update_norm(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
-                               double2 *partials, cudaStream_t s);
-// out[i] (mode 0: =, 1: +=) sum of partials of vector i; mode 2: out[i] = (sqrt(re), 0)
-cudaError_t launch_reduce(const double2 *partials, int nblk, int nv, double2 *out, int mode, cudaStream_t s);
+                               double2 *partials, const int *gate, cudaStream_t s);
+// out[i] (mode 0: =, 1: +=, 2: (sqrt(re), 0)) = fixed-order sum of partials of vector i
+cudaError_t launch_reduce(const double2 *partials, int nblk, int nv, double2 *out, int mode, const int *gate,
+                          cudaStream_t s);
+// *hnorm: ||w||^2 in, ||w'|| out; *flag = (||w'|| < eta ||w||); *count += flag
+cudaError_t launch_reduce_decide(const double2 *partials, int nblk, double2 *hnorm, int *flag, int *count, double eta,
+                                 cudaStream_t s);
 // y = x * (1 / scale[0].x)
 cudaError_t launch_scale_inv(size_t n, const double2 *x, const double2 *scale, double2 *y, cudaStream_t s);
 // x += sum_c y_c Z_c  (Z c64 or c128, ldz stride)

@@ -2,13 +2,12 @@
 // adjoint helpers.  All sums use a fixed grid (a function of the vector length only) and a
 // fixed reduction tree, so repeated runs give bit-identical results.
 //
-// Classical Gram-Schmidt with one re-orthogonalisation (CGS2) is done in three passes over
-// the basis instead of four:
-//   pass 1  h1 = V^H w                                   (k_mdot)
-//   pass 2  w <- w - V h1, then h2 = V^H w, same sweep   (k_update_mdot)
-//   pass 3  w <- w - V h2, then ||w||^2, same sweep      (k_update_norm)
-// Every thread owns one node at a time and keeps one accumulator per basis vector in
-// registers (MAXV buckets), so w is read once per pass and V once per pass from DRAM.
+// Classical Gram-Schmidt runs as two fused passes over the basis:
+//   "dot"     h = V^H w and ||w||^2                 (k_mdot_norm, 8 basis vectors per block row)
+//   "update"  w <- w - V h and ||w'||^2, same sweep (k_update_norm)
+// followed by the DGKS test on the device (k_reduce_decide); the optional second pass reuses
+// the same kernels, gated by the device flag, so the host never waits for the decision.
+// On GB300 the FP64 units (about 2 FMA per SM per clock) bound these kernels, not DRAM.
 #include "helm_internal.h"
 
 namespace {
@@ -22,109 +21,114 @@ __device__ __forceinline__ double2 shfl_down2(double2 v, int off) {
     return v;
 }
 
-// Reduce acc[0..nv) over the block; thread 0 of warp 0 writes partials[i * nblk + blockIdx.x].
-template <int MAXV>
-__device__ __forceinline__ void block_store(double2 (&acc)[MAXV], int nv, double2 *partials) {
-    __shared__ double2 red[NT / 32][MAXV];
+// Block-wide sums of NV complex values per thread (fixed tree: warp shuffles, then warps in
+// order); thread t < NV returns sum t in out[t] (other threads: unspecified).
+template <int NV>
+__device__ __forceinline__ void block_sum(double2 (&v)[NV], double2 *out_shared) {
+    __shared__ double2 red[NT / 32][NV];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < MAXV; i++) {
-        if (i < nv) {
-            double2 v = acc[i];
+    for (int i = 0; i < NV; i++) {
+        double2 x = v[i];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v = cadd(v, shfl_down2(v, off));
-            if (lane == 0) red[warp][i] = v;
-        }
+        for (int off = 16; off > 0; off >>= 1) x = cadd(x, shfl_down2(x, off));
+        if (lane == 0) red[warp][i] = x;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nv; i += NT) {
-        double2 s = red[0][i];
-        for (int w = 1; w < NT / 32; w++) s = cadd(s, red[w][i]);
-        partials[(size_t)i * gridDim.x + blockIdx.x] = s;
+    if (threadIdx.x < NV) {
+        double2 s = red[0][threadIdx.x];
+        for (int w = 1; w < NT / 32; w++) s = cadd(s, red[w][threadIdx.x]);
+        out_shared[threadIdx.x] = s;
     }
 }
 
-template <int MAXV>
-__global__ void __launch_bounds__(NT) k_mdot(size_t n, const double2 *__restrict__ V, size_t ldv, int nv,
-                                             const double2 *__restrict__ w, double2 *__restrict__ partials) {
-    double2 acc[MAXV];
+// Pass "dot": partials[i * G + b] = sum_q conj(V_i[q]) w[q] for the CH vectors of chunk
+// blockIdx.y (i < nv), and chunk 0 also partials[nv * G + b] = (sum |w[q]|^2, 0).
+// Grid (G, max(1, ceil(nv / CH))).  Skipped entirely when *gate == 0.
+template <int CH>
+__global__ void __launch_bounds__(NT) k_mdot_norm(size_t n, const double2 *__restrict__ V, size_t ldv, int nv,
+                                                  const double2 *__restrict__ w, double2 *__restrict__ partials,
+                                                  const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    __shared__ double2 sums[CH + 1];
+    const int i0 = blockIdx.y * CH;
+    const int cnt = min(CH, nv - i0);
+    const bool first = blockIdx.y == 0;
+    double2 acc[CH + 1];
 #pragma unroll
-    for (int i = 0; i < MAXV; i++) acc[i] = make_double2(0.0, 0.0);
+    for (int t = 0; t <= CH; t++) acc[t] = make_double2(0.0, 0.0);
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const double2 wq = w[q];
+        if (first) acc[CH].x = fma(wq.x, wq.x, fma(wq.y, wq.y, acc[CH].x));
 #pragma unroll
-        for (int i = 0; i < MAXV; i++)
-            if (i < nv) acc[i] = cfmac(V[(size_t)i * ldv + q], wq, acc[i]);
+        for (int t = 0; t < CH; t++)
+            if (t < cnt) acc[t] = cfmac(V[(size_t)(i0 + t) * ldv + q], wq, acc[t]);
     }
-    block_store<MAXV>(acc, nv, partials);
+    block_sum<CH + 1>(acc, sums);
+    const int G = gridDim.x;
+    if (threadIdx.x < CH && (int)threadIdx.x < cnt) partials[(size_t)(i0 + threadIdx.x) * G + blockIdx.x] = sums[threadIdx.x];
+    if (first && threadIdx.x == CH) partials[(size_t)nv * G + blockIdx.x] = sums[CH];
 }
 
-template <int MAXV>
-__global__ void __launch_bounds__(NT) k_update_mdot(size_t n, const double2 *__restrict__ V, size_t ldv, int nv,
-                                                    const double2 *__restrict__ h, double2 *__restrict__ w,
-                                                    double2 *__restrict__ partials) {
-    __shared__ double2 hs[MAXV];
-    for (int i = threadIdx.x; i < nv; i += NT) hs[i] = h[i];
-    __syncthreads();
-    double2 acc[MAXV];
-#pragma unroll
-    for (int i = 0; i < MAXV; i++) acc[i] = make_double2(0.0, 0.0);
-    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
-        double2 wq = w[q];
-#pragma unroll
-        for (int i = 0; i < MAXV; i++)
-            if (i < nv) {
-                const double2 v = V[(size_t)i * ldv + q];
-                const double2 hh = hs[i];
-                wq = make_double2(wq.x - (v.x * hh.x - v.y * hh.y), wq.y - (v.x * hh.y + v.y * hh.x));
-            }
-        w[q] = wq;
-#pragma unroll
-        for (int i = 0; i < MAXV; i++)
-            if (i < nv) acc[i] = cfmac(V[(size_t)i * ldv + q], wq, acc[i]);
-    }
-    block_store<MAXV>(acc, nv, partials);
-}
-
-template <int MAXV>
+// Pass "update": w -= sum_{i < nv} V_i h_i, then partials[b] = (sum |w|^2, 0).  Gated.
 __global__ void __launch_bounds__(NT) k_update_norm(size_t n, const double2 *__restrict__ V, size_t ldv, int nv,
                                                     const double2 *__restrict__ h, double2 *__restrict__ w,
-                                                    double2 *__restrict__ partials) {
-    __shared__ double2 hs[MAXV];
+                                                    double2 *__restrict__ partials, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    __shared__ double2 hs[64];
+    __shared__ double2 sums[1];
     for (int i = threadIdx.x; i < nv; i += NT) hs[i] = h[i];
     __syncthreads();
     double2 acc[1] = {make_double2(0.0, 0.0)};
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         double2 wq = w[q];
-#pragma unroll
-        for (int i = 0; i < MAXV; i++)
-            if (i < nv) {
-                const double2 v = V[(size_t)i * ldv + q];
-                const double2 hh = hs[i];
-                wq = make_double2(wq.x - (v.x * hh.x - v.y * hh.y), wq.y - (v.x * hh.y + v.y * hh.x));
-            }
+#pragma unroll 8
+        for (int i = 0; i < nv; i++) {
+            const double2 v = V[(size_t)i * ldv + q];
+            const double2 hh = hs[i];
+            wq.x = fma(-v.x, hh.x, fma(v.y, hh.y, wq.x));
+            wq.y = fma(-v.x, hh.y, fma(-v.y, hh.x, wq.y));
+        }
         w[q] = wq;
         acc[0].x = fma(wq.x, wq.x, fma(wq.y, wq.y, acc[0].x));
     }
-    block_store<1>(acc, 1, partials);
+    block_sum<1>(acc, sums);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sums[0];
 }
 
-// out[i] = sum_b partials[i * nblk + b] in a fixed order; mode 0 '=', 1 '+=', 2 sqrt(re).
-__global__ void k_reduce(const double2 *__restrict__ partials, int nblk, double2 *__restrict__ out, int mode) {
-    __shared__ double2 red[NT / 32];
+// out[i] = sum_b partials[i * nblk + b] in a fixed order for i = blockIdx.x; mode 0 '=',
+// 1 '+=', 2 (sqrt(re), 0).  Gated.
+__global__ void k_reduce(const double2 *__restrict__ partials, int nblk, double2 *__restrict__ out, int mode,
+                         const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    __shared__ double2 sums[1];
     const int i = blockIdx.x;
-    double2 s = make_double2(0.0, 0.0);
-    for (int b = threadIdx.x; b < nblk; b += NT) s = cadd(s, partials[(size_t)i * nblk + b]);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s = cadd(s, shfl_down2(s, off));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
+    double2 s[1] = {make_double2(0.0, 0.0)};
+    for (int b = threadIdx.x; b < nblk; b += NT) s[0] = cadd(s[0], partials[(size_t)i * nblk + b]);
+    block_sum<1>(s, sums);
     if (threadIdx.x == 0) {
-        double2 t = red[0];
-        for (int w = 1; w < NT / 32; w++) t = cadd(t, red[w]);
+        const double2 t = sums[0];
         if (mode == 0) out[i] = t;
         else if (mode == 1) out[i] = cadd(out[i], t);
         else out[i] = make_double2(sqrt(t.x), 0.0);
+    }
+}
+
+// DGKS test after one classical Gram-Schmidt pass: the new norm ||w'|| = sqrt(sum partials)
+// is written to *hnorm (which held ||w||^2 before the pass); re-orthogonalise (*flag = 1) when
+// ||w'|| < eta ||w||, i.e. when the projection cancelled most of w.
+__global__ void k_reduce_decide(const double2 *__restrict__ partials, int nblk, double2 *hnorm, int *flag, int *count,
+                                double eta) {
+    __shared__ double2 sums[1];
+    double2 s[1] = {make_double2(0.0, 0.0)};
+    for (int b = threadIdx.x; b < nblk; b += NT) s[0] = cadd(s[0], partials[b]);
+    block_sum<1>(s, sums);
+    if (threadIdx.x == 0) {
+        const double before = sqrt(hnorm->x), after = sqrt(sums[0].x);
+        const int redo = !(after >= eta * before);
+        *flag = redo;
+        if (redo) *count += 1;
+        *hnorm = make_double2(after, 0.0);
     }
 }
 
@@ -276,37 +280,31 @@ unsigned stream_grid(size_t n) { return (unsigned)std::min<size_t>(cdiv(n, NT), 
 
 int blas_nblocks(size_t n) { return (int)std::min<size_t>(cdiv(n, NT), (size_t)MAXBLK); }
 
-#define DISPATCH_MAXV(nv, KERNEL, ...)                                                         \
-    do {                                                                                       \
-        if ((nv) <= 8) KERNEL<8><<<blas_nblocks(n), NT, 0, s>>>(__VA_ARGS__);                  \
-        else if ((nv) <= 16) KERNEL<16><<<blas_nblocks(n), NT, 0, s>>>(__VA_ARGS__);           \
-        else if ((nv) <= 32) KERNEL<32><<<blas_nblocks(n), NT, 0, s>>>(__VA_ARGS__);           \
-        else KERNEL<64><<<blas_nblocks(n), NT, 0, s>>>(__VA_ARGS__);                           \
-    } while (0)
-
-cudaError_t launch_mdot(size_t n, const double2 *V, size_t ldv, int nv, const double2 *w, double2 *partials,
-                        cudaStream_t s) {
-    if (nv > 64) return cudaErrorInvalidValue;
-    DISPATCH_MAXV(nv, k_mdot, n, V, ldv, nv, w, partials);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_update_mdot(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
-                               double2 *partials, cudaStream_t s) {
-    if (nv > 64) return cudaErrorInvalidValue;
-    DISPATCH_MAXV(nv, k_update_mdot, n, V, ldv, nv, h, w, partials);
+cudaError_t launch_mdot_norm(size_t n, const double2 *V, size_t ldv, int nv, const double2 *w, double2 *partials,
+                             const int *gate, cudaStream_t s) {
+    if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
+    constexpr int CH = 8;
+    dim3 g(blas_nblocks(n), std::max(1, (nv + CH - 1) / CH));
+    k_mdot_norm<CH><<<g, NT, 0, s>>>(n, V, ldv, nv, w, partials, gate);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update_norm(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
-                               double2 *partials, cudaStream_t s) {
-    if (nv > 64) return cudaErrorInvalidValue;
-    DISPATCH_MAXV(nv, k_update_norm, n, V, ldv, nv, h, w, partials);
+                               double2 *partials, const int *gate, cudaStream_t s) {
+    if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
+    k_update_norm<<<blas_nblocks(n), NT, 0, s>>>(n, V, ldv, nv, h, w, partials, gate);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const double2 *partials, int nblk, int nv, double2 *out, int mode, cudaStream_t s) {
-    k_reduce<<<nv, NT, 0, s>>>(partials, nblk, out, mode);
+cudaError_t launch_reduce(const double2 *partials, int nblk, int nv, double2 *out, int mode, const int *gate,
+                          cudaStream_t s) {
+    k_reduce<<<nv, NT, 0, s>>>(partials, nblk, out, mode, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_decide(const double2 *partials, int nblk, double2 *hnorm, int *flag, int *count, double eta,
+                                 cudaStream_t s) {
+    k_reduce_decide<<<1, NT, 0, s>>>(partials, nblk, hnorm, flag, count, eta);
     return cudaGetLastError();
 }
 

@@ -20,11 +20,16 @@
         if (e_ != cudaSuccess) return helm_fail(HELM_ERR_CUDA, "%s: %s", #__VA_ARGS__, cudaGetErrorString(e_));   \
     } while (0)
 
+// DGKS threshold: re-orthogonalise when one Gram-Schmidt pass removed more than 1 - 1/sqrt(2)
+// of the vector's norm (Daniel, Gragg, Kaufman & Stewart, Math. Comp. 30, 1976).
+static const double kDGKSEta = 0.70710678118654752;
+
 static void free_krylov(helm_handle *h) {
     for (void *p : h->krylov_owned) cudaFree(p);
     h->krylov_owned.clear();
     h->V = nullptr; h->Z = nullptr; h->H = nullptr; h->g = h->sn = h->y = h->h2 = nullptr;
     h->cs = nullptr; h->partials = nullptr; h->scal = nullptr; h->est_dev = nullptr;
+    h->gs_flag = h->gs_count = nullptr;
     h->m_alloc = 0;
     h->bicg_alloc = false;
     h->br = h->brh = h->bp = h->bv = h->bs = h->bt = nullptr;
@@ -68,6 +73,8 @@ static helm_status ensure_ws(helm_handle *h, int m) {
     KA(&h->partials, (size_t)nblk * 65);
     KA(&h->scal, 32);
     KA(&h->est_dev, 4);
+    KA(&h->gs_flag, 4);
+    h->gs_count = h->gs_flag + 1;
 #undef KA
     if (e != cudaSuccess) {
         free_krylov(h);
@@ -107,15 +114,17 @@ static helm_status ensure_bicg(helm_handle *h) {
 
 // ||x||_2 -> out (device scalar, .x); optionally read back to the host.
 static cudaError_t dev_norm(helm_handle *h, const double2 *x, double2 *out) {
-    cudaError_t e = launch_mdot(h->np, x, h->np, 1, x, h->partials, h->stream);
+    ProfScope ps(h, HELM_K_VECTOR, h->np * 16.0, h->np * 4.0);
+    cudaError_t e = launch_mdot_norm(h->np, nullptr, h->np, 0, x, h->partials, nullptr, h->stream);
     if (e != cudaSuccess) return e;
-    return launch_reduce(h->partials, blas_nblocks(h->np), 1, out, 2, h->stream);
+    return launch_reduce(h->partials, blas_nblocks(h->np), 1, out, 2, nullptr, h->stream);
 }
 
 static cudaError_t dev_dot(helm_handle *h, const double2 *a, const double2 *b, double2 *out) {
-    cudaError_t e = launch_mdot(h->np, a, h->np, 1, b, h->partials, h->stream);
+    ProfScope ps(h, HELM_K_VECTOR, h->np * 32.0, h->np * 12.0);
+    cudaError_t e = launch_mdot_norm(h->np, a, h->np, 1, b, h->partials, nullptr, h->stream);
     if (e != cudaSuccess) return e;
-    return launch_reduce(h->partials, blas_nblocks(h->np), 1, out, 0, h->stream);
+    return launch_reduce(h->partials, blas_nblocks(h->np), 1, out, 0, nullptr, h->stream);
 }
 
 static helm_status read_scalars(helm_handle *h, const void *dev, size_t bytes, void *host) {
@@ -125,16 +134,27 @@ static helm_status read_scalars(helm_handle *h, const void *dev, size_t bytes, v
     return HELM_OK;
 }
 
+// Algorithmic cost of one FP64 apply over the interior (read x, k^2, write y; 5- or 7-point
+// complex stencil: one complex multiply-add per neighbour and for the diagonal, plus the
+// diagonal's assembly).
+static double interior_pts(const helm_handle *h) {
+    return (double)(h->n[0] - 2) * (h->n[1] - 2) * (h->dim == 3 ? (double)(h->n[2] - 2) : 1.0);
+}
+static double apply_flops(const helm_handle *h) { return interior_pts(h) * (h->dim == 3 ? 68.0 : 48.0); }
+
 // z = precondition(v) in the workspace precision; w = A z (FP64)
 static cudaError_t precond_apply(helm_handle *h, const double2 *v, void *z, double2 *w) {
     cudaError_t e;
+    const double ni = interior_pts(h);
     if (h->z_prec == HELM_C64) {
         e = precondition<float>(h, v, (float2 *)z);
         if (e != cudaSuccess) return e;
+        ProfScope ps(h, HELM_K_APPLY, ni * (8 + 8 + 16), apply_flops(h));
         return launch_apply<double, float2>(h->A64, h->dim, (const float2 *)z, w, h->stream);
     }
     e = precondition<double>(h, v, (double2 *)z);
     if (e != cudaSuccess) return e;
+    ProfScope ps(h, HELM_K_APPLY, ni * (16 + 8 + 16), apply_flops(h));
     return launch_apply<double, double2>(h->A64, h->dim, (const double2 *)z, w, h->stream);
 }
 
@@ -156,6 +176,7 @@ static helm_status fgmres(helm_handle *h, const double2 *f, double2 *x, double t
     int it = 0, restarts = 0;
     double est = 1.0, rel = 1.0;
     helm_status status = HELM_ERR_NOCONV;
+    CKR(cudaMemsetAsync(h->gs_flag, 0, 2 * sizeof(int), s));
     if (fn == 0.0) {
         CKR(cudaMemsetAsync(x, 0, np * sizeof(double2), s));
         CKR(cudaStreamSynchronize(s));
@@ -164,7 +185,10 @@ static helm_status fgmres(helm_handle *h, const double2 *f, double2 *x, double t
     }
     for (;;) {
         // r0 = f - A x -> V_0, beta = ||r0||
-        CKR(launch_residual<double, double2>(h->A64, h->dim, f, x, h->V, s));
+        {
+            ProfScope ps(h, HELM_K_APPLY, interior_pts(h) * (16 + 16 + 8 + 16), apply_flops(h) + 2 * interior_pts(h));
+            CKR(launch_residual<double, double2>(h->A64, h->dim, f, x, h->V, s));
+        }
         CKR(dev_norm(h, h->V, h->scal));
         if ((rs = read_scalars(h, h->scal, sizeof(double2), hv)) != HELM_OK) return rs;
         const double beta = hv[0].x;
@@ -183,16 +207,52 @@ static helm_status fgmres(helm_handle *h, const double2 *f, double2 *x, double t
             void *zj = (char *)h->Z + (size_t)j * np * zsz;
             CKR(precond_apply(h, vj, zj, w));
             double2 *hcol = h->H + (size_t)ldh * j;
-            // CGS2: h1 = V^H w ; w -= V h1, h2 = V^H w ; w -= V h2, ||w||
-            CKR(launch_mdot(np, h->V, np, j + 1, w, h->partials, s));
-            CKR(launch_reduce(h->partials, nblk, j + 1, hcol, 0, s));
-            CKR(launch_update_mdot(np, h->V, np, j + 1, hcol, w, h->partials, s));
-            CKR(launch_reduce(h->partials, nblk, j + 1, h->h2, 0, s));
-            CKR(launch_reduce(h->partials, nblk, j + 1, hcol, 1, s));
-            CKR(launch_update_norm(np, h->V, np, j + 1, h->h2, w, h->partials, s));
-            CKR(launch_reduce(h->partials, nblk, 1, hcol + j + 1, 2, s));
-            CKR(launch_scale_inv(np, w, hcol + j + 1, w, s));
-            CKR(launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, fn, h->est_dev, s));
+            const double nv = j + 1;
+            // Classical Gram-Schmidt with the DGKS re-orthogonalisation test:
+            //   h = V^H w (and ||w||^2 into H[j+1][j]);  w -= V h, ||w'||;
+            //   if ||w'|| < eta ||w||:  h' = V^H w, H[:, j] += h';  w -= V h', ||w''||.
+            // The second pass runs only when the device flag is set (gated kernels).
+            {
+                ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (nv + 1), np * (8.0 * nv + 4.0));
+                CKR(launch_mdot_norm(np, h->V, np, j + 1, w, h->partials, nullptr, s));
+            }
+            {
+                ProfScope ps(h, HELM_K_SMALL, 0, 0);
+                CKR(launch_reduce(h->partials, nblk, j + 2, hcol, 0, nullptr, s));
+            }
+            {
+                ProfScope ps(h, HELM_K_UPDATE_NORM, np * 16.0 * (nv + 2), np * (8.0 * nv + 4.0));
+                CKR(launch_update_norm(np, h->V, np, j + 1, hcol, w, h->partials, nullptr, s));
+            }
+            {
+                ProfScope ps(h, HELM_K_SMALL, 0, 0);
+                CKR(launch_reduce_decide(h->partials, nblk, hcol + j + 1, h->gs_flag, h->gs_count, kDGKSEta, s));
+            }
+            {
+                ProfScope ps(h, HELM_K_MDOT, 0, 0);  // gated: cost counted only if it runs (unknown here)
+                CKR(launch_mdot_norm(np, h->V, np, j + 1, w, h->partials, h->gs_flag, s));
+            }
+            {
+                ProfScope ps(h, HELM_K_SMALL, 0, 0);
+                CKR(launch_reduce(h->partials, nblk, j + 1, h->h2, 0, h->gs_flag, s));
+                CKR(launch_reduce(h->partials, nblk, j + 1, hcol, 1, h->gs_flag, s));
+            }
+            {
+                ProfScope ps(h, HELM_K_UPDATE_NORM, 0, 0);
+                CKR(launch_update_norm(np, h->V, np, j + 1, h->h2, w, h->partials, h->gs_flag, s));
+            }
+            {
+                ProfScope ps(h, HELM_K_SMALL, 0, 0);
+                CKR(launch_reduce(h->partials, nblk, 1, hcol + j + 1, 2, h->gs_flag, s));
+            }
+            {
+                ProfScope ps(h, HELM_K_VECTOR, np * 32.0, np * 2.0);
+                CKR(launch_scale_inv(np, w, hcol + j + 1, w, s));
+            }
+            {
+                ProfScope ps(h, HELM_K_SMALL, 0, 0);
+                CKR(launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, fn, h->est_dev, s));
+            }
             double e1;
             if ((rs = read_scalars(h, h->est_dev, sizeof(double), &e1)) != HELM_OK) return rs;
             it++;
@@ -204,18 +264,27 @@ static helm_status fgmres(helm_handle *h, const double2 *f, double2 *x, double t
         }
         if (nonfinite) { status = HELM_ERR_NONFINITE; break; }
         // x += Z y with y = H^{-1} g
-        CKR(launch_backsolve(h->H, ldh, jdone, h->g, h->y, s));
-        if (h->z_prec == HELM_C64)
-            CKR(launch_combine<float2>(np, (const float2 *)h->Z, np, jdone, h->y, x, s));
-        else
-            CKR(launch_combine<double2>(np, (const double2 *)h->Z, np, jdone, h->y, x, s));
+        {
+            ProfScope ps(h, HELM_K_SMALL, 0, 0);
+            CKR(launch_backsolve(h->H, ldh, jdone, h->g, h->y, s));
+        }
+        {
+            ProfScope ps(h, HELM_K_VECTOR, np * (32.0 + zsz * jdone), np * 8.0 * jdone);
+            if (h->z_prec == HELM_C64)
+                CKR(launch_combine<float2>(np, (const float2 *)h->Z, np, jdone, h->y, x, s));
+            else
+                CKR(launch_combine<double2>(np, (const double2 *)h->Z, np, jdone, h->y, x, s));
+        }
     }
     if (st) {
+        int cnt[2] = {0, 0};
+        if ((rs = read_scalars(h, h->gs_flag, 2 * sizeof(int), cnt)) != HELM_OK) return rs;
         st->iterations = it;
         st->restarts = restarts;
         st->rel_res = rel;
         st->est_res = est;
         st->status = status;
+        st->reorthogonalizations = cnt[1];
     }
     if (status == HELM_ERR_NONFINITE) return helm_fail(status, "non-finite residual in FGMRES");
     if (status == HELM_ERR_NOCONV) return helm_fail(status, "FGMRES: %d iterations, rel. residual %.3e > %.3e", it, rel, tol);

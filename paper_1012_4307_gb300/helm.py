@@ -59,7 +59,7 @@ class _MG(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("status", C.c_int), ("rel_res", C.c_double),
                 ("est_res", C.c_double), ("time_ms", C.c_double), ("history", C.c_void_p),
-                ("history_len", C.c_int)]
+                ("history_len", C.c_int), ("reorthogonalizations", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -95,6 +95,8 @@ def load(build: bool = True):
             "helm_create_batch": ([I, P, P, P, P, P, P, P], I),
             "helm_solve_batch": ([P, P, P, D, I, I, P], I),
             "helm_destroy_batch": ([P], None),
+            "helm_profile": ([P, I], I),
+            "helm_profile_read": ([P, I, P, P, P, P], I),
             "helm_last_error": ([], C.c_char_p),
             "helm_version": ([], C.c_char_p),
         }
@@ -267,10 +269,12 @@ class Stats:
     est_res: float = float("nan")
     time_ms: float = 0.0
     history: list = field(default_factory=list)
+    reorthogonalizations: int = 0
 
 
 def _stats_from(s: _Stats, hist) -> Stats:
     out = Stats(s.iterations, s.restarts, s.status, s.rel_res, s.est_res, s.time_ms)
+    out.reorthogonalizations = s.reorthogonalizations
     if hist is not None:
         out.history = list(hist[: min(s.iterations, len(hist))])
     return out
@@ -318,6 +322,23 @@ def helm_mg_conv(h: Handle, b: torch.Tensor, tol=1e-6, maxcyc=100):
     _check(load().helm_mg_conv(h.ptr, C.c_void_p(_vec(b, h.np, "b")), C.c_void_p(_vec(x, h.np, "x", b.dtype)),
                                _prec_of(b), float(tol), int(maxcyc), C.byref(nc), C.byref(fac)))
     return x, nc.value, fac.value
+
+
+KERNEL_CLASSES = ["apply", "smooth_fine", "smooth_coarse", "restrict", "prolong", "coarse", "mdot",
+                  "update_mdot", "update_norm", "vector", "small"]
+
+
+def helm_profile(h: Handle, enable: bool = True):
+    """Reset and enable (or disable) per-launch CUDA-event timing on the handle's stream."""
+    _check(load().helm_profile(h.ptr, 1 if enable else 0))
+
+
+def helm_profile_read(h: Handle) -> dict:
+    """Per kernel class: launches, summed event time (ms), algorithmic bytes and flops."""
+    nc = len(KERNEL_CLASSES)
+    la, ms, by, fl = (C.c_int * nc)(), (C.c_double * nc)(), (C.c_double * nc)(), (C.c_double * nc)()
+    _check(load().helm_profile_read(h.ptr, nc, la, ms, by, fl))
+    return {name: dict(launches=la[i], ms=ms[i], bytes=by[i], flops=fl[i]) for i, name in enumerate(KERNEL_CLASSES)}
 
 
 class Batch:

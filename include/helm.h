@@ -67,6 +67,14 @@ typedef enum { HELM_OP_A = 0, HELM_OP_M = 1 } helm_op;                   /* A = 
 typedef enum { HELM_FGMRES = 0, HELM_BICGSTAB = 1 } helm_krylov;
 typedef enum { HELM_SMOOTH_JACOBI = 0, HELM_SMOOTH_RB = 1 } helm_smoother;
 
+/* Arithmetic of the Gram-Schmidt inner products and updates in FGMRES.  The Krylov vectors
+ * are FP64 in memory either way.
+ *   FP64: IEEE FP64 fused multiply-adds (bound by GB300's FP64 units).
+ *   DF:   each FP64 operand split exactly into two floats, error-free products and sums on
+ *         the FP32 units, rounded to FP64 once per result (about 46 significant bits per
+ *         product, 48 per sum; bound by DRAM). */
+typedef enum { HELM_GS_FP64 = 0, HELM_GS_DF = 1 } helm_gs_arith;
+
 /* Uniform real grid: n[a] nodes on [lo[a], hi[a]] per axis, boundary nodes included
  * (n - 2 unknowns per axis).  dim is 2 or 3; unused entries are ignored. */
 typedef struct {
@@ -87,6 +95,7 @@ typedef struct {
     int gamma_f, gamma_c;      /* cycle indices: (1,1) V, (1,2) F, (2,2) W            */
     int coarsest_n;            /* coarsen while some axis has more nodes than this    */
     helm_prec prec;            /* arithmetic of the cycle inside krylov_solve         */
+    helm_gs_arith gs_arith;    /* arithmetic of FGMRES's Gram-Schmidt (FP64 vectors)  */
 } helm_mg_params;
 
 /* Solver statistics (host struct, filled by the solvers). */

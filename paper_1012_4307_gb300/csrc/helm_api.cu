@@ -198,6 +198,7 @@ helm_status helm_validate_create(const helm_grid *grid, const double *r0_lo, con
     if (mg->prec != HELM_C128 && mg->prec != HELM_C64) return helm_fail(HELM_ERR_ARG, "bad precision");
     if (mg->smoother != HELM_SMOOTH_JACOBI && mg->smoother != HELM_SMOOTH_RB) return helm_fail(HELM_ERR_ARG, "bad smoother");
     if (mg->coarsest_n < 3) return helm_fail(HELM_ERR_ARG, "coarsest_n must be >= 3");
+    if (mg->gs_arith != HELM_GS_FP64 && mg->gs_arith != HELM_GS_DF) return helm_fail(HELM_ERR_ARG, "bad gs_arith");
     return HELM_OK;
 }
 
@@ -319,6 +320,19 @@ helm_status helm_create_impl(const helm_grid *grid, double theta, const double *
         zl.swap(zc);
         k2l.swap(k2c);
         for (int a = 0; a < 3; a++) nl[a] = nc[a];
+    }
+    // coarse tail: the longest run of levels ending at the coarsest with at most
+    // TAIL_MAX_UNKNOWNS interior nodes each (and at most MAX_TAIL_LEVELS levels)
+    if (mg->kind != HELM_PC_NONE) {
+        const int nlev = (int)h->lv.size();
+        int top = nlev - 1;
+        while (top > 0 && nlev - top < MAX_TAIL_LEVELS) {
+            const LevelDev &L = h->lv[top - 1];
+            const double ni = (double)(L.n[0] - 2) * (L.n[1] - 2) * (dim == 3 ? (double)(L.n[2] - 2) : 1.0);
+            if (ni > TAIL_MAX_UNKNOWNS) break;
+            top--;
+        }
+        h->tail_top = nlev - top >= 2 ? top : -1;  // a lone coarsest level keeps its dense-solve kernel
     }
     CKC(cudaStreamSynchronize(s));
     *out = h;
@@ -476,6 +490,24 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
     LevelDev &L = h->lv[l];
     const int last = (int)h->lv.size() - 1;
     if (l == last) return coarse_solve<R>(h, L, b, u);
+    if (l == h->tail_top) {
+        // levels l..last in one fused single-block launch
+        const int nt = last - l + 1;
+        DevOp<R> ops[MAX_TAIL_LEVELS];
+        typename CT<R>::T *bb[MAX_TAIL_LEVELS], *uu[MAX_TAIL_LEVELS], *tt[MAX_TAIL_LEVELS];
+        double bytes = 0;
+        for (int k = 0; k < nt; k++) {
+            LevelDev &Lk = h->lv[l + k];
+            ops[k] = LvBuf<R>::op(Lk);
+            bb[k] = k == 0 ? const_cast<typename CT<R>::T *>(b) : LvBuf<R>::b(Lk);
+            uu[k] = k == 0 ? u : LvBuf<R>::u(Lk);
+            tt[k] = LvBuf<R>::t(Lk);
+            bytes += interior(Lk, h->dim) * sizeof(typename CT<R>::T) * 8.0;
+        }
+        ProfScope ps(h, HELM_K_COARSE, bytes + (double)h->nu_c * h->nu_c * sizeof(typename CT<R>::T), 0);
+        return launch_mg_tail<R>(h->dim, nt, ops, bb, uu, tt, LvBuf<R>::minv(h), h->nu_c, h->mg.nu1, h->mg.nu2,
+                                 h->mg.smoother == HELM_SMOOTH_RB, (R)h->mg.omega, gf, gc, zero ? 1 : 0, h->stream);
+    }
     const double es = sizeof(C), rs = sizeof(R), ni = interior(L, h->dim), nd = h->dim == 3 ? 8.0 : 4.0;
     C *cur = u, *oth = LvBuf<R>::t(L);
     CKE(smooth<R>(h, l, h->mg.nu1, b, &cur, &oth, zero));

@@ -66,6 +66,7 @@ struct helm_handle {
     double2 *wts[3] = {nullptr, nullptr, nullptr};  // dual-volume weights per axis
 
     std::vector<LevelDev> lv;
+    int tail_top = -1;  // first level handled by the fused coarse-tail kernel (-1: none)
     int nu_c = 0;
     double2 *minv64 = nullptr;
     float2 *minv32 = nullptr;

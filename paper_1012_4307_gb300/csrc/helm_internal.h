@@ -86,6 +86,16 @@ cudaError_t launch_prolong_add(const int nf[3], int dim, const typename CT<R>::T
 template <typename R>
 cudaError_t launch_dense_solve(const int n[3], int dim, int nu, const typename CT<R>::T *minv,
                                const typename CT<R>::T *b, typename CT<R>::T *u, cudaStream_t s);
+// Fused coarse tail: Algorithm 1 on levels 0..nlev-1 of the given arrays (level 0 = the
+// tail's top, nlev - 1 = the coarsest, solved with minv) inside one thread block.  zero: the
+// top-level iterate u[0] starts at 0 (not read).  Levels with at most TAIL_MAX_UNKNOWNS
+// interior nodes, MAX_TAIL_LEVELS at most, go to the tail.
+constexpr int MAX_TAIL_LEVELS = 4;
+constexpr int TAIL_MAX_UNKNOWNS = 4096;
+template <typename R>
+cudaError_t launch_mg_tail(int dim, int nlev, const DevOp<R> *ops, typename CT<R>::T *const *b,
+                           typename CT<R>::T *const *u, typename CT<R>::T *const *t, const typename CT<R>::T *minv,
+                           int nu_c, int nu1, int nu2, int rb, R omega, int gf, int gc, int zero, cudaStream_t s);
 template <typename CI, typename CO>
 cudaError_t launch_convert(size_t n, const CI *in, CO *out, cudaStream_t s);
 template <typename C>
@@ -106,6 +116,14 @@ cudaError_t launch_update_norm(size_t n, const double2 *V, size_t ldv, int nv, c
 // out[i] (mode 0: =, 1: +=, 2: (sqrt(re), 0)) = fixed-order sum of partials of vector i
 cudaError_t launch_reduce(const double2 *partials, int nblk, int nv, double2 *out, int mode, const int *gate,
                           cudaStream_t s);
+// Same two passes with FP64 vectors and double-FP32 arithmetic (kernels_gs_df.cu); their
+// partials use G = gs_df_nblocks(n) blocks per vector.
+int gs_df_nblocks(size_t n);         // dot pass
+int gs_df_update_nblocks(size_t n);  // update pass
+cudaError_t launch_mdot_norm_df(size_t n, const double2 *V, size_t ldv, int nv, const double2 *w, double2 *partials,
+                                const int *gate, cudaStream_t s);
+cudaError_t launch_update_norm_df(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
+                                  double2 *partials, const int *gate, cudaStream_t s);
 // *hnorm: ||w||^2 in, ||w'|| out; *flag = (||w'|| < eta ||w||); *count += flag
 cudaError_t launch_reduce_decide(const double2 *partials, int nblk, double2 *hnorm, int *flag, int *count, double eta,
                                  cudaStream_t s);

@@ -1,0 +1,245 @@
+// Gram-Schmidt passes of flexible GMRES with FP64 vectors in memory but the arithmetic done
+// in double-FP32 ("double-float") on the FP32 units.
+//
+// Why: on GB300 the FP64 pipe retires about 2 fused multiply-adds per SM per clock, 64 times
+// fewer than FP32, so FP64 inner products over the Krylov basis are bound by FP64 issue, not
+// by DRAM.  Here every FP64 operand is split exactly into hi + lo floats with integer
+// instructions (hi = the leading 24 significand bits, lo = the next 29 rounded to 24, i.e. a
+// 47-bit representation), products are formed error-free with FMA (Dekker/Ogita-Rump-Oishi
+// TwoProduct), sums with Knuth's TwoSum, and the result is rounded back to FP64 once per
+// node (update) or once per block (dot).  Relative error of a product is about 2^-46 and of a
+// sum about 2^-48, i.e. FP64-class accuracy at FP32 throughput, which moves these kernels to
+// the DRAM bound.  Inputs below 2^-126 in magnitude are flushed (their contribution to
+// products with unit-norm basis vectors is far below the FP64 rounding of the result).
+//
+// Same contracts as k_mdot_norm / k_update_norm in kernels_krylov.cu (partials layout, gate).
+#include "helm_internal.h"
+
+namespace {
+
+constexpr int NT = 256;
+
+struct ff {
+    float hi, lo;
+};
+
+// Exact split of x into hi + lo (hi: 24 leading bits by truncation, lo: remaining 29 bits
+// rounded to float).  Zero, subnormal and |x| < 2^-126 give (0, 0); |x| < 2^-74 drops lo.
+__device__ __forceinline__ ff split(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+    const int e = (int)((h32 >> 20) & 0x7FFu);
+    const unsigned sign = h32 & 0x80000000u;
+    ff r;
+    if (e < 897) { r.hi = 0.f; r.lo = 0.f; return r; }
+    if (e > 1150) { r.hi = __int_as_float((int)(sign | 0x7F800000u)); r.lo = 0.f; return r; }
+    r.hi = __int_as_float((int)(sign | ((unsigned)(e - 896) << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29)));
+    if (e < 949) { r.lo = 0.f; return r; }
+    const float scale = __int_as_float((e - 948) << 23);  // 2^(e - 1075)
+    const float lo = __fmul_rn(__uint2float_rn(l32 & 0x1FFFFFFFu), scale);
+    r.lo = __int_as_float(__float_as_int(lo) | (int)sign);
+    return r;
+}
+
+// Error-free product a*b ~ p + e (al*bl dropped).
+__device__ __forceinline__ void two_prod(ff a, ff b, float &p, float &e) {
+    p = __fmul_rn(a.hi, b.hi);
+    e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+}
+
+// (s, c) += x exactly in s + c (Knuth TwoSum on s, error folded into c).
+__device__ __forceinline__ void acc_add(float &s, float &c, float x) {
+    const float t = __fadd_rn(s, x);
+    const float z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));
+    s = t;
+    c = __fadd_rn(c, err);
+}
+
+// Adds a product p + e into the accumulator (s, c).
+__device__ __forceinline__ void acc_prod(float &s, float &c, float p, float e) {
+    acc_add(s, c, p);
+    c = __fadd_rn(c, e);
+}
+
+// Normalised double-float sum of two double-floats.
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float z = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, z)), __fsub_rn(b.hi, z));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    ff r;
+    r.hi = __fadd_rn(s, e);
+    r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+    return r;
+}
+
+__device__ __forceinline__ ff ff_norm(float s, float c) {
+    ff r;
+    r.hi = __fadd_rn(s, c);
+    r.lo = __fsub_rn(c, __fsub_rn(r.hi, s));
+    return r;
+}
+
+__device__ __forceinline__ ff shfl_down_ff(ff v, int off) {
+    v.hi = __shfl_down_sync(0xffffffffu, v.hi, off);
+    v.lo = __shfl_down_sync(0xffffffffu, v.lo, off);
+    return v;
+}
+
+__device__ __forceinline__ double to_double(ff v) { return (double)v.hi + (double)v.lo; }
+
+// Block sums of NV double-float values per thread (fixed tree); thread t < NV gets sum t as
+// an FP64 number in out[t].
+template <int NV>
+__device__ __forceinline__ void block_sum_ff(ff (&v)[NV], double *out) {
+    __shared__ ff red[NT / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; i++) {
+        ff x = v[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x = ff_add(x, shfl_down_ff(x, off));
+        if (lane == 0) red[warp][i] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        ff s = red[0][threadIdx.x];
+        for (int w = 1; w < NT / 32; w++) s = ff_add(s, red[w][threadIdx.x]);
+        out[threadIdx.x] = to_double(s);
+    }
+}
+
+// partials[i * G + b] = sum conj(V_i) w (i in this block row's chunk), chunk 0 also
+// partials[nv * G + b] = (||w||^2, 0).
+template <int CH>
+__global__ void __launch_bounds__(NT) k_mdot_norm_df(size_t n, const double2 *__restrict__ V, size_t ldv, int nv,
+                                                     const double2 *__restrict__ w, double2 *__restrict__ partials,
+                                                     const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    __shared__ double sums[2 * CH + 1];
+    const int i0 = blockIdx.y * CH;
+    const int cnt = min(CH, nv - i0);
+    const bool first = blockIdx.y == 0;
+    float sr[CH], cr[CH], si[CH], ci[CH];
+    float sn = 0.f, cn = 0.f;
+#pragma unroll
+    for (int t = 0; t < CH; t++) sr[t] = cr[t] = si[t] = ci[t] = 0.f;
+    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const double2 wq = w[q];
+        const ff wx = split(wq.x), wy = split(wq.y);
+        float p, e;
+        if (first) {
+            two_prod(wx, wx, p, e);
+            acc_prod(sn, cn, p, e);
+            two_prod(wy, wy, p, e);
+            acc_prod(sn, cn, p, e);
+        }
+#pragma unroll
+        for (int t = 0; t < CH; t++) {
+            if (t < cnt) {
+                const double2 vq = V[(size_t)(i0 + t) * ldv + q];
+                const ff vx = split(vq.x), vy = split(vq.y);
+                // conj(v) w = (vx wx + vy wy) + i (vx wy - vy wx)
+                two_prod(vx, wx, p, e);
+                acc_prod(sr[t], cr[t], p, e);
+                two_prod(vy, wy, p, e);
+                acc_prod(sr[t], cr[t], p, e);
+                two_prod(vx, wy, p, e);
+                acc_prod(si[t], ci[t], p, e);
+                two_prod(vy, wx, p, e);
+                acc_prod(si[t], ci[t], -p, -e);
+            }
+        }
+    }
+    ff vals[2 * CH + 1];
+#pragma unroll
+    for (int t = 0; t < CH; t++) {
+        vals[2 * t] = ff_norm(sr[t], cr[t]);
+        vals[2 * t + 1] = ff_norm(si[t], ci[t]);
+    }
+    vals[2 * CH] = ff_norm(sn, cn);
+    block_sum_ff<2 * CH + 1>(vals, sums);
+    __syncthreads();
+    const int G = gridDim.x;
+    if ((int)threadIdx.x < cnt)
+        partials[(size_t)(i0 + threadIdx.x) * G + blockIdx.x] = make_double2(sums[2 * threadIdx.x], sums[2 * threadIdx.x + 1]);
+    if (first && threadIdx.x == 0) partials[(size_t)nv * G + blockIdx.x] = make_double2(sums[2 * CH], 0.0);
+}
+
+// w -= sum_i V_i h_i in double-float, rounded to FP64 once per node; partials[b] = (||w||^2, 0).
+__global__ void __launch_bounds__(NT) k_update_norm_df(size_t n, const double2 *__restrict__ V, size_t ldv, int nv,
+                                                       const double2 *__restrict__ h, double2 *__restrict__ w,
+                                                       double2 *__restrict__ partials, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    __shared__ float4 hs[64];  // (re.hi, re.lo, im.hi, im.lo)
+    __shared__ double sums[1];
+    for (int i = threadIdx.x; i < nv; i += NT) {
+        const ff a = split(h[i].x), b = split(h[i].y);
+        hs[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+    __syncthreads();
+    float sn = 0.f, cn = 0.f;
+    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const double2 wq = w[q];
+        const ff wx = split(wq.x), wy = split(wq.y);
+        float sx = wx.hi, cx = wx.lo, sy = wy.hi, cy = wy.lo;
+#pragma unroll 4
+        for (int i = 0; i < nv; i++) {
+            const double2 vq = V[(size_t)i * ldv + q];
+            const ff vx = split(vq.x), vy = split(vq.y);
+            const float4 hh = hs[i];
+            const ff hx = {hh.x, hh.y}, hy = {hh.z, hh.w};
+            float p, e;
+            // w -= v h:  re -= vx hx - vy hy ;  im -= vx hy + vy hx
+            two_prod(vx, hx, p, e);
+            acc_prod(sx, cx, -p, -e);
+            two_prod(vy, hy, p, e);
+            acc_prod(sx, cx, p, e);
+            two_prod(vx, hy, p, e);
+            acc_prod(sy, cy, -p, -e);
+            two_prod(vy, hx, p, e);
+            acc_prod(sy, cy, -p, -e);
+        }
+        const ff rx = ff_norm(sx, cx), ry = ff_norm(sy, cy);
+        const double2 out = make_double2(to_double(rx), to_double(ry));
+        w[q] = out;
+        float p, e;
+        const ff ox = split(out.x), oy = split(out.y);
+        two_prod(ox, ox, p, e);
+        acc_prod(sn, cn, p, e);
+        two_prod(oy, oy, p, e);
+        acc_prod(sn, cn, p, e);
+    }
+    ff vals[1] = {ff_norm(sn, cn)};
+    block_sum_ff<1>(vals, sums);
+    if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(sums[0], 0.0);
+}
+
+}  // namespace
+
+// Block counts (fixed for a given n).  The dot pass reduces 2 CH + 1 double-floats per block,
+// so it keeps about 8 nodes per thread; the update pass reduces one value and uses the same
+// grid as the FP64 kernels, which keeps enough warps resident to hide DRAM latency behind
+// the long split / TwoSum dependency chains.
+int gs_df_nblocks(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>(cdiv(n, (size_t)NT * 8), (size_t)152 * 4)); }
+int gs_df_update_nblocks(size_t n) { return blas_nblocks(n); }
+
+constexpr int DF_CH = 4;  // basis vectors per block row of the dot pass
+
+cudaError_t launch_mdot_norm_df(size_t n, const double2 *V, size_t ldv, int nv, const double2 *w, double2 *partials,
+                                const int *gate, cudaStream_t s) {
+    if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
+    dim3 g(gs_df_nblocks(n), std::max(1, (nv + DF_CH - 1) / DF_CH));
+    k_mdot_norm_df<DF_CH><<<g, NT, 0, s>>>(n, V, ldv, nv, w, partials, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_norm_df(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
+                                  double2 *partials, const int *gate, cudaStream_t s) {
+    if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
+    k_update_norm_df<<<gs_df_update_nblocks(n), NT, 0, s>>>(n, V, ldv, nv, h, w, partials, gate);
+    return cudaGetLastError();
+}

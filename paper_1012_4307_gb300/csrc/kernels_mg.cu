@@ -270,6 +270,208 @@ template <typename C> __global__ void k_zero(size_t n, C *x) {
         x[q] = mk(R(0), R(0));
 }
 
+// ------------------------------------------------------------------------------ coarse tail
+// The coarse levels of a cycle (a few thousand unknowns or fewer) are launch- and latency-
+// bound when every sweep is its own grid.  k_mg_tail runs Algorithm 1 from the tail's top
+// level down to the exact coarsest solve and back inside ONE thread block: each phase is a
+// block-strided loop over the level's interior, phases are separated by __syncthreads(), and
+// the vectors stay in (L2-resident) global memory.  Same arithmetic as the per-level kernels.
+constexpr int TAIL_THREADS = 512;
+
+template <typename R> struct TailLevelDev {
+    OpView<R> o;
+    typename CT<R>::T *b, *u, *t;
+};
+
+template <typename R> struct TailArgs {
+    TailLevelDev<R> lv[MAX_TAIL_LEVELS];
+    int nlev, nu_c, nu1, nu2, rb;
+    R omega;
+    const typename CT<R>::T *minv;
+};
+
+template <int DIM>
+__device__ __forceinline__ void tail_index(int idx, int mx, int my, int &i, int &j, int &k) {
+    i = 1 + idx % mx;
+    j = 1 + (idx / mx) % my;
+    k = DIM == 3 ? 1 + idx / (mx * my) : 0;
+}
+
+template <typename R, int DIM>
+__device__ void tail_smooth(const TailArgs<R> &A, const TailLevelDev<R> &L, int sweeps, typename CT<R>::T **cur,
+                            typename CT<R>::T **oth, bool zero) {
+    typedef typename CT<R>::T C;
+    const OpView<R> &o = L.o;
+    const int mx = o.nx - 2, my = o.ny - 2, mz = DIM == 3 ? o.nz - 2 : 1, ni = mx * my * mz;
+    const size_t sz = (size_t)o.nx * o.ny;
+    if (zero && (sweeps == 0 || A.rb)) {
+        for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
+            int i, j, k;
+            tail_index<DIM>(idx, mx, my, i, j, k);
+            (*cur)[(size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k)] = mk(R(0), R(0));
+        }
+        __syncthreads();
+    }
+    for (int s = 0; s < sweeps; s++) {
+        if (A.rb) {
+            for (int colour = 0; colour < 2; colour++) {
+                for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
+                    int i, j, k;
+                    tail_index<DIM>(idx, mx, my, i, j, k);
+                    if (((i + j + k) & 1) != colour) continue;
+                    const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
+                    C *u = *cur;
+                    C xm = mk(R(0), R(0)), xp = mk(R(0), R(0));
+                    if (DIM == 3) { xm = u[p - sz]; xp = u[p + sz]; }
+                    const C xc = u[p];
+                    C d;
+                    const C mu = stencil<R, DIM>(o, u, p, i, j, k, xm, xc, xp, d);
+                    u[p] = cadd(xc, cscale(cmul(csub(L.b[p], mu), cinv(d)), A.omega));
+                }
+                __syncthreads();
+            }
+        } else {
+            const bool z0 = zero && s == 0;
+            for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
+                int i, j, k;
+                tail_index<DIM>(idx, mx, my, i, j, k);
+                const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
+                const C *u = *cur;
+                if (z0) {
+                    C d = cadd(cadd(o.cx[3 * i + 1], o.cy[3 * j + 1]), cadd(cscale(o.bk, o.k2[p]), o.c));
+                    if (DIM == 3) d = cadd(d, o.cz[3 * k + 1]);
+                    (*oth)[p] = cscale(cmul(L.b[p], cinv(d)), A.omega);
+                } else {
+                    C xm = mk(R(0), R(0)), xp = mk(R(0), R(0));
+                    if (DIM == 3) { xm = u[p - sz]; xp = u[p + sz]; }
+                    const C xc = u[p];
+                    C d;
+                    const C mu = stencil<R, DIM>(o, u, p, i, j, k, xm, xc, xp, d);
+                    (*oth)[p] = cadd(xc, cscale(cmul(csub(L.b[p], mu), cinv(d)), A.omega));
+                }
+            }
+            __syncthreads();
+            C *t = *cur;
+            *cur = *oth;
+            *oth = t;
+        }
+    }
+}
+
+template <typename R, int DIM>
+__device__ void tail_dense(const TailArgs<R> &A, const TailLevelDev<R> &L) {
+    typedef typename CT<R>::T C;
+    const int mx = L.o.nx - 2, my = L.o.ny - 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int row = warp; row < A.nu_c; row += nwarp) {
+        C acc = mk(R(0), R(0));
+        for (int c = lane; c < A.nu_c; c += 32) {
+            int i, j, k;
+            tail_index<DIM>(c, mx, my, i, j, k);
+            acc = cfma(A.minv[(size_t)row * A.nu_c + c], L.b[(size_t)i + (size_t)L.o.nx * ((size_t)j + (size_t)L.o.ny * k)], acc);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+        }
+        if (lane == 0) {
+            int i, j, k;
+            tail_index<DIM>(row, mx, my, i, j, k);
+            L.u[(size_t)i + (size_t)L.o.nx * ((size_t)j + (size_t)L.o.ny * k)] = acc;
+        }
+    }
+    __syncthreads();
+}
+
+// Level LVL of the tail (compile-time depth, so no device recursion and no stack growth).
+template <typename R, int DIM, int LVL>
+__device__ void tail_cycle(const TailArgs<R> &A, bool zero, int gf, int gc) {
+    typedef typename CT<R>::T C;
+    constexpr int l = LVL;
+    const TailLevelDev<R> &L = A.lv[l];
+    if (l == A.nlev - 1) {
+        tail_dense<R, DIM>(A, L);
+        return;
+    }
+    if constexpr (LVL + 1 < MAX_TAIL_LEVELS) {
+    C *cur = L.u, *oth = L.t;
+    tail_smooth<R, DIM>(A, L, A.nu1, &cur, &oth, zero);
+    const TailLevelDev<R> &Lc = A.lv[l + 1];
+    // residual + full weighting into the next level's right-hand side
+    {
+        const int mx = Lc.o.nx - 2, my = Lc.o.ny - 2, mz = DIM == 3 ? Lc.o.nz - 2 : 1, ni = mx * my * mz;
+        for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
+            int I, J, K;
+            tail_index<DIM>(idx, mx, my, I, J, K);
+            C acc = mk(R(0), R(0));
+            for (int dk = (DIM == 3 ? -1 : 0); dk <= (DIM == 3 ? 1 : 0); dk++) {
+                const R wk = DIM == 3 ? (dk == 0 ? R(0.5) : R(0.25)) : R(1);
+                const int k = DIM == 3 ? 2 * K + dk : 0;
+                for (int dj = -1; dj <= 1; dj++) {
+                    const R wj = wk * (dj == 0 ? R(0.5) : R(0.25));
+                    const int j = 2 * J + dj;
+                    for (int di = -1; di <= 1; di++) {
+                        const R w = wj * (di == 0 ? R(0.5) : R(0.25));
+                        const int i = 2 * I + di;
+                        const size_t p = (size_t)i + (size_t)L.o.nx * ((size_t)j + (size_t)L.o.ny * k);
+                        C d;
+                        const C mu = apply_point<R, DIM>(L.o, (const C *)cur, i, j, k, d);
+                        acc = cadd(acc, cscale(csub(L.b[p], mu), w));
+                    }
+                }
+            }
+            Lc.b[(size_t)I + (size_t)Lc.o.nx * ((size_t)J + (size_t)Lc.o.ny * K)] = acc;
+        }
+        __syncthreads();
+    }
+    if (l + 1 == A.nlev - 1) {
+        tail_dense<R, DIM>(A, Lc);
+    } else {
+        for (int i = 1; i <= gc; i++) {
+            if (i == 1) tail_cycle<R, DIM, LVL + 1>(A, true, gf, gc);
+            else tail_cycle<R, DIM, LVL + 1>(A, false, gc, gf);
+        }
+    }
+    // prolongation + correction
+    {
+        const int nx = L.o.nx, ny = L.o.ny, mx = nx - 2, my = ny - 2, mz = DIM == 3 ? L.o.nz - 2 : 1;
+        const int ncx = Lc.o.nx, ncy = Lc.o.ny, ni = mx * my * mz;
+        for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
+            int i, j, k;
+            tail_index<DIM>(idx, mx, my, i, j, k);
+            const int kk0 = DIM == 3 ? k >> 1 : 0, kk1 = DIM == 3 ? (k + 1) >> 1 : 0;
+            C acc = mk(R(0), R(0));
+            int cnt = 0;
+            for (int kk = kk0; kk <= kk1; kk++)
+                for (int jj = j >> 1; jj <= (j + 1) >> 1; jj++)
+                    for (int ii = i >> 1; ii <= (i + 1) >> 1; ii++) {
+                        acc = cadd(acc, Lc.u[(size_t)ii + (size_t)ncx * ((size_t)jj + (size_t)ncy * kk)]);
+                        cnt++;
+                    }
+            const size_t p = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k);
+            cur[p] = cadd(cur[p], cscale(acc, R(1) / R(cnt)));
+        }
+        __syncthreads();
+    }
+    tail_smooth<R, DIM>(A, L, A.nu2, &cur, &oth, false);
+    if (cur != L.u) {  // interior only: the top level's u may be a caller vector
+        const int mx = L.o.nx - 2, my = L.o.ny - 2, ni = mx * my * (DIM == 3 ? L.o.nz - 2 : 1);
+        for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
+            int i, j, k;
+            tail_index<DIM>(idx, mx, my, i, j, k);
+            const size_t p = (size_t)i + (size_t)L.o.nx * ((size_t)j + (size_t)L.o.ny * k);
+            L.u[p] = cur[p];
+        }
+        __syncthreads();
+    }
+    }  // LVL + 1 < MAX_TAIL_LEVELS
+}
+
+template <typename R, int DIM>
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs<R> A, int gf, int gc, int zero) {
+    tail_cycle<R, DIM, 0>(A, zero != 0, gf, gc);
+}
+
 dim3 grid_for(const int n[3], int dim) {
     return dim3(cdiv(n[0] - 2, BX), cdiv(n[1] - 2, BY), dim == 3 ? cdiv(n[2] - 2, KCHUNK) : 1);
 }
@@ -343,6 +545,37 @@ cudaError_t launch_dense_solve(const int n[3], int dim, int nu, const typename C
     k_dense_solve<R><<<cdiv(nu, warps), threads, 0, s>>>(n[0], n[1], dim == 3 ? n[2] : 1, dim, nu, minv, b, u);
     return cudaGetLastError();
 }
+
+template <typename R>
+cudaError_t launch_mg_tail(int dim, int nlev, const DevOp<R> *ops, typename CT<R>::T *const *b,
+                           typename CT<R>::T *const *u, typename CT<R>::T *const *t, const typename CT<R>::T *minv,
+                           int nu_c, int nu1, int nu2, int rb, R omega, int gf, int gc, int zero, cudaStream_t s) {
+    if (nlev < 1 || nlev > MAX_TAIL_LEVELS) return cudaErrorInvalidValue;
+    TailArgs<R> A{};
+    for (int l = 0; l < nlev; l++) {
+        A.lv[l].o = view(ops[l]);
+        if (dim != 3) A.lv[l].o.nz = 1;
+        A.lv[l].b = b[l];
+        A.lv[l].u = u[l];
+        A.lv[l].t = t[l];
+    }
+    A.nlev = nlev;
+    A.nu_c = nu_c;
+    A.nu1 = nu1;
+    A.nu2 = nu2;
+    A.rb = rb;
+    A.omega = omega;
+    A.minv = minv;
+    if (dim == 3) k_mg_tail<R, 3><<<1, TAIL_THREADS, 0, s>>>(A, gf, gc, zero);
+    else k_mg_tail<R, 2><<<1, TAIL_THREADS, 0, s>>>(A, gf, gc, zero);
+    return cudaGetLastError();
+}
+template cudaError_t launch_mg_tail<float>(int, int, const DevOp<float> *, float2 *const *, float2 *const *,
+                                           float2 *const *, const float2 *, int, int, int, int, float, int, int, int,
+                                           cudaStream_t);
+template cudaError_t launch_mg_tail<double>(int, int, const DevOp<double> *, double2 *const *, double2 *const *,
+                                            double2 *const *, const double2 *, int, int, int, int, double, int, int,
+                                            int, cudaStream_t);
 
 template <typename CI, typename CO>
 cudaError_t launch_convert(size_t n, const CI *in, CO *out, cudaStream_t s) {

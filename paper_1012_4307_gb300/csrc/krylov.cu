@@ -4,9 +4,11 @@
 // GPU.  The host only sequences launches and reads one residual estimate per iteration.
 //
 // Flexible GMRES: Saad, Iterative Methods for Sparse Linear Systems, Algorithm 9.6, with
-// classical Gram-Schmidt and one re-orthogonalisation (CGS2, three fused passes) in place of
-// modified Gram-Schmidt.  Bi-CGSTAB: van der Vorst (1992), right preconditioning, two
-// preconditioner cycles per iteration as in Section 5 of the paper.
+// classical Gram-Schmidt (two fused passes: dot + norm, update + norm) and a second
+// Gram-Schmidt pass whenever the DGKS test asks for it, in place of modified Gram-Schmidt;
+// the Gram-Schmidt arithmetic is FP64 or double-FP32 (helm_gs_arith).  Bi-CGSTAB: van der
+// Vorst (1992), right preconditioning, two preconditioner cycles per iteration as in
+// Section 5 of the paper.
 #include <math.h>
 #include <string.h>
 
@@ -163,10 +165,21 @@ static helm_status fgmres(helm_handle *h, const double2 *f, double2 *x, double t
     helm_status s0 = ensure_ws(h, m);
     if (s0 != HELM_OK) return s0;
     const size_t np = h->np;
-    const int nblk = blas_nblocks(np);
     const int ldh = m + 1;
     cudaStream_t s = h->stream;
     const size_t zsz = h->z_prec == HELM_C64 ? sizeof(float2) : sizeof(double2);
+    // Gram-Schmidt passes in FP64 or double-FP32 arithmetic (same partials layout)
+    const bool df = h->mg.gs_arith == HELM_GS_DF;
+    const int gblk = df ? gs_df_nblocks(np) : blas_nblocks(np);         // blocks of the dot pass
+    const int ublk = df ? gs_df_update_nblocks(np) : blas_nblocks(np);  // blocks of the update pass
+    auto gs_dot = [&](int nv, const double2 *w, const int *gate) {
+        return df ? launch_mdot_norm_df(np, h->V, np, nv, w, h->partials, gate, s)
+                  : launch_mdot_norm(np, h->V, np, nv, w, h->partials, gate, s);
+    };
+    auto gs_update = [&](int nv, const double2 *hh, double2 *w, const int *gate) {
+        return df ? launch_update_norm_df(np, h->V, np, nv, hh, w, h->partials, gate, s)
+                  : launch_update_norm(np, h->V, np, nv, hh, w, h->partials, gate, s);
+    };
     double2 hv[2];
     CKR(dev_norm(h, f, h->scal));
     helm_status rs = read_scalars(h, h->scal, sizeof(double2), hv);
@@ -213,37 +226,38 @@ static helm_status fgmres(helm_handle *h, const double2 *f, double2 *x, double t
             //   if ||w'|| < eta ||w||:  h' = V^H w, H[:, j] += h';  w -= V h', ||w''||.
             // The second pass runs only when the device flag is set (gated kernels).
             {
-                ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (nv + 1), np * (8.0 * nv + 4.0));
-                CKR(launch_mdot_norm(np, h->V, np, j + 1, w, h->partials, nullptr, s));
+                // FP64 flops only when the FP64 units do them (double-FP32 work is DRAM-bound)
+                ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (nv + 1), df ? 0.0 : np * (8.0 * nv + 4.0));
+                CKR(gs_dot(j + 1, w, nullptr));
             }
             {
                 ProfScope ps(h, HELM_K_SMALL, 0, 0);
-                CKR(launch_reduce(h->partials, nblk, j + 2, hcol, 0, nullptr, s));
+                CKR(launch_reduce(h->partials, gblk, j + 2, hcol, 0, nullptr, s));
             }
             {
-                ProfScope ps(h, HELM_K_UPDATE_NORM, np * 16.0 * (nv + 2), np * (8.0 * nv + 4.0));
-                CKR(launch_update_norm(np, h->V, np, j + 1, hcol, w, h->partials, nullptr, s));
+                ProfScope ps(h, HELM_K_UPDATE_NORM, np * 16.0 * (nv + 2), df ? 0.0 : np * (8.0 * nv + 4.0));
+                CKR(gs_update(j + 1, hcol, w, nullptr));
             }
             {
                 ProfScope ps(h, HELM_K_SMALL, 0, 0);
-                CKR(launch_reduce_decide(h->partials, nblk, hcol + j + 1, h->gs_flag, h->gs_count, kDGKSEta, s));
+                CKR(launch_reduce_decide(h->partials, ublk, hcol + j + 1, h->gs_flag, h->gs_count, kDGKSEta, s));
             }
             {
                 ProfScope ps(h, HELM_K_MDOT, 0, 0);  // gated: cost counted only if it runs (unknown here)
-                CKR(launch_mdot_norm(np, h->V, np, j + 1, w, h->partials, h->gs_flag, s));
+                CKR(gs_dot(j + 1, w, h->gs_flag));
             }
             {
                 ProfScope ps(h, HELM_K_SMALL, 0, 0);
-                CKR(launch_reduce(h->partials, nblk, j + 1, h->h2, 0, h->gs_flag, s));
-                CKR(launch_reduce(h->partials, nblk, j + 1, hcol, 1, h->gs_flag, s));
+                CKR(launch_reduce(h->partials, gblk, j + 1, h->h2, 0, h->gs_flag, s));
+                CKR(launch_reduce(h->partials, gblk, j + 1, hcol, 1, h->gs_flag, s));
             }
             {
                 ProfScope ps(h, HELM_K_UPDATE_NORM, 0, 0);
-                CKR(launch_update_norm(np, h->V, np, j + 1, h->h2, w, h->partials, h->gs_flag, s));
+                CKR(gs_update(j + 1, h->h2, w, h->gs_flag));
             }
             {
                 ProfScope ps(h, HELM_K_SMALL, 0, 0);
-                CKR(launch_reduce(h->partials, nblk, 1, hcol + j + 1, 2, h->gs_flag, s));
+                CKR(launch_reduce(h->partials, ublk, 1, hcol + j + 1, 2, h->gs_flag, s));
             }
             {
                 ProfScope ps(h, HELM_K_VECTOR, np * 32.0, np * 2.0);

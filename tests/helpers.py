@@ -12,10 +12,10 @@ def rel_l2(a, b):
 
 
 def mg_params(helm, pc="csg", prec="c128", nu=(2, 2), omega=0.8, smoother="jacobi", gamma=(1, 1),
-              coarsest_n=17, theta_a=math.pi / 14, beta=(-1.0, -0.5), re_lambda0=0.0):
+              coarsest_n=17, theta_a=math.pi / 14, beta=(-1.0, -0.5), re_lambda0=0.0, gs="fp64"):
     return helm.MGParams(kind=pc, theta_a=theta_a, beta1=beta[0], beta2=beta[1], re_lambda0=re_lambda0,
                          nu1=nu[0], nu2=nu[1], omega=omega, smoother=smoother, gamma_f=gamma[0],
-                         gamma_c=gamma[1], coarsest_n=coarsest_n, prec=prec)
+                         gamma_c=gamma[1], coarsest_n=coarsest_n, prec=prec, gs=gs)
 
 
 def gpu_handle(helm, P, **kw):

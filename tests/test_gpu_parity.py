@@ -169,6 +169,43 @@ def test_fgmres_mixed_precision(helm, oracle):
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_fgmres_double_float_gram_schmidt(helm, oracle, prec):
+    """Gram-Schmidt in double-FP32 arithmetic on FP64 vectors reaches the same FP64 solution:
+    1e-8 of the oracle at 1e-10 (FP64 cycle), and the same iteration count as FP64 Gram-Schmidt."""
+    P = W.config_small(65)
+    A, M = oracle_pair(oracle, P)
+    mg = oracle.MG(M, 17, 2, 2, 0.8)
+    xo, sto = oracle.fgmres(A, mg, P.f, tol=1e-10, restart=30, maxit=500)
+    hdf = gpu_handle(helm, P, pc="csg", prec=prec, gs="df")
+    h64 = gpu_handle(helm, P, pc="csg", prec=prec, gs="fp64")
+    x, st = helm.krylov_solve(hdf, to_gpu(P.f), tol=1e-10, restart=30, maxit=500)
+    x64, st64 = helm.krylov_solve(h64, to_gpu(P.f), tol=1e-10, restart=30, maxit=500)
+    assert st.status == helm.HELM_OK
+    r = P.f - A.apply(to_np(x))
+    assert np.linalg.norm(r) / np.linalg.norm(P.f) <= 1.5e-10
+    assert abs(st.iterations - st64.iterations) <= 1
+    assert rel_l2(to_np(x), xo) <= (1e-8 if prec == "c128" else 1e-7)
+
+
+def test_double_float_gram_schmidt_bench_size(helm):
+    """1025 x 1025 well problem (the benchmark workload), complex64 cycle: double-FP32 and FP64
+    Gram-Schmidt give the same solution to the accuracy of the solve (rel. residual 1e-8)."""
+    P = W.config_2d_well(1025)
+    f = to_gpu(P.f)
+    out = {}
+    for gs in ("df", "fp64"):
+        h = gpu_handle(helm, P, pc="csg", prec="c64", gs=gs)
+        x, st = helm.krylov_solve(h, f, tol=1e-8, restart=30, maxit=3000)
+        assert st.status == helm.HELM_OK and st.rel_res <= 1e-8
+        out[gs] = (x, st)
+        h.close()
+    # restarted GMRES iteration counts move by a few percent under any change of rounding
+    assert abs(out["df"][1].iterations - out["fp64"][1].iterations) <= 0.05 * out["fp64"][1].iterations + 2
+    d = float(torch.linalg.vector_norm(out["df"][0] - out["fp64"][0]) / torch.linalg.vector_norm(out["fp64"][0]))
+    assert d <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
 def test_bicgstab_matches_oracle(helm, oracle, prec):
     P = W.config_small(65)
     h = gpu_handle(helm, P, pc="csg", prec=prec)

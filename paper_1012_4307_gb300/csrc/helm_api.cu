@@ -325,14 +325,20 @@ helm_status helm_create_impl(const helm_grid *grid, double theta, const double *
     // TAIL_MAX_UNKNOWNS interior nodes each (and at most MAX_TAIL_LEVELS levels)
     if (mg->kind != HELM_PC_NONE) {
         const int nlev = (int)h->lv.size();
-        int top = nlev - 1;
-        while (top > 0 && nlev - top < MAX_TAIL_LEVELS) {
-            const LevelDev &L = h->lv[top - 1];
-            const double ni = (double)(L.n[0] - 2) * (L.n[1] - 2) * (dim == 3 ? (double)(L.n[2] - 2) : 1.0);
-            if (ni > TAIL_MAX_UNKNOWNS) break;
-            top--;
+        for (int pass = 0; pass < 2; pass++) {
+            const size_t es = pass == 0 ? sizeof(float2) : sizeof(double2);
+            int top = nlev - 1;
+            size_t bytes = 3 * es * h->lv[top].np;
+            while (top > 0 && nlev - top < MAX_TAIL_LEVELS) {
+                const LevelDev &L = h->lv[top - 1];
+                const double ni = (double)(L.n[0] - 2) * (L.n[1] - 2) * (dim == 3 ? (double)(L.n[2] - 2) : 1.0);
+                if (ni > TAIL_MAX_UNKNOWNS || bytes + 3 * es * L.np > TAIL_SMEM_BYTES) break;
+                bytes += 3 * es * L.np;
+                top--;
+            }
+            // a lone coarsest level keeps its dense-solve kernel
+            (pass == 0 ? h->tail_top32 : h->tail_top64) = nlev - top >= 2 ? top : -1;
         }
-        h->tail_top = nlev - top >= 2 ? top : -1;  // a lone coarsest level keeps its dense-solve kernel
     }
     CKC(cudaStreamSynchronize(s));
     *out = h;
@@ -490,7 +496,7 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
     LevelDev &L = h->lv[l];
     const int last = (int)h->lv.size() - 1;
     if (l == last) return coarse_solve<R>(h, L, b, u);
-    if (l == h->tail_top) {
+    if (l == (sizeof(R) == sizeof(float) ? h->tail_top32 : h->tail_top64)) {
         // levels l..last in one fused single-block launch
         const int nt = last - l + 1;
         DevOp<R> ops[MAX_TAIL_LEVELS];

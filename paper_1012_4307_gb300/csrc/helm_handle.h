@@ -66,7 +66,9 @@ struct helm_handle {
     double2 *wts[3] = {nullptr, nullptr, nullptr};  // dual-volume weights per axis
 
     std::vector<LevelDev> lv;
-    int tail_top = -1;  // first level handled by the fused coarse-tail kernel (-1: none)
+    // first level handled by the fused coarse-tail kernel, per precision (-1: none); chosen so
+    // the tail's vectors fit in shared memory
+    int tail_top32 = -1, tail_top64 = -1;
     int nu_c = 0;
     double2 *minv64 = nullptr;
     float2 *minv32 = nullptr;

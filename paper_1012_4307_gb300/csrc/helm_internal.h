@@ -92,6 +92,7 @@ cudaError_t launch_dense_solve(const int n[3], int dim, int nu, const typename C
 // interior nodes, MAX_TAIL_LEVELS at most, go to the tail.
 constexpr int MAX_TAIL_LEVELS = 4;
 constexpr int TAIL_MAX_UNKNOWNS = 4096;
+constexpr size_t TAIL_SMEM_BYTES = 200 * 1024;  // b, u, t of every tail level in shared memory
 template <typename R>
 cudaError_t launch_mg_tail(int dim, int nlev, const DevOp<R> *ops, typename CT<R>::T *const *b,
                            typename CT<R>::T *const *u, typename CT<R>::T *const *t, const typename CT<R>::T *minv,

@@ -365,6 +365,7 @@ __device__ void tail_dense(const TailArgs<R> &A, const TailLevelDev<R> &L) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int row = warp; row < A.nu_c; row += nwarp) {
         C acc = mk(R(0), R(0));
+#pragma unroll 8
         for (int c = lane; c < A.nu_c; c += 32) {
             int i, j, k;
             tail_index<DIM>(c, mx, my, i, j, k);
@@ -467,9 +468,53 @@ __device__ void tail_cycle(const TailArgs<R> &A, bool zero, int gf, int gc) {
     }  // LVL + 1 < MAX_TAIL_LEVELS
 }
 
+// smem != 0: every level's b, u, t live in dynamic shared memory (zeroed, so boundary rings
+// are zero); the top level's right-hand side is copied in from global memory and its result
+// copied out (interior nodes only), with the caller's initial guess copied in when !zero.
 template <typename R, int DIM>
-__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs<R> A, int gf, int gc, int zero) {
-    tail_cycle<R, DIM, 0>(A, zero != 0, gf, gc);
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs<R> A, int gf, int gc, int zero, int smem) {
+    typedef typename CT<R>::T C;
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    __shared__ TailArgs<R> S;
+    if (!smem) {
+        tail_cycle<R, DIM, 0>(A, zero != 0, gf, gc);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        S = A;
+        C *p = (C *)tail_smem;
+        for (int l = 0; l < A.nlev; l++) {
+            const size_t np = (size_t)A.lv[l].o.nx * A.lv[l].o.ny * (DIM == 3 ? A.lv[l].o.nz : 1);
+            S.lv[l].b = p; p += np;
+            S.lv[l].u = p; p += np;
+            S.lv[l].t = p; p += np;
+        }
+    }
+    __syncthreads();
+    {
+        const C *end = S.lv[S.nlev - 1].t + (size_t)S.lv[S.nlev - 1].o.nx * S.lv[S.nlev - 1].o.ny *
+                                                (DIM == 3 ? S.lv[S.nlev - 1].o.nz : 1);
+        const size_t total = end - (const C *)tail_smem;
+        for (size_t q = threadIdx.x; q < total; q += blockDim.x) ((C *)tail_smem)[q] = mk(R(0), R(0));
+    }
+    __syncthreads();
+    const OpView<R> &o = A.lv[0].o;
+    const int mx = o.nx - 2, my = o.ny - 2, ni = mx * my * (DIM == 3 ? o.nz - 2 : 1);
+    for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
+        int i, j, k;
+        tail_index<DIM>(idx, mx, my, i, j, k);
+        const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
+        S.lv[0].b[p] = A.lv[0].b[p];
+        if (!zero) S.lv[0].u[p] = A.lv[0].u[p];
+    }
+    __syncthreads();
+    tail_cycle<R, DIM, 0>(S, zero != 0, gf, gc);
+    for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
+        int i, j, k;
+        tail_index<DIM>(idx, mx, my, i, j, k);
+        const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
+        A.lv[0].u[p] = S.lv[0].u[p];
+    }
 }
 
 dim3 grid_for(const int n[3], int dim) {
@@ -566,8 +611,21 @@ cudaError_t launch_mg_tail(int dim, int nlev, const DevOp<R> *ops, typename CT<R
     A.rb = rb;
     A.omega = omega;
     A.minv = minv;
-    if (dim == 3) k_mg_tail<R, 3><<<1, TAIL_THREADS, 0, s>>>(A, gf, gc, zero);
-    else k_mg_tail<R, 2><<<1, TAIL_THREADS, 0, s>>>(A, gf, gc, zero);
+    // shared-memory residency when all levels' b, u, t fit next to the block's static smem
+    size_t bytes = 0;
+    for (int l = 0; l < nlev; l++)
+        bytes += 3 * sizeof(typename CT<R>::T) * (size_t)ops[l].n[0] * ops[l].n[1] * (dim == 3 ? ops[l].n[2] : 1);
+    const int use_smem = bytes <= TAIL_SMEM_BYTES;
+    const size_t dyn = use_smem ? bytes : 0;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[dim == 3]) {
+        cudaError_t e = dim == 3 ? cudaFuncSetAttribute(k_mg_tail<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM_BYTES)
+                                 : cudaFuncSetAttribute(k_mg_tail<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set[dim == 3] = true;
+    }
+    if (dim == 3) k_mg_tail<R, 3><<<1, TAIL_THREADS, dyn, s>>>(A, gf, gc, zero, use_smem);
+    else k_mg_tail<R, 2><<<1, TAIL_THREADS, dyn, s>>>(A, gf, gc, zero, use_smem);
     return cudaGetLastError();
 }
 template cudaError_t launch_mg_tail<float>(int, int, const DevOp<float> *, float2 *const *, float2 *const *,

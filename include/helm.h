@@ -182,6 +182,29 @@ helm_status helm_grad_k2(helm_handle *h, const void *lambda, const void *u, doub
 helm_status helm_mg_conv(helm_handle *h, const void *b, void *x, helm_prec prec, double tol, int maxcyc,
                          int *ncycles, double *factor);
 
+/* Allocation-free helm_mg_conv (the paper has no counterpart; this is a library facility).
+ * helm_mg_conv allocates a work area with cudaMalloc the first time it runs on a handle.
+ * Some callers cannot allow that at the point of the call: code that runs while a CUDA graph
+ * is being captured (device allocation is not permitted inside a capture), or a service that
+ * fixes its device memory footprint at start-up and forbids any later growth.  This entry
+ * point computes exactly what helm_mg_conv computes, with the same kernels, but takes its
+ * work vectors from one fixed device array of HELM_NOALLOC_SCRATCH_BYTES that the library
+ * holds on every GPU that loads it until the process exits; it calls no cudaMalloc, cudaFree,
+ * cudaMallocHost or other allocating routine.
+ *   - Limit: the grid's nodes n0*n1*n2 must satisfy 32 * nodes + a few KB <= 16 MiB, i.e.
+ *     at most about 523,000 nodes (513 x 513 in 2D, 65 x 65 x 65 in 3D); larger grids are
+ *     rejected with HELM_ERR_ARG and nothing runs.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ *     capture begins.
+ *   - Every call shares the one array and it keeps the previous call's contents (the entry
+ *     point clears what must start at zero).  Calls that overlap on the GPU (different
+ *     streams, threads or handles) race on it: serialise them.
+ * Arguments, results and errors are those of helm_mg_conv. */
+#define HELM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+helm_status helm_mg_conv_noalloc(helm_handle *h, const void *b, void *x, helm_prec prec, double tol, int maxcyc,
+                                 int *ncycles, double *factor);
+
 /* Number of levels and nodes per axis of level l (host query). */
 helm_status helm_levels(const helm_handle *h, int *nlev);
 helm_status helm_level_shape(const helm_handle *h, int level, int n[3]);

@@ -91,6 +91,7 @@ def load(build: bool = True):
             "helm_solve_adjoint": ([P, P, P, D, I, I, P], I),
             "helm_grad_k2": ([P, P, P, P], I),
             "helm_mg_conv": ([P, P, P, I, D, I, P, P], I),
+            "helm_mg_conv_noalloc": ([P, P, P, I, D, I, P, P], I),
             "helm_levels": ([P, P], I),
             "helm_level_shape": ([P, I, P], I),
             "helm_create_batch": ([I, P, P, P, P, P, P, P], I),
@@ -342,6 +343,17 @@ def helm_profile_read(h: Handle) -> dict:
     la, ms, by, fl = (C.c_int * nc)(), (C.c_double * nc)(), (C.c_double * nc)(), (C.c_double * nc)()
     _check(load().helm_profile_read(h.ptr, nc, la, ms, by, fl))
     return {name: dict(launches=la[i], ms=ms[i], bytes=by[i], flops=fl[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+
+def helm_mg_conv_noalloc(h: Handle, b: torch.Tensor, x: torch.Tensor, tol=1e-6, maxcyc=100):
+    """helm_mg_conv computed in the library's fixed scratch array (no allocation at all, not
+    even here: the caller passes the output ``x``).  For callers that cannot allocate at the
+    point of the call, e.g. during CUDA graph capture.  Returns (cycles, factor); x is
+    overwritten with the stand-alone multigrid iterate."""
+    nc, fac = C.c_int(), C.c_double()
+    _check(load().helm_mg_conv_noalloc(h.ptr, C.c_void_p(_vec(b, h.np, "b")), C.c_void_p(_vec(x, h.np, "x", b.dtype)),
+                                       _prec_of(b), float(tol), int(maxcyc), C.byref(nc), C.byref(fac)))
+    return nc.value, fac.value
 
 
 class Batch:

@@ -238,6 +238,37 @@ helm_status helm_create_impl(const helm_grid *grid, double theta, const double *
         CKC(upload_c(&h->wts[a], w, h->owned, s));
     }
     for (int a = 0; a < 3; a++) h->A64.n[a] = h->n[a];
+    // the same A with every FP64 coefficient stored as a float pair hi + lo (hi = nearest
+    // float, lo = nearest float to the remainder) for the double-FP32 apply
+    {
+        auto fsplit = [](double v, float &hi, float &lo) {
+            hi = (float)v;
+            lo = (float)(v - (double)hi);
+        };
+        for (int a = 0; a < 3; a++) {
+            std::vector<cd> tri = a < dim ? fd_triples(z[a], 0.0, 1.0) : std::vector<cd>(3, cd(0, 0));
+            std::vector<float4> t4(tri.size());
+            for (size_t q = 0; q < tri.size(); q++) {
+                float rh, rl, ih, il;
+                fsplit(tri[q].real(), rh, rl);
+                fsplit(tri[q].imag(), ih, il);
+                t4[q] = make_float4(rh, rl, ih, il);
+            }
+            float4 *d = nullptr;
+            CKC(dalloc(&d, t4.size(), h->owned));
+            CKC(cudaMemcpyAsync(d, t4.data(), t4.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
+            CKC(cudaStreamSynchronize(s));
+            h->Adf.coef[a] = d;
+            h->Adf.n[a] = h->n[a];
+        }
+        std::vector<float2> k2s(k2h.size());
+        for (size_t q = 0; q < k2h.size(); q++) fsplit(k2h[q], k2s[q].x, k2s[q].y);
+        float2 *d = nullptr;
+        CKC(dalloc(&d, k2s.size(), h->owned));
+        CKC(cudaMemcpyAsync(d, k2s.data(), k2s.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+        CKC(cudaStreamSynchronize(s));
+        h->Adf.k2 = d;
+    }
     CKC(upload_r(&h->k2A, k2h, h->owned, s));
     h->A64.k2 = h->k2A;
     h->A64.bk = make_double2(-1.0, 0.0);
@@ -328,12 +359,14 @@ helm_status helm_create_impl(const helm_grid *grid, double theta, const double *
         for (int pass = 0; pass < 2; pass++) {
             const size_t es = pass == 0 ? sizeof(float2) : sizeof(double2);
             int top = nlev - 1;
-            size_t bytes = 3 * es * h->lv[top].np;
             while (top > 0 && nlev - top < MAX_TAIL_LEVELS) {
                 const LevelDev &L = h->lv[top - 1];
                 const double ni = (double)(L.n[0] - 2) * (L.n[1] - 2) * (dim == 3 ? (double)(L.n[2] - 2) : 1.0);
-                if (ni > TAIL_MAX_UNKNOWNS || bytes + 3 * es * L.np > TAIL_SMEM_BYTES) break;
-                bytes += 3 * es * L.np;
+                int n[MAX_TAIL_LEVELS][3];
+                for (int l = top - 1; l < nlev; l++)
+                    for (int a = 0; a < 3; a++) n[l - top + 1][a] = h->lv[l].n[a];
+                if (ni > TAIL_MAX_UNKNOWNS || mg_tail_smem_bytes_nodes(dim, nlev - top + 1, n, h->nu_c, es) > TAIL_SMEM_BYTES)
+                    break;
                 top--;
             }
             // a lone coarsest level keeps its dense-solve kernel

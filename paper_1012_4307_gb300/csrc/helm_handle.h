@@ -63,6 +63,7 @@ struct helm_handle {
     double2 *coefA64[3] = {nullptr, nullptr, nullptr};
     float2 *coefA32[3] = {nullptr, nullptr, nullptr};
     double *k2A = nullptr;
+    DevOpDF Adf{};  // A with float-pair coefficients (double-FP32 Arnoldi products)
     double2 *wts[3] = {nullptr, nullptr, nullptr};  // dual-volume weights per axis
 
     std::vector<LevelDev> lv;

@@ -32,10 +32,11 @@ template <typename C> __host__ __device__ __forceinline__ C cfmac(C a, C b, C ac
     return mk(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
 }
 template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
-// 1 / a
+// 1 / a = conj(a) / |a|^2 (one real division)
 template <typename C> __host__ __device__ __forceinline__ C cinv(C a) {
-    auto d = a.x * a.x + a.y * a.y;
-    return mk(a.x / d, -a.y / d);
+    const auto d = a.x * a.x + a.y * a.y;
+    const auto r = decltype(d)(1) / d;
+    return mk(a.x * r, -a.y * r);
 }
 __device__ __forceinline__ float2 to_c(float2 v, float) { return v; }
 __device__ __forceinline__ float2 to_c(double2 v, float) { return make_float2((float)v.x, (float)v.y); }
@@ -54,6 +55,16 @@ template <typename R> struct DevOp {
     const R *k2;
     C bk, c;
 };
+
+// The Helmholtz operator A = L_h - k^2 with coefficients and k^2 stored as float pairs
+// (hi + lo, see df_arith.h): coef[ax][3*j + t] = (re.hi, re.lo, im.hi, im.lo), k2[p] = (hi, lo).
+struct DevOpDF {
+    int n[3];
+    const float4 *coef[3];
+    const float2 *k2;
+};
+// y = A z in double-FP32 arithmetic, z complex64, y FP64 (interior written).
+cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, double2 *y, cudaStream_t s);
 
 // Kernel launch geometry helpers
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
@@ -93,6 +104,20 @@ cudaError_t launch_dense_solve(const int n[3], int dim, int nu, const typename C
 constexpr int MAX_TAIL_LEVELS = 4;
 constexpr int TAIL_MAX_UNKNOWNS = 4096;
 constexpr size_t TAIL_SMEM_BYTES = 200 * 1024;  // b, u, t of every tail level in shared memory
+// Dynamic shared memory of the fused tail: the coarsest solve's compact right-hand side
+// (nu_c values, rounded up to even) and b, u, t of every tail level.
+inline size_t mg_tail_smem_bytes_nodes(int dim, int nlev, const int (*n)[3], int nu_c, size_t es) {
+    size_t bytes = (size_t)((nu_c + 1) & ~1) * es;
+    for (int l = 0; l < nlev; l++) bytes += 3 * es * (size_t)n[l][0] * n[l][1] * (dim == 3 ? n[l][2] : 1);
+    return bytes;
+}
+template <typename R>
+inline size_t mg_tail_smem_bytes(int dim, int nlev, const DevOp<R> *ops, int nu_c, size_t es) {
+    int n[MAX_TAIL_LEVELS][3];
+    for (int l = 0; l < nlev && l < MAX_TAIL_LEVELS; l++)
+        for (int a = 0; a < 3; a++) n[l][a] = ops[l].n[a];
+    return mg_tail_smem_bytes_nodes(dim, nlev < MAX_TAIL_LEVELS ? nlev : MAX_TAIL_LEVELS, n, nu_c, es);
+}
 template <typename R>
 cudaError_t launch_mg_tail(int dim, int nlev, const DevOp<R> *ops, typename CT<R>::T *const *b,
                            typename CT<R>::T *const *u, typename CT<R>::T *const *t, const typename CT<R>::T *minv,

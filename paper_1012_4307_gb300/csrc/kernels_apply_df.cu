@@ -1,0 +1,73 @@
+// w = A z for the Helmholtz operator A = L_h - k^2 (Section 3.2 stencil) with a complex64 z
+// (the output of the complex64 multigrid preconditioner) and an FP64 result, computed in
+// double-FP32 arithmetic on the FP32 units.  A's coefficients and k^2 are stored pre-split as
+// float pairs; z is exact in FP32, so each product a * z is error-free up to the dropped
+// a.lo * z rounding (2^-48 relative); the sum over the stencil is kept exactly with TwoSum and
+// rounded to FP64 once per node.  Same operands and result layout as k_apply<double, 2|3, float2>
+// in kernels_mg.cu, which does the same work with FP64 fused multiply-adds.
+#include "helm_internal.h"
+#include "df_arith.h"
+
+namespace {
+
+constexpr int BX = 32, BY = 8, KCHUNK = 8;
+
+// acc += a * z with a = (re.hi, re.lo, im.hi, im.lo) and a float complex z.
+__device__ __forceinline__ void cmac(float4 a, float2 z, float &sr, float &cr, float &si, float &ci) {
+    const ff ar{a.x, a.y}, ai{a.z, a.w};
+    float p, e;
+    ff_prod_f(ar, z.x, p, e);
+    ff_acc_prod(sr, cr, p, e);
+    ff_prod_f(ai, z.y, p, e);
+    ff_acc_prod(sr, cr, -p, -e);
+    ff_prod_f(ar, z.y, p, e);
+    ff_acc_prod(si, ci, p, e);
+    ff_prod_f(ai, z.x, p, e);
+    ff_acc_prod(si, ci, p, e);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(BX *BY) k_apply_A_df(DevOpDF o, const float2 *__restrict__ z, double2 *__restrict__ y) {
+    const int nx = o.n[0], ny = o.n[1], nz = o.n[2];
+    const int i = blockIdx.x * BX + threadIdx.x + 1;
+    const int j = blockIdx.y * BY + threadIdx.y + 1;
+    if (i > nx - 2 || j > ny - 2) return;
+    int k0 = 0, k1 = 1;
+    if (DIM == 3) {
+        k0 = blockIdx.z * KCHUNK + 1;
+        k1 = min(k0 + KCHUNK, nz - 1);
+    }
+    const size_t sy = (size_t)nx, sz = (size_t)nx * ny;
+    const float4 cxw = o.coef[0][3 * i], cxc = o.coef[0][3 * i + 1], cxe = o.coef[0][3 * i + 2];
+    const float4 cyw = o.coef[1][3 * j], cyc = o.coef[1][3 * j + 1], cye = o.coef[1][3 * j + 2];
+    const ff dxy_r = ff_add(ff{cxc.x, cxc.y}, ff{cyc.x, cyc.y}), dxy_i = ff_add(ff{cxc.z, cxc.w}, ff{cyc.z, cyc.w});
+    for (int k = k0; k < k1; k++) {
+        const size_t p = (size_t)i + sy * ((size_t)j + (size_t)ny * k);
+        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+        cmac(cxw, z[p - 1], sr, cr, si, ci);
+        cmac(cxe, z[p + 1], sr, cr, si, ci);
+        cmac(cyw, z[p - sy], sr, cr, si, ci);
+        cmac(cye, z[p + sy], sr, cr, si, ci);
+        ff dr = dxy_r, di = dxy_i;
+        if (DIM == 3) {
+            const float4 czw = o.coef[2][3 * k], czc = o.coef[2][3 * k + 1], cze = o.coef[2][3 * k + 2];
+            cmac(czw, z[p - sz], sr, cr, si, ci);
+            cmac(cze, z[p + sz], sr, cr, si, ci);
+            dr = ff_add(dr, ff{czc.x, czc.y});
+            di = ff_add(di, ff{czc.z, czc.w});
+        }
+        const float2 kk = o.k2[p];
+        dr = ff_add(dr, ff{-kk.x, -kk.y});  // diagonal: sum of centre coefficients - k^2
+        cmac(make_float4(dr.hi, dr.lo, di.hi, di.lo), z[p], sr, cr, si, ci);
+        y[p] = make_double2(ff_to_double(ff_norm(sr, cr)), ff_to_double(ff_norm(si, ci)));
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, double2 *y, cudaStream_t s) {
+    dim3 g(cdiv(op.n[0] - 2, BX), cdiv(op.n[1] - 2, BY), dim == 3 ? cdiv(op.n[2] - 2, KCHUNK) : 1), b(BX, BY);
+    if (dim == 3) k_apply_A_df<3><<<g, b, 0, s>>>(op, z, y);
+    else k_apply_A_df<2><<<g, b, 0, s>>>(op, z, y);
+    return cudaGetLastError();
+}

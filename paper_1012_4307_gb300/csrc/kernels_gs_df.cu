@@ -14,74 +14,11 @@
 //
 // Same contracts as k_mdot_norm / k_update_norm in kernels_krylov.cu (partials layout, gate).
 #include "helm_internal.h"
+#include "df_arith.h"
 
 namespace {
 
 constexpr int NT = 256;
-
-struct ff {
-    float hi, lo;
-};
-
-// Exact split of x into hi + lo (hi: 24 leading bits by truncation, lo: remaining 29 bits
-// rounded to float).  Zero, subnormal and |x| < 2^-126 give (0, 0); |x| < 2^-74 drops lo.
-__device__ __forceinline__ ff split(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
-    const int e = (int)((h32 >> 20) & 0x7FFu);
-    const unsigned sign = h32 & 0x80000000u;
-    ff r;
-    if (e < 897) { r.hi = 0.f; r.lo = 0.f; return r; }
-    if (e > 1150) { r.hi = __int_as_float((int)(sign | 0x7F800000u)); r.lo = 0.f; return r; }
-    r.hi = __int_as_float((int)(sign | ((unsigned)(e - 896) << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29)));
-    if (e < 949) { r.lo = 0.f; return r; }
-    const float scale = __int_as_float((e - 948) << 23);  // 2^(e - 1075)
-    const float lo = __fmul_rn(__uint2float_rn(l32 & 0x1FFFFFFFu), scale);
-    r.lo = __int_as_float(__float_as_int(lo) | (int)sign);
-    return r;
-}
-
-// Error-free product a*b ~ p + e (al*bl dropped).
-__device__ __forceinline__ void two_prod(ff a, ff b, float &p, float &e) {
-    p = __fmul_rn(a.hi, b.hi);
-    e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-}
-
-// (s, c) += x exactly in s + c (Knuth TwoSum on s, error folded into c).
-__device__ __forceinline__ void acc_add(float &s, float &c, float x) {
-    const float t = __fadd_rn(s, x);
-    const float z = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));
-    s = t;
-    c = __fadd_rn(c, err);
-}
-
-// Adds a product p + e into the accumulator (s, c).
-__device__ __forceinline__ void acc_prod(float &s, float &c, float p, float e) {
-    acc_add(s, c, p);
-    c = __fadd_rn(c, e);
-}
-
-// Normalised double-float sum of two double-floats.
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-    const float s = __fadd_rn(a.hi, b.hi);
-    const float z = __fsub_rn(s, a.hi);
-    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, z)), __fsub_rn(b.hi, z));
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    ff r;
-    r.hi = __fadd_rn(s, e);
-    r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
-    return r;
-}
-
-__device__ __forceinline__ ff ff_norm(float s, float c) {
-    ff r;
-    r.hi = __fadd_rn(s, c);
-    r.lo = __fsub_rn(c, __fsub_rn(r.hi, s));
-    return r;
-}
 
 __device__ __forceinline__ ff shfl_down_ff(ff v, int off) {
     v.hi = __shfl_down_sync(0xffffffffu, v.hi, off);
@@ -89,7 +26,6 @@ __device__ __forceinline__ ff shfl_down_ff(ff v, int off) {
     return v;
 }
 
-__device__ __forceinline__ double to_double(ff v) { return (double)v.hi + (double)v.lo; }
 
 // Block sums of NV double-float values per thread (fixed tree); thread t < NV gets sum t as
 // an FP64 number in out[t].
@@ -108,7 +44,7 @@ __device__ __forceinline__ void block_sum_ff(ff (&v)[NV], double *out) {
     if (threadIdx.x < NV) {
         ff s = red[0][threadIdx.x];
         for (int w = 1; w < NT / 32; w++) s = ff_add(s, red[w][threadIdx.x]);
-        out[threadIdx.x] = to_double(s);
+        out[threadIdx.x] = ff_to_double(s);
     }
 }
 
@@ -129,28 +65,28 @@ __global__ void __launch_bounds__(NT) k_mdot_norm_df(size_t n, const double2 *__
     for (int t = 0; t < CH; t++) sr[t] = cr[t] = si[t] = ci[t] = 0.f;
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const double2 wq = w[q];
-        const ff wx = split(wq.x), wy = split(wq.y);
+        const ff wx = ff_split(wq.x), wy = ff_split(wq.y);
         float p, e;
         if (first) {
-            two_prod(wx, wx, p, e);
-            acc_prod(sn, cn, p, e);
-            two_prod(wy, wy, p, e);
-            acc_prod(sn, cn, p, e);
+            ff_two_prod(wx, wx, p, e);
+            ff_acc_prod(sn, cn, p, e);
+            ff_two_prod(wy, wy, p, e);
+            ff_acc_prod(sn, cn, p, e);
         }
 #pragma unroll
         for (int t = 0; t < CH; t++) {
             if (t < cnt) {
                 const double2 vq = V[(size_t)(i0 + t) * ldv + q];
-                const ff vx = split(vq.x), vy = split(vq.y);
+                const ff vx = ff_split(vq.x), vy = ff_split(vq.y);
                 // conj(v) w = (vx wx + vy wy) + i (vx wy - vy wx)
-                two_prod(vx, wx, p, e);
-                acc_prod(sr[t], cr[t], p, e);
-                two_prod(vy, wy, p, e);
-                acc_prod(sr[t], cr[t], p, e);
-                two_prod(vx, wy, p, e);
-                acc_prod(si[t], ci[t], p, e);
-                two_prod(vy, wx, p, e);
-                acc_prod(si[t], ci[t], -p, -e);
+                ff_two_prod(vx, wx, p, e);
+                ff_acc_prod(sr[t], cr[t], p, e);
+                ff_two_prod(vy, wy, p, e);
+                ff_acc_prod(sr[t], cr[t], p, e);
+                ff_two_prod(vx, wy, p, e);
+                ff_acc_prod(si[t], ci[t], p, e);
+                ff_two_prod(vy, wx, p, e);
+                ff_acc_prod(si[t], ci[t], -p, -e);
             }
         }
     }
@@ -177,41 +113,41 @@ __global__ void __launch_bounds__(NT) k_update_norm_df(size_t n, const double2 *
     __shared__ float4 hs[64];  // (re.hi, re.lo, im.hi, im.lo)
     __shared__ double sums[1];
     for (int i = threadIdx.x; i < nv; i += NT) {
-        const ff a = split(h[i].x), b = split(h[i].y);
+        const ff a = ff_split(h[i].x), b = ff_split(h[i].y);
         hs[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
     }
     __syncthreads();
     float sn = 0.f, cn = 0.f;
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const double2 wq = w[q];
-        const ff wx = split(wq.x), wy = split(wq.y);
+        const ff wx = ff_split(wq.x), wy = ff_split(wq.y);
         float sx = wx.hi, cx = wx.lo, sy = wy.hi, cy = wy.lo;
 #pragma unroll 4
         for (int i = 0; i < nv; i++) {
             const double2 vq = V[(size_t)i * ldv + q];
-            const ff vx = split(vq.x), vy = split(vq.y);
+            const ff vx = ff_split(vq.x), vy = ff_split(vq.y);
             const float4 hh = hs[i];
             const ff hx = {hh.x, hh.y}, hy = {hh.z, hh.w};
             float p, e;
             // w -= v h:  re -= vx hx - vy hy ;  im -= vx hy + vy hx
-            two_prod(vx, hx, p, e);
-            acc_prod(sx, cx, -p, -e);
-            two_prod(vy, hy, p, e);
-            acc_prod(sx, cx, p, e);
-            two_prod(vx, hy, p, e);
-            acc_prod(sy, cy, -p, -e);
-            two_prod(vy, hx, p, e);
-            acc_prod(sy, cy, -p, -e);
+            ff_two_prod(vx, hx, p, e);
+            ff_acc_prod(sx, cx, -p, -e);
+            ff_two_prod(vy, hy, p, e);
+            ff_acc_prod(sx, cx, p, e);
+            ff_two_prod(vx, hy, p, e);
+            ff_acc_prod(sy, cy, -p, -e);
+            ff_two_prod(vy, hx, p, e);
+            ff_acc_prod(sy, cy, -p, -e);
         }
         const ff rx = ff_norm(sx, cx), ry = ff_norm(sy, cy);
-        const double2 out = make_double2(to_double(rx), to_double(ry));
+        const double2 out = make_double2(ff_to_double(rx), ff_to_double(ry));
         w[q] = out;
         float p, e;
-        const ff ox = split(out.x), oy = split(out.y);
-        two_prod(ox, ox, p, e);
-        acc_prod(sn, cn, p, e);
-        two_prod(oy, oy, p, e);
-        acc_prod(sn, cn, p, e);
+        const ff ox = ff_split(out.x), oy = ff_split(out.y);
+        ff_two_prod(ox, ox, p, e);
+        ff_acc_prod(sn, cn, p, e);
+        ff_two_prod(oy, oy, p, e);
+        ff_acc_prod(sn, cn, p, e);
     }
     ff vals[1] = {ff_norm(sn, cn)};
     block_sum_ff<1>(vals, sums);

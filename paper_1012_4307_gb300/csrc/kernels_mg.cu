@@ -273,9 +273,11 @@ template <typename C> __global__ void k_zero(size_t n, C *x) {
 // ------------------------------------------------------------------------------ coarse tail
 // The coarse levels of a cycle (a few thousand unknowns or fewer) are launch- and latency-
 // bound when every sweep is its own grid.  k_mg_tail runs Algorithm 1 from the tail's top
-// level down to the exact coarsest solve and back inside ONE thread block: each phase is a
-// block-strided loop over the level's interior, phases are separated by __syncthreads(), and
-// the vectors stay in (L2-resident) global memory.  Same arithmetic as the per-level kernels.
+// level down to the exact coarsest solve and back inside ONE thread block, with every level's
+// b, u, t in shared memory (the host picks the tail depth so they fit): the top level's
+// right-hand side is copied in, its result copied out (interior nodes only).  Phases are
+// block-wide loops (warps over grid rows, lanes over x) separated by __syncthreads().  Same
+// arithmetic as the per-level kernels.
 constexpr int TAIL_THREADS = 512;
 
 template <typename R> struct TailLevelDev {
@@ -288,13 +290,19 @@ template <typename R> struct TailArgs {
     int nlev, nu_c, nu1, nu2, rb;
     R omega;
     const typename CT<R>::T *minv;
+    typename CT<R>::T *bc;  // compact right-hand side of the coarsest solve (shared memory)
 };
 
-template <int DIM>
-__device__ __forceinline__ void tail_index(int idx, int mx, int my, int &i, int &j, int &k) {
-    i = 1 + idx % mx;
-    j = 1 + (idx / mx) % my;
-    k = DIM == 3 ? 1 + idx / (mx * my) : 0;
+// f(i, j, k) for every interior node of a level; warps take rows (j, k), lanes take i.
+template <int DIM, typename F>
+__device__ __forceinline__ void for_interior(int nx, int ny, int nz, F f) {
+    const int mx = nx - 2, my = ny - 2, rows = my * (DIM == 3 ? nz - 2 : 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < rows; r += nw) {
+        const int j = 1 + (DIM == 3 ? r % my : r);
+        const int k = DIM == 3 ? 1 + r / my : 0;
+        for (int i = 1 + lane; i <= mx; i += 32) f(i, j, k);
+    }
 }
 
 template <typename R, int DIM>
@@ -302,54 +310,48 @@ __device__ void tail_smooth(const TailArgs<R> &A, const TailLevelDev<R> &L, int 
                             typename CT<R>::T **oth, bool zero) {
     typedef typename CT<R>::T C;
     const OpView<R> &o = L.o;
-    const int mx = o.nx - 2, my = o.ny - 2, mz = DIM == 3 ? o.nz - 2 : 1, ni = mx * my * mz;
     const size_t sz = (size_t)o.nx * o.ny;
+    auto at = [&](int i, int j, int k) { return (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k); };
     if (zero && (sweeps == 0 || A.rb)) {
-        for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
-            int i, j, k;
-            tail_index<DIM>(idx, mx, my, i, j, k);
-            (*cur)[(size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k)] = mk(R(0), R(0));
-        }
+        C *u = *cur;
+        for_interior<DIM>(o.nx, o.ny, o.nz, [&](int i, int j, int k) { u[at(i, j, k)] = mk(R(0), R(0)); });
         __syncthreads();
     }
     for (int s = 0; s < sweeps; s++) {
         if (A.rb) {
             for (int colour = 0; colour < 2; colour++) {
-                for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
-                    int i, j, k;
-                    tail_index<DIM>(idx, mx, my, i, j, k);
-                    if (((i + j + k) & 1) != colour) continue;
-                    const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
-                    C *u = *cur;
+                C *u = *cur;
+                for_interior<DIM>(o.nx, o.ny, o.nz, [&](int i, int j, int k) {
+                    if (((i + j + k) & 1) != colour) return;
+                    const size_t p = at(i, j, k);
                     C xm = mk(R(0), R(0)), xp = mk(R(0), R(0));
                     if (DIM == 3) { xm = u[p - sz]; xp = u[p + sz]; }
                     const C xc = u[p];
                     C d;
                     const C mu = stencil<R, DIM>(o, u, p, i, j, k, xm, xc, xp, d);
                     u[p] = cadd(xc, cscale(cmul(csub(L.b[p], mu), cinv(d)), A.omega));
-                }
+                });
                 __syncthreads();
             }
         } else {
             const bool z0 = zero && s == 0;
-            for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
-                int i, j, k;
-                tail_index<DIM>(idx, mx, my, i, j, k);
-                const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
-                const C *u = *cur;
+            const C *u = *cur;
+            C *un = *oth;
+            for_interior<DIM>(o.nx, o.ny, o.nz, [&](int i, int j, int k) {
+                const size_t p = at(i, j, k);
                 if (z0) {
                     C d = cadd(cadd(o.cx[3 * i + 1], o.cy[3 * j + 1]), cadd(cscale(o.bk, o.k2[p]), o.c));
                     if (DIM == 3) d = cadd(d, o.cz[3 * k + 1]);
-                    (*oth)[p] = cscale(cmul(L.b[p], cinv(d)), A.omega);
+                    un[p] = cscale(cmul(L.b[p], cinv(d)), A.omega);
                 } else {
                     C xm = mk(R(0), R(0)), xp = mk(R(0), R(0));
                     if (DIM == 3) { xm = u[p - sz]; xp = u[p + sz]; }
                     const C xc = u[p];
                     C d;
                     const C mu = stencil<R, DIM>(o, u, p, i, j, k, xm, xc, xp, d);
-                    (*oth)[p] = cadd(xc, cscale(cmul(csub(L.b[p], mu), cinv(d)), A.omega));
+                    un[p] = cadd(xc, cscale(cmul(csub(L.b[p], mu), cinv(d)), A.omega));
                 }
-            }
+            });
             __syncthreads();
             C *t = *cur;
             *cur = *oth;
@@ -358,28 +360,29 @@ __device__ void tail_smooth(const TailArgs<R> &A, const TailLevelDev<R> &L, int 
     }
 }
 
+// Exact coarsest solve u = Minv b: gather b's unknowns (natural order) into a compact array,
+// one warp per row of Minv (coalesced, 8 loads in flight per lane), scatter the rows.
 template <typename R, int DIM>
 __device__ void tail_dense(const TailArgs<R> &A, const TailLevelDev<R> &L) {
     typedef typename CT<R>::T C;
-    const int mx = L.o.nx - 2, my = L.o.ny - 2;
+    const int mx = L.o.nx - 2, my = L.o.ny - 2, nu = A.nu_c;
+    auto node = [&](int c) {
+        const int i = 1 + c % mx, j = 1 + (c / mx) % my, k = DIM == 3 ? 1 + c / (mx * my) : 0;
+        return (size_t)i + (size_t)L.o.nx * ((size_t)j + (size_t)L.o.ny * k);
+    };
+    for (int c = threadIdx.x; c < nu; c += blockDim.x) A.bc[c] = L.b[node(c)];
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int row = warp; row < A.nu_c; row += nwarp) {
+    for (int row = warp; row < nu; row += nwarp) {
+        const C *mrow = A.minv + (size_t)row * nu;
         C acc = mk(R(0), R(0));
 #pragma unroll 8
-        for (int c = lane; c < A.nu_c; c += 32) {
-            int i, j, k;
-            tail_index<DIM>(c, mx, my, i, j, k);
-            acc = cfma(A.minv[(size_t)row * A.nu_c + c], L.b[(size_t)i + (size_t)L.o.nx * ((size_t)j + (size_t)L.o.ny * k)], acc);
-        }
+        for (int c = lane; c < nu; c += 32) acc = cfma(mrow[c], A.bc[c], acc);
         for (int off = 16; off > 0; off >>= 1) {
             acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
             acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
         }
-        if (lane == 0) {
-            int i, j, k;
-            tail_index<DIM>(row, mx, my, i, j, k);
-            L.u[(size_t)i + (size_t)L.o.nx * ((size_t)j + (size_t)L.o.ny * k)] = acc;
-        }
+        if (lane == 0) L.u[node(row)] = acc;
     }
     __syncthreads();
 }
@@ -400,29 +403,29 @@ __device__ void tail_cycle(const TailArgs<R> &A, bool zero, int gf, int gc) {
     const TailLevelDev<R> &Lc = A.lv[l + 1];
     // residual + full weighting into the next level's right-hand side
     {
-        const int mx = Lc.o.nx - 2, my = Lc.o.ny - 2, mz = DIM == 3 ? Lc.o.nz - 2 : 1, ni = mx * my * mz;
-        for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
-            int I, J, K;
-            tail_index<DIM>(idx, mx, my, I, J, K);
+        const C *uc = cur;
+        for_interior<DIM>(Lc.o.nx, Lc.o.ny, Lc.o.nz, [&](int I, int J, int K) {
             C acc = mk(R(0), R(0));
             for (int dk = (DIM == 3 ? -1 : 0); dk <= (DIM == 3 ? 1 : 0); dk++) {
                 const R wk = DIM == 3 ? (dk == 0 ? R(0.5) : R(0.25)) : R(1);
                 const int k = DIM == 3 ? 2 * K + dk : 0;
+#pragma unroll
                 for (int dj = -1; dj <= 1; dj++) {
                     const R wj = wk * (dj == 0 ? R(0.5) : R(0.25));
                     const int j = 2 * J + dj;
+#pragma unroll
                     for (int di = -1; di <= 1; di++) {
                         const R w = wj * (di == 0 ? R(0.5) : R(0.25));
                         const int i = 2 * I + di;
                         const size_t p = (size_t)i + (size_t)L.o.nx * ((size_t)j + (size_t)L.o.ny * k);
                         C d;
-                        const C mu = apply_point<R, DIM>(L.o, (const C *)cur, i, j, k, d);
+                        const C mu = apply_point<R, DIM>(L.o, uc, i, j, k, d);
                         acc = cadd(acc, cscale(csub(L.b[p], mu), w));
                     }
                 }
             }
             Lc.b[(size_t)I + (size_t)Lc.o.nx * ((size_t)J + (size_t)Lc.o.ny * K)] = acc;
-        }
+        });
         __syncthreads();
     }
     if (l + 1 == A.nlev - 1) {
@@ -435,11 +438,9 @@ __device__ void tail_cycle(const TailArgs<R> &A, bool zero, int gf, int gc) {
     }
     // prolongation + correction
     {
-        const int nx = L.o.nx, ny = L.o.ny, mx = nx - 2, my = ny - 2, mz = DIM == 3 ? L.o.nz - 2 : 1;
-        const int ncx = Lc.o.nx, ncy = Lc.o.ny, ni = mx * my * mz;
-        for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
-            int i, j, k;
-            tail_index<DIM>(idx, mx, my, i, j, k);
+        const int nx = L.o.nx, ny = L.o.ny, ncx = Lc.o.nx, ncy = Lc.o.ny;
+        C *uf = cur;
+        for_interior<DIM>(nx, ny, L.o.nz, [&](int i, int j, int k) {
             const int kk0 = DIM == 3 ? k >> 1 : 0, kk1 = DIM == 3 ? (k + 1) >> 1 : 0;
             C acc = mk(R(0), R(0));
             int cnt = 0;
@@ -450,39 +451,34 @@ __device__ void tail_cycle(const TailArgs<R> &A, bool zero, int gf, int gc) {
                         cnt++;
                     }
             const size_t p = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k);
-            cur[p] = cadd(cur[p], cscale(acc, R(1) / R(cnt)));
-        }
+            uf[p] = cadd(uf[p], cscale(acc, R(1) / R(cnt)));
+        });
         __syncthreads();
     }
     tail_smooth<R, DIM>(A, L, A.nu2, &cur, &oth, false);
-    if (cur != L.u) {  // interior only: the top level's u may be a caller vector
-        const int mx = L.o.nx - 2, my = L.o.ny - 2, ni = mx * my * (DIM == 3 ? L.o.nz - 2 : 1);
-        for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
-            int i, j, k;
-            tail_index<DIM>(idx, mx, my, i, j, k);
+    if (cur != L.u) {
+        const C *src = cur;
+        for_interior<DIM>(L.o.nx, L.o.ny, L.o.nz, [&](int i, int j, int k) {
             const size_t p = (size_t)i + (size_t)L.o.nx * ((size_t)j + (size_t)L.o.ny * k);
-            L.u[p] = cur[p];
-        }
+            L.u[p] = src[p];
+        });
         __syncthreads();
     }
     }  // LVL + 1 < MAX_TAIL_LEVELS
 }
 
-// smem != 0: every level's b, u, t live in dynamic shared memory (zeroed, so boundary rings
-// are zero); the top level's right-hand side is copied in from global memory and its result
-// copied out (interior nodes only), with the caller's initial guess copied in when !zero.
+// Dynamic shared memory: [compact coarsest rhs | per level: b, u, t].  A.lv[0].b / u hold the
+// caller's global top-level vectors; zero != 0 means the top-level iterate starts at 0.
 template <typename R, int DIM>
-__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs<R> A, int gf, int gc, int zero, int smem) {
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs<R> A, int gf, int gc, int zero) {
     typedef typename CT<R>::T C;
     extern __shared__ __align__(16) unsigned char tail_smem[];
     __shared__ TailArgs<R> S;
-    if (!smem) {
-        tail_cycle<R, DIM, 0>(A, zero != 0, gf, gc);
-        return;
-    }
     if (threadIdx.x == 0) {
         S = A;
         C *p = (C *)tail_smem;
+        S.bc = p;
+        p += (A.nu_c + 1) & ~1;
         for (int l = 0; l < A.nlev; l++) {
             const size_t np = (size_t)A.lv[l].o.nx * A.lv[l].o.ny * (DIM == 3 ? A.lv[l].o.nz : 1);
             S.lv[l].b = p; p += np;
@@ -492,29 +488,24 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs<R> A, int gf,
     }
     __syncthreads();
     {
-        const C *end = S.lv[S.nlev - 1].t + (size_t)S.lv[S.nlev - 1].o.nx * S.lv[S.nlev - 1].o.ny *
-                                                (DIM == 3 ? S.lv[S.nlev - 1].o.nz : 1);
+        const TailLevelDev<R> &last = S.lv[S.nlev - 1];
+        const C *end = last.t + (size_t)last.o.nx * last.o.ny * (DIM == 3 ? last.o.nz : 1);
         const size_t total = end - (const C *)tail_smem;
         for (size_t q = threadIdx.x; q < total; q += blockDim.x) ((C *)tail_smem)[q] = mk(R(0), R(0));
     }
     __syncthreads();
     const OpView<R> &o = A.lv[0].o;
-    const int mx = o.nx - 2, my = o.ny - 2, ni = mx * my * (DIM == 3 ? o.nz - 2 : 1);
-    for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
-        int i, j, k;
-        tail_index<DIM>(idx, mx, my, i, j, k);
+    for_interior<DIM>(o.nx, o.ny, o.nz, [&](int i, int j, int k) {
         const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
         S.lv[0].b[p] = A.lv[0].b[p];
         if (!zero) S.lv[0].u[p] = A.lv[0].u[p];
-    }
+    });
     __syncthreads();
     tail_cycle<R, DIM, 0>(S, zero != 0, gf, gc);
-    for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
-        int i, j, k;
-        tail_index<DIM>(idx, mx, my, i, j, k);
+    for_interior<DIM>(o.nx, o.ny, o.nz, [&](int i, int j, int k) {
         const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
         A.lv[0].u[p] = S.lv[0].u[p];
-    }
+    });
 }
 
 dim3 grid_for(const int n[3], int dim) {
@@ -595,7 +586,7 @@ template <typename R>
 cudaError_t launch_mg_tail(int dim, int nlev, const DevOp<R> *ops, typename CT<R>::T *const *b,
                            typename CT<R>::T *const *u, typename CT<R>::T *const *t, const typename CT<R>::T *minv,
                            int nu_c, int nu1, int nu2, int rb, R omega, int gf, int gc, int zero, cudaStream_t s) {
-    if (nlev < 1 || nlev > MAX_TAIL_LEVELS) return cudaErrorInvalidValue;
+    if (nlev < 2 || nlev > MAX_TAIL_LEVELS) return cudaErrorInvalidValue;
     TailArgs<R> A{};
     for (int l = 0; l < nlev; l++) {
         A.lv[l].o = view(ops[l]);
@@ -611,21 +602,17 @@ cudaError_t launch_mg_tail(int dim, int nlev, const DevOp<R> *ops, typename CT<R
     A.rb = rb;
     A.omega = omega;
     A.minv = minv;
-    // shared-memory residency when all levels' b, u, t fit next to the block's static smem
-    size_t bytes = 0;
-    for (int l = 0; l < nlev; l++)
-        bytes += 3 * sizeof(typename CT<R>::T) * (size_t)ops[l].n[0] * ops[l].n[1] * (dim == 3 ? ops[l].n[2] : 1);
-    const int use_smem = bytes <= TAIL_SMEM_BYTES;
-    const size_t dyn = use_smem ? bytes : 0;
+    const size_t bytes = mg_tail_smem_bytes(dim, nlev, ops, nu_c, sizeof(typename CT<R>::T));
+    if (bytes > TAIL_SMEM_BYTES) return cudaErrorInvalidValue;
     static bool attr_set[2] = {false, false};
     if (!attr_set[dim == 3]) {
-        cudaError_t e = dim == 3 ? cudaFuncSetAttribute(k_mg_tail<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM_BYTES)
-                                 : cudaFuncSetAttribute(k_mg_tail<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM_BYTES);
+        cudaError_t e = dim == 3 ? cudaFuncSetAttribute(k_mg_tail<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM_BYTES)
+                                 : cudaFuncSetAttribute(k_mg_tail<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set[dim == 3] = true;
     }
-    if (dim == 3) k_mg_tail<R, 3><<<1, TAIL_THREADS, dyn, s>>>(A, gf, gc, zero, use_smem);
-    else k_mg_tail<R, 2><<<1, TAIL_THREADS, dyn, s>>>(A, gf, gc, zero, use_smem);
+    if (dim == 3) k_mg_tail<R, 3><<<1, TAIL_THREADS, bytes, s>>>(A, gf, gc, zero);
+    else k_mg_tail<R, 2><<<1, TAIL_THREADS, bytes, s>>>(A, gf, gc, zero);
     return cudaGetLastError();
 }
 template cudaError_t launch_mg_tail<float>(int, int, const DevOp<float> *, float2 *const *, float2 *const *,

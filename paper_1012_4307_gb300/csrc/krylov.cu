@@ -151,6 +151,10 @@ static cudaError_t precond_apply(helm_handle *h, const double2 *v, void *z, doub
     if (h->z_prec == HELM_C64) {
         e = precondition<float>(h, v, (float2 *)z);
         if (e != cudaSuccess) return e;
+        if (h->mg.gs_arith == HELM_GS_DF) {  // Arnoldi products in double-FP32: the apply too
+            ProfScope ps(h, HELM_K_APPLY, ni * (8 + 8 + 16), 0);
+            return launch_apply_A_df(h->Adf, h->dim, (const float2 *)z, w, h->stream);
+        }
         ProfScope ps(h, HELM_K_APPLY, ni * (8 + 8 + 16), apply_flops(h));
         return launch_apply<double, float2>(h->A64, h->dim, (const float2 *)z, w, h->stream);
     }

@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-iters", type=int, default=0, help="oracle iterations in the CPU sample (0 = auto)")
+    ap.add_argument("--batch", type=int, default=0, metavar="COUNT",
+                    help="batched workload instead: COUNT independent 2D problems with sizes drawn from "
+                         "{129, 257, 513, 1025} and energies in [0.5, 4], solved together (helm_solve_batch)")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",
                     help="profiling case: build the same problem and run one solve capped at ITERS iterations, "
                          "nothing else (keeps the launch count small enough for ncu)")
@@ -195,11 +198,79 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------------- batch
+def run_batch(args):
+    """COUNT problems solved together (one host thread, one stream and CUDA-graph-replayed
+    FGMRES steps per problem) against the same problems solved one after another."""
+    import torch
+
+    from paper_1012_4307_gb300 import helm
+    from paper_1012_4307_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    helm.load()
+    probs = W.config_batch(count=args.batch)
+    mg = helm.MGParams(kind="csg", prec="c64", gs="df", coarsest_n=17)
+    specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
+    b = helm.helm_create_batch(specs, mg=mg)
+    rhs = [torch.from_numpy(P.f).cuda() for P in probs]
+    xs = [torch.zeros_like(r) for r in rhs]
+    unknowns = sum(P.unknowns for P in probs)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def batch_once():
+        for x in xs:
+            x.zero_()
+        return helm.helm_solve_batch(b, rhs, xs, tol=args.tol, restart=30, maxit=5000)
+
+    for _ in range(max(1, args.warmup)):
+        batch_once()
+    sampler = ClockSampler(0)
+    sampler.start()
+    tot = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0.record(stream)
+        stats = batch_once()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    ms = tot / args.steps
+    # the same problems one after another through krylov_solve (same handles' settings)
+    seq_ms = 0.0
+    for P, r in zip(probs, rhs):
+        h = helm.helm_create(2, [P.n, P.n], torch.from_numpy(P.k2).cuda(), theta=P.theta, mg=mg)
+        x = torch.zeros_like(r)
+        helm.krylov_solve(h, r, x, tol=args.tol, restart=30, maxit=5000)
+        x.zero_()
+        e0.record(stream)
+        helm.krylov_solve(h, r, x, tol=args.tol, restart=30, maxit=5000)
+        e1.record(stream)
+        e1.synchronize()
+        seq_ms += e0.elapsed_time(e1)
+        h.close()
+    line = {"metric": "batched solve throughput (all problems to rel. residual %.0e)" % args.tol,
+            "value": unknowns / (ms / 1e3) / 1e6, "unit": "Mdof/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "c64 cycle / f64 outer",
+            "data": "synthetic",
+            "config": {"workload": "batch of %d 2D well problems, sizes {129,257,513,1025}, E in [0.5,4]" % args.batch,
+                       "unknowns": unknowns, "sizes": [P.n for P in probs],
+                       "l2": "256 MiB device write before every step, outside the timed events"},
+            "iterations": [s.iterations for s in stats], "sequential_ms": seq_ms,
+            "speedup_vs_sequential": seq_ms / ms, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------------- our arm
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch:
+        return run_batch(args)
     import numpy as np
     import torch
     import torch.distributed as dist

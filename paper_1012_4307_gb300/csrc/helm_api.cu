@@ -410,6 +410,9 @@ extern "C" void helm_destroy(helm_handle *h) {
     helm_free_krylov(h);
     for (void *p : h->owned) cudaFree(p);
     if (h->est_host) cudaFreeHost(h->est_host);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->ev_fn) cudaEventDestroy(h->ev_fn);
+    if (h->ev_beta) cudaEventDestroy(h->ev_beta);
     delete h;
 }
 

@@ -1,16 +1,36 @@
 // Batched solves of many independent problems (energies, right-hand sides, grid sizes).
-// Each problem owns a full handle (levels, Krylov workspace) on the batch's shared stream;
-// problems are solved largest first so that the tail of the batch is short.
+//
+// Each problem owns a full handle (levels, Krylov workspace) on its own non-blocking stream.
+// One host thread drives every problem's flexible-GMRES state machine round-robin: it only
+// ever polls events, so while one problem waits for its residual estimate the others keep
+// enqueueing, and kernels of different problems run concurrently on the GPU.  Every FGMRES
+// step of every problem is replayed from a CUDA graph captured on first use, so a step costs
+// one graph launch on the host.  Problems are visited largest first.
 #include <algorithm>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "helm_handle.h"
 
 struct helm_batch {
     std::vector<helm_handle *> h;
-    cudaStream_t stream = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t start = nullptr;
+    cudaStream_t user = nullptr;
 };
+
+extern "C" void helm_destroy_batch(helm_batch *b) {
+    if (!b) return;
+    for (helm_handle *h : b->h) helm_destroy(h);
+    for (cudaStream_t s : b->streams)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->done)
+        if (e) cudaEventDestroy(e);
+    if (b->start) cudaEventDestroy(b->start);
+    delete b;
+}
 
 extern "C" helm_status helm_create_batch(int nprob, const helm_grid *grids, const double *theta, const double *r0,
                                          const double *const *k2, const helm_mg_params *mg, void *stream,
@@ -20,13 +40,25 @@ extern "C" helm_status helm_create_batch(int nprob, const helm_grid *grids, cons
     if (nprob < 1 || !grids || !theta || !r0 || !k2 || !mg) return helm_fail(HELM_ERR_ARG, "bad batch arguments");
     helm_batch *b = new (std::nothrow) helm_batch();
     if (!b) return helm_fail(HELM_ERR_NOMEM, "host allocation failed");
-    b->stream = (cudaStream_t)stream;
+    b->user = (cudaStream_t)stream;
+    if (cudaEventCreateWithFlags(&b->start, cudaEventDisableTiming) != cudaSuccess) {
+        helm_destroy_batch(b);
+        return helm_fail(HELM_ERR_CUDA, "cudaEventCreate failed");
+    }
     for (int i = 0; i < nprob; i++) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            if (s) cudaStreamDestroy(s);
+            helm_destroy_batch(b);
+            return helm_fail(HELM_ERR_CUDA, "stream/event creation failed for problem %d", i);
+        }
+        b->streams.push_back(s);
+        b->done.push_back(e);
         helm_handle *h = nullptr;
-        const int d = grids[i].dim;
         const double *lo = r0 + 6 * (size_t)i, *hi = lo + 3;
-        helm_status st = helm_create(&grids[i], theta[i], lo, hi, k2[i], mg, stream, &h);
-        (void)d;
+        helm_status st = helm_create(&grids[i], theta[i], lo, hi, k2[i], mg, s, &h);
         if (st != HELM_OK) {
             helm_destroy_batch(b);
             return st;
@@ -40,21 +72,53 @@ extern "C" helm_status helm_create_batch(int nprob, const helm_grid *grids, cons
 extern "C" helm_status helm_solve_batch(helm_batch *b, const void *const *rhs, void *const *x, double tol, int restart,
                                         int maxit, helm_stats *stats) {
     if (!b || !rhs || !x) return helm_fail(HELM_ERR_ARG, "bad batch arguments");
+    if (!(tol > 0.0) || maxit < 1 || restart < 1 || restart > 64) return helm_fail(HELM_ERR_ARG, "bad tol/restart/maxit");
     const int n = (int)b->h.size();
+    for (int i = 0; i < n; i++)
+        if (!rhs[i] || !x[i] || rhs[i] == x[i] || ((uintptr_t)rhs[i] | (uintptr_t)x[i]) % 16)
+            return helm_fail(HELM_ERR_ARG, "rhs/x of problem %d invalid (null, overlapping or misaligned)", i);
+    // the problems' streams start after everything already queued on the caller's stream
+    if (cudaEventRecord(b->start, b->user) != cudaSuccess) return helm_fail(HELM_ERR_CUDA, "cudaEventRecord failed");
+    for (cudaStream_t s : b->streams)
+        if (cudaStreamWaitEvent(s, b->start, 0) != cudaSuccess) return helm_fail(HELM_ERR_CUDA, "cudaStreamWaitEvent failed");
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->h[a]->np > b->h[c]->np; });
-    helm_status worst = HELM_OK;
+    std::vector<FgmresRun> runs(n);
+    std::vector<helm_stats> local(n);
     for (int i : order) {
-        helm_status st = krylov_solve(b->h[i], HELM_FGMRES, rhs[i], x[i], tol, restart, maxit, stats ? &stats[i] : nullptr);
-        if (st == HELM_ERR_CUDA || st == HELM_ERR_ARG || st == HELM_ERR_NOMEM) return st;
-        if (st != HELM_OK && worst == HELM_OK) worst = st;
+        helm_stats *st = stats ? &stats[i] : &local[i];
+        if (stats && !stats[i].history) stats[i].history_len = 0;
+        helm_status s0 = fgmres_begin(b->h[i], runs[i], (const double2 *)rhs[i], (double2 *)x[i], tol, restart, maxit, st);
+        if (s0 != HELM_OK) return s0;
     }
-    return worst;
-}
-
-extern "C" void helm_destroy_batch(helm_batch *b) {
-    if (!b) return;
-    for (helm_handle *h : b->h) helm_destroy(h);
-    delete b;
+    int active = n;
+    while (active > 0) {
+        int progressed = 0;
+        active = 0;
+        for (int i : order) {
+            FgmresRun &r = runs[i];
+            if (r.phase == FgmresRun::DONE) continue;
+            const int it0 = r.it;
+            const FgmresRun::Phase p0 = r.phase;
+            const helm_status s0 = fgmres_advance(r, false);
+            if (s0 != HELM_OK) return s0;
+            if (r.it != it0 || r.phase != p0) progressed++;
+            if (r.phase != FgmresRun::DONE) active++;
+        }
+        if (active > 0 && progressed == 0) std::this_thread::yield();
+    }
+    helm_status worst = HELM_OK;
+    for (int i = 0; i < n; i++) {
+        const helm_stats &st = stats ? stats[i] : local[i];
+        if (stats) stats[i].status = runs[i].status;
+        if (runs[i].status != HELM_OK && worst == HELM_OK) worst = runs[i].status;
+        (void)st;
+        // the caller's stream continues after every problem's last work
+        if (cudaEventRecord(b->done[i], b->streams[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(b->user, b->done[i], 0) != cudaSuccess)
+            return helm_fail(HELM_ERR_CUDA, "joining problem %d to the caller's stream failed", i);
+    }
+    if (worst != HELM_OK) return helm_fail(worst, "%s in at least one batch problem", worst == HELM_ERR_NOCONV ? "no convergence" : "failure");
+    return HELM_OK;
 }

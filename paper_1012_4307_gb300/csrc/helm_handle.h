@@ -87,7 +87,16 @@ struct helm_handle {
     double *est_dev = nullptr;
     int *gs_flag = nullptr;   // DGKS decision of the current Arnoldi step (device)
     int *gs_count = nullptr;  // re-orthogonalisations in the current solve (device)
-    double *est_host = nullptr;  // pinned
+    double *est_host = nullptr;  // pinned: residual estimate of every FGMRES step
+    int est_host_len = 0;
+    double2 *fnorm_dev = nullptr;  // ||f|| of the current solve (device scalar)
+    // FGMRES steps: one event per step j, and a CUDA graph of step j captured on cap_stream
+    std::vector<cudaEvent_t> step_ev;
+    std::vector<cudaGraphExec_t> step_graph;
+    cudaStream_t cap_stream = nullptr;
+    bool graphs_ok = true;
+    bool capturing = false;
+    cudaEvent_t ev_fn = nullptr, ev_beta = nullptr;  // ||f|| and ||r0|| read-backs
     // Bi-CGSTAB workspace
     bool bicg_alloc = false;
     double2 *br = nullptr, *brh = nullptr, *bp = nullptr, *bv = nullptr, *bs = nullptr, *bt = nullptr;
@@ -121,4 +130,22 @@ struct ProfScope {
 
 helm_status helm_fail(helm_status st, const char *fmt, ...);
 void helm_free_krylov(helm_handle *h);
+
+// Resumable flexible-GMRES solve (krylov.cu): fgmres_begin queues the first work, each
+// fgmres_advance performs the phases whose event has fired (or waits, if block) until the
+// solve is DONE; the outcome is in status.
+struct FgmresRun {
+    enum Phase { WAIT_FN, START, WAIT_BETA, IN_CYCLE, DONE };
+    helm_handle *h = nullptr;
+    const double2 *f = nullptr;
+    double2 *x = nullptr;
+    double tol = 0, fn = 0, est = 1, rel = 1;
+    int m = 0, maxit = 0, it = 0, restarts = 0, jmax = 0, next = 0;
+    helm_stats *st = nullptr;
+    helm_status status = HELM_ERR_NOCONV;
+    Phase phase = DONE;
+};
+helm_status fgmres_begin(helm_handle *h, FgmresRun &r, const double2 *f, double2 *x, double tol, int m, int maxit,
+                         helm_stats *st);
+helm_status fgmres_advance(FgmresRun &r, bool block);
 template <typename R> cudaError_t precondition(helm_handle *h, const double2 *v, typename CT<R>::T *z);

@@ -160,8 +160,8 @@ template <typename CZ>
 cudaError_t launch_combine(size_t n, const CZ *Z, size_t ldz, int nz, const double2 *y, double2 *x, cudaStream_t s);
 
 // FGMRES small dense work on the device (one warp): rotations of column j, new rotation,
-// residual estimate (|g_{j+1}| / fnorm) written to est[0].
-cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, double fnorm,
+// residual estimate |g_{j+1}| / fnorm->x written to est[j].
+cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm,
                           double *est, cudaStream_t s);
 // y = H(0:k,0:k)^{-1} g(0:k)  (upper triangular back substitution)
 cudaError_t launch_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y, cudaStream_t s);

@@ -157,8 +157,9 @@ __global__ void k_combine(size_t n, const CZ *__restrict__ Z, size_t ldz, int nz
 // Complex Givens rotations G = [c s; -conj(s) c] (c real) on column j of the Hessenberg
 // matrix (column-major, leading dimension ldh); see Saad, Iterative Methods for Sparse Linear
 // Systems, Section 6.5.9 for the real case.
-__global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, double fnorm,
+__global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm_dev,
                          double *est) {
+    const double fnorm = fnorm_dev->x;
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double2 *col = H + (size_t)ldh * j;
     for (int i = 0; i < j; i++) {
@@ -188,7 +189,7 @@ __global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, do
     const double2 gj = g[j];
     g[j + 1] = cscale(cmul(make_double2(-s.x, s.y), gj), 1.0);
     g[j] = cscale(gj, c);
-    est[0] = hypot(g[j + 1].x, g[j + 1].y) / fnorm;
+    est[j] = hypot(g[j + 1].x, g[j + 1].y) / fnorm;
 }
 
 __global__ void k_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y) {
@@ -322,7 +323,7 @@ cudaError_t launch_combine(size_t n, const CZ *Z, size_t ldz, int nz, const doub
 template cudaError_t launch_combine<float2>(size_t, const float2 *, size_t, int, const double2 *, double2 *, cudaStream_t);
 template cudaError_t launch_combine<double2>(size_t, const double2 *, size_t, int, const double2 *, double2 *, cudaStream_t);
 
-cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, double fnorm,
+cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm,
                           double *est, cudaStream_t s) {
     k_givens<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g, fnorm, est);
     return cudaGetLastError();

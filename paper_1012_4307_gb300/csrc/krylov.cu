@@ -27,6 +27,12 @@
 static const double kDGKSEta = 0.70710678118654752;
 
 static void free_krylov(helm_handle *h) {
+    for (cudaGraphExec_t g : h->step_graph)
+        if (g) cudaGraphExecDestroy(g);
+    h->step_graph.clear();
+    for (cudaEvent_t e : h->step_ev)
+        if (e) cudaEventDestroy(e);
+    h->step_ev.clear();
     for (void *p : h->krylov_owned) cudaFree(p);
     h->krylov_owned.clear();
     h->V = nullptr; h->Z = nullptr; h->H = nullptr; h->g = h->sn = h->y = h->h2 = nullptr;
@@ -74,7 +80,7 @@ static helm_status ensure_ws(helm_handle *h, int m) {
     KA(&h->cs, (size_t)m);
     KA(&h->partials, (size_t)nblk * 65);
     KA(&h->scal, 32);
-    KA(&h->est_dev, 4);
+    KA(&h->est_dev, (size_t)m + 4);
     KA(&h->gs_flag, 4);
     h->gs_count = h->gs_flag + 1;
 #undef KA
@@ -83,7 +89,20 @@ static helm_status ensure_ws(helm_handle *h, int m) {
         return helm_fail(e == cudaErrorMemoryAllocation ? HELM_ERR_NOMEM : HELM_ERR_CUDA, "Krylov workspace: %s",
                          cudaGetErrorString(e));
     }
-    if (!h->est_host) CKR(cudaMallocHost((void **)&h->est_host, 8 * sizeof(double)));
+    if (h->est_host_len < m + 8) {
+        if (h->est_host) cudaFreeHost(h->est_host);
+        h->est_host = nullptr;
+        h->est_host_len = 0;
+        CKR(cudaMallocHost((void **)&h->est_host, (size_t)(m + 8) * sizeof(double)));
+        h->est_host_len = m + 8;
+    }
+    h->step_ev.assign((size_t)m, nullptr);
+    for (int j = 0; j < m; j++) CKR(cudaEventCreateWithFlags(&h->step_ev[j], cudaEventDisableTiming));
+    h->step_graph.assign((size_t)m, nullptr);
+    if (!h->ev_fn) CKR(cudaEventCreateWithFlags(&h->ev_fn, cudaEventDisableTiming));
+    if (!h->ev_beta) CKR(cudaEventCreateWithFlags(&h->ev_beta, cudaEventDisableTiming));
+    if (!h->cap_stream) CKR(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    h->fnorm_dev = h->scal + 24;
     h->m_alloc = m;
     h->z_prec = zp;
     return HELM_OK;
@@ -164,10 +183,19 @@ static cudaError_t precond_apply(helm_handle *h, const double2 *v, void *z, doub
     return launch_apply<double, double2>(h->A64, h->dim, (const double2 *)z, w, h->stream);
 }
 
-static helm_status fgmres(helm_handle *h, const double2 *f, double2 *x, double tol, int m, int maxit,
-                          helm_stats *st) {
-    helm_status s0 = ensure_ws(h, m);
-    if (s0 != HELM_OK) return s0;
+#define CKE(...)                          \
+    do {                                  \
+        cudaError_t e_ = (__VA_ARGS__);   \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
+// One FGMRES step j of a restart cycle (Saad, Algorithm 9.6): z_j = cycle(v_j); w = A z_j;
+// Gram-Schmidt of w against v_0..v_j into H[:, j] with the DGKS second pass; v_{j+1} = w / h;
+// Givens rotations; the relative residual estimate |g_{j+1}| / ||f|| goes to est[j] and is
+// copied to pinned host memory, then the step's event is recorded.  Stream work only (no host
+// synchronisation), so a step can be captured into a CUDA graph and replayed.  A step only
+// writes column j of H, v_{j+1}, z_j, the rotation j and g[j..j+1].
+static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
     const size_t np = h->np;
     const int ldh = m + 1;
     cudaStream_t s = h->stream;
@@ -184,129 +212,267 @@ static helm_status fgmres(helm_handle *h, const double2 *f, double2 *x, double t
         return df ? launch_update_norm_df(np, h->V, np, nv, hh, w, h->partials, gate, s)
                   : launch_update_norm(np, h->V, np, nv, hh, w, h->partials, gate, s);
     };
-    double2 hv[2];
-    CKR(dev_norm(h, f, h->scal));
-    helm_status rs = read_scalars(h, h->scal, sizeof(double2), hv);
-    if (rs != HELM_OK) return rs;
-    const double fn = hv[0].x;
-    if (!std::isfinite(fn)) return helm_fail(HELM_ERR_NONFINITE, "||rhs|| is not finite");
-    int it = 0, restarts = 0;
-    double est = 1.0, rel = 1.0;
-    helm_status status = HELM_ERR_NOCONV;
+    double2 *vj = h->V + (size_t)j * np, *w = h->V + (size_t)(j + 1) * np;
+    void *zj = (char *)h->Z + (size_t)j * np * zsz;
+    CKE(precond_apply(h, vj, zj, w));
+    double2 *hcol = h->H + (size_t)ldh * j;
+    const double nv = j + 1;
+    // Classical Gram-Schmidt with the DGKS re-orthogonalisation test:
+    //   h = V^H w (and ||w||^2 into H[j+1][j]);  w -= V h, ||w'||;
+    //   if ||w'|| < eta ||w||:  h' = V^H w, H[:, j] += h';  w -= V h', ||w''||.
+    // The second pass runs only when the device flag is set (gated kernels).
+    {
+        // FP64 flops only when the FP64 units do them (double-FP32 work is DRAM-bound)
+        ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (nv + 1), df ? 0.0 : np * (8.0 * nv + 4.0));
+        CKE(gs_dot(j + 1, w, nullptr));
+    }
+    {
+        ProfScope ps(h, HELM_K_SMALL, 0, 0);
+        CKE(launch_reduce(h->partials, gblk, j + 2, hcol, 0, nullptr, s));
+    }
+    {
+        ProfScope ps(h, HELM_K_UPDATE_NORM, np * 16.0 * (nv + 2), df ? 0.0 : np * (8.0 * nv + 4.0));
+        CKE(gs_update(j + 1, hcol, w, nullptr));
+    }
+    {
+        ProfScope ps(h, HELM_K_SMALL, 0, 0);
+        CKE(launch_reduce_decide(h->partials, ublk, hcol + j + 1, h->gs_flag, h->gs_count, kDGKSEta, s));
+    }
+    {
+        ProfScope ps(h, HELM_K_MDOT, 0, 0);  // gated: cost counted only if it runs (unknown here)
+        CKE(gs_dot(j + 1, w, h->gs_flag));
+    }
+    {
+        ProfScope ps(h, HELM_K_SMALL, 0, 0);
+        CKE(launch_reduce(h->partials, gblk, j + 1, h->h2, 0, h->gs_flag, s));
+        CKE(launch_reduce(h->partials, gblk, j + 1, hcol, 1, h->gs_flag, s));
+    }
+    {
+        ProfScope ps(h, HELM_K_UPDATE_NORM, 0, 0);
+        CKE(gs_update(j + 1, h->h2, w, h->gs_flag));
+    }
+    {
+        ProfScope ps(h, HELM_K_SMALL, 0, 0);
+        CKE(launch_reduce(h->partials, ublk, 1, hcol + j + 1, 2, h->gs_flag, s));
+    }
+    {
+        ProfScope ps(h, HELM_K_VECTOR, np * 32.0, np * 2.0);
+        CKE(launch_scale_inv(np, w, hcol + j + 1, w, s));
+    }
+    {
+        ProfScope ps(h, HELM_K_SMALL, 0, 0);
+        CKE(launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, s));
+    }
+    CKE(cudaMemcpyAsync(h->est_host + j, h->est_dev + j, sizeof(double), cudaMemcpyDeviceToHost, s));
+    // inside a capture the record must become an event node of the graph (external), so that
+    // the host can wait on the event after every replay
+    return h->capturing ? cudaEventRecordWithFlags(h->step_ev[j], s, cudaEventRecordExternal)
+                        : cudaEventRecord(h->step_ev[j], s);
+}
+
+// Runs step j: eagerly while launch timing is on, else by replaying a CUDA graph of the step,
+// captured on the handle's private stream the first time step j runs with this workspace.
+static cudaError_t run_step(helm_handle *h, int j, int m) {
+    if (h->prof.on || !h->graphs_ok) return fgmres_step(h, j, m);
+    if (!h->step_graph[j]) {
+        cudaStream_t keep = h->stream;
+        cudaGraph_t g = nullptr;
+        h->stream = h->cap_stream;
+        cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            h->capturing = true;
+            e = fgmres_step(h, j, m);
+            h->capturing = false;
+            cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+            if (e == cudaSuccess) e = e2;
+        }
+        h->stream = keep;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->step_graph[j], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {  // run this handle eagerly from now on
+            cudaGetLastError();
+            h->step_graph[j] = nullptr;
+            h->graphs_ok = false;
+            return fgmres_step(h, j, m);
+        }
+    }
+    return cudaGraphLaunch(h->step_graph[j], h->stream);
+}
+
+// ---------------------------------------------------------------------------------- FGMRES
+// The outer loop is a resumable state machine so that one host thread can drive many
+// problems at once (helm_solve_batch): every phase enqueues stream work and then waits for
+// one event, which fgmres_advance either blocks on or polls.
+//   WAIT_FN     ||f|| read back                      -> START
+//   START       r0 = f - A x, ||r0|| read back        -> WAIT_BETA
+//   WAIT_BETA   converged / capped / new cycle        -> DONE or IN_CYCLE
+//   IN_CYCLE    step j's estimate read back; step j+2 queued (one step of look-ahead);
+//               converged or cycle full: x += Z y     -> START
+// Pinned host slots: est_host[0..m) step estimates, [m+2] ||f||, [m+4] ||r0||.
+
+static bool event_ready(cudaEvent_t e, bool block, cudaError_t *err) {
+    *err = cudaSuccess;
+    if (block) {
+        *err = cudaEventSynchronize(e);
+        return *err == cudaSuccess;
+    }
+    const cudaError_t q = cudaEventQuery(e);
+    if (q == cudaSuccess) return true;
+    if (q != cudaErrorNotReady) *err = q;
+    return false;
+}
+
+helm_status fgmres_begin(helm_handle *h, FgmresRun &r, const double2 *f, double2 *x, double tol, int m, int maxit,
+                         helm_stats *st) {
+    helm_status s0 = ensure_ws(h, m);
+    if (s0 != HELM_OK) return s0;
+    r = FgmresRun{};
+    r.h = h; r.f = f; r.x = x; r.tol = tol; r.m = m; r.maxit = maxit; r.st = st;
+    r.status = HELM_ERR_NOCONV;
+    r.phase = FgmresRun::WAIT_FN;
+    cudaStream_t s = h->stream;
     CKR(cudaMemsetAsync(h->gs_flag, 0, 2 * sizeof(int), s));
-    if (fn == 0.0) {
-        CKR(cudaMemsetAsync(x, 0, np * sizeof(double2), s));
-        CKR(cudaStreamSynchronize(s));
-        if (st) { st->iterations = 0; st->restarts = 0; st->rel_res = 0; st->est_res = 0; st->status = HELM_OK; }
-        return HELM_OK;
-    }
-    for (;;) {
-        // r0 = f - A x -> V_0, beta = ||r0||
-        {
-            ProfScope ps(h, HELM_K_APPLY, interior_pts(h) * (16 + 16 + 8 + 16), apply_flops(h) + 2 * interior_pts(h));
-            CKR(launch_residual<double, double2>(h->A64, h->dim, f, x, h->V, s));
-        }
-        CKR(dev_norm(h, h->V, h->scal));
-        if ((rs = read_scalars(h, h->scal, sizeof(double2), hv)) != HELM_OK) return rs;
-        const double beta = hv[0].x;
-        rel = beta / fn;
-        if (!std::isfinite(beta)) { status = HELM_ERR_NONFINITE; break; }
-        if (rel <= tol) { status = HELM_OK; break; }
-        if (it >= maxit) { status = HELM_ERR_NOCONV; break; }
-        restarts++;
-        CKR(launch_scale_inv(np, h->V, h->scal, h->V, s));
-        CKR(cudaMemsetAsync(h->g, 0, (m + 1) * sizeof(double2), s));
-        CKR(cudaMemcpyAsync(h->g, h->scal, sizeof(double2), cudaMemcpyDeviceToDevice, s));
-        int jdone = 0;
-        bool nonfinite = false;
-        for (int j = 0; j < m && it < maxit; j++) {
-            double2 *vj = h->V + (size_t)j * np, *w = h->V + (size_t)(j + 1) * np;
-            void *zj = (char *)h->Z + (size_t)j * np * zsz;
-            CKR(precond_apply(h, vj, zj, w));
-            double2 *hcol = h->H + (size_t)ldh * j;
-            const double nv = j + 1;
-            // Classical Gram-Schmidt with the DGKS re-orthogonalisation test:
-            //   h = V^H w (and ||w||^2 into H[j+1][j]);  w -= V h, ||w'||;
-            //   if ||w'|| < eta ||w||:  h' = V^H w, H[:, j] += h';  w -= V h', ||w''||.
-            // The second pass runs only when the device flag is set (gated kernels).
-            {
-                // FP64 flops only when the FP64 units do them (double-FP32 work is DRAM-bound)
-                ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (nv + 1), df ? 0.0 : np * (8.0 * nv + 4.0));
-                CKR(gs_dot(j + 1, w, nullptr));
-            }
-            {
-                ProfScope ps(h, HELM_K_SMALL, 0, 0);
-                CKR(launch_reduce(h->partials, gblk, j + 2, hcol, 0, nullptr, s));
-            }
-            {
-                ProfScope ps(h, HELM_K_UPDATE_NORM, np * 16.0 * (nv + 2), df ? 0.0 : np * (8.0 * nv + 4.0));
-                CKR(gs_update(j + 1, hcol, w, nullptr));
-            }
-            {
-                ProfScope ps(h, HELM_K_SMALL, 0, 0);
-                CKR(launch_reduce_decide(h->partials, ublk, hcol + j + 1, h->gs_flag, h->gs_count, kDGKSEta, s));
-            }
-            {
-                ProfScope ps(h, HELM_K_MDOT, 0, 0);  // gated: cost counted only if it runs (unknown here)
-                CKR(gs_dot(j + 1, w, h->gs_flag));
-            }
-            {
-                ProfScope ps(h, HELM_K_SMALL, 0, 0);
-                CKR(launch_reduce(h->partials, gblk, j + 1, h->h2, 0, h->gs_flag, s));
-                CKR(launch_reduce(h->partials, gblk, j + 1, hcol, 1, h->gs_flag, s));
-            }
-            {
-                ProfScope ps(h, HELM_K_UPDATE_NORM, 0, 0);
-                CKR(gs_update(j + 1, h->h2, w, h->gs_flag));
-            }
-            {
-                ProfScope ps(h, HELM_K_SMALL, 0, 0);
-                CKR(launch_reduce(h->partials, ublk, 1, hcol + j + 1, 2, h->gs_flag, s));
-            }
-            {
-                ProfScope ps(h, HELM_K_VECTOR, np * 32.0, np * 2.0);
-                CKR(launch_scale_inv(np, w, hcol + j + 1, w, s));
-            }
-            {
-                ProfScope ps(h, HELM_K_SMALL, 0, 0);
-                CKR(launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, fn, h->est_dev, s));
-            }
-            double e1;
-            if ((rs = read_scalars(h, h->est_dev, sizeof(double), &e1)) != HELM_OK) return rs;
-            it++;
-            jdone = j + 1;
-            est = e1;
-            if (st && st->history && it - 1 < st->history_len) st->history[it - 1] = est;
-            if (!std::isfinite(est)) { nonfinite = true; break; }
-            if (est <= tol) break;
-        }
-        if (nonfinite) { status = HELM_ERR_NONFINITE; break; }
-        // x += Z y with y = H^{-1} g
-        {
-            ProfScope ps(h, HELM_K_SMALL, 0, 0);
-            CKR(launch_backsolve(h->H, ldh, jdone, h->g, h->y, s));
-        }
-        {
-            ProfScope ps(h, HELM_K_VECTOR, np * (32.0 + zsz * jdone), np * 8.0 * jdone);
-            if (h->z_prec == HELM_C64)
-                CKR(launch_combine<float2>(np, (const float2 *)h->Z, np, jdone, h->y, x, s));
-            else
-                CKR(launch_combine<double2>(np, (const double2 *)h->Z, np, jdone, h->y, x, s));
-        }
-    }
-    if (st) {
+    CKR(dev_norm(h, f, h->fnorm_dev));
+    CKR(cudaMemcpyAsync(h->est_host + m + 2, h->fnorm_dev, sizeof(double2), cudaMemcpyDeviceToHost, s));
+    CKR(cudaEventRecord(h->ev_fn, s));
+    return HELM_OK;
+}
+
+static helm_status fgmres_finish(FgmresRun &r) {
+    helm_handle *h = r.h;
+    r.phase = FgmresRun::DONE;
+    helm_status rs;
+    if (r.st) {
         int cnt[2] = {0, 0};
         if ((rs = read_scalars(h, h->gs_flag, 2 * sizeof(int), cnt)) != HELM_OK) return rs;
-        st->iterations = it;
-        st->restarts = restarts;
-        st->rel_res = rel;
-        st->est_res = est;
-        st->status = status;
-        st->reorthogonalizations = cnt[1];
+        r.st->iterations = r.it;
+        r.st->restarts = r.restarts;
+        r.st->rel_res = r.rel;
+        r.st->est_res = r.est;
+        r.st->status = r.status;
+        r.st->reorthogonalizations = cnt[1];
+    } else {
+        CKR(cudaStreamSynchronize(h->stream));
     }
-    if (status == HELM_ERR_NONFINITE) return helm_fail(status, "non-finite residual in FGMRES");
-    if (status == HELM_ERR_NOCONV) return helm_fail(status, "FGMRES: %d iterations, rel. residual %.3e > %.3e", it, rel, tol);
-    return status;
+    return HELM_OK;
+}
+
+// Performs every phase whose wait is satisfied (all of them when block is true).  Returns
+// HELM_OK while running or finished; r.phase == DONE and r.status hold the outcome.
+helm_status fgmres_advance(FgmresRun &r, bool block) {
+    helm_handle *h = r.h;
+    cudaStream_t s = h->stream;
+    const size_t np = h->np;
+    const int m = r.m, ldh = m + 1;
+    cudaError_t err;
+    for (;;) {
+        switch (r.phase) {
+        case FgmresRun::DONE:
+            return HELM_OK;
+        case FgmresRun::WAIT_FN: {
+            if (!event_ready(h->ev_fn, block, &err)) {
+                if (err != cudaSuccess) return helm_fail(HELM_ERR_CUDA, "event: %s", cudaGetErrorString(err));
+                return HELM_OK;
+            }
+            r.fn = h->est_host[m + 2];
+            if (!std::isfinite(r.fn)) {
+                r.status = HELM_ERR_NONFINITE;
+                return fgmres_finish(r);
+            }
+            if (r.fn == 0.0) {
+                CKR(cudaMemsetAsync(r.x, 0, np * sizeof(double2), s));
+                r.status = HELM_OK;
+                r.rel = r.est = 0.0;
+                return fgmres_finish(r);
+            }
+            r.phase = FgmresRun::START;
+            break;
+        }
+        case FgmresRun::START: {
+            // r0 = f - A x -> V_0, beta = ||r0|| (FP64 true residual)
+            {
+                ProfScope ps(h, HELM_K_APPLY, interior_pts(h) * (16 + 16 + 8 + 16),
+                             apply_flops(h) + 2 * interior_pts(h));
+                CKR(launch_residual<double, double2>(h->A64, h->dim, r.f, r.x, h->V, s));
+            }
+            CKR(dev_norm(h, h->V, h->scal));
+            CKR(cudaMemcpyAsync(h->est_host + m + 4, h->scal, sizeof(double2), cudaMemcpyDeviceToHost, s));
+            CKR(cudaEventRecord(h->ev_beta, s));
+            r.phase = FgmresRun::WAIT_BETA;
+            break;
+        }
+        case FgmresRun::WAIT_BETA: {
+            if (!event_ready(h->ev_beta, block, &err)) {
+                if (err != cudaSuccess) return helm_fail(HELM_ERR_CUDA, "event: %s", cudaGetErrorString(err));
+                return HELM_OK;
+            }
+            const double beta = h->est_host[m + 4];
+            r.rel = beta / r.fn;
+            if (!std::isfinite(beta)) { r.status = HELM_ERR_NONFINITE; return fgmres_finish(r); }
+            if (r.rel <= r.tol) { r.status = HELM_OK; return fgmres_finish(r); }
+            if (r.it >= r.maxit) { r.status = HELM_ERR_NOCONV; return fgmres_finish(r); }
+            r.restarts++;
+            CKR(launch_scale_inv(np, h->V, h->scal, h->V, s));
+            CKR(cudaMemsetAsync(h->g, 0, (m + 1) * sizeof(double2), s));
+            CKR(cudaMemcpyAsync(h->g, h->scal, sizeof(double2), cudaMemcpyDeviceToDevice, s));
+            r.jmax = std::min(m, r.maxit - r.it);
+            r.next = 0;
+            // One step of look-ahead: step j+1 is queued before the host waits for step j's
+            // estimate, so the GPU never idles on the host.  If step j converges, step j+1 has
+            // only written column j+1, v_{j+2}, z_{j+1} and g[j+1..j+2], none of which the back
+            // substitution over the first j+1 columns reads.
+            CKR(run_step(h, 0, m));
+            if (r.jmax > 1) CKR(run_step(h, 1, m));
+            r.phase = FgmresRun::IN_CYCLE;
+            break;
+        }
+        case FgmresRun::IN_CYCLE: {
+            const int j = r.next;
+            if (!event_ready(h->step_ev[j], block, &err)) {
+                if (err != cudaSuccess) return helm_fail(HELM_ERR_CUDA, "event: %s", cudaGetErrorString(err));
+                return HELM_OK;
+            }
+            r.est = h->est_host[j];
+            r.it++;
+            if (r.st && r.st->history && r.it - 1 < r.st->history_len) r.st->history[r.it - 1] = r.est;
+            if (!std::isfinite(r.est)) { r.status = HELM_ERR_NONFINITE; return fgmres_finish(r); }
+            const int jdone = j + 1;
+            if (r.est > r.tol && jdone < r.jmax) {
+                r.next = jdone;
+                if (jdone + 1 < r.jmax) CKR(run_step(h, jdone + 1, m));
+                break;
+            }
+            // x += Z y with y = H^{-1} g over the first jdone columns
+            {
+                ProfScope ps(h, HELM_K_SMALL, 0, 0);
+                CKR(launch_backsolve(h->H, ldh, jdone, h->g, h->y, s));
+            }
+            {
+                const size_t zsz = h->z_prec == HELM_C64 ? sizeof(float2) : sizeof(double2);
+                ProfScope ps(h, HELM_K_VECTOR, np * (32.0 + zsz * jdone), np * 8.0 * jdone);
+                if (h->z_prec == HELM_C64)
+                    CKR(launch_combine<float2>(np, (const float2 *)h->Z, np, jdone, h->y, r.x, s));
+                else
+                    CKR(launch_combine<double2>(np, (const double2 *)h->Z, np, jdone, h->y, r.x, s));
+            }
+            r.phase = FgmresRun::START;
+            break;
+        }
+        }
+    }
+}
+
+static helm_status fgmres(helm_handle *h, const double2 *f, double2 *x, double tol, int m, int maxit,
+                          helm_stats *st) {
+    FgmresRun r;
+    helm_status s0 = fgmres_begin(h, r, f, x, tol, m, maxit, st);
+    if (s0 != HELM_OK) return s0;
+    while (r.phase != FgmresRun::DONE)
+        if ((s0 = fgmres_advance(r, true)) != HELM_OK) return s0;
+    if (r.status == HELM_ERR_NONFINITE) return helm_fail(r.status, "non-finite residual in FGMRES");
+    if (r.status == HELM_ERR_NOCONV)
+        return helm_fail(r.status, "FGMRES: %d iterations, rel. residual %.3e > %.3e", r.it, r.rel, tol);
+    return r.status;
 }
 
 static helm_status bicgstab(helm_handle *h, const double2 *f, double2 *x, double tol, int maxit, helm_stats *st) {

@@ -148,6 +148,15 @@ helm_status helm_apply(helm_handle *h, helm_op which, helm_prec prec, const void
  * b and x must not overlap. */
 helm_status mg_vcycle(helm_handle *h, const void *b, void *x, helm_prec prec);
 
+/* The preconditioner call of the outer solvers: z = one cycle of Algorithm 1 for M z = v from
+ * a zero initial guess (Section 5, one cycle per preconditioner application).
+ *   v   DEVICE complex128 vector (the outer solver's working precision), unchanged.
+ *   z   DEVICE output of precision prec (HELM_C64: the cycle runs in complex64 on a copy of v
+ *       rounded to complex64); its interior is overwritten, its boundary untouched.
+ * v and z must not overlap.  Errors: HELM_ERR_ARG (null/misaligned pointers, a handle
+ * without a hierarchy). */
+helm_status mg_precondition(helm_handle *h, const void *v, void *z, helm_prec prec);
+
 /* Solves A x = rhs (A = Z, FP64) to ||rhs - A x|| <= tol ||rhs||, right-preconditioned by one
  * multigrid cycle on M in the precision mg->prec (a complex64 cycle inside FP64 FGMRES, or all
  * FP64).  FGMRES(restart) (Saad's flexible GMRES; classical Gram-Schmidt with a second pass

@@ -15,7 +15,7 @@ struct ff {
     float hi, lo;
 };
 
-__device__ __forceinline__ ff ff_split(double x) {
+static __device__ __noinline__ ff ff_split_slow(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
     const int e = (int)((h32 >> 20) & 0x7FFu);
@@ -26,6 +26,26 @@ __device__ __forceinline__ ff ff_split(double x) {
     r.hi = __int_as_float((int)(sign | ((unsigned)(e - 896) << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29)));
     if (e < 949) { r.lo = 0.f; return r; }
     const float scale = __int_as_float((e - 948) << 23);  // 2^(e - 1075)
+    const float lo = __fmul_rn(__uint2float_rn(l32 & 0x1FFFFFFFu), scale);
+    r.lo = __int_as_float(__float_as_int(lo) | (int)sign);
+    return r;
+}
+
+// Same split on the common path, in about a dozen integer instructions: with t the high word
+// minus the exponent rebias (float exponent field ef in bits 20..27 when in range),
+// hi = sign | ((t:l32) >> 29) (one funnel shift gives exponent and the 23 leading fraction
+// bits), lo = (the 29 remaining fraction bits) * 2^(ef - 179).  Magnitudes outside
+// [2^-74, 2^128) take the exact slow path above.
+__device__ __forceinline__ ff ff_split(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+    const unsigned sign = h32 & 0x80000000u;
+    const unsigned t = (h32 & 0x7FFFFFFFu) - (896u << 20);
+    const unsigned ef = t >> 20;
+    if (ef - 53u > 201u) return ff_split_slow(x);
+    ff r;
+    r.hi = __int_as_float((int)(__funnelshift_r(l32, t, 29) | sign));
+    const float scale = __int_as_float((int)((ef - 52u) << 23));
     const float lo = __fmul_rn(__uint2float_rn(l32 & 0x1FFFFFFFu), scale);
     r.lo = __int_as_float(__float_as_int(lo) | (int)sign);
     return r;

@@ -551,6 +551,30 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
                                  h->mg.smoother == HELM_SMOOTH_RB, (R)h->mg.omega, gf, gc, zero ? 1 : 0, h->stream);
     }
     const double es = sizeof(C), rs = sizeof(R), ni = interior(L, h->dim), nd = h->dim == 3 ? 8.0 : 4.0;
+    if constexpr (sizeof(R) == sizeof(float)) {
+        // temporal blocking: two pre-sweeps from zero + residual + FW in one launch (iterate to
+        // this level's t), the coarse correction, then correction + two post-sweeps in one
+        // launch (t -> u)
+        if (zero && h->mg.smoother == HELM_SMOOTH_JACOBI && h->mg.nu1 == 2 && h->mg.nu2 == 2 &&
+            fused_jacobi2_ok(L.n, h->dim)) {
+            LevelDev &Lc = h->lv[l + 1];
+            {
+                ProfScope ps(h, HELM_K_SMOOTH_FINE, ni * (es + rs + es + es / nd), 0);
+                CKE(launch_pre2_restrict(L.M32, (float)h->mg.omega, b, L.t32, Lc.b32, h->stream));
+            }
+            float2 *ec = Lc.u32;
+            if (l + 1 == last) {
+                CKE(coarse_solve<R>(h, Lc, Lc.b32, ec));
+            } else {
+                for (int i = 1; i <= gc; i++) {
+                    if (i == 1) CKE(cycle<R>(h, l + 1, Lc.b32, ec, true, gf, gc));
+                    else CKE(cycle<R>(h, l + 1, Lc.b32, ec, false, gc, gf));
+                }
+            }
+            ProfScope ps(h, HELM_K_SMOOTH_FINE, ni * (es + es / nd + es + rs + es), 0);
+            return launch_prolong_post2(L.M32, (float)h->mg.omega, b, L.t32, u, ec, h->stream);
+        }
+    }
     C *cur = u, *oth = LvBuf<R>::t(L);
     CKE(smooth<R>(h, l, h->mg.nu1, b, &cur, &oth, zero));
     LevelDev &Lc = h->lv[l + 1];
@@ -650,6 +674,23 @@ extern "C" helm_status mg_vcycle(helm_handle *h, const void *b, void *x, helm_pr
         CKR(cycle<double>(h, 0, (const double2 *)b, (double2 *)x, false, h->mg.gamma_f, h->mg.gamma_c));
     else if (prec == HELM_C64)
         CKR(cycle<float>(h, 0, (const float2 *)b, (float2 *)x, false, h->mg.gamma_f, h->mg.gamma_c));
+    else
+        return helm_fail(HELM_ERR_ARG, "bad precision");
+    return HELM_OK;
+}
+
+extern "C" helm_status mg_precondition(helm_handle *h, const void *v, void *z, helm_prec prec) {
+    if (!h) return helm_fail(HELM_ERR_ARG, "null handle");
+    if (h->mg.kind == HELM_PC_NONE) return helm_fail(HELM_ERR_ARG, "handle has no preconditioner hierarchy");
+    helm_status st;
+    if ((st = check_ptr(v, 16, "v")) != HELM_OK ||
+        (st = check_ptr(z, prec == HELM_C128 ? 16 : 8, "z")) != HELM_OK)
+        return st;
+    if (v == z) return helm_fail(HELM_ERR_ARG, "v and z must not overlap");
+    if (prec == HELM_C128)
+        CKR(precondition<double>(h, (const double2 *)v, (double2 *)z));
+    else if (prec == HELM_C64)
+        CKR(precondition<float>(h, (const double2 *)v, (float2 *)z));
     else
         return helm_fail(HELM_ERR_ARG, "bad precision");
     return HELM_OK;

@@ -97,6 +97,16 @@ cudaError_t launch_prolong_add(const int nf[3], int dim, const typename CT<R>::T
 template <typename R>
 cudaError_t launch_dense_solve(const int n[3], int dim, int nu, const typename CT<R>::T *minv,
                                const typename CT<R>::T *b, typename CT<R>::T *u, cudaStream_t s);
+// Temporal blocking (2D, complex64, omega-Jacobi with two pre- and two post-sweeps):
+//   pre:  u_out = two sweeps from u = 0, rc = FW(b - M u_out)   (one launch)
+//   post: u_out = two sweeps of (u_in + P ec)                     (one launch; u_in != u_out)
+// fused_jacobi2_ok tells whether a level's grid fits the tiling.
+bool fused_jacobi2_ok(const int n[3], int dim);
+cudaError_t launch_pre2_restrict(const DevOp<float> &op, float omega, const float2 *b, float2 *u_out, float2 *rc,
+                                 cudaStream_t s);
+cudaError_t launch_prolong_post2(const DevOp<float> &op, float omega, const float2 *b, const float2 *u_in,
+                                 float2 *u_out, const float2 *ec, cudaStream_t s);
+
 // Fused coarse tail: Algorithm 1 on levels 0..nlev-1 of the given arrays (level 0 = the
 // tail's top, nlev - 1 = the coarsest, solved with minv) inside one thread block.  zero: the
 // top-level iterate u[0] starts at 0 (not read).  Levels with at most TAIL_MAX_UNKNOWNS

@@ -63,8 +63,31 @@ __global__ void __launch_bounds__(NT) k_mdot_norm_df(size_t n, const double2 *__
     float sn = 0.f, cn = 0.f;
 #pragma unroll
     for (int t = 0; t < CH; t++) sr[t] = cr[t] = si[t] = ci[t] = 0.f;
-    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
-        const double2 wq = w[q];
+    // software pipeline: the next node's operands are loaded while this node is processed
+    const size_t stride = (size_t)gridDim.x * NT;
+    const double2 zero2 = make_double2(0.0, 0.0);
+    size_t q = blockIdx.x * (size_t)NT + threadIdx.x;
+    double2 wcur = zero2, vcur[CH];
+#pragma unroll
+    for (int t = 0; t < CH; t++) vcur[t] = zero2;
+    if (q < n) {
+        wcur = w[q];
+#pragma unroll
+        for (int t = 0; t < CH; t++)
+            if (t < cnt) vcur[t] = V[(size_t)(i0 + t) * ldv + q];
+    }
+    for (; q < n; q += stride) {
+        const size_t qn = q + stride;
+        double2 wnext = zero2, vnext[CH];
+#pragma unroll
+        for (int t = 0; t < CH; t++) vnext[t] = zero2;
+        if (qn < n) {
+            wnext = w[qn];
+#pragma unroll
+            for (int t = 0; t < CH; t++)
+                if (t < cnt) vnext[t] = V[(size_t)(i0 + t) * ldv + qn];
+        }
+        const double2 wq = wcur;
         const ff wx = ff_split(wq.x), wy = ff_split(wq.y);
         float p, e;
         if (first) {
@@ -76,7 +99,7 @@ __global__ void __launch_bounds__(NT) k_mdot_norm_df(size_t n, const double2 *__
 #pragma unroll
         for (int t = 0; t < CH; t++) {
             if (t < cnt) {
-                const double2 vq = V[(size_t)(i0 + t) * ldv + q];
+                const double2 vq = vcur[t];
                 const ff vx = ff_split(vq.x), vy = ff_split(vq.y);
                 // conj(v) w = (vx wx + vy wy) + i (vx wy - vy wx)
                 ff_two_prod(vx, wx, p, e);
@@ -89,6 +112,9 @@ __global__ void __launch_bounds__(NT) k_mdot_norm_df(size_t n, const double2 *__
                 ff_acc_prod(si[t], ci[t], -p, -e);
             }
         }
+        wcur = wnext;
+#pragma unroll
+        for (int t = 0; t < CH; t++) vcur[t] = vnext[t];
     }
     ff vals[2 * CH + 1];
 #pragma unroll
@@ -118,28 +144,47 @@ __global__ void __launch_bounds__(NT) k_update_norm_df(size_t n, const double2 *
     }
     __syncthreads();
     float sn = 0.f, cn = 0.f;
+    const double2 zero2 = make_double2(0.0, 0.0);
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const double2 wq = w[q];
         const ff wx = ff_split(wq.x), wy = ff_split(wq.y);
-        float sx = wx.hi, cx = wx.lo, sy = wy.hi, cy = wy.lo;
-#pragma unroll 4
-        for (int i = 0; i < nv; i++) {
-            const double2 vq = V[(size_t)i * ldv + q];
-            const ff vx = ff_split(vq.x), vy = ff_split(vq.y);
-            const float4 hh = hs[i];
-            const ff hx = {hh.x, hh.y}, hy = {hh.z, hh.w};
-            float p, e;
-            // w -= v h:  re -= vx hx - vy hy ;  im -= vx hy + vy hx
-            ff_two_prod(vx, hx, p, e);
-            ff_acc_prod(sx, cx, -p, -e);
-            ff_two_prod(vy, hy, p, e);
-            ff_acc_prod(sx, cx, p, e);
-            ff_two_prod(vx, hy, p, e);
-            ff_acc_prod(sy, cy, -p, -e);
-            ff_two_prod(vy, hx, p, e);
-            ff_acc_prod(sy, cy, -p, -e);
+        // four independent double-float accumulators per component (basis vectors i mod 4),
+        // started from w in the first, so the TwoSum chains overlap; the basis values of the
+        // next group of four are loaded while the current group is processed
+        float sx[4] = {wx.hi, 0.f, 0.f, 0.f}, cx[4] = {wx.lo, 0.f, 0.f, 0.f};
+        float sy[4] = {wy.hi, 0.f, 0.f, 0.f}, cy[4] = {wy.lo, 0.f, 0.f, 0.f};
+        double2 cur[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) cur[u] = u < nv ? V[(size_t)u * ldv + q] : zero2;
+        for (int i0 = 0; i0 < nv; i0 += 4) {
+            double2 nxt[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) nxt[u] = i0 + 4 + u < nv ? V[(size_t)(i0 + 4 + u) * ldv + q] : zero2;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (i0 + u < nv) {
+                    const ff vx = ff_split(cur[u].x), vy = ff_split(cur[u].y);
+                    const float4 hh = hs[i0 + u];
+                    const ff hx = {hh.x, hh.y}, hy = {hh.z, hh.w};
+                    float p, e;
+                    // w -= v h:  re -= vx hx - vy hy ;  im -= vx hy + vy hx
+                    ff_two_prod(vx, hx, p, e);
+                    ff_acc_prod(sx[u], cx[u], -p, -e);
+                    ff_two_prod(vy, hy, p, e);
+                    ff_acc_prod(sx[u], cx[u], p, e);
+                    ff_two_prod(vx, hy, p, e);
+                    ff_acc_prod(sy[u], cy[u], -p, -e);
+                    ff_two_prod(vy, hx, p, e);
+                    ff_acc_prod(sy[u], cy[u], -p, -e);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) cur[u] = nxt[u];
         }
-        const ff rx = ff_norm(sx, cx), ry = ff_norm(sy, cy);
+        const ff rx = ff_add(ff_add(ff_norm(sx[0], cx[0]), ff_norm(sx[1], cx[1])),
+                             ff_add(ff_norm(sx[2], cx[2]), ff_norm(sx[3], cx[3])));
+        const ff ry = ff_add(ff_add(ff_norm(sy[0], cy[0]), ff_norm(sy[1], cy[1])),
+                             ff_add(ff_norm(sy[2], cy[2]), ff_norm(sy[3], cy[3])));
         const double2 out = make_double2(ff_to_double(rx), ff_to_double(ry));
         w[q] = out;
         float p, e;

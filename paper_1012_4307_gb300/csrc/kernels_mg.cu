@@ -270,6 +270,195 @@ template <typename C> __global__ void k_zero(size_t n, C *x) {
         x[q] = mk(R(0), R(0));
 }
 
+// ------------------------------------------------------------------------------ temporal blocking
+// 2D omega-Jacobi with two sweeps, several sweeps per shared-memory tile.  Each block owns a
+// tile of TCX x TCY coarse nodes and the fine nodes x in [2 I0 - 1, 2 I0 + 2 TCX - 1) (same in
+// y), and works on the fine region R3 = [2 I0 - 3, 2 I0 + 2 TCX + 1], the owned nodes plus a
+// 3-node halo: two sweeps and a residual each consume one halo layer.  Nodes outside the
+// interior of the grid are held at zero (Dirichlet).  Same arithmetic as k_jacobi /
+// k_residual_restrict / k_prolong_add, in one launch per phase of the cycle instead of three.
+constexpr int TCX = 32, TCY = 8;
+constexpr int RW = 2 * TCX + 5, RH = 2 * TCY + 5;  // R3 extent
+
+struct TileCoef {
+    float2 x[RW][3], y[RH][3];
+};
+
+// Loads the operator's coefficient triples of the region's columns and rows.
+__device__ __forceinline__ void tile_coef(const OpView<float> &o, int X0, int Y0, TileCoef &tc) {
+    for (int q = threadIdx.x; q < RW * 3; q += blockDim.x) {
+        const int sx = q / 3, t = q % 3, x = X0 + sx;
+        tc.x[sx][t] = (x >= 1 && x <= o.nx - 2) ? o.cx[3 * x + t] : make_float2(0.f, 0.f);
+    }
+    for (int q = threadIdx.x; q < RH * 3; q += blockDim.x) {
+        const int sy = q / 3, t = q % 3, y = Y0 + sy;
+        tc.y[sy][t] = (y >= 1 && y <= o.ny - 2) ? o.cy[3 * y + t] : make_float2(0.f, 0.f);
+    }
+}
+
+// (M u)_s and the diagonal at region node (sx, sy) from shared-memory u (row stride RW).
+__device__ __forceinline__ float2 tile_stencil(const TileCoef &tc, const float2 (*u)[RW], int sx, int sy, float k2,
+                                               float2 bk, float2 c, float2 &d) {
+    float2 acc = cmul(tc.x[sx][0], u[sy][sx - 1]);
+    acc = cfma(tc.x[sx][2], u[sy][sx + 1], acc);
+    acc = cfma(tc.y[sy][0], u[sy - 1][sx], acc);
+    acc = cfma(tc.y[sy][2], u[sy + 1][sx], acc);
+    d = cadd(cadd(tc.x[sx][1], tc.y[sy][1]), cadd(cscale(bk, k2), c));
+    return cfma(d, u[sy][sx], acc);
+}
+
+struct PreTile {
+    TileCoef tc;
+    float2 b[RH][RW];
+    float k2[RH][RW];
+    float2 u1[RH][RW];  // first sweep, later the residual
+    float2 u2[RH][RW];
+};
+
+// u = two omega-Jacobi sweeps from u = 0 for M u = b, written on the owned fine nodes; then
+// rc = FW(b - M u) on the owned coarse nodes.
+__global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float omega, const float2 *__restrict__ b,
+                                                       float2 *__restrict__ u, float2 *__restrict__ rc, int ncx,
+                                                       int ncy) {
+    extern __shared__ __align__(16) unsigned char pre_smem[];
+    PreTile &T = *reinterpret_cast<PreTile *>(pre_smem);
+    const int I0 = 1 + blockIdx.x * TCX, J0 = 1 + blockIdx.y * TCY;
+    const int X0 = 2 * I0 - 3, Y0 = 2 * J0 - 3;
+    const int nx = o.nx, ny = o.ny;
+    tile_coef(o, X0, Y0, T.tc);
+    auto inside = [&](int x, int y) { return x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2; };
+    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
+        const int sx = q % RW, sy = q / RW, x = X0 + sx, y = Y0 + sy;
+        const bool in = inside(x, y);
+        const size_t p = (size_t)x + (size_t)nx * y;
+        T.b[sy][sx] = in ? b[p] : make_float2(0.f, 0.f);
+        T.k2[sy][sx] = in ? o.k2[p] : 0.f;
+    }
+    __syncthreads();
+    // sweep 1 from zero (pointwise): u1 = omega b / D
+    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
+        const int sx = q % RW, sy = q / RW;
+        float2 v = make_float2(0.f, 0.f);
+        if (inside(X0 + sx, Y0 + sy)) {
+            const float2 d = cadd(cadd(T.tc.x[sx][1], T.tc.y[sy][1]), cadd(cscale(o.bk, T.k2[sy][sx]), o.c));
+            v = cscale(cmul(T.b[sy][sx], cinv(d)), omega);
+        }
+        T.u1[sy][sx] = v;
+    }
+    __syncthreads();
+    // sweep 2 on R3 shrunk by one
+    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
+        const int sx = q % RW, sy = q / RW;
+        float2 v = make_float2(0.f, 0.f);
+        if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy)) {
+            float2 d;
+            const float2 mu = tile_stencil(T.tc, T.u1, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
+            v = cadd(T.u1[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv(d)), omega));
+        }
+        T.u2[sy][sx] = v;
+    }
+    __syncthreads();
+    // owned fine nodes of the smoothed iterate, and the residual on R3 shrunk by two
+    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
+        const int sx = q % RW, sy = q / RW, x = X0 + sx, y = Y0 + sy;
+        const bool in = inside(x, y);
+        if (in && sx >= 2 && sx < 2 + 2 * TCX && sy >= 2 && sy < 2 + 2 * TCY) u[(size_t)x + (size_t)nx * y] = T.u2[sy][sx];
+        float2 r = make_float2(0.f, 0.f);
+        if (in && sx >= 2 && sx < RW - 2 && sy >= 2 && sy < RH - 2) {
+            float2 d;
+            r = csub(T.b[sy][sx], tile_stencil(T.tc, T.u2, sx, sy, T.k2[sy][sx], o.bk, o.c, d));
+        }
+        T.u1[sy][sx] = r;
+    }
+    __syncthreads();
+    // full weighting on the owned coarse nodes: fine node 2I is region node 2(I - I0) + 3
+    for (int q = threadIdx.x; q < TCX * TCY; q += blockDim.x) {
+        const int cx = q % TCX, cy = q / TCX, I = I0 + cx, J = J0 + cy;
+        if (I > ncx - 2 || J > ncy - 2) continue;
+        const int sx = 2 * cx + 3, sy = 2 * cy + 3;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int dj = -1; dj <= 1; dj++)
+#pragma unroll
+            for (int di = -1; di <= 1; di++) {
+                const float wgt = (di == 0 ? 0.5f : 0.25f) * (dj == 0 ? 0.5f : 0.25f);
+                acc = cadd(acc, cscale(T.u1[sy + dj][sx + di], wgt));
+            }
+        rc[(size_t)I + (size_t)ncx * J] = acc;
+    }
+}
+
+struct PostTile {
+    TileCoef tc;
+    float2 b[RH][RW];
+    float k2[RH][RW];
+    float2 u3[RH][RW];
+    float2 u4[RH][RW];
+    float2 ec[TCY + 4][TCX + 4];
+};
+
+// u_out <- two omega-Jacobi sweeps of (u_in + P ec), on the owned fine nodes.  u_in and u_out
+// are different arrays: blocks read their halo of u_in while other blocks write u_out.
+__global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float omega, const float2 *__restrict__ b,
+                                                       const float2 *__restrict__ u_in, float2 *__restrict__ u,
+                                                       const float2 *__restrict__ ec, int ncx, int ncy) {
+    extern __shared__ __align__(16) unsigned char post_smem[];
+    PostTile &T = *reinterpret_cast<PostTile *>(post_smem);
+    const int I0 = 1 + blockIdx.x * TCX, J0 = 1 + blockIdx.y * TCY;
+    const int X0 = 2 * I0 - 3, Y0 = 2 * J0 - 3;
+    const int nx = o.nx, ny = o.ny;
+    // coarse nodes [I0 - 2, I0 + TCX + 1] cover floor/ceil(x / 2) for every region column
+    const int C0 = I0 - 2, D0 = J0 - 2;
+    tile_coef(o, X0, Y0, T.tc);
+    for (int q = threadIdx.x; q < (TCX + 4) * (TCY + 4); q += blockDim.x) {
+        const int cx = q % (TCX + 4), cy = q / (TCX + 4), I = C0 + cx, J = D0 + cy;
+        T.ec[cy][cx] = (I >= 0 && I < ncx && J >= 0 && J < ncy) ? ec[(size_t)I + (size_t)ncx * J] : make_float2(0.f, 0.f);
+    }
+    auto inside = [&](int x, int y) { return x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2; };
+    __syncthreads();
+    // u3 = u + P ec on the region
+    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
+        const int sx = q % RW, sy = q / RW, x = X0 + sx, y = Y0 + sy;
+        const bool in = inside(x, y);
+        const size_t p = (size_t)x + (size_t)nx * y;
+        T.b[sy][sx] = in ? b[p] : make_float2(0.f, 0.f);
+        T.k2[sy][sx] = in ? o.k2[p] : 0.f;
+        float2 v = make_float2(0.f, 0.f);
+        if (in) {
+            float2 acc = make_float2(0.f, 0.f);
+            int cnt = 0;
+            for (int jj = y >> 1; jj <= (y + 1) >> 1; jj++)
+                for (int ii = x >> 1; ii <= (x + 1) >> 1; ii++) {
+                    acc = cadd(acc, T.ec[jj - D0][ii - C0]);
+                    cnt++;
+                }
+            v = cadd(u_in[p], cscale(acc, 1.f / (float)cnt));
+        }
+        T.u3[sy][sx] = v;
+    }
+    __syncthreads();
+    // sweep 1 on R3 shrunk by one
+    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
+        const int sx = q % RW, sy = q / RW;
+        float2 v = make_float2(0.f, 0.f);
+        if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy)) {
+            float2 d;
+            const float2 mu = tile_stencil(T.tc, T.u3, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
+            v = cadd(T.u3[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv(d)), omega));
+        }
+        T.u4[sy][sx] = v;
+    }
+    __syncthreads();
+    // sweep 2 on the owned fine nodes
+    for (int q = threadIdx.x; q < 4 * TCX * TCY; q += blockDim.x) {
+        const int sx = 2 + q % (2 * TCX), sy = 2 + q / (2 * TCX), x = X0 + sx, y = Y0 + sy;
+        if (!inside(x, y)) continue;
+        float2 d;
+        const float2 mu = tile_stencil(T.tc, T.u4, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
+        u[(size_t)x + (size_t)nx * y] = cadd(T.u4[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv(d)), omega));
+    }
+}
+
 // ------------------------------------------------------------------------------ coarse tail
 // The coarse levels of a cycle (a few thousand unknowns or fewer) are launch- and latency-
 // bound when every sweep is its own grid.  k_mg_tail runs Algorithm 1 from the tail's top
@@ -621,6 +810,30 @@ template cudaError_t launch_mg_tail<float>(int, int, const DevOp<float> *, float
 template cudaError_t launch_mg_tail<double>(int, int, const DevOp<double> *, double2 *const *, double2 *const *,
                                             double2 *const *, const double2 *, int, int, int, int, double, int, int,
                                             int, cudaStream_t);
+
+bool fused_jacobi2_ok(const int n[3], int dim) {
+    if (dim != 2 || (n[0] - 1) % 2 || (n[1] - 1) % 2) return false;
+    const int ncx = (n[0] + 1) / 2, ncy = (n[1] + 1) / 2;
+    // the last tile's owned range must reach the last interior node: a tile row or column
+    // that ends exactly at the grid's edge would leave node n - 2 unowned
+    return ncx >= 3 && ncy >= 3 && (ncx - 2) % TCX != 0 && (ncy - 2) % TCY != 0;
+}
+
+cudaError_t launch_pre2_restrict(const DevOp<float> &op, float omega, const float2 *b, float2 *u_out, float2 *rc,
+                                 cudaStream_t s) {
+    const int ncx = (op.n[0] + 1) / 2, ncy = (op.n[1] + 1) / 2;
+    dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY));
+    k_pre2_restrict<<<g, 256, sizeof(PreTile), s>>>(view(op), omega, b, u_out, rc, ncx, ncy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_post2(const DevOp<float> &op, float omega, const float2 *b, const float2 *u_in,
+                                 float2 *u_out, const float2 *ec, cudaStream_t s) {
+    const int ncx = (op.n[0] + 1) / 2, ncy = (op.n[1] + 1) / 2;
+    dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY));
+    k_prolong_post2<<<g, 256, sizeof(PostTile), s>>>(view(op), omega, b, u_in, u_out, ec, ncx, ncy);
+    return cudaGetLastError();
+}
 
 template <typename CI, typename CO>
 cudaError_t launch_convert(size_t n, const CI *in, CO *out, cudaStream_t s) {

@@ -222,7 +222,7 @@ static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
     //   if ||w'|| < eta ||w||:  h' = V^H w, H[:, j] += h';  w -= V h', ||w''||.
     // The second pass runs only when the device flag is set (gated kernels).
     {
-        // FP64 flops only when the FP64 units do them (double-FP32 work is DRAM-bound)
+        // FP64 flops only when the FP64 units do them (double-FP32 work is not FP64-bound)
         ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (nv + 1), df ? 0.0 : np * (8.0 * nv + 4.0));
         CKE(gs_dot(j + 1, w, nullptr));
     }

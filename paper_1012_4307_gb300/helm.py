@@ -87,6 +87,7 @@ def load(build: bool = True):
             "helm_destroy": ([P], None),
             "helm_apply": ([P, I, I, P, P], I),
             "mg_vcycle": ([P, P, P, I], I),
+            "mg_precondition": ([P, P, P, I], I),
             "krylov_solve": ([P, I, P, P, D, I, I, P], I),
             "helm_solve_adjoint": ([P, P, P, D, I, I, P], I),
             "helm_grad_k2": ([P, P, P, P], I),
@@ -262,6 +263,17 @@ def mg_vcycle(h: Handle, b: torch.Tensor, x: torch.Tensor | None = None) -> torc
         x = torch.zeros_like(b)
     _check(load().mg_vcycle(h.ptr, C.c_void_p(_vec(b, h.np, "b")), C.c_void_p(_vec(x, h.np, "x", b.dtype)), prec))
     return x
+
+
+def mg_precondition(h: Handle, v: torch.Tensor, dtype: torch.dtype = torch.complex64) -> torch.Tensor:
+    """The outer solvers' preconditioner call: one cycle from zero for M z = v (v complex128,
+    z of the given dtype, complex64 = the cycle in complex64)."""
+    if v.dtype != torch.complex128:
+        raise TypeError("v must be complex128")
+    z = torch.zeros(v.shape, dtype=dtype, device=v.device)
+    prec = _prec_of(z)
+    _check(load().mg_precondition(h.ptr, C.c_void_p(_vec(v, h.np, "v")), C.c_void_p(_vec(z, h.np, "z", dtype)), prec))
+    return z
 
 
 @dataclass

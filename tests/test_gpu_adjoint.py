@@ -2,7 +2,10 @@
 513 x 513 ECS grid (k^2 = 2(E - V), E = 2, growth toward the boundary), u = A(k^2)^{-1} f with a
 complex64 V-cycle inside FP64 FGMRES.  torch.autograd through HelmholtzSolve (adjoint solve
 A^T lambda = conj(dL/du) by A^T = W A W^{-1}, then dL/dk^2 = Re(lambda u)) against central
-differences with step 1e-6 at 32 seeded points; dL/dV = -2 dL/dk^2."""
+differences of L along 8 seeded smooth directions (Gaussian bumps of k^2 in the real region):
+the directional derivative sum_p grad_p d_p must match (L(k^2 + eps d) - L(k^2 - eps d)) / 2 eps.
+A bump moves L far above the solver's residual floor, so the difference quotient is clean; a
+single-node perturbation of k^2 at this size would not be.  dL/dV = -2 dL/dk^2."""
 import numpy as np
 import pytest
 
@@ -28,7 +31,7 @@ def test_adjoint_gradient_513_central_differences(helm):
     n = P.n
     g = to_gpu(P.extra["probe"]).to(torch.complex128)
     f = to_gpu(P.f)
-    tol = 1e-13
+    tol = 2e-12  # the FP64 true residual bottoms out near 4e-13 at this size
 
     def factory(k2):
         Pk = W.Problem("adj", 2, n, k2.cpu().numpy(), P.f, coarsest_n=17)
@@ -41,20 +44,24 @@ def test_adjoint_gradient_513_central_differences(helm):
     grad = k2.grad.cpu().numpy()
     gmax = np.abs(grad).max()
     assert np.isfinite(gmax) and gmax > 0
-    # dL/dV = -2 dL/dk^2 since k^2 = 2 (E - V)
     rng = np.random.default_rng(2024)
-    idx = rng.integers(n // 4, 3 * n // 4, size=(32, 2))  # interior (real) region
-    errs = []
-    for (j, i) in idx:
+    centres = rng.integers(n // 4, 3 * n // 4, size=(8, 2))  # interior (real) region
+    yy, xx = np.mgrid[0:n, 0:n]
+    eps = 1e-4
+    fds, dds = [], []
+    for (cj, ci) in centres:
+        d = np.exp(-((xx - ci) ** 2 + (yy - cj) ** 2) / (2.0 * 6.0 ** 2))
         vals = []
         for sgn in (1, -1):
-            kk = P.k2.copy()
-            kk[j, i] += sgn * 1e-6
-            h = factory(torch.from_numpy(kk))
+            h = factory(torch.from_numpy(P.k2 + sgn * eps * d))
             uu, st = helm.krylov_solve(h, f, tol=tol, restart=30, maxit=6000)
+            assert st.status == helm.HELM_OK
             vals.append(float(((g * uu).sum().abs() ** 2).item()))
             h.close()
-        fd = (vals[0] - vals[1]) / 2e-6
-        errs.append(abs(fd - grad[j, i]))
-    # normwise relative gradient error (the difference quotient carries ~tol * L / step of noise)
-    assert max(errs) <= 1e-5 * gmax, (max(errs), gmax)
+        fds.append((vals[0] - vals[1]) / (2 * eps))
+        dds.append(float((grad * d).sum()))
+    fds, dds = np.array(fds), np.array(dds)
+    # normwise over the directions: central-difference truncation O(eps^2) and solve noise
+    # (relative residual 2e-12) both sit well below 1e-4 of the largest directional derivative
+    err = np.abs(fds - dds).max()
+    assert err <= 1e-4 * np.abs(dds).max(), (err, fds.tolist(), dds.tolist())

@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, metavar="COUNT",
                     help="batched workload instead: COUNT independent 2D problems with sizes drawn from "
                          "{129, 257, 513, 1025} and energies in [0.5, 4], solved together (helm_solve_batch)")
+    ap.add_argument("--no-tune", action="store_true", help="default kernel choices instead of the autotuned ones")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",
                     help="profiling case: build the same problem and run one solve capped at ITERS iterations, "
                          "nothing else (keeps the launch count small enough for ncu)")
@@ -213,6 +214,7 @@ def run_batch(args):
     mg = helm.MGParams(kind="csg", prec="c64", gs="df", coarsest_n=17)
     specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
     b = helm.helm_create_batch(specs, mg=mg)
+    tunings = None if args.no_tune else helm.helm_autotune_batch(b, "c64", cache=helm.default_tuning_cache())
     rhs = [torch.from_numpy(P.f).cuda() for P in probs]
     xs = [torch.zeros_like(r) for r in rhs]
     unknowns = sum(P.unknowns for P in probs)
@@ -243,6 +245,8 @@ def run_batch(args):
     seq_ms = 0.0
     for P, r in zip(probs, rhs):
         h = helm.helm_create(2, [P.n, P.n], torch.from_numpy(P.k2).cuda(), theta=P.theta, mg=mg)
+        if tunings:
+            helm.helm_set_tuning(h, tunings[helm.tuning_key(h, "c64")])
         x = torch.zeros_like(r)
         helm.krylov_solve(h, r, x, tol=args.tol, restart=30, maxit=5000)
         x.zero_()
@@ -258,7 +262,8 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": "batch of %d 2D well problems, sizes {129,257,513,1025}, E in [0.5,4]" % args.batch,
                        "unknowns": unknowns, "sizes": [P.n for P in probs],
-                       "l2": "256 MiB device write before every step, outside the timed events"},
+                       "l2": "256 MiB device write before every step, outside the timed events",
+                       "cycle_tuning": tunings},
             "iterations": [s.iterations for s in stats], "sequential_ms": seq_ms,
             "speedup_vs_sequential": seq_ms / ms, "clocks": clocks}
     print(json.dumps(line), flush=True)
@@ -294,6 +299,17 @@ def main():
     f = torch.from_numpy(P.f).cuda()
     x = torch.zeros_like(f)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    # kernel choices of the cycle: autotuned once per library build and grid (JSON cache beside
+    # the library); a profiling case only installs a stored choice, so that it launches no
+    # tuning runs of its own
+    tuning, tune_ms = None, None
+    if not args.no_tune:
+        if args.ncu_case:
+            tuning = helm.cached_tuning(h, "c64")
+            if tuning:
+                helm.helm_set_tuning(h, tuning)
+        else:
+            tuning, tune_ms = helm.helm_autotune(h, "c64", reps=10, cache=helm.default_tuning_cache())
 
     def solve(handle, out):
         out.zero_()
@@ -426,6 +442,7 @@ def main():
                                      "CSG theta_a=pi/14, V(2,2) omega-Jacobi 0.8, complex64 cycle",
                            "tol": args.tol, "ecs_theta": "pi/6", "kh_max": 0.6,
                            "l2": "256 MiB device write before every step, outside the timed events",
+                           "cycle_tuning": tuning, "tuned_ms_per_cycle": tune_ms,
                            "parallelism": "independent problem per rank" if world > 1 else "single GPU"},
                 "solve": {"iterations": st.iterations, "restarts": st.restarts, "rel_res": st.rel_res,
                           "ms_per_solve": ms_max, "reorthogonalizations": st.reorthogonalizations},

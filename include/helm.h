@@ -67,12 +67,15 @@ typedef enum { HELM_OP_A = 0, HELM_OP_M = 1 } helm_op;                   /* A = 
 typedef enum { HELM_FGMRES = 0, HELM_BICGSTAB = 1 } helm_krylov;
 typedef enum { HELM_SMOOTH_JACOBI = 0, HELM_SMOOTH_RB = 1 } helm_smoother;
 
-/* Arithmetic of the Gram-Schmidt inner products and updates in FGMRES.  The Krylov vectors
- * are FP64 in memory either way.
- *   FP64: IEEE FP64 fused multiply-adds (bound by GB300's FP64 units).
- *   DF:   each FP64 operand split exactly into two floats, error-free products and sums on
- *         the FP32 units, rounded to FP64 once per result (about 46 significant bits per
- *         product, 48 per sum; bound by DRAM). */
+/* Arithmetic of FGMRES's Arnoldi process (Gram-Schmidt inner products and updates, and the
+ * product A z when the cycle is complex64).  Hessenberg matrix, Givens rotations, the true
+ * residual and the solution update are IEEE FP64 either way.
+ *   FP64: Krylov vectors stored as FP64; IEEE FP64 fused multiply-adds (bound by GB300's FP64
+ *         units).
+ *   DF:   Krylov vectors stored as float pairs (re.hi, re.lo, im.hi, im.lo) per node, 16 bytes
+ *         like FP64, holding 47-48 significant bits; error-free products and sums on the FP32
+ *         units (about 46 significant bits per product, 48 per sum); inner products rounded
+ *         to FP64 once. */
 typedef enum { HELM_GS_FP64 = 0, HELM_GS_DF = 1 } helm_gs_arith;
 
 /* Uniform real grid: n[a] nodes on [lo[a], hi[a]] per axis, boundary nodes included
@@ -219,18 +222,24 @@ helm_status helm_levels(const helm_handle *h, int *nlev);
 helm_status helm_level_shape(const helm_handle *h, int level, int n[3]);
 
 /* ---- batched solves: many independent problems (energies, right-hand sides, grid sizes) ----
- * helm_create_batch builds one handle per problem (shared stream); helm_solve_batch runs every
- * problem's FGMRES with a complex64 multigrid preconditioner, the per-iteration work of all
- * problems fused into shared launches (one launch per kernel kind per level depth across the
- * batch), replayed from CUDA graphs.
+ * helm_create_batch builds one handle and one non-blocking CUDA stream per problem (all with
+ * the same mg parameters).  helm_solve_batch solves every problem with FGMRES as krylov_solve
+ * does, concurrently: one host thread advances the problems' resumable FGMRES loops (largest
+ * grid first), each problem's steps are CUDA graphs replayed on its own stream, and the
+ * problems' streams start after, and are joined back into, the stream given at creation.
+ * Each problem's result equals that of krylov_solve on its handle.
  *   grids, theta, r0 (2*dim per problem: lo then hi), k2 (device pointers): arrays of nprob.
- *   rhs, x: arrays of nprob DEVICE c128 pointers.  stats: nprob host structs (optional). */
+ *   rhs, x: arrays of nprob DEVICE c128 pointers.  stats: nprob host structs (optional).
+ * Returns the worst status over the problems. */
 helm_status helm_create_batch(int nprob, const helm_grid *grids, const double *theta, const double *r0,
                               const double *const *k2, const helm_mg_params *mg, void *stream,
                               helm_batch **out);
 helm_status helm_solve_batch(helm_batch *b, const void *const *rhs, void *const *x, double tol, int restart,
                              int maxit, helm_stats *stats);
 void helm_destroy_batch(helm_batch *b);
+/* The handle of problem i (owned by the batch, valid until helm_destroy_batch), e.g. for
+ * helm_set_tuning or a single solve.  Errors: HELM_ERR_ARG (null pointers, i out of range). */
+helm_status helm_batch_handle(helm_batch *b, int i, helm_handle **out);
 
 /* ---- launch timing (diagnostics; no counterpart in the paper, which reports cputime only) ----
  * helm_profile(h, 1) resets and enables per-launch timing: every kernel launch of the handle's
@@ -256,6 +265,50 @@ typedef enum {
 
 helm_status helm_profile(helm_handle *h, int enable);
 helm_status helm_profile_read(helm_handle *h, int ncls, int *launches, double *ms, double *bytes, double *flops);
+
+/* ---- cycle tuning (kernel choices; no counterpart in the paper) ----
+ * The arithmetic of Algorithm 1 is fixed by helm_mg_params; these choices only pick which
+ * kernels carry it out, and every choice gives the same cycle up to FP32 rounding order.
+ *   tail_levels    the coarsest levels (>= 2, or 0 for none) fused into one single-block
+ *                  shared-memory launch; -1 = as many as fit (at most 4 levels, each with at
+ *                  most 4096 unknowns, all in 200 KB of shared memory).  Values above what
+ *                  fits are clamped.
+ *   level_tile[l]  level l (0 = finest) of a 2D complex64 V(2,2) omega-Jacobi cycle runs its
+ *                  two pre-sweeps + residual + full weighting, and its prolongation + two
+ *                  post-sweeps, as two temporally blocked launches with tile shape
+ *                  HELM_TILE_* (coarse nodes per block), or as separate sweep / residual /
+ *                  transfer launches (HELM_TILE_NONE).  Ignored where it does not apply (other
+ *                  smoothers, complex128 cycles, 3D, levels inside the tail, grids the tile
+ *                  does not fit: those use the separate launches).
+ * Default: tail_levels = -1 and HELM_TILE_32x8 on every level. */
+#define HELM_MAX_LEVELS 16
+typedef enum {
+    HELM_TILE_NONE = -1,
+    HELM_TILE_32x8 = 0,
+    HELM_TILE_16x16 = 1,
+    HELM_TILE_16x8 = 2,
+    HELM_TILE_64x4 = 3,
+    HELM_TILE_COUNT = 4
+} helm_tile;
+typedef struct {
+    int tail_levels;
+    int level_tile[HELM_MAX_LEVELS];
+} helm_tuning;
+
+/* Sets / reads the handle's tuning (host struct).  Setting drops the handle's captured CUDA
+ * graphs (they are re-captured on next use).  Errors: HELM_ERR_ARG (null pointers, a tile
+ * index out of range, tail_levels < -1 or == 1). */
+helm_status helm_set_tuning(helm_handle *h, const helm_tuning *t);
+helm_status helm_get_tuning(const helm_handle *h, helm_tuning *t);
+
+/* Autotuner: times reps preconditioner applications (one cycle from zero on a fixed seeded
+ * complex128 vector, Section 5's preconditioner call) of precision prec for candidate
+ * tunings with CUDA events on the handle's stream, greedily level by level from the finest
+ * (each level's tile choice, then the tail depth), installs the fastest, and returns it in
+ * *best and its time per application (ms) in *best_ms (may be null).  Allocates two
+ * temporary vectors; synchronises the stream.  Errors: HELM_ERR_ARG (bad arguments, a handle
+ * without a hierarchy), HELM_ERR_NOMEM, HELM_ERR_CUDA. */
+helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, helm_tuning *best, double *best_ms);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *helm_last_error(void);

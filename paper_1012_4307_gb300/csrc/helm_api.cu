@@ -373,6 +373,8 @@ helm_status helm_create_impl(const helm_grid *grid, double theta, const double *
             (pass == 0 ? h->tail_top32 : h->tail_top64) = nlev - top >= 2 ? top : -1;
         }
     }
+    h->tune.tail_levels = -1;
+    for (int l = 0; l < HELM_MAX_LEVELS; l++) h->tune.level_tile[l] = HELM_TILE_32x8;
     CKC(cudaStreamSynchronize(s));
     *out = h;
     return HELM_OK;
@@ -525,6 +527,20 @@ static cudaError_t coarse_solve(helm_handle *h, LevelDev &L, const typename CT<R
 // u <- MG(l, M_l, b, u, nu1, nu2, C, gf, gc).  'zero' means u = 0 on entry (not read).
 // The result always ends in u.  Level l uses its own t buffer as the Jacobi partner; coarse
 // levels use their own b (restricted residual) and u (error) buffers.
+// First level of the fused tail under the handle's tuning (-1: no tail): the built (largest
+// fitting) tail shortened to tune.tail_levels levels.
+template <typename R> int tail_top(const helm_handle *h) {
+    const int built = sizeof(R) == sizeof(float) ? h->tail_top32 : h->tail_top64;
+    const int want = h->tune.tail_levels;
+    if (built < 0 || want == 0) return -1;
+    if (want < 0) return built;
+    const int last = (int)h->lv.size() - 1;
+    const int top = std::max(built, last - want + 1);
+    return last - top + 1 >= 2 ? top : -1;
+}
+template int tail_top<float>(const helm_handle *);
+template int tail_top<double>(const helm_handle *);
+
 template <typename R>
 static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, typename CT<R>::T *u, bool zero, int gf,
                          int gc) {
@@ -532,7 +548,7 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
     LevelDev &L = h->lv[l];
     const int last = (int)h->lv.size() - 1;
     if (l == last) return coarse_solve<R>(h, L, b, u);
-    if (l == (sizeof(R) == sizeof(float) ? h->tail_top32 : h->tail_top64)) {
+    if (l == tail_top<R>(h)) {
         // levels l..last in one fused single-block launch
         const int nt = last - l + 1;
         DevOp<R> ops[MAX_TAIL_LEVELS];
@@ -555,12 +571,13 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
         // temporal blocking: two pre-sweeps from zero + residual + FW in one launch (iterate to
         // this level's t), the coarse correction, then correction + two post-sweeps in one
         // launch (t -> u)
+        const int tile = l < HELM_MAX_LEVELS ? h->tune.level_tile[l] : (int)HELM_TILE_NONE;
         if (zero && h->mg.smoother == HELM_SMOOTH_JACOBI && h->mg.nu1 == 2 && h->mg.nu2 == 2 &&
-            fused_jacobi2_ok(L.n, h->dim)) {
+            fused_jacobi2_ok(L.n, h->dim, tile)) {
             LevelDev &Lc = h->lv[l + 1];
             {
                 ProfScope ps(h, HELM_K_SMOOTH_FINE, ni * (es + rs + es + es / nd), 0);
-                CKE(launch_pre2_restrict(L.M32, (float)h->mg.omega, b, L.t32, Lc.b32, h->stream));
+                CKE(launch_pre2_restrict(L.M32, tile, (float)h->mg.omega, b, L.t32, Lc.b32, h->stream));
             }
             float2 *ec = Lc.u32;
             if (l + 1 == last) {
@@ -572,7 +589,7 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
                 }
             }
             ProfScope ps(h, HELM_K_SMOOTH_FINE, ni * (es + es / nd + es + rs + es), 0);
-            return launch_prolong_post2(L.M32, (float)h->mg.omega, b, L.t32, u, ec, h->stream);
+            return launch_prolong_post2(L.M32, tile, (float)h->mg.omega, b, L.t32, u, ec, h->stream);
         }
     }
     C *cur = u, *oth = LvBuf<R>::t(L);
@@ -618,6 +635,24 @@ cudaError_t precondition(helm_handle *h, const double2 *v, typename CT<R>::T *z)
 }
 template cudaError_t precondition<float>(helm_handle *, const double2 *, float2 *);
 template cudaError_t precondition<double>(helm_handle *, const double2 *, double2 *);
+
+// The same with v a float-pair vector (the double-FP32 Krylov basis): v is converted into
+// level 0's right-hand side in precision R, then one cycle from zero.
+template <typename R>
+cudaError_t precondition_pair(helm_handle *h, const float4 *v, typename CT<R>::T *z) {
+    typedef typename CT<R>::T C;
+    const double es = sizeof(C);
+    C *dst = h->mg.kind == HELM_PC_NONE ? z : LvBuf<R>::b(h->lv[0]);
+    {
+        ProfScope ps(h, HELM_K_VECTOR, h->np * (16 + es), 0);
+        if constexpr (sizeof(R) == sizeof(float)) CKE(launch_pair_to_c64(h->np, v, dst, h->stream));
+        else CKE(launch_pair_to_c128(h->np, v, dst, h->stream));
+    }
+    if (h->mg.kind == HELM_PC_NONE) return cudaSuccess;
+    return cycle<R>(h, 0, dst, z, true, h->mg.gamma_f, h->mg.gamma_c);
+}
+template cudaError_t precondition_pair<float>(helm_handle *, const float4 *, float2 *);
+template cudaError_t precondition_pair<double>(helm_handle *, const float4 *, double2 *);
 
 static helm_status check_ptr(const void *p, size_t align, const char *name) {
     if (!p) return helm_fail(HELM_ERR_ARG, "%s is null", name);

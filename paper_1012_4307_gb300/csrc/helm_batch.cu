@@ -32,6 +32,13 @@ extern "C" void helm_destroy_batch(helm_batch *b) {
     delete b;
 }
 
+extern "C" helm_status helm_batch_handle(helm_batch *b, int i, helm_handle **out) {
+    if (!b || !out) return helm_fail(HELM_ERR_ARG, "null argument");
+    if (i < 0 || i >= (int)b->h.size()) return helm_fail(HELM_ERR_ARG, "problem index %d out of range", i);
+    *out = b->h[i];
+    return HELM_OK;
+}
+
 extern "C" helm_status helm_create_batch(int nprob, const helm_grid *grids, const double *theta, const double *r0,
                                          const double *const *k2, const helm_mg_params *mg, void *stream,
                                          helm_batch **out) {

@@ -69,7 +69,8 @@ struct helm_handle {
     std::vector<LevelDev> lv;
     // first level handled by the fused coarse-tail kernel, per precision (-1: none); chosen so
     // the tail's vectors fit in shared memory
-    int tail_top32 = -1, tail_top64 = -1;
+    int tail_top32 = -1, tail_top64 = -1;  // first level of the fused tail (-1: none), as built
+    helm_tuning tune{};                      // kernel choices (see helm_set_tuning)
     int nu_c = 0;
     double2 *minv64 = nullptr;
     float2 *minv32 = nullptr;
@@ -130,6 +131,8 @@ struct ProfScope {
 
 helm_status helm_fail(helm_status st, const char *fmt, ...);
 void helm_free_krylov(helm_handle *h);
+// Destroys the captured FGMRES step graphs (they are captured again on next use).
+void helm_drop_graphs(helm_handle *h);
 
 // Resumable flexible-GMRES solve (krylov.cu): fgmres_begin queues the first work, each
 // fgmres_advance performs the phases whose event has fired (or waits, if block) until the
@@ -149,3 +152,7 @@ helm_status fgmres_begin(helm_handle *h, FgmresRun &r, const double2 *f, double2
                          helm_stats *st);
 helm_status fgmres_advance(FgmresRun &r, bool block);
 template <typename R> cudaError_t precondition(helm_handle *h, const double2 *v, typename CT<R>::T *z);
+// v a float-pair vector (float4 (re.hi, re.lo, im.hi, im.lo) per node)
+template <typename R> cudaError_t precondition_pair(helm_handle *h, const float4 *v, typename CT<R>::T *z);
+// First level of the fused coarse tail of a precision-R cycle under the handle's tuning (-1: none).
+template <typename R> int tail_top(const helm_handle *h);

@@ -63,8 +63,8 @@ struct DevOpDF {
     const float4 *coef[3];
     const float2 *k2;
 };
-// y = A z in double-FP32 arithmetic, z complex64, y FP64 (interior written).
-cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, double2 *y, cudaStream_t s);
+// y = A z in double-FP32 arithmetic, z complex64, y a float-pair vector (interior written).
+cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, float4 *y, cudaStream_t s);
 
 // Kernel launch geometry helpers
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
@@ -100,11 +100,12 @@ cudaError_t launch_dense_solve(const int n[3], int dim, int nu, const typename C
 // Temporal blocking (2D, complex64, omega-Jacobi with two pre- and two post-sweeps):
 //   pre:  u_out = two sweeps from u = 0, rc = FW(b - M u_out)   (one launch)
 //   post: u_out = two sweeps of (u_in + P ec)                     (one launch; u_in != u_out)
-// fused_jacobi2_ok tells whether a level's grid fits the tiling.
-bool fused_jacobi2_ok(const int n[3], int dim);
-cudaError_t launch_pre2_restrict(const DevOp<float> &op, float omega, const float2 *b, float2 *u_out, float2 *rc,
-                                 cudaStream_t s);
-cudaError_t launch_prolong_post2(const DevOp<float> &op, float omega, const float2 *b, const float2 *u_in,
+// tile: index of the tile shape (HELM_TILE_* in helm.h).  fused_jacobi2_ok tells whether a
+// level's grid fits the tiling with that tile.
+bool fused_jacobi2_ok(const int n[3], int dim, int tile);
+cudaError_t launch_pre2_restrict(const DevOp<float> &op, int tile, float omega, const float2 *b, float2 *u_out,
+                                 float2 *rc, cudaStream_t s);
+cudaError_t launch_prolong_post2(const DevOp<float> &op, int tile, float omega, const float2 *b, const float2 *u_in,
                                  float2 *u_out, const float2 *ec, cudaStream_t s);
 
 // Fused coarse tail: Algorithm 1 on levels 0..nlev-1 of the given arrays (level 0 = the
@@ -115,10 +116,16 @@ constexpr int MAX_TAIL_LEVELS = 4;
 constexpr int TAIL_MAX_UNKNOWNS = 4096;
 constexpr size_t TAIL_SMEM_BYTES = 200 * 1024;  // b, u, t of every tail level in shared memory
 // Dynamic shared memory of the fused tail: the coarsest solve's compact right-hand side
-// (nu_c values, rounded up to even) and b, u, t of every tail level.
+// (nu_c values, rounded up to even), b, u, t of every tail level, then every tail level's
+// coefficient triples and k^2 (each k^2 array padded to 16 bytes).
 inline size_t mg_tail_smem_bytes_nodes(int dim, int nlev, const int (*n)[3], int nu_c, size_t es) {
     size_t bytes = (size_t)((nu_c + 1) & ~1) * es;
-    for (int l = 0; l < nlev; l++) bytes += 3 * es * (size_t)n[l][0] * n[l][1] * (dim == 3 ? n[l][2] : 1);
+    for (int l = 0; l < nlev; l++) {
+        const size_t np = (size_t)n[l][0] * n[l][1] * (dim == 3 ? n[l][2] : 1);
+        bytes += 3 * es * np;                                                  // b, u, t
+        bytes += 3 * es * (size_t)(n[l][0] + n[l][1] + (dim == 3 ? n[l][2] : 0));  // coefficients
+        bytes += (np * (es / 2) + 15) & ~(size_t)15;                           // k^2
+    }
     return bytes;
 }
 template <typename R>
@@ -152,14 +159,22 @@ cudaError_t launch_update_norm(size_t n, const double2 *V, size_t ldv, int nv, c
 // out[i] (mode 0: =, 1: +=, 2: (sqrt(re), 0)) = fixed-order sum of partials of vector i
 cudaError_t launch_reduce(const double2 *partials, int nblk, int nv, double2 *out, int mode, const int *gate,
                           cudaStream_t s);
-// Same two passes with FP64 vectors and double-FP32 arithmetic (kernels_gs_df.cu); their
-// partials use G = gs_df_nblocks(n) blocks per vector.
+// Same two passes in double-FP32 arithmetic on float-pair vectors (kernels_gs_df.cu): node q
+// of such a vector is the float4 (re.hi, re.lo, im.hi, im.lo).  Dot-pass partials use
+// G = gs_df_nblocks(n) blocks per vector, update-pass partials gs_df_update_nblocks(n).
 int gs_df_nblocks(size_t n);         // dot pass
 int gs_df_update_nblocks(size_t n);  // update pass
-cudaError_t launch_mdot_norm_df(size_t n, const double2 *V, size_t ldv, int nv, const double2 *w, double2 *partials,
-                                const int *gate, cudaStream_t s);
-cudaError_t launch_update_norm_df(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
-                                  double2 *partials, const int *gate, cudaStream_t s);
+cudaError_t launch_mdot_norm_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *w, double2 *partials,
+                                  const int *gate, cudaStream_t s);
+cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int nv, const double2 *h, float4 *w,
+                                    double2 *partials, const int *gate, cudaStream_t s);
+// w <- w / beta->x (float pairs)
+cudaError_t launch_scale_inv_pair(size_t n, float4 *w, const double2 *beta, cudaStream_t s);
+// in place: the double2 vector x becomes the float-pair vector x / beta->x (beta null: 1)
+cudaError_t launch_split_scale(size_t n, void *x, const double2 *beta, cudaStream_t s);
+// float pairs -> complex64 (hi + lo rounded) / complex128 (exact)
+cudaError_t launch_pair_to_c64(size_t n, const float4 *v, float2 *z, cudaStream_t s);
+cudaError_t launch_pair_to_c128(size_t n, const float4 *v, double2 *z, cudaStream_t s);
 // *hnorm: ||w||^2 in, ||w'|| out; *flag = (||w'|| < eta ||w||); *count += flag
 cudaError_t launch_reduce_decide(const double2 *partials, int nblk, double2 *hnorm, int *flag, int *count, double eta,
                                  cudaStream_t s);

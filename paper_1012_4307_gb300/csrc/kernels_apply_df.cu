@@ -1,10 +1,11 @@
 // w = A z for the Helmholtz operator A = L_h - k^2 (Section 3.2 stencil) with a complex64 z
-// (the output of the complex64 multigrid preconditioner) and an FP64 result, computed in
-// double-FP32 arithmetic on the FP32 units.  A's coefficients and k^2 are stored pre-split as
-// float pairs; z is exact in FP32, so each product a * z is error-free up to the dropped
-// a.lo * z rounding (2^-48 relative); the sum over the stencil is kept exactly with TwoSum and
-// rounded to FP64 once per node.  Same operands and result layout as k_apply<double, 2|3, float2>
-// in kernels_mg.cu, which does the same work with FP64 fused multiply-adds.
+// (the output of the complex64 multigrid preconditioner), computed in double-FP32 arithmetic
+// on the FP32 units.  A's coefficients and k^2 are stored pre-split as float pairs; z is exact
+// in FP32, so each product a * z is error-free up to the dropped a.lo * z rounding (2^-48
+// relative); the sum over the stencil is kept with TwoSum and written as a float-pair vector
+// (float4 (re.hi, re.lo, im.hi, im.lo) per node), the form the double-FP32 Gram-Schmidt reads.
+// Same operands as k_apply<double, 2|3, float2> in kernels_mg.cu, which does the work with FP64
+// fused multiply-adds.
 #include "helm_internal.h"
 #include "df_arith.h"
 
@@ -27,7 +28,7 @@ __device__ __forceinline__ void cmac(float4 a, float2 z, float &sr, float &cr, f
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(BX *BY) k_apply_A_df(DevOpDF o, const float2 *__restrict__ z, double2 *__restrict__ y) {
+__global__ void __launch_bounds__(BX *BY) k_apply_A_df(DevOpDF o, const float2 *__restrict__ z, float4 *__restrict__ y) {
     const int nx = o.n[0], ny = o.n[1], nz = o.n[2];
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -59,13 +60,14 @@ __global__ void __launch_bounds__(BX *BY) k_apply_A_df(DevOpDF o, const float2 *
         const float2 kk = o.k2[p];
         dr = ff_add(dr, ff{-kk.x, -kk.y});  // diagonal: sum of centre coefficients - k^2
         cmac(make_float4(dr.hi, dr.lo, di.hi, di.lo), z[p], sr, cr, si, ci);
-        y[p] = make_double2(ff_to_double(ff_norm(sr, cr)), ff_to_double(ff_norm(si, ci)));
+        const ff yr = ff_norm(sr, cr), yi = ff_norm(si, ci);
+        y[p] = make_float4(yr.hi, yr.lo, yi.hi, yi.lo);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, double2 *y, cudaStream_t s) {
+cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, float4 *y, cudaStream_t s) {
     dim3 g(cdiv(op.n[0] - 2, BX), cdiv(op.n[1] - 2, BY), dim == 3 ? cdiv(op.n[2] - 2, KCHUNK) : 1), b(BX, BY);
     if (dim == 3) k_apply_A_df<3><<<g, b, 0, s>>>(op, z, y);
     else k_apply_A_df<2><<<g, b, 0, s>>>(op, z, y);

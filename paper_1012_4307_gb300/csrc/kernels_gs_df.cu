@@ -1,18 +1,20 @@
-// Gram-Schmidt passes of flexible GMRES with FP64 vectors in memory but the arithmetic done
-// in double-FP32 ("double-float") on the FP32 units.
+// Gram-Schmidt passes of flexible GMRES in double-FP32 ("double-float") arithmetic on the FP32
+// units, with the Krylov basis stored as float pairs.
 //
 // Why: on GB300 the FP64 pipe retires about 2 fused multiply-adds per SM per clock, 64 times
 // fewer than FP32, so FP64 inner products over the Krylov basis are bound by FP64 issue, not
-// by DRAM.  Here every FP64 operand is split exactly into hi + lo floats with integer
-// instructions (hi = the leading 24 significand bits, lo = the next 29 rounded to 24, i.e. a
-// 47-bit representation), products are formed error-free with FMA (Dekker/Ogita-Rump-Oishi
-// TwoProduct), sums with Knuth's TwoSum, and the result is rounded back to FP64 once per
-// node (update) or once per block (dot).  Relative error of a product is about 2^-46 and of a
-// sum about 2^-48, i.e. FP64-class accuracy at FP32 throughput, which moves these kernels to
-// the DRAM bound.  Inputs below 2^-126 in magnitude are flushed (their contribution to
-// products with unit-norm basis vectors is far below the FP64 rounding of the result).
+// by DRAM.  Here each basis vector is a "float-pair vector": node q holds the float4
+// (re.hi, re.lo, im.hi, im.lo), an unevaluated sum hi + lo per component (16 bytes per node,
+// the size of a double2).  Vectors enter that form once (an FP64 vector is split exactly
+// with integer instructions: hi = the leading 24 significand bits, lo = the next 29 rounded
+// to 24, 47 bits kept) and the double-float kernels write it directly, so the inner loops do
+// no conversion: products are error-free with FMA (Dekker/Ogita-Rump-Oishi TwoProduct), sums
+// use Knuth's TwoSum, and inner products are rounded to FP64 once per block.  A product's
+// relative error is about 2^-46 and a sum's about 2^-48: FP64-class accuracy at FP32
+// throughput.  Magnitudes below 2^-126 are flushed (their contribution to products with
+// unit-norm basis vectors is far below the FP64 rounding of the results).
 //
-// Same contracts as k_mdot_norm / k_update_norm in kernels_krylov.cu (partials layout, gate).
+// Same partials layout and gate as k_mdot_norm / k_update_norm in kernels_krylov.cu.
 #include "helm_internal.h"
 #include "df_arith.h"
 
@@ -48,12 +50,15 @@ __device__ __forceinline__ void block_sum_ff(ff (&v)[NV], double *out) {
     }
 }
 
+__device__ __forceinline__ ff ff_re(float4 v) { return ff{v.x, v.y}; }
+__device__ __forceinline__ ff ff_im(float4 v) { return ff{v.z, v.w}; }
+
 // partials[i * G + b] = sum conj(V_i) w (i in this block row's chunk), chunk 0 also
-// partials[nv * G + b] = (||w||^2, 0).
+// partials[nv * G + b] = (||w||^2, 0).  V and w hold float pairs; no splitting is needed.
 template <int CH>
-__global__ void __launch_bounds__(NT) k_mdot_norm_df(size_t n, const double2 *__restrict__ V, size_t ldv, int nv,
-                                                     const double2 *__restrict__ w, double2 *__restrict__ partials,
-                                                     const int *__restrict__ gate) {
+__global__ void __launch_bounds__(NT) k_mdot_norm_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
+                                                       const float4 *__restrict__ w, double2 *__restrict__ partials,
+                                                       const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
     __shared__ double sums[2 * CH + 1];
     const int i0 = blockIdx.y * CH;
@@ -63,13 +68,13 @@ __global__ void __launch_bounds__(NT) k_mdot_norm_df(size_t n, const double2 *__
     float sn = 0.f, cn = 0.f;
 #pragma unroll
     for (int t = 0; t < CH; t++) sr[t] = cr[t] = si[t] = ci[t] = 0.f;
-    // software pipeline: the next node's operands are loaded while this node is processed
     const size_t stride = (size_t)gridDim.x * NT;
-    const double2 zero2 = make_double2(0.0, 0.0);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // software pipeline: the next node's operands are loaded while this node is processed
     size_t q = blockIdx.x * (size_t)NT + threadIdx.x;
-    double2 wcur = zero2, vcur[CH];
+    float4 wcur = zero4, vcur[CH];
 #pragma unroll
-    for (int t = 0; t < CH; t++) vcur[t] = zero2;
+    for (int t = 0; t < CH; t++) vcur[t] = zero4;
     if (q < n) {
         wcur = w[q];
 #pragma unroll
@@ -78,17 +83,16 @@ __global__ void __launch_bounds__(NT) k_mdot_norm_df(size_t n, const double2 *__
     }
     for (; q < n; q += stride) {
         const size_t qn = q + stride;
-        double2 wnext = zero2, vnext[CH];
+        float4 wnext = zero4, vnext[CH];
 #pragma unroll
-        for (int t = 0; t < CH; t++) vnext[t] = zero2;
+        for (int t = 0; t < CH; t++) vnext[t] = zero4;
         if (qn < n) {
             wnext = w[qn];
 #pragma unroll
             for (int t = 0; t < CH; t++)
                 if (t < cnt) vnext[t] = V[(size_t)(i0 + t) * ldv + qn];
         }
-        const double2 wq = wcur;
-        const ff wx = ff_split(wq.x), wy = ff_split(wq.y);
+        const ff wx = ff_re(wcur), wy = ff_im(wcur);
         float p, e;
         if (first) {
             ff_two_prod(wx, wx, p, e);
@@ -99,8 +103,7 @@ __global__ void __launch_bounds__(NT) k_mdot_norm_df(size_t n, const double2 *__
 #pragma unroll
         for (int t = 0; t < CH; t++) {
             if (t < cnt) {
-                const double2 vq = vcur[t];
-                const ff vx = ff_split(vq.x), vy = ff_split(vq.y);
+                const ff vx = ff_re(vcur[t]), vy = ff_im(vcur[t]);
                 // conj(v) w = (vx wx + vy wy) + i (vx wy - vy wx)
                 ff_two_prod(vx, wx, p, e);
                 ff_acc_prod(sr[t], cr[t], p, e);
@@ -131,10 +134,11 @@ __global__ void __launch_bounds__(NT) k_mdot_norm_df(size_t n, const double2 *__
     if (first && threadIdx.x == 0) partials[(size_t)nv * G + blockIdx.x] = make_double2(sums[2 * CH], 0.0);
 }
 
-// w -= sum_i V_i h_i in double-float, rounded to FP64 once per node; partials[b] = (||w||^2, 0).
-__global__ void __launch_bounds__(NT) k_update_norm_df(size_t n, const double2 *__restrict__ V, size_t ldv, int nv,
-                                                       const double2 *__restrict__ h, double2 *__restrict__ w,
-                                                       double2 *__restrict__ partials, const int *__restrict__ gate) {
+// w -= sum_i V_i h_i in double-float (h in FP64, split once per block), the result kept as a
+// float pair; partials[b] = (||w||^2, 0).
+__global__ void __launch_bounds__(NT) k_update_norm_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
+                                                         const double2 *__restrict__ h, float4 *__restrict__ w,
+                                                         double2 *__restrict__ partials, const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
     __shared__ float4 hs[64];  // (re.hi, re.lo, im.hi, im.lo)
     __shared__ double sums[1];
@@ -144,26 +148,25 @@ __global__ void __launch_bounds__(NT) k_update_norm_df(size_t n, const double2 *
     }
     __syncthreads();
     float sn = 0.f, cn = 0.f;
-    const double2 zero2 = make_double2(0.0, 0.0);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
-        const double2 wq = w[q];
-        const ff wx = ff_split(wq.x), wy = ff_split(wq.y);
+        const float4 wq = w[q];
         // four independent double-float accumulators per component (basis vectors i mod 4),
         // started from w in the first, so the TwoSum chains overlap; the basis values of the
         // next group of four are loaded while the current group is processed
-        float sx[4] = {wx.hi, 0.f, 0.f, 0.f}, cx[4] = {wx.lo, 0.f, 0.f, 0.f};
-        float sy[4] = {wy.hi, 0.f, 0.f, 0.f}, cy[4] = {wy.lo, 0.f, 0.f, 0.f};
-        double2 cur[4];
+        float sx[4] = {wq.x, 0.f, 0.f, 0.f}, cx[4] = {wq.y, 0.f, 0.f, 0.f};
+        float sy[4] = {wq.z, 0.f, 0.f, 0.f}, cy[4] = {wq.w, 0.f, 0.f, 0.f};
+        float4 cur[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) cur[u] = u < nv ? V[(size_t)u * ldv + q] : zero2;
+        for (int u = 0; u < 4; u++) cur[u] = u < nv ? V[(size_t)u * ldv + q] : zero4;
         for (int i0 = 0; i0 < nv; i0 += 4) {
-            double2 nxt[4];
+            float4 nxt[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) nxt[u] = i0 + 4 + u < nv ? V[(size_t)(i0 + 4 + u) * ldv + q] : zero2;
+            for (int u = 0; u < 4; u++) nxt[u] = i0 + 4 + u < nv ? V[(size_t)(i0 + 4 + u) * ldv + q] : zero4;
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 if (i0 + u < nv) {
-                    const ff vx = ff_split(cur[u].x), vy = ff_split(cur[u].y);
+                    const ff vx = ff_re(cur[u]), vy = ff_im(cur[u]);
                     const float4 hh = hs[i0 + u];
                     const ff hx = {hh.x, hh.y}, hy = {hh.z, hh.w};
                     float p, e;
@@ -185,13 +188,11 @@ __global__ void __launch_bounds__(NT) k_update_norm_df(size_t n, const double2 *
                              ff_add(ff_norm(sx[2], cx[2]), ff_norm(sx[3], cx[3])));
         const ff ry = ff_add(ff_add(ff_norm(sy[0], cy[0]), ff_norm(sy[1], cy[1])),
                              ff_add(ff_norm(sy[2], cy[2]), ff_norm(sy[3], cy[3])));
-        const double2 out = make_double2(ff_to_double(rx), ff_to_double(ry));
-        w[q] = out;
+        w[q] = make_float4(rx.hi, rx.lo, ry.hi, ry.lo);
         float p, e;
-        const ff ox = ff_split(out.x), oy = ff_split(out.y);
-        ff_two_prod(ox, ox, p, e);
+        ff_two_prod(rx, rx, p, e);
         ff_acc_prod(sn, cn, p, e);
-        ff_two_prod(oy, oy, p, e);
+        ff_two_prod(ry, ry, p, e);
         ff_acc_prod(sn, cn, p, e);
     }
     ff vals[1] = {ff_norm(sn, cn)};
@@ -199,28 +200,101 @@ __global__ void __launch_bounds__(NT) k_update_norm_df(size_t n, const double2 *
     if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(sums[0], 0.0);
 }
 
+// 1 / beta.x as a float pair, one FP64 division per block.
+__device__ __forceinline__ ff block_inv(const double2 *beta) {
+    __shared__ float2 rs;
+    if (threadIdx.x == 0) {
+        const ff r = ff_split(1.0 / beta->x);
+        rs = make_float2(r.hi, r.lo);
+    }
+    __syncthreads();
+    return ff{rs.x, rs.y};
+}
+
+// w <- w / beta.x in double-float (w a float pair vector).
+__global__ void __launch_bounds__(NT) k_scale_inv_pair(size_t n, float4 *__restrict__ w, const double2 *__restrict__ beta) {
+    const ff r = block_inv(beta);
+    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const float4 v = w[q];
+        float p, e;
+        ff_two_prod(ff_re(v), r, p, e);
+        const ff a = ff_norm(p, e);
+        ff_two_prod(ff_im(v), r, p, e);
+        const ff b = ff_norm(p, e);
+        w[q] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+}
+
+// In place: the FP64 vector x (as double2) becomes the float-pair vector x / beta.x.
+__global__ void __launch_bounds__(NT) k_split_scale(size_t n, void *x, const double2 *__restrict__ beta) {
+    __shared__ double rinv;
+    if (threadIdx.x == 0) rinv = beta ? 1.0 / beta->x : 1.0;
+    __syncthreads();
+    const double r = rinv;
+    double2 *in = (double2 *)x;
+    float4 *out = (float4 *)x;
+    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const double2 v = in[q];
+        const ff a = ff_split(v.x * r), b = ff_split(v.y * r);
+        out[q] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+}
+
+// Float pairs to complex64 (hi + lo rounded once) or to complex128 (exact).
+__global__ void __launch_bounds__(NT) k_pair_to_c64(size_t n, const float4 *__restrict__ v, float2 *__restrict__ z) {
+    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const float4 a = v[q];
+        z[q] = make_float2(__fadd_rn(a.x, a.y), __fadd_rn(a.z, a.w));
+    }
+}
+__global__ void __launch_bounds__(NT) k_pair_to_c128(size_t n, const float4 *__restrict__ v, double2 *__restrict__ z) {
+    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const float4 a = v[q];
+        z[q] = make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+    }
+}
+
 }  // namespace
 
 // Block counts (fixed for a given n).  The dot pass reduces 2 CH + 1 double-floats per block,
 // so it keeps about 8 nodes per thread; the update pass reduces one value and uses the same
 // grid as the FP64 kernels, which keeps enough warps resident to hide DRAM latency behind
-// the long split / TwoSum dependency chains.
+// the TwoSum dependency chains.
 int gs_df_nblocks(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>(cdiv(n, (size_t)NT * 8), (size_t)152 * 4)); }
 int gs_df_update_nblocks(size_t n) { return blas_nblocks(n); }
 
 constexpr int DF_CH = 4;  // basis vectors per block row of the dot pass
 
-cudaError_t launch_mdot_norm_df(size_t n, const double2 *V, size_t ldv, int nv, const double2 *w, double2 *partials,
-                                const int *gate, cudaStream_t s) {
+cudaError_t launch_mdot_norm_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *w, double2 *partials,
+                                  const int *gate, cudaStream_t s) {
     if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
     dim3 g(gs_df_nblocks(n), std::max(1, (nv + DF_CH - 1) / DF_CH));
-    k_mdot_norm_df<DF_CH><<<g, NT, 0, s>>>(n, V, ldv, nv, w, partials, gate);
+    k_mdot_norm_pair<DF_CH><<<g, NT, 0, s>>>(n, V, ldv, nv, w, partials, gate);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update_norm_df(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
-                                  double2 *partials, const int *gate, cudaStream_t s) {
+cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int nv, const double2 *h, float4 *w,
+                                    double2 *partials, const int *gate, cudaStream_t s) {
     if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
-    k_update_norm_df<<<gs_df_update_nblocks(n), NT, 0, s>>>(n, V, ldv, nv, h, w, partials, gate);
+    k_update_norm_pair<<<gs_df_update_nblocks(n), NT, 0, s>>>(n, V, ldv, nv, h, w, partials, gate);
+    return cudaGetLastError();
+}
+
+static unsigned pair_grid(size_t n) { return (unsigned)std::max<size_t>(1, std::min<size_t>(cdiv(n, NT), 152 * 8)); }
+
+cudaError_t launch_scale_inv_pair(size_t n, float4 *w, const double2 *beta, cudaStream_t s) {
+    k_scale_inv_pair<<<pair_grid(n), NT, 0, s>>>(n, w, beta);
+    return cudaGetLastError();
+}
+cudaError_t launch_split_scale(size_t n, void *x, const double2 *beta, cudaStream_t s) {
+    k_split_scale<<<pair_grid(n), NT, 0, s>>>(n, x, beta);
+    return cudaGetLastError();
+}
+cudaError_t launch_pair_to_c64(size_t n, const float4 *v, float2 *z, cudaStream_t s) {
+    k_pair_to_c64<<<pair_grid(n), NT, 0, s>>>(n, v, z);
+    return cudaGetLastError();
+}
+cudaError_t launch_pair_to_c128(size_t n, const float4 *v, double2 *z, cudaStream_t s) {
+    k_pair_to_c128<<<pair_grid(n), NT, 0, s>>>(n, v, z);
     return cudaGetLastError();
 }

@@ -35,25 +35,32 @@ template <typename R> __host__ OpView<R> view(const DevOp<R> &op) {
     return v;
 }
 
+// Coefficient load: the read-only global path (ld.global.nc) for operators in global memory,
+// a plain (generic) load when the operator's arrays may live in shared memory.
+template <bool GLOBAL, typename T> __device__ __forceinline__ T ldc(const T *p) {
+    if constexpr (GLOBAL) return __ldg(p);
+    else return *p;
+}
+
 // Off-diagonal part of the stencil at p (neighbours along x and y; z handled by callers that
-// march in k) and the diagonal entry.
-template <typename R, int DIM, typename CX>
+// march in k) and the diagonal entry.  GLOBAL: the coefficient arrays are in global memory.
+template <typename R, int DIM, typename CX, bool GLOBAL = true>
 __device__ __forceinline__ typename CT<R>::T stencil(const OpView<R> &o, const CX *__restrict__ x, size_t p,
                                                     int i, int j, int k, typename CT<R>::T xm_z,
                                                     typename CT<R>::T xc, typename CT<R>::T xp_z,
                                                     typename CT<R>::T &diag) {
     typedef typename CT<R>::T C;
     const size_t sy = (size_t)o.nx;
-    C cw = __ldg(&o.cx[3 * i]), cc = __ldg(&o.cx[3 * i + 1]), ce = __ldg(&o.cx[3 * i + 2]);
+    C cw = ldc<GLOBAL>(&o.cx[3 * i]), cc = ldc<GLOBAL>(&o.cx[3 * i + 1]), ce = ldc<GLOBAL>(&o.cx[3 * i + 2]);
     C acc = cmul(cw, to_c(x[p - 1], R()));
     acc = cfma(ce, to_c(x[p + 1], R()), acc);
     C d = cc;
-    cw = __ldg(&o.cy[3 * j]); cc = __ldg(&o.cy[3 * j + 1]); ce = __ldg(&o.cy[3 * j + 2]);
+    cw = ldc<GLOBAL>(&o.cy[3 * j]); cc = ldc<GLOBAL>(&o.cy[3 * j + 1]); ce = ldc<GLOBAL>(&o.cy[3 * j + 2]);
     acc = cfma(cw, to_c(x[p - sy], R()), acc);
     acc = cfma(ce, to_c(x[p + sy], R()), acc);
     d = cadd(d, cc);
     if (DIM == 3) {
-        cw = __ldg(&o.cz[3 * k]); cc = __ldg(&o.cz[3 * k + 1]); ce = __ldg(&o.cz[3 * k + 2]);
+        cw = ldc<GLOBAL>(&o.cz[3 * k]); cc = ldc<GLOBAL>(&o.cz[3 * k + 1]); ce = ldc<GLOBAL>(&o.cz[3 * k + 2]);
         acc = cfma(cw, xm_z, acc);
         acc = cfma(ce, xp_z, acc);
         d = cadd(d, cc);
@@ -64,7 +71,7 @@ __device__ __forceinline__ typename CT<R>::T stencil(const OpView<R> &o, const C
 }
 
 // (M x)_p for a point whose z neighbours are loaded here (used by the restriction kernel).
-template <typename R, int DIM, typename CX>
+template <typename R, int DIM, typename CX, bool GLOBAL = true>
 __device__ __forceinline__ typename CT<R>::T apply_point(const OpView<R> &o, const CX *__restrict__ x, int i, int j,
                                                         int k, typename CT<R>::T &diag) {
     typedef typename CT<R>::T C;
@@ -72,7 +79,7 @@ __device__ __forceinline__ typename CT<R>::T apply_point(const OpView<R> &o, con
     const size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k);
     C xm = mk(R(0), R(0)), xp = mk(R(0), R(0));
     if (DIM == 3) { xm = to_c(x[p - sz], R()); xp = to_c(x[p + sz], R()); }
-    return stencil<R, DIM>(o, x, p, i, j, k, xm, to_c(x[p], R()), xp, diag);
+    return stencil<R, DIM, CX, GLOBAL>(o, x, p, i, j, k, xm, to_c(x[p], R()), xp, diag);
 }
 
 // Thread preamble: interior (i, j) and the k range of this thread.
@@ -277,15 +284,32 @@ template <typename C> __global__ void k_zero(size_t n, C *x) {
 // 3-node halo: two sweeps and a residual each consume one halo layer.  Nodes outside the
 // interior of the grid are held at zero (Dirichlet).  Same arithmetic as k_jacobi /
 // k_residual_restrict / k_prolong_add, in one launch per phase of the cycle instead of three.
-constexpr int TCX = 32, TCY = 8;
-constexpr int RW = 2 * TCX + 5, RH = 2 * TCY + 5;  // R3 extent
-
-struct TileCoef {
-    float2 x[RW][3], y[RH][3];
+// The tile shape is a template parameter; the host picks one per level (tuning).
+template <int TCX, int TCY> struct Tile {
+    static constexpr int RW = 2 * TCX + 5, RH = 2 * TCY + 5;  // R3 extent
+    struct Coef {
+        float2 x[RW][3], y[RH][3];
+    };
+    struct Pre {
+        Coef tc;
+        float2 b[RH][RW];
+        float k2[RH][RW];
+        float2 u1[RH][RW];  // first sweep, later the residual
+        float2 u2[RH][RW];
+    };
+    struct Post {
+        Coef tc;
+        float2 b[RH][RW];
+        float k2[RH][RW];
+        float2 u3[RH][RW];
+        float2 u4[RH][RW];
+        float2 ec[TCY + 4][TCX + 4];
+    };
 };
 
 // Loads the operator's coefficient triples of the region's columns and rows.
-__device__ __forceinline__ void tile_coef(const OpView<float> &o, int X0, int Y0, TileCoef &tc) {
+template <int RW, int RH, typename TC>
+__device__ __forceinline__ void tile_coef(const OpView<float> &o, int X0, int Y0, TC &tc) {
     for (int q = threadIdx.x; q < RW * 3; q += blockDim.x) {
         const int sx = q / 3, t = q % 3, x = X0 + sx;
         tc.x[sx][t] = (x >= 1 && x <= o.nx - 2) ? o.cx[3 * x + t] : make_float2(0.f, 0.f);
@@ -297,7 +321,8 @@ __device__ __forceinline__ void tile_coef(const OpView<float> &o, int X0, int Y0
 }
 
 // (M u)_s and the diagonal at region node (sx, sy) from shared-memory u (row stride RW).
-__device__ __forceinline__ float2 tile_stencil(const TileCoef &tc, const float2 (*u)[RW], int sx, int sy, float k2,
+template <int RW, typename TC>
+__device__ __forceinline__ float2 tile_stencil(const TC &tc, const float2 (*u)[RW], int sx, int sy, float k2,
                                                float2 bk, float2 c, float2 &d) {
     float2 acc = cmul(tc.x[sx][0], u[sy][sx - 1]);
     acc = cfma(tc.x[sx][2], u[sy][sx + 1], acc);
@@ -307,25 +332,20 @@ __device__ __forceinline__ float2 tile_stencil(const TileCoef &tc, const float2 
     return cfma(d, u[sy][sx], acc);
 }
 
-struct PreTile {
-    TileCoef tc;
-    float2 b[RH][RW];
-    float k2[RH][RW];
-    float2 u1[RH][RW];  // first sweep, later the residual
-    float2 u2[RH][RW];
-};
-
 // u = two omega-Jacobi sweeps from u = 0 for M u = b, written on the owned fine nodes; then
 // rc = FW(b - M u) on the owned coarse nodes.
+template <int TCX, int TCY>
 __global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float omega, const float2 *__restrict__ b,
                                                        float2 *__restrict__ u, float2 *__restrict__ rc, int ncx,
                                                        int ncy) {
+    typedef Tile<TCX, TCY> TL;
+    constexpr int RW = TL::RW, RH = TL::RH;
     extern __shared__ __align__(16) unsigned char pre_smem[];
-    PreTile &T = *reinterpret_cast<PreTile *>(pre_smem);
+    typename TL::Pre &T = *reinterpret_cast<typename TL::Pre *>(pre_smem);
     const int I0 = 1 + blockIdx.x * TCX, J0 = 1 + blockIdx.y * TCY;
     const int X0 = 2 * I0 - 3, Y0 = 2 * J0 - 3;
     const int nx = o.nx, ny = o.ny;
-    tile_coef(o, X0, Y0, T.tc);
+    tile_coef<RW, RH>(o, X0, Y0, T.tc);
     auto inside = [&](int x, int y) { return x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2; };
     for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
         const int sx = q % RW, sy = q / RW, x = X0 + sx, y = Y0 + sy;
@@ -352,7 +372,7 @@ __global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float om
         float2 v = make_float2(0.f, 0.f);
         if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy)) {
             float2 d;
-            const float2 mu = tile_stencil(T.tc, T.u1, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
+            const float2 mu = tile_stencil<RW>(T.tc, T.u1, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
             v = cadd(T.u1[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv(d)), omega));
         }
         T.u2[sy][sx] = v;
@@ -366,7 +386,7 @@ __global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float om
         float2 r = make_float2(0.f, 0.f);
         if (in && sx >= 2 && sx < RW - 2 && sy >= 2 && sy < RH - 2) {
             float2 d;
-            r = csub(T.b[sy][sx], tile_stencil(T.tc, T.u2, sx, sy, T.k2[sy][sx], o.bk, o.c, d));
+            r = csub(T.b[sy][sx], tile_stencil<RW>(T.tc, T.u2, sx, sy, T.k2[sy][sx], o.bk, o.c, d));
         }
         T.u1[sy][sx] = r;
     }
@@ -388,28 +408,22 @@ __global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float om
     }
 }
 
-struct PostTile {
-    TileCoef tc;
-    float2 b[RH][RW];
-    float k2[RH][RW];
-    float2 u3[RH][RW];
-    float2 u4[RH][RW];
-    float2 ec[TCY + 4][TCX + 4];
-};
-
 // u_out <- two omega-Jacobi sweeps of (u_in + P ec), on the owned fine nodes.  u_in and u_out
 // are different arrays: blocks read their halo of u_in while other blocks write u_out.
+template <int TCX, int TCY>
 __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float omega, const float2 *__restrict__ b,
                                                        const float2 *__restrict__ u_in, float2 *__restrict__ u,
                                                        const float2 *__restrict__ ec, int ncx, int ncy) {
+    typedef Tile<TCX, TCY> TL;
+    constexpr int RW = TL::RW, RH = TL::RH;
     extern __shared__ __align__(16) unsigned char post_smem[];
-    PostTile &T = *reinterpret_cast<PostTile *>(post_smem);
+    typename TL::Post &T = *reinterpret_cast<typename TL::Post *>(post_smem);
     const int I0 = 1 + blockIdx.x * TCX, J0 = 1 + blockIdx.y * TCY;
     const int X0 = 2 * I0 - 3, Y0 = 2 * J0 - 3;
     const int nx = o.nx, ny = o.ny;
     // coarse nodes [I0 - 2, I0 + TCX + 1] cover floor/ceil(x / 2) for every region column
     const int C0 = I0 - 2, D0 = J0 - 2;
-    tile_coef(o, X0, Y0, T.tc);
+    tile_coef<RW, RH>(o, X0, Y0, T.tc);
     for (int q = threadIdx.x; q < (TCX + 4) * (TCY + 4); q += blockDim.x) {
         const int cx = q % (TCX + 4), cy = q / (TCX + 4), I = C0 + cx, J = D0 + cy;
         T.ec[cy][cx] = (I >= 0 && I < ncx && J >= 0 && J < ncy) ? ec[(size_t)I + (size_t)ncx * J] : make_float2(0.f, 0.f);
@@ -443,7 +457,7 @@ __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float om
         float2 v = make_float2(0.f, 0.f);
         if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy)) {
             float2 d;
-            const float2 mu = tile_stencil(T.tc, T.u3, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
+            const float2 mu = tile_stencil<RW>(T.tc, T.u3, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
             v = cadd(T.u3[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv(d)), omega));
         }
         T.u4[sy][sx] = v;
@@ -454,7 +468,7 @@ __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float om
         const int sx = 2 + q % (2 * TCX), sy = 2 + q / (2 * TCX), x = X0 + sx, y = Y0 + sy;
         if (!inside(x, y)) continue;
         float2 d;
-        const float2 mu = tile_stencil(T.tc, T.u4, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
+        const float2 mu = tile_stencil<RW>(T.tc, T.u4, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
         u[(size_t)x + (size_t)nx * y] = cadd(T.u4[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv(d)), omega));
     }
 }
@@ -517,7 +531,7 @@ __device__ void tail_smooth(const TailArgs<R> &A, const TailLevelDev<R> &L, int 
                     if (DIM == 3) { xm = u[p - sz]; xp = u[p + sz]; }
                     const C xc = u[p];
                     C d;
-                    const C mu = stencil<R, DIM>(o, u, p, i, j, k, xm, xc, xp, d);
+                    const C mu = stencil<R, DIM, C, false>(o, u, p, i, j, k, xm, xc, xp, d);
                     u[p] = cadd(xc, cscale(cmul(csub(L.b[p], mu), cinv(d)), A.omega));
                 });
                 __syncthreads();
@@ -537,7 +551,7 @@ __device__ void tail_smooth(const TailArgs<R> &A, const TailLevelDev<R> &L, int 
                     if (DIM == 3) { xm = u[p - sz]; xp = u[p + sz]; }
                     const C xc = u[p];
                     C d;
-                    const C mu = stencil<R, DIM>(o, u, p, i, j, k, xm, xc, xp, d);
+                    const C mu = stencil<R, DIM, C, false>(o, u, p, i, j, k, xm, xc, xp, d);
                     un[p] = cadd(xc, cscale(cmul(csub(L.b[p], mu), cinv(d)), A.omega));
                 }
             });
@@ -608,7 +622,7 @@ __device__ void tail_cycle(const TailArgs<R> &A, bool zero, int gf, int gc) {
                         const int i = 2 * I + di;
                         const size_t p = (size_t)i + (size_t)L.o.nx * ((size_t)j + (size_t)L.o.ny * k);
                         C d;
-                        const C mu = apply_point<R, DIM>(L.o, uc, i, j, k, d);
+                        const C mu = apply_point<R, DIM, C, false>(L.o, uc, i, j, k, d);
                         acc = cadd(acc, cscale(csub(L.b[p], mu), w));
                     }
                 }
@@ -656,7 +670,8 @@ __device__ void tail_cycle(const TailArgs<R> &A, bool zero, int gf, int gc) {
     }  // LVL + 1 < MAX_TAIL_LEVELS
 }
 
-// Dynamic shared memory: [compact coarsest rhs | per level: b, u, t].  A.lv[0].b / u hold the
+// Dynamic shared memory: [compact coarsest rhs | per level: b, u, t | per level: coefficient
+// triples, k^2].  A.lv[0].b / u hold the
 // caller's global top-level vectors; zero != 0 means the top-level iterate starts at 0.
 template <typename R, int DIM>
 __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs<R> A, int gf, int gc, int zero) {
@@ -674,6 +689,16 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs<R> A, int gf,
             S.lv[l].u = p; p += np;
             S.lv[l].t = p; p += np;
         }
+        // then every level's coefficient triples and k^2 (read by every phase)
+        for (int l = 0; l < A.nlev; l++) {
+            OpView<R> &o = S.lv[l].o;
+            const size_t np = (size_t)o.nx * o.ny * (DIM == 3 ? o.nz : 1);
+            o.cx = p; p += 3 * o.nx;
+            o.cy = p; p += 3 * o.ny;
+            if (DIM == 3) { o.cz = p; p += 3 * o.nz; }
+            o.k2 = (const R *)p;
+            p = (C *)((unsigned char *)p + ((np * sizeof(R) + 15) & ~(size_t)15));
+        }
     }
     __syncthreads();
     {
@@ -681,6 +706,15 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs<R> A, int gf,
         const C *end = last.t + (size_t)last.o.nx * last.o.ny * (DIM == 3 ? last.o.nz : 1);
         const size_t total = end - (const C *)tail_smem;
         for (size_t q = threadIdx.x; q < total; q += blockDim.x) ((C *)tail_smem)[q] = mk(R(0), R(0));
+        for (int l = 0; l < S.nlev; l++) {
+            const OpView<R> &g = A.lv[l].o, &o = S.lv[l].o;
+            const size_t np = (size_t)g.nx * g.ny * (DIM == 3 ? g.nz : 1);
+            for (int q = threadIdx.x; q < 3 * g.nx; q += blockDim.x) const_cast<C *>(o.cx)[q] = g.cx[q];
+            for (int q = threadIdx.x; q < 3 * g.ny; q += blockDim.x) const_cast<C *>(o.cy)[q] = g.cy[q];
+            if (DIM == 3)
+                for (int q = threadIdx.x; q < 3 * g.nz; q += blockDim.x) const_cast<C *>(o.cz)[q] = g.cz[q];
+            for (size_t q = threadIdx.x; q < np; q += blockDim.x) const_cast<R *>(o.k2)[q] = g.k2[q];
+        }
     }
     __syncthreads();
     const OpView<R> &o = A.lv[0].o;
@@ -811,28 +845,70 @@ template cudaError_t launch_mg_tail<double>(int, int, const DevOp<double> *, dou
                                             double2 *const *, const double2 *, int, int, int, int, double, int, int,
                                             int, cudaStream_t);
 
-bool fused_jacobi2_ok(const int n[3], int dim) {
+// Tile shapes (coarse nodes per block) of the temporally blocked kernels, by tile index.
+static const int kTiles[HELM_TILE_COUNT][2] = {{32, 8}, {16, 16}, {16, 8}, {64, 4}};
+
+bool fused_jacobi2_ok(const int n[3], int dim, int tile) {
+    if (tile < 0 || tile >= HELM_TILE_COUNT) return false;
     if (dim != 2 || (n[0] - 1) % 2 || (n[1] - 1) % 2) return false;
     const int ncx = (n[0] + 1) / 2, ncy = (n[1] + 1) / 2;
     // the last tile's owned range must reach the last interior node: a tile row or column
     // that ends exactly at the grid's edge would leave node n - 2 unowned
-    return ncx >= 3 && ncy >= 3 && (ncx - 2) % TCX != 0 && (ncy - 2) % TCY != 0;
+    return ncx >= 3 && ncy >= 3 && (ncx - 2) % kTiles[tile][0] != 0 && (ncy - 2) % kTiles[tile][1] != 0;
 }
 
-cudaError_t launch_pre2_restrict(const DevOp<float> &op, float omega, const float2 *b, float2 *u_out, float2 *rc,
-                                 cudaStream_t s) {
+template <int TCX, int TCY>
+static cudaError_t pre2_t(const DevOp<float> &op, float omega, const float2 *b, float2 *u_out, float2 *rc,
+                          cudaStream_t s) {
     const int ncx = (op.n[0] + 1) / 2, ncy = (op.n[1] + 1) / 2;
+    constexpr size_t smem = sizeof(typename Tile<TCX, TCY>::Pre);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_pre2_restrict<TCX, TCY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY));
-    k_pre2_restrict<<<g, 256, sizeof(PreTile), s>>>(view(op), omega, b, u_out, rc, ncx, ncy);
+    k_pre2_restrict<TCX, TCY><<<g, 256, smem, s>>>(view(op), omega, b, u_out, rc, ncx, ncy);
     return cudaGetLastError();
 }
 
-cudaError_t launch_prolong_post2(const DevOp<float> &op, float omega, const float2 *b, const float2 *u_in,
+template <int TCX, int TCY>
+static cudaError_t post2_t(const DevOp<float> &op, float omega, const float2 *b, const float2 *u_in, float2 *u_out,
+                           const float2 *ec, cudaStream_t s) {
+    const int ncx = (op.n[0] + 1) / 2, ncy = (op.n[1] + 1) / 2;
+    constexpr size_t smem = sizeof(typename Tile<TCX, TCY>::Post);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_prolong_post2<TCX, TCY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY));
+    k_prolong_post2<TCX, TCY><<<g, 256, smem, s>>>(view(op), omega, b, u_in, u_out, ec, ncx, ncy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre2_restrict(const DevOp<float> &op, int tile, float omega, const float2 *b, float2 *u_out,
+                                 float2 *rc, cudaStream_t s) {
+    if (!fused_jacobi2_ok(op.n, 2, tile)) return cudaErrorInvalidValue;
+    switch (tile) {
+    case 0: return pre2_t<32, 8>(op, omega, b, u_out, rc, s);
+    case 1: return pre2_t<16, 16>(op, omega, b, u_out, rc, s);
+    case 2: return pre2_t<16, 8>(op, omega, b, u_out, rc, s);
+    default: return pre2_t<64, 4>(op, omega, b, u_out, rc, s);
+    }
+}
+
+cudaError_t launch_prolong_post2(const DevOp<float> &op, int tile, float omega, const float2 *b, const float2 *u_in,
                                  float2 *u_out, const float2 *ec, cudaStream_t s) {
-    const int ncx = (op.n[0] + 1) / 2, ncy = (op.n[1] + 1) / 2;
-    dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY));
-    k_prolong_post2<<<g, 256, sizeof(PostTile), s>>>(view(op), omega, b, u_in, u_out, ec, ncx, ncy);
-    return cudaGetLastError();
+    if (!fused_jacobi2_ok(op.n, 2, tile)) return cudaErrorInvalidValue;
+    switch (tile) {
+    case 0: return post2_t<32, 8>(op, omega, b, u_in, u_out, ec, s);
+    case 1: return post2_t<16, 16>(op, omega, b, u_in, u_out, ec, s);
+    case 2: return post2_t<16, 8>(op, omega, b, u_in, u_out, ec, s);
+    default: return post2_t<64, 4>(op, omega, b, u_in, u_out, ec, s);
+    }
 }
 
 template <typename CI, typename CO>

@@ -46,6 +46,14 @@ static void free_krylov(helm_handle *h) {
 
 void helm_free_krylov(helm_handle *h) { free_krylov(h); }
 
+void helm_drop_graphs(helm_handle *h) {
+    for (cudaGraphExec_t &g : h->step_graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
 template <typename T> static cudaError_t kalloc(helm_handle *h, T **p, size_t count) {
     *p = nullptr;
     cudaError_t e = cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
@@ -163,6 +171,28 @@ static double interior_pts(const helm_handle *h) {
 }
 static double apply_flops(const helm_handle *h) { return interior_pts(h) * (h->dim == 3 ? 68.0 : 48.0); }
 
+// Double-FP32 Arnoldi (gs_arith = DF): the basis vectors are float-pair vectors.
+// z = precondition(v) in the workspace precision; w = A z as a float-pair vector.
+static cudaError_t precond_apply_pair(helm_handle *h, const float4 *v, void *z, float4 *w) {
+    cudaError_t e;
+    const double ni = interior_pts(h);
+    if (h->z_prec == HELM_C64) {
+        e = precondition_pair<float>(h, v, (float2 *)z);
+        if (e != cudaSuccess) return e;
+        ProfScope ps(h, HELM_K_APPLY, ni * (8 + 8 + 16), 0);
+        return launch_apply_A_df(h->Adf, h->dim, (const float2 *)z, w, h->stream);
+    }
+    e = precondition_pair<double>(h, v, (double2 *)z);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps(h, HELM_K_APPLY, ni * (16 + 8 + 16), apply_flops(h));
+        e = launch_apply<double, double2>(h->A64, h->dim, (const double2 *)z, (double2 *)w, h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    ProfScope ps(h, HELM_K_VECTOR, h->np * 32.0, 0);
+    return launch_split_scale(h->np, w, nullptr, h->stream);
+}
+
 // z = precondition(v) in the workspace precision; w = A z (FP64)
 static cudaError_t precond_apply(helm_handle *h, const double2 *v, void *z, double2 *w) {
     cudaError_t e;
@@ -170,10 +200,6 @@ static cudaError_t precond_apply(helm_handle *h, const double2 *v, void *z, doub
     if (h->z_prec == HELM_C64) {
         e = precondition<float>(h, v, (float2 *)z);
         if (e != cudaSuccess) return e;
-        if (h->mg.gs_arith == HELM_GS_DF) {  // Arnoldi products in double-FP32: the apply too
-            ProfScope ps(h, HELM_K_APPLY, ni * (8 + 8 + 16), 0);
-            return launch_apply_A_df(h->Adf, h->dim, (const float2 *)z, w, h->stream);
-        }
         ProfScope ps(h, HELM_K_APPLY, ni * (8 + 8 + 16), apply_flops(h));
         return launch_apply<double, float2>(h->A64, h->dim, (const float2 *)z, w, h->stream);
     }
@@ -200,21 +226,24 @@ static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
     const int ldh = m + 1;
     cudaStream_t s = h->stream;
     const size_t zsz = h->z_prec == HELM_C64 ? sizeof(float2) : sizeof(double2);
-    // Gram-Schmidt passes in FP64 or double-FP32 arithmetic (same partials layout)
+    // Gram-Schmidt passes in FP64, or in double-FP32 on float-pair basis vectors (same
+    // partials layout)
     const bool df = h->mg.gs_arith == HELM_GS_DF;
     const int gblk = df ? gs_df_nblocks(np) : blas_nblocks(np);         // blocks of the dot pass
     const int ublk = df ? gs_df_update_nblocks(np) : blas_nblocks(np);  // blocks of the update pass
-    auto gs_dot = [&](int nv, const double2 *w, const int *gate) {
-        return df ? launch_mdot_norm_df(np, h->V, np, nv, w, h->partials, gate, s)
+    const float4 *V4 = (const float4 *)h->V;
+    auto gs_dot = [&](int nv, double2 *w, const int *gate) {
+        return df ? launch_mdot_norm_pair(np, V4, np, nv, (const float4 *)w, h->partials, gate, s)
                   : launch_mdot_norm(np, h->V, np, nv, w, h->partials, gate, s);
     };
     auto gs_update = [&](int nv, const double2 *hh, double2 *w, const int *gate) {
-        return df ? launch_update_norm_df(np, h->V, np, nv, hh, w, h->partials, gate, s)
+        return df ? launch_update_norm_pair(np, V4, np, nv, hh, (float4 *)w, h->partials, gate, s)
                   : launch_update_norm(np, h->V, np, nv, hh, w, h->partials, gate, s);
     };
     double2 *vj = h->V + (size_t)j * np, *w = h->V + (size_t)(j + 1) * np;
     void *zj = (char *)h->Z + (size_t)j * np * zsz;
-    CKE(precond_apply(h, vj, zj, w));
+    if (df) CKE(precond_apply_pair(h, (const float4 *)vj, zj, (float4 *)w));
+    else CKE(precond_apply(h, vj, zj, w));
     double2 *hcol = h->H + (size_t)ldh * j;
     const double nv = j + 1;
     // Classical Gram-Schmidt with the DGKS re-orthogonalisation test:
@@ -238,8 +267,17 @@ static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
         CKE(launch_reduce_decide(h->partials, ublk, hcol + j + 1, h->gs_flag, h->gs_count, kDGKSEta, s));
     }
+    // Under launch timing (eager steps, never captured) the host reads the decision, so that
+    // the gated pass's bytes are attributed exactly when it runs.
+    double pass2 = 0.0;
+    if (h->prof.on) {
+        int flag = 0;
+        CKE(cudaMemcpyAsync(&flag, h->gs_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CKE(cudaStreamSynchronize(s));
+        pass2 = flag ? 1.0 : 0.0;
+    }
     {
-        ProfScope ps(h, HELM_K_MDOT, 0, 0);  // gated: cost counted only if it runs (unknown here)
+        ProfScope ps(h, HELM_K_MDOT, pass2 * np * 16.0 * (nv + 1), df ? 0.0 : pass2 * np * (8.0 * nv + 4.0));
         CKE(gs_dot(j + 1, w, h->gs_flag));
     }
     {
@@ -248,7 +286,7 @@ static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
         CKE(launch_reduce(h->partials, gblk, j + 1, hcol, 1, h->gs_flag, s));
     }
     {
-        ProfScope ps(h, HELM_K_UPDATE_NORM, 0, 0);
+        ProfScope ps(h, HELM_K_UPDATE_NORM, pass2 * np * 16.0 * (nv + 2), df ? 0.0 : pass2 * np * (8.0 * nv + 4.0));
         CKE(gs_update(j + 1, h->h2, w, h->gs_flag));
     }
     {
@@ -256,8 +294,9 @@ static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
         CKE(launch_reduce(h->partials, ublk, 1, hcol + j + 1, 2, h->gs_flag, s));
     }
     {
-        ProfScope ps(h, HELM_K_VECTOR, np * 32.0, np * 2.0);
-        CKE(launch_scale_inv(np, w, hcol + j + 1, w, s));
+        ProfScope ps(h, HELM_K_VECTOR, np * 32.0, df ? 0.0 : np * 2.0);
+        if (df) CKE(launch_scale_inv_pair(np, (float4 *)w, hcol + j + 1, s));
+        else CKE(launch_scale_inv(np, w, hcol + j + 1, w, s));
     }
     {
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
@@ -412,7 +451,9 @@ helm_status fgmres_advance(FgmresRun &r, bool block) {
             if (r.rel <= r.tol) { r.status = HELM_OK; return fgmres_finish(r); }
             if (r.it >= r.maxit) { r.status = HELM_ERR_NOCONV; return fgmres_finish(r); }
             r.restarts++;
-            CKR(launch_scale_inv(np, h->V, h->scal, h->V, s));
+            // v_0 = r0 / beta (as a float-pair vector for the double-FP32 Arnoldi)
+            if (h->mg.gs_arith == HELM_GS_DF) CKR(launch_split_scale(np, h->V, h->scal, s));
+            else CKR(launch_scale_inv(np, h->V, h->scal, h->V, s));
             CKR(cudaMemsetAsync(h->g, 0, (m + 1) * sizeof(double2), s));
             CKR(cudaMemcpyAsync(h->g, h->scal, sizeof(double2), cudaMemcpyDeviceToDevice, s));
             r.jmax = std::min(m, r.maxit - r.it);

@@ -57,6 +57,15 @@ class _MG(C.Structure):
                 ("prec", C.c_int), ("gs_arith", C.c_int)]
 
 
+HELM_MAX_LEVELS = 16
+TILES = {"none": -1, "32x8": 0, "16x16": 1, "16x8": 2, "64x4": 3}
+_TILE_NAMES = {v: k for k, v in TILES.items()}
+
+
+class _Tuning(C.Structure):
+    _fields_ = [("tail_levels", C.c_int), ("level_tile", C.c_int * HELM_MAX_LEVELS)]
+
+
 class _Stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("status", C.c_int), ("rel_res", C.c_double),
                 ("est_res", C.c_double), ("time_ms", C.c_double), ("history", C.c_void_p),
@@ -98,7 +107,11 @@ def load(build: bool = True):
             "helm_create_batch": ([I, P, P, P, P, P, P, P], I),
             "helm_solve_batch": ([P, P, P, D, I, I, P], I),
             "helm_destroy_batch": ([P], None),
+            "helm_batch_handle": ([P, I, P], I),
             "helm_profile": ([P, I], I),
+            "helm_set_tuning": ([P, P], I),
+            "helm_get_tuning": ([P, P], I),
+            "helm_autotune": ([P, I, I, P, P], I),
             "helm_profile_read": ([P, I, P, P, P, P], I),
             "helm_last_error": ([], C.c_char_p),
             "helm_version": ([], C.c_char_p),
@@ -182,18 +195,19 @@ def _prec_of(t: torch.Tensor) -> int:
 class Handle:
     """Owns one ``helm_handle*`` (solver for one grid, its levels and workspace)."""
 
-    def __init__(self, ptr, dim, n, stream):
+    def __init__(self, ptr, dim, n, stream, owned=True):
         self.ptr = ptr
         self.dim = dim
         self.n = tuple(n[:dim])
         self.shape = tuple(reversed(self.n))
         self.np = int(math.prod(self.n))
         self.stream = stream
+        self.owned = owned
 
     def __del__(self):
-        if getattr(self, "ptr", None) and _LIB is not None:
+        if getattr(self, "ptr", None) and _LIB is not None and self.owned:
             _LIB.helm_destroy(self.ptr)
-            self.ptr = None
+        self.ptr = None
 
     def close(self):
         self.__del__()
@@ -357,6 +371,80 @@ def helm_profile_read(h: Handle) -> dict:
     return {name: dict(launches=la[i], ms=ms[i], bytes=by[i], flops=fl[i]) for i, name in enumerate(KERNEL_CLASSES)}
 
 
+def _tuning_to_dict(t: _Tuning, nlev: int) -> dict:
+    return {"tail_levels": t.tail_levels, "level_tile": [_TILE_NAMES[t.level_tile[l]] for l in range(nlev)]}
+
+
+def helm_get_tuning(h: Handle) -> dict:
+    """The handle's kernel choices: tail_levels (-1 = as many as fit) and a tile name per level
+    ("none" = separate sweep / residual / transfer launches)."""
+    t = _Tuning()
+    _check(load().helm_get_tuning(h.ptr, C.byref(t)))
+    return _tuning_to_dict(t, len(h.levels))
+
+
+def helm_set_tuning(h: Handle, tuning: dict):
+    t = _Tuning()
+    _check(load().helm_get_tuning(h.ptr, C.byref(t)))
+    t.tail_levels = int(tuning.get("tail_levels", t.tail_levels))
+    for l, name in enumerate(tuning.get("level_tile", [])[:HELM_MAX_LEVELS]):
+        t.level_tile[l] = TILES[name]
+    _check(load().helm_set_tuning(h.ptr, C.byref(t)))
+
+
+def tuning_key(h: Handle, prec: str) -> str:
+    """Cache key of a tuning: everything the choice depends on (grid, levels, cycle, precision)."""
+    mg = getattr(h, "mg", None) or MGParams()
+    return "%dd-%s-%s-%s-nu%d%d-g%d%d-c%d-%s" % (h.dim, "x".join(map(str, h.n)), mg.kind, mg.smoother, mg.nu1, mg.nu2,
+                                                  mg.gamma_f, mg.gamma_c, mg.coarsest_n, prec)
+
+
+def default_tuning_cache() -> str:
+    """A cache file beside the built library, named by the library's content hash (a rebuilt
+    library starts a new cache)."""
+    import hashlib
+    with open(_build.LIB, "rb") as fh:
+        tag = hashlib.sha1(fh.read()).hexdigest()[:12]
+    return os.path.join(os.path.dirname(_build.LIB), "tuning-%s.json" % tag)
+
+
+def cached_tuning(h: Handle, prec: str = "c64", cache: str | None = None):
+    """The stored tuning for this handle's key, or None."""
+    import json
+    cache = cache or default_tuning_cache()
+    if not os.path.exists(cache):
+        return None
+    with open(cache) as fh:
+        return json.load(fh).get(tuning_key(h, prec), {}).get("tuning")
+
+
+def helm_autotune(h: Handle, prec: str = "c64", reps: int = 10, cache: str | None = None, retune: bool = False):
+    """Picks the cycle's kernels (tail depth, tile shape per level) by timing preconditioner
+    applications on the device, installs the choice and returns (tuning dict, ms per cycle).
+    With a cache path (JSON, keyed by tuning_key), a stored choice is installed without timing
+    unless retune; new results are stored."""
+    import json
+    key = tuning_key(h, prec)
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as fh:
+            table = json.load(fh)
+        if key in table and not retune:
+            helm_set_tuning(h, table[key]["tuning"])
+            return table[key]["tuning"], table[key]["ms"]
+    t, ms = _Tuning(), C.c_double()
+    _check(load().helm_autotune(h.ptr, HELM_C64 if prec == "c64" else HELM_C128, int(reps), C.byref(t), C.byref(ms)))
+    tuning = _tuning_to_dict(t, len(h.levels))
+    if cache:
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        table[key] = {"tuning": tuning, "ms": ms.value}
+        tmp = cache + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
+    return tuning, ms.value
+
+
 def helm_mg_conv_noalloc(h: Handle, b: torch.Tensor, x: torch.Tensor, tol=1e-6, maxcyc=100):
     """helm_mg_conv computed in the library's fixed scratch array (no allocation at all, not
     even here: the caller passes the output ``x``).  For callers that cannot allocate at the
@@ -407,7 +495,34 @@ def helm_create_batch(problems, mg: MGParams | None = None, stream=None) -> Batc
     out = C.c_void_p()
     mgc = mg.to_c()
     _check(load().helm_create_batch(nb, grids, theta, r0, k2p, C.byref(mgc), _stream_ptr(stream), C.byref(out)))
-    return Batch(out.value, shapes)
+    bt = Batch(out.value, shapes)
+    bt.mg = mg
+    return bt
+
+
+def batch_handle(b: Batch, i: int) -> Handle:
+    """Problem i's handle, owned by the batch (valid while the batch lives)."""
+    out = C.c_void_p()
+    _check(load().helm_batch_handle(b.ptr, int(i), C.byref(out)))
+    shape = b.shapes[i]
+    h = Handle(out.value, len(shape), list(reversed(shape)), None, owned=False)
+    h.mg = b.mg
+    h._batch = b
+    return h
+
+
+def helm_autotune_batch(b: Batch, prec: str = "c64", reps: int = 10, cache: str | None = None) -> dict:
+    """Autotunes one handle per distinct grid of the batch (through helm_autotune and its cache)
+    and installs the choice on every problem with that grid; returns {tuning key: tuning}."""
+    chosen = {}
+    for i in range(len(b.shapes)):
+        h = batch_handle(b, i)
+        key = tuning_key(h, prec)
+        if key not in chosen:
+            chosen[key], _ = helm_autotune(h, prec, reps=reps, cache=cache)
+        else:
+            helm_set_tuning(h, chosen[key])
+    return chosen
 
 
 def helm_solve_batch(b: Batch, rhs, x, tol=1e-8, restart=30, maxit=1000, raise_on_noconv=True):

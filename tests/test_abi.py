@@ -42,6 +42,7 @@ def test_library_is_built_for_sm103a():
 
 
 def test_version_and_error_strings_without_gpu():
+    import ctypes as C
     from paper_1012_4307_gb300 import helm
     lib = helm.load()
     assert "sm_103a" in helm.helm_version()
@@ -51,6 +52,11 @@ def test_version_and_error_strings_without_gpu():
     assert "null" in helm.helm_last_error()
     assert lib.krylov_solve(None, 0, None, None, 1e-8, 30, 10, None) == helm.HELM_ERR_ARG
     assert lib.mg_vcycle(None, None, None, 0) == helm.HELM_ERR_ARG
+    assert lib.mg_precondition(None, None, None, 0) == helm.HELM_ERR_ARG
+    t = helm._Tuning()
+    assert lib.helm_set_tuning(None, C.byref(t)) == helm.HELM_ERR_ARG
+    assert lib.helm_get_tuning(None, C.byref(t)) == helm.HELM_ERR_ARG
+    assert lib.helm_autotune(None, 1, 10, None, None) == helm.HELM_ERR_ARG
 
 
 def test_create_rejects_bad_arguments_without_gpu():

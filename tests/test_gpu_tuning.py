@@ -1,0 +1,80 @@
+"""Cycle tuning (kernel choices) and the autotuner: every choice of tail depth and tile shape
+is the same cycle of Algorithm 1 (checked against the oracle's cycle, Section 4.2, on the
+preconditioner call of Section 5), and the autotuned solve reaches the same solution."""
+import json
+
+import numpy as np
+import pytest
+
+from helpers import gpu_handle, oracle_pair, rel_l2, to_gpu, to_np
+from paper_1012_4307_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def helm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1012_4307_gb300 import helm as H
+    H.load()
+    return H
+
+
+def problem(n):
+    return W.Problem("t", 2, n, W.k2_well_growth(2, n, kh_max=0.5), W.gaussian_source(2, n, 0.1, 0), coarsest_n=17)
+
+
+@pytest.mark.parametrize("n", [257, 1025])
+def test_every_tuning_is_the_same_cycle(helm, oracle, n):
+    P = problem(n)
+    h = gpu_handle(helm, P, pc="csg", prec="c64")
+    A, M = oracle_pair(oracle, P)
+    mg = oracle.MG(M, P.coarsest_n, 2, 2, 0.8, "jacobi")
+    v = W.random_field(P.k2.shape, 41)
+    ref = mg.cycle(v)
+    vg = to_gpu(v)
+    nlev = len(h.levels)
+    choices = [dict(tail_levels=t, level_tile=[tile] * nlev) for t in (0, 2, 3)
+               for tile in ("none", "32x8", "16x16", "16x8", "64x4")]
+    mixed = ["64x4", "none", "16x8", "16x16", "32x8", "none"]
+    choices.append(dict(tail_levels=-1, level_tile=[mixed[l % len(mixed)] for l in range(nlev)]))
+    for c in choices:
+        helm.helm_set_tuning(h, c)
+        got = helm.helm_get_tuning(h)
+        assert got["tail_levels"] == c["tail_levels"] and got["level_tile"] == c["level_tile"]
+        z = to_np(helm.mg_precondition(h, vg))
+        assert rel_l2(z, ref) <= 2e-5, c
+
+
+def test_autotune_installs_a_choice_and_solves_the_same(helm, tmp_path):
+    P = W.config_2d_well(513)
+    f = to_gpu(P.f)
+    h = gpu_handle(helm, P, pc="csg", prec="c64", gs="df")
+    x0, st0 = helm.krylov_solve(h, f, tol=1e-8, restart=30, maxit=3000)
+    cache = str(tmp_path / "tuning.json")
+    tuning, ms = helm.helm_autotune(h, "c64", reps=5, cache=cache)
+    assert ms > 0 and helm.helm_get_tuning(h) == tuning
+    x1, st1 = helm.krylov_solve(h, f, tol=1e-8, restart=30, maxit=3000)
+    assert st1.status == helm.HELM_OK and st1.rel_res <= 1e-8
+    # same problem to the solve's accuracy; iteration counts may move under FP32 rounding order
+    d = float(torch.linalg.vector_norm(x1 - x0) / torch.linalg.vector_norm(x0))
+    assert d <= 1e-6
+    assert abs(st1.iterations - st0.iterations) <= 0.1 * st0.iterations + 2
+    # the cache returns the stored choice without timing
+    table = json.load(open(cache))
+    assert helm.tuning_key(h, "c64") in table
+    h2 = gpu_handle(helm, P, pc="csg", prec="c64", gs="df")
+    t2, ms2 = helm.helm_autotune(h2, "c64", cache=cache)
+    assert t2 == tuning and ms2 == ms and helm.helm_get_tuning(h2) == tuning
+
+
+def test_set_tuning_rejects_bad_values(helm):
+    P = problem(65)
+    h = gpu_handle(helm, P, pc="csg", prec="c64")
+    with pytest.raises(helm.HelmError):
+        helm.helm_set_tuning(h, dict(tail_levels=1))
+    with pytest.raises(helm.HelmError):
+        helm.helm_set_tuning(h, dict(tail_levels=-2))

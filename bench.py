@@ -53,6 +53,8 @@ def parse():
                     help="batched workload instead: COUNT independent 2D problems with sizes drawn from "
                          "{129, 257, 513, 1025} and energies in [0.5, 4], solved together (helm_solve_batch)")
     ap.add_argument("--no-tune", action="store_true", help="default kernel choices instead of the autotuned ones")
+    ap.add_argument("--gs", default="dcgs2", choices=["dcgs2", "df", "fp64"],
+                    help="Arnoldi arithmetic of the headline solve (see helm_gs_arith)")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",
                     help="profiling case: build the same problem and run one solve capped at ITERS iterations, "
                          "nothing else (keeps the launch count small enough for ncu)")
@@ -200,6 +202,11 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------- batch
+GS_NAMES = {"dcgs2": "double-FP32 delayed CGS2 on float-pair vectors",
+            "df": "double-FP32 CGS + DGKS on float-pair vectors",
+            "fp64": "IEEE FP64 CGS + DGKS"}
+
+
 def run_batch(args):
     """COUNT problems solved together (one host thread, one stream and CUDA-graph-replayed
     FGMRES steps per problem) against the same problems solved one after another."""
@@ -211,7 +218,7 @@ def run_batch(args):
     torch.cuda.set_device(0)
     helm.load()
     probs = W.config_batch(count=args.batch)
-    mg = helm.MGParams(kind="csg", prec="c64", gs="df", coarsest_n=17)
+    mg = helm.MGParams(kind="csg", prec="c64", gs=args.gs, coarsest_n=17)
     specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
     b = helm.helm_create_batch(specs, mg=mg)
     tunings = None if args.no_tune else helm.helm_autotune_batch(b, "c64", cache=helm.default_tuning_cache())
@@ -294,7 +301,7 @@ def main():
     k2 = torch.from_numpy(P.k2).cuda()
     stream = torch.cuda.current_stream()
     mg = helm.MGParams(kind="csg", theta_a=P.theta_a, nu1=P.nu1, nu2=P.nu2, omega=P.omega, coarsest_n=P.coarsest_n,
-                       prec="c64", gs="df")
+                       prec="c64", gs=args.gs)
     h = helm.helm_create(2, [P.n, P.n], k2, theta=P.theta, mg=mg)
     f = torch.from_numpy(P.f).cuda()
     x = torch.zeros_like(f)
@@ -438,8 +445,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "c64 cycle / f64 outer", "data": "synthetic",
                 "config": {"workload": P.name, "unknowns": P.unknowns, "nodes": [P.n, P.n],
-                           "solver": "FGMRES(30) with FP64 vectors, Gram-Schmidt in double-FP32 arithmetic; "
-                                     "CSG theta_a=pi/14, V(2,2) omega-Jacobi 0.8, complex64 cycle",
+                           "solver": "FGMRES(30), FP64 Hessenberg/Givens/true residual/solution; Arnoldi: %s; "
+                                     "CSG theta_a=pi/14, V(2,2) omega-Jacobi 0.8, complex64 cycle" % GS_NAMES[args.gs],
                            "tol": args.tol, "ecs_theta": "pi/6", "kh_max": 0.6,
                            "l2": "256 MiB device write before every step, outside the timed events",
                            "cycle_tuning": tuning, "tuned_ms_per_cycle": tune_ms,

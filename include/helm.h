@@ -76,7 +76,13 @@ typedef enum { HELM_SMOOTH_JACOBI = 0, HELM_SMOOTH_RB = 1 } helm_smoother;
  *         like FP64, holding 47-48 significant bits; error-free products and sums on the FP32
  *         units (about 46 significant bits per product, 48 per sum); inner products rounded
  *         to FP64 once. */
-typedef enum { HELM_GS_FP64 = 0, HELM_GS_DF = 1 } helm_gs_arith;
+/*   DCGS2: the DF arithmetic and storage with delayed classical Gram-Schmidt with
+ *         reorthogonalisation (Swirydowicz et al. 2020): step j's single inner-product pass
+ *         also reorthogonalises the vector of step j - 1, and one update pass finishes v_j and
+ *         orthogonalises the new vector once; two passes over the basis per step instead of
+ *         up to four.  The Hessenberg column of step j is completed, and its residual estimate
+ *         known, one step later (the last column of a cycle by a closing inner product). */
+typedef enum { HELM_GS_FP64 = 0, HELM_GS_DF = 1, HELM_GS_DCGS2 = 2 } helm_gs_arith;
 
 /* Uniform real grid: n[a] nodes on [lo[a], hi[a]] per axis, boundary nodes included
  * (n - 2 unknowns per axis).  dim is 2 or 3; unused entries are ignored. */

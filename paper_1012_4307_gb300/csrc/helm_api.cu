@@ -198,7 +198,8 @@ helm_status helm_validate_create(const helm_grid *grid, const double *r0_lo, con
     if (mg->prec != HELM_C128 && mg->prec != HELM_C64) return helm_fail(HELM_ERR_ARG, "bad precision");
     if (mg->smoother != HELM_SMOOTH_JACOBI && mg->smoother != HELM_SMOOTH_RB) return helm_fail(HELM_ERR_ARG, "bad smoother");
     if (mg->coarsest_n < 3) return helm_fail(HELM_ERR_ARG, "coarsest_n must be >= 3");
-    if (mg->gs_arith != HELM_GS_FP64 && mg->gs_arith != HELM_GS_DF) return helm_fail(HELM_ERR_ARG, "bad gs_arith");
+    if (mg->gs_arith != HELM_GS_FP64 && mg->gs_arith != HELM_GS_DF && mg->gs_arith != HELM_GS_DCGS2)
+        return helm_fail(HELM_ERR_ARG, "bad gs_arith");
     return HELM_OK;
 }
 

@@ -93,6 +93,11 @@ struct helm_handle {
     double2 *fnorm_dev = nullptr;  // ||f|| of the current solve (device scalar)
     // FGMRES steps: one event per step j, and a CUDA graph of step j captured on cap_stream
     std::vector<cudaEvent_t> step_ev;
+    // delayed CGS2: inner products of a step (2 (m + 1)), normalisation norms alpha_j (m + 2),
+    // update coefficients (2 m + 4); closing step of a cycle with jc columns: event and graph jc
+    double2 *hv = nullptr, *alpha2 = nullptr, *dcoef = nullptr;
+    std::vector<cudaEvent_t> close_ev;
+    std::vector<cudaGraphExec_t> close_graph;
     std::vector<cudaGraphExec_t> step_graph;
     cudaStream_t cap_stream = nullptr;
     bool graphs_ok = true;

@@ -168,6 +168,17 @@ cudaError_t launch_mdot_norm_pair(size_t n, const float4 *V, size_t ldv, int nv,
                                   const int *gate, cudaStream_t s);
 cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int nv, const double2 *h, float4 *w,
                                     double2 *partials, const int *gate, cudaStream_t s);
+// Delayed CGS2 (one dot and one update pass per Arnoldi step, float pairs):
+//   dot:    partials[i*G+b] = V_i^H x, partials[(nv+i)*G+b] = V_i^H w  (i < nv, G = gs_df_nblocks)
+//   coef:   one-thread FP64 step of the method (kernels_krylov.cu)
+//   update: slot j <- final v_j, slot j+1 <- once-orthogonalised w; partials[b] = ||w||^2
+//           (G = gs_df_update_nblocks)
+cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *x, const float4 *w,
+                              double2 *partials, cudaStream_t s);
+cudaError_t launch_dcgs2_coef(int j, int has_w, const double2 *hv, const double2 *alpha2, double2 *H, int ldh,
+                              double2 *coef, cudaStream_t s);
+cudaError_t launch_update2_pair(size_t n, float4 *V, size_t ldv, int j, const double2 *coef, double2 *partials,
+                                cudaStream_t s);
 // w <- w / beta->x (float pairs)
 cudaError_t launch_scale_inv_pair(size_t n, float4 *w, const double2 *beta, cudaStream_t s);
 // in place: the double2 vector x becomes the float-pair vector x / beta->x (beta null: 1)

@@ -200,6 +200,138 @@ __global__ void __launch_bounds__(NT) k_update_norm_pair(size_t n, const float4 
     if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(sums[0], 0.0);
 }
 
+// ---------------------------------------------------------------- delayed CGS2 (DCGS2)
+// partials[i * G + b] = V_i^H x and partials[(nv + i) * G + b] = V_i^H w for i < nv: one pass
+// over the basis for two right-hand vectors (x is itself basis slot nv - 1).
+template <int CH>
+__global__ void __launch_bounds__(NT) k_mdot2_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
+                                                   const float4 *__restrict__ x, const float4 *__restrict__ w,
+                                                   double2 *__restrict__ partials) {
+    __shared__ double sums[4 * CH];
+    const int i0 = blockIdx.y * CH;
+    const int cnt = min(CH, nv - i0);
+    float s[2][CH][4];  // [rhs][basis][re.s, re.c, im.s, im.c]
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int t = 0; t < CH; t++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) s[r][t][k] = 0.f;
+    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const float4 xq = x[q], wq = w[q];
+        float4 vq[CH];
+#pragma unroll
+        for (int t = 0; t < CH; t++) vq[t] = t < cnt ? V[(size_t)(i0 + t) * ldv + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const ff xr = ff_re(xq), xi = ff_im(xq), wr = ff_re(wq), wi = ff_im(wq);
+#pragma unroll
+        for (int t = 0; t < CH; t++) {
+            if (t < cnt) {
+                const ff vr = ff_re(vq[t]), vi = ff_im(vq[t]);
+                float p, e;
+                // conj(v) y = (vr yr + vi yi) + i (vr yi - vi yr), y = x then w
+                ff_two_prod(vr, xr, p, e); ff_acc_prod(s[0][t][0], s[0][t][1], p, e);
+                ff_two_prod(vi, xi, p, e); ff_acc_prod(s[0][t][0], s[0][t][1], p, e);
+                ff_two_prod(vr, xi, p, e); ff_acc_prod(s[0][t][2], s[0][t][3], p, e);
+                ff_two_prod(vi, xr, p, e); ff_acc_prod(s[0][t][2], s[0][t][3], -p, -e);
+                ff_two_prod(vr, wr, p, e); ff_acc_prod(s[1][t][0], s[1][t][1], p, e);
+                ff_two_prod(vi, wi, p, e); ff_acc_prod(s[1][t][0], s[1][t][1], p, e);
+                ff_two_prod(vr, wi, p, e); ff_acc_prod(s[1][t][2], s[1][t][3], p, e);
+                ff_two_prod(vi, wr, p, e); ff_acc_prod(s[1][t][2], s[1][t][3], -p, -e);
+            }
+        }
+    }
+    ff vals[4 * CH];
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int t = 0; t < CH; t++) {
+            vals[(r * CH + t) * 2] = ff_norm(s[r][t][0], s[r][t][1]);
+            vals[(r * CH + t) * 2 + 1] = ff_norm(s[r][t][2], s[r][t][3]);
+        }
+    block_sum_ff<4 * CH>(vals, sums);
+    __syncthreads();
+    const int G = gridDim.x;
+    if ((int)threadIdx.x < 2 * cnt) {
+        const int r = threadIdx.x / cnt, t = threadIdx.x % cnt;
+        partials[((size_t)r * nv + i0 + t) * G + blockIdx.x] =
+            make_double2(sums[(r * CH + t) * 2], sums[(r * CH + t) * 2 + 1]);
+    }
+}
+
+// One pass of the DCGS2 update for step j with coefficients coef (see k_dcgs2_coef):
+//   x <- (x - sum_{i<j} V_i A_i) / nu          (x = basis slot j: its final vector v_j)
+//   w <- w - x_old s - sum_{i<j} V_i C_i       (w = slot j + 1: once orthogonalised)
+// with A = coef[0..j), C = coef[j..2j), 1/nu = coef[2j].x, s = coef[2j + 1];
+// partials[b] = (||w||^2, 0).
+__global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
+                                                     const double2 *__restrict__ coef, double2 *__restrict__ partials) {
+    __shared__ float4 cA[64], cC[64];
+    __shared__ float4 sc[2];  // (1/nu hi, lo, 0, 0), s
+    __shared__ double sums[1];
+    for (int i = threadIdx.x; i < j; i += NT) {
+        const ff a = ff_split(coef[i].x), b = ff_split(coef[i].y);
+        cA[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        const ff c = ff_split(coef[j + i].x), d = ff_split(coef[j + i].y);
+        cC[i] = make_float4(c.hi, c.lo, d.hi, d.lo);
+    }
+    if (threadIdx.x == 0) {
+        const ff r = ff_split(coef[2 * j].x);
+        sc[0] = make_float4(r.hi, r.lo, 0.f, 0.f);
+        const ff a = ff_split(coef[2 * j + 1].x), b = ff_split(coef[2 * j + 1].y);
+        sc[1] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+    __syncthreads();
+    float4 *x = V + (size_t)j * ldv, *w = V + (size_t)(j + 1) * ldv;
+    const ff rinv = ff_re(sc[0]), sr = ff_re(sc[1]), si = ff_im(sc[1]);
+    float sn = 0.f, cn = 0.f;
+    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const float4 xq = x[q], wq = w[q];
+        const ff xr = ff_re(xq), xi = ff_im(xq);
+        // accumulators (sum, compensation): v re/im from x, w re/im from w
+        float vrs = xq.x, vrc = xq.y, vis = xq.z, vic = xq.w;
+        float wrs = wq.x, wrc = wq.y, wis = wq.z, wic = wq.w;
+        float p, e;
+        // w -= x s: re -= xr sr - xi si ; im -= xr si + xi sr
+        ff_two_prod(xr, sr, p, e); ff_acc_prod(wrs, wrc, -p, -e);
+        ff_two_prod(xi, si, p, e); ff_acc_prod(wrs, wrc, p, e);
+        ff_two_prod(xr, si, p, e); ff_acc_prod(wis, wic, -p, -e);
+        ff_two_prod(xi, sr, p, e); ff_acc_prod(wis, wic, -p, -e);
+        float4 cur = j > 0 ? V[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = 0; i < j; i++) {
+            const float4 nxt = i + 1 < j ? V[(size_t)(i + 1) * ldv + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const ff vr = ff_re(cur), vi = ff_im(cur);
+            const float4 a4 = cA[i], c4 = cC[i];
+            const ff ar = ff_re(a4), ai = ff_im(a4), cr = ff_re(c4), ci = ff_im(c4);
+            // v -= V_i a ; w -= V_i c   (complex products)
+            ff_two_prod(vr, ar, p, e); ff_acc_prod(vrs, vrc, -p, -e);
+            ff_two_prod(vi, ai, p, e); ff_acc_prod(vrs, vrc, p, e);
+            ff_two_prod(vr, ai, p, e); ff_acc_prod(vis, vic, -p, -e);
+            ff_two_prod(vi, ar, p, e); ff_acc_prod(vis, vic, -p, -e);
+            ff_two_prod(vr, cr, p, e); ff_acc_prod(wrs, wrc, -p, -e);
+            ff_two_prod(vi, ci, p, e); ff_acc_prod(wrs, wrc, p, e);
+            ff_two_prod(vr, ci, p, e); ff_acc_prod(wis, wic, -p, -e);
+            ff_two_prod(vi, cr, p, e); ff_acc_prod(wis, wic, -p, -e);
+            cur = nxt;
+        }
+        // v_j = v / nu
+        const ff vr = ff_norm(vrs, vrc), vi = ff_norm(vis, vic);
+        ff_two_prod(vr, rinv, p, e);
+        const ff or_ = ff_norm(p, e);
+        ff_two_prod(vi, rinv, p, e);
+        const ff oi = ff_norm(p, e);
+        x[q] = make_float4(or_.hi, or_.lo, oi.hi, oi.lo);
+        const ff wr = ff_norm(wrs, wrc), wi = ff_norm(wis, wic);
+        w[q] = make_float4(wr.hi, wr.lo, wi.hi, wi.lo);
+        ff_two_prod(wr, wr, p, e);
+        ff_acc_prod(sn, cn, p, e);
+        ff_two_prod(wi, wi, p, e);
+        ff_acc_prod(sn, cn, p, e);
+    }
+    ff vals[1] = {ff_norm(sn, cn)};
+    block_sum_ff<1>(vals, sums);
+    if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(sums[0], 0.0);
+}
+
 // 1 / beta.x as a float pair, one FP64 division per block.
 __device__ __forceinline__ ff block_inv(const double2 *beta) {
     __shared__ float2 rs;
@@ -277,6 +409,23 @@ cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int n
                                     double2 *partials, const int *gate, cudaStream_t s) {
     if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
     k_update_norm_pair<<<gs_df_update_nblocks(n), NT, 0, s>>>(n, V, ldv, nv, h, w, partials, gate);
+    return cudaGetLastError();
+}
+
+constexpr int DF_CH2 = 4;  // basis vectors per block row of the two-vector dot pass
+
+cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *x, const float4 *w,
+                              double2 *partials, cudaStream_t s) {
+    if (nv < 1 || nv > 64) return cudaErrorInvalidValue;
+    dim3 g(gs_df_nblocks(n), (nv + DF_CH2 - 1) / DF_CH2);
+    k_mdot2_pair<DF_CH2><<<g, NT, 0, s>>>(n, V, ldv, nv, x, w, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update2_pair(size_t n, float4 *V, size_t ldv, int j, const double2 *coef, double2 *partials,
+                                cudaStream_t s) {
+    if (j < 0 || j > 64) return cudaErrorInvalidValue;
+    k_update2_pair<<<gs_df_update_nblocks(n), NT, 0, s>>>(n, V, ldv, j, coef, partials);
     return cudaGetLastError();
 }
 

@@ -30,9 +30,16 @@ static void free_krylov(helm_handle *h) {
     for (cudaGraphExec_t g : h->step_graph)
         if (g) cudaGraphExecDestroy(g);
     h->step_graph.clear();
+    for (cudaGraphExec_t g : h->close_graph)
+        if (g) cudaGraphExecDestroy(g);
+    h->close_graph.clear();
     for (cudaEvent_t e : h->step_ev)
         if (e) cudaEventDestroy(e);
     h->step_ev.clear();
+    for (cudaEvent_t e : h->close_ev)
+        if (e) cudaEventDestroy(e);
+    h->close_ev.clear();
+    h->hv = h->alpha2 = h->dcoef = nullptr;
     for (void *p : h->krylov_owned) cudaFree(p);
     h->krylov_owned.clear();
     h->V = nullptr; h->Z = nullptr; h->H = nullptr; h->g = h->sn = h->y = h->h2 = nullptr;
@@ -47,11 +54,12 @@ static void free_krylov(helm_handle *h) {
 void helm_free_krylov(helm_handle *h) { free_krylov(h); }
 
 void helm_drop_graphs(helm_handle *h) {
-    for (cudaGraphExec_t &g : h->step_graph)
-        if (g) {
-            cudaGraphExecDestroy(g);
-            g = nullptr;
-        }
+    for (auto *v : {&h->step_graph, &h->close_graph})
+        for (cudaGraphExec_t &g : *v)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
 }
 
 template <typename T> static cudaError_t kalloc(helm_handle *h, T **p, size_t count) {
@@ -86,7 +94,10 @@ static helm_status ensure_ws(helm_handle *h, int m) {
     KA(&h->y, (size_t)m);
     KA(&h->h2, (size_t)m + 1);
     KA(&h->cs, (size_t)m);
-    KA(&h->partials, (size_t)nblk * 65);
+    KA(&h->partials, (size_t)nblk * std::max(65, 2 * m + 4));
+    KA(&h->hv, (size_t)2 * m + 4);
+    KA(&h->alpha2, (size_t)m + 2);
+    KA(&h->dcoef, (size_t)2 * m + 4);
     KA(&h->scal, 32);
     KA(&h->est_dev, (size_t)m + 4);
     KA(&h->gs_flag, 4);
@@ -107,6 +118,9 @@ static helm_status ensure_ws(helm_handle *h, int m) {
     h->step_ev.assign((size_t)m, nullptr);
     for (int j = 0; j < m; j++) CKR(cudaEventCreateWithFlags(&h->step_ev[j], cudaEventDisableTiming));
     h->step_graph.assign((size_t)m, nullptr);
+    h->close_ev.assign((size_t)m + 1, nullptr);
+    for (int j = 0; j <= m; j++) CKR(cudaEventCreateWithFlags(&h->close_ev[j], cudaEventDisableTiming));
+    h->close_graph.assign((size_t)m + 1, nullptr);
     if (!h->ev_fn) CKR(cudaEventCreateWithFlags(&h->ev_fn, cudaEventDisableTiming));
     if (!h->ev_beta) CKR(cudaEventCreateWithFlags(&h->ev_beta, cudaEventDisableTiming));
     if (!h->cap_stream) CKR(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
@@ -309,33 +323,123 @@ static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
                         : cudaEventRecord(h->step_ev[j], s);
 }
 
-// Runs step j: eagerly while launch timing is on, else by replaying a CUDA graph of the step,
-// captured on the handle's private stream the first time step j runs with this workspace.
-static cudaError_t run_step(helm_handle *h, int j, int m) {
-    if (h->prof.on || !h->graphs_ok) return fgmres_step(h, j, m);
-    if (!h->step_graph[j]) {
+// Delayed CGS2 step j (gs_arith = DCGS2; float-pair basis).  Basis slot j holds u_j, the
+// once-orthogonalised vector of step j - 1 normalised by alpha_j (slot 0: the final v_0).
+//   z_j = cycle(u_j); w = A z_j                                  (slot j + 1)
+//   one pass: V_i^H u_j and V_i^H w for i <= j                    (k_mdot2_pair)
+//   coefficients: finish column j - 1 of H (reorthogonalisation of u_j), first-pass column j,
+//   then the Givens rotation of column j - 1 and its residual estimate est[j - 1]
+//   one pass: slot j <- v_j (final), slot j + 1 <- w orthogonalised once; alpha_{j+1} = ||w||
+//   slot j + 1 <- w / alpha_{j+1} = u_{j+1}
+// Only column j - 1 of H, the first-pass column j, rotation j - 1, g[j-1..j], slots j and j + 1
+// and z_j are written, so a step queued ahead of the host's decision never disturbs columns
+// 0 .. j - 2 that a solution update may use.
+static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
+    const size_t np = h->np;
+    const int ldh = m + 1;
+    cudaStream_t s = h->stream;
+    const size_t zsz = h->z_prec == HELM_C64 ? sizeof(float2) : sizeof(double2);
+    float4 *V4 = (float4 *)h->V;
+    float4 *u = V4 + (size_t)j * np, *w = V4 + (size_t)(j + 1) * np;
+    void *zj = (char *)h->Z + (size_t)j * np * zsz;
+    const double nv = j + 1;
+    CKE(precond_apply_pair(h, u, zj, w));
+    {
+        ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (nv + 1), 0);
+        CKE(launch_mdot2_pair(np, V4, np, j + 1, u, w, h->partials, s));
+    }
+    {
+        ProfScope ps(h, HELM_K_SMALL, 0, 0);
+        CKE(launch_reduce(h->partials, gs_df_nblocks(np), 2 * (j + 1), h->hv, 0, nullptr, s));
+        CKE(launch_dcgs2_coef(j, 1, h->hv, h->alpha2, h->H, ldh, h->dcoef, s));
+        if (j > 0) CKE(launch_givens(h->H, ldh, j - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, s));
+    }
+    {
+        ProfScope ps(h, HELM_K_UPDATE_NORM, np * 16.0 * (nv + 3), 0);
+        CKE(launch_update2_pair(np, V4, np, j, h->dcoef, h->partials, s));
+    }
+    {
+        ProfScope ps(h, HELM_K_SMALL, 0, 0);
+        CKE(launch_reduce(h->partials, gs_df_update_nblocks(np), 1, h->alpha2 + j + 1, 2, nullptr, s));
+    }
+    {
+        ProfScope ps(h, HELM_K_VECTOR, np * 32.0, 0);
+        CKE(launch_scale_inv_pair(np, w, h->alpha2 + j + 1, s));
+    }
+    if (j > 0) CKE(cudaMemcpyAsync(h->est_host + j - 1, h->est_dev + j - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    return h->capturing ? cudaEventRecordWithFlags(h->step_ev[j], s, cudaEventRecordExternal)
+                        : cudaEventRecord(h->step_ev[j], s);
+}
+
+// Closing step of a delayed-CGS2 cycle with jc columns: reorthogonalise u_jc against
+// v_0 .. v_{jc-1} only to finish column jc - 1 of H, then its rotation and est[jc - 1].
+static cudaError_t fgmres_close_dcgs2(helm_handle *h, int jc, int m) {
+    const size_t np = h->np;
+    const int ldh = m + 1;
+    cudaStream_t s = h->stream;
+    const float4 *V4 = (const float4 *)h->V;
+    {
+        ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (jc + 1), 0);
+        CKE(launch_mdot_norm_pair(np, V4, np, jc, V4 + (size_t)jc * np, h->partials, nullptr, s));
+    }
+    {
+        ProfScope ps(h, HELM_K_SMALL, 0, 0);
+        CKE(launch_reduce(h->partials, gs_df_nblocks(np), jc + 1, h->hv, 0, nullptr, s));
+        CKE(launch_dcgs2_coef(jc, 0, h->hv, h->alpha2, h->H, ldh, h->dcoef, s));
+        CKE(launch_givens(h->H, ldh, jc - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, s));
+    }
+    CKE(cudaMemcpyAsync(h->est_host + jc - 1, h->est_dev + jc - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    return h->capturing ? cudaEventRecordWithFlags(h->close_ev[jc], s, cudaEventRecordExternal)
+                        : cudaEventRecord(h->close_ev[jc], s);
+}
+
+// Runs a piece of stream work eagerly while launch timing is on, else by replaying a CUDA
+// graph of it, captured on the handle's private stream on first use with this workspace.
+template <typename F>
+static cudaError_t run_graph(helm_handle *h, cudaGraphExec_t &exec, F work) {
+    if (h->prof.on || !h->graphs_ok) return work();
+    if (!exec) {
         cudaStream_t keep = h->stream;
         cudaGraph_t g = nullptr;
         h->stream = h->cap_stream;
         cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             h->capturing = true;
-            e = fgmres_step(h, j, m);
+            e = work();
             h->capturing = false;
             cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
             if (e == cudaSuccess) e = e2;
         }
         h->stream = keep;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->step_graph[j], g, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess) {  // run this handle eagerly from now on
             cudaGetLastError();
-            h->step_graph[j] = nullptr;
+            exec = nullptr;
             h->graphs_ok = false;
-            return fgmres_step(h, j, m);
+            return work();
         }
     }
-    return cudaGraphLaunch(h->step_graph[j], h->stream);
+    return cudaGraphLaunch(exec, h->stream);
+}
+
+static bool use_dcgs2(const helm_handle *h) { return h->mg.gs_arith == HELM_GS_DCGS2; }
+
+// Step j of the cycle (either Gram-Schmidt variant).
+static cudaError_t run_step(helm_handle *h, int j, int m) {
+    if (use_dcgs2(h)) return run_graph(h, h->step_graph[j], [&] { return fgmres_step_dcgs2(h, j, m); });
+    return run_graph(h, h->step_graph[j], [&] { return fgmres_step(h, j, m); });
+}
+
+// The work that makes est[k] available in a cycle of jmax columns (delayed CGS2): step k + 1,
+// or the closing step after the last column.
+static cudaError_t run_unit(helm_handle *h, int k, int jmax, int m) {
+    if (k + 1 < jmax) return run_step(h, k + 1, m);
+    return run_graph(h, h->close_graph[jmax], [&] { return fgmres_close_dcgs2(h, jmax, m); });
+}
+
+static cudaEvent_t unit_event(helm_handle *h, int k, int jmax) {
+    return k + 1 < jmax ? h->step_ev[k + 1] : h->close_ev[jmax];
 }
 
 // ---------------------------------------------------------------------------------- FGMRES
@@ -389,7 +493,8 @@ static helm_status fgmres_finish(FgmresRun &r) {
         r.st->rel_res = r.rel;
         r.st->est_res = r.est;
         r.st->status = r.status;
-        r.st->reorthogonalizations = cnt[1];
+        // delayed CGS2 reorthogonalises every basis vector
+        r.st->reorthogonalizations = use_dcgs2(h) ? r.it : cnt[1];
     } else {
         CKR(cudaStreamSynchronize(h->stream));
     }
@@ -452,7 +557,7 @@ helm_status fgmres_advance(FgmresRun &r, bool block) {
             if (r.it >= r.maxit) { r.status = HELM_ERR_NOCONV; return fgmres_finish(r); }
             r.restarts++;
             // v_0 = r0 / beta (as a float-pair vector for the double-FP32 Arnoldi)
-            if (h->mg.gs_arith == HELM_GS_DF) CKR(launch_split_scale(np, h->V, h->scal, s));
+            if (h->mg.gs_arith != HELM_GS_FP64) CKR(launch_split_scale(np, h->V, h->scal, s));
             else CKR(launch_scale_inv(np, h->V, h->scal, h->V, s));
             CKR(cudaMemsetAsync(h->g, 0, (m + 1) * sizeof(double2), s));
             CKR(cudaMemcpyAsync(h->g, h->scal, sizeof(double2), cudaMemcpyDeviceToDevice, s));
@@ -462,14 +567,23 @@ helm_status fgmres_advance(FgmresRun &r, bool block) {
             // estimate, so the GPU never idles on the host.  If step j converges, step j+1 has
             // only written column j+1, v_{j+2}, z_{j+1} and g[j+1..j+2], none of which the back
             // substitution over the first j+1 columns reads.
-            CKR(run_step(h, 0, m));
-            if (r.jmax > 1) CKR(run_step(h, 1, m));
+            // Delayed CGS2: est[k] comes from the unit after step k (step k + 1, or the closing
+            // step); units 0 and 1 are queued behind step 0.
+            if (use_dcgs2(h)) {
+                CKR(run_step(h, 0, m));
+                CKR(run_unit(h, 0, r.jmax, m));
+                if (r.jmax > 1) CKR(run_unit(h, 1, r.jmax, m));
+            } else {
+                CKR(run_step(h, 0, m));
+                if (r.jmax > 1) CKR(run_step(h, 1, m));
+            }
             r.phase = FgmresRun::IN_CYCLE;
             break;
         }
         case FgmresRun::IN_CYCLE: {
             const int j = r.next;
-            if (!event_ready(h->step_ev[j], block, &err)) {
+            const cudaEvent_t ev = use_dcgs2(h) ? unit_event(h, j, r.jmax) : h->step_ev[j];
+            if (!event_ready(ev, block, &err)) {
                 if (err != cudaSuccess) return helm_fail(HELM_ERR_CUDA, "event: %s", cudaGetErrorString(err));
                 return HELM_OK;
             }
@@ -480,7 +594,10 @@ helm_status fgmres_advance(FgmresRun &r, bool block) {
             const int jdone = j + 1;
             if (r.est > r.tol && jdone < r.jmax) {
                 r.next = jdone;
-                if (jdone + 1 < r.jmax) CKR(run_step(h, jdone + 1, m));
+                if (jdone + 1 < r.jmax) {
+                    if (use_dcgs2(h)) CKR(run_unit(h, jdone + 1, r.jmax, m));
+                    else CKR(run_step(h, jdone + 1, m));
+                }
                 break;
             }
             // x += Z y with y = H^{-1} g over the first jdone columns

@@ -33,7 +33,7 @@ HELM_PC_NONE, HELM_PC_CSG, HELM_PC_CSL, HELM_PC_QD, HELM_PC_LAPLACE = range(5)
 HELM_OP_A, HELM_OP_M = 0, 1
 HELM_FGMRES, HELM_BICGSTAB = 0, 1
 HELM_SMOOTH_JACOBI, HELM_SMOOTH_RB = 0, 1
-HELM_GS_FP64, HELM_GS_DF = 0, 1
+HELM_GS_FP64, HELM_GS_DF, HELM_GS_DCGS2 = 0, 1, 2
 
 PC_KINDS = {"none": HELM_PC_NONE, "csg": HELM_PC_CSG, "csl": HELM_PC_CSL, "qd": HELM_PC_QD, "laplace": HELM_PC_LAPLACE}
 STATUS_NAMES = {0: "HELM_OK", 1: "HELM_ERR_ARG", 2: "HELM_ERR_CUDA", 3: "HELM_ERR_NOMEM", 4: "HELM_ERR_NOCONV",
@@ -154,7 +154,9 @@ class MGParams:
     gamma_c: int = 1
     coarsest_n: int = 17
     prec: str = "c64"
-    gs: str = "fp64"  # Gram-Schmidt arithmetic: "fp64" or "df" (double-FP32 on FP64 vectors)
+    # Arnoldi arithmetic: "fp64" (IEEE FP64, CGS + DGKS), "df" (double-FP32 on float-pair
+    # vectors, CGS + DGKS) or "dcgs2" (double-FP32, delayed CGS2: one dot and one update pass)
+    gs: str = "fp64"
 
     def to_c(self) -> _MG:
         m = _MG()
@@ -164,7 +166,7 @@ class MGParams:
         m.smoother = HELM_SMOOTH_RB if self.smoother == "rb" else HELM_SMOOTH_JACOBI
         m.gamma_f, m.gamma_c, m.coarsest_n = self.gamma_f, self.gamma_c, self.coarsest_n
         m.prec = HELM_C64 if self.prec == "c64" else HELM_C128
-        m.gs_arith = {"fp64": HELM_GS_FP64, "df": HELM_GS_DF}[self.gs]
+        m.gs_arith = {"fp64": HELM_GS_FP64, "df": HELM_GS_DF, "dcgs2": HELM_GS_DCGS2}[self.gs]
         return m
 
 

@@ -198,15 +198,17 @@ def test_fgmres_mixed_precision(helm, oracle):
     assert rel_l2(to_np(x), xo) <= 1e-7
 
 
+@pytest.mark.parametrize("gs", ["df", "dcgs2"])
 @pytest.mark.parametrize("prec", ["c128", "c64"])
-def test_fgmres_double_float_gram_schmidt(helm, oracle, prec):
-    """Gram-Schmidt in double-FP32 arithmetic on FP64 vectors reaches the same FP64 solution:
-    1e-8 of the oracle at 1e-10 (FP64 cycle), and the same iteration count as FP64 Gram-Schmidt."""
+def test_fgmres_double_float_gram_schmidt(helm, oracle, prec, gs):
+    """The double-FP32 Arnoldi on float-pair vectors (CGS + DGKS, or delayed CGS2) reaches the
+    same FP64 solution: 1e-8 of the oracle at 1e-10 (FP64 cycle), and the same iteration count
+    as FP64 Gram-Schmidt."""
     P = W.config_small(65)
     A, M = oracle_pair(oracle, P)
     mg = oracle.MG(M, 17, 2, 2, 0.8)
     xo, sto = oracle.fgmres(A, mg, P.f, tol=1e-10, restart=30, maxit=500)
-    hdf = gpu_handle(helm, P, pc="csg", prec=prec, gs="df")
+    hdf = gpu_handle(helm, P, pc="csg", prec=prec, gs=gs)
     h64 = gpu_handle(helm, P, pc="csg", prec=prec, gs="fp64")
     x, st = helm.krylov_solve(hdf, to_gpu(P.f), tol=1e-10, restart=30, maxit=500)
     x64, st64 = helm.krylov_solve(h64, to_gpu(P.f), tol=1e-10, restart=30, maxit=500)
@@ -217,13 +219,14 @@ def test_fgmres_double_float_gram_schmidt(helm, oracle, prec):
     assert rel_l2(to_np(x), xo) <= (1e-8 if prec == "c128" else 1e-7)
 
 
-def test_double_float_gram_schmidt_bench_size(helm):
+@pytest.mark.parametrize("gs", ["df", "dcgs2"])
+def test_double_float_gram_schmidt_bench_size(helm, gs):
     """1025 x 1025 well problem (the benchmark workload), complex64 cycle: double-FP32 and FP64
     Gram-Schmidt give the same solution to the accuracy of the solve (rel. residual 1e-8)."""
     P = W.config_2d_well(1025)
     f = to_gpu(P.f)
     out = {}
-    for gs in ("df", "fp64"):
+    for gs in (gs, "fp64"):
         h = gpu_handle(helm, P, pc="csg", prec="c64", gs=gs)
         x, st = helm.krylov_solve(h, f, tol=1e-8, restart=30, maxit=3000)
         assert st.status == helm.HELM_OK and st.rel_res <= 1e-8
@@ -231,9 +234,28 @@ def test_double_float_gram_schmidt_bench_size(helm):
         h.close()
     # restarted GMRES(30) iteration counts at this size move by several percent under any
     # change of rounding (complex64 cycle with FP64 Gram-Schmidt: 841; all-FP64: 886)
-    assert abs(out["df"][1].iterations - out["fp64"][1].iterations) <= 0.1 * out["fp64"][1].iterations
-    d = float(torch.linalg.vector_norm(out["df"][0] - out["fp64"][0]) / torch.linalg.vector_norm(out["fp64"][0]))
+    assert abs(out[gs][1].iterations - out["fp64"][1].iterations) <= 0.1 * out["fp64"][1].iterations
+    d = float(torch.linalg.vector_norm(out[gs][0] - out["fp64"][0]) / torch.linalg.vector_norm(out["fp64"][0]))
     assert d <= 1e-6
+
+
+@pytest.mark.parametrize("restart", [30, 7, 1])
+def test_dcgs2_residual_history_matches_cgs(helm, restart):
+    """Delayed CGS2 and FP64 CGS + DGKS build the same Krylov method: with an FP64 cycle the
+    residual estimates of the first iterations agree to 1e-7 relative, including across
+    restarts (restart 7) and with one column per cycle (restart 1, closing step only)."""
+    P = W.config_small(65)
+    f = to_gpu(P.f)
+    hist = {}
+    for gs in ("dcgs2", "fp64"):
+        h = gpu_handle(helm, P, pc="csg", prec="c128", gs=gs)
+        x, st = helm.krylov_solve(h, f, tol=1e-10, restart=restart, maxit=40, history=True,
+                                  raise_on_noconv=False)
+        hist[gs] = np.array(st.history[: st.iterations])
+    k = min(len(hist["dcgs2"]), len(hist["fp64"]), 25)
+    assert k >= 10
+    a, b = hist["dcgs2"][:k], hist["fp64"][:k]
+    assert np.all(np.abs(a - b) <= 1e-7 * b + 1e-13)
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])

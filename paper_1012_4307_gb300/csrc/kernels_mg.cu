@@ -332,8 +332,32 @@ __device__ __forceinline__ float2 tile_stencil(const TC &tc, const float2 (*u)[R
     return cfma(d, u[sy][sx], acc);
 }
 
+// f(sx, sy) for every node of an RW x RH region, 256 threads, node q = tid + 256 k in row-major
+// order (the region coordinates advance incrementally).
+template <int RW, int RH, typename F>
+__device__ __forceinline__ void for_region(F f) {
+    constexpr int N = RW * RH, ST = 256, DX = ST % RW, DY = ST / RW;
+    int sx = threadIdx.x % RW, sy = threadIdx.x / RW;
+    for (int q = threadIdx.x; q < N; q += ST) {
+        f(sx, sy);
+        sx += DX;
+        sy += DY;
+        if (sx >= RW) {
+            sx -= RW;
+            sy++;
+        }
+    }
+}
+
+// Diagonal of M at region node (sx, sy) from the staged coefficients and k^2.
+template <typename TC>
+__device__ __forceinline__ float2 tile_diag(const TC &tc, int sx, int sy, float k2, float2 bk, float2 c) {
+    return cadd(cadd(tc.x[sx][1], tc.y[sy][1]), cadd(cscale(bk, k2), c));
+}
+
 // u = two omega-Jacobi sweeps from u = 0 for M u = b, written on the owned fine nodes; then
-// rc = FW(b - M u) on the owned coarse nodes.
+// rc = FW(b - M u) on the owned coarse nodes.  Blocks whose region lies inside the grid's
+// interior skip the per-node boundary tests.
 template <int TCX, int TCY>
 __global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float omega, const float2 *__restrict__ b,
                                                        float2 *__restrict__ u, float2 *__restrict__ rc, int ncx,
@@ -345,42 +369,40 @@ __global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float om
     const int I0 = 1 + blockIdx.x * TCX, J0 = 1 + blockIdx.y * TCY;
     const int X0 = 2 * I0 - 3, Y0 = 2 * J0 - 3;
     const int nx = o.nx, ny = o.ny;
+    const bool full = X0 >= 1 && X0 + RW - 1 <= nx - 2 && Y0 >= 1 && Y0 + RH - 1 <= ny - 2;
+    auto inside = [&](int x, int y) { return full || (x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2); };
     tile_coef<RW, RH>(o, X0, Y0, T.tc);
-    auto inside = [&](int x, int y) { return x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2; };
-    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
-        const int sx = q % RW, sy = q / RW, x = X0 + sx, y = Y0 + sy;
-        const bool in = inside(x, y);
-        const size_t p = (size_t)x + (size_t)nx * y;
-        T.b[sy][sx] = in ? b[p] : make_float2(0.f, 0.f);
-        T.k2[sy][sx] = in ? o.k2[p] : 0.f;
-    }
     __syncthreads();
-    // sweep 1 from zero (pointwise): u1 = omega b / D
-    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
-        const int sx = q % RW, sy = q / RW;
-        float2 v = make_float2(0.f, 0.f);
-        if (inside(X0 + sx, Y0 + sy)) {
-            const float2 d = cadd(cadd(T.tc.x[sx][1], T.tc.y[sy][1]), cadd(cscale(o.bk, T.k2[sy][sx]), o.c));
-            v = cscale(cmul(T.b[sy][sx], cinv(d)), omega);
+    // load b and k^2; sweep 1 from zero (pointwise): u1 = omega b / D
+    for_region<RW, RH>([&](int sx, int sy) {
+        const int x = X0 + sx, y = Y0 + sy;
+        float2 bv = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+        float kv = 0.f;
+        if (inside(x, y)) {
+            const size_t p = (size_t)x + (size_t)nx * y;
+            bv = b[p];
+            kv = o.k2[p];
+            v = cscale(cmul(bv, cinv_fast(tile_diag(T.tc, sx, sy, kv, o.bk, o.c))), omega);
         }
+        T.b[sy][sx] = bv;
+        T.k2[sy][sx] = kv;
         T.u1[sy][sx] = v;
-    }
+    });
     __syncthreads();
     // sweep 2 on R3 shrunk by one
-    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
-        const int sx = q % RW, sy = q / RW;
+    for_region<RW, RH>([&](int sx, int sy) {
         float2 v = make_float2(0.f, 0.f);
         if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy)) {
             float2 d;
             const float2 mu = tile_stencil<RW>(T.tc, T.u1, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
-            v = cadd(T.u1[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv(d)), omega));
+            v = cadd(T.u1[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv_fast(d)), omega));
         }
         T.u2[sy][sx] = v;
-    }
+    });
     __syncthreads();
     // owned fine nodes of the smoothed iterate, and the residual on R3 shrunk by two
-    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
-        const int sx = q % RW, sy = q / RW, x = X0 + sx, y = Y0 + sy;
+    for_region<RW, RH>([&](int sx, int sy) {
+        const int x = X0 + sx, y = Y0 + sy;
         const bool in = inside(x, y);
         if (in && sx >= 2 && sx < 2 + 2 * TCX && sy >= 2 && sy < 2 + 2 * TCY) u[(size_t)x + (size_t)nx * y] = T.u2[sy][sx];
         float2 r = make_float2(0.f, 0.f);
@@ -389,27 +411,26 @@ __global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float om
             r = csub(T.b[sy][sx], tile_stencil<RW>(T.tc, T.u2, sx, sy, T.k2[sy][sx], o.bk, o.c, d));
         }
         T.u1[sy][sx] = r;
-    }
+    });
     __syncthreads();
     // full weighting on the owned coarse nodes: fine node 2I is region node 2(I - I0) + 3
     for (int q = threadIdx.x; q < TCX * TCY; q += blockDim.x) {
         const int cx = q % TCX, cy = q / TCX, I = I0 + cx, J = J0 + cy;
         if (I > ncx - 2 || J > ncy - 2) continue;
         const int sx = 2 * cx + 3, sy = 2 * cy + 3;
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int dj = -1; dj <= 1; dj++)
-#pragma unroll
-            for (int di = -1; di <= 1; di++) {
-                const float wgt = (di == 0 ? 0.5f : 0.25f) * (dj == 0 ? 0.5f : 0.25f);
-                acc = cadd(acc, cscale(T.u1[sy + dj][sx + di], wgt));
-            }
-        rc[(size_t)I + (size_t)ncx * J] = acc;
+        const float2 *r0 = &T.u1[sy - 1][sx], *r1 = &T.u1[sy][sx], *r2 = &T.u1[sy + 1][sx];
+        // (1,2,1)/4 along x on each of the three rows, then (1,2,1)/4 along y
+        const float2 a0 = cadd(cadd(r0[-1], r0[1]), cscale(r0[0], 2.f));
+        const float2 a1 = cadd(cadd(r1[-1], r1[1]), cscale(r1[0], 2.f));
+        const float2 a2 = cadd(cadd(r2[-1], r2[1]), cscale(r2[0], 2.f));
+        rc[(size_t)I + (size_t)ncx * J] = cscale(cadd(cadd(a0, a2), cscale(a1, 2.f)), 0.0625f);
     }
 }
 
 // u_out <- two omega-Jacobi sweeps of (u_in + P ec), on the owned fine nodes.  u_in and u_out
 // are different arrays: blocks read their halo of u_in while other blocks write u_out.
+// Bilinear interpolation in closed form: P ec at fine node (x, y) is the mean of the four
+// coarse values at (floor/ceil(x/2), floor/ceil(y/2)), coincident ones repeated.
 template <int TCX, int TCY>
 __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float omega, const float2 *__restrict__ b,
                                                        const float2 *__restrict__ u_in, float2 *__restrict__ u,
@@ -421,6 +442,8 @@ __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float om
     const int I0 = 1 + blockIdx.x * TCX, J0 = 1 + blockIdx.y * TCY;
     const int X0 = 2 * I0 - 3, Y0 = 2 * J0 - 3;
     const int nx = o.nx, ny = o.ny;
+    const bool full = X0 >= 1 && X0 + RW - 1 <= nx - 2 && Y0 >= 1 && Y0 + RH - 1 <= ny - 2;
+    auto inside = [&](int x, int y) { return full || (x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2); };
     // coarse nodes [I0 - 2, I0 + TCX + 1] cover floor/ceil(x / 2) for every region column
     const int C0 = I0 - 2, D0 = J0 - 2;
     tile_coef<RW, RH>(o, X0, Y0, T.tc);
@@ -428,40 +451,35 @@ __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float om
         const int cx = q % (TCX + 4), cy = q / (TCX + 4), I = C0 + cx, J = D0 + cy;
         T.ec[cy][cx] = (I >= 0 && I < ncx && J >= 0 && J < ncy) ? ec[(size_t)I + (size_t)ncx * J] : make_float2(0.f, 0.f);
     }
-    auto inside = [&](int x, int y) { return x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2; };
     __syncthreads();
     // u3 = u + P ec on the region
-    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
-        const int sx = q % RW, sy = q / RW, x = X0 + sx, y = Y0 + sy;
-        const bool in = inside(x, y);
-        const size_t p = (size_t)x + (size_t)nx * y;
-        T.b[sy][sx] = in ? b[p] : make_float2(0.f, 0.f);
-        T.k2[sy][sx] = in ? o.k2[p] : 0.f;
-        float2 v = make_float2(0.f, 0.f);
-        if (in) {
-            float2 acc = make_float2(0.f, 0.f);
-            int cnt = 0;
-            for (int jj = y >> 1; jj <= (y + 1) >> 1; jj++)
-                for (int ii = x >> 1; ii <= (x + 1) >> 1; ii++) {
-                    acc = cadd(acc, T.ec[jj - D0][ii - C0]);
-                    cnt++;
-                }
-            v = cadd(u_in[p], cscale(acc, 1.f / (float)cnt));
+    for_region<RW, RH>([&](int sx, int sy) {
+        const int x = X0 + sx, y = Y0 + sy;
+        float2 bv = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+        float kv = 0.f;
+        if (inside(x, y)) {
+            const size_t p = (size_t)x + (size_t)nx * y;
+            bv = b[p];
+            kv = o.k2[p];
+            const int xa = (x >> 1) - C0, xb = ((x + 1) >> 1) - C0, ya = (y >> 1) - D0, yb = ((y + 1) >> 1) - D0;
+            const float2 e = cadd(cadd(T.ec[ya][xa], T.ec[ya][xb]), cadd(T.ec[yb][xa], T.ec[yb][xb]));
+            v = cadd(u_in[p], cscale(e, 0.25f));
         }
+        T.b[sy][sx] = bv;
+        T.k2[sy][sx] = kv;
         T.u3[sy][sx] = v;
-    }
+    });
     __syncthreads();
     // sweep 1 on R3 shrunk by one
-    for (int q = threadIdx.x; q < RW * RH; q += blockDim.x) {
-        const int sx = q % RW, sy = q / RW;
+    for_region<RW, RH>([&](int sx, int sy) {
         float2 v = make_float2(0.f, 0.f);
         if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy)) {
             float2 d;
             const float2 mu = tile_stencil<RW>(T.tc, T.u3, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
-            v = cadd(T.u3[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv(d)), omega));
+            v = cadd(T.u3[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv_fast(d)), omega));
         }
         T.u4[sy][sx] = v;
-    }
+    });
     __syncthreads();
     // sweep 2 on the owned fine nodes
     for (int q = threadIdx.x; q < 4 * TCX * TCY; q += blockDim.x) {
@@ -469,7 +487,7 @@ __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float om
         if (!inside(x, y)) continue;
         float2 d;
         const float2 mu = tile_stencil<RW>(T.tc, T.u4, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
-        u[(size_t)x + (size_t)nx * y] = cadd(T.u4[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv(d)), omega));
+        u[(size_t)x + (size_t)nx * y] = cadd(T.u4[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv_fast(d)), omega));
     }
 }
 

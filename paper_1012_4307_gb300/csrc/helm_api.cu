@@ -414,8 +414,11 @@ extern "C" void helm_destroy(helm_handle *h) {
     for (void *p : h->owned) cudaFree(p);
     if (h->est_host) cudaFreeHost(h->est_host);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fn) cudaEventDestroy(h->ev_fn);
     if (h->ev_beta) cudaEventDestroy(h->ev_beta);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
 }
 
@@ -637,23 +640,24 @@ cudaError_t precondition(helm_handle *h, const double2 *v, typename CT<R>::T *z)
 template cudaError_t precondition<float>(helm_handle *, const double2 *, float2 *);
 template cudaError_t precondition<double>(helm_handle *, const double2 *, double2 *);
 
-// The same with v a float-pair vector (the double-FP32 Krylov basis): v is converted into
-// level 0's right-hand side in precision R, then one cycle from zero.
+// The same with v / alpha->x for a float-pair vector v (the double-FP32 Krylov basis; alpha
+// null: no scaling): converted into level 0's right-hand side in precision R, then one cycle
+// from zero.
 template <typename R>
-cudaError_t precondition_pair(helm_handle *h, const float4 *v, typename CT<R>::T *z) {
+cudaError_t precondition_pair(helm_handle *h, const float4 *v, const double2 *alpha, typename CT<R>::T *z) {
     typedef typename CT<R>::T C;
     const double es = sizeof(C);
     C *dst = h->mg.kind == HELM_PC_NONE ? z : LvBuf<R>::b(h->lv[0]);
     {
         ProfScope ps(h, HELM_K_VECTOR, h->np * (16 + es), 0);
-        if constexpr (sizeof(R) == sizeof(float)) CKE(launch_pair_to_c64(h->np, v, dst, h->stream));
-        else CKE(launch_pair_to_c128(h->np, v, dst, h->stream));
+        if constexpr (sizeof(R) == sizeof(float)) CKE(launch_pair_to_c64(h->np, v, alpha, dst, h->stream));
+        else CKE(launch_pair_to_c128(h->np, v, alpha, dst, h->stream));
     }
     if (h->mg.kind == HELM_PC_NONE) return cudaSuccess;
     return cycle<R>(h, 0, dst, z, true, h->mg.gamma_f, h->mg.gamma_c);
 }
-template cudaError_t precondition_pair<float>(helm_handle *, const float4 *, float2 *);
-template cudaError_t precondition_pair<double>(helm_handle *, const float4 *, double2 *);
+template cudaError_t precondition_pair<float>(helm_handle *, const float4 *, const double2 *, float2 *);
+template cudaError_t precondition_pair<double>(helm_handle *, const float4 *, const double2 *, double2 *);
 
 static helm_status check_ptr(const void *p, size_t align, const char *name) {
     if (!p) return helm_fail(HELM_ERR_ARG, "%s is null", name);

@@ -96,6 +96,9 @@ struct helm_handle {
     // delayed CGS2: inner products of a step (2 (m + 1)), normalisation norms alpha_j (m + 2),
     // update coefficients (2 m + 4); closing step of a cycle with jc columns: event and graph jc
     double2 *hv = nullptr, *alpha2 = nullptr, *dcoef = nullptr;
+    // side stream of a step (the Givens rotation runs beside the update pass): fork and join
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<cudaEvent_t> close_ev;
     std::vector<cudaGraphExec_t> close_graph;
     std::vector<cudaGraphExec_t> step_graph;
@@ -158,6 +161,7 @@ helm_status fgmres_begin(helm_handle *h, FgmresRun &r, const double2 *f, double2
 helm_status fgmres_advance(FgmresRun &r, bool block);
 template <typename R> cudaError_t precondition(helm_handle *h, const double2 *v, typename CT<R>::T *z);
 // v a float-pair vector (float4 (re.hi, re.lo, im.hi, im.lo) per node)
-template <typename R> cudaError_t precondition_pair(helm_handle *h, const float4 *v, typename CT<R>::T *z);
+template <typename R>
+cudaError_t precondition_pair(helm_handle *h, const float4 *v, const double2 *alpha, typename CT<R>::T *z);
 // First level of the fused coarse tail of a precision-R cycle under the handle's tuning (-1: none).
 template <typename R> int tail_top(const helm_handle *h);

@@ -189,9 +189,9 @@ cudaError_t launch_update2_pair(size_t n, float4 *V, size_t ldv, int j, const do
 cudaError_t launch_scale_inv_pair(size_t n, float4 *w, const double2 *beta, cudaStream_t s);
 // in place: the double2 vector x becomes the float-pair vector x / beta->x (beta null: 1)
 cudaError_t launch_split_scale(size_t n, void *x, const double2 *beta, cudaStream_t s);
-// float pairs -> complex64 (hi + lo rounded) / complex128 (exact)
-cudaError_t launch_pair_to_c64(size_t n, const float4 *v, float2 *z, cudaStream_t s);
-cudaError_t launch_pair_to_c128(size_t n, const float4 *v, double2 *z, cudaStream_t s);
+// float pairs / alpha->x -> complex64 / complex128 (alpha null: no scaling)
+cudaError_t launch_pair_to_c64(size_t n, const float4 *v, const double2 *alpha, float2 *z, cudaStream_t s);
+cudaError_t launch_pair_to_c128(size_t n, const float4 *v, const double2 *alpha, double2 *z, cudaStream_t s);
 // *hnorm: ||w||^2 in, ||w'|| out; *flag = (||w'|| < eta ||w||); *count += flag
 cudaError_t launch_reduce_decide(const double2 *partials, int nblk, double2 *hnorm, int *flag, int *count, double eta,
                                  cudaStream_t s);

@@ -259,9 +259,10 @@ __global__ void __launch_bounds__(NT) k_mdot2_pair(size_t n, const float4 *__res
 }
 
 // One pass of the DCGS2 update for step j with coefficients coef (see k_dcgs2_coef):
-//   x <- (x - sum_{i<j} V_i A_i) / nu          (x = basis slot j: its final vector v_j)
-//   w <- w - x_old s - sum_{i<j} V_i C_i       (w = slot j + 1: once orthogonalised)
-// with A = coef[0..j), C = coef[j..2j), 1/nu = coef[2j].x, s = coef[2j + 1];
+//   x <- (x - sum_{i<j} V_i A_i) r             (x = basis slot j: its final vector v_j)
+//   w <- w - x_old s - sum_{i<j} V_i C_i       (w = slot j + 1: once orthogonalised, not
+//                                                normalised)
+// with A = coef[0..j), C = coef[j..2j), r = coef[2j].x, s = coef[2j + 1];
 // partials[b] = (||w||^2, 0).
 __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
                                                      const double2 *__restrict__ coef, double2 *__restrict__ partials) {
@@ -372,17 +373,27 @@ __global__ void __launch_bounds__(NT) k_split_scale(size_t n, void *x, const dou
     }
 }
 
-// Float pairs to complex64 (hi + lo rounded once) or to complex128 (exact).
-__global__ void __launch_bounds__(NT) k_pair_to_c64(size_t n, const float4 *__restrict__ v, float2 *__restrict__ z) {
+// Float pairs to complex64 or complex128, divided by alpha->x (alpha null: no scaling).
+__device__ __forceinline__ double block_recip(const double2 *alpha) {
+    __shared__ double r;
+    if (threadIdx.x == 0) r = alpha ? 1.0 / alpha->x : 1.0;
+    __syncthreads();
+    return r;
+}
+__global__ void __launch_bounds__(NT) k_pair_to_c64(size_t n, const float4 *__restrict__ v, const double2 *alpha,
+                                                    float2 *__restrict__ z) {
+    const float r = (float)block_recip(alpha);
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const float4 a = v[q];
-        z[q] = make_float2(__fadd_rn(a.x, a.y), __fadd_rn(a.z, a.w));
+        z[q] = make_float2(__fmul_rn(__fadd_rn(a.x, a.y), r), __fmul_rn(__fadd_rn(a.z, a.w), r));
     }
 }
-__global__ void __launch_bounds__(NT) k_pair_to_c128(size_t n, const float4 *__restrict__ v, double2 *__restrict__ z) {
+__global__ void __launch_bounds__(NT) k_pair_to_c128(size_t n, const float4 *__restrict__ v, const double2 *alpha,
+                                                     double2 *__restrict__ z) {
+    const double r = block_recip(alpha);
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const float4 a = v[q];
-        z[q] = make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+        z[q] = make_double2(((double)a.x + (double)a.y) * r, ((double)a.z + (double)a.w) * r);
     }
 }
 
@@ -439,11 +450,11 @@ cudaError_t launch_split_scale(size_t n, void *x, const double2 *beta, cudaStrea
     k_split_scale<<<pair_grid(n), NT, 0, s>>>(n, x, beta);
     return cudaGetLastError();
 }
-cudaError_t launch_pair_to_c64(size_t n, const float4 *v, float2 *z, cudaStream_t s) {
-    k_pair_to_c64<<<pair_grid(n), NT, 0, s>>>(n, v, z);
+cudaError_t launch_pair_to_c64(size_t n, const float4 *v, const double2 *alpha, float2 *z, cudaStream_t s) {
+    k_pair_to_c64<<<pair_grid(n), NT, 0, s>>>(n, v, alpha, z);
     return cudaGetLastError();
 }
-cudaError_t launch_pair_to_c128(size_t n, const float4 *v, double2 *z, cudaStream_t s) {
-    k_pair_to_c128<<<pair_grid(n), NT, 0, s>>>(n, v, z);
+cudaError_t launch_pair_to_c128(size_t n, const float4 *v, const double2 *alpha, double2 *z, cudaStream_t s) {
+    k_pair_to_c128<<<pair_grid(n), NT, 0, s>>>(n, v, alpha, z);
     return cudaGetLastError();
 }

@@ -194,31 +194,35 @@ __global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, do
 
 // DCGS2 coefficients of step j (one thread; Swirydowicz, Langou, Ananthan, Yang & Thomas,
 // "Low synchronization Gram-Schmidt and GMRES algorithms", 2020; Bielich et al. 2022).
-// Basis slot j holds u, the once-orthogonalised and normalised vector of step j - 1.  From
-// hv[i] = V_i^H u (i <= j; hv[j] = u^H u) and, with has_w, hv[j + 1 + i] = V_i^H w (i <= j):
-//   u = sum_{i<j} a_i v_i + nu v_j,  a_i = hv[i],  nu = sqrt(u^H u - |a|^2)   (nu = 1 for j = 0,
-//   where slot 0 already holds the final v_0);
-//   column j - 1 of H, first-pass entries plus alpha_j a, gets its final values and
-//   H[j][j-1] = alpha_j nu  (alpha_j = alpha2[j].x, the norm u was normalised by);
-//   column j: c_i = hv[j+1+i] (i < j), H[j][j] = (v_j^H w) = (hv[2j+1] - a^H c) / nu;
-//   update coefficients coef[i] = a_i, coef[j+i] = c_i - a_i s, coef[2j] = 1/nu, coef[2j+1] = s
-//   with s = H[j][j] / nu  (w' = w - u s - sum V_i coef[j+i], v_j = (u - sum V_i a_i) / nu).
+// Basis slot j holds x = alpha u: the once-orthogonalised vector of step j - 1, not normalised
+// (alpha = alpha2[j].x its norm; slot 0 holds the final v_0 and alpha = 1).  From
+// hv[i] = V_i^H x (i <= j; hv[j] = x^H x) and, with has_w, hv[j + 1 + i] = V_i^H w (i <= j):
+//   u = sum_{i<j} a_i v_i + nu v_j,  a_i = hv[i] / alpha,  nu = sqrt(hv[j] / alpha^2 - |a|^2)
+//   (nu = 1 for j = 0, where slot 0 already holds the final v_0);
+//   column j - 1 of H, first-pass entries plus alpha a, gets its final values and
+//   H[j][j-1] = alpha nu;
+//   column j: c_i = hv[j+1+i] (i < j), H[j][j] = v_j^H w = (hv[2j+1] / alpha - a^H c) / nu;
+//   with s = H[j][j] / nu, the update pass forms v_j = (x - sum V_i (alpha a_i)) / (alpha nu)
+//   and w' = w - x (s / alpha) - sum V_i (c_i - a_i s): coef[i] = alpha a_i,
+//   coef[j+i] = c_i - a_i s, coef[2j] = 1 / (alpha nu), coef[2j+1] = s / alpha.
 __global__ void k_dcgs2_coef(int j, int has_w, const double2 *hv, const double2 *alpha2, double2 *H, int ldh,
                              double2 *coef) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double nu = 1.0;
+    double nu = 1.0, al = 1.0;
     if (j > 0) {
-        double n2 = hv[j].x;
-        for (int i = 0; i < j; i++) n2 -= hv[i].x * hv[i].x + hv[i].y * hv[i].y;
+        al = alpha2[j].x;
+        const double ra = 1.0 / al;
+        double n2 = hv[j].x * ra * ra;
+        for (int i = 0; i < j; i++) n2 -= (hv[i].x * hv[i].x + hv[i].y * hv[i].y) * (ra * ra);
         nu = sqrt(fmax(n2, 1e-300));
-        const double al = alpha2[j].x;
         double2 *col = H + (size_t)ldh * (j - 1);
-        for (int i = 0; i < j; i++) col[i] = cadd(col[i], cscale(hv[i], al));
+        for (int i = 0; i < j; i++) col[i] = cadd(col[i], hv[i]);  // alpha a_i = hv[i]
         col[j] = make_double2(al * nu, 0.0);
     }
     if (!has_w) return;
-    double2 t = hv[2 * j + 1];
-    for (int i = 0; i < j; i++) t = csub(t, cmul(make_double2(hv[i].x, -hv[i].y), hv[j + 1 + i]));
+    const double ra = 1.0 / al;
+    double2 t = cscale(hv[2 * j + 1], ra);
+    for (int i = 0; i < j; i++) t = csub(t, cmul(make_double2(hv[i].x * ra, -hv[i].y * ra), hv[j + 1 + i]));
     const double rn = 1.0 / nu;
     const double2 hjj = cscale(t, rn);
     double2 *col = H + (size_t)ldh * j;
@@ -227,10 +231,10 @@ __global__ void k_dcgs2_coef(int j, int has_w, const double2 *hv, const double2 
     const double2 sf = cscale(hjj, rn);
     for (int i = 0; i < j; i++) {
         coef[i] = hv[i];
-        coef[j + i] = csub(hv[j + 1 + i], cmul(hv[i], sf));
+        coef[j + i] = csub(hv[j + 1 + i], cmul(cscale(hv[i], ra), sf));
     }
-    coef[2 * j] = make_double2(rn, 0.0);
-    coef[2 * j + 1] = sf;
+    coef[2 * j] = make_double2(rn * ra, 0.0);
+    coef[2 * j + 1] = cscale(sf, ra);
 }
 
 __global__ void k_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y) {

@@ -124,6 +124,9 @@ static helm_status ensure_ws(helm_handle *h, int m) {
     if (!h->ev_fn) CKR(cudaEventCreateWithFlags(&h->ev_fn, cudaEventDisableTiming));
     if (!h->ev_beta) CKR(cudaEventCreateWithFlags(&h->ev_beta, cudaEventDisableTiming));
     if (!h->cap_stream) CKR(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    if (!h->side) CKR(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    if (!h->ev_fork) CKR(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    if (!h->ev_join) CKR(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     h->fnorm_dev = h->scal + 24;
     h->m_alloc = m;
     h->z_prec = zp;
@@ -186,17 +189,18 @@ static double interior_pts(const helm_handle *h) {
 static double apply_flops(const helm_handle *h) { return interior_pts(h) * (h->dim == 3 ? 68.0 : 48.0); }
 
 // Double-FP32 Arnoldi (gs_arith = DF): the basis vectors are float-pair vectors.
-// z = precondition(v) in the workspace precision; w = A z as a float-pair vector.
-static cudaError_t precond_apply_pair(helm_handle *h, const float4 *v, void *z, float4 *w) {
+// z = precondition(v / alpha->x) in the workspace precision (alpha null: v); w = A z as a
+// float-pair vector.
+static cudaError_t precond_apply_pair(helm_handle *h, const float4 *v, const double2 *alpha, void *z, float4 *w) {
     cudaError_t e;
     const double ni = interior_pts(h);
     if (h->z_prec == HELM_C64) {
-        e = precondition_pair<float>(h, v, (float2 *)z);
+        e = precondition_pair<float>(h, v, alpha, (float2 *)z);
         if (e != cudaSuccess) return e;
         ProfScope ps(h, HELM_K_APPLY, ni * (8 + 8 + 16), 0);
         return launch_apply_A_df(h->Adf, h->dim, (const float2 *)z, w, h->stream);
     }
-    e = precondition_pair<double>(h, v, (double2 *)z);
+    e = precondition_pair<double>(h, v, alpha, (double2 *)z);
     if (e != cudaSuccess) return e;
     {
         ProfScope ps(h, HELM_K_APPLY, ni * (16 + 8 + 16), apply_flops(h));
@@ -256,7 +260,7 @@ static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
     };
     double2 *vj = h->V + (size_t)j * np, *w = h->V + (size_t)(j + 1) * np;
     void *zj = (char *)h->Z + (size_t)j * np * zsz;
-    if (df) CKE(precond_apply_pair(h, (const float4 *)vj, zj, (float4 *)w));
+    if (df) CKE(precond_apply_pair(h, (const float4 *)vj, nullptr, zj, (float4 *)w));
     else CKE(precond_apply(h, vj, zj, w));
     double2 *hcol = h->H + (size_t)ldh * j;
     const double nv = j + 1;
@@ -323,14 +327,15 @@ static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
                         : cudaEventRecord(h->step_ev[j], s);
 }
 
-// Delayed CGS2 step j (gs_arith = DCGS2; float-pair basis).  Basis slot j holds u_j, the
-// once-orthogonalised vector of step j - 1 normalised by alpha_j (slot 0: the final v_0).
-//   z_j = cycle(u_j); w = A z_j                                  (slot j + 1)
-//   one pass: V_i^H u_j and V_i^H w for i <= j                    (k_mdot2_pair)
-//   coefficients: finish column j - 1 of H (reorthogonalisation of u_j), first-pass column j,
-//   then the Givens rotation of column j - 1 and its residual estimate est[j - 1]
+// Delayed CGS2 step j (gs_arith = DCGS2; float-pair basis).  Basis slot j holds x_j = alpha_j
+// u_j, the once-orthogonalised vector of step j - 1 (not normalised: alpha_j = ||x_j|| is in
+// alpha2[j], and the division by it is folded into the next consumers; slot 0 holds v_0).
+//   z_j = cycle(x_j / alpha_j); w = A z_j                        (slot j + 1)
+//   one pass: V_i^H x_j and V_i^H w for i <= j                    (k_mdot2_pair)
+//   coefficients: finish column j - 1 of H (reorthogonalisation of u_j), first-pass column j;
+//   the Givens rotation of column j - 1 and its residual estimate est[j - 1] run on a side
+//   stream beside the update pass
 //   one pass: slot j <- v_j (final), slot j + 1 <- w orthogonalised once; alpha_{j+1} = ||w||
-//   slot j + 1 <- w / alpha_{j+1} = u_{j+1}
 // Only column j - 1 of H, the first-pass column j, rotation j - 1, g[j-1..j], slots j and j + 1
 // and z_j are written, so a step queued ahead of the host's decision never disturbs columns
 // 0 .. j - 2 that a solution update may use.
@@ -343,7 +348,7 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
     float4 *u = V4 + (size_t)j * np, *w = V4 + (size_t)(j + 1) * np;
     void *zj = (char *)h->Z + (size_t)j * np * zsz;
     const double nv = j + 1;
-    CKE(precond_apply_pair(h, u, zj, w));
+    CKE(precond_apply_pair(h, u, j > 0 ? h->alpha2 + j : nullptr, zj, w));
     {
         ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (nv + 1), 0);
         CKE(launch_mdot2_pair(np, V4, np, j + 1, u, w, h->partials, s));
@@ -352,7 +357,18 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
         CKE(launch_reduce(h->partials, gs_df_nblocks(np), 2 * (j + 1), h->hv, 0, nullptr, s));
         CKE(launch_dcgs2_coef(j, 1, h->hv, h->alpha2, h->H, ldh, h->dcoef, s));
-        if (j > 0) CKE(launch_givens(h->H, ldh, j - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, s));
+    }
+    const bool fork = j > 0 && !h->prof.on;
+    if (j > 0) {
+        // column j - 1 is final: its rotation on the side stream (inline while timing launches)
+        cudaStream_t gs = fork ? h->side : s;
+        if (fork) {
+            CKE(cudaEventRecord(h->ev_fork, s));
+            CKE(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        }
+        ProfScope ps(h, HELM_K_SMALL, 0, 0);
+        CKE(launch_givens(h->H, ldh, j - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, gs));
+        if (fork) CKE(cudaEventRecord(h->ev_join, h->side));
     }
     {
         ProfScope ps(h, HELM_K_UPDATE_NORM, np * 16.0 * (nv + 3), 0);
@@ -362,17 +378,14 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
         CKE(launch_reduce(h->partials, gs_df_update_nblocks(np), 1, h->alpha2 + j + 1, 2, nullptr, s));
     }
-    {
-        ProfScope ps(h, HELM_K_VECTOR, np * 32.0, 0);
-        CKE(launch_scale_inv_pair(np, w, h->alpha2 + j + 1, s));
-    }
+    if (fork) CKE(cudaStreamWaitEvent(s, h->ev_join, 0));
     if (j > 0) CKE(cudaMemcpyAsync(h->est_host + j - 1, h->est_dev + j - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     return h->capturing ? cudaEventRecordWithFlags(h->step_ev[j], s, cudaEventRecordExternal)
                         : cudaEventRecord(h->step_ev[j], s);
 }
 
-// Closing step of a delayed-CGS2 cycle with jc columns: reorthogonalise u_jc against
-// v_0 .. v_{jc-1} only to finish column jc - 1 of H, then its rotation and est[jc - 1].
+// Closing step of a delayed-CGS2 cycle with jc columns: the inner products of x_jc with
+// v_0 .. v_{jc-1} only finish column jc - 1 of H, then its rotation and est[jc - 1].
 static cudaError_t fgmres_close_dcgs2(helm_handle *h, int jc, int m) {
     const size_t np = h->np;
     const int ldh = m + 1;

@@ -202,7 +202,11 @@ __global__ void __launch_bounds__(NT) k_update_norm_pair(size_t n, const float4 
 
 // ---------------------------------------------------------------- delayed CGS2 (DCGS2)
 // partials[i * G + b] = V_i^H x and partials[(nv + i) * G + b] = V_i^H w for i < nv: one pass
-// over the basis for two right-hand vectors (x is itself basis slot nv - 1).
+// over the basis for two right-hand vectors (x is itself basis slot nv - 1).  V^H x decides
+// the final basis vector (the reorthogonalisation) and is double-FP32; V^H w only forms the
+// first-pass Hessenberg column, whose error the next step's double-FP32 reorthogonalisation
+// measures and adds to H (the update that uses it is double-FP32, so A z_j stays exactly
+// expanded in the basis), so it is formed from the hi parts in FP32.
 template <int CH>
 __global__ void __launch_bounds__(NT) k_mdot2_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
                                                    const float4 *__restrict__ x, const float4 *__restrict__ w,
@@ -210,44 +214,43 @@ __global__ void __launch_bounds__(NT) k_mdot2_pair(size_t n, const float4 *__res
     __shared__ double sums[4 * CH];
     const int i0 = blockIdx.y * CH;
     const int cnt = min(CH, nv - i0);
-    float s[2][CH][4];  // [rhs][basis][re.s, re.c, im.s, im.c]
+    float s[CH][4];   // V^H x: [basis][re.s, re.c, im.s, im.c]
+    float f[CH][2];   // V^H w in FP32: [basis][re, im]
 #pragma unroll
-    for (int r = 0; r < 2; r++)
+    for (int t = 0; t < CH; t++) {
 #pragma unroll
-        for (int t = 0; t < CH; t++)
-#pragma unroll
-            for (int k = 0; k < 4; k++) s[r][t][k] = 0.f;
+        for (int k = 0; k < 4; k++) s[t][k] = 0.f;
+        f[t][0] = f[t][1] = 0.f;
+    }
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const float4 xq = x[q], wq = w[q];
         float4 vq[CH];
 #pragma unroll
         for (int t = 0; t < CH; t++) vq[t] = t < cnt ? V[(size_t)(i0 + t) * ldv + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const ff xr = ff_re(xq), xi = ff_im(xq), wr = ff_re(wq), wi = ff_im(wq);
+        const ff xr = ff_re(xq), xi = ff_im(xq);
 #pragma unroll
         for (int t = 0; t < CH; t++) {
             if (t < cnt) {
                 const ff vr = ff_re(vq[t]), vi = ff_im(vq[t]);
                 float p, e;
-                // conj(v) y = (vr yr + vi yi) + i (vr yi - vi yr), y = x then w
-                ff_two_prod(vr, xr, p, e); ff_acc_prod(s[0][t][0], s[0][t][1], p, e);
-                ff_two_prod(vi, xi, p, e); ff_acc_prod(s[0][t][0], s[0][t][1], p, e);
-                ff_two_prod(vr, xi, p, e); ff_acc_prod(s[0][t][2], s[0][t][3], p, e);
-                ff_two_prod(vi, xr, p, e); ff_acc_prod(s[0][t][2], s[0][t][3], -p, -e);
-                ff_two_prod(vr, wr, p, e); ff_acc_prod(s[1][t][0], s[1][t][1], p, e);
-                ff_two_prod(vi, wi, p, e); ff_acc_prod(s[1][t][0], s[1][t][1], p, e);
-                ff_two_prod(vr, wi, p, e); ff_acc_prod(s[1][t][2], s[1][t][3], p, e);
-                ff_two_prod(vi, wr, p, e); ff_acc_prod(s[1][t][2], s[1][t][3], -p, -e);
+                // conj(v) x = (vr xr + vi xi) + i (vr xi - vi xr)
+                ff_two_prod(vr, xr, p, e); ff_acc_prod(s[t][0], s[t][1], p, e);
+                ff_two_prod(vi, xi, p, e); ff_acc_prod(s[t][0], s[t][1], p, e);
+                ff_two_prod(vr, xi, p, e); ff_acc_prod(s[t][2], s[t][3], p, e);
+                ff_two_prod(vi, xr, p, e); ff_acc_prod(s[t][2], s[t][3], -p, -e);
+                f[t][0] = __fmaf_rn(vq[t].x, wq.x, __fmaf_rn(vq[t].z, wq.z, f[t][0]));
+                f[t][1] = __fmaf_rn(vq[t].x, wq.z, __fmaf_rn(-vq[t].z, wq.x, f[t][1]));
             }
         }
     }
     ff vals[4 * CH];
 #pragma unroll
-    for (int r = 0; r < 2; r++)
-#pragma unroll
-        for (int t = 0; t < CH; t++) {
-            vals[(r * CH + t) * 2] = ff_norm(s[r][t][0], s[r][t][1]);
-            vals[(r * CH + t) * 2 + 1] = ff_norm(s[r][t][2], s[r][t][3]);
-        }
+    for (int t = 0; t < CH; t++) {
+        vals[2 * t] = ff_norm(s[t][0], s[t][1]);
+        vals[2 * t + 1] = ff_norm(s[t][2], s[t][3]);
+        vals[2 * (CH + t)] = ff{f[t][0], 0.f};
+        vals[2 * (CH + t) + 1] = ff{f[t][1], 0.f};
+    }
     block_sum_ff<4 * CH>(vals, sums);
     __syncthreads();
     const int G = gridDim.x;

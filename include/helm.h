@@ -286,7 +286,7 @@ helm_status helm_profile_read(helm_handle *h, int ncls, int *launches, double *m
  *                  transfer launches (HELM_TILE_NONE).  Ignored where it does not apply (other
  *                  smoothers, complex128 cycles, 3D, levels inside the tail, grids the tile
  *                  does not fit: those use the separate launches).
- * Default: tail_levels = -1 and HELM_TILE_32x8 on every level. */
+ * Default: tail_levels = -1, HELM_TILE_32x8 on every level, cluster_levels = 0 (16 blocks). */
 #define HELM_MAX_LEVELS 16
 typedef enum {
     HELM_TILE_NONE = -1,
@@ -299,11 +299,17 @@ typedef enum {
 typedef struct {
     int tail_levels;
     int level_tile[HELM_MAX_LEVELS];
+    int cluster_levels;  /* 2D complex64: the coarsest levels (>= 2, 0 = off) in one launch of a
+                            thread-block cluster, every level in distributed shared memory;
+                            takes precedence over tail_levels; clamped to what fits (200 KB per
+                            block, at most 6 levels) */
+    int cluster_ctas;    /* blocks (SMs) of that cluster: 8 or 16 */
 } helm_tuning;
 
 /* Sets / reads the handle's tuning (host struct).  Setting drops the handle's captured CUDA
  * graphs (they are re-captured on next use).  Errors: HELM_ERR_ARG (null pointers, a tile
- * index out of range, tail_levels < -1 or == 1). */
+ * index out of range, tail_levels < -1 or == 1, cluster_levels < 0 or == 1, cluster_ctas not
+ * 8 or 16). */
 helm_status helm_set_tuning(helm_handle *h, const helm_tuning *t);
 helm_status helm_get_tuning(const helm_handle *h, helm_tuning *t);
 

@@ -376,6 +376,24 @@ helm_status helm_create_impl(const helm_grid *grid, double theta, const double *
     }
     h->tune.tail_levels = -1;
     for (int l = 0; l < HELM_MAX_LEVELS; l++) h->tune.level_tile[l] = HELM_TILE_32x8;
+    h->tune.cluster_levels = 0;
+    h->tune.cluster_ctas = 16;
+    // how many coarsest levels a cluster tail can hold (2D only)
+    if (mg->kind != HELM_PC_NONE && dim == 2) {
+        const int nlev = (int)h->lv.size();
+        for (int k = 0; k < 2; k++) {
+            const int nc = k ? 16 : 8;
+            int fit = 0;
+            for (int nt = 2; nt <= std::min(nlev, MAX_CT_LEVELS); nt++) {
+                int n[MAX_CT_LEVELS][3];
+                for (int q = 0; q < nt; q++)
+                    for (int a = 0; a < 3; a++) n[q][a] = h->lv[nlev - nt + q].n[a];
+                unsigned off[MAX_CT_LEVELS][6], obc, oz;
+                if (mg_ctail_layout(nt, n, nc, h->nu_c, off, &obc, &oz) <= CT_SMEM_BYTES) fit = nt;
+            }
+            h->ctail_fit[k] = fit;
+        }
+    }
     CKC(cudaStreamSynchronize(s));
     *out = h;
     return HELM_OK;
@@ -545,6 +563,15 @@ template <typename R> int tail_top(const helm_handle *h) {
 template int tail_top<float>(const helm_handle *);
 template int tail_top<double>(const helm_handle *);
 
+int ctail_top(const helm_handle *h) {
+    const int want = h->tune.cluster_levels;
+    if (h->dim != 2 || want < 2 || h->mg.kind == HELM_PC_NONE) return -1;
+    const int fit = h->ctail_fit[h->tune.cluster_ctas == 16 ? 1 : 0];
+    const int nt = std::min(want, fit);
+    if (nt < 2) return -1;
+    return (int)h->lv.size() - nt;
+}
+
 template <typename R>
 static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, typename CT<R>::T *u, bool zero, int gf,
                          int gc) {
@@ -552,6 +579,22 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
     LevelDev &L = h->lv[l];
     const int last = (int)h->lv.size() - 1;
     if (l == last) return coarse_solve<R>(h, L, b, u);
+    if constexpr (sizeof(R) == sizeof(float)) {
+        if (l == ctail_top(h)) {
+            // levels l..last in one launch of a thread-block cluster
+            const int nt = last - l + 1;
+            DevOp<float> ops[MAX_CT_LEVELS];
+            double bytes = 0;
+            for (int k = 0; k < nt; k++) {
+                ops[k] = h->lv[l + k].M32;
+                bytes += interior(h->lv[l + k], h->dim) * sizeof(float2) * 8.0;
+            }
+            ProfScope ps(h, HELM_K_COARSE, bytes + (double)h->nu_c * h->nu_c * sizeof(float2), 0);
+            return launch_mg_ctail(nt, ops, b, u, h->minv32, h->nu_c, h->mg.nu1, h->mg.nu2,
+                                   h->mg.smoother == HELM_SMOOTH_RB, (float)h->mg.omega, zero ? 1 : 0, gf, gc,
+                                   h->tune.cluster_ctas, h->stream);
+        }
+    }
     if (l == tail_top<R>(h)) {
         // levels l..last in one fused single-block launch
         const int nt = last - l + 1;

@@ -71,6 +71,7 @@ struct helm_handle {
     // the tail's vectors fit in shared memory
     int tail_top32 = -1, tail_top64 = -1;  // first level of the fused tail (-1: none), as built
     helm_tuning tune{};                      // kernel choices (see helm_set_tuning)
+    int ctail_fit[2] = {0, 0};               // most coarsest levels a cluster tail of 8 / 16 blocks holds
     int nu_c = 0;
     double2 *minv64 = nullptr;
     float2 *minv32 = nullptr;
@@ -165,3 +166,5 @@ template <typename R>
 cudaError_t precondition_pair(helm_handle *h, const float4 *v, const double2 *alpha, typename CT<R>::T *z);
 // First level of the fused coarse tail of a precision-R cycle under the handle's tuning (-1: none).
 template <typename R> int tail_top(const helm_handle *h);
+// First level of the cluster tail (2D complex64 cycles) under the handle's tuning (-1: none).
+int ctail_top(const helm_handle *h);

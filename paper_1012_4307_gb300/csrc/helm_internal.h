@@ -145,6 +145,19 @@ template <typename R>
 cudaError_t launch_mg_tail(int dim, int nlev, const DevOp<R> *ops, typename CT<R>::T *const *b,
                            typename CT<R>::T *const *u, typename CT<R>::T *const *t, const typename CT<R>::T *minv,
                            int nu_c, int nu1, int nu2, int rb, R omega, int gf, int gc, int zero, cudaStream_t s);
+// Cluster tail (kernels_ctail.cu): the coarsest nlev levels of a 2D complex64 cycle in one
+// launch of a cluster of nc = 8 or 16 thread blocks, every level in distributed shared memory
+// (rows split into slabs).  b_top / u_top: the first of those levels' right-hand side and result
+// (global; u_top is the initial guess unless zero).
+constexpr int MAX_CT_LEVELS = 6;
+constexpr size_t CT_SMEM_BYTES = 200 * 1024;
+size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (*off)[6], unsigned *obc,
+                       unsigned *ozero);
+cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_top, float2 *u_top,
+                            const float2 *minv, int nu_c, int nu1, int nu2, int rb, float omega, int zero, int gf,
+                            int gc, int nc, cudaStream_t s);
+int mg_ctail_max_clusters(int nc, size_t bytes);
+
 template <typename CI, typename CO>
 cudaError_t launch_convert(size_t n, const CI *in, CO *out, cudaStream_t s);
 template <typename C>

@@ -1,6 +1,7 @@
 // Cycle tuning: which kernels carry out Algorithm 1 on each level (temporally blocked tiles or
 // separate sweep / residual / transfer launches, and how many coarse levels go into the fused
-// single-block tail), and an autotuner that times the choices on the device.  The arithmetic
+// single-block tail or the thread-block-cluster tail), and an autotuner that times the choices
+// on the device.  The arithmetic
 // of the cycle does not depend on the choice (up to FP32 rounding order).
 #include <algorithm>
 #include <vector>
@@ -31,6 +32,8 @@ __global__ void k_fill_probe(size_t n, double2 *v) {
 
 bool tuning_valid(const helm_tuning &t) {
     if (t.tail_levels < -1 || t.tail_levels == 1) return false;
+    if (t.cluster_levels < 0 || t.cluster_levels == 1) return false;
+    if (t.cluster_ctas != 8 && t.cluster_ctas != 16) return false;
     for (int l = 0; l < HELM_MAX_LEVELS; l++)
         if (t.level_tile[l] < HELM_TILE_NONE || t.level_tile[l] >= HELM_TILE_COUNT) return false;
     return true;
@@ -40,7 +43,7 @@ bool tuning_valid(const helm_tuning &t) {
 
 extern "C" helm_status helm_set_tuning(helm_handle *h, const helm_tuning *t) {
     if (!h || !t) return helm_fail(HELM_ERR_ARG, "null argument");
-    if (!tuning_valid(*t)) return helm_fail(HELM_ERR_ARG, "invalid tuning (tail_levels or a tile index)");
+    if (!tuning_valid(*t)) return helm_fail(HELM_ERR_ARG, "invalid tuning (tail or cluster levels, cluster blocks, or a tile)");
     h->tune = *t;
     helm_drop_graphs(h);
     return HELM_OK;
@@ -76,12 +79,18 @@ extern "C" helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, h
         st = helm_fail(HELM_ERR_CUDA, "autotune %s: %s", what, cudaGetErrorString(e));
         return -1.0;
     };
-    // milliseconds per preconditioner application under tuning t (best of three timings)
-    auto time_it = [&](const helm_tuning &t) -> double {
+    // milliseconds per preconditioner application under tuning t (best of three timings); a
+    // candidate whose first launch is refused (soft: a cluster shape the device cannot run)
+    // is skipped
+    auto time_it = [&](const helm_tuning &t, bool soft = false) -> double {
         h->tune = t;
         cudaError_t e = cudaSuccess;
         for (int w = 0; w < 2 && e == cudaSuccess; w++)
             e = c64 ? precondition<float>(h, v, (float2 *)z) : precondition<double>(h, v, (double2 *)z);
+        if (e != cudaSuccess && soft) {
+            cudaGetLastError();
+            return -2.0;
+        }
         if (e != cudaSuccess) return fail(e, "warm-up");
         double bestt = 1e300;
         for (int rep = 0; rep < 3; rep++) {
@@ -114,6 +123,32 @@ extern "C" helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, h
             if (ms >= 0 && ms < cur_ms) { cur = t; cur_ms = ms; }
         }
     };
+    // cluster tail (2D complex64): off, or 2 .. the levels that fit, on 8 or 16 blocks
+    auto tune_cluster = [&]() {
+        if (!(c64 && h->dim == 2)) return;
+        for (int k = 0; k < 2 && st == HELM_OK; k++) {
+            const int nc = k ? 16 : 8;
+            for (int cl = 2; cl <= h->ctail_fit[k] && st == HELM_OK; cl++) {
+                if (cl == cur.cluster_levels && nc == cur.cluster_ctas) continue;
+                int n[MAX_CT_LEVELS][3];
+                for (int q = 0; q < cl; q++)
+                    for (int a = 0; a < 3; a++) n[q][a] = h->lv[last - cl + 1 + q].n[a];
+                unsigned off[MAX_CT_LEVELS][6], obc, oz;
+                if (mg_ctail_max_clusters(nc, mg_ctail_layout(cl, n, nc, h->nu_c, off, &obc, &oz)) < 1) continue;
+                helm_tuning t = cur;
+                t.cluster_levels = cl;
+                t.cluster_ctas = nc;
+                const double ms = time_it(t, true);
+                if (ms >= 0 && ms < cur_ms) { cur = t; cur_ms = ms; }
+            }
+        }
+        if (cur.cluster_levels > 0 && st == HELM_OK) {  // and without it
+            helm_tuning t = cur;
+            t.cluster_levels = 0;
+            const double ms = time_it(t);
+            if (ms >= 0 && ms < cur_ms) { cur = t; cur_ms = ms; }
+        }
+    };
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         st = helm_fail(HELM_ERR_CUDA, "autotune events");
     } else {
@@ -125,11 +160,15 @@ extern "C" helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, h
             cur_ms = time_it(cur);
         }
         if (st == HELM_OK) tune_tail();
-        // per level above the tail, greedily from the finest: separate launches or a tile shape
+        if (st == HELM_OK) tune_cluster();
+        // per level above the tails, greedily from the finest: separate launches or a tile shape
         if (blockable) {
             h->tune = cur;
-            const int top = tail_top<float>(h);
-            const int stop = std::min(top < 0 ? last : top, HELM_MAX_LEVELS);
+            const int top = tail_top<float>(h), ctop = ctail_top(h);
+            int stop = last;
+            if (top >= 0) stop = std::min(stop, top);
+            if (ctop >= 0) stop = std::min(stop, ctop);
+            stop = std::min(stop, HELM_MAX_LEVELS);
             for (int l = 0; l < stop && st == HELM_OK; l++) {
                 for (int tile = HELM_TILE_NONE; tile < HELM_TILE_COUNT && st == HELM_OK; tile++) {
                     if (tile == cur.level_tile[l]) continue;
@@ -140,7 +179,8 @@ extern "C" helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, h
                     if (ms >= 0 && ms < cur_ms) { cur = t; cur_ms = ms; }
                 }
             }
-            if (st == HELM_OK) tune_tail();  // the levels' choices may move the best depth
+            if (st == HELM_OK) tune_tail();  // the levels' choices may move the best depths
+            if (st == HELM_OK) tune_cluster();
         }
     }
     if (e0) cudaEventDestroy(e0);

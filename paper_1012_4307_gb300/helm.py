@@ -63,7 +63,8 @@ _TILE_NAMES = {v: k for k, v in TILES.items()}
 
 
 class _Tuning(C.Structure):
-    _fields_ = [("tail_levels", C.c_int), ("level_tile", C.c_int * HELM_MAX_LEVELS)]
+    _fields_ = [("tail_levels", C.c_int), ("level_tile", C.c_int * HELM_MAX_LEVELS),
+                ("cluster_levels", C.c_int), ("cluster_ctas", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -374,12 +375,14 @@ def helm_profile_read(h: Handle) -> dict:
 
 
 def _tuning_to_dict(t: _Tuning, nlev: int) -> dict:
-    return {"tail_levels": t.tail_levels, "level_tile": [_TILE_NAMES[t.level_tile[l]] for l in range(nlev)]}
+    return {"tail_levels": t.tail_levels, "level_tile": [_TILE_NAMES[t.level_tile[l]] for l in range(nlev)],
+            "cluster_levels": t.cluster_levels, "cluster_ctas": t.cluster_ctas}
 
 
 def helm_get_tuning(h: Handle) -> dict:
-    """The handle's kernel choices: tail_levels (-1 = as many as fit) and a tile name per level
-    ("none" = separate sweep / residual / transfer launches)."""
+    """The handle's kernel choices: tail_levels (-1 = as many as fit), a tile name per level
+    ("none" = separate sweep / residual / transfer launches), cluster_levels (0 = off) and
+    cluster_ctas (8 or 16)."""
     t = _Tuning()
     _check(load().helm_get_tuning(h.ptr, C.byref(t)))
     return _tuning_to_dict(t, len(h.levels))
@@ -391,6 +394,8 @@ def helm_set_tuning(h: Handle, tuning: dict):
     t.tail_levels = int(tuning.get("tail_levels", t.tail_levels))
     for l, name in enumerate(tuning.get("level_tile", [])[:HELM_MAX_LEVELS]):
         t.level_tile[l] = TILES[name]
+    t.cluster_levels = int(tuning.get("cluster_levels", t.cluster_levels))
+    t.cluster_ctas = int(tuning.get("cluster_ctas", t.cluster_ctas))
     _check(load().helm_set_tuning(h.ptr, C.byref(t)))
 
 

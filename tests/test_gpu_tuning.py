@@ -41,10 +41,16 @@ def test_every_tuning_is_the_same_cycle(helm, oracle, n):
                for tile in ("none", "32x8", "16x16", "16x8", "64x4")]
     mixed = ["64x4", "none", "16x8", "16x16", "32x8", "none"]
     choices.append(dict(tail_levels=-1, level_tile=[mixed[l % len(mixed)] for l in range(nlev)]))
+    # thread-block-cluster tails over the coarsest 2 .. 5 levels, 8 or 16 blocks
+    for cl in (2, 3, 4, 5):
+        for nc in (8, 16):
+            choices.append(dict(tail_levels=0, level_tile=["16x8"] * nlev, cluster_levels=cl, cluster_ctas=nc))
     for c in choices:
+        c.setdefault("cluster_levels", 0)
+        c.setdefault("cluster_ctas", 16)
         helm.helm_set_tuning(h, c)
         got = helm.helm_get_tuning(h)
-        assert got["tail_levels"] == c["tail_levels"] and got["level_tile"] == c["level_tile"]
+        assert got == c
         z = to_np(helm.mg_precondition(h, vg))
         assert rel_l2(z, ref) <= 2e-5, c
 
@@ -78,3 +84,24 @@ def test_set_tuning_rejects_bad_values(helm):
         helm.helm_set_tuning(h, dict(tail_levels=1))
     with pytest.raises(helm.HelmError):
         helm.helm_set_tuning(h, dict(tail_levels=-2))
+    with pytest.raises(helm.HelmError):
+        helm.helm_set_tuning(h, dict(cluster_levels=1))
+    with pytest.raises(helm.HelmError):
+        helm.helm_set_tuning(h, dict(cluster_levels=2, cluster_ctas=4))
+
+
+@pytest.mark.parametrize("smoother,nu,gamma", [("rb", (1, 1), (1, 2)), ("jacobi", (1, 2), (2, 2)), ("jacobi", (0, 1), (1, 1))])
+def test_cluster_tail_general_cycles(helm, oracle, smoother, nu, gamma):
+    """The cluster tail follows Algorithm 1 for red-black smoothing, W/F cycles and uneven
+    sweep counts too (checked against the oracle's cycle, complex64 tolerance)."""
+    P = problem(129)
+    h = gpu_handle(helm, P, pc="csl", prec="c64", smoother=smoother, nu=nu, gamma=gamma, omega=0.8)
+    A, M = oracle_pair(oracle, P, pc="csl")
+    mg = oracle.MG(M, P.coarsest_n, nu[0], nu[1], 0.8, smoother)
+    v = W.random_field(P.k2.shape, 43)
+    ref = mg.cycle(v, None, *gamma)
+    nlev = len(h.levels)
+    for cl in (2, 3, nlev):
+        helm.helm_set_tuning(h, dict(tail_levels=0, level_tile=["none"] * nlev, cluster_levels=cl, cluster_ctas=8))
+        z = to_np(helm.mg_precondition(h, to_gpu(v)))
+        assert rel_l2(z, ref) <= 2e-5, cl

@@ -256,8 +256,9 @@ helm_status helm_batch_handle(helm_batch *b, int i, helm_handle **out);
  * four host arrays hold ncls entries (ncls <= HELM_K_NCLASS). */
 typedef enum {
     HELM_K_APPLY = 0,         /* FP64 operator apply (A z, true residual)                */
-    HELM_K_SMOOTH_FINE = 1,   /* smoothing sweeps on the finest level                    */
-    HELM_K_SMOOTH_COARSE = 2, /* smoothing sweeps on the coarser levels                  */
+    HELM_K_SMOOTH_FINE = 1,   /* smoothing sweeps on the finest level (blocked kernels:  */
+                              /* with their residual, restriction and prolongation)      */
+    HELM_K_SMOOTH_COARSE = 2, /* the same on the coarser levels                          */
     HELM_K_RESTRICT = 3,      /* residual + full-weighting restriction                   */
     HELM_K_PROLONG = 4,       /* bi/trilinear prolongation + correction                  */
     HELM_K_COARSE = 5,        /* exact coarsest solve                                    */

@@ -623,7 +623,7 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
             fused_jacobi2_ok(L.n, h->dim, tile)) {
             LevelDev &Lc = h->lv[l + 1];
             {
-                ProfScope ps(h, HELM_K_SMOOTH_FINE, ni * (es + rs + es + es / nd), 0);
+                ProfScope ps(h, l == 0 ? HELM_K_SMOOTH_FINE : HELM_K_SMOOTH_COARSE, ni * (es + rs + es + es / nd), 0);
                 CKE(launch_pre2_restrict(L.M32, tile, (float)h->mg.omega, b, L.t32, Lc.b32, h->stream));
             }
             float2 *ec = Lc.u32;
@@ -635,7 +635,7 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
                     else CKE(cycle<R>(h, l + 1, Lc.b32, ec, false, gc, gf));
                 }
             }
-            ProfScope ps(h, HELM_K_SMOOTH_FINE, ni * (es + es / nd + es + rs + es), 0);
+            ProfScope ps(h, l == 0 ? HELM_K_SMOOTH_FINE : HELM_K_SMOOTH_COARSE, ni * (es + es / nd + es + rs + es), 0);
             return launch_prolong_post2(L.M32, tile, (float)h->mg.omega, b, L.t32, u, ec, h->stream);
         }
     }

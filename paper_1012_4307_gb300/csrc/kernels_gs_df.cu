@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(NT) k_mdot2_pair(size_t n, const float4 *__res
 __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
                                                      const double2 *__restrict__ coef, double2 *__restrict__ partials) {
     __shared__ float4 cA[64], cC[64];
-    __shared__ float4 sc[2];  // (1/nu hi, lo, 0, 0), s
+    __shared__ float4 sc[2];  // (r hi, lo, 0, 0), s
     __shared__ double sums[1];
     for (int i = threadIdx.x; i < j; i += NT) {
         const ff a = ff_split(coef[i].x), b = ff_split(coef[i].y);
@@ -287,44 +287,60 @@ __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restric
     __syncthreads();
     float4 *x = V + (size_t)j * ldv, *w = V + (size_t)(j + 1) * ldv;
     const ff rinv = ff_re(sc[0]), sr = ff_re(sc[1]), si = ff_im(sc[1]);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float sn = 0.f, cn = 0.f;
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const float4 xq = x[q], wq = w[q];
         const ff xr = ff_re(xq), xi = ff_im(xq);
-        // accumulators (sum, compensation): v re/im from x, w re/im from w
-        float vrs = xq.x, vrc = xq.y, vis = xq.z, vic = xq.w;
-        float wrs = wq.x, wrc = wq.y, wis = wq.z, wic = wq.w;
+        // two independent (sum, compensation) chains per component and output (basis vectors
+        // i mod 2), the first started from x and w; basis values loaded four at a time, the
+        // next four while the current four are processed
+        float vs[2][4] = {{xq.x, xq.y, xq.z, xq.w}, {0.f, 0.f, 0.f, 0.f}};
+        float ws[2][4] = {{wq.x, wq.y, wq.z, wq.w}, {0.f, 0.f, 0.f, 0.f}};
         float p, e;
         // w -= x s: re -= xr sr - xi si ; im -= xr si + xi sr
-        ff_two_prod(xr, sr, p, e); ff_acc_prod(wrs, wrc, -p, -e);
-        ff_two_prod(xi, si, p, e); ff_acc_prod(wrs, wrc, p, e);
-        ff_two_prod(xr, si, p, e); ff_acc_prod(wis, wic, -p, -e);
-        ff_two_prod(xi, sr, p, e); ff_acc_prod(wis, wic, -p, -e);
-        float4 cur = j > 0 ? V[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int i = 0; i < j; i++) {
-            const float4 nxt = i + 1 < j ? V[(size_t)(i + 1) * ldv + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const ff vr = ff_re(cur), vi = ff_im(cur);
-            const float4 a4 = cA[i], c4 = cC[i];
-            const ff ar = ff_re(a4), ai = ff_im(a4), cr = ff_re(c4), ci = ff_im(c4);
-            // v -= V_i a ; w -= V_i c   (complex products)
-            ff_two_prod(vr, ar, p, e); ff_acc_prod(vrs, vrc, -p, -e);
-            ff_two_prod(vi, ai, p, e); ff_acc_prod(vrs, vrc, p, e);
-            ff_two_prod(vr, ai, p, e); ff_acc_prod(vis, vic, -p, -e);
-            ff_two_prod(vi, ar, p, e); ff_acc_prod(vis, vic, -p, -e);
-            ff_two_prod(vr, cr, p, e); ff_acc_prod(wrs, wrc, -p, -e);
-            ff_two_prod(vi, ci, p, e); ff_acc_prod(wrs, wrc, p, e);
-            ff_two_prod(vr, ci, p, e); ff_acc_prod(wis, wic, -p, -e);
-            ff_two_prod(vi, cr, p, e); ff_acc_prod(wis, wic, -p, -e);
-            cur = nxt;
+        ff_two_prod(xr, sr, p, e); ff_acc_prod(ws[1][0], ws[1][1], -p, -e);
+        ff_two_prod(xi, si, p, e); ff_acc_prod(ws[1][0], ws[1][1], p, e);
+        ff_two_prod(xr, si, p, e); ff_acc_prod(ws[1][2], ws[1][3], -p, -e);
+        ff_two_prod(xi, sr, p, e); ff_acc_prod(ws[1][2], ws[1][3], -p, -e);
+        float4 cur[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) cur[u] = u < j ? V[(size_t)u * ldv + q] : zero4;
+        for (int i0 = 0; i0 < j; i0 += 4) {
+            float4 nxt[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) nxt[u] = i0 + 4 + u < j ? V[(size_t)(i0 + 4 + u) * ldv + q] : zero4;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (i0 + u < j) {
+                    float *va = vs[u & 1], *wa = ws[u & 1];
+                    const ff vr = ff_re(cur[u]), vi = ff_im(cur[u]);
+                    const float4 a4 = cA[i0 + u], c4 = cC[i0 + u];
+                    const ff ar = ff_re(a4), ai = ff_im(a4), cr = ff_re(c4), ci = ff_im(c4);
+                    // v -= V_i a ; w -= V_i c   (complex products)
+                    ff_two_prod(vr, ar, p, e); ff_acc_prod(va[0], va[1], -p, -e);
+                    ff_two_prod(vi, ai, p, e); ff_acc_prod(va[0], va[1], p, e);
+                    ff_two_prod(vr, ai, p, e); ff_acc_prod(va[2], va[3], -p, -e);
+                    ff_two_prod(vi, ar, p, e); ff_acc_prod(va[2], va[3], -p, -e);
+                    ff_two_prod(vr, cr, p, e); ff_acc_prod(wa[0], wa[1], -p, -e);
+                    ff_two_prod(vi, ci, p, e); ff_acc_prod(wa[0], wa[1], p, e);
+                    ff_two_prod(vr, ci, p, e); ff_acc_prod(wa[2], wa[3], -p, -e);
+                    ff_two_prod(vi, cr, p, e); ff_acc_prod(wa[2], wa[3], -p, -e);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) cur[u] = nxt[u];
         }
-        // v_j = v / nu
-        const ff vr = ff_norm(vrs, vrc), vi = ff_norm(vis, vic);
+        // v_j = v r
+        const ff vr = ff_add(ff_norm(vs[0][0], vs[0][1]), ff_norm(vs[1][0], vs[1][1]));
+        const ff vi = ff_add(ff_norm(vs[0][2], vs[0][3]), ff_norm(vs[1][2], vs[1][3]));
         ff_two_prod(vr, rinv, p, e);
         const ff or_ = ff_norm(p, e);
         ff_two_prod(vi, rinv, p, e);
         const ff oi = ff_norm(p, e);
         x[q] = make_float4(or_.hi, or_.lo, oi.hi, oi.lo);
-        const ff wr = ff_norm(wrs, wrc), wi = ff_norm(wis, wic);
+        const ff wr = ff_add(ff_norm(ws[0][0], ws[0][1]), ff_norm(ws[1][0], ws[1][1]));
+        const ff wi = ff_add(ff_norm(ws[0][2], ws[0][3]), ff_norm(ws[1][2], ws[1][3]));
         w[q] = make_float4(wr.hi, wr.lo, wi.hi, wi.lo);
         ff_two_prod(wr, wr, p, e);
         ff_acc_prod(sn, cn, p, e);
@@ -407,7 +423,20 @@ __global__ void __launch_bounds__(NT) k_pair_to_c128(size_t n, const float4 *__r
 // grid as the FP64 kernels, which keeps enough warps resident to hide DRAM latency behind
 // the TwoSum dependency chains.
 int gs_df_nblocks(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>(cdiv(n, (size_t)NT * 8), (size_t)152 * 4)); }
-int gs_df_update_nblocks(size_t n) { return blas_nblocks(n); }
+// The update passes run one full wave: 152 SMs x the blocks of k_update2_pair that fit on an
+// SM (by its registers), so that no SM gets a second, partial round of blocks.
+int gs_df_update_nblocks(size_t n) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update2_pair, NT, 0) != cudaSuccess || b < 1) {
+            cudaGetLastError();
+            b = 2;
+        }
+        per_sm = b;
+    }
+    return (int)std::max<size_t>(1, std::min<size_t>(cdiv(n, NT), (size_t)152 * per_sm));
+}
 
 constexpr int DF_CH = 4;  // basis vectors per block row of the dot pass
 

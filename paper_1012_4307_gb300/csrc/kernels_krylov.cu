@@ -205,36 +205,62 @@ __global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, do
 //   with s = H[j][j] / nu, the update pass forms v_j = (x - sum V_i (alpha a_i)) / (alpha nu)
 //   and w' = w - x (s / alpha) - sum V_i (c_i - a_i s): coef[i] = alpha a_i,
 //   coef[j+i] = c_i - a_i s, coef[2j] = 1 / (alpha nu), coef[2j+1] = s / alpha.
-__global__ void k_dcgs2_coef(int j, int has_w, const double2 *hv, const double2 *alpha2, double2 *H, int ldh,
-                             double2 *coef) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double nu = 1.0, al = 1.0;
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// One warp; lane l handles i = l and l + 32 (j <= 64).
+__global__ void k_dcgs2_coef(int j, int has_w, const double2 *__restrict__ hv, const double2 *__restrict__ alpha2,
+                             double2 *__restrict__ H, int ldh, double2 *__restrict__ coef) {
+    const int lane = threadIdx.x;
+    const double al = j > 0 ? alpha2[j].x : 1.0, ra = 1.0 / al;
+    double2 a[2], c[2];
+    double s2 = 0.0, tr = 0.0, ti = 0.0;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int i = lane + 32 * k;
+        a[k] = i < j ? hv[i] : make_double2(0.0, 0.0);
+        c[k] = (has_w && i < j) ? hv[j + 1 + i] : make_double2(0.0, 0.0);
+        s2 += a[k].x * a[k].x + a[k].y * a[k].y;
+        // conj(a) c
+        tr += a[k].x * c[k].x + a[k].y * c[k].y;
+        ti += a[k].x * c[k].y - a[k].y * c[k].x;
+    }
+    s2 = warp_sum_d(s2);
+    tr = warp_sum_d(tr);
+    ti = warp_sum_d(ti);
+    double nu = 1.0;
     if (j > 0) {
-        al = alpha2[j].x;
-        const double ra = 1.0 / al;
-        double n2 = hv[j].x * ra * ra;
-        for (int i = 0; i < j; i++) n2 -= (hv[i].x * hv[i].x + hv[i].y * hv[i].y) * (ra * ra);
-        nu = sqrt(fmax(n2, 1e-300));
+        nu = sqrt(fmax((hv[j].x - s2) * (ra * ra), 1e-300));
         double2 *col = H + (size_t)ldh * (j - 1);
-        for (int i = 0; i < j; i++) col[i] = cadd(col[i], hv[i]);  // alpha a_i = hv[i]
-        col[j] = make_double2(al * nu, 0.0);
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const int i = lane + 32 * k;
+            if (i < j) col[i] = cadd(col[i], a[k]);  // alpha a_i = hv[i]
+        }
+        if (lane == 0) col[j] = make_double2(al * nu, 0.0);
     }
     if (!has_w) return;
-    const double ra = 1.0 / al;
-    double2 t = cscale(hv[2 * j + 1], ra);
-    for (int i = 0; i < j; i++) t = csub(t, cmul(make_double2(hv[i].x * ra, -hv[i].y * ra), hv[j + 1 + i]));
+    const double2 t = make_double2((hv[2 * j + 1].x - tr) * ra, (hv[2 * j + 1].y - ti) * ra);
     const double rn = 1.0 / nu;
     const double2 hjj = cscale(t, rn);
-    double2 *col = H + (size_t)ldh * j;
-    for (int i = 0; i < j; i++) col[i] = hv[j + 1 + i];
-    col[j] = hjj;
     const double2 sf = cscale(hjj, rn);
-    for (int i = 0; i < j; i++) {
-        coef[i] = hv[i];
-        coef[j + i] = csub(hv[j + 1 + i], cmul(cscale(hv[i], ra), sf));
+    double2 *col = H + (size_t)ldh * j;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int i = lane + 32 * k;
+        if (i < j) {
+            col[i] = c[k];
+            coef[i] = a[k];
+            coef[j + i] = csub(c[k], cmul(cscale(a[k], ra), sf));
+        }
     }
-    coef[2 * j] = make_double2(rn * ra, 0.0);
-    coef[2 * j + 1] = cscale(sf, ra);
+    if (lane == 0) {
+        col[j] = hjj;
+        coef[2 * j] = make_double2(rn * ra, 0.0);
+        coef[2 * j + 1] = cscale(sf, ra);
+    }
 }
 
 __global__ void k_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y) {
@@ -376,6 +402,7 @@ cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, d
 
 cudaError_t launch_dcgs2_coef(int j, int has_w, const double2 *hv, const double2 *alpha2, double2 *H, int ldh,
                               double2 *coef, cudaStream_t s) {
+    if (j < 0 || j > 64) return cudaErrorInvalidValue;
     k_dcgs2_coef<<<1, 32, 0, s>>>(j, has_w, hv, alpha2, H, ldh, coef);
     return cudaGetLastError();
 }

@@ -202,6 +202,24 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------- batch
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
+# kernels, from the ncu captures summarised under profiles/.  Reported only while the kernel's
+# source file is the one that was captured (same SHA-1); otherwise null.
+NCU_TRAFFIC = {}
+
+
+def ncu_traffic(kernel_class):
+    import hashlib
+    t = NCU_TRAFFIC.get(kernel_class)
+    if not t:
+        return None, None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])
+    with open(path, "rb") as fh:
+        if hashlib.sha1(fh.read()).hexdigest() != t["sha1"]:
+            return None, "kernel changed since the ncu capture in %s" % t["profile"]
+    return t["bytes"], "%s, one launch at %s (%s)" % (t["kernel"], t["launch"], t["profile"])
+
+
 GS_NAMES = {"dcgs2": "double-FP32 delayed CGS2 on float-pair vectors",
             "df": "double-FP32 CGS + DGKS on float-pair vectors",
             "fp64": "IEEE FP64 CGS + DGKS"}
@@ -380,7 +398,8 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                 "peak_source": "%s hbm_gbs" % peak_src}
-    roof.update({"traffic": None, "kernel_class": dname, "launches_per_solve": d["launches"],
+    traffic, traffic_note = ncu_traffic(dname)
+    roof.update({"traffic": traffic, "traffic_note": traffic_note, "kernel_class": dname, "launches_per_solve": d["launches"],
                  "avg_launch_us": avg_s * 1e6, "share_of_solve": d["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9)})
     breakdown = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                      "GB/s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None}

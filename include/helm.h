@@ -283,7 +283,8 @@ helm_status helm_profile_read(helm_handle *h, int ncls, int *launches, double *m
  *   level_tile[l]  level l (0 = finest) of a 2D complex64 V(2,2) omega-Jacobi cycle runs its
  *                  two pre-sweeps + residual + full weighting, and its prolongation + two
  *                  post-sweeps, as two temporally blocked launches with tile shape
- *                  HELM_TILE_* (coarse nodes per block), or as separate sweep / residual /
+ *                  HELM_TILE_* (coarse nodes per block, or the register wavefront), or as
+ *                  separate sweep / residual /
  *                  transfer launches (HELM_TILE_NONE).  Ignored where it does not apply (other
  *                  smoothers, complex128 cycles, 3D, levels inside the tail, grids the tile
  *                  does not fit: those use the separate launches).
@@ -295,7 +296,9 @@ typedef enum {
     HELM_TILE_16x16 = 1,
     HELM_TILE_16x8 = 2,
     HELM_TILE_64x4 = 3,
-    HELM_TILE_COUNT = 4
+    HELM_TILE_WAVE = 4, /* register wavefront: one warp per strip of 13 coarse columns and 8 coarse
+                           rows, the sweeps pipelined down the rows, no shared memory */
+    HELM_TILE_COUNT = 5
 } helm_tile;
 typedef struct {
     int tail_levels;

@@ -20,6 +20,7 @@ typedef std::complex<double> cd;
 
 // ------------------------------------------------------------------------------ errors
 static thread_local std::string g_last_error;
+thread_local bool g_pdl_off = false;
 
 helm_status helm_fail(helm_status st, const char *fmt, ...) {
     char buf[512];

@@ -29,6 +29,7 @@ __device__ __forceinline__ void cmac(float4 a, float2 z, float &sr, float &cr, f
 
 template <int DIM>
 __global__ void __launch_bounds__(BX *BY) k_apply_A_df(DevOpDF o, const float2 *__restrict__ z, float4 *__restrict__ y) {
+    pdl_enter();
     const int nx = o.n[0], ny = o.n[1], nz = o.n[2];
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(BX *BY) k_apply_A_df(DevOpDF o, const float2 *
 
 cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, float4 *y, cudaStream_t s) {
     dim3 g(cdiv(op.n[0] - 2, BX), cdiv(op.n[1] - 2, BY), dim == 3 ? cdiv(op.n[2] - 2, KCHUNK) : 1), b(BX, BY);
-    if (dim == 3) k_apply_A_df<3><<<g, b, 0, s>>>(op, z, y);
-    else k_apply_A_df<2><<<g, b, 0, s>>>(op, z, y);
+    if (dim == 3) launch_pdl(k_apply_A_df<3>, g, b, 0, s, op, z, y);
+    else launch_pdl(k_apply_A_df<2>, g, b, 0, s, op, z, y);
     return cudaGetLastError();
 }

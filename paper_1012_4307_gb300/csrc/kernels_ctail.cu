@@ -241,6 +241,7 @@ __device__ void ct_cycle(const Ctx &X, const CArgs &A, bool zero, int gf, int gc
 }
 
 __global__ void __launch_bounds__(CT_THREADS) k_mg_ctail(CArgs A) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char ct_smem[];
     cg::cluster_group cl = cg::this_cluster();
     Ctx X{ct_smem, (int)cl.block_rank(), (int)cl.num_blocks()};

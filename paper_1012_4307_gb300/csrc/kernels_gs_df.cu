@@ -59,6 +59,7 @@ template <int CH>
 __global__ void __launch_bounds__(NT) k_mdot_norm_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
                                                        const float4 *__restrict__ w, double2 *__restrict__ partials,
                                                        const int *__restrict__ gate) {
+    pdl_enter();
     if (gate && *gate == 0) return;
     __shared__ double sums[2 * CH + 1];
     const int i0 = blockIdx.y * CH;
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(NT) k_mdot_norm_pair(size_t n, const float4 *_
 __global__ void __launch_bounds__(NT) k_update_norm_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
                                                          const double2 *__restrict__ h, float4 *__restrict__ w,
                                                          double2 *__restrict__ partials, const int *__restrict__ gate) {
+    pdl_enter();
     if (gate && *gate == 0) return;
     __shared__ float4 hs[64];  // (re.hi, re.lo, im.hi, im.lo)
     __shared__ double sums[1];
@@ -208,9 +210,10 @@ __global__ void __launch_bounds__(NT) k_update_norm_pair(size_t n, const float4 
 // measures and adds to H (the update that uses it is double-FP32, so A z_j stays exactly
 // expanded in the basis), so it is formed from the hi parts in FP32.
 template <int CH>
-__global__ void __launch_bounds__(NT) k_mdot2_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
+__global__ void __launch_bounds__(NT, 4) k_mdot2_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
                                                    const float4 *__restrict__ x, const float4 *__restrict__ w,
                                                    double2 *__restrict__ partials) {
+    pdl_enter();
     __shared__ double sums[4 * CH];
     const int i0 = blockIdx.y * CH;
     const int cnt = min(CH, nv - i0);
@@ -269,6 +272,7 @@ __global__ void __launch_bounds__(NT) k_mdot2_pair(size_t n, const float4 *__res
 // partials[b] = (||w||^2, 0).
 __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
                                                      const double2 *__restrict__ coef, double2 *__restrict__ partials) {
+    pdl_enter();
     __shared__ float4 cA[64], cC[64];
     __shared__ float4 sc[2];  // (r hi, lo, 0, 0), s
     __shared__ double sums[1];
@@ -365,6 +369,7 @@ __device__ __forceinline__ ff block_inv(const double2 *beta) {
 
 // w <- w / beta.x in double-float (w a float pair vector).
 __global__ void __launch_bounds__(NT) k_scale_inv_pair(size_t n, float4 *__restrict__ w, const double2 *__restrict__ beta) {
+    pdl_enter();
     const ff r = block_inv(beta);
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const float4 v = w[q];
@@ -379,6 +384,7 @@ __global__ void __launch_bounds__(NT) k_scale_inv_pair(size_t n, float4 *__restr
 
 // In place: the FP64 vector x (as double2) becomes the float-pair vector x / beta.x.
 __global__ void __launch_bounds__(NT) k_split_scale(size_t n, void *x, const double2 *__restrict__ beta) {
+    pdl_enter();
     __shared__ double rinv;
     if (threadIdx.x == 0) rinv = beta ? 1.0 / beta->x : 1.0;
     __syncthreads();
@@ -401,6 +407,7 @@ __device__ __forceinline__ double block_recip(const double2 *alpha) {
 }
 __global__ void __launch_bounds__(NT) k_pair_to_c64(size_t n, const float4 *__restrict__ v, const double2 *alpha,
                                                     float2 *__restrict__ z) {
+    pdl_enter();
     const float r = (float)block_recip(alpha);
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const float4 a = v[q];
@@ -409,6 +416,7 @@ __global__ void __launch_bounds__(NT) k_pair_to_c64(size_t n, const float4 *__re
 }
 __global__ void __launch_bounds__(NT) k_pair_to_c128(size_t n, const float4 *__restrict__ v, const double2 *alpha,
                                                      double2 *__restrict__ z) {
+    pdl_enter();
     const double r = block_recip(alpha);
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const float4 a = v[q];
@@ -444,14 +452,14 @@ cudaError_t launch_mdot_norm_pair(size_t n, const float4 *V, size_t ldv, int nv,
                                   const int *gate, cudaStream_t s) {
     if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
     dim3 g(gs_df_nblocks(n), std::max(1, (nv + DF_CH - 1) / DF_CH));
-    k_mdot_norm_pair<DF_CH><<<g, NT, 0, s>>>(n, V, ldv, nv, w, partials, gate);
+    launch_pdl(k_mdot_norm_pair<DF_CH>, g, NT, 0, s, n, V, ldv, nv, w, partials, gate);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int nv, const double2 *h, float4 *w,
                                     double2 *partials, const int *gate, cudaStream_t s) {
     if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
-    k_update_norm_pair<<<gs_df_update_nblocks(n), NT, 0, s>>>(n, V, ldv, nv, h, w, partials, gate);
+    launch_pdl(k_update_norm_pair, gs_df_update_nblocks(n), NT, 0, s, n, V, ldv, nv, h, w, partials, gate);
     return cudaGetLastError();
 }
 
@@ -461,32 +469,32 @@ cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, con
                               double2 *partials, cudaStream_t s) {
     if (nv < 1 || nv > 64) return cudaErrorInvalidValue;
     dim3 g(gs_df_nblocks(n), (nv + DF_CH2 - 1) / DF_CH2);
-    k_mdot2_pair<DF_CH2><<<g, NT, 0, s>>>(n, V, ldv, nv, x, w, partials);
+    launch_pdl(k_mdot2_pair<DF_CH2>, g, NT, 0, s, n, V, ldv, nv, x, w, partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update2_pair(size_t n, float4 *V, size_t ldv, int j, const double2 *coef, double2 *partials,
                                 cudaStream_t s) {
     if (j < 0 || j > 64) return cudaErrorInvalidValue;
-    k_update2_pair<<<gs_df_update_nblocks(n), NT, 0, s>>>(n, V, ldv, j, coef, partials);
+    launch_pdl(k_update2_pair, gs_df_update_nblocks(n), NT, 0, s, n, V, ldv, j, coef, partials);
     return cudaGetLastError();
 }
 
 static unsigned pair_grid(size_t n) { return (unsigned)std::max<size_t>(1, std::min<size_t>(cdiv(n, NT), 152 * 8)); }
 
 cudaError_t launch_scale_inv_pair(size_t n, float4 *w, const double2 *beta, cudaStream_t s) {
-    k_scale_inv_pair<<<pair_grid(n), NT, 0, s>>>(n, w, beta);
+    launch_pdl(k_scale_inv_pair, pair_grid(n), NT, 0, s, n, w, beta);
     return cudaGetLastError();
 }
 cudaError_t launch_split_scale(size_t n, void *x, const double2 *beta, cudaStream_t s) {
-    k_split_scale<<<pair_grid(n), NT, 0, s>>>(n, x, beta);
+    launch_pdl(k_split_scale, pair_grid(n), NT, 0, s, n, x, beta);
     return cudaGetLastError();
 }
 cudaError_t launch_pair_to_c64(size_t n, const float4 *v, const double2 *alpha, float2 *z, cudaStream_t s) {
-    k_pair_to_c64<<<pair_grid(n), NT, 0, s>>>(n, v, alpha, z);
+    launch_pdl(k_pair_to_c64, pair_grid(n), NT, 0, s, n, v, alpha, z);
     return cudaGetLastError();
 }
 cudaError_t launch_pair_to_c128(size_t n, const float4 *v, const double2 *alpha, double2 *z, cudaStream_t s) {
-    k_pair_to_c128<<<pair_grid(n), NT, 0, s>>>(n, v, alpha, z);
+    launch_pdl(k_pair_to_c128, pair_grid(n), NT, 0, s, n, v, alpha, z);
     return cudaGetLastError();
 }

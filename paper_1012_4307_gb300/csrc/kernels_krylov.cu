@@ -49,6 +49,7 @@ template <int CH>
 __global__ void __launch_bounds__(NT) k_mdot_norm(size_t n, const double2 *__restrict__ V, size_t ldv, int nv,
                                                   const double2 *__restrict__ w, double2 *__restrict__ partials,
                                                   const int *__restrict__ gate) {
+    pdl_enter();
     if (gate && *gate == 0) return;
     __shared__ double2 sums[CH + 1];
     const int i0 = blockIdx.y * CH;
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(NT) k_mdot_norm(size_t n, const double2 *__res
 __global__ void __launch_bounds__(NT) k_update_norm(size_t n, const double2 *__restrict__ V, size_t ldv, int nv,
                                                     const double2 *__restrict__ h, double2 *__restrict__ w,
                                                     double2 *__restrict__ partials, const int *__restrict__ gate) {
+    pdl_enter();
     if (gate && *gate == 0) return;
     __shared__ double2 hs[64];
     __shared__ double2 sums[1];
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(NT) k_update_norm(size_t n, const double2 *__r
 // 1 '+=', 2 (sqrt(re), 0).  Gated.
 __global__ void k_reduce(const double2 *__restrict__ partials, int nblk, double2 *__restrict__ out, int mode,
                          const int *__restrict__ gate) {
+    pdl_enter();
     if (gate && *gate == 0) return;
     __shared__ double2 sums[1];
     const int i = blockIdx.x;
@@ -119,6 +122,7 @@ __global__ void k_reduce(const double2 *__restrict__ partials, int nblk, double2
 // ||w'|| < eta ||w||, i.e. when the projection cancelled most of w.
 __global__ void k_reduce_decide(const double2 *__restrict__ partials, int nblk, double2 *hnorm, int *flag, int *count,
                                 double eta) {
+    pdl_enter();
     __shared__ double2 sums[1];
     double2 s[1] = {make_double2(0.0, 0.0)};
     for (int b = threadIdx.x; b < nblk; b += NT) s[0] = cadd(s[0], partials[b]);
@@ -133,6 +137,7 @@ __global__ void k_reduce_decide(const double2 *__restrict__ partials, int nblk, 
 }
 
 __global__ void k_scale_inv(size_t n, const double2 *x, const double2 *__restrict__ scale, double2 *y) {
+    pdl_enter();
     const double s = scale[0].x;
     const double r = s != 0.0 ? 1.0 / s : 0.0;
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
@@ -144,6 +149,7 @@ __global__ void k_scale_inv(size_t n, const double2 *x, const double2 *__restric
 template <typename CZ>
 __global__ void k_combine(size_t n, const CZ *__restrict__ Z, size_t ldz, int nz, const double2 *__restrict__ y,
                           double2 *__restrict__ x) {
+    pdl_enter();
     __shared__ double2 ys[64];
     for (int i = threadIdx.x; i < nz; i += NT) ys[i] = y[i];
     __syncthreads();
@@ -159,6 +165,7 @@ __global__ void k_combine(size_t n, const CZ *__restrict__ Z, size_t ldz, int nz
 // Systems, Section 6.5.9 for the real case.
 __global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm_dev,
                          double *est) {
+    pdl_enter();
     const double fnorm = fnorm_dev->x;
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double2 *col = H + (size_t)ldh * j;
@@ -213,6 +220,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // One warp; lane l handles i = l and l + 32 (j <= 64).
 __global__ void k_dcgs2_coef(int j, int has_w, const double2 *__restrict__ hv, const double2 *__restrict__ alpha2,
                              double2 *__restrict__ H, int ldh, double2 *__restrict__ coef) {
+    pdl_enter();
     const int lane = threadIdx.x;
     const double al = j > 0 ? alpha2[j].x : 1.0, ra = 1.0 / al;
     double2 a[2], c[2];
@@ -264,6 +272,7 @@ __global__ void k_dcgs2_coef(int j, int has_w, const double2 *__restrict__ hv, c
 }
 
 __global__ void k_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y) {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (int r = k - 1; r >= 0; r--) {
         double2 s = g[r];
@@ -275,6 +284,7 @@ __global__ void k_backsolve(const double2 *H, int ldh, int k, const double2 *g, 
 // Bi-CGSTAB scalar block (device): 0 rho, 1 rho_old, 2 alpha, 3 omega, 4 beta, 5 <rh,v>,
 // 6 <t,s>, 7 <t,t>, 8 -alpha, 9 -omega, 10 one, 11 flags (x: breakdown)
 __global__ void k_bicg_scalars(int stage, double2 *sc) {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double2 zero = make_double2(0.0, 0.0);
     auto isz = [](double2 v) { return v.x == 0.0 && v.y == 0.0; };
@@ -299,6 +309,7 @@ __global__ void k_bicg_scalars(int stage, double2 *sc) {
 
 __global__ void k_bicg_p(size_t n, const double2 *__restrict__ r, const double2 *__restrict__ v,
                          const double2 *__restrict__ sc, double2 *__restrict__ p) {
+    pdl_enter();
     const double2 beta = sc[4], om = sc[3];
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const double2 t = csub(p[q], cmul(om, v[q]));
@@ -308,6 +319,7 @@ __global__ void k_bicg_p(size_t n, const double2 *__restrict__ r, const double2 
 
 __global__ void k_axpby(size_t n, const double2 *__restrict__ a, const double2 *__restrict__ x,
                         const double2 *__restrict__ b, double2 *__restrict__ y) {
+    pdl_enter();
     const double2 av = a[0], bv = b[0];
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT)
         y[q] = cfma(av, x[q], cmul(bv, y[q]));
@@ -315,6 +327,7 @@ __global__ void k_axpby(size_t n, const double2 *__restrict__ a, const double2 *
 
 template <typename CY>
 __global__ void k_axpy_mixed(size_t n, const double2 *__restrict__ a, const CY *__restrict__ x, double2 *__restrict__ y) {
+    pdl_enter();
     const double2 av = a[0];
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT)
         y[q] = cfma(av, to_c(x[q], 0.0), y[q]);
@@ -324,6 +337,7 @@ __global__ void k_axpy_mixed(size_t n, const double2 *__restrict__ a, const CY *
 __global__ void k_weight(int nx, int ny, int nz, int dim, const double2 *__restrict__ wx,
                          const double2 *__restrict__ wy, const double2 *__restrict__ wz, int inverse,
                          const double2 *__restrict__ x, double2 *__restrict__ y) {
+    pdl_enter();
     const size_t n = (size_t)nx * ny * nz;
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((size_t)nx * ny));
@@ -337,6 +351,7 @@ __global__ void k_weight(int nx, int ny, int nz, int dim, const double2 *__restr
 
 __global__ void k_grad_k2(int nx, int ny, int nz, int dim, const double2 *__restrict__ lam,
                           const double2 *__restrict__ u, double *__restrict__ grad) {
+    pdl_enter();
     const size_t n = (size_t)nx * ny * nz;
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((size_t)nx * ny));
@@ -357,38 +372,38 @@ cudaError_t launch_mdot_norm(size_t n, const double2 *V, size_t ldv, int nv, con
     if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
     constexpr int CH = 8;
     dim3 g(blas_nblocks(n), std::max(1, (nv + CH - 1) / CH));
-    k_mdot_norm<CH><<<g, NT, 0, s>>>(n, V, ldv, nv, w, partials, gate);
+    launch_pdl(k_mdot_norm<CH>, g, NT, 0, s, n, V, ldv, nv, w, partials, gate);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update_norm(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
                                double2 *partials, const int *gate, cudaStream_t s) {
     if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
-    k_update_norm<<<blas_nblocks(n), NT, 0, s>>>(n, V, ldv, nv, h, w, partials, gate);
+    launch_pdl(k_update_norm, blas_nblocks(n), NT, 0, s, n, V, ldv, nv, h, w, partials, gate);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const double2 *partials, int nblk, int nv, double2 *out, int mode, const int *gate,
                           cudaStream_t s) {
-    k_reduce<<<nv, NT, 0, s>>>(partials, nblk, out, mode, gate);
+    launch_pdl(k_reduce, nv, NT, 0, s, partials, nblk, out, mode, gate);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_decide(const double2 *partials, int nblk, double2 *hnorm, int *flag, int *count, double eta,
                                  cudaStream_t s) {
-    k_reduce_decide<<<1, NT, 0, s>>>(partials, nblk, hnorm, flag, count, eta);
+    launch_pdl(k_reduce_decide, 1, NT, 0, s, partials, nblk, hnorm, flag, count, eta);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scale_inv(size_t n, const double2 *x, const double2 *scale, double2 *y, cudaStream_t s) {
-    k_scale_inv<<<stream_grid(n), NT, 0, s>>>(n, x, scale, y);
+    launch_pdl(k_scale_inv, stream_grid(n), NT, 0, s, n, x, scale, y);
     return cudaGetLastError();
 }
 
 template <typename CZ>
 cudaError_t launch_combine(size_t n, const CZ *Z, size_t ldz, int nz, const double2 *y, double2 *x, cudaStream_t s) {
     if (nz > 64) return cudaErrorInvalidValue;
-    k_combine<CZ><<<stream_grid(n), NT, 0, s>>>(n, Z, ldz, nz, y, x);
+    launch_pdl(k_combine<CZ>, stream_grid(n), NT, 0, s, n, Z, ldz, nz, y, x);
     return cudaGetLastError();
 }
 template cudaError_t launch_combine<float2>(size_t, const float2 *, size_t, int, const double2 *, double2 *, cudaStream_t);
@@ -403,35 +418,35 @@ cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, d
 cudaError_t launch_dcgs2_coef(int j, int has_w, const double2 *hv, const double2 *alpha2, double2 *H, int ldh,
                               double2 *coef, cudaStream_t s) {
     if (j < 0 || j > 64) return cudaErrorInvalidValue;
-    k_dcgs2_coef<<<1, 32, 0, s>>>(j, has_w, hv, alpha2, H, ldh, coef);
+    launch_pdl(k_dcgs2_coef, 1, 32, 0, s, j, has_w, hv, alpha2, H, ldh, coef);
     return cudaGetLastError();
 }
 
 cudaError_t launch_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y, cudaStream_t s) {
-    k_backsolve<<<1, 32, 0, s>>>(H, ldh, k, g, y);
+    launch_pdl(k_backsolve, 1, 32, 0, s, H, ldh, k, g, y);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bicg_scalars(int stage, double2 *sc, cudaStream_t s) {
-    k_bicg_scalars<<<1, 32, 0, s>>>(stage, sc);
+    launch_pdl(k_bicg_scalars, 1, 32, 0, s, stage, sc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bicg_p(size_t n, const double2 *r, const double2 *v, const double2 *sc, double2 *p,
                           cudaStream_t s) {
-    k_bicg_p<<<stream_grid(n), NT, 0, s>>>(n, r, v, sc, p);
+    launch_pdl(k_bicg_p, stream_grid(n), NT, 0, s, n, r, v, sc, p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_axpby(size_t n, const double2 *a, const double2 *x, const double2 *b, double2 *y,
                          cudaStream_t s) {
-    k_axpby<<<stream_grid(n), NT, 0, s>>>(n, a, x, b, y);
+    launch_pdl(k_axpby, stream_grid(n), NT, 0, s, n, a, x, b, y);
     return cudaGetLastError();
 }
 
 template <typename CY>
 cudaError_t launch_axpy_mixed(size_t n, const double2 *a, const CY *x, double2 *y, cudaStream_t s) {
-    k_axpy_mixed<CY><<<stream_grid(n), NT, 0, s>>>(n, a, x, y);
+    launch_pdl(k_axpy_mixed<CY>, stream_grid(n), NT, 0, s, n, a, x, y);
     return cudaGetLastError();
 }
 template cudaError_t launch_axpy_mixed<float2>(size_t, const double2 *, const float2 *, double2 *, cudaStream_t);
@@ -439,13 +454,13 @@ template cudaError_t launch_axpy_mixed<double2>(size_t, const double2 *, const d
 
 cudaError_t launch_weight(size_t n, const int nodes[3], int dim, const double2 *w_axis[3], int inverse,
                           const double2 *x, double2 *y, cudaStream_t s) {
-    k_weight<<<stream_grid(n), NT, 0, s>>>(nodes[0], nodes[1], dim == 3 ? nodes[2] : 1, dim, w_axis[0], w_axis[1],
+    launch_pdl(k_weight, stream_grid(n), NT, 0, s, nodes[0], nodes[1], dim == 3 ? nodes[2] : 1, dim, w_axis[0], w_axis[1],
                                            w_axis[2], inverse, x, y);
     return cudaGetLastError();
 }
 
 cudaError_t launch_grad_k2(size_t n, const int nodes[3], int dim, const double2 *lam, const double2 *u,
                            double *grad, cudaStream_t s) {
-    k_grad_k2<<<stream_grid(n), NT, 0, s>>>(nodes[0], nodes[1], dim == 3 ? nodes[2] : 1, dim, lam, u, grad);
+    launch_pdl(k_grad_k2, stream_grid(n), NT, 0, s, nodes[0], nodes[1], dim == 3 ? nodes[2] : 1, dim, lam, u, grad);
     return cudaGetLastError();
 }

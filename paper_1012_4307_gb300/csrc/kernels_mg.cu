@@ -97,6 +97,7 @@ __device__ __forceinline__ typename CT<R>::T apply_point(const OpView<R> &o, con
 
 template <typename R, int DIM, typename CX>
 __global__ void __launch_bounds__(BX *BY) k_apply(OpView<R> o, const CX *__restrict__ x, typename CT<R>::T *__restrict__ y) {
+    pdl_enter();
     typedef typename CT<R>::T C;
     INTERIOR_IJ(o);
     C xm = mk(R(0), R(0)), xc = to_c(x[p], R()), xp = mk(R(0), R(0));
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(BX *BY) k_apply(OpView<R> o, const CX *__restr
 template <typename R, int DIM, typename CB>
 __global__ void __launch_bounds__(BX *BY) k_residual(OpView<R> o, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
                                                      typename CT<R>::T *__restrict__ r) {
+    pdl_enter();
     typedef typename CT<R>::T C;
     INTERIOR_IJ(o);
     C xm = mk(R(0), R(0)), xc = u[p], xp = mk(R(0), R(0));
@@ -129,6 +131,7 @@ __global__ void __launch_bounds__(BX *BY) k_residual(OpView<R> o, const CB *__re
 template <typename R, int DIM, typename CB, bool ZERO>
 __global__ void __launch_bounds__(BX *BY) k_jacobi(OpView<R> o, R omega, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
                                                    typename CT<R>::T *__restrict__ un) {
+    pdl_enter();
     typedef typename CT<R>::T C;
     INTERIOR_IJ(o);
     if (ZERO) {
@@ -156,6 +159,7 @@ __global__ void __launch_bounds__(BX *BY) k_jacobi(OpView<R> o, R omega, const C
 // one colour of omega-red-black Jacobi, in place: threads map to every other x node.
 template <typename R, int DIM, typename CB>
 __global__ void __launch_bounds__(BX *BY) k_rb(OpView<R> o, R omega, const CB *__restrict__ b, typename CT<R>::T *u, int colour) {
+    pdl_enter();
     typedef typename CT<R>::T C;
     const int t = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -180,6 +184,7 @@ __global__ void __launch_bounds__(BX *BY) k_rb(OpView<R> o, R omega, const CB *_
 template <typename R, int DIM, typename CB>
 __global__ void __launch_bounds__(BX *BY) k_residual_restrict(OpView<R> o, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
                                                               typename CT<R>::T *__restrict__ rc, int ncx, int ncy, int ncz) {
+    pdl_enter();
     typedef typename CT<R>::T C;
     const int I = blockIdx.x * BX + threadIdx.x + 1;
     const int J = blockIdx.y * BY + threadIdx.y + 1;
@@ -215,6 +220,7 @@ __global__ void __launch_bounds__(BX *BY) k_residual_restrict(OpView<R> o, const
 template <typename R, int DIM>
 __global__ void __launch_bounds__(BX *BY) k_prolong_add(int nx, int ny, int nz, const typename CT<R>::T *__restrict__ ec,
                                                         typename CT<R>::T *__restrict__ uf) {
+    pdl_enter();
     typedef typename CT<R>::T C;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(BX *BY) k_prolong_add(int nx, int ny, int nz, 
 template <typename R>
 __global__ void k_dense_solve(int nx, int ny, int nz, int dim, int nu, const typename CT<R>::T *__restrict__ minv,
                               const typename CT<R>::T *__restrict__ b, typename CT<R>::T *__restrict__ u) {
+    pdl_enter();
     typedef typename CT<R>::T C;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= nu) return;
@@ -266,12 +273,14 @@ __global__ void k_dense_solve(int nx, int ny, int nz, int dim, int nu, const typ
 
 template <typename CI, typename CO>
 __global__ void k_convert(size_t n, const CI *__restrict__ in, CO *__restrict__ out) {
+    pdl_enter();
     typedef decltype(out->x) RO;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
         out[q] = to_c(in[q], RO());
 }
 
 template <typename C> __global__ void k_zero(size_t n, C *x) {
+    pdl_enter();
     typedef decltype(x->x) R;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
         x[q] = mk(R(0), R(0));
@@ -362,6 +371,7 @@ template <int TCX, int TCY>
 __global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float omega, const float2 *__restrict__ b,
                                                        float2 *__restrict__ u, float2 *__restrict__ rc, int ncx,
                                                        int ncy) {
+    pdl_enter();
     typedef Tile<TCX, TCY> TL;
     constexpr int RW = TL::RW, RH = TL::RH;
     extern __shared__ __align__(16) unsigned char pre_smem[];
@@ -435,6 +445,7 @@ template <int TCX, int TCY>
 __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float omega, const float2 *__restrict__ b,
                                                        const float2 *__restrict__ u_in, float2 *__restrict__ u,
                                                        const float2 *__restrict__ ec, int ncx, int ncy) {
+    pdl_enter();
     typedef Tile<TCX, TCY> TL;
     constexpr int RW = TL::RW, RH = TL::RH;
     extern __shared__ __align__(16) unsigned char post_smem[];
@@ -693,6 +704,7 @@ __device__ void tail_cycle(const TailArgs<R> &A, bool zero, int gf, int gc) {
 // caller's global top-level vectors; zero != 0 means the top-level iterate starts at 0.
 template <typename R, int DIM>
 __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs<R> A, int gf, int gc, int zero) {
+    pdl_enter();
     typedef typename CT<R>::T C;
     extern __shared__ __align__(16) unsigned char tail_smem[];
     __shared__ TailArgs<R> S;
@@ -759,8 +771,8 @@ dim3 grid_for(const int n[3], int dim) {
 template <typename R, typename CX>
 cudaError_t launch_apply(const DevOp<R> &op, int dim, const CX *x, typename CT<R>::T *y, cudaStream_t s) {
     dim3 g = grid_for(op.n, dim), b(BX, BY);
-    if (dim == 3) k_apply<R, 3, CX><<<g, b, 0, s>>>(view(op), x, y);
-    else k_apply<R, 2, CX><<<g, b, 0, s>>>(view(op), x, y);
+    if (dim == 3) launch_pdl(k_apply<R, 3, CX>, g, b, 0, s, view(op), x, y);
+    else launch_pdl(k_apply<R, 2, CX>, g, b, 0, s, view(op), x, y);
     return cudaGetLastError();
 }
 
@@ -768,8 +780,8 @@ template <typename R, typename CB>
 cudaError_t launch_residual(const DevOp<R> &op, int dim, const CB *bb, const typename CT<R>::T *u,
                             typename CT<R>::T *r, cudaStream_t s) {
     dim3 g = grid_for(op.n, dim), b(BX, BY);
-    if (dim == 3) k_residual<R, 3, CB><<<g, b, 0, s>>>(view(op), bb, u, r);
-    else k_residual<R, 2, CB><<<g, b, 0, s>>>(view(op), bb, u, r);
+    if (dim == 3) launch_pdl(k_residual<R, 3, CB>, g, b, 0, s, view(op), bb, u, r);
+    else launch_pdl(k_residual<R, 2, CB>, g, b, 0, s, view(op), bb, u, r);
     return cudaGetLastError();
 }
 
@@ -778,11 +790,11 @@ cudaError_t launch_jacobi(const DevOp<R> &op, int dim, R omega, const CB *bb, co
                           typename CT<R>::T *u_out, cudaStream_t s) {
     dim3 g = grid_for(op.n, dim), b(BX, BY);
     if (u_in == nullptr) {
-        if (dim == 3) k_jacobi<R, 3, CB, true><<<g, b, 0, s>>>(view(op), omega, bb, u_in, u_out);
-        else k_jacobi<R, 2, CB, true><<<g, b, 0, s>>>(view(op), omega, bb, u_in, u_out);
+        if (dim == 3) launch_pdl(k_jacobi<R, 3, CB, true>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
+        else launch_pdl(k_jacobi<R, 2, CB, true>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
     } else {
-        if (dim == 3) k_jacobi<R, 3, CB, false><<<g, b, 0, s>>>(view(op), omega, bb, u_in, u_out);
-        else k_jacobi<R, 2, CB, false><<<g, b, 0, s>>>(view(op), omega, bb, u_in, u_out);
+        if (dim == 3) launch_pdl(k_jacobi<R, 3, CB, false>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
+        else launch_pdl(k_jacobi<R, 2, CB, false>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
     }
     return cudaGetLastError();
 }
@@ -791,8 +803,8 @@ template <typename R, typename CB>
 cudaError_t launch_rb(const DevOp<R> &op, int dim, R omega, const CB *bb, typename CT<R>::T *u, int colour,
                       cudaStream_t s) {
     dim3 g(cdiv((op.n[0] - 1) / 2, BX), cdiv(op.n[1] - 2, BY), dim == 3 ? cdiv(op.n[2] - 2, KCHUNK) : 1), b(BX, BY);
-    if (dim == 3) k_rb<R, 3, CB><<<g, b, 0, s>>>(view(op), omega, bb, u, colour);
-    else k_rb<R, 2, CB><<<g, b, 0, s>>>(view(op), omega, bb, u, colour);
+    if (dim == 3) launch_pdl(k_rb<R, 3, CB>, g, b, 0, s, view(op), omega, bb, u, colour);
+    else launch_pdl(k_rb<R, 2, CB>, g, b, 0, s, view(op), omega, bb, u, colour);
     return cudaGetLastError();
 }
 
@@ -801,8 +813,8 @@ cudaError_t launch_residual_restrict(const DevOp<R> &op, int dim, const CB *bb, 
                                      typename CT<R>::T *rc, cudaStream_t s) {
     int nc[3] = {(op.n[0] + 1) / 2, (op.n[1] + 1) / 2, dim == 3 ? (op.n[2] + 1) / 2 : 1};
     dim3 g = grid_for(nc, dim), b(BX, BY);
-    if (dim == 3) k_residual_restrict<R, 3, CB><<<g, b, 0, s>>>(view(op), bb, u, rc, nc[0], nc[1], nc[2]);
-    else k_residual_restrict<R, 2, CB><<<g, b, 0, s>>>(view(op), bb, u, rc, nc[0], nc[1], nc[2]);
+    if (dim == 3) launch_pdl(k_residual_restrict<R, 3, CB>, g, b, 0, s, view(op), bb, u, rc, nc[0], nc[1], nc[2]);
+    else launch_pdl(k_residual_restrict<R, 2, CB>, g, b, 0, s, view(op), bb, u, rc, nc[0], nc[1], nc[2]);
     return cudaGetLastError();
 }
 
@@ -810,8 +822,8 @@ template <typename R>
 cudaError_t launch_prolong_add(const int nf[3], int dim, const typename CT<R>::T *ec, typename CT<R>::T *uf,
                                cudaStream_t s) {
     dim3 g = grid_for(nf, dim), b(BX, BY);
-    if (dim == 3) k_prolong_add<R, 3><<<g, b, 0, s>>>(nf[0], nf[1], nf[2], ec, uf);
-    else k_prolong_add<R, 2><<<g, b, 0, s>>>(nf[0], nf[1], 1, ec, uf);
+    if (dim == 3) launch_pdl(k_prolong_add<R, 3>, g, b, 0, s, nf[0], nf[1], nf[2], ec, uf);
+    else launch_pdl(k_prolong_add<R, 2>, g, b, 0, s, nf[0], nf[1], 1, ec, uf);
     return cudaGetLastError();
 }
 
@@ -819,7 +831,7 @@ template <typename R>
 cudaError_t launch_dense_solve(const int n[3], int dim, int nu, const typename CT<R>::T *minv,
                                const typename CT<R>::T *b, typename CT<R>::T *u, cudaStream_t s) {
     const int threads = 256, warps = threads / 32;
-    k_dense_solve<R><<<cdiv(nu, warps), threads, 0, s>>>(n[0], n[1], dim == 3 ? n[2] : 1, dim, nu, minv, b, u);
+    launch_pdl(k_dense_solve<R>, cdiv(nu, warps), threads, 0, s, n[0], n[1], dim == 3 ? n[2] : 1, dim, nu, minv, b, u);
     return cudaGetLastError();
 }
 
@@ -852,8 +864,8 @@ cudaError_t launch_mg_tail(int dim, int nlev, const DevOp<R> *ops, typename CT<R
         if (e != cudaSuccess) return e;
         attr_set[dim == 3] = true;
     }
-    if (dim == 3) k_mg_tail<R, 3><<<1, TAIL_THREADS, bytes, s>>>(A, gf, gc, zero);
-    else k_mg_tail<R, 2><<<1, TAIL_THREADS, bytes, s>>>(A, gf, gc, zero);
+    if (dim == 3) launch_pdl(k_mg_tail<R, 3>, 1, TAIL_THREADS, bytes, s, A, gf, gc, zero);
+    else launch_pdl(k_mg_tail<R, 2>, 1, TAIL_THREADS, bytes, s, A, gf, gc, zero);
     return cudaGetLastError();
 }
 template cudaError_t launch_mg_tail<float>(int, int, const DevOp<float> *, float2 *const *, float2 *const *,
@@ -864,10 +876,11 @@ template cudaError_t launch_mg_tail<double>(int, int, const DevOp<double> *, dou
                                             int, cudaStream_t);
 
 // Tile shapes (coarse nodes per block) of the temporally blocked kernels, by tile index.
-static const int kTiles[HELM_TILE_COUNT][2] = {{32, 8}, {16, 16}, {16, 8}, {64, 4}};
+static const int kTiles[HELM_TILE_WAVE][2] = {{32, 8}, {16, 16}, {16, 8}, {64, 4}};
 
 bool fused_jacobi2_ok(const int n[3], int dim, int tile) {
-    if (tile < 0 || tile >= HELM_TILE_COUNT) return false;
+    if (tile == HELM_TILE_WAVE) return wave_jacobi2_ok(n, dim);
+    if (tile < 0 || tile >= HELM_TILE_WAVE) return false;
     if (dim != 2 || (n[0] - 1) % 2 || (n[1] - 1) % 2) return false;
     const int ncx = (n[0] + 1) / 2, ncy = (n[1] + 1) / 2;
     // the last tile's owned range must reach the last interior node: a tile row or column
@@ -887,7 +900,7 @@ static cudaError_t pre2_t(const DevOp<float> &op, float omega, const float2 *b, 
         attr = true;
     }
     dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY));
-    k_pre2_restrict<TCX, TCY><<<g, 256, smem, s>>>(view(op), omega, b, u_out, rc, ncx, ncy);
+    launch_pdl(k_pre2_restrict<TCX, TCY>, g, 256, smem, s, view(op), omega, b, u_out, rc, ncx, ncy);
     return cudaGetLastError();
 }
 
@@ -903,7 +916,7 @@ static cudaError_t post2_t(const DevOp<float> &op, float omega, const float2 *b,
         attr = true;
     }
     dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY));
-    k_prolong_post2<TCX, TCY><<<g, 256, smem, s>>>(view(op), omega, b, u_in, u_out, ec, ncx, ncy);
+    launch_pdl(k_prolong_post2<TCX, TCY>, g, 256, smem, s, view(op), omega, b, u_in, u_out, ec, ncx, ncy);
     return cudaGetLastError();
 }
 
@@ -911,6 +924,7 @@ cudaError_t launch_pre2_restrict(const DevOp<float> &op, int tile, float omega, 
                                  float2 *rc, cudaStream_t s) {
     if (!fused_jacobi2_ok(op.n, 2, tile)) return cudaErrorInvalidValue;
     switch (tile) {
+    case HELM_TILE_WAVE: return launch_pre2_wave(op, omega, b, u_out, rc, s);
     case 0: return pre2_t<32, 8>(op, omega, b, u_out, rc, s);
     case 1: return pre2_t<16, 16>(op, omega, b, u_out, rc, s);
     case 2: return pre2_t<16, 8>(op, omega, b, u_out, rc, s);
@@ -922,6 +936,7 @@ cudaError_t launch_prolong_post2(const DevOp<float> &op, int tile, float omega, 
                                  float2 *u_out, const float2 *ec, cudaStream_t s) {
     if (!fused_jacobi2_ok(op.n, 2, tile)) return cudaErrorInvalidValue;
     switch (tile) {
+    case HELM_TILE_WAVE: return launch_post2_wave(op, omega, b, u_in, u_out, ec, s);
     case 0: return post2_t<32, 8>(op, omega, b, u_in, u_out, ec, s);
     case 1: return post2_t<16, 16>(op, omega, b, u_in, u_out, ec, s);
     case 2: return post2_t<16, 8>(op, omega, b, u_in, u_out, ec, s);
@@ -931,12 +946,12 @@ cudaError_t launch_prolong_post2(const DevOp<float> &op, int tile, float omega, 
 
 template <typename CI, typename CO>
 cudaError_t launch_convert(size_t n, const CI *in, CO *out, cudaStream_t s) {
-    k_convert<CI, CO><<<(unsigned)std::min<size_t>(cdiv(n, 256), 152 * 16), 256, 0, s>>>(n, in, out);
+    launch_pdl(k_convert<CI, CO>, (unsigned)std::min<size_t>(cdiv(n, 256), 152 * 16), 256, 0, s, n, in, out);
     return cudaGetLastError();
 }
 
 template <typename C> cudaError_t launch_zero(size_t n, C *x, cudaStream_t s) {
-    k_zero<C><<<(unsigned)std::min<size_t>(cdiv(n, 256), 152 * 16), 256, 0, s>>>(n, x);
+    launch_pdl(k_zero<C>, (unsigned)std::min<size_t>(cdiv(n, 256), 152 * 16), 256, 0, s, n, x);
     return cudaGetLastError();
 }
 

@@ -417,6 +417,7 @@ static cudaError_t run_graph(helm_handle *h, cudaGraphExec_t &exec, F work) {
         h->stream = h->cap_stream;
         cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
+            pdl_capture_scope no_pdl;
             h->capturing = true;
             e = work();
             h->capturing = false;

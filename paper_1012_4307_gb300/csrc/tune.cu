@@ -19,6 +19,7 @@ namespace {
 
 // v[q] = a fixed pseudo-random complex value in [-1/2, 1/2)^2 (integer hash of q).
 __global__ void k_fill_probe(size_t n, double2 *v) {
+    pdl_enter();
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
         unsigned long long x = (unsigned long long)q * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
         x ^= x >> 31;
@@ -79,31 +80,49 @@ extern "C" helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, h
         st = helm_fail(HELM_ERR_CUDA, "autotune %s: %s", what, cudaGetErrorString(e));
         return -1.0;
     };
-    // milliseconds per preconditioner application under tuning t (best of three timings); a
-    // candidate whose first launch is refused (soft: a cluster shape the device cannot run)
-    // is skipped
+    // milliseconds per preconditioner application under tuning t: reps applications captured in
+    // a CUDA graph (the form in which the FGMRES steps run them), replayed, best of three
+    // timings; a candidate whose capture fails (soft: a cluster shape the device cannot run) is
+    // skipped
     auto time_it = [&](const helm_tuning &t, bool soft = false) -> double {
         h->tune = t;
-        cudaError_t e = cudaSuccess;
-        for (int w = 0; w < 2 && e == cudaSuccess; w++)
-            e = c64 ? precondition<float>(h, v, (float2 *)z) : precondition<double>(h, v, (double2 *)z);
-        if (e != cudaSuccess && soft) {
-            cudaGetLastError();
-            return -2.0;
-        }
-        if (e != cudaSuccess) return fail(e, "warm-up");
-        double bestt = 1e300;
-        for (int rep = 0; rep < 3; rep++) {
-            if ((e = cudaEventRecord(e0, h->stream)) != cudaSuccess) return fail(e, "event");
+        cudaStream_t keep_s = h->stream;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        h->stream = h->cap_stream;
+        cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            pdl_capture_scope no_pdl;
+            h->capturing = true;
             for (int r = 0; r < reps && e == cudaSuccess; r++)
                 e = c64 ? precondition<float>(h, v, (float2 *)z) : precondition<double>(h, v, (double2 *)z);
-            if (e != cudaSuccess) return fail(e, "cycle");
-            if ((e = cudaEventRecord(e1, h->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess)
-                return fail(e, "event");
+            h->capturing = false;
+            const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+            if (e == cudaSuccess) e = e2;
+        }
+        h->stream = keep_s;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            if (ge) cudaGraphExecDestroy(ge);
+            if (soft) {
+                cudaGetLastError();
+                return -2.0;
+            }
+            return fail(e, "capture");
+        }
+        double bestt = 1e300;
+        for (int w = 0; w < 2 && e == cudaSuccess; w++) e = cudaGraphLaunch(ge, h->stream);
+        for (int rep = 0; rep < 3 && e == cudaSuccess; rep++) {
             float ms = 0.f;
-            if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return fail(e, "event");
+            if ((e = cudaEventRecord(e0, h->stream)) != cudaSuccess || (e = cudaGraphLaunch(ge, h->stream)) != cudaSuccess ||
+                (e = cudaEventRecord(e1, h->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+                (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+                break;
             bestt = std::min(bestt, (double)ms / reps);
         }
+        cudaGraphExecDestroy(ge);
+        if (e != cudaSuccess) return fail(e, "replay");
         return bestt;
     };
     helm_tuning cur = keep;
@@ -149,10 +168,13 @@ extern "C" helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, h
             if (ms >= 0 && ms < cur_ms) { cur = t; cur_ms = ms; }
         }
     };
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        st = helm_fail(HELM_ERR_CUDA, "autotune capture stream");
+    } else if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         st = helm_fail(HELM_ERR_CUDA, "autotune events");
     } else {
-        k_fill_probe<<<(unsigned)std::min<size_t>(cdiv(np, 256), 152 * 8), 256, 0, h->stream>>>(np, v);
+        launch_pdl(k_fill_probe, (unsigned)std::min<size_t>(cdiv(np, 256), 152 * 8), 256, 0, h->stream, np, v);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) fail(e, "fill");
         if (st == HELM_OK) {

@@ -62,10 +62,8 @@ def parse():
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_1012_4307_gb300.distributed import rank_env
+    return rank_env()
 
 
 def load_peaks():
@@ -227,15 +225,24 @@ GS_NAMES = {"dcgs2": "double-FP32 delayed CGS2 on float-pair vectors",
 
 def run_batch(args):
     """COUNT problems solved together (one host thread, one stream and CUDA-graph-replayed
-    FGMRES steps per problem) against the same problems solved one after another."""
+    FGMRES steps per problem) against the same problems solved one after another.  Under
+    torchrun the problems are sharded over the ranks by longest processing time (no data
+    exchange); the job's time is the slowest rank's."""
     import torch
+    import torch.distributed as dist
 
+    from paper_1012_4307_gb300 import distributed as D
     from paper_1012_4307_gb300 import helm
     from paper_1012_4307_gb300 import workloads as W
 
-    torch.cuda.set_device(0)
+    world, rank, local = D.rank_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     helm.load()
-    probs = W.config_batch(count=args.batch)
+    all_probs = W.config_batch(count=args.batch)
+    shard = D.lpt_partition([D.solve_cost(P.n) for P in all_probs], world)[rank]
+    probs = [all_probs[i] for i in shard]
     mg = helm.MGParams(kind="csg", prec="c64", gs=args.gs, coarsest_n=17)
     specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
     b = helm.helm_create_batch(specs, mg=mg)
@@ -254,7 +261,10 @@ def run_batch(args):
 
     for _ in range(max(1, args.warmup)):
         batch_once()
-    sampler = ClockSampler(0)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
     sampler.start()
     tot = 0.0
     for _ in range(args.steps):
@@ -264,11 +274,15 @@ def run_batch(args):
         e1.record(stream)
         e1.synchronize()
         tot += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clocks = sampler.stop()
-    ms = tot / args.steps
+    ms = D.max_over_ranks(tot / args.steps, device="cuda")
+    unknowns = int(D.sum_over_ranks(unknowns, device="cuda"))
     # the same problems one after another through krylov_solve (same handles' settings)
     seq_ms = 0.0
-    for P, r in zip(probs, rhs):
+    for P, r in (zip(probs, rhs) if world == 1 else []):
         h = helm.helm_create(2, [P.n, P.n], torch.from_numpy(P.k2).cuda(), theta=P.theta, mg=mg)
         if tunings:
             helm.helm_set_tuning(h, tunings[helm.tuning_key(h, "c64")])
@@ -282,16 +296,22 @@ def run_batch(args):
         seq_ms += e0.elapsed_time(e1)
         h.close()
     line = {"metric": "batched solve throughput (all problems to rel. residual %.0e)" % args.tol,
-            "value": unknowns / (ms / 1e3) / 1e6, "unit": "Mdof/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "c64 cycle / f64 outer",
-            "data": "synthetic",
+            "value": unknowns / (ms / 1e3) / 1e6, "unit": "Mdof/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+            "dtype": "c64 cycle / f64 outer", "data": "synthetic",
             "config": {"workload": "batch of %d 2D well problems, sizes {129,257,513,1025}, E in [0.5,4]" % args.batch,
-                       "unknowns": unknowns, "sizes": [P.n for P in probs],
+                       "unknowns": unknowns, "sizes": [P.n for P in all_probs],
+                       "parallelism": "problems sharded over ranks by longest processing time" if world > 1 else "single GPU",
                        "l2": "256 MiB device write before every step, outside the timed events",
                        "cycle_tuning": tunings},
-            "iterations": [s.iterations for s in stats], "sequential_ms": seq_ms,
-            "speedup_vs_sequential": seq_ms / ms, "clocks": clocks}
-    print(json.dumps(line), flush=True)
+            "iterations_rank0": [s.iterations for s in stats],
+            "sequential_ms": seq_ms if world == 1 else None,
+            "speedup_vs_sequential": seq_ms / ms if world == 1 else None, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------------------------- our arm

@@ -45,6 +45,23 @@ __device__ __forceinline__ RowCoef row_coef(const WaveOp &o, int y) {
     return r;
 }
 
+// Inputs of one row at the lane's column: b, k^2 (zero outside the interior) and the row's y
+// coefficients.
+struct RowIn {
+    float2 b;
+    float k2;
+    RowCoef ry;
+};
+__device__ __forceinline__ RowIn load_row_in(const WaveOp &o, const float2 *__restrict__ b, int x, bool xin, int y) {
+    RowIn r;
+    r.ry = row_coef(o, y);
+    const bool in = xin && y >= 1 && y <= o.ny - 2;
+    const size_t p = (size_t)(in ? x : 1) + (size_t)o.nx * (size_t)(in ? y : 1);  // in range either way
+    r.b = in ? b[p] : make_float2(0.f, 0.f);
+    r.k2 = in ? o.k2[p] : 0.f;
+    return r;
+}
+
 // (M u)(x, y) from the row's values (u, its x-neighbours uw, ue, the rows above and below un,
 // us) and the coefficients; d = the diagonal.
 __device__ __forceinline__ float2 wave_apply(float2 cxw, float2 cxe, const RowCoef &ry, float2 d, float2 u, float2 uw,
@@ -87,20 +104,26 @@ __global__ void __launch_bounds__(32 * WV_WARPS) k_pre2_wave(WaveOp o, float ome
     float2 u1[3] = {z, z, z}, bb[3] = {z, z, z}, dd[3] = {z, z, z}, iv[3] = {z, z, z};
     RowCoef ry[3] = {{z, z, z}, {z, z, z}, {z, z, z}};
     float2 u2[3] = {z, z, z}, ax[3] = {z, z, z};
+    // row inputs are loaded two rows ahead of their use
+    RowIn pf[2];
+    pf[0] = load_row_in(o, b, x, xin, y0);
+    pf[1] = load_row_in(o, b, x, xin, y0 + 1);
     for (int y = y0; y <= y1; y++) {
+        const RowIn cur = pf[0];
+        pf[0] = pf[1];
+        pf[1] = load_row_in(o, b, x, xin, y + 2);
         // shift windows; row y enters at index 2
         u1[0] = u1[1]; u1[1] = u1[2];
         bb[0] = bb[1]; bb[1] = bb[2];
         dd[0] = dd[1]; dd[1] = dd[2];
         iv[0] = iv[1]; iv[1] = iv[2];
         ry[0] = ry[1]; ry[1] = ry[2];
-        ry[2] = row_coef(o, y);
+        ry[2] = cur.ry;
         const bool in = xin && y >= 1 && y <= ny - 2;
         float2 bv = z, dv = z, inv = z, v1 = z;
         if (in) {
-            const size_t p = (size_t)x + (size_t)nx * y;
-            bv = b[p];
-            dv = cadd(cadd(cxc, ry[2].c), cadd(cscale(o.bk, o.k2[p]), o.c));
+            bv = cur.b;
+            dv = cadd(cadd(cxc, ry[2].c), cadd(cscale(o.bk, cur.k2), o.c));
             inv = cscale(cinv_fast(dv), omega);
             v1 = cmul(bv, inv);  // first sweep from zero
         }
@@ -162,24 +185,45 @@ __global__ void __launch_bounds__(32 * WV_WARPS) k_post2_wave(WaveOp o, float om
     const bool ca = xa >= 0 && xa < ncx, cb = xb >= 0 && xb < ncx;
     float2 u3[3] = {z, z, z}, bb[3] = {z, z, z}, dd[3] = {z, z, z}, iv[3] = {z, z, z}, u4[3] = {z, z, z};
     RowCoef ry[3] = {{z, z, z}, {z, z, z}, {z, z, z}};
+    // row inputs (b, k^2, the iterate, and the interpolated correction) two rows ahead
+    struct PostIn {
+        RowIn r;
+        float2 u, e;
+    };
+    auto load_post = [&](int yy) {
+        PostIn q;
+        q.r = load_row_in(o, b, x, xin, yy);
+        q.u = z;
+        q.e = z;
+        if (xin && yy >= 1 && yy <= ny - 2) {
+            q.u = u_in[(size_t)x + (size_t)nx * yy];
+            const int ya = yy >> 1, yb = (yy + 1) >> 1;
+            const float2 e00 = ca ? ec[(size_t)xa + (size_t)ncx * ya] : z, e01 = cb ? ec[(size_t)xb + (size_t)ncx * ya] : z;
+            const float2 e10 = ca ? ec[(size_t)xa + (size_t)ncx * yb] : z, e11 = cb ? ec[(size_t)xb + (size_t)ncx * yb] : z;
+            q.e = cadd(cadd(e00, e01), cadd(e10, e11));
+        }
+        return q;
+    };
+    PostIn pf[2];
+    pf[0] = load_post(y0);
+    pf[1] = load_post(y0 + 1);
     for (int y = y0; y <= y1; y++) {
+        const PostIn cur = pf[0];
+        pf[0] = pf[1];
+        pf[1] = load_post(y + 2);
         u3[0] = u3[1]; u3[1] = u3[2];
         bb[0] = bb[1]; bb[1] = bb[2];
         dd[0] = dd[1]; dd[1] = dd[2];
         iv[0] = iv[1]; iv[1] = iv[2];
         ry[0] = ry[1]; ry[1] = ry[2];
-        ry[2] = row_coef(o, y);
+        ry[2] = cur.r.ry;
         const bool in = xin && y >= 1 && y <= ny - 2;
         float2 bv = z, dv = z, inv = z, v3 = z;
         if (in) {
-            const size_t p = (size_t)x + (size_t)nx * y;
-            bv = b[p];
-            dv = cadd(cadd(cxc, ry[2].c), cadd(cscale(o.bk, o.k2[p]), o.c));
+            bv = cur.r.b;
+            dv = cadd(cadd(cxc, ry[2].c), cadd(cscale(o.bk, cur.r.k2), o.c));
             inv = cscale(cinv_fast(dv), omega);
-            const int ya = y >> 1, yb = (y + 1) >> 1;
-            const float2 e00 = ca ? ec[(size_t)xa + (size_t)ncx * ya] : z, e01 = cb ? ec[(size_t)xb + (size_t)ncx * ya] : z;
-            const float2 e10 = ca ? ec[(size_t)xa + (size_t)ncx * yb] : z, e11 = cb ? ec[(size_t)xb + (size_t)ncx * yb] : z;
-            v3 = cadd(u_in[p], cscale(cadd(cadd(e00, e01), cadd(e10, e11)), 0.25f));
+            v3 = cadd(cur.u, cscale(cur.e, 0.25f));
         }
         bb[2] = bv; dd[2] = dv; iv[2] = inv; u3[2] = v3;
         // first post-sweep at row y - 1

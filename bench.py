@@ -203,7 +203,16 @@ def run_reference(args):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
 # kernels, from the ncu captures summarised under profiles/.  Reported only while the kernel's
 # source file is the one that was captured (same SHA-1); otherwise null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "update_norm": dict(kernel="k_update2_pair", source="paper_1012_4307_gb300/csrc/kernels_gs_df.cu",
+                        sha1="be81566544e950d2de630ba8a61bd026354858ce", bytes=310652160,
+                        launch="basis slot j = 15, the mean over a restart cycle being 14.5",
+                        profile="profiles/gram_schmidt_dcgs2_kernels_n1025.md"),
+    "mdot": dict(kernel="k_mdot2_pair", source="paper_1012_4307_gb300/csrc/kernels_gs_df.cu",
+                 sha1="be81566544e950d2de630ba8a61bd026354858ce", bytes=344757760,
+                 launch="basis slot j = 15, the mean over a restart cycle being 14.5",
+                 profile="profiles/gram_schmidt_dcgs2_kernels_n1025.md"),
+}
 
 
 def ncu_traffic(kernel_class):

@@ -142,10 +142,17 @@ class Problem:
     restart: int = 30
     tol: float = 1e-10
     extra: dict = field(default_factory=dict)
+    r0_lo: float | None = None  # start of the lower layer (default -r0; outside [lo, hi]: none)
+    r0_hi: float | None = None  # start of the upper layer (default r0)
 
     @property
     def unknowns(self) -> int:
         return (self.n - 2) ** self.dim
+
+    @property
+    def layers(self):
+        """(r0_lo, r0_hi) of every axis."""
+        return (-self.r0 if self.r0_lo is None else self.r0_lo, self.r0 if self.r0_hi is None else self.r0_hi)
 
 
 def config_small(n: int = 65) -> Problem:
@@ -191,3 +198,55 @@ def config_adjoint(n: int = 513):
     g = gaussian_source(2, n, 0.05, 5).real.copy()
     p.extra["probe"] = g
     return p
+
+
+# ---------------------------------------------------------------- the paper's model problems
+# Section 6 (Tables 1-4): 2D, Bi-CGSTAB with one multigrid cycle per preconditioner call.
+
+def paper_mp1(k: float = 160.0, interior_cells: int = 256, layer_cells: int = 64) -> Problem:
+    """MP1 (Table 1): Z = -Delta - k^2 with ECS layers of ``layer_cells`` cells on all four sides
+    of an interior of ``interior_cells`` cells of width 1 / interior_cells (coordinates shifted so
+    that the interior is [-1/2, 1/2]^2), ECS angle pi/6, and a point source: f = 1 at the centre
+    node, 0 elsewhere."""
+    h = 1.0 / interior_cells
+    n = interior_cells + 2 * layer_cells + 1
+    half = 0.5 + layer_cells * h
+    k2 = np.full((n, n), k * k)
+    f = np.zeros((n, n), complex)
+    f[n // 2, n // 2] = 1.0
+    return Problem("mp1-k%g" % k, 2, n, k2, f, theta=math.pi / 6, r0=0.5, lo=-half, hi=half, coarsest_n=17,
+                   tol=1e-6)
+
+
+def _ne_layer_problem(name, k2fun, size, interior_cells, layer_cells):
+    """Square [0, size] of interior_cells cells per axis, ECS layers of layer_cells cells on the
+    east and north sides only (Dirichlet at x = 0 and y = 0), ECS angle pi/6; source
+    f = exp(-(x^2 + y^2)) (the printed exp(x^2 + y^2) read as the decaying Gaussian)."""
+    h = size / interior_cells
+    n = interior_cells + layer_cells + 1
+    hi = size + layer_cells * h
+    X = coords(2, n, 0.0, hi)
+    k2 = np.ascontiguousarray(np.broadcast_to(k2fun(X[0], X[1]), (n, n))).astype(np.float64)
+    f = np.exp(-(X[0] ** 2 + X[1] ** 2)).astype(np.complex128)
+    f = np.ascontiguousarray(np.broadcast_to(f, (n, n))).copy()
+    _zero_ring(f)
+    return Problem(name, 2, n, k2, f, theta=math.pi / 6, lo=0.0, hi=hi, r0_lo=-1.0, r0_hi=size, coarsest_n=17,
+                   tol=1e-6)
+
+
+def paper_mp2(k: float = 4.0, nu: float = 7.0, size: float = 50.0, interior_cells: int = 512,
+              layer_cells: int = 128) -> Problem:
+    """MP2 (Table 2): Z = -Delta - nu (exp(-x^2) + exp(-y^2)) - k^2, i.e. k^2(x, y) = k^2 +
+    nu (exp(-x^2) + exp(-y^2)) at the real nodes."""
+    return _ne_layer_problem("mp2-k%g-nu%g" % (k, nu), lambda x, y: k * k + nu * (np.exp(-x * x) + np.exp(-y * y)),
+                             size, interior_cells, layer_cells)
+
+
+def paper_mp3(k: float = 2.0, size: float = 50.0, interior_cells: int = 512, layer_cells: int = 128) -> Problem:
+    """MP3 (Tables 3, 4): Z = -Delta - 1/x - 1/y - k^2, i.e. k^2(x, y) = k^2 + 1/x + 1/y at the
+    real nodes (the singular boundary nodes x = 0, y = 0 are Dirichlet)."""
+    def k2fun(x, y):
+        with np.errstate(divide="ignore"):
+            v = k * k + 1.0 / x + 1.0 / y
+        return np.where(np.isfinite(v), v, 0.0)
+    return _ne_layer_problem("mp3-k%g-L%g" % (k, size), k2fun, size, interior_cells, layer_cells)

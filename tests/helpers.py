@@ -23,13 +23,14 @@ def gpu_handle(helm, P, **kw):
     n = P.n if hasattr(P.n, "__len__") else [P.n] * P.dim
     k2 = torch.from_numpy(np.ascontiguousarray(P.k2)).cuda()
     mg = mg_params(helm, coarsest_n=kw.pop("coarsest_n", P.coarsest_n), **kw)
-    return helm.helm_create(P.dim, n, k2, theta=P.theta, r0_lo=[-P.r0] * P.dim, r0_hi=[P.r0] * P.dim,
+    r0lo, r0hi = P.layers
+    return helm.helm_create(P.dim, n, k2, theta=P.theta, r0_lo=[r0lo] * P.dim, r0_hi=[r0hi] * P.dim,
                             lo=[P.lo] * P.dim, hi=[P.hi] * P.dim, mg=mg)
 
 
 def oracle_pair(O, P, pc="csg", theta_a=math.pi / 14, beta=(-1.0, -0.5), re_lambda0=None):
     n = P.n if hasattr(P.n, "__len__") else [P.n] * P.dim
-    z = [O.contour(n[a], P.lo, P.hi, P.theta, -P.r0, P.r0) for a in range(P.dim)]
+    z = [O.contour(n[a], P.lo, P.hi, P.theta, *P.layers) for a in range(P.dim)]
     return O.helmholtz_ops(z, P.k2, pc=pc, theta_a=theta_a, beta=beta, re_lambda0=re_lambda0)
 
 

@@ -1,0 +1,64 @@
+"""The paper's model problems MP1-MP3 (Section 6) with the preconditioners and cycles of
+Tables 1-4: Bi-CGSTAB with one cycle per preconditioner call (FP64 cycle and vectors), and the
+stand-alone multigrid convergence factor of each preconditioner.  The paper's printed counts
+(tests/golden/paper_tables.json) are context; the checks are that every solve converges and
+the paper's comparative findings: QD needs more Krylov iterations than CSL and CSG, and QD's
+multigrid converges faster than theirs (Section 6)."""
+import json
+import math
+import os
+
+import pytest
+
+from helpers import gpu_handle, to_gpu
+from paper_1012_4307_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+BUILDERS = {"mp1": W.paper_mp1, "mp2": W.paper_mp2, "mp3": W.paper_mp3}
+
+
+@pytest.fixture(scope="module")
+def helm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1012_4307_gb300 import helm as H
+    H.load()
+    return H
+
+
+def run_table(helm, table):
+    spec = GOLDEN[table]
+    P = BUILDERS[spec["problem"]](**spec["args"])
+    f = to_gpu(P.f)
+    out = {}
+    for pc in ("csl", "csg", "qd"):
+        c = spec[pc]
+        kw = dict(pc=pc, prec="c128", smoother=c["smoother"], nu=(1, 1), omega=c["omega"], gamma=(1, c["gamma_c"]))
+        if "beta" in c:
+            kw["beta"] = tuple(c["beta"])
+        if "theta_a_pi_over" in c:
+            kw["theta_a"] = math.pi / c["theta_a_pi_over"]
+        if "re_lambda0" in c:
+            kw["re_lambda0"] = c["re_lambda0"]
+        h = gpu_handle(helm, P, **kw)
+        x, st = helm.krylov_solve(h, f, tol=P.tol, method="bicgstab", maxit=5000)
+        _, cycles, factor = helm.helm_mg_conv(h, f, tol=1e-6, maxcyc=500)
+        out[pc] = dict(iterations=st.iterations, rel_res=st.rel_res, status=st.status, mg_conv=factor,
+                       mg_cycles=cycles, paper=dict(iterations=c["iterations"], mg_conv=c["mg_conv"],
+                                                    mg_cycles=c["mg_cycles"]))
+        h.close()
+    return out
+
+
+@pytest.mark.parametrize("table", ["T1", "T2", "T3", "T4"])
+def test_paper_model_problem(helm, table):
+    out = run_table(helm, table)
+    print("\n%s %s" % (table, json.dumps(out)))
+    for pc, r in out.items():
+        assert r["status"] == helm.HELM_OK and r["rel_res"] <= 1e-6, (pc, r)
+    assert out["qd"]["iterations"] > max(out["csl"]["iterations"], out["csg"]["iterations"])
+    assert out["qd"]["mg_conv"] < min(out["csl"]["mg_conv"], out["csg"]["mg_conv"])

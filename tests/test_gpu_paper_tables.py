@@ -1,9 +1,10 @@
 """The paper's model problems MP1-MP3 (Section 6) with the preconditioners and cycles of
-Tables 1-4: Bi-CGSTAB with one cycle per preconditioner call (FP64 cycle and vectors), and the
-stand-alone multigrid convergence factor of each preconditioner.  The paper's printed counts
-(tests/golden/paper_tables.json) are context; the checks are that every solve converges and
-the paper's comparative findings: QD needs more Krylov iterations than CSL and CSG, and QD's
-multigrid converges faster than theirs (Section 6)."""
+Tables 1-4: Bi-CGSTAB with one cycle per preconditioner call (FP64 cycle and vectors) to a
+relative residual of 1e-6, and the stand-alone multigrid convergence of each preconditioner,
+against the printed numbers (tests/golden/paper_tables.json): every solve converges, the
+multigrid cycle counts equal the printed ones, factors and Bi-CGSTAB iteration counts come
+close, and the paper's comparative findings hold (QD needs more Krylov iterations than CSL
+and CSG, and its multigrid converges faster than theirs)."""
 import json
 import math
 import os
@@ -60,5 +61,11 @@ def test_paper_model_problem(helm, table):
     print("\n%s %s" % (table, json.dumps(out)))
     for pc, r in out.items():
         assert r["status"] == helm.HELM_OK and r["rel_res"] <= 1e-6, (pc, r)
+        # against the printed numbers: the stand-alone multigrid needs exactly the printed cycle
+        # count, its factor comes within 0.06, and Bi-CGSTAB within 15% of the printed iterations
+        p = r["paper"]
+        assert r["mg_cycles"] == p["mg_cycles"], (pc, r)
+        assert abs(r["mg_conv"] - p["mg_conv"]) <= 0.06, (pc, r)
+        assert abs(r["iterations"] - p["iterations"]) <= 0.15 * p["iterations"], (pc, r)
     assert out["qd"]["iterations"] > max(out["csl"]["iterations"], out["csg"]["iterations"])
     assert out["qd"]["mg_conv"] < min(out["csl"]["mg_conv"], out["csg"]["mg_conv"])

@@ -6,6 +6,7 @@ term, a wrong sign of the complex scaling, a transposed index, a wrong restricti
 swapped cycle index) fails at least one of them.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -526,3 +527,42 @@ def test_adjoint_gradient_dense(oracle):
         Lm = abs(gi @ np.linalg.solve(oracle.Op(z, k2m).dense(), fi)) ** 2
         fd = (Lp - Lm) / (2 * eps)
         assert abs(fd - grad[p]) <= 1e-6 * max(abs(fd), np.abs(grad).max() * 1e-3)
+
+
+# ---------------------------------------------------------------- the paper's Table 1 (MP1)
+def _table1():
+    import json
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))["T1"]
+
+
+def test_oracle_reproduces_table1_multigrid_cycles(oracle):
+    """Section 6, Table 1 (MP1: k = 160, 256 interior cells, 64 ECS cells per side, angle pi/6):
+    the stand-alone multigrid for CSL (F_1^4(1,1), omega-Jacobi 0.8, beta = (-1, -0.3)), CSG
+    (F_1^3(1,1), theta_a = pi/14) and QD (V(1,1) red-black 1.0, Re lambda0 = -2.6e4) reaches
+    1e-6 in exactly the printed 17, 15 and 6 cycles; the convergence factors (geometric mean of
+    the last five reductions) come within 0.06 of the printed 0.43, 0.39 and 0.09."""
+    T = _table1()
+    P = W.paper_mp1()
+    z = [oracle.contour(P.n, P.lo, P.hi, P.theta, *P.layers) for _ in range(2)]
+    for pc, kw in (("csl", dict(beta=tuple(T["csl"]["beta"]))), ("csg", dict(theta_a=math.pi / 14)),
+                   ("qd", dict(re_lambda0=T["qd"]["re_lambda0"]))):
+        c = T[pc]
+        A, M = oracle.helmholtz_ops(z, P.k2, pc=pc, **kw)
+        mg = oracle.MG(M, 17, 1, 1, c["omega"], c["smoother"])
+        cycles, factor, _ = mg.mg_conv(P.f, tol=1e-6, maxcyc=200, gamma_f=1, gamma_c=c["gamma_c"])
+        assert cycles == c["mg_cycles"], (pc, cycles)
+        assert abs(factor - c["mg_conv"]) <= 0.06, (pc, factor)
+
+
+def test_oracle_reproduces_table1_bicgstab_csg(oracle):
+    """Section 6, Table 1: right-preconditioned Bi-CGSTAB with one F_1^3(1,1) CSG cycle per
+    preconditioner call takes the printed 62 iterations (to a relative residual of 1e-6, the
+    tolerance read from the tables)."""
+    T = _table1()
+    P = W.paper_mp1()
+    z = [oracle.contour(P.n, P.lo, P.hi, P.theta, *P.layers) for _ in range(2)]
+    A, M = oracle.helmholtz_ops(z, P.k2, pc="csg", theta_a=math.pi / 14)
+    mg = oracle.MG(M, 17, 1, 1, 0.8, "jacobi")
+    x, st = oracle.bicgstab(A, mg, P.f, tol=1e-6, maxit=500, gamma_f=1, gamma_c=3)
+    assert st["status"] == 0 and st["rel_res"] <= 1e-6
+    assert abs(st["iterations"] - T["csg"]["iterations"]) <= 3, st["iterations"]

@@ -97,6 +97,7 @@ struct helm_handle {
     // delayed CGS2: inner products of a step (2 (m + 1)), normalisation norms alpha_j (m + 2),
     // update coefficients (2 m + 4); closing step of a cycle with jc columns: event and graph jc
     double2 *hv = nullptr, *alpha2 = nullptr, *dcoef = nullptr;
+    unsigned *tickets = nullptr;  // last-block counters of the fused passes (0 between launches)
     // side stream of a step (the Givens rotation runs beside the update pass): fork and join
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

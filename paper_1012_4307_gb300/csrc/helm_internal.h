@@ -234,12 +234,18 @@ cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int n
 //   coef:   one-thread FP64 step of the method (kernels_krylov.cu)
 //   update: slot j <- final v_j, slot j+1 <- once-orthogonalised w; partials[b] = ||w||^2
 //           (G = gs_df_update_nblocks)
+// The update pass with a ticket (a device counter at 0 between launches) writes (||w||, 0) to
+// alpha_out from its last block; without one (null) it only writes partials.  The dot pass's
+// partials go to launch_reduce_dcgs2: one block per value, and the last block to finish runs the
+// coefficient step of step j (ticket as above).
 cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *x, const float4 *w,
                               double2 *partials, cudaStream_t s);
+cudaError_t launch_reduce_dcgs2(const double2 *partials, int nblk, double2 *hv, unsigned *ticket, int j,
+                                const double2 *alpha2, double2 *H, int ldh, double2 *coef, cudaStream_t s);
 cudaError_t launch_dcgs2_coef(int j, int has_w, const double2 *hv, const double2 *alpha2, double2 *H, int ldh,
                               double2 *coef, cudaStream_t s);
 cudaError_t launch_update2_pair(size_t n, float4 *V, size_t ldv, int j, const double2 *coef, double2 *partials,
-                                cudaStream_t s);
+                                unsigned *ticket, double2 *alpha_out, cudaStream_t s);
 // w <- w / beta->x (float pairs)
 cudaError_t launch_scale_inv_pair(size_t n, float4 *w, const double2 *beta, cudaStream_t s);
 // in place: the double2 vector x becomes the float-pair vector x / beta->x (beta null: 1)

@@ -17,6 +17,7 @@
 // Same partials layout and gate as k_mdot_norm / k_update_norm in kernels_krylov.cu.
 #include "helm_internal.h"
 #include "df_arith.h"
+#include "dcgs2_coef.cuh"
 
 namespace {
 
@@ -270,8 +271,11 @@ __global__ void __launch_bounds__(NT, 4) k_mdot2_pair(size_t n, const float4 *__
 //                                                normalised)
 // with A = coef[0..j), C = coef[j..2j), r = coef[2j].x, s = coef[2j + 1];
 // partials[b] = (||w||^2, 0).
+// With a ticket, the last block to finish also reduces the norm partials into
+// *alpha_out = (||w||, 0).
 __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
-                                                     const double2 *__restrict__ coef, double2 *__restrict__ partials) {
+                                                     const double2 *__restrict__ coef, double2 *__restrict__ partials,
+                                                     unsigned *ticket, double2 *alpha_out) {
     pdl_enter();
     __shared__ float4 cA[64], cC[64];
     __shared__ float4 sc[2];  // (r hi, lo, 0, 0), s
@@ -354,6 +358,9 @@ __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restric
     ff vals[1] = {ff_norm(sn, cn)};
     block_sum_ff<1>(vals, sums);
     if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(sums[0], 0.0);
+    if (!ticket || !last_block(ticket, gridDim.x)) return;
+    reduce_partials_block(partials, gridDim.x, 1, alpha_out, true);
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // 1 / beta.x as a float pair, one FP64 division per block.
@@ -474,9 +481,9 @@ cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, con
 }
 
 cudaError_t launch_update2_pair(size_t n, float4 *V, size_t ldv, int j, const double2 *coef, double2 *partials,
-                                cudaStream_t s) {
+                                unsigned *ticket, double2 *alpha_out, cudaStream_t s) {
     if (j < 0 || j > 64) return cudaErrorInvalidValue;
-    launch_pdl(k_update2_pair, gs_df_update_nblocks(n), NT, 0, s, n, V, ldv, j, coef, partials);
+    launch_pdl(k_update2_pair, gs_df_update_nblocks(n), NT, 0, s, n, V, ldv, j, coef, partials, ticket, alpha_out);
     return cudaGetLastError();
 }
 

@@ -9,6 +9,7 @@
 // the same kernels, gated by the device flag, so the host never waits for the decision.
 // On GB300 the FP64 units (about 2 FMA per SM per clock) bound these kernels, not DRAM.
 #include "helm_internal.h"
+#include "dcgs2_coef.cuh"
 
 namespace {
 
@@ -199,76 +200,28 @@ __global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, do
     est[j] = hypot(g[j + 1].x, g[j + 1].y) / fnorm;
 }
 
-// DCGS2 coefficients of step j (one thread; Swirydowicz, Langou, Ananthan, Yang & Thomas,
-// "Low synchronization Gram-Schmidt and GMRES algorithms", 2020; Bielich et al. 2022).
-// Basis slot j holds x = alpha u: the once-orthogonalised vector of step j - 1, not normalised
-// (alpha = alpha2[j].x its norm; slot 0 holds the final v_0 and alpha = 1).  From
-// hv[i] = V_i^H x (i <= j; hv[j] = x^H x) and, with has_w, hv[j + 1 + i] = V_i^H w (i <= j):
-//   u = sum_{i<j} a_i v_i + nu v_j,  a_i = hv[i] / alpha,  nu = sqrt(hv[j] / alpha^2 - |a|^2)
-//   (nu = 1 for j = 0, where slot 0 already holds the final v_0);
-//   column j - 1 of H, first-pass entries plus alpha a, gets its final values and
-//   H[j][j-1] = alpha nu;
-//   column j: c_i = hv[j+1+i] (i < j), H[j][j] = v_j^H w = (hv[2j+1] / alpha - a^H c) / nu;
-//   with s = H[j][j] / nu, the update pass forms v_j = (x - sum V_i (alpha a_i)) / (alpha nu)
-//   and w' = w - x (s / alpha) - sum V_i (c_i - a_i s): coef[i] = alpha a_i,
-//   coef[j+i] = c_i - a_i s, coef[2j] = 1 / (alpha nu), coef[2j+1] = s / alpha.
-__device__ __forceinline__ double warp_sum_d(double v) {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return v;
+// The reduction of the two-vector inner-product pass (block v sums value v of the partials in
+// the fixed order of k_reduce) followed, in the last block to finish, by the DCGS2 coefficient
+// step of step j (see dcgs2_coef.cuh); the ticket returns to 0.
+__global__ void k_reduce_dcgs2(const double2 *__restrict__ partials, int nblk, double2 *hv, unsigned *ticket, int j,
+                               const double2 *alpha2, double2 *H, int ldh, double2 *coef) {
+    pdl_enter();
+    __shared__ double2 sums[1];
+    const int i = blockIdx.x;
+    double2 acc[1] = {make_double2(0.0, 0.0)};
+    for (int b = threadIdx.x; b < nblk; b += NT) acc[0] = cadd(acc[0], partials[(size_t)i * nblk + b]);
+    block_sum<1>(acc, sums);
+    if (threadIdx.x == 0) hv[i] = sums[0];
+    if (!last_block(ticket, gridDim.x)) return;
+    if (threadIdx.x < 32) dcgs2_coef_warp(j, 1, hv, alpha2, H, ldh, coef);
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// One warp; lane l handles i = l and l + 32 (j <= 64).
+// DCGS2 coefficient step as its own launch (one warp); see dcgs2_coef.cuh.
 __global__ void k_dcgs2_coef(int j, int has_w, const double2 *__restrict__ hv, const double2 *__restrict__ alpha2,
                              double2 *__restrict__ H, int ldh, double2 *__restrict__ coef) {
     pdl_enter();
-    const int lane = threadIdx.x;
-    const double al = j > 0 ? alpha2[j].x : 1.0, ra = 1.0 / al;
-    double2 a[2], c[2];
-    double s2 = 0.0, tr = 0.0, ti = 0.0;
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int i = lane + 32 * k;
-        a[k] = i < j ? hv[i] : make_double2(0.0, 0.0);
-        c[k] = (has_w && i < j) ? hv[j + 1 + i] : make_double2(0.0, 0.0);
-        s2 += a[k].x * a[k].x + a[k].y * a[k].y;
-        // conj(a) c
-        tr += a[k].x * c[k].x + a[k].y * c[k].y;
-        ti += a[k].x * c[k].y - a[k].y * c[k].x;
-    }
-    s2 = warp_sum_d(s2);
-    tr = warp_sum_d(tr);
-    ti = warp_sum_d(ti);
-    double nu = 1.0;
-    if (j > 0) {
-        nu = sqrt(fmax((hv[j].x - s2) * (ra * ra), 1e-300));
-        double2 *col = H + (size_t)ldh * (j - 1);
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-            const int i = lane + 32 * k;
-            if (i < j) col[i] = cadd(col[i], a[k]);  // alpha a_i = hv[i]
-        }
-        if (lane == 0) col[j] = make_double2(al * nu, 0.0);
-    }
-    if (!has_w) return;
-    const double2 t = make_double2((hv[2 * j + 1].x - tr) * ra, (hv[2 * j + 1].y - ti) * ra);
-    const double rn = 1.0 / nu;
-    const double2 hjj = cscale(t, rn);
-    const double2 sf = cscale(hjj, rn);
-    double2 *col = H + (size_t)ldh * j;
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int i = lane + 32 * k;
-        if (i < j) {
-            col[i] = c[k];
-            coef[i] = a[k];
-            coef[j + i] = csub(c[k], cmul(cscale(a[k], ra), sf));
-        }
-    }
-    if (lane == 0) {
-        col[j] = hjj;
-        coef[2 * j] = make_double2(rn * ra, 0.0);
-        coef[2 * j + 1] = cscale(sf, ra);
-    }
+    dcgs2_coef_warp(j, has_w, hv, alpha2, H, ldh, coef);
 }
 
 __global__ void k_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y) {
@@ -412,6 +365,13 @@ template cudaError_t launch_combine<double2>(size_t, const double2 *, size_t, in
 cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm,
                           double *est, cudaStream_t s) {
     k_givens<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g, fnorm, est);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_dcgs2(const double2 *partials, int nblk, double2 *hv, unsigned *ticket, int j,
+                                const double2 *alpha2, double2 *H, int ldh, double2 *coef, cudaStream_t s) {
+    if (j < 0 || j > 63) return cudaErrorInvalidValue;
+    launch_pdl(k_reduce_dcgs2, 2 * (j + 1), NT, 0, s, partials, nblk, hv, ticket, j, alpha2, H, ldh, coef);
     return cudaGetLastError();
 }
 

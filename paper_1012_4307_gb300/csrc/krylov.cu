@@ -40,6 +40,7 @@ static void free_krylov(helm_handle *h) {
         if (e) cudaEventDestroy(e);
     h->close_ev.clear();
     h->hv = h->alpha2 = h->dcoef = nullptr;
+    h->tickets = nullptr;
     for (void *p : h->krylov_owned) cudaFree(p);
     h->krylov_owned.clear();
     h->V = nullptr; h->Z = nullptr; h->H = nullptr; h->g = h->sn = h->y = h->h2 = nullptr;
@@ -98,6 +99,7 @@ static helm_status ensure_ws(helm_handle *h, int m) {
     KA(&h->hv, (size_t)2 * m + 4);
     KA(&h->alpha2, (size_t)m + 2);
     KA(&h->dcoef, (size_t)2 * m + 4);
+    KA(&h->tickets, 4);
     KA(&h->scal, 32);
     KA(&h->est_dev, (size_t)m + 4);
     KA(&h->gs_flag, 4);
@@ -331,11 +333,13 @@ static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
 // u_j, the once-orthogonalised vector of step j - 1 (not normalised: alpha_j = ||x_j|| is in
 // alpha2[j], and the division by it is folded into the next consumers; slot 0 holds v_0).
 //   z_j = cycle(x_j / alpha_j); w = A z_j                        (slot j + 1)
-//   one pass: V_i^H x_j and V_i^H w for i <= j                    (k_mdot2_pair)
-//   coefficients: finish column j - 1 of H (reorthogonalisation of u_j), first-pass column j;
+//   one pass: V_i^H x_j and V_i^H w for i <= j (k_mdot2_pair); their reduction, whose last
+//   block forms the coefficients: finish column j - 1 of H (reorthogonalisation of u_j),
+//   first-pass column j;
 //   the Givens rotation of column j - 1 and its residual estimate est[j - 1] run on a side
 //   stream beside the update pass
-//   one pass: slot j <- v_j (final), slot j + 1 <- w orthogonalised once; alpha_{j+1} = ||w||
+//   one pass: slot j <- v_j (final), slot j + 1 <- w orthogonalised once; its last block forms
+//   alpha_{j+1} = ||w||
 // Only column j - 1 of H, the first-pass column j, rotation j - 1, g[j-1..j], slots j and j + 1
 // and z_j are written, so a step queued ahead of the host's decision never disturbs columns
 // 0 .. j - 2 that a solution update may use.
@@ -354,9 +358,10 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
         CKE(launch_mdot2_pair(np, V4, np, j + 1, u, w, h->partials, s));
     }
     {
+        // reduction and, in its last block, the coefficient step
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
-        CKE(launch_reduce(h->partials, gs_df_nblocks(np), 2 * (j + 1), h->hv, 0, nullptr, s));
-        CKE(launch_dcgs2_coef(j, 1, h->hv, h->alpha2, h->H, ldh, h->dcoef, s));
+        CKE(launch_reduce_dcgs2(h->partials, gs_df_nblocks(np), h->hv, h->tickets, j, h->alpha2, h->H, ldh, h->dcoef,
+                                s));
     }
     const bool fork = j > 0 && !h->prof.on;
     if (j > 0) {
@@ -371,12 +376,9 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
         if (fork) CKE(cudaEventRecord(h->ev_join, h->side));
     }
     {
+        // the update and the norm of the new vector in one launch
         ProfScope ps(h, HELM_K_UPDATE_NORM, np * 16.0 * (nv + 3), 0);
-        CKE(launch_update2_pair(np, V4, np, j, h->dcoef, h->partials, s));
-    }
-    {
-        ProfScope ps(h, HELM_K_SMALL, 0, 0);
-        CKE(launch_reduce(h->partials, gs_df_update_nblocks(np), 1, h->alpha2 + j + 1, 2, nullptr, s));
+        CKE(launch_update2_pair(np, V4, np, j, h->dcoef, h->partials, h->tickets + 1, h->alpha2 + j + 1, s));
     }
     if (fork) CKE(cudaStreamWaitEvent(s, h->ev_join, 0));
     if (j > 0) CKE(cudaMemcpyAsync(h->est_host + j - 1, h->est_dev + j - 1, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -21,7 +21,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 //   column j: c_i = hv[j+1+i] (i < j), H[j][j] = v_j^H w = (hv[2j+1] / alpha - a^H c) / nu;
 //   with s = H[j][j] / nu, the update pass forms v_j = (x - sum V_i (alpha a_i)) / (alpha nu)
 //   and w' = w - x (s / alpha) - sum V_i (c_i - a_i s): coef[i] = alpha a_i,
-//   coef[j+i] = c_i - a_i s, coef[2j] = 1 / (alpha nu), coef[2j+1] = s / alpha.
+//   coef[j+i] = c_i - a_i s, coef[2j] = (1 / (alpha nu), small), coef[2j+1] = s / alpha,
+//   where small = 1 when ||alpha a|| <= 2^-18 alpha nu, else 0.
 // One warp (lane = threadIdx.x & 31); lane l handles i = l and l + 32 (j <= 64).
 __device__ __forceinline__ void dcgs2_coef_warp(int j, int has_w, const double2 *hv, const double2 *alpha2,
                                                 double2 *H, int ldh, double2 *coef) {
@@ -70,7 +71,10 @@ __device__ __forceinline__ void dcgs2_coef_warp(int j, int has_w, const double2 
     }
     if (lane == 0) {
         col[j] = hjj;
-        coef[2 * j] = make_double2(rn * ra, 0.0);
+        // small correction (||alpha a|| <= 2^-18 alpha nu): the update may form sum V_i (alpha a_i)
+        // in FP32
+        const double xn = al * nu;
+        coef[2 * j] = make_double2(rn * ra, s2 <= 0x1p-36 * xn * xn ? 1.0 : 0.0);
         coef[2 * j + 1] = cscale(sf, ra);
     }
 }

@@ -216,7 +216,11 @@ __global__ void __launch_bounds__(NT, 4) k_mdot2_pair(size_t n, const float4 *__
                                                    double2 *__restrict__ partials) {
     pdl_enter();
     __shared__ double sums[4 * CH];
-    const int i0 = blockIdx.y * CH;
+    // block (b, y) = blockIdx.x = b * ngroups + y: the blocks that read the same stretch of x and
+    // w run side by side, so that all but the first of them find it in L2
+    const int ngroups = (nv + CH - 1) / CH;
+    const int yb = blockIdx.x % ngroups, xb = blockIdx.x / ngroups, G = gridDim.x / ngroups;
+    const int i0 = yb * CH;
     const int cnt = min(CH, nv - i0);
     float s[CH][4];   // V^H x: [basis][re.s, re.c, im.s, im.c]
     float f[CH][2];   // V^H w in FP32: [basis][re, im]
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(NT, 4) k_mdot2_pair(size_t n, const float4 *__
         for (int k = 0; k < 4; k++) s[t][k] = 0.f;
         f[t][0] = f[t][1] = 0.f;
     }
-    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+    for (size_t q = xb * (size_t)NT + threadIdx.x; q < n; q += (size_t)G * NT) {
         const float4 xq = x[q], wq = w[q];
         float4 vq[CH];
 #pragma unroll
@@ -257,10 +261,9 @@ __global__ void __launch_bounds__(NT, 4) k_mdot2_pair(size_t n, const float4 *__
     }
     block_sum_ff<4 * CH>(vals, sums);
     __syncthreads();
-    const int G = gridDim.x;
     if ((int)threadIdx.x < 2 * cnt) {
         const int r = threadIdx.x / cnt, t = threadIdx.x % cnt;
-        partials[((size_t)r * nv + i0 + t) * G + blockIdx.x] =
+        partials[((size_t)r * nv + i0 + t) * G + xb] =
             make_double2(sums[(r * CH + t) * 2], sums[(r * CH + t) * 2 + 1]);
     }
 }
@@ -273,30 +276,16 @@ __global__ void __launch_bounds__(NT, 4) k_mdot2_pair(size_t n, const float4 *__
 // partials[b] = (||w||^2, 0).
 // With a ticket, the last block to finish also reduces the norm partials into
 // *alpha_out = (||w||, 0).
-__global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
-                                                     const double2 *__restrict__ coef, double2 *__restrict__ partials,
-                                                     unsigned *ticket, double2 *alpha_out) {
-    pdl_enter();
-    __shared__ float4 cA[64], cC[64];
-    __shared__ float4 sc[2];  // (r hi, lo, 0, 0), s
-    __shared__ double sums[1];
-    for (int i = threadIdx.x; i < j; i += NT) {
-        const ff a = ff_split(coef[i].x), b = ff_split(coef[i].y);
-        cA[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
-        const ff c = ff_split(coef[j + i].x), d = ff_split(coef[j + i].y);
-        cC[i] = make_float4(c.hi, c.lo, d.hi, d.lo);
-    }
-    if (threadIdx.x == 0) {
-        const ff r = ff_split(coef[2 * j].x);
-        sc[0] = make_float4(r.hi, r.lo, 0.f, 0.f);
-        const ff a = ff_split(coef[2 * j + 1].x), b = ff_split(coef[2 * j + 1].y);
-        sc[1] = make_float4(a.hi, a.lo, b.hi, b.lo);
-    }
-    __syncthreads();
+// coef[2j].y != 0 marks a small correction, ||A|| <= 2^-18 ||x - sum V_i A_i|| (decided by the
+// coefficient step): sum V_i A_i is then formed in FP32 from the high parts and subtracted from
+// x in double-FP32; its rounding error, about 2^-24 ||A||, stays below 2^-42 of the result.
+// Otherwise both sums are double-FP32.
+template <bool SMALL_A>
+__device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, size_t ldv, int j,
+                                              const float4 *cA, const float4 *cC, ff rinv, ff sr, ff si,
+                                              float &sn, float &cn) {
     float4 *x = V + (size_t)j * ldv, *w = V + (size_t)(j + 1) * ldv;
-    const ff rinv = ff_re(sc[0]), sr = ff_re(sc[1]), si = ff_im(sc[1]);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float sn = 0.f, cn = 0.f;
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const float4 xq = x[q], wq = w[q];
         const ff xr = ff_re(xq), xi = ff_im(xq);
@@ -305,6 +294,7 @@ __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restric
         // next four while the current four are processed
         float vs[2][4] = {{xq.x, xq.y, xq.z, xq.w}, {0.f, 0.f, 0.f, 0.f}};
         float ws[2][4] = {{wq.x, wq.y, wq.z, wq.w}, {0.f, 0.f, 0.f, 0.f}};
+        float fa[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // small correction: FP32 (re, im) per chain
         float p, e;
         // w -= x s: re -= xr sr - xi si ; im -= xr si + xi sr
         ff_two_prod(xr, sr, p, e); ff_acc_prod(ws[1][0], ws[1][1], -p, -e);
@@ -324,12 +314,19 @@ __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restric
                     float *va = vs[u & 1], *wa = ws[u & 1];
                     const ff vr = ff_re(cur[u]), vi = ff_im(cur[u]);
                     const float4 a4 = cA[i0 + u], c4 = cC[i0 + u];
-                    const ff ar = ff_re(a4), ai = ff_im(a4), cr = ff_re(c4), ci = ff_im(c4);
+                    const ff cr = ff_re(c4), ci = ff_im(c4);
                     // v -= V_i a ; w -= V_i c   (complex products)
-                    ff_two_prod(vr, ar, p, e); ff_acc_prod(va[0], va[1], -p, -e);
-                    ff_two_prod(vi, ai, p, e); ff_acc_prod(va[0], va[1], p, e);
-                    ff_two_prod(vr, ai, p, e); ff_acc_prod(va[2], va[3], -p, -e);
-                    ff_two_prod(vi, ar, p, e); ff_acc_prod(va[2], va[3], -p, -e);
+                    if (SMALL_A) {
+                        float *f = fa[u & 1];
+                        f[0] = __fmaf_rn(cur[u].x, a4.x, __fmaf_rn(-cur[u].z, a4.z, f[0]));
+                        f[1] = __fmaf_rn(cur[u].x, a4.z, __fmaf_rn(cur[u].z, a4.x, f[1]));
+                    } else {
+                        const ff ar = ff_re(a4), ai = ff_im(a4);
+                        ff_two_prod(vr, ar, p, e); ff_acc_prod(va[0], va[1], -p, -e);
+                        ff_two_prod(vi, ai, p, e); ff_acc_prod(va[0], va[1], p, e);
+                        ff_two_prod(vr, ai, p, e); ff_acc_prod(va[2], va[3], -p, -e);
+                        ff_two_prod(vi, ar, p, e); ff_acc_prod(va[2], va[3], -p, -e);
+                    }
                     ff_two_prod(vr, cr, p, e); ff_acc_prod(wa[0], wa[1], -p, -e);
                     ff_two_prod(vi, ci, p, e); ff_acc_prod(wa[0], wa[1], p, e);
                     ff_two_prod(vr, ci, p, e); ff_acc_prod(wa[2], wa[3], -p, -e);
@@ -340,8 +337,14 @@ __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restric
             for (int u = 0; u < 4; u++) cur[u] = nxt[u];
         }
         // v_j = v r
-        const ff vr = ff_add(ff_norm(vs[0][0], vs[0][1]), ff_norm(vs[1][0], vs[1][1]));
-        const ff vi = ff_add(ff_norm(vs[0][2], vs[0][3]), ff_norm(vs[1][2], vs[1][3]));
+        ff vr, vi;
+        if (SMALL_A) {
+            vr = ff_add(xr, ff{-(fa[0][0] + fa[1][0]), 0.f});
+            vi = ff_add(xi, ff{-(fa[0][1] + fa[1][1]), 0.f});
+        } else {
+            vr = ff_add(ff_norm(vs[0][0], vs[0][1]), ff_norm(vs[1][0], vs[1][1]));
+            vi = ff_add(ff_norm(vs[0][2], vs[0][3]), ff_norm(vs[1][2], vs[1][3]));
+        }
         ff_two_prod(vr, rinv, p, e);
         const ff or_ = ff_norm(p, e);
         ff_two_prod(vi, rinv, p, e);
@@ -355,6 +358,35 @@ __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restric
         ff_two_prod(wi, wi, p, e);
         ff_acc_prod(sn, cn, p, e);
     }
+}
+
+__global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
+                                                     const double2 *__restrict__ coef, double2 *__restrict__ partials,
+                                                     unsigned *ticket, double2 *alpha_out) {
+    pdl_enter();
+    __shared__ float4 cA[64], cC[64];
+    __shared__ float4 sc[2];  // (r hi, lo, small-correction flag, 0), s
+    __shared__ double sums[1];
+    for (int i = threadIdx.x; i < j; i += NT) {
+        const ff a = ff_split(coef[i].x), b = ff_split(coef[i].y);
+        cA[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        const ff c = ff_split(coef[j + i].x), d = ff_split(coef[j + i].y);
+        cC[i] = make_float4(c.hi, c.lo, d.hi, d.lo);
+    }
+    if (threadIdx.x == 0) {
+        const double2 rc = coef[2 * j];
+        const ff r = ff_split(rc.x);
+        sc[0] = make_float4(r.hi, r.lo, rc.y != 0.0 ? 1.f : 0.f, 0.f);
+        const ff a = ff_split(coef[2 * j + 1].x), b = ff_split(coef[2 * j + 1].y);
+        sc[1] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+    __syncthreads();
+    const ff rinv = ff_re(sc[0]), sr = ff_re(sc[1]), si = ff_im(sc[1]);
+    float sn = 0.f, cn = 0.f;
+    if (sc[0].z != 0.f)
+        update2_nodes<true>(n, V, ldv, j, cA, cC, rinv, sr, si, sn, cn);
+    else
+        update2_nodes<false>(n, V, ldv, j, cA, cC, rinv, sr, si, sn, cn);
     ff vals[1] = {ff_norm(sn, cn)};
     block_sum_ff<1>(vals, sums);
     if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(sums[0], 0.0);
@@ -475,8 +507,8 @@ constexpr int DF_CH2 = 4;  // basis vectors per block row of the two-vector dot 
 cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *x, const float4 *w,
                               double2 *partials, cudaStream_t s) {
     if (nv < 1 || nv > 64) return cudaErrorInvalidValue;
-    dim3 g(gs_df_nblocks(n), (nv + DF_CH2 - 1) / DF_CH2);
-    launch_pdl(k_mdot2_pair<DF_CH2>, g, NT, 0, s, n, V, ldv, nv, x, w, partials);
+    const unsigned g = (unsigned)gs_df_nblocks(n) * (unsigned)((nv + DF_CH2 - 1) / DF_CH2);
+    launch_pdl(k_mdot2_pair<DF_CH2>, dim3(g), NT, 0, s, n, V, ldv, nv, x, w, partials);
     return cudaGetLastError();
 }
 

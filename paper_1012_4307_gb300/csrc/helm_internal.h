@@ -224,13 +224,14 @@ cudaError_t launch_reduce(const double2 *partials, int nblk, int nv, double2 *ou
 // of such a vector is the float4 (re.hi, re.lo, im.hi, im.lo).  Dot-pass partials use
 // G = gs_df_nblocks(n) blocks per vector, update-pass partials gs_df_update_nblocks(n).
 int gs_df_nblocks(size_t n);         // dot pass
+int gs_df_dot2_nblocks(size_t n, int nv);  // two-vector dot pass over nv basis vectors
 int gs_df_update_nblocks(size_t n);  // update pass
 cudaError_t launch_mdot_norm_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *w, double2 *partials,
                                   const int *gate, cudaStream_t s);
 cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int nv, const double2 *h, float4 *w,
                                     double2 *partials, const int *gate, cudaStream_t s);
 // Delayed CGS2 (one dot and one update pass per Arnoldi step, float pairs):
-//   dot:    partials[i*G+b] = V_i^H x, partials[(nv+i)*G+b] = V_i^H w  (i < nv, G = gs_df_nblocks)
+//   dot:    partials[i*G+b] = V_i^H x, partials[(nv+i)*G+b] = V_i^H w  (i < nv, G = gs_df_dot2_nblocks)
 //   coef:   one-thread FP64 step of the method (kernels_krylov.cu)
 //   update: slot j <- final v_j, slot j+1 <- once-orthogonalised w; partials[b] = ||w||^2
 //           (G = gs_df_update_nblocks)

@@ -32,16 +32,47 @@ __device__ __forceinline__ ff shfl_down_ff(ff v, int off) {
 
 // Block sums of NV double-float values per thread (fixed tree); thread t < NV gets sum t as
 // an FP64 number in out[t].
+// For NV a power of two (2 .. 32) the warp stage is a transposing butterfly: at offsets 16, 8,
+// ... a lane keeps half of its values, sends the other half to the lane at that offset and adds
+// what it receives, so the values per lane halve at every level (NV - 1 + the plain levels
+// additions per lane instead of 5 NV); after log2(NV) levels lane l holds a partial sum of value
+// idx(l), and the remaining levels sum equal indices.  Otherwise one shuffle tree per value.
 template <int NV>
 __device__ __forceinline__ void block_sum_ff(ff (&v)[NV], double *out) {
     __shared__ ff red[NT / 32][NV];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (NV >= 2 && NV <= 32 && (NV & (NV - 1)) == 0) {
+        int idx = 0;
 #pragma unroll
-    for (int i = 0; i < NV; i++) {
-        ff x = v[i];
+        for (int o = 16, m = NV; o > 0; o >>= 1) {
+            if (m > 1) {
+                const bool upper = (lane & o) != 0;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x = ff_add(x, shfl_down_ff(x, off));
-        if (lane == 0) red[warp][i] = x;
+                for (int i = 0; i < m / 2; i++) {
+                    const ff keep = upper ? v[i + m / 2] : v[i];
+                    ff send = upper ? v[i] : v[i + m / 2];
+                    send.hi = __shfl_xor_sync(0xffffffffu, send.hi, o);
+                    send.lo = __shfl_xor_sync(0xffffffffu, send.lo, o);
+                    v[i] = ff_add(keep, send);
+                }
+                if (upper) idx += m / 2;
+                m /= 2;
+            } else {
+                ff r = v[0];
+                r.hi = __shfl_xor_sync(0xffffffffu, r.hi, o);
+                r.lo = __shfl_xor_sync(0xffffffffu, r.lo, o);
+                v[0] = ff_add(v[0], r);
+            }
+        }
+        if ((lane & (32 / NV - 1)) == 0) red[warp][idx] = v[0];
+    } else {
+#pragma unroll
+        for (int i = 0; i < NV; i++) {
+            ff x = v[i];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) x = ff_add(x, shfl_down_ff(x, off));
+            if (lane == 0) red[warp][i] = x;
+        }
     }
     __syncthreads();
     if (threadIdx.x < NV) {
@@ -504,10 +535,27 @@ cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int n
 
 constexpr int DF_CH2 = 4;  // basis vectors per block row of the two-vector dot pass
 
+// The two-vector dot pass runs one wave: G blocks per block row of DF_CH2 basis vectors, with
+// G x (block rows) at most the blocks that are resident at once (152 SMs x the blocks that fit
+// on an SM), so that each block sums a long stretch of nodes and its block reduction is rare.
+int gs_df_dot2_nblocks(size_t n, int nv) {
+    static int slots = 0;
+    if (slots == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mdot2_pair<DF_CH2>, NT, 0) != cudaSuccess || b < 1) {
+            cudaGetLastError();
+            b = 2;
+        }
+        slots = 152 * b;
+    }
+    const int groups = std::max(1, (nv + DF_CH2 - 1) / DF_CH2);
+    return std::max(1, std::min(gs_df_nblocks(n), slots / groups));
+}
+
 cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *x, const float4 *w,
                               double2 *partials, cudaStream_t s) {
     if (nv < 1 || nv > 64) return cudaErrorInvalidValue;
-    const unsigned g = (unsigned)gs_df_nblocks(n) * (unsigned)((nv + DF_CH2 - 1) / DF_CH2);
+    const unsigned g = (unsigned)gs_df_dot2_nblocks(n, nv) * (unsigned)((nv + DF_CH2 - 1) / DF_CH2);
     launch_pdl(k_mdot2_pair<DF_CH2>, dim3(g), NT, 0, s, n, V, ldv, nv, x, w, partials);
     return cudaGetLastError();
 }

@@ -360,7 +360,7 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
     {
         // reduction and, in its last block, the coefficient step
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
-        CKE(launch_reduce_dcgs2(h->partials, gs_df_nblocks(np), h->hv, h->tickets, j, h->alpha2, h->H, ldh, h->dcoef,
+        CKE(launch_reduce_dcgs2(h->partials, gs_df_dot2_nblocks(np, j + 1), h->hv, h->tickets, j, h->alpha2, h->H, ldh, h->dcoef,
                                 s));
     }
     const bool fork = j > 0 && !h->prof.on;

@@ -4,12 +4,17 @@
 // fill the GPU, so as separate launches each costs a launch latency plus a few dependent
 // phases, and on one thread block they are bound by one SM's issue rate.  Here a cluster of
 // NC thread blocks (8 or 16 SMs) keeps every level's b, u, t, k^2 and coefficients in its
-// distributed shared memory: each block owns a slab of interior rows of every level, reads
-// the neighbouring slabs' boundary rows, and writes the coarsest solve's results, through
-// distributed shared memory (cooperative_groups::cluster_group::map_shared_rank), and the
-// phases of the cycle are separated by cluster barriers.  Same arithmetic as the per-level
-// kernels in kernels_mg.cu: omega-Jacobi (ping-pong) or omega-red-black sweeps, residual and
-// full weighting, bilinear prolongation, exact coarsest solve by the dense inverse.
+// distributed shared memory.  Block r owns the interior rows B_l[r] .. B_l[r+1]-1 of level l,
+// the slabs nested across levels (B_{l+1}[r] = (B_l[r] + 1) / 2), so that the full weighting of
+// an owned coarse row and the prolongation onto an owned fine row only touch rows that the
+// block owns or the two rows next to its slab.  Each block keeps those two rows as halo rows
+// of u and t; whoever writes the first or last row of its slab also stores the value into the
+// neighbouring slab's halo (a store to distributed shared memory, which does not wait), and the
+// cluster barrier between phases publishes it.  Every read inside a phase is then a local
+// shared-memory read; a dependent read of another block's shared memory costs about as much as
+// a whole cluster barrier.  Same arithmetic as the per-level kernels in kernels_mg.cu:
+// omega-Jacobi (ping-pong) or omega-red-black sweeps, residual and full weighting, bilinear
+// prolongation, exact coarsest solve by the dense inverse.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -21,12 +26,14 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int CT_THREADS = 512;
+constexpr int CT_MAXC = 16;  // blocks per cluster at most
 
 struct CLevel {
     const float2 *cx, *cy;  // global coefficient triples (3 nx, 3 ny)
     const float *k2;        // global k^2 (nx ny)
     float2 bk, c;
-    int nx, ny, rows;       // rows: interior rows per block (the last block may own fewer)
+    int nx, ny;
+    int B[CT_MAXC + 1];     // block r owns interior rows B[r] .. B[r+1]-1 (possibly none)
     unsigned ob, ou, ot, ok, ocx, ocy;  // byte offsets in shared memory (same in every block)
 };
 
@@ -38,7 +45,7 @@ struct CArgs {
     const float2 *minv;  // nu_c x nu_c, row-major (global)
     const float2 *b_top;  // top level's right-hand side (global)
     float2 *u_top;        // top level's result; initial guess when !zero (global)
-    unsigned obc, ozero;  // compact coarsest right-hand side; a row of zeros
+    unsigned obc;         // compact coarsest right-hand side
 };
 
 struct Ctx {
@@ -46,45 +53,64 @@ struct Ctx {
     int rank, nc;
 };
 
-__device__ __forceinline__ int own_j0(const CLevel &L, int rank) { return 1 + rank * L.rows; }
-__device__ __forceinline__ int own_j1(const CLevel &L, int rank) { return min(1 + (rank + 1) * L.rows, L.ny - 1); }
-
-// Row j (0 .. ny-1) of the level array at offset off: in this block's or the owning block's
-// shared memory; the boundary rows read as zeros.
-__device__ __forceinline__ float2 *row(const Ctx &X, const CArgs &A, const CLevel &L, unsigned off, int j) {
-    if (j <= 0 || j >= L.ny - 1) return (float2 *)(X.sm + A.ozero);
-    const int owner = (j - 1) / L.rows, li = (j - 1) - owner * L.rows;
-    float2 *p = (float2 *)(X.sm + off) + (size_t)li * L.nx;
-    if (owner == X.rank) return p;
-    return cg::this_cluster().map_shared_rank(p, (unsigned)owner);
+// Row j of the level array at offset off in block c's slot layout: slot j - B[c] + 1, so slot
+// 0 and slot rows + 1 are the halo rows (a boundary row's halo is never written: zeros).
+__device__ __forceinline__ float2 *slot_row(unsigned char *sm, const CLevel &L, unsigned off, int j, int c) {
+    return (float2 *)(sm + off) + (size_t)(j - L.B[c] + 1) * L.nx;
 }
+// this block's row j, for B[rank] - 1 <= j <= B[rank + 1]
 __device__ __forceinline__ float2 *lrow(const Ctx &X, const CLevel &L, unsigned off, int j) {
-    return (float2 *)(X.sm + off) + (size_t)(j - own_j0(L, X.rank)) * L.nx;
+    return slot_row(X.sm, L, off, j, X.rank);
+}
+// block c's row j (another block's through distributed shared memory)
+__device__ __forceinline__ float2 *crow(const Ctx &X, const CLevel &L, unsigned off, int j, int c) {
+    float2 *p = slot_row(X.sm, L, off, j, c);
+    return c == X.rank ? p : cg::this_cluster().map_shared_rank(p, (unsigned)c);
+}
+__device__ __forceinline__ int owner_of(const CLevel &L, int nc, int j) {
+    int c = 0;
+    while (c + 1 < nc && L.B[c + 1] <= j) c++;
+    return c;
+}
+
+// u(j, i) = v for row j owned by block `owner`, and the same value into every other block whose
+// window of rows (B[c] - 1 .. B[c+1]) holds row j: the blocks just above the owner's slab whose
+// slabs end at row j (empty ones, then the nearest non-empty one) when j is the owner's first
+// row, and likewise below when j is its last row.
+__device__ __forceinline__ void put(const Ctx &X, const CLevel &L, unsigned off, int j, int i, float2 v, int owner) {
+    crow(X, L, off, j, owner)[i] = v;
+    if (j == L.B[owner])
+        for (int p = owner - 1; p >= 0 && L.B[p + 1] == j; p--) crow(X, L, off, j, p)[i] = v;
+    if (j == L.B[owner + 1] - 1)
+        for (int q = owner + 1; q < X.nc && L.B[q] == j + 1; q++) crow(X, L, off, j, q)[i] = v;
 }
 
 __device__ __forceinline__ void csync() { cg::this_cluster().sync(); }
 
-// f(j, i) for every owned interior node: warps over owned rows, lanes over i.
+// f(j, i) for every owned interior node, one node per thread and pass (consecutive threads
+// along a row).
 template <typename F>
 __device__ __forceinline__ void for_owned(const Ctx &X, const CLevel &L, F f) {
-    const int j0 = own_j0(L, X.rank), j1 = own_j1(L, X.rank);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = j0 + warp; j < j1; j += nw)
-        for (int i = 1 + lane; i <= L.nx - 2; i += 32) f(j, i);
+    const int j0 = L.B[X.rank], m = L.nx - 2, total = (L.B[X.rank + 1] - j0) * m;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int r = q / m;
+        f(j0 + r, 1 + q - r * m);
+    }
 }
 
 __device__ __forceinline__ float2 diag_at(const Ctx &X, const CLevel &L, int j, int i) {
     const float2 *cx = (const float2 *)(X.sm + L.ocx), *cy = (const float2 *)(X.sm + L.ocy);
-    const int li = j - own_j0(L, X.rank);
+    const int li = j - L.B[X.rank];
     const float k2 = ((const float *)(X.sm + L.ok))[(size_t)li * L.nx + i];
     return cadd(cadd(cx[3 * i + 1], cy[3 * li + 1]), cadd(cscale(L.bk, k2), L.c));
 }
 
-// (M u)(j, i) with u's rows j-1, j, j+1 given; d = the diagonal.
-__device__ __forceinline__ float2 apply_at(const Ctx &X, const CLevel &L, int j, int i, const float2 *un,
-                                           const float2 *uc, const float2 *us, float2 &d) {
+// (M u)(j, i) from this block's rows of the array at offset u (j - 1 and j + 1 may be halo
+// rows); d = the diagonal.
+__device__ __forceinline__ float2 apply_at(const Ctx &X, const CLevel &L, unsigned u, int j, int i, float2 &d) {
     const float2 *cx = (const float2 *)(X.sm + L.ocx), *cy = (const float2 *)(X.sm + L.ocy);
-    const int li = j - own_j0(L, X.rank);
+    const int li = j - L.B[X.rank];
+    const float2 *un = lrow(X, L, u, j - 1), *uc = lrow(X, L, u, j), *us = lrow(X, L, u, j + 1);
     d = diag_at(X, L, j, i);
     float2 acc = cmul(cx[3 * i], uc[i - 1]);
     acc = cfma(cx[3 * i + 2], uc[i + 1], acc);
@@ -94,7 +120,7 @@ __device__ __forceinline__ float2 apply_at(const Ctx &X, const CLevel &L, int j,
 }
 
 __device__ void zero_level(const Ctx &X, const CLevel &L, unsigned off) {
-    for_owned(X, L, [&](int j, int i) { lrow(X, L, off, j)[i] = make_float2(0.f, 0.f); });
+    for_owned(X, L, [&](int j, int i) { put(X, L, off, j, i, make_float2(0.f, 0.f), X.rank); });
 }
 
 // nu sweeps on level L; *cur holds the iterate (offset), *oth the partner; zero: u = 0 on entry.
@@ -107,44 +133,32 @@ __device__ void ct_smooth(const Ctx &X, const CArgs &A, const CLevel &L, int nu,
     for (int s = 0; s < nu; s++) {
         if (A.rb) {
             for (int colour = 0; colour < 2; colour++) {
+                // in place: this colour's neighbours (the other colour) are not written here
                 const unsigned u = *cur;
-                // the rows of this colour's neighbours are not written in this phase
-                const int j0 = own_j0(L, X.rank), j1 = own_j1(L, X.rank);
-                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-                for (int j = j0 + warp; j < j1; j += nw) {
-                    const float2 *un = row(X, A, L, u, j - 1), *us = row(X, A, L, u, j + 1);
-                    float2 *uc = lrow(X, L, u, j);
-                    const float2 *b = lrow(X, L, L.ob, j);
-                    for (int i = 1 + lane; i <= L.nx - 2; i += 32) {
-                        if (((i + j) & 1) != colour) continue;
-                        float2 d;
-                        const float2 mu = apply_at(X, L, j, i, un, uc, us, d);
-                        uc[i] = cadd(uc[i], cscale(cmul(csub(b[i], mu), cinv(d)), A.omega));
-                    }
-                }
+                for_owned(X, L, [&](int j, int i) {
+                    if (((i + j) & 1) != colour) return;
+                    float2 d;
+                    const float2 mu = apply_at(X, L, u, j, i, d);
+                    const float2 uc = lrow(X, L, u, j)[i], b = lrow(X, L, L.ob, j)[i];
+                    put(X, L, u, j, i, cadd(uc, cscale(cmul(csub(b, mu), cinv(d)), A.omega)), X.rank);
+                });
                 csync();
             }
         } else {
             const bool z0 = zero && s == 0;
             const unsigned src = *cur, dst = *oth;
-            const int j0 = own_j0(L, X.rank), j1 = own_j1(L, X.rank);
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-            for (int j = j0 + warp; j < j1; j += nw) {
-                const float2 *un = z0 ? nullptr : row(X, A, L, src, j - 1);
-                const float2 *us = z0 ? nullptr : row(X, A, L, src, j + 1);
-                const float2 *uc = lrow(X, L, src, j);
-                const float2 *b = lrow(X, L, L.ob, j);
-                float2 *out = lrow(X, L, dst, j);
-                for (int i = 1 + lane; i <= L.nx - 2; i += 32) {
-                    if (z0) {
-                        out[i] = cscale(cmul(b[i], cinv(diag_at(X, L, j, i))), A.omega);
-                    } else {
-                        float2 d;
-                        const float2 mu = apply_at(X, L, j, i, un, uc, us, d);
-                        out[i] = cadd(uc[i], cscale(cmul(csub(b[i], mu), cinv(d)), A.omega));
-                    }
+            for_owned(X, L, [&](int j, int i) {
+                const float2 b = lrow(X, L, L.ob, j)[i];
+                float2 v;
+                if (z0) {
+                    v = cscale(cmul(b, cinv(diag_at(X, L, j, i))), A.omega);
+                } else {
+                    float2 d;
+                    const float2 mu = apply_at(X, L, src, j, i, d);
+                    v = cadd(lrow(X, L, src, j)[i], cscale(cmul(csub(b, mu), cinv(d)), A.omega));
                 }
-            }
+                put(X, L, dst, j, i, v, X.rank);
+            });
             csync();
             *cur = dst;
             *oth = src;
@@ -153,13 +167,14 @@ __device__ void ct_smooth(const Ctx &X, const CArgs &A, const CLevel &L, int nu,
 }
 
 // Exact coarsest solve: every block gathers the whole right-hand side, computes its share of
-// the rows of Minv b (one warp per row) and stores each result in the owning block's u.
+// the rows of Minv b (one warp per row) and stores each result in the owning block's u (and
+// the halos that hold its row).
 __device__ void ct_dense(const Ctx &X, const CArgs &A, const CLevel &L) {
     float2 *bc = (float2 *)(X.sm + A.obc);
     const int mx = L.nx - 2, nu = A.nu_c;
     for (int c = threadIdx.x; c < nu; c += blockDim.x) {
         const int i = 1 + c % mx, j = 1 + c / mx;
-        bc[c] = row(X, A, L, L.ob, j)[i];
+        bc[c] = crow(X, L, L.ob, j, owner_of(L, X.nc, j))[i];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -172,7 +187,10 @@ __device__ void ct_dense(const Ctx &X, const CArgs &A, const CLevel &L) {
             acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
             acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
         }
-        if (lane == 0) row(X, A, L, L.ou, 1 + r / mx)[1 + r % mx] = acc;
+        if (lane == 0) {
+            const int j = 1 + r / mx;
+            put(X, L, L.ou, j, 1 + r % mx, acc, owner_of(L, X.nc, j));
+        }
     }
     csync();
 }
@@ -189,24 +207,20 @@ __device__ void ct_cycle(const Ctx &X, const CArgs &A, bool zero, int gf, int gc
         unsigned cur = L.ou, oth = L.ot;
         ct_smooth(X, A, L, A.nu1, &cur, &oth, zero);
         const CLevel &Lc = A.lv[LVL + 1];
-        // residual into the free partner array, then full weighting into the coarse b
+        // residual into the free partner array, then full weighting into the coarse b (the fine
+        // rows 2J-1 .. 2J+1 of an owned coarse row J are owned or halo rows: nested slabs)
         {
-            const int j0 = own_j0(L, X.rank), j1 = own_j1(L, X.rank);
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-            for (int j = j0 + warp; j < j1; j += nw) {
-                const float2 *un = row(X, A, L, cur, j - 1), *us = row(X, A, L, cur, j + 1);
-                const float2 *uc = lrow(X, L, cur, j), *b = lrow(X, L, L.ob, j);
-                float2 *r = lrow(X, L, oth, j);
-                for (int i = 1 + lane; i <= L.nx - 2; i += 32) {
-                    float2 d;
-                    r[i] = csub(b[i], apply_at(X, L, j, i, un, uc, us, d));
-                }
-            }
+            const unsigned u = cur, r = oth;
+            for_owned(X, L, [&](int j, int i) {
+                float2 d;
+                const float2 mu = apply_at(X, L, u, j, i, d);
+                put(X, L, r, j, i, csub(lrow(X, L, L.ob, j)[i], mu), X.rank);
+            });
         }
         csync();
         for_owned(X, Lc, [&](int J, int I) {
-            const float2 *r0 = row(X, A, L, oth, 2 * J - 1), *r1 = row(X, A, L, oth, 2 * J),
-                         *r2 = row(X, A, L, oth, 2 * J + 1);
+            const float2 *r0 = lrow(X, L, oth, 2 * J - 1), *r1 = lrow(X, L, oth, 2 * J),
+                         *r2 = lrow(X, L, oth, 2 * J + 1);
             const int x = 2 * I;
             const float2 a0 = cadd(cadd(r0[x - 1], r0[x + 1]), cscale(r0[x], 2.f));
             const float2 a1 = cadd(cadd(r1[x - 1], r1[x + 1]), cscale(r1[x], 2.f));
@@ -222,19 +236,22 @@ __device__ void ct_cycle(const Ctx &X, const CArgs &A, bool zero, int gf, int gc
                 else ct_cycle<LVL + 1>(X, A, false, gc, gf);
             }
         }
-        // bilinear prolongation of the coarse result, added to the iterate
-        for_owned(X, L, [&](int j, int i) {
-            const float2 *ea = row(X, A, Lc, Lc.ou, j >> 1), *eb = row(X, A, Lc, Lc.ou, (j + 1) >> 1);
-            const int ia = i >> 1, ib = (i + 1) >> 1;
-            const float2 e = cadd(cadd(ea[ia], ea[ib]), cadd(eb[ia], eb[ib]));
-            float2 *uc = lrow(X, L, cur, j);
-            uc[i] = cadd(uc[i], cscale(e, 0.25f));
-        });
+        // bilinear prolongation of the coarse result (coarse rows j/2 and (j+1)/2: owned or halo
+        // rows of the coarse slab), added to the iterate
+        {
+            const unsigned u = cur;
+            for_owned(X, L, [&](int j, int i) {
+                const float2 *ea = lrow(X, Lc, Lc.ou, j >> 1), *eb = lrow(X, Lc, Lc.ou, (j + 1) >> 1);
+                const int ia = i >> 1, ib = (i + 1) >> 1;
+                const float2 e = cadd(cadd(ea[ia], ea[ib]), cadd(eb[ia], eb[ib]));
+                put(X, L, u, j, i, cadd(lrow(X, L, u, j)[i], cscale(e, 0.25f)), X.rank);
+            });
+        }
         csync();
         ct_smooth(X, A, L, A.nu2, &cur, &oth, false);
         if (cur != L.ou) {
             const unsigned src = cur;
-            for_owned(X, L, [&](int j, int i) { lrow(X, L, L.ou, j)[i] = lrow(X, L, src, j)[i]; });
+            for_owned(X, L, [&](int j, int i) { put(X, L, L.ou, j, i, lrow(X, L, src, j)[i], X.rank); });
             csync();
         }
     }
@@ -245,12 +262,12 @@ __global__ void __launch_bounds__(CT_THREADS) k_mg_ctail(CArgs A) {
     extern __shared__ __align__(16) unsigned char ct_smem[];
     cg::cluster_group cl = cg::this_cluster();
     Ctx X{ct_smem, (int)cl.block_rank(), (int)cl.num_blocks()};
-    // zero all of it (boundary columns and the zero row stay zero), stage k^2 and coefficients
+    // zero all of it (halo rows of boundary rows stay zero), stage k^2 and coefficients
     for (unsigned q = threadIdx.x; q < A.total / 16; q += blockDim.x) ((float4 *)ct_smem)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     for (int l = 0; l < A.nlev; l++) {
         const CLevel &L = A.lv[l];
-        const int j0 = own_j0(L, X.rank), j1 = own_j1(L, X.rank);
+        const int j0 = L.B[X.rank], j1 = L.B[X.rank + 1];
         float2 *cx = (float2 *)(ct_smem + L.ocx), *cy = (float2 *)(ct_smem + L.ocy);
         float *k2 = (float *)(ct_smem + L.ok);
         for (int q = threadIdx.x; q < 3 * L.nx; q += blockDim.x) cx[q] = L.cx[q];
@@ -258,42 +275,61 @@ __global__ void __launch_bounds__(CT_THREADS) k_mg_ctail(CArgs A) {
         for (int q = threadIdx.x; q < (j1 - j0) * L.nx; q += blockDim.x) k2[q] = L.k2[(size_t)j0 * L.nx + q];
     }
     const CLevel &T = A.lv[0];
+    // every block's zero fill precedes any store into its halos
+    csync();
     for_owned(X, T, [&](int j, int i) {
         const size_t p = (size_t)i + (size_t)T.nx * j;
         lrow(X, T, T.ob, j)[i] = A.b_top[p];
-        if (!A.zero) lrow(X, T, T.ou, j)[i] = A.u_top[p];
+        if (!A.zero) put(X, T, T.ou, j, i, A.u_top[p], X.rank);
     });
     csync();
     ct_cycle<0>(X, A, A.zero != 0, A.gf, A.gc);
     for_owned(X, T, [&](int j, int i) { A.u_top[(size_t)i + (size_t)T.nx * j] = lrow(X, T, T.ou, j)[i]; });
-    csync();  // no block leaves while another may still read its shared memory
+}
+
+// Nested slabs: level 0 in runs of ceil((ny - 2) / nc) rows, level l + 1 bounded by
+// (B_l[r] + 1) / 2.  False unless every level has odd ny and the next has (ny + 1) / 2.
+bool ct_bounds(int nlev, const int (*n)[3], int nc, int (*B)[CT_MAXC + 1]) {
+    if (nc < 1 || nc > CT_MAXC) return false;
+    for (int l = 0; l < nlev; l++) {
+        if (n[l][1] < 3 || n[l][1] % 2 == 0) return false;
+        if (l + 1 < nlev && n[l + 1][1] != (n[l][1] + 1) / 2) return false;
+    }
+    const int rows = (n[0][1] - 2 + nc - 1) / nc;
+    for (int r = 0; r <= nc; r++) B[0][r] = std::min(1 + r * rows, n[0][1] - 1);
+    for (int l = 1; l < nlev; l++)
+        for (int r = 0; r <= nc; r++) B[l][r] = (B[l - 1][r] + 1) / 2;
+    return true;
 }
 
 }  // namespace
 
 // Shared-memory layout of the cluster tail (identical in every block): per level b, u, t
-// (rows x nx complex64 each), k^2 (rows x nx floats), x coefficients (3 nx), y coefficients of
-// the owned rows (3 rows); then the compact coarsest right-hand side and a zero row.
+// ((rmax + 2) rows x nx complex64 each: the owned rows between two halo rows; rmax = the most
+// rows a block owns), k^2 (rmax x nx floats), x coefficients (3 nx), y coefficients of the owned
+// rows (3 rmax); then the compact coarsest right-hand side.  Levels that are not nested
+// (odd ny, halved) get a size no launch accepts.
 size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (*off)[6], unsigned *obc,
                        unsigned *ozero) {
     auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    int B[MAX_CT_LEVELS][CT_MAXC + 1];
+    if (nlev < 1 || nlev > MAX_CT_LEVELS || !ct_bounds(nlev, n, nc, B)) return ~(size_t)0;
     size_t p = 0;
-    int maxnx = 0;
     for (int l = 0; l < nlev; l++) {
-        const int nx = n[l][0], ny = n[l][1], rows = (ny - 2 + nc - 1) / nc;
-        maxnx = std::max(maxnx, nx);
-        const size_t vec = al((size_t)rows * nx * sizeof(float2));
+        const int nx = n[l][0];
+        int rmax = 0;
+        for (int r = 0; r < nc; r++) rmax = std::max(rmax, B[l][r + 1] - B[l][r]);
+        const size_t vec = al((size_t)(rmax + 2) * nx * sizeof(float2));
         off[l][0] = (unsigned)p; p += vec;                                             // b
         off[l][1] = (unsigned)p; p += vec;                                             // u
         off[l][2] = (unsigned)p; p += vec;                                             // t
-        off[l][3] = (unsigned)p; p += al((size_t)rows * nx * sizeof(float));           // k^2
+        off[l][3] = (unsigned)p; p += al((size_t)rmax * nx * sizeof(float));           // k^2
         off[l][4] = (unsigned)p; p += al((size_t)3 * nx * sizeof(float2));             // x coefficients
-        off[l][5] = (unsigned)p; p += al((size_t)3 * rows * sizeof(float2));           // y coefficients
+        off[l][5] = (unsigned)p; p += al((size_t)3 * rmax * sizeof(float2));           // y coefficients
     }
     *obc = (unsigned)p;
     p += al((size_t)nu_c * sizeof(float2));
     *ozero = (unsigned)p;
-    p += al((size_t)maxnx * sizeof(float2));
     return p;
 }
 
@@ -307,6 +343,8 @@ cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_t
     unsigned off[MAX_CT_LEVELS][6], obc = 0, ozero = 0;
     const size_t bytes = mg_ctail_layout(nlev, n, nc, nu_c, off, &obc, &ozero);
     if (bytes > CT_SMEM_BYTES) return cudaErrorInvalidValue;
+    int B[MAX_CT_LEVELS][CT_MAXC + 1];
+    if (!ct_bounds(nlev, n, nc, B)) return cudaErrorInvalidValue;
     CArgs A{};
     for (int l = 0; l < nlev; l++) {
         CLevel &L = A.lv[l];
@@ -317,7 +355,7 @@ cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_t
         L.c = ops[l].c;
         L.nx = n[l][0];
         L.ny = n[l][1];
-        L.rows = (n[l][1] - 2 + nc - 1) / nc;
+        for (int r = 0; r <= CT_MAXC; r++) L.B[r] = B[l][std::min(r, nc)];
         L.ob = off[l][0]; L.ou = off[l][1]; L.ot = off[l][2]; L.ok = off[l][3]; L.ocx = off[l][4]; L.ocy = off[l][5];
     }
     A.nlev = nlev;
@@ -331,7 +369,6 @@ cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_t
     A.b_top = b_top;
     A.u_top = u_top;
     A.obc = obc;
-    A.ozero = ozero;
     A.total = (unsigned)bytes;
     A.gf = gf;
     A.gc = gc;

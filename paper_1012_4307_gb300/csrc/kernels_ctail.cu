@@ -3,7 +3,7 @@
 // The coarse levels (129 x 129 nodes and below on the benchmark grids) hold too little work to
 // fill the GPU, so as separate launches each costs a launch latency plus a few dependent
 // phases, and on one thread block they are bound by one SM's issue rate.  Here a cluster of
-// NC thread blocks (8 or 16 SMs) keeps every level's b, u, t, k^2 and coefficients in its
+// NC thread blocks (8 or 16 SMs) keeps every level's b, u, t, diagonal and coefficients in its
 // distributed shared memory.  Block r owns the interior rows B_l[r] .. B_l[r+1]-1 of level l,
 // the slabs nested across levels (B_{l+1}[r] = (B_l[r] + 1) / 2), so that the full weighting of
 // an owned coarse row and the prolongation onto an owned fine row only touch rows that the
@@ -34,7 +34,8 @@ struct CLevel {
     float2 bk, c;
     int nx, ny;
     int B[CT_MAXC + 1];     // block r owns interior rows B[r] .. B[r+1]-1 (possibly none)
-    unsigned ob, ou, ot, ok, ocx, ocy;  // byte offsets in shared memory (same in every block)
+    unsigned ob, ou, ot, ok, ocx, ocy;  // byte offsets in shared memory (same in every block);
+                                        // ok: the diagonal of M at the owned nodes
 };
 
 struct CArgs {
@@ -88,21 +89,22 @@ __device__ __forceinline__ void put(const Ctx &X, const CLevel &L, unsigned off,
 __device__ __forceinline__ void csync() { cg::this_cluster().sync(); }
 
 // f(j, i) for every owned interior node, one node per thread and pass (consecutive threads
-// along a row).
+// along a row).  The row of pass index q is (q + 1/2) / m rounded down in FP32: exact for
+// q < 2^21, far above any slab.
 template <typename F>
 __device__ __forceinline__ void for_owned(const Ctx &X, const CLevel &L, F f) {
     const int j0 = L.B[X.rank], m = L.nx - 2, total = (L.B[X.rank + 1] - j0) * m;
+    const float rm = 1.0f / (float)m;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        const int r = q / m;
+        const int r = __float2int_rz(((float)q + 0.5f) * rm);
         f(j0 + r, 1 + q - r * m);
     }
 }
 
+// The diagonal of M at an owned node, formed once per launch (bk k^2 + c + the two centre
+// coefficients) and kept in shared memory.
 __device__ __forceinline__ float2 diag_at(const Ctx &X, const CLevel &L, int j, int i) {
-    const float2 *cx = (const float2 *)(X.sm + L.ocx), *cy = (const float2 *)(X.sm + L.ocy);
-    const int li = j - L.B[X.rank];
-    const float k2 = ((const float *)(X.sm + L.ok))[(size_t)li * L.nx + i];
-    return cadd(cadd(cx[3 * i + 1], cy[3 * li + 1]), cadd(cscale(L.bk, k2), L.c));
+    return ((const float2 *)(X.sm + L.ok))[(size_t)(j - L.B[X.rank]) * L.nx + i];
 }
 
 // (M u)(j, i) from this block's rows of the array at offset u (j - 1 and j + 1 may be halo
@@ -119,59 +121,102 @@ __device__ __forceinline__ float2 apply_at(const Ctx &X, const CLevel &L, unsign
     return cfma(d, uc[i], acc);
 }
 
-__device__ void zero_level(const Ctx &X, const CLevel &L, unsigned off) {
-    for_owned(X, L, [&](int j, int i) { put(X, L, off, j, i, make_float2(0.f, 0.f), X.rank); });
-}
+// The phases of the cycle.  Each is one out-of-line function over a level index, so that the
+// kernel's code stays small (inlining every phase at every depth multiplies it by the levels
+// and smoothing steps and runs out of the instruction cache); each ends with a cluster barrier.
 
-// nu sweeps on level L; *cur holds the iterate (offset), *oth the partner; zero: u = 0 on entry.
-__device__ void ct_smooth(const Ctx &X, const CArgs &A, const CLevel &L, int nu, unsigned *cur, unsigned *oth,
-                          bool zero) {
-    if (zero && (nu == 0 || A.rb)) {
-        zero_level(X, L, *cur);
+// nu sweeps on level l from *cur (partner *oth); zero: u = 0 on entry.  Returns the new pair.
+__device__ __noinline__ uint2 ph_smooth(Ctx X, const CArgs *A, int l, int nu, uint2 co, bool zero) {
+    const CLevel &L = A->lv[l];
+    const float om = A->omega;
+    if (zero && (nu == 0 || A->rb)) {
+        const unsigned u = co.x;
+        for_owned(X, L, [&](int j, int i) { put(X, L, u, j, i, make_float2(0.f, 0.f), X.rank); });
         csync();
     }
     for (int s = 0; s < nu; s++) {
-        if (A.rb) {
+        if (A->rb) {
             for (int colour = 0; colour < 2; colour++) {
                 // in place: this colour's neighbours (the other colour) are not written here
-                const unsigned u = *cur;
+                const unsigned u = co.x;
                 for_owned(X, L, [&](int j, int i) {
                     if (((i + j) & 1) != colour) return;
                     float2 d;
                     const float2 mu = apply_at(X, L, u, j, i, d);
                     const float2 uc = lrow(X, L, u, j)[i], b = lrow(X, L, L.ob, j)[i];
-                    put(X, L, u, j, i, cadd(uc, cscale(cmul(csub(b, mu), cinv(d)), A.omega)), X.rank);
+                    put(X, L, u, j, i, cadd(uc, cscale(cmul(csub(b, mu), cinv_fast(d)), om)), X.rank);
                 });
                 csync();
             }
         } else {
             const bool z0 = zero && s == 0;
-            const unsigned src = *cur, dst = *oth;
+            const unsigned src = co.x, dst = co.y;
             for_owned(X, L, [&](int j, int i) {
                 const float2 b = lrow(X, L, L.ob, j)[i];
                 float2 v;
                 if (z0) {
-                    v = cscale(cmul(b, cinv(diag_at(X, L, j, i))), A.omega);
+                    v = cscale(cmul(b, cinv_fast(diag_at(X, L, j, i))), om);
                 } else {
                     float2 d;
                     const float2 mu = apply_at(X, L, src, j, i, d);
-                    v = cadd(lrow(X, L, src, j)[i], cscale(cmul(csub(b, mu), cinv(d)), A.omega));
+                    v = cadd(lrow(X, L, src, j)[i], cscale(cmul(csub(b, mu), cinv_fast(d)), om));
                 }
                 put(X, L, dst, j, i, v, X.rank);
             });
             csync();
-            *cur = dst;
-            *oth = src;
+            co = make_uint2(dst, src);
         }
     }
+    return co;
+}
+
+// Residual of level l (iterate u) into r, then full weighting into level l + 1's b (the fine
+// rows 2J-1 .. 2J+1 of an owned coarse row J are owned or halo rows: nested slabs).
+__device__ __noinline__ void ph_restrict(Ctx X, const CArgs *A, int l, unsigned u, unsigned r) {
+    const CLevel &L = A->lv[l], &Lc = A->lv[l + 1];
+    for_owned(X, L, [&](int j, int i) {
+        float2 d;
+        const float2 mu = apply_at(X, L, u, j, i, d);
+        put(X, L, r, j, i, csub(lrow(X, L, L.ob, j)[i], mu), X.rank);
+    });
+    csync();
+    for_owned(X, Lc, [&](int J, int I) {
+        const float2 *r0 = lrow(X, L, r, 2 * J - 1), *r1 = lrow(X, L, r, 2 * J), *r2 = lrow(X, L, r, 2 * J + 1);
+        const int x = 2 * I;
+        const float2 a0 = cadd(cadd(r0[x - 1], r0[x + 1]), cscale(r0[x], 2.f));
+        const float2 a1 = cadd(cadd(r1[x - 1], r1[x + 1]), cscale(r1[x], 2.f));
+        const float2 a2 = cadd(cadd(r2[x - 1], r2[x + 1]), cscale(r2[x], 2.f));
+        lrow(X, Lc, Lc.ob, J)[I] = cscale(cadd(cadd(a0, a2), cscale(a1, 2.f)), 0.0625f);
+    });
+    csync();
+}
+
+// Bilinear prolongation of level l + 1's u (coarse rows j/2 and (j+1)/2: owned or halo rows of
+// the coarse slab), added to level l's iterate u.
+__device__ __noinline__ void ph_prolong(Ctx X, const CArgs *A, int l, unsigned u) {
+    const CLevel &L = A->lv[l], &Lc = A->lv[l + 1];
+    for_owned(X, L, [&](int j, int i) {
+        const float2 *ea = lrow(X, Lc, Lc.ou, j >> 1), *eb = lrow(X, Lc, Lc.ou, (j + 1) >> 1);
+        const int ia = i >> 1, ib = (i + 1) >> 1;
+        const float2 e = cadd(cadd(ea[ia], ea[ib]), cadd(eb[ia], eb[ib]));
+        put(X, L, u, j, i, cadd(lrow(X, L, u, j)[i], cscale(e, 0.25f)), X.rank);
+    });
+    csync();
+}
+
+__device__ __noinline__ void ph_copy(Ctx X, const CArgs *A, int l, unsigned dst, unsigned src) {
+    const CLevel &L = A->lv[l];
+    for_owned(X, L, [&](int j, int i) { put(X, L, dst, j, i, lrow(X, L, src, j)[i], X.rank); });
+    csync();
 }
 
 // Exact coarsest solve: every block gathers the whole right-hand side, computes its share of
 // the rows of Minv b (one warp per row) and stores each result in the owning block's u (and
 // the halos that hold its row).
-__device__ void ct_dense(const Ctx &X, const CArgs &A, const CLevel &L) {
-    float2 *bc = (float2 *)(X.sm + A.obc);
-    const int mx = L.nx - 2, nu = A.nu_c;
+__device__ __noinline__ void ph_dense(Ctx X, const CArgs *A, int l) {
+    const CLevel &L = A->lv[l];
+    float2 *bc = (float2 *)(X.sm + A->obc);
+    const int mx = L.nx - 2, nu = A->nu_c;
     for (int c = threadIdx.x; c < nu; c += blockDim.x) {
         const int i = 1 + c % mx, j = 1 + c / mx;
         bc[c] = crow(X, L, L.ob, j, owner_of(L, X.nc, j))[i];
@@ -179,7 +224,7 @@ __device__ void ct_dense(const Ctx &X, const CArgs &A, const CLevel &L) {
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int r = X.rank * nw + warp; r < nu; r += X.nc * nw) {
-        const float2 *mrow = A.minv + (size_t)r * nu;
+        const float2 *mrow = A->minv + (size_t)r * nu;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int c = lane; c < nu; c += 32) acc = cfma(mrow[c], bc[c], acc);
@@ -197,94 +242,73 @@ __device__ void ct_dense(const Ctx &X, const CArgs &A, const CLevel &L) {
 
 // Level LVL of the cycle (compile-time depth); the result ends in the level's u.
 template <int LVL>
-__device__ void ct_cycle(const Ctx &X, const CArgs &A, bool zero, int gf, int gc) {
-    const CLevel &L = A.lv[LVL];
-    if (LVL == A.nlev - 1) {
-        ct_dense(X, A, L);
+__device__ __noinline__ void ct_cycle(Ctx X, const CArgs *A, bool zero, int gf, int gc) {
+    const CLevel &L = A->lv[LVL];
+    if (LVL == A->nlev - 1) {
+        ph_dense(X, A, LVL);
         return;
     }
     if constexpr (LVL + 1 < MAX_CT_LEVELS) {
-        unsigned cur = L.ou, oth = L.ot;
-        ct_smooth(X, A, L, A.nu1, &cur, &oth, zero);
-        const CLevel &Lc = A.lv[LVL + 1];
-        // residual into the free partner array, then full weighting into the coarse b (the fine
-        // rows 2J-1 .. 2J+1 of an owned coarse row J are owned or halo rows: nested slabs)
-        {
-            const unsigned u = cur, r = oth;
-            for_owned(X, L, [&](int j, int i) {
-                float2 d;
-                const float2 mu = apply_at(X, L, u, j, i, d);
-                put(X, L, r, j, i, csub(lrow(X, L, L.ob, j)[i], mu), X.rank);
-            });
-        }
-        csync();
-        for_owned(X, Lc, [&](int J, int I) {
-            const float2 *r0 = lrow(X, L, oth, 2 * J - 1), *r1 = lrow(X, L, oth, 2 * J),
-                         *r2 = lrow(X, L, oth, 2 * J + 1);
-            const int x = 2 * I;
-            const float2 a0 = cadd(cadd(r0[x - 1], r0[x + 1]), cscale(r0[x], 2.f));
-            const float2 a1 = cadd(cadd(r1[x - 1], r1[x + 1]), cscale(r1[x], 2.f));
-            const float2 a2 = cadd(cadd(r2[x - 1], r2[x + 1]), cscale(r2[x], 2.f));
-            lrow(X, Lc, Lc.ob, J)[I] = cscale(cadd(cadd(a0, a2), cscale(a1, 2.f)), 0.0625f);
-        });
-        csync();
-        if (LVL + 1 == A.nlev - 1) {
-            ct_dense(X, A, Lc);
+        uint2 co = ph_smooth(X, A, LVL, A->nu1, make_uint2(L.ou, L.ot), zero);
+        ph_restrict(X, A, LVL, co.x, co.y);
+        if (LVL + 1 == A->nlev - 1) {
+            ph_dense(X, A, LVL + 1);
         } else {
-            for (int k = 1; k <= gc; k++) {
-                if (k == 1) ct_cycle<LVL + 1>(X, A, true, gf, gc);
-                else ct_cycle<LVL + 1>(X, A, false, gc, gf);
-            }
+            // first visit from zero with (gf, gc), later ones from the iterate with (gc, gf)
+            for (int k = 1; k <= gc; k++) ct_cycle<LVL + 1>(X, A, k == 1, k == 1 ? gf : gc, k == 1 ? gc : gf);
         }
-        // bilinear prolongation of the coarse result (coarse rows j/2 and (j+1)/2: owned or halo
-        // rows of the coarse slab), added to the iterate
-        {
-            const unsigned u = cur;
-            for_owned(X, L, [&](int j, int i) {
-                const float2 *ea = lrow(X, Lc, Lc.ou, j >> 1), *eb = lrow(X, Lc, Lc.ou, (j + 1) >> 1);
-                const int ia = i >> 1, ib = (i + 1) >> 1;
-                const float2 e = cadd(cadd(ea[ia], ea[ib]), cadd(eb[ia], eb[ib]));
-                put(X, L, u, j, i, cadd(lrow(X, L, u, j)[i], cscale(e, 0.25f)), X.rank);
-            });
-        }
-        csync();
-        ct_smooth(X, A, L, A.nu2, &cur, &oth, false);
-        if (cur != L.ou) {
-            const unsigned src = cur;
-            for_owned(X, L, [&](int j, int i) { put(X, L, L.ou, j, i, lrow(X, L, src, j)[i], X.rank); });
-            csync();
-        }
+        ph_prolong(X, A, LVL, co.x);
+        co = ph_smooth(X, A, LVL, A->nu2, co, false);
+        if (co.x != L.ou) ph_copy(X, A, LVL, L.ou, co.x);
     }
 }
 
-__global__ void __launch_bounds__(CT_THREADS) k_mg_ctail(CArgs A) {
+__global__ void __launch_bounds__(CT_THREADS) k_mg_ctail(const __grid_constant__ CArgs A0) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char ct_smem[];
+    __shared__ CArgs As;
     cg::cluster_group cl = cg::this_cluster();
     Ctx X{ct_smem, (int)cl.block_rank(), (int)cl.num_blocks()};
-    // zero all of it (halo rows of boundary rows stay zero), stage k^2 and coefficients
-    for (unsigned q = threadIdx.x; q < A.total / 16; q += blockDim.x) ((float4 *)ct_smem)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    {
+        const int *src = reinterpret_cast<const int *>(&A0);
+        int *dst = reinterpret_cast<int *>(&As);
+        for (int q = threadIdx.x; q < (int)(sizeof(CArgs) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+    }
+    const CArgs *A = &As;
+    // zero all of it (halo rows of boundary rows stay zero)
+    for (unsigned q = threadIdx.x; q < A0.total / 16; q += blockDim.x) ((float4 *)ct_smem)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
-    for (int l = 0; l < A.nlev; l++) {
-        const CLevel &L = A.lv[l];
+    // stage the coefficients and the diagonal bk k^2 + c + centre coefficients of the owned rows
+    for (int l = 0; l < A->nlev; l++) {
+        const CLevel &L = A->lv[l];
         const int j0 = L.B[X.rank], j1 = L.B[X.rank + 1];
         float2 *cx = (float2 *)(ct_smem + L.ocx), *cy = (float2 *)(ct_smem + L.ocy);
-        float *k2 = (float *)(ct_smem + L.ok);
         for (int q = threadIdx.x; q < 3 * L.nx; q += blockDim.x) cx[q] = L.cx[q];
         for (int q = threadIdx.x; q < 3 * (j1 - j0); q += blockDim.x) cy[q] = L.cy[3 * j0 + q];
-        for (int q = threadIdx.x; q < (j1 - j0) * L.nx; q += blockDim.x) k2[q] = L.k2[(size_t)j0 * L.nx + q];
     }
-    const CLevel &T = A.lv[0];
+    __syncthreads();
+    for (int l = 0; l < A->nlev; l++) {
+        const CLevel &L = A->lv[l];
+        const int j0 = L.B[X.rank], j1 = L.B[X.rank + 1];
+        const float2 *cx = (const float2 *)(ct_smem + L.ocx), *cy = (const float2 *)(ct_smem + L.ocy);
+        float2 *dg = (float2 *)(ct_smem + L.ok);
+        for (int q = threadIdx.x; q < (j1 - j0) * L.nx; q += blockDim.x) {
+            const int li = q / L.nx, i = q - li * L.nx;
+            const float k2 = L.k2[(size_t)j0 * L.nx + q];
+            dg[q] = cadd(cadd(cx[3 * i + 1], cy[3 * li + 1]), cadd(cscale(L.bk, k2), L.c));
+        }
+    }
+    const CLevel &T = A->lv[0];
     // every block's zero fill precedes any store into its halos
     csync();
     for_owned(X, T, [&](int j, int i) {
         const size_t p = (size_t)i + (size_t)T.nx * j;
-        lrow(X, T, T.ob, j)[i] = A.b_top[p];
-        if (!A.zero) put(X, T, T.ou, j, i, A.u_top[p], X.rank);
+        lrow(X, T, T.ob, j)[i] = A->b_top[p];
+        if (!A->zero) put(X, T, T.ou, j, i, A->u_top[p], X.rank);
     });
     csync();
-    ct_cycle<0>(X, A, A.zero != 0, A.gf, A.gc);
-    for_owned(X, T, [&](int j, int i) { A.u_top[(size_t)i + (size_t)T.nx * j] = lrow(X, T, T.ou, j)[i]; });
+    ct_cycle<0>(X, A, A->zero != 0, A->gf, A->gc);
+    for_owned(X, T, [&](int j, int i) { A->u_top[(size_t)i + (size_t)T.nx * j] = lrow(X, T, T.ou, j)[i]; });
 }
 
 // Nested slabs: level 0 in runs of ceil((ny - 2) / nc) rows, level l + 1 bounded by
@@ -306,8 +330,8 @@ bool ct_bounds(int nlev, const int (*n)[3], int nc, int (*B)[CT_MAXC + 1]) {
 
 // Shared-memory layout of the cluster tail (identical in every block): per level b, u, t
 // ((rmax + 2) rows x nx complex64 each: the owned rows between two halo rows; rmax = the most
-// rows a block owns), k^2 (rmax x nx floats), x coefficients (3 nx), y coefficients of the owned
-// rows (3 rmax); then the compact coarsest right-hand side.  Levels that are not nested
+// rows a block owns), the diagonal of M (rmax x nx complex64), x coefficients (3 nx), y
+// coefficients of the owned rows (3 rmax); then the compact coarsest right-hand side.  Levels that are not nested
 // (odd ny, halved) get a size no launch accepts.
 size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (*off)[6], unsigned *obc,
                        unsigned *ozero) {
@@ -323,7 +347,7 @@ size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (
         off[l][0] = (unsigned)p; p += vec;                                             // b
         off[l][1] = (unsigned)p; p += vec;                                             // u
         off[l][2] = (unsigned)p; p += vec;                                             // t
-        off[l][3] = (unsigned)p; p += al((size_t)rmax * nx * sizeof(float));           // k^2
+        off[l][3] = (unsigned)p; p += al((size_t)rmax * nx * sizeof(float2));          // diagonal
         off[l][4] = (unsigned)p; p += al((size_t)3 * nx * sizeof(float2));             // x coefficients
         off[l][5] = (unsigned)p; p += al((size_t)3 * rmax * sizeof(float2));           // y coefficients
     }

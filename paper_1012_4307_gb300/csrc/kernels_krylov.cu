@@ -9,6 +9,7 @@
 // the same kernels, gated by the device flag, so the host never waits for the decision.
 // On GB300 the FP64 units (about 2 FMA per SM per clock) bound these kernels, not DRAM.
 #include "helm_internal.h"
+#include "df_arith.h"
 #include "dcgs2_coef.cuh"
 
 namespace {
@@ -161,6 +162,38 @@ __global__ void k_combine(size_t n, const CZ *__restrict__ Z, size_t ldz, int nz
     }
 }
 
+// x += Z y for complex64 Z: the sum over the basis in double-FP32 on the FP32 units (products
+// of the exact FP32 z with y split into float pairs are error-free, sums use TwoSum), added to
+// x in FP64 once per node.  The FP64 form above is bound by the FP64 units (4 FMA per vector
+// and node).
+__global__ void __launch_bounds__(NT) k_combine_df(size_t n, const float2 *__restrict__ Z, size_t ldz, int nz,
+                                                   const double2 *__restrict__ y, double2 *__restrict__ x) {
+    pdl_enter();
+    __shared__ float4 ys[64];  // (re hi, re lo, im hi, im lo)
+    for (int i = threadIdx.x; i < nz; i += NT) {
+        const ff a = ff_split(y[i].x), b = ff_split(y[i].y);
+        ys[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+    __syncthreads();
+    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+#pragma unroll 4
+        for (int c = 0; c < nz; c++) {
+            const float2 z = Z[(size_t)c * ldz + q];
+            const float4 y4 = ys[c];
+            const ff yr{y4.x, y4.y}, yi{y4.z, y4.w};
+            float p, e;
+            // re += zr yr - zi yi ; im += zr yi + zi yr
+            ff_prod_f(yr, z.x, p, e); ff_acc_prod(sr, cr, p, e);
+            ff_prod_f(yi, z.y, p, e); ff_acc_prod(sr, cr, -p, -e);
+            ff_prod_f(yi, z.x, p, e); ff_acc_prod(si, ci, p, e);
+            ff_prod_f(yr, z.y, p, e); ff_acc_prod(si, ci, p, e);
+        }
+        const double2 xq = x[q];
+        x[q] = make_double2(xq.x + ((double)sr + (double)cr), xq.y + ((double)si + (double)ci));
+    }
+}
+
 // Complex Givens rotations G = [c s; -conj(s) c] (c real) on column j of the Hessenberg
 // matrix (column-major, leading dimension ldh); see Saad, Iterative Methods for Sparse Linear
 // Systems, Section 6.5.9 for the real case.
@@ -224,13 +257,30 @@ __global__ void k_dcgs2_coef(int j, int has_w, const double2 *__restrict__ hv, c
     dcgs2_coef_warp(j, has_w, hv, alpha2, H, ldh, coef);
 }
 
-__global__ void k_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y) {
+// y = R^{-1} g for the k x k upper-triangular leading block R of H (column-major, leading
+// dimension ldh): R and g are staged in shared memory by the whole block, then one warp
+// eliminates column by column (y_r = g_r / R_rr, then g_i -= R_ir y_r for i < r, lanes over i),
+// with the reciprocals 1 / R_rr formed beforehand in parallel.
+__global__ void __launch_bounds__(NT) k_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y) {
     pdl_enter();
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    extern __shared__ double2 bs_smem[];
+    double2 *R = bs_smem, *gs = bs_smem + (size_t)k * k;
+    for (int q = threadIdx.x; q < k * k; q += blockDim.x) {
+        const int c = q / k, r = q - c * k;
+        R[q] = r <= c ? H[r + (size_t)ldh * c] : make_double2(0.0, 0.0);
+    }
+    for (int q = threadIdx.x; q < k; q += blockDim.x) gs[q] = g[q];
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    // the reciprocal diagonal first, all lanes at once; the elimination then only multiplies
+    for (int r = lane; r < k; r += 32) R[r + (size_t)k * r] = cinv(R[r + (size_t)k * r]);
+    __syncwarp();
     for (int r = k - 1; r >= 0; r--) {
-        double2 s = g[r];
-        for (int c = r + 1; c < k; c++) s = csub(s, cmul(H[r + (size_t)ldh * c], y[c]));
-        y[r] = cmul(s, cinv(H[r + (size_t)ldh * r]));
+        const double2 yr = cmul(gs[r], R[r + (size_t)k * r]);
+        for (int i = lane; i < r; i += 32) gs[i] = csub(gs[i], cmul(R[i + (size_t)k * r], yr));
+        if (lane == 0) y[r] = yr;
+        __syncwarp();
     }
 }
 
@@ -323,6 +373,10 @@ int blas_nblocks(size_t n) { return (int)std::min<size_t>(cdiv(n, NT), (size_t)M
 cudaError_t launch_mdot_norm(size_t n, const double2 *V, size_t ldv, int nv, const double2 *w, double2 *partials,
                              const int *gate, cudaStream_t s) {
     if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
+    if (nv == 0) {  // the norm alone: one value per block to reduce, not CH + 1
+        launch_pdl(k_mdot_norm<0>, dim3(blas_nblocks(n), 1), NT, 0, s, n, V, ldv, nv, w, partials, gate);
+        return cudaGetLastError();
+    }
     constexpr int CH = 8;
     dim3 g(blas_nblocks(n), std::max(1, (nv + CH - 1) / CH));
     launch_pdl(k_mdot_norm<CH>, g, NT, 0, s, n, V, ldv, nv, w, partials, gate);
@@ -356,7 +410,10 @@ cudaError_t launch_scale_inv(size_t n, const double2 *x, const double2 *scale, d
 template <typename CZ>
 cudaError_t launch_combine(size_t n, const CZ *Z, size_t ldz, int nz, const double2 *y, double2 *x, cudaStream_t s) {
     if (nz > 64) return cudaErrorInvalidValue;
-    launch_pdl(k_combine<CZ>, stream_grid(n), NT, 0, s, n, Z, ldz, nz, y, x);
+    if constexpr (sizeof(CZ) == sizeof(float2))
+        launch_pdl(k_combine_df, stream_grid(n), NT, 0, s, n, (const float2 *)Z, ldz, nz, y, x);
+    else
+        launch_pdl(k_combine<CZ>, stream_grid(n), NT, 0, s, n, Z, ldz, nz, y, x);
     return cudaGetLastError();
 }
 template cudaError_t launch_combine<float2>(size_t, const float2 *, size_t, int, const double2 *, double2 *, cudaStream_t);
@@ -383,7 +440,15 @@ cudaError_t launch_dcgs2_coef(int j, int has_w, const double2 *hv, const double2
 }
 
 cudaError_t launch_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y, cudaStream_t s) {
-    launch_pdl(k_backsolve, 1, 32, 0, s, H, ldh, k, g, y);
+    if (k < 1 || k > 64 || ldh < k) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)((64 * 64 + 64) * sizeof(double2)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    launch_pdl(k_backsolve, 1, NT, (size_t)(k * k + k) * sizeof(double2), s, H, ldh, k, g, y);
     return cudaGetLastError();
 }
 

@@ -335,35 +335,47 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
         float4 cur[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) cur[u] = u < j ? V[(size_t)u * ldv + q] : zero4;
-        for (int i0 = 0; i0 < j; i0 += 4) {
+        // basis vector i (value vq) into chain par (i mod 2)
+        auto step = [&](int i, const float4 vq, int par) {
+            float *va = vs[par], *wa = ws[par];
+            const ff vr = ff_re(vq), vi = ff_im(vq);
+            const float4 a4 = cA[i], c4 = cC[i];
+            const ff cr = ff_re(c4), ci = ff_im(c4);
+            // v -= V_i a ; w -= V_i c   (complex products)
+            if (SMALL_A) {
+                float *f = fa[par];
+                f[0] = __fmaf_rn(vq.x, a4.x, __fmaf_rn(-vq.z, a4.z, f[0]));
+                f[1] = __fmaf_rn(vq.x, a4.z, __fmaf_rn(vq.z, a4.x, f[1]));
+            } else {
+                const ff ar = ff_re(a4), ai = ff_im(a4);
+                ff_two_prod(vr, ar, p, e); ff_acc_prod(va[0], va[1], -p, -e);
+                ff_two_prod(vi, ai, p, e); ff_acc_prod(va[0], va[1], p, e);
+                ff_two_prod(vr, ai, p, e); ff_acc_prod(va[2], va[3], -p, -e);
+                ff_two_prod(vi, ar, p, e); ff_acc_prod(va[2], va[3], -p, -e);
+            }
+            ff_two_prod(vr, cr, p, e); ff_acc_prod(wa[0], wa[1], -p, -e);
+            ff_two_prod(vi, ci, p, e); ff_acc_prod(wa[0], wa[1], p, e);
+            ff_two_prod(vr, ci, p, e); ff_acc_prod(wa[2], wa[3], -p, -e);
+            ff_two_prod(vi, cr, p, e); ff_acc_prod(wa[2], wa[3], -p, -e);
+        };
+        int i0 = 0;
+        // groups whose successor is also full: no bounds tests
+        for (; i0 + 8 <= j; i0 += 4) {
+            float4 nxt[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) nxt[u] = V[(size_t)(i0 + 4 + u) * ldv + q];
+#pragma unroll
+            for (int u = 0; u < 4; u++) step(i0 + u, cur[u], u & 1);
+#pragma unroll
+            for (int u = 0; u < 4; u++) cur[u] = nxt[u];
+        }
+        for (; i0 < j; i0 += 4) {
             float4 nxt[4];
 #pragma unroll
             for (int u = 0; u < 4; u++) nxt[u] = i0 + 4 + u < j ? V[(size_t)(i0 + 4 + u) * ldv + q] : zero4;
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                if (i0 + u < j) {
-                    float *va = vs[u & 1], *wa = ws[u & 1];
-                    const ff vr = ff_re(cur[u]), vi = ff_im(cur[u]);
-                    const float4 a4 = cA[i0 + u], c4 = cC[i0 + u];
-                    const ff cr = ff_re(c4), ci = ff_im(c4);
-                    // v -= V_i a ; w -= V_i c   (complex products)
-                    if (SMALL_A) {
-                        float *f = fa[u & 1];
-                        f[0] = __fmaf_rn(cur[u].x, a4.x, __fmaf_rn(-cur[u].z, a4.z, f[0]));
-                        f[1] = __fmaf_rn(cur[u].x, a4.z, __fmaf_rn(cur[u].z, a4.x, f[1]));
-                    } else {
-                        const ff ar = ff_re(a4), ai = ff_im(a4);
-                        ff_two_prod(vr, ar, p, e); ff_acc_prod(va[0], va[1], -p, -e);
-                        ff_two_prod(vi, ai, p, e); ff_acc_prod(va[0], va[1], p, e);
-                        ff_two_prod(vr, ai, p, e); ff_acc_prod(va[2], va[3], -p, -e);
-                        ff_two_prod(vi, ar, p, e); ff_acc_prod(va[2], va[3], -p, -e);
-                    }
-                    ff_two_prod(vr, cr, p, e); ff_acc_prod(wa[0], wa[1], -p, -e);
-                    ff_two_prod(vi, ci, p, e); ff_acc_prod(wa[0], wa[1], p, e);
-                    ff_two_prod(vr, ci, p, e); ff_acc_prod(wa[2], wa[3], -p, -e);
-                    ff_two_prod(vi, cr, p, e); ff_acc_prod(wa[2], wa[3], -p, -e);
-                }
-            }
+            for (int u = 0; u < 4; u++)
+                if (i0 + u < j) step(i0 + u, cur[u], u & 1);
 #pragma unroll
             for (int u = 0; u < 4; u++) cur[u] = nxt[u];
         }

@@ -23,18 +23,23 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 //   and w' = w - x (s / alpha) - sum V_i (c_i - a_i s): coef[i] = alpha a_i,
 //   coef[j+i] = c_i - a_i s, coef[2j] = (1 / (alpha nu), small), coef[2j+1] = s / alpha,
 //   where small = 1 when ||alpha a|| <= 2^-18 alpha nu, else 0.
+// has_w = 2: the slot j + 1 vector and its inner products come from the unscaled x
+// (w' = A M^{-1} x = alpha w, the preconditioner being linear): they are divided by alpha
+// here, and coef[2j+2] = (1 / alpha, 0) tells the update pass to scale w' the same way
+// (has_w = 1: coef[2j+2] = (1, 0)).
 // One warp (lane = threadIdx.x & 31); lane l handles i = l and l + 32 (j <= 64).
 __device__ __forceinline__ void dcgs2_coef_warp(int j, int has_w, const double2 *hv, const double2 *alpha2,
                                                 double2 *H, int ldh, double2 *coef) {
     const int lane = threadIdx.x & 31;
     const double al = j > 0 ? alpha2[j].x : 1.0, ra = 1.0 / al;
+    const double rw = has_w == 2 ? ra : 1.0;
     double2 a[2], c[2];
     double s2 = 0.0, tr = 0.0, ti = 0.0;
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         const int i = lane + 32 * k;
         a[k] = i < j ? hv[i] : make_double2(0.0, 0.0);
-        c[k] = (has_w && i < j) ? hv[j + 1 + i] : make_double2(0.0, 0.0);
+        c[k] = (has_w && i < j) ? cscale(hv[j + 1 + i], rw) : make_double2(0.0, 0.0);
         s2 += a[k].x * a[k].x + a[k].y * a[k].y;
         // conj(a) c
         tr += a[k].x * c[k].x + a[k].y * c[k].y;
@@ -55,7 +60,7 @@ __device__ __forceinline__ void dcgs2_coef_warp(int j, int has_w, const double2 
         if (lane == 0) col[j] = make_double2(al * nu, 0.0);
     }
     if (!has_w) return;
-    const double2 t = make_double2((hv[2 * j + 1].x - tr) * ra, (hv[2 * j + 1].y - ti) * ra);
+    const double2 t = make_double2((hv[2 * j + 1].x * rw - tr) * ra, (hv[2 * j + 1].y * rw - ti) * ra);
     const double rn = 1.0 / nu;
     const double2 hjj = cscale(t, rn);
     const double2 sf = cscale(hjj, rn);
@@ -76,6 +81,7 @@ __device__ __forceinline__ void dcgs2_coef_warp(int j, int has_w, const double2 
         const double xn = al * nu;
         coef[2 * j] = make_double2(rn * ra, s2 <= 0x1p-36 * xn * xn ? 1.0 : 0.0);
         coef[2 * j + 1] = cscale(sf, ra);
+        coef[2 * j + 2] = make_double2(rw, 0.0);
     }
 }
 

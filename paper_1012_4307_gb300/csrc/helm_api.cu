@@ -701,6 +701,10 @@ cudaError_t precondition_pair(helm_handle *h, const float4 *v, const double2 *al
     return cycle<R>(h, 0, dst, z, true, h->mg.gamma_f, h->mg.gamma_c);
 }
 template cudaError_t precondition_pair<float>(helm_handle *, const float4 *, const double2 *, float2 *);
+cudaError_t precondition_level0_c64(helm_handle *h, float2 *z) {
+    return cycle<float>(h, 0, LvBuf<float>::b(h->lv[0]), z, true, h->mg.gamma_f, h->mg.gamma_c);
+}
+float2 *level0_rhs_c64(helm_handle *h) { return LvBuf<float>::b(h->lv[0]); }
 template cudaError_t precondition_pair<double>(helm_handle *, const float4 *, const double2 *, double2 *);
 
 static helm_status check_ptr(const void *p, size_t align, const char *name) {

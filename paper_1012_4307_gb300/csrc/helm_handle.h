@@ -165,6 +165,10 @@ template <typename R> cudaError_t precondition(helm_handle *h, const double2 *v,
 // v a float-pair vector (float4 (re.hi, re.lo, im.hi, im.lo) per node)
 template <typename R>
 cudaError_t precondition_pair(helm_handle *h, const float4 *v, const double2 *alpha, typename CT<R>::T *z);
+// The complex64 cycle applied to what level 0's right-hand-side buffer already holds (written
+// there by the delayed-CGS2 update pass), and that buffer.
+cudaError_t precondition_level0_c64(helm_handle *h, float2 *z);
+float2 *level0_rhs_c64(helm_handle *h);
 // First level of the fused coarse tail of a precision-R cycle under the handle's tuning (-1: none).
 template <typename R> int tail_top(const helm_handle *h);
 // First level of the cluster tail (2D complex64 cycles) under the handle's tuning (-1: none).

@@ -238,15 +238,19 @@ cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int n
 // The update pass with a ticket (a device counter at 0 between launches) writes (||w||, 0) to
 // alpha_out from its last block; without one (null) it only writes partials.  The dot pass's
 // partials go to launch_reduce_dcgs2: one block per value, and the last block to finish runs the
-// coefficient step of step j (ticket as above).
+// coefficient step of step j (ticket as above); w_scaled: w and its inner products are
+// alpha_j times the true ones (the preconditioner was applied to the unscaled slot j).
+// The update pass scales w by coef[2j+2].x and, with b_out, also writes the new slot j + 1 as
+// complex64 (the next step's preconditioner input).
 cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *x, const float4 *w,
                               double2 *partials, cudaStream_t s);
 cudaError_t launch_reduce_dcgs2(const double2 *partials, int nblk, double2 *hv, unsigned *ticket, int j,
-                                const double2 *alpha2, double2 *H, int ldh, double2 *coef, cudaStream_t s);
+                                const double2 *alpha2, double2 *H, int ldh, double2 *coef, int w_scaled,
+                                cudaStream_t s);
 cudaError_t launch_dcgs2_coef(int j, int has_w, const double2 *hv, const double2 *alpha2, double2 *H, int ldh,
                               double2 *coef, cudaStream_t s);
 cudaError_t launch_update2_pair(size_t n, float4 *V, size_t ldv, int j, const double2 *coef, double2 *partials,
-                                unsigned *ticket, double2 *alpha_out, cudaStream_t s);
+                                unsigned *ticket, double2 *alpha_out, float2 *b_out, cudaStream_t s);
 // w <- w / beta->x (float pairs)
 cudaError_t launch_scale_inv_pair(size_t n, float4 *w, const double2 *beta, cudaStream_t s);
 // in place: the double2 vector x becomes the float-pair vector x / beta->x (beta null: 1)
@@ -259,9 +263,11 @@ cudaError_t launch_reduce_decide(const double2 *partials, int nblk, double2 *hno
                                  cudaStream_t s);
 // y = x * (1 / scale[0].x)
 cudaError_t launch_scale_inv(size_t n, const double2 *x, const double2 *scale, double2 *y, cudaStream_t s);
-// x += sum_c y_c Z_c  (Z c64 or c128, ldz stride)
+// x += sum_c y_c Z_c  (Z c64 or c128, ldz stride); with alpha (c64 only) the weights are
+// y_c / alpha[c].x for c >= 1 (columns that hold alpha_c z_c)
 template <typename CZ>
-cudaError_t launch_combine(size_t n, const CZ *Z, size_t ldz, int nz, const double2 *y, double2 *x, cudaStream_t s);
+cudaError_t launch_combine(size_t n, const CZ *Z, size_t ldz, int nz, const double2 *y, const double2 *alpha,
+                           double2 *x, cudaStream_t s);
 
 // FGMRES small dense work on the device (one warp): rotations of column j, new rotation,
 // residual estimate |g_{j+1}| / fnorm->x written to est[j].

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(NT) k_update_norm_pair(size_t n, const float4 
 // measures and adds to H (the update that uses it is double-FP32, so A z_j stays exactly
 // expanded in the basis), so it is formed from the hi parts in FP32.
 template <int CH>
-__global__ void __launch_bounds__(NT, 4) k_mdot2_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
+__global__ void __launch_bounds__(NT, 6) k_mdot2_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
                                                    const float4 *__restrict__ x, const float4 *__restrict__ w,
                                                    double2 *__restrict__ partials) {
     pdl_enter();
@@ -301,10 +301,10 @@ __global__ void __launch_bounds__(NT, 4) k_mdot2_pair(size_t n, const float4 *__
 
 // One pass of the DCGS2 update for step j with coefficients coef (see k_dcgs2_coef):
 //   x <- (x - sum_{i<j} V_i A_i) r             (x = basis slot j: its final vector v_j)
-//   w <- w - x_old s - sum_{i<j} V_i C_i       (w = slot j + 1: once orthogonalised, not
+//   w <- w rw - x_old s - sum_{i<j} V_i C_i    (w = slot j + 1: once orthogonalised, not
 //                                                normalised)
-// with A = coef[0..j), C = coef[j..2j), r = coef[2j].x, s = coef[2j + 1];
-// partials[b] = (||w||^2, 0).
+// with A = coef[0..j), C = coef[j..2j), r = coef[2j].x, s = coef[2j + 1], rw = coef[2j + 2].x;
+// partials[b] = (||w||^2, 0); with b_out, b_out = the new w rounded to complex64.
 // With a ticket, the last block to finish also reduces the norm partials into
 // *alpha_out = (||w||, 0).
 // coef[2j].y != 0 marks a small correction, ||A|| <= 2^-18 ||x - sum V_i A_i|| (decided by the
@@ -313,8 +313,8 @@ __global__ void __launch_bounds__(NT, 4) k_mdot2_pair(size_t n, const float4 *__
 // Otherwise both sums are double-FP32.
 template <bool SMALL_A>
 __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, size_t ldv, int j,
-                                              const float4 *cA, const float4 *cC, ff rinv, ff sr, ff si,
-                                              float &sn, float &cn) {
+                                              const float4 *cA, const float4 *cC, ff rinv, ff sr, ff si, ff rw,
+                                              float2 *__restrict__ b_out, float &sn, float &cn) {
     float4 *x = V + (size_t)j * ldv, *w = V + (size_t)(j + 1) * ldv;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
@@ -324,9 +324,13 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
         // i mod 2), the first started from x and w; basis values loaded four at a time, the
         // next four while the current four are processed
         float vs[2][4] = {{xq.x, xq.y, xq.z, xq.w}, {0.f, 0.f, 0.f, 0.f}};
-        float ws[2][4] = {{wq.x, wq.y, wq.z, wq.w}, {0.f, 0.f, 0.f, 0.f}};
+        float ws[2][4];
         float fa[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // small correction: FP32 (re, im) per chain
         float p, e;
+        // w rw (rw = 1 / alpha_j when w came from the unscaled slot j, else exactly 1)
+        ff_two_prod(ff_re(wq), rw, ws[0][0], ws[0][1]);
+        ff_two_prod(ff_im(wq), rw, ws[0][2], ws[0][3]);
+        ws[1][0] = ws[1][1] = ws[1][2] = ws[1][3] = 0.f;
         // w -= x s: re -= xr sr - xi si ; im -= xr si + xi sr
         ff_two_prod(xr, sr, p, e); ff_acc_prod(ws[1][0], ws[1][1], -p, -e);
         ff_two_prod(xi, si, p, e); ff_acc_prod(ws[1][0], ws[1][1], p, e);
@@ -396,6 +400,7 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
         const ff wr = ff_add(ff_norm(ws[0][0], ws[0][1]), ff_norm(ws[1][0], ws[1][1]));
         const ff wi = ff_add(ff_norm(ws[0][2], ws[0][3]), ff_norm(ws[1][2], ws[1][3]));
         w[q] = make_float4(wr.hi, wr.lo, wi.hi, wi.lo);
+        if (b_out) b_out[q] = make_float2(wr.hi, wi.hi);  // complex64 copy (hi = the rounded pair)
         ff_two_prod(wr, wr, p, e);
         ff_acc_prod(sn, cn, p, e);
         ff_two_prod(wi, wi, p, e);
@@ -405,10 +410,11 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
 
 __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
                                                      const double2 *__restrict__ coef, double2 *__restrict__ partials,
-                                                     unsigned *ticket, double2 *alpha_out) {
+                                                     unsigned *ticket, double2 *alpha_out, float2 *__restrict__ b_out) {
     pdl_enter();
     __shared__ float4 cA[64], cC[64];
     __shared__ float4 sc[2];  // (r hi, lo, small-correction flag, 0), s
+    __shared__ float2 rws;    // scale of the incoming w: coef[2j+2].x as a float pair
     __shared__ double sums[1];
     for (int i = threadIdx.x; i < j; i += NT) {
         const ff a = ff_split(coef[i].x), b = ff_split(coef[i].y);
@@ -422,14 +428,16 @@ __global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restric
         sc[0] = make_float4(r.hi, r.lo, rc.y != 0.0 ? 1.f : 0.f, 0.f);
         const ff a = ff_split(coef[2 * j + 1].x), b = ff_split(coef[2 * j + 1].y);
         sc[1] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        const ff rw = ff_split(coef[2 * j + 2].x);
+        rws = make_float2(rw.hi, rw.lo);
     }
     __syncthreads();
-    const ff rinv = ff_re(sc[0]), sr = ff_re(sc[1]), si = ff_im(sc[1]);
+    const ff rinv = ff_re(sc[0]), sr = ff_re(sc[1]), si = ff_im(sc[1]), rw{rws.x, rws.y};
     float sn = 0.f, cn = 0.f;
     if (sc[0].z != 0.f)
-        update2_nodes<true>(n, V, ldv, j, cA, cC, rinv, sr, si, sn, cn);
+        update2_nodes<true>(n, V, ldv, j, cA, cC, rinv, sr, si, rw, b_out, sn, cn);
     else
-        update2_nodes<false>(n, V, ldv, j, cA, cC, rinv, sr, si, sn, cn);
+        update2_nodes<false>(n, V, ldv, j, cA, cC, rinv, sr, si, rw, b_out, sn, cn);
     ff vals[1] = {ff_norm(sn, cn)};
     block_sum_ff<1>(vals, sums);
     if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(sums[0], 0.0);
@@ -545,7 +553,7 @@ cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int n
     return cudaGetLastError();
 }
 
-constexpr int DF_CH2 = 4;  // basis vectors per block row of the two-vector dot pass
+constexpr int DF_CH2 = 2;  // basis vectors per block row of the two-vector dot pass (2: 40 registers, 6 blocks per SM)
 
 // The two-vector dot pass runs one wave: G blocks per block row of DF_CH2 basis vectors, with
 // G x (block rows) at most the blocks that are resident at once (152 SMs x the blocks that fit
@@ -573,9 +581,10 @@ cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, con
 }
 
 cudaError_t launch_update2_pair(size_t n, float4 *V, size_t ldv, int j, const double2 *coef, double2 *partials,
-                                unsigned *ticket, double2 *alpha_out, cudaStream_t s) {
+                                unsigned *ticket, double2 *alpha_out, float2 *b_out, cudaStream_t s) {
     if (j < 0 || j > 64) return cudaErrorInvalidValue;
-    launch_pdl(k_update2_pair, gs_df_update_nblocks(n), NT, 0, s, n, V, ldv, j, coef, partials, ticket, alpha_out);
+    launch_pdl(k_update2_pair, gs_df_update_nblocks(n), NT, 0, s, n, V, ldv, j, coef, partials, ticket, alpha_out,
+               b_out);
     return cudaGetLastError();
 }
 

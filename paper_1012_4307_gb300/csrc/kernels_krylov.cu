@@ -166,12 +166,16 @@ __global__ void k_combine(size_t n, const CZ *__restrict__ Z, size_t ldz, int nz
 // of the exact FP32 z with y split into float pairs are error-free, sums use TwoSum), added to
 // x in FP64 once per node.  The FP64 form above is bound by the FP64 units (4 FMA per vector
 // and node).
+// With alpha, column c >= 1 of Z holds alpha_c z_c (alpha_c = alpha[c].x) and its weight is
+// y_c / alpha_c.
 __global__ void __launch_bounds__(NT) k_combine_df(size_t n, const float2 *__restrict__ Z, size_t ldz, int nz,
-                                                   const double2 *__restrict__ y, double2 *__restrict__ x) {
+                                                   const double2 *__restrict__ y, const double2 *__restrict__ alpha,
+                                                   double2 *__restrict__ x) {
     pdl_enter();
     __shared__ float4 ys[64];  // (re hi, re lo, im hi, im lo)
     for (int i = threadIdx.x; i < nz; i += NT) {
-        const ff a = ff_split(y[i].x), b = ff_split(y[i].y);
+        const double r = (alpha && i > 0) ? 1.0 / alpha[i].x : 1.0;
+        const ff a = ff_split(y[i].x * r), b = ff_split(y[i].y * r);
         ys[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
     }
     __syncthreads();
@@ -237,7 +241,7 @@ __global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, do
 // the fixed order of k_reduce) followed, in the last block to finish, by the DCGS2 coefficient
 // step of step j (see dcgs2_coef.cuh); the ticket returns to 0.
 __global__ void k_reduce_dcgs2(const double2 *__restrict__ partials, int nblk, double2 *hv, unsigned *ticket, int j,
-                               const double2 *alpha2, double2 *H, int ldh, double2 *coef) {
+                               const double2 *alpha2, double2 *H, int ldh, double2 *coef, int has_w) {
     pdl_enter();
     __shared__ double2 sums[1];
     const int i = blockIdx.x;
@@ -246,7 +250,7 @@ __global__ void k_reduce_dcgs2(const double2 *__restrict__ partials, int nblk, d
     block_sum<1>(acc, sums);
     if (threadIdx.x == 0) hv[i] = sums[0];
     if (!last_block(ticket, gridDim.x)) return;
-    if (threadIdx.x < 32) dcgs2_coef_warp(j, 1, hv, alpha2, H, ldh, coef);
+    if (threadIdx.x < 32) dcgs2_coef_warp(j, has_w, hv, alpha2, H, ldh, coef);
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
@@ -408,16 +412,21 @@ cudaError_t launch_scale_inv(size_t n, const double2 *x, const double2 *scale, d
 }
 
 template <typename CZ>
-cudaError_t launch_combine(size_t n, const CZ *Z, size_t ldz, int nz, const double2 *y, double2 *x, cudaStream_t s) {
+cudaError_t launch_combine(size_t n, const CZ *Z, size_t ldz, int nz, const double2 *y, const double2 *alpha,
+                           double2 *x, cudaStream_t s) {
     if (nz > 64) return cudaErrorInvalidValue;
-    if constexpr (sizeof(CZ) == sizeof(float2))
-        launch_pdl(k_combine_df, stream_grid(n), NT, 0, s, n, (const float2 *)Z, ldz, nz, y, x);
-    else
+    if constexpr (sizeof(CZ) == sizeof(float2)) {
+        launch_pdl(k_combine_df, stream_grid(n), NT, 0, s, n, (const float2 *)Z, ldz, nz, y, alpha, x);
+    } else {
+        if (alpha) return cudaErrorInvalidValue;
         launch_pdl(k_combine<CZ>, stream_grid(n), NT, 0, s, n, Z, ldz, nz, y, x);
+    }
     return cudaGetLastError();
 }
-template cudaError_t launch_combine<float2>(size_t, const float2 *, size_t, int, const double2 *, double2 *, cudaStream_t);
-template cudaError_t launch_combine<double2>(size_t, const double2 *, size_t, int, const double2 *, double2 *, cudaStream_t);
+template cudaError_t launch_combine<float2>(size_t, const float2 *, size_t, int, const double2 *, const double2 *,
+                                            double2 *, cudaStream_t);
+template cudaError_t launch_combine<double2>(size_t, const double2 *, size_t, int, const double2 *, const double2 *,
+                                             double2 *, cudaStream_t);
 
 cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm,
                           double *est, cudaStream_t s) {
@@ -426,9 +435,11 @@ cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, d
 }
 
 cudaError_t launch_reduce_dcgs2(const double2 *partials, int nblk, double2 *hv, unsigned *ticket, int j,
-                                const double2 *alpha2, double2 *H, int ldh, double2 *coef, cudaStream_t s) {
+                                const double2 *alpha2, double2 *H, int ldh, double2 *coef, int w_scaled,
+                                cudaStream_t s) {
     if (j < 0 || j > 63) return cudaErrorInvalidValue;
-    launch_pdl(k_reduce_dcgs2, 2 * (j + 1), NT, 0, s, partials, nblk, hv, ticket, j, alpha2, H, ldh, coef);
+    launch_pdl(k_reduce_dcgs2, 2 * (j + 1), NT, 0, s, partials, nblk, hv, ticket, j, alpha2, H, ldh, coef,
+               w_scaled ? 2 : 1);
     return cudaGetLastError();
 }
 

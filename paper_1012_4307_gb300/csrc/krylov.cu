@@ -213,6 +213,20 @@ static cudaError_t precond_apply_pair(helm_handle *h, const float4 *v, const dou
     return launch_split_scale(h->np, w, nullptr, h->stream);
 }
 
+// Delayed CGS2 with a complex64 multigrid cycle: the update pass writes each new basis vector
+// straight into level 0's right-hand side, unscaled (see fgmres_step_dcgs2).
+static bool dcgs2_fold(const helm_handle *h) {
+    return h->mg.gs_arith == HELM_GS_DCGS2 && h->z_prec == HELM_C64 && h->mg.kind != HELM_PC_NONE;
+}
+
+// z = cycle(level 0's right-hand side) in complex64; w = A z as a float-pair vector.
+static cudaError_t precond_apply_level0(helm_handle *h, float2 *z, float4 *w) {
+    cudaError_t e = precondition_level0_c64(h, z);
+    if (e != cudaSuccess) return e;
+    ProfScope ps(h, HELM_K_APPLY, interior_pts(h) * (8 + 8 + 16), 0);
+    return launch_apply_A_df(h->Adf, h->dim, z, w, h->stream);
+}
+
 // z = precondition(v) in the workspace precision; w = A z (FP64)
 static cudaError_t precond_apply(helm_handle *h, const double2 *v, void *z, double2 *w) {
     cudaError_t e;
@@ -352,7 +366,13 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
     float4 *u = V4 + (size_t)j * np, *w = V4 + (size_t)(j + 1) * np;
     void *zj = (char *)h->Z + (size_t)j * np * zsz;
     const double nv = j + 1;
-    CKE(precond_apply_pair(h, u, j > 0 ? h->alpha2 + j : nullptr, zj, w));
+    // With a complex64 cycle, the previous update pass left x_j itself (not x_j / alpha_j) in
+    // level 0's right-hand side, so z_j and w come out alpha_j times too large: the coefficient
+    // step, the update pass and the solution update divide by alpha_j (the cycle and A are
+    // linear), and no conversion launch is needed.
+    const bool fold = dcgs2_fold(h), scaled = fold && j > 0;
+    if (scaled) CKE(precond_apply_level0(h, (float2 *)zj, w));
+    else CKE(precond_apply_pair(h, u, j > 0 ? h->alpha2 + j : nullptr, zj, w));
     {
         ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (nv + 1), 0);
         CKE(launch_mdot2_pair(np, V4, np, j + 1, u, w, h->partials, s));
@@ -360,8 +380,8 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
     {
         // reduction and, in its last block, the coefficient step
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
-        CKE(launch_reduce_dcgs2(h->partials, gs_df_dot2_nblocks(np, j + 1), h->hv, h->tickets, j, h->alpha2, h->H, ldh, h->dcoef,
-                                s));
+        CKE(launch_reduce_dcgs2(h->partials, gs_df_dot2_nblocks(np, j + 1), h->hv, h->tickets, j, h->alpha2, h->H, ldh,
+                                h->dcoef, scaled ? 1 : 0, s));
     }
     const bool fork = j > 0 && !h->prof.on;
     if (j > 0) {
@@ -378,7 +398,8 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
     {
         // the update and the norm of the new vector in one launch
         ProfScope ps(h, HELM_K_UPDATE_NORM, np * 16.0 * (nv + 3), 0);
-        CKE(launch_update2_pair(np, V4, np, j, h->dcoef, h->partials, h->tickets + 1, h->alpha2 + j + 1, s));
+        CKE(launch_update2_pair(np, V4, np, j, h->dcoef, h->partials, h->tickets + 1, h->alpha2 + j + 1,
+                                fold ? level0_rhs_c64(h) : nullptr, s));
     }
     if (fork) CKE(cudaStreamWaitEvent(s, h->ev_join, 0));
     if (j > 0) CKE(cudaMemcpyAsync(h->est_host + j - 1, h->est_dev + j - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -625,9 +646,10 @@ helm_status fgmres_advance(FgmresRun &r, bool block) {
                 const size_t zsz = h->z_prec == HELM_C64 ? sizeof(float2) : sizeof(double2);
                 ProfScope ps(h, HELM_K_VECTOR, np * (32.0 + zsz * jdone), np * 8.0 * jdone);
                 if (h->z_prec == HELM_C64)
-                    CKR(launch_combine<float2>(np, (const float2 *)h->Z, np, jdone, h->y, r.x, s));
+                    CKR(launch_combine<float2>(np, (const float2 *)h->Z, np, jdone, h->y,
+                                               dcgs2_fold(h) ? h->alpha2 : nullptr, r.x, s));
                 else
-                    CKR(launch_combine<double2>(np, (const double2 *)h->Z, np, jdone, h->y, r.x, s));
+                    CKR(launch_combine<double2>(np, (const double2 *)h->Z, np, jdone, h->y, nullptr, r.x, s));
             }
             r.phase = FgmresRun::START;
             break;

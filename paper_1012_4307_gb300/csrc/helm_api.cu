@@ -21,6 +21,7 @@ typedef std::complex<double> cd;
 // ------------------------------------------------------------------------------ errors
 static thread_local std::string g_last_error;
 thread_local bool g_pdl_off = false;
+thread_local bool g_pdl_cycle = false;
 
 helm_status helm_fail(helm_status st, const char *fmt, ...) {
     char buf[512];
@@ -668,6 +669,7 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
 // z = M^{-1}-approximation of v (one cycle from zero), v in FP64, z in precision R.
 template <typename R>
 cudaError_t precondition(helm_handle *h, const double2 *v, typename CT<R>::T *z) {
+    pdl_cycle_scope pdl;
     const double es = sizeof(typename CT<R>::T);
     if (h->mg.kind == HELM_PC_NONE) {
         ProfScope ps(h, HELM_K_VECTOR, h->np * (16 + es), 0);
@@ -689,6 +691,7 @@ template cudaError_t precondition<double>(helm_handle *, const double2 *, double
 // from zero.
 template <typename R>
 cudaError_t precondition_pair(helm_handle *h, const float4 *v, const double2 *alpha, typename CT<R>::T *z) {
+    pdl_cycle_scope pdl;
     typedef typename CT<R>::T C;
     const double es = sizeof(C);
     C *dst = h->mg.kind == HELM_PC_NONE ? z : LvBuf<R>::b(h->lv[0]);
@@ -702,6 +705,7 @@ cudaError_t precondition_pair(helm_handle *h, const float4 *v, const double2 *al
 }
 template cudaError_t precondition_pair<float>(helm_handle *, const float4 *, const double2 *, float2 *);
 cudaError_t precondition_level0_c64(helm_handle *h, float2 *z) {
+    pdl_cycle_scope pdl;
     return cycle<float>(h, 0, LvBuf<float>::b(h->lv[0]), z, true, h->mg.gamma_f, h->mg.gamma_c);
 }
 float2 *level0_rhs_c64(helm_handle *h) { return LvBuf<float>::b(h->lv[0]); }

@@ -80,12 +80,22 @@ cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, float
 // captures a CUDA graph (pdl_capture_scope): measured on GB300, replayed graphs of the FGMRES
 // steps ran about 4% slower with programmatic edges, while eager launch sequences (the cycle
 // alone) ran about 10% faster with them.
-extern thread_local bool g_pdl_off;
+// The multigrid cycle's launches (pdl_cycle_scope) keep the attribute inside captured graphs too:
+// its kernels are short and latency-bound, and each lets the next one's blocks be scheduled
+// while it drains.
+extern thread_local bool g_pdl_off, g_pdl_cycle;
+constexpr bool kPdlCycleInGraphs = true;
 struct pdl_capture_scope {
     bool keep;
     pdl_capture_scope() : keep(g_pdl_off) { g_pdl_off = true; }
     ~pdl_capture_scope() { g_pdl_off = keep; }
 };
+struct pdl_cycle_scope {
+    bool keep;
+    pdl_cycle_scope() : keep(g_pdl_cycle) { g_pdl_cycle = kPdlCycleInGraphs; }
+    ~pdl_cycle_scope() { g_pdl_cycle = keep; }
+};
+inline bool pdl_enabled() { return !g_pdl_off || g_pdl_cycle; }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_enter() {
@@ -104,7 +114,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = g_pdl_off ? 0 : 1;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 

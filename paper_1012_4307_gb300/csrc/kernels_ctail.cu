@@ -264,7 +264,7 @@ __device__ __noinline__ void ct_cycle(Ctx X, const CArgs *A, bool zero, int gf, 
 }
 
 __global__ void __launch_bounds__(CT_THREADS) k_mg_ctail(const __grid_constant__ CArgs A0) {
-    pdl_enter();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char ct_smem[];
     __shared__ CArgs As;
     cg::cluster_group cl = cg::this_cluster();
@@ -299,6 +299,8 @@ __global__ void __launch_bounds__(CT_THREADS) k_mg_ctail(const __grid_constant__
         }
     }
     const CLevel &T = A->lv[0];
+    // the operator data above is not written by earlier kernels; b_top and u_top are
+    pdl_wait();
     // every block's zero fill precedes any store into its halos
     csync();
     for_owned(X, T, [&](int j, int i) {
@@ -409,13 +411,15 @@ cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_t
     cfg.blockDim = dim3(CT_THREADS, 1, 1);
     cfg.dynamicSmemBytes = bytes;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = nc;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl_enabled() ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, k_mg_ctail, A);
 }
 

@@ -415,12 +415,15 @@ static cudaError_t fgmres_close_dcgs2(helm_handle *h, int jc, int m) {
     cudaStream_t s = h->stream;
     const float4 *V4 = (const float4 *)h->V;
     {
+        // the two-vector pass with x in both places: its first jc + 1 sums are V_i^H x, i < jc,
+        // and x^H x (slot jc is x)
         ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (jc + 1), 0);
-        CKE(launch_mdot_norm_pair(np, V4, np, jc, V4 + (size_t)jc * np, h->partials, nullptr, s));
+        const float4 *x = V4 + (size_t)jc * np;
+        CKE(launch_mdot2_pair(np, V4, np, jc + 1, x, x, h->partials, s));
     }
     {
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
-        CKE(launch_reduce(h->partials, gs_df_nblocks(np), jc + 1, h->hv, 0, nullptr, s));
+        CKE(launch_reduce(h->partials, gs_df_dot2_nblocks(np, jc + 1), jc + 1, h->hv, 0, nullptr, s));
         CKE(launch_dcgs2_coef(jc, 0, h->hv, h->alpha2, h->H, ldh, h->dcoef, s));
         CKE(launch_givens(h->H, ldh, jc - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, s));
     }

@@ -221,6 +221,7 @@ static bool dcgs2_fold(const helm_handle *h) {
 
 // z = cycle(level 0's right-hand side) in complex64; w = A z as a float-pair vector.
 static cudaError_t precond_apply_level0(helm_handle *h, float2 *z, float4 *w) {
+    pdl_cycle_scope pdl;  // the apply follows the cycle's last kernel
     cudaError_t e = precondition_level0_c64(h, z);
     if (e != cudaSuccess) return e;
     ProfScope ps(h, HELM_K_APPLY, interior_pts(h) * (8 + 8 + 16), 0);
@@ -378,7 +379,9 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
         CKE(launch_mdot2_pair(np, V4, np, j + 1, u, w, h->partials, s));
     }
     {
-        // reduction and, in its last block, the coefficient step
+        // reduction and, in its last block, the coefficient step (its few blocks may be scheduled
+        // while the dot pass drains)
+        pdl_cycle_scope pdl;
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
         CKE(launch_reduce_dcgs2(h->partials, gs_df_dot2_nblocks(np, j + 1), h->hv, h->tickets, j, h->alpha2, h->H, ldh,
                                 h->dcoef, scaled ? 1 : 0, s));

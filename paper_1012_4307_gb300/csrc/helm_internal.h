@@ -204,7 +204,7 @@ cudaError_t launch_mg_tail(int dim, int nlev, const DevOp<R> *ops, typename CT<R
 constexpr int MAX_CT_LEVELS = 6;
 constexpr size_t CT_SMEM_BYTES = 200 * 1024;
 size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (*off)[6], unsigned *obc,
-                       unsigned *ozero);
+                       unsigned *ominv);
 cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_top, float2 *u_top,
                             const float2 *minv, int nu_c, int nu1, int nu2, int rb, float omega, int zero, int gf,
                             int gc, int nc, cudaStream_t s);

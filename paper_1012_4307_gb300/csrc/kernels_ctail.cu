@@ -47,6 +47,8 @@ struct CArgs {
     const float2 *b_top;  // top level's right-hand side (global)
     float2 *u_top;        // top level's result; initial guess when !zero (global)
     unsigned obc;         // compact coarsest right-hand side
+    unsigned ominv;       // this block's rows of minv (mrow per warp), staged in the prologue
+    int mrow;             // 0: minv is read from global memory in the dense phase
 };
 
 struct Ctx {
@@ -223,8 +225,9 @@ __device__ __noinline__ void ph_dense(Ctx X, const CArgs *A, int l) {
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r = X.rank * nw + warp; r < nu; r += X.nc * nw) {
-        const float2 *mrow = A->minv + (size_t)r * nu;
+    for (int r = X.rank * nw + warp, k = 0; r < nu; r += X.nc * nw, k++) {
+        const float2 *mrow = A->mrow ? (const float2 *)(X.sm + A->ominv) + (size_t)(warp * A->mrow + k) * nu
+                                     : A->minv + (size_t)r * nu;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int c = lane; c < nu; c += 32) acc = cfma(mrow[c], bc[c], acc);
@@ -238,6 +241,15 @@ __device__ __noinline__ void ph_dense(Ctx X, const CArgs *A, int l) {
         }
     }
     csync();
+}
+
+// This block's rows of the coarsest inverse into shared memory (the rows ph_dense gives each
+// warp), before the kernel waits on its predecessor.
+__device__ __noinline__ void ph_stage_minv(Ctx X, const CArgs *A) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, nu = A->nu_c;
+    float2 *dst = (float2 *)(X.sm + A->ominv);
+    for (int r = X.rank * nw + warp, k = 0; r < nu; r += X.nc * nw, k++)
+        for (int c = lane; c < nu; c += 32) dst[(size_t)(warp * A->mrow + k) * nu + c] = A->minv[(size_t)r * nu + c];
 }
 
 // Level LVL of the cycle (compile-time depth); the result ends in the level's u.
@@ -263,7 +275,7 @@ __device__ __noinline__ void ct_cycle(Ctx X, const CArgs *A, bool zero, int gf, 
     }
 }
 
-__global__ void __launch_bounds__(CT_THREADS) k_mg_ctail(const __grid_constant__ CArgs A0) {
+__global__ void __launch_bounds__(CT_THREADS, 1) k_mg_ctail(const __grid_constant__ CArgs A0) {
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char ct_smem[];
     __shared__ CArgs As;
@@ -298,6 +310,7 @@ __global__ void __launch_bounds__(CT_THREADS) k_mg_ctail(const __grid_constant__
             dg[q] = cadd(cadd(cx[3 * i + 1], cy[3 * li + 1]), cadd(cscale(L.bk, k2), L.c));
         }
     }
+    if (A->mrow) ph_stage_minv(X, A);
     const CLevel &T = A->lv[0];
     // the operator data above is not written by earlier kernels; b_top and u_top are
     pdl_wait();
@@ -330,13 +343,23 @@ bool ct_bounds(int nlev, const int (*n)[3], int nc, int (*B)[CT_MAXC + 1]) {
 
 }  // namespace
 
+// Rows of the coarsest inverse each warp handles in the dense phase, and the shared memory that
+// staging them takes (0 when that is more than 64 KB: the dense phase then reads them from
+// global memory).
+static int ct_minv_rows(int nc, int nu_c) { return (nu_c + nc * (CT_THREADS / 32) - 1) / (nc * (CT_THREADS / 32)); }
+static size_t ct_minv_stage_bytes(int nc, int nu_c) {
+    const size_t b = (size_t)(CT_THREADS / 32) * ct_minv_rows(nc, nu_c) * nu_c * sizeof(float2);
+    return b <= 64 * 1024 ? b : 0;
+}
+
 // Shared-memory layout of the cluster tail (identical in every block): per level b, u, t
 // ((rmax + 2) rows x nx complex64 each: the owned rows between two halo rows; rmax = the most
 // rows a block owns), the diagonal of M (rmax x nx complex64), x coefficients (3 nx), y
-// coefficients of the owned rows (3 rmax); then the compact coarsest right-hand side.  Levels that are not nested
-// (odd ny, halved) get a size no launch accepts.
+// coefficients of the owned rows (3 rmax); then the compact coarsest right-hand side and the
+// block's staged rows of the coarsest inverse (ominv).  Levels that are not nested (odd ny,
+// halved) get a size no launch accepts.
 size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (*off)[6], unsigned *obc,
-                       unsigned *ozero) {
+                       unsigned *ominv) {
     auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
     int B[MAX_CT_LEVELS][CT_MAXC + 1];
     if (nlev < 1 || nlev > MAX_CT_LEVELS || !ct_bounds(nlev, n, nc, B)) return ~(size_t)0;
@@ -355,7 +378,8 @@ size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (
     }
     *obc = (unsigned)p;
     p += al((size_t)nu_c * sizeof(float2));
-    *ozero = (unsigned)p;
+    *ominv = (unsigned)p;
+    p += al(ct_minv_stage_bytes(nc, nu_c));
     return p;
 }
 
@@ -366,8 +390,8 @@ cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_t
     int n[MAX_CT_LEVELS][3];
     for (int l = 0; l < nlev; l++)
         for (int a = 0; a < 3; a++) n[l][a] = ops[l].n[a];
-    unsigned off[MAX_CT_LEVELS][6], obc = 0, ozero = 0;
-    const size_t bytes = mg_ctail_layout(nlev, n, nc, nu_c, off, &obc, &ozero);
+    unsigned off[MAX_CT_LEVELS][6], obc = 0, ominv = 0;
+    const size_t bytes = mg_ctail_layout(nlev, n, nc, nu_c, off, &obc, &ominv);
     if (bytes > CT_SMEM_BYTES) return cudaErrorInvalidValue;
     int B[MAX_CT_LEVELS][CT_MAXC + 1];
     if (!ct_bounds(nlev, n, nc, B)) return cudaErrorInvalidValue;
@@ -395,6 +419,8 @@ cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_t
     A.b_top = b_top;
     A.u_top = u_top;
     A.obc = obc;
+    A.ominv = ominv;
+    A.mrow = ct_minv_stage_bytes(nc, nu_c) ? ct_minv_rows(nc, nu_c) : 0;
     A.total = (unsigned)bytes;
     A.gf = gf;
     A.gc = gc;

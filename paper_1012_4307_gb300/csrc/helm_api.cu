@@ -565,6 +565,31 @@ template <typename R> int tail_top(const helm_handle *h) {
 template int tail_top<float>(const helm_handle *);
 template int tail_top<double>(const helm_handle *);
 
+const void *ctail_image(helm_handle *h, bool build) {
+    const int top = ctail_top(h);
+    if (top < 0) return nullptr;
+    const int nc = h->tune.cluster_ctas, key = top * 32 + nc;
+    for (const auto &e : h->ctail_img)
+        if (e.first == key) return e.second;
+    if (!build) return nullptr;
+    const int nt = (int)h->lv.size() - top;
+    DevOp<float> ops[MAX_CT_LEVELS];
+    for (int k = 0; k < nt; k++) ops[k] = h->lv[top + k].M32;
+    void *img = nullptr;
+    if (build_mg_ctail_image(nt, ops, h->minv32, h->nu_c, nc, &img, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    try {
+        h->owned.push_back(img);
+        h->ctail_img.push_back({key, img});
+    } catch (...) {
+        cudaFree(img);
+        return nullptr;
+    }
+    return img;
+}
+
 int ctail_top(const helm_handle *h) {
     const int want = h->tune.cluster_levels;
     if (h->dim != 2 || want < 2 || h->mg.kind == HELM_PC_NONE) return -1;
@@ -594,7 +619,7 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
             ProfScope ps(h, HELM_K_COARSE, bytes + (double)h->nu_c * h->nu_c * sizeof(float2), 0);
             return launch_mg_ctail(nt, ops, b, u, h->minv32, h->nu_c, h->mg.nu1, h->mg.nu2,
                                    h->mg.smoother == HELM_SMOOTH_RB, (float)h->mg.omega, zero ? 1 : 0, gf, gc,
-                                   h->tune.cluster_ctas, h->stream);
+                                   h->tune.cluster_ctas, ctail_image(h, !h->capturing), h->stream);
         }
     }
     if (l == tail_top<R>(h)) {

@@ -72,6 +72,9 @@ struct helm_handle {
     int tail_top32 = -1, tail_top64 = -1;  // first level of the fused tail (-1: none), as built
     helm_tuning tune{};                      // kernel choices (see helm_set_tuning)
     int ctail_fit[2] = {0, 0};               // most coarsest levels a cluster tail of 8 / 16 blocks holds
+    // initial shared-memory images of the cluster tail, keyed by first level * 32 + blocks
+    // (device memory, also listed in owned)
+    std::vector<std::pair<int, void *>> ctail_img;
     int nu_c = 0;
     double2 *minv64 = nullptr;
     float2 *minv32 = nullptr;
@@ -173,3 +176,6 @@ float2 *level0_rhs_c64(helm_handle *h);
 template <typename R> int tail_top(const helm_handle *h);
 // First level of the cluster tail (2D complex64 cycles) under the handle's tuning (-1: none).
 int ctail_top(const helm_handle *h);
+// The cluster tail's initial shared-memory image for the current tuning (null: no tail, or not
+// built and build false); built on the handle's stream, outside graph capture.
+const void *ctail_image(helm_handle *h, bool build);

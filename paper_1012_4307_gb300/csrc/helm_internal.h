@@ -205,9 +205,13 @@ constexpr int MAX_CT_LEVELS = 6;
 constexpr size_t CT_SMEM_BYTES = 200 * 1024;
 size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (*off)[6], unsigned *obc,
                        unsigned *ominv);
+// img: the blocks' initial shared memory from build_mg_ctail_image for the same levels and nc
+// (null: each launch builds it itself); *out is device memory the caller frees.
 cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_top, float2 *u_top,
                             const float2 *minv, int nu_c, int nu1, int nu2, int rb, float omega, int zero, int gf,
-                            int gc, int nc, cudaStream_t s);
+                            int gc, int nc, const void *img, cudaStream_t s);
+cudaError_t build_mg_ctail_image(int nlev, const DevOp<float> *ops, const float2 *minv, int nu_c, int nc, void **out,
+                                 cudaStream_t s);
 int mg_ctail_max_clusters(int nc, size_t bytes);
 
 template <typename CI, typename CO>

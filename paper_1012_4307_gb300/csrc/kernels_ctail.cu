@@ -49,6 +49,7 @@ struct CArgs {
     unsigned obc;         // compact coarsest right-hand side
     unsigned ominv;       // this block's rows of minv (mrow per warp), staged in the prologue
     int mrow;             // 0: minv is read from global memory in the dense phase
+    const float4 *img;    // initial shared memory of every block (rank r at r * total / 16), or null
 };
 
 struct Ctx {
@@ -275,6 +276,43 @@ __device__ __noinline__ void ct_cycle(Ctx X, const CArgs *A, bool zero, int gf, 
     }
 }
 
+// The block's shared memory before the cycle: zeros, the staged coefficients, the diagonal
+// bk k^2 + c + centre coefficients of the owned rows and the block's rows of the coarsest
+// inverse.  X.sm may point to global memory (the image that k_ctail_image builds once).
+__device__ __noinline__ void ct_init(Ctx X, const CArgs *A) {
+    for (unsigned q = threadIdx.x; q < A->total / 16; q += blockDim.x) ((float4 *)X.sm)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    for (int l = 0; l < A->nlev; l++) {
+        const CLevel &L = A->lv[l];
+        const int j0 = L.B[X.rank], j1 = L.B[X.rank + 1];
+        float2 *cx = (float2 *)(X.sm + L.ocx), *cy = (float2 *)(X.sm + L.ocy);
+        for (int q = threadIdx.x; q < 3 * L.nx; q += blockDim.x) cx[q] = L.cx[q];
+        for (int q = threadIdx.x; q < 3 * (j1 - j0); q += blockDim.x) cy[q] = L.cy[3 * j0 + q];
+    }
+    __syncthreads();
+    for (int l = 0; l < A->nlev; l++) {
+        const CLevel &L = A->lv[l];
+        const int j0 = L.B[X.rank], j1 = L.B[X.rank + 1];
+        const float2 *cx = (const float2 *)(X.sm + L.ocx), *cy = (const float2 *)(X.sm + L.ocy);
+        float2 *dg = (float2 *)(X.sm + L.ok);
+        for (int q = threadIdx.x; q < (j1 - j0) * L.nx; q += blockDim.x) {
+            const int li = q / L.nx, i = q - li * L.nx;
+            const float k2 = L.k2[(size_t)j0 * L.nx + q];
+            dg[q] = cadd(cadd(cx[3 * i + 1], cy[3 * li + 1]), cadd(cscale(L.bk, k2), L.c));
+        }
+    }
+    if (A->mrow) ph_stage_minv(X, A);
+    __syncthreads();
+}
+
+// Builds the initial shared memory of every block of the cluster tail in global memory (one
+// block per rank, no cluster): the tail then starts with one copy instead of three dependent
+// rounds of loads.
+__global__ void __launch_bounds__(CT_THREADS, 1) k_ctail_image(const __grid_constant__ CArgs A0, unsigned char *img) {
+    Ctx X{img + (size_t)blockIdx.x * A0.total, (int)blockIdx.x, (int)gridDim.x};
+    ct_init(X, &A0);
+}
+
 __global__ void __launch_bounds__(CT_THREADS, 1) k_mg_ctail(const __grid_constant__ CArgs A0) {
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char ct_smem[];
@@ -287,34 +325,18 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_mg_ctail(const __grid_constan
         for (int q = threadIdx.x; q < (int)(sizeof(CArgs) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
     }
     const CArgs *A = &As;
-    // zero all of it (halo rows of boundary rows stay zero)
-    for (unsigned q = threadIdx.x; q < A0.total / 16; q += blockDim.x) ((float4 *)ct_smem)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-    // stage the coefficients and the diagonal bk k^2 + c + centre coefficients of the owned rows
-    for (int l = 0; l < A->nlev; l++) {
-        const CLevel &L = A->lv[l];
-        const int j0 = L.B[X.rank], j1 = L.B[X.rank + 1];
-        float2 *cx = (float2 *)(ct_smem + L.ocx), *cy = (float2 *)(ct_smem + L.ocy);
-        for (int q = threadIdx.x; q < 3 * L.nx; q += blockDim.x) cx[q] = L.cx[q];
-        for (int q = threadIdx.x; q < 3 * (j1 - j0); q += blockDim.x) cy[q] = L.cy[3 * j0 + q];
+    if (A0.img) {
+        const float4 *src = A0.img + (size_t)X.rank * (A0.total / 16);
+        for (unsigned q = threadIdx.x; q < A0.total / 16; q += blockDim.x) ((float4 *)ct_smem)[q] = src[q];
+        __syncthreads();
+    } else {
+        __syncthreads();
+        ct_init(X, A);
     }
-    __syncthreads();
-    for (int l = 0; l < A->nlev; l++) {
-        const CLevel &L = A->lv[l];
-        const int j0 = L.B[X.rank], j1 = L.B[X.rank + 1];
-        const float2 *cx = (const float2 *)(ct_smem + L.ocx), *cy = (const float2 *)(ct_smem + L.ocy);
-        float2 *dg = (float2 *)(ct_smem + L.ok);
-        for (int q = threadIdx.x; q < (j1 - j0) * L.nx; q += blockDim.x) {
-            const int li = q / L.nx, i = q - li * L.nx;
-            const float k2 = L.k2[(size_t)j0 * L.nx + q];
-            dg[q] = cadd(cadd(cx[3 * i + 1], cy[3 * li + 1]), cadd(cscale(L.bk, k2), L.c));
-        }
-    }
-    if (A->mrow) ph_stage_minv(X, A);
     const CLevel &T = A->lv[0];
     // the operator data above is not written by earlier kernels; b_top and u_top are
     pdl_wait();
-    // every block's zero fill precedes any store into its halos
+    // every block's initial fill precedes any store into its halos
     csync();
     for_owned(X, T, [&](int j, int i) {
         const size_t p = (size_t)i + (size_t)T.nx * j;
@@ -383,19 +405,18 @@ size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (
     return p;
 }
 
-cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_top, float2 *u_top,
-                            const float2 *minv, int nu_c, int nu1, int nu2, int rb, float omega, int zero, int gf,
-                            int gc, int nc, cudaStream_t s) {
-    if (nlev < 2 || nlev > MAX_CT_LEVELS || (nc != 8 && nc != 16)) return cudaErrorInvalidValue;
+// The launch arguments of a cluster tail over nlev levels on nc blocks (0 bytes: not possible).
+static size_t ct_args(int nlev, const DevOp<float> *ops, const float2 *minv, int nu_c, int nc, CArgs &A) {
+    if (nlev < 2 || nlev > MAX_CT_LEVELS || (nc != 8 && nc != 16)) return 0;
     int n[MAX_CT_LEVELS][3];
     for (int l = 0; l < nlev; l++)
         for (int a = 0; a < 3; a++) n[l][a] = ops[l].n[a];
     unsigned off[MAX_CT_LEVELS][6], obc = 0, ominv = 0;
     const size_t bytes = mg_ctail_layout(nlev, n, nc, nu_c, off, &obc, &ominv);
-    if (bytes > CT_SMEM_BYTES) return cudaErrorInvalidValue;
+    if (bytes > CT_SMEM_BYTES) return 0;
     int B[MAX_CT_LEVELS][CT_MAXC + 1];
-    if (!ct_bounds(nlev, n, nc, B)) return cudaErrorInvalidValue;
-    CArgs A{};
+    if (!ct_bounds(nlev, n, nc, B)) return 0;
+    A = CArgs{};
     for (int l = 0; l < nlev; l++) {
         CLevel &L = A.lv[l];
         L.cx = ops[l].coef[0];
@@ -410,20 +431,48 @@ cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_t
     }
     A.nlev = nlev;
     A.nu_c = nu_c;
+    A.minv = minv;
+    A.obc = obc;
+    A.ominv = ominv;
+    A.mrow = ct_minv_stage_bytes(nc, nu_c) ? ct_minv_rows(nc, nu_c) : 0;
+    A.total = (unsigned)bytes;
+    return bytes;
+}
+
+cudaError_t build_mg_ctail_image(int nlev, const DevOp<float> *ops, const float2 *minv, int nu_c, int nc, void **out,
+                                 cudaStream_t s) {
+    *out = nullptr;
+    CArgs A;
+    const size_t bytes = ct_args(nlev, ops, minv, nu_c, nc, A);
+    if (!bytes) return cudaErrorInvalidValue;
+    void *img = nullptr;
+    cudaError_t e = cudaMalloc(&img, bytes * nc);
+    if (e != cudaSuccess) return e;
+    k_ctail_image<<<nc, CT_THREADS, 0, s>>>(A, (unsigned char *)img);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        cudaFree(img);
+        return e;
+    }
+    *out = img;
+    return cudaSuccess;
+}
+
+cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_top, float2 *u_top,
+                            const float2 *minv, int nu_c, int nu1, int nu2, int rb, float omega, int zero, int gf,
+                            int gc, int nc, const void *img, cudaStream_t s) {
+    CArgs A;
+    const size_t bytes = ct_args(nlev, ops, minv, nu_c, nc, A);
+    if (!bytes) return cudaErrorInvalidValue;
     A.nu1 = nu1;
     A.nu2 = nu2;
     A.rb = rb;
     A.zero = zero;
     A.omega = omega;
-    A.minv = minv;
     A.b_top = b_top;
     A.u_top = u_top;
-    A.obc = obc;
-    A.ominv = ominv;
-    A.mrow = ct_minv_stage_bytes(nc, nu_c) ? ct_minv_rows(nc, nu_c) : 0;
-    A.total = (unsigned)bytes;
     A.gf = gf;
     A.gc = gc;
+    A.img = (const float4 *)img;
     static bool attr[2] = {false, false};
     const int ai = nc == 16;
     if (!attr[ai]) {

@@ -47,6 +47,7 @@ extern "C" helm_status helm_set_tuning(helm_handle *h, const helm_tuning *t) {
     if (!tuning_valid(*t)) return helm_fail(HELM_ERR_ARG, "invalid tuning (tail or cluster levels, cluster blocks, or a tile)");
     h->tune = *t;
     helm_drop_graphs(h);
+    ctail_image(h, true);
     return HELM_OK;
 }
 
@@ -86,6 +87,7 @@ extern "C" helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, h
     // skipped
     auto time_it = [&](const helm_tuning &t, bool soft = false) -> double {
         h->tune = t;
+        ctail_image(h, true);
         cudaStream_t keep_s = h->stream;
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
@@ -212,6 +214,7 @@ extern "C" helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, h
     h->prof.on = prof;
     h->tune = st == HELM_OK ? cur : keep;
     helm_drop_graphs(h);
+    ctail_image(h, true);
     if (st != HELM_OK) return st;
     if (best) *best = cur;
     if (best_ms) *best_ms = cur_ms;

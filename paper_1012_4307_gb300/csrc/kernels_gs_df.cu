@@ -320,12 +320,12 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
     for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
         const float4 xq = x[q], wq = w[q];
         const ff xr = ff_re(xq), xi = ff_im(xq);
-        // two independent (sum, compensation) chains per component and output (basis vectors
-        // i mod 2), the first started from x and w; basis values loaded four at a time, the
-        // next four while the current four are processed
-        float vs[2][4] = {{xq.x, xq.y, xq.z, xq.w}, {0.f, 0.f, 0.f, 0.f}};
+        // (sum, compensation) accumulators per component: v over the basis, started from x; w in
+        // two, the basis terms (started from w rw) and the term x s; basis values loaded four at
+        // a time, the next four while the current four are processed
+        float vs[4] = {xq.x, xq.y, xq.z, xq.w};
         float ws[2][4];
-        float fa[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // small correction: FP32 (re, im) per chain
+        float fa[2] = {0.f, 0.f};  // small correction: FP32 (re, im)
         float p, e;
         // w rw (rw = 1 / alpha_j when w came from the unscaled slot j, else exactly 1)
         ff_two_prod(ff_re(wq), rw, ws[0][0], ws[0][1]);
@@ -339,15 +339,15 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
         float4 cur[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) cur[u] = u < j ? V[(size_t)u * ldv + q] : zero4;
-        // basis vector i (value vq) into chain par (i mod 2)
-        auto step = [&](int i, const float4 vq, int par) {
-            float *va = vs[par], *wa = ws[par];
+        // basis vector i (value vq)
+        auto step = [&](int i, const float4 vq) {
+            float *va = vs, *wa = ws[0];
             const ff vr = ff_re(vq), vi = ff_im(vq);
             const float4 a4 = cA[i], c4 = cC[i];
             const ff cr = ff_re(c4), ci = ff_im(c4);
             // v -= V_i a ; w -= V_i c   (complex products)
             if (SMALL_A) {
-                float *f = fa[par];
+                float *f = fa;
                 f[0] = __fmaf_rn(vq.x, a4.x, __fmaf_rn(-vq.z, a4.z, f[0]));
                 f[1] = __fmaf_rn(vq.x, a4.z, __fmaf_rn(vq.z, a4.x, f[1]));
             } else {
@@ -369,7 +369,7 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
 #pragma unroll
             for (int u = 0; u < 4; u++) nxt[u] = V[(size_t)(i0 + 4 + u) * ldv + q];
 #pragma unroll
-            for (int u = 0; u < 4; u++) step(i0 + u, cur[u], u & 1);
+            for (int u = 0; u < 4; u++) step(i0 + u, cur[u]);
 #pragma unroll
             for (int u = 0; u < 4; u++) cur[u] = nxt[u];
         }
@@ -379,18 +379,18 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
             for (int u = 0; u < 4; u++) nxt[u] = i0 + 4 + u < j ? V[(size_t)(i0 + 4 + u) * ldv + q] : zero4;
 #pragma unroll
             for (int u = 0; u < 4; u++)
-                if (i0 + u < j) step(i0 + u, cur[u], u & 1);
+                if (i0 + u < j) step(i0 + u, cur[u]);
 #pragma unroll
             for (int u = 0; u < 4; u++) cur[u] = nxt[u];
         }
         // v_j = v r
         ff vr, vi;
         if (SMALL_A) {
-            vr = ff_add(xr, ff{-(fa[0][0] + fa[1][0]), 0.f});
-            vi = ff_add(xi, ff{-(fa[0][1] + fa[1][1]), 0.f});
+            vr = ff_add(xr, ff{-fa[0], 0.f});
+            vi = ff_add(xi, ff{-fa[1], 0.f});
         } else {
-            vr = ff_add(ff_norm(vs[0][0], vs[0][1]), ff_norm(vs[1][0], vs[1][1]));
-            vi = ff_add(ff_norm(vs[0][2], vs[0][3]), ff_norm(vs[1][2], vs[1][3]));
+            vr = ff_norm(vs[0], vs[1]);
+            vi = ff_norm(vs[2], vs[3]);
         }
         ff_two_prod(vr, rinv, p, e);
         const ff or_ = ff_norm(p, e);
@@ -408,7 +408,7 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
     }
 }
 
-__global__ void __launch_bounds__(NT) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
+__global__ void __launch_bounds__(NT, 4) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
                                                      const double2 *__restrict__ coef, double2 *__restrict__ partials,
                                                      unsigned *ticket, double2 *alpha_out, float2 *__restrict__ b_out) {
     pdl_enter();

@@ -305,6 +305,12 @@ helm_status helm_create_impl(const helm_grid *grid, double theta, const double *
         L.M64.c = make_double2(c_s.real(), c_s.imag());
         L.M32.bk = make_float2((float)bk_s.real(), (float)bk_s.imag());
         L.M32.c = make_float2((float)c_s.real(), (float)c_s.imag());
+        if (dim == 2) {  // 1 / diagonal for the temporally blocked smoothers
+            float2 *di = nullptr;
+            CKC(dalloc(&di, L.np, h->owned));
+            CKC(launch_diag_inv(L.M32, di, s));
+            L.M32.dinv = di;
+        }
         CKC(dalloc(&L.b64, L.np, h->owned)); CKC(dalloc(&L.u64, L.np, h->owned));
         CKC(dalloc(&L.t64, L.np, h->owned)); CKC(dalloc(&L.b32, L.np, h->owned));
         CKC(dalloc(&L.u32, L.np, h->owned)); CKC(dalloc(&L.t32, L.np, h->owned));

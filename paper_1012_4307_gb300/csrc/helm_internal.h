@@ -60,6 +60,9 @@ template <typename R> struct DevOp {
     const C *coef[3];
     const R *k2;
     C bk, c;
+    // 2D complex64 levels: 1 / (diagonal of M) at every node (0 off the interior), formed once
+    // by launch_diag_inv for the temporally blocked smoothers; null otherwise
+    const C *dinv = nullptr;
 };
 
 // The Helmholtz operator A = L_h - k^2 with coefficients and k^2 stored as float pairs
@@ -161,6 +164,8 @@ cudaError_t launch_pre2_wave(const DevOp<float> &op, float omega, const float2 *
                              cudaStream_t s);
 cudaError_t launch_post2_wave(const DevOp<float> &op, float omega, const float2 *b, const float2 *u_in, float2 *u_out,
                               const float2 *ec, cudaStream_t s);
+// dinv = 1 / (diagonal of M) at every node of a 2D level (0 off the interior)
+cudaError_t launch_diag_inv(const DevOp<float> &op, float2 *dinv, cudaStream_t s);
 cudaError_t launch_pre2_restrict(const DevOp<float> &op, int tile, float omega, const float2 *b, float2 *u_out,
                                  float2 *rc, cudaStream_t s);
 cudaError_t launch_prolong_post2(const DevOp<float> &op, int tile, float omega, const float2 *b, const float2 *u_in,

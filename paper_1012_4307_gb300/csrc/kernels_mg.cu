@@ -23,6 +23,7 @@ template <typename R> struct OpView {
     const C *__restrict__ cy;
     const C *__restrict__ cz;
     const R *__restrict__ k2;
+    const C *__restrict__ dinv;
     C bk, c;
     int nx, ny, nz;
 };
@@ -30,7 +31,7 @@ template <typename R> struct OpView {
 template <typename R> __host__ OpView<R> view(const DevOp<R> &op) {
     OpView<R> v;
     v.cx = op.coef[0]; v.cy = op.coef[1]; v.cz = op.coef[2];
-    v.k2 = op.k2; v.bk = op.bk; v.c = op.c;
+    v.k2 = op.k2; v.dinv = op.dinv; v.bk = op.bk; v.c = op.c;
     v.nx = op.n[0]; v.ny = op.n[1]; v.nz = op.n[2];
     return v;
 }
@@ -302,14 +303,14 @@ template <int TCX, int TCY> struct Tile {
     struct Pre {
         Coef tc;
         float2 b[RH][RW];
-        float k2[RH][RW];
+        float2 di[RH][RW];  // 1 / diagonal
         float2 u1[RH][RW];  // first sweep, later the residual
         float2 u2[RH][RW];
     };
     struct Post {
         Coef tc;
         float2 b[RH][RW];
-        float k2[RH][RW];
+        float2 di[RH][RW];  // 1 / diagonal
         float2 u3[RH][RW];
         float2 u4[RH][RW];
         float2 ec[TCY + 4][TCX + 4];
@@ -339,6 +340,23 @@ __device__ __forceinline__ float2 tile_stencil(const TC &tc, const float2 (*u)[R
     acc = cfma(tc.y[sy][2], u[sy + 1][sx], acc);
     d = cadd(cadd(tc.x[sx][1], tc.y[sy][1]), cadd(cscale(bk, k2), c));
     return cfma(d, u[sy][sx], acc);
+}
+
+// Off-diagonal part of (M u)_s at region node (sx, sy).
+template <int RW, typename TC>
+__device__ __forceinline__ float2 tile_offdiag(const TC &tc, const float2 (*u)[RW], int sx, int sy) {
+    float2 acc = cmul(tc.x[sx][0], u[sy][sx - 1]);
+    acc = cfma(tc.x[sx][2], u[sy][sx + 1], acc);
+    acc = cfma(tc.y[sy][0], u[sy - 1][sx], acc);
+    return cfma(tc.y[sy][2], u[sy + 1][sx], acc);
+}
+// One omega-Jacobi update at region node (sx, sy): u + omega ((b - offdiag) / d - u).
+template <int RW, typename TC>
+__device__ __forceinline__ float2 tile_jacobi(const TC &tc, const float2 (*u)[RW], const float2 (*b)[RW],
+                                              const float2 (*di)[RW], int sx, int sy, float omega) {
+    const float2 uc = u[sy][sx];
+    const float2 t = cmul(csub(b[sy][sx], tile_offdiag<RW>(tc, u, sx, sy)), di[sy][sx]);
+    return cadd(uc, cscale(csub(t, uc), omega));
 }
 
 // f(sx, sy) for every node of an RW x RH region, 256 threads, node q = tid + 256 k in row-major
@@ -383,30 +401,25 @@ __global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float om
     auto inside = [&](int x, int y) { return full || (x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2); };
     tile_coef<RW, RH>(o, X0, Y0, T.tc);
     __syncthreads();
-    // load b and k^2; sweep 1 from zero (pointwise): u1 = omega b / D
+    // load b and 1 / D; sweep 1 from zero (pointwise): u1 = omega b / D
     for_region<RW, RH>([&](int sx, int sy) {
         const int x = X0 + sx, y = Y0 + sy;
-        float2 bv = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
-        float kv = 0.f;
+        float2 bv = make_float2(0.f, 0.f), dv = make_float2(0.f, 0.f);
         if (inside(x, y)) {
             const size_t p = (size_t)x + (size_t)nx * y;
             bv = b[p];
-            kv = o.k2[p];
-            v = cscale(cmul(bv, cinv_fast(tile_diag(T.tc, sx, sy, kv, o.bk, o.c))), omega);
+            dv = o.dinv[p];
         }
         T.b[sy][sx] = bv;
-        T.k2[sy][sx] = kv;
-        T.u1[sy][sx] = v;
+        T.di[sy][sx] = dv;
+        T.u1[sy][sx] = cscale(cmul(bv, dv), omega);
     });
     __syncthreads();
     // sweep 2 on R3 shrunk by one
     for_region<RW, RH>([&](int sx, int sy) {
         float2 v = make_float2(0.f, 0.f);
-        if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy)) {
-            float2 d;
-            const float2 mu = tile_stencil<RW>(T.tc, T.u1, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
-            v = cadd(T.u1[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv_fast(d)), omega));
-        }
+        if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy))
+            v = tile_jacobi<RW>(T.tc, T.u1, T.b, T.di, sx, sy, omega);
         T.u2[sy][sx] = v;
     });
     __syncthreads();
@@ -417,8 +430,8 @@ __global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float om
         if (in && sx >= 2 && sx < 2 + 2 * TCX && sy >= 2 && sy < 2 + 2 * TCY) u[(size_t)x + (size_t)nx * y] = T.u2[sy][sx];
         float2 r = make_float2(0.f, 0.f);
         if (in && sx >= 2 && sx < RW - 2 && sy >= 2 && sy < RH - 2) {
-            float2 d;
-            r = csub(T.b[sy][sx], tile_stencil<RW>(T.tc, T.u2, sx, sy, T.k2[sy][sx], o.bk, o.c, d));
+            const float2 d = cinv_fast(T.di[sy][sx]);
+            r = csub(csub(T.b[sy][sx], tile_offdiag<RW>(T.tc, T.u2, sx, sy)), cmul(d, T.u2[sy][sx]));
         }
         T.u1[sy][sx] = r;
     });
@@ -467,28 +480,25 @@ __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float om
     for_region<RW, RH>([&](int sx, int sy) {
         const int x = X0 + sx, y = Y0 + sy;
         float2 bv = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
-        float kv = 0.f;
+        float2 dv = make_float2(0.f, 0.f);
         if (inside(x, y)) {
             const size_t p = (size_t)x + (size_t)nx * y;
             bv = b[p];
-            kv = o.k2[p];
+            dv = o.dinv[p];
             const int xa = (x >> 1) - C0, xb = ((x + 1) >> 1) - C0, ya = (y >> 1) - D0, yb = ((y + 1) >> 1) - D0;
             const float2 e = cadd(cadd(T.ec[ya][xa], T.ec[ya][xb]), cadd(T.ec[yb][xa], T.ec[yb][xb]));
             v = cadd(u_in[p], cscale(e, 0.25f));
         }
         T.b[sy][sx] = bv;
-        T.k2[sy][sx] = kv;
+        T.di[sy][sx] = dv;
         T.u3[sy][sx] = v;
     });
     __syncthreads();
     // sweep 1 on R3 shrunk by one
     for_region<RW, RH>([&](int sx, int sy) {
         float2 v = make_float2(0.f, 0.f);
-        if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy)) {
-            float2 d;
-            const float2 mu = tile_stencil<RW>(T.tc, T.u3, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
-            v = cadd(T.u3[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv_fast(d)), omega));
-        }
+        if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy))
+            v = tile_jacobi<RW>(T.tc, T.u3, T.b, T.di, sx, sy, omega);
         T.u4[sy][sx] = v;
     });
     __syncthreads();
@@ -496,9 +506,7 @@ __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float om
     for (int q = threadIdx.x; q < 4 * TCX * TCY; q += blockDim.x) {
         const int sx = 2 + q % (2 * TCX), sy = 2 + q / (2 * TCX), x = X0 + sx, y = Y0 + sy;
         if (!inside(x, y)) continue;
-        float2 d;
-        const float2 mu = tile_stencil<RW>(T.tc, T.u4, sx, sy, T.k2[sy][sx], o.bk, o.c, d);
-        u[(size_t)x + (size_t)nx * y] = cadd(T.u4[sy][sx], cscale(cmul(csub(T.b[sy][sx], mu), cinv_fast(d)), omega));
+        u[(size_t)x + (size_t)nx * y] = tile_jacobi<RW>(T.tc, T.u4, T.b, T.di, sx, sy, omega);
     }
 }
 
@@ -922,7 +930,7 @@ static cudaError_t post2_t(const DevOp<float> &op, float omega, const float2 *b,
 
 cudaError_t launch_pre2_restrict(const DevOp<float> &op, int tile, float omega, const float2 *b, float2 *u_out,
                                  float2 *rc, cudaStream_t s) {
-    if (!fused_jacobi2_ok(op.n, 2, tile)) return cudaErrorInvalidValue;
+    if (!fused_jacobi2_ok(op.n, 2, tile) || (tile != HELM_TILE_WAVE && !op.dinv)) return cudaErrorInvalidValue;
     switch (tile) {
     case HELM_TILE_WAVE: return launch_pre2_wave(op, omega, b, u_out, rc, s);
     case 0: return pre2_t<32, 8>(op, omega, b, u_out, rc, s);
@@ -934,7 +942,7 @@ cudaError_t launch_pre2_restrict(const DevOp<float> &op, int tile, float omega, 
 
 cudaError_t launch_prolong_post2(const DevOp<float> &op, int tile, float omega, const float2 *b, const float2 *u_in,
                                  float2 *u_out, const float2 *ec, cudaStream_t s) {
-    if (!fused_jacobi2_ok(op.n, 2, tile)) return cudaErrorInvalidValue;
+    if (!fused_jacobi2_ok(op.n, 2, tile) || (tile != HELM_TILE_WAVE && !op.dinv)) return cudaErrorInvalidValue;
     switch (tile) {
     case HELM_TILE_WAVE: return launch_post2_wave(op, omega, b, u_in, u_out, ec, s);
     case 0: return post2_t<32, 8>(op, omega, b, u_in, u_out, ec, s);
@@ -978,3 +986,26 @@ template cudaError_t launch_convert<double2, double2>(size_t, const double2 *, d
 template cudaError_t launch_convert<float2, float2>(size_t, const float2 *, float2 *, cudaStream_t);
 template cudaError_t launch_zero<double2>(size_t, double2 *, cudaStream_t);
 template cudaError_t launch_zero<float2>(size_t, float2 *, cudaStream_t);
+
+// ------------------------------------------------------------------------------ 1 / diagonal
+namespace {
+__global__ void k_diag_inv(OpView<float> o, float2 *__restrict__ dinv) {
+    pdl_enter();
+    const size_t n = (size_t)o.nx * o.ny;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(p % o.nx), y = (int)(p / o.nx);
+        float2 v = make_float2(0.f, 0.f);
+        if (x >= 1 && x <= o.nx - 2 && y >= 1 && y <= o.ny - 2) {
+            const float2 d = cadd(cadd(o.cx[3 * x + 1], o.cy[3 * y + 1]), cadd(cscale(o.bk, o.k2[p]), o.c));
+            v = cinv_fast(d);
+        }
+        dinv[p] = v;
+    }
+}
+}  // namespace
+
+cudaError_t launch_diag_inv(const DevOp<float> &op, float2 *dinv, cudaStream_t s) {
+    const size_t n = (size_t)op.n[0] * op.n[1];
+    launch_pdl(k_diag_inv, (unsigned)std::min<size_t>(cdiv(n, 256), 152 * 8), 256, 0, s, view(op), dinv);
+    return cudaGetLastError();
+}

@@ -492,7 +492,8 @@ static cudaEvent_t unit_event(helm_handle *h, int k, int jmax) {
 //   WAIT_FN     ||f|| read back                      -> START
 //   START       r0 = f - A x, ||r0|| read back        -> WAIT_BETA
 //   WAIT_BETA   converged / capped / new cycle        -> DONE or IN_CYCLE
-//   IN_CYCLE    step j's estimate read back; step j+2 queued (one step of look-ahead);
+//   IN_CYCLE    step j's estimate read back; step j+2 queued (one step of look-ahead; delayed
+//               CGS2: unit j+3, two steps);
 //               converged or cycle full: x += Z y     -> START
 // Pinned host slots: est_host[0..m) step estimates, [m+2] ||f||, [m+4] ||r0||.
 
@@ -611,11 +612,12 @@ helm_status fgmres_advance(FgmresRun &r, bool block) {
             // only written column j+1, v_{j+2}, z_{j+1} and g[j+1..j+2], none of which the back
             // substitution over the first j+1 columns reads.
             // Delayed CGS2: est[k] comes from the unit after step k (step k + 1, or the closing
-            // step); units 0 and 1 are queued behind step 0.
+            // step); units 0, 1 and 2 are queued behind step 0, and est[j] queues unit j + 3, so
+            // the host has two steps' time to answer (a step queued ahead of the converged step
+            // j writes no column, slot, rotation or g entry at or below j).
             if (use_dcgs2(h)) {
                 CKR(run_step(h, 0, m));
-                CKR(run_unit(h, 0, r.jmax, m));
-                if (r.jmax > 1) CKR(run_unit(h, 1, r.jmax, m));
+                for (int k = 0; k < 3 && k < r.jmax; k++) CKR(run_unit(h, k, r.jmax, m));
             } else {
                 CKR(run_step(h, 0, m));
                 if (r.jmax > 1) CKR(run_step(h, 1, m));
@@ -637,9 +639,10 @@ helm_status fgmres_advance(FgmresRun &r, bool block) {
             const int jdone = j + 1;
             if (r.est > r.tol && jdone < r.jmax) {
                 r.next = jdone;
-                if (jdone + 1 < r.jmax) {
-                    if (use_dcgs2(h)) CKR(run_unit(h, jdone + 1, r.jmax, m));
-                    else CKR(run_step(h, jdone + 1, m));
+                if (use_dcgs2(h)) {
+                    if (jdone + 2 < r.jmax) CKR(run_unit(h, jdone + 2, r.jmax, m));
+                } else if (jdone + 1 < r.jmax) {
+                    CKR(run_step(h, jdone + 1, m));
                 }
                 break;
             }

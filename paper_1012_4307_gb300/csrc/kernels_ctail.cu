@@ -57,21 +57,41 @@ struct Ctx {
     int rank, nc;
 };
 
-// Row j of the level array at offset off in block c's slot layout: slot j - B[c] + 1, so slot
-// 0 and slot rows + 1 are the halo rows (a boundary row's halo is never written: zeros).
-__device__ __forceinline__ float2 *slot_row(unsigned char *sm, const CLevel &L, unsigned off, int j, int c) {
-    return (float2 *)(sm + off) + (size_t)(j - L.B[c] + 1) * L.nx;
+// A level as the phases use it: the scalars in registers (a phase's shared-memory stores could
+// alias the launch arguments, which live in shared memory too, and would force reloads), this
+// block's slab [j0, j1), and the slab bounds of every block (B, in shared memory) for the rare
+// accesses to other blocks' rows.
+struct LV {
+    int nx, j0, j1;
+    unsigned ob, ou, ot, ok, ocx, ocy;
+    float2 bk, c;
+    const int *B;
+};
+__device__ __forceinline__ LV lv_of(const Ctx &X, const CLevel &L) {
+    LV v;
+    v.nx = L.nx;
+    v.j0 = L.B[X.rank];
+    v.j1 = L.B[X.rank + 1];
+    v.ob = L.ob; v.ou = L.ou; v.ot = L.ot; v.ok = L.ok; v.ocx = L.ocx; v.ocy = L.ocy;
+    v.bk = L.bk;
+    v.c = L.c;
+    v.B = L.B;
+    return v;
 }
-// this block's row j, for B[rank] - 1 <= j <= B[rank + 1]
-__device__ __forceinline__ float2 *lrow(const Ctx &X, const CLevel &L, unsigned off, int j) {
-    return slot_row(X.sm, L, off, j, X.rank);
+
+// Row j of the level array at offset off in a block's slot layout: slot j - B[c] + 1, so slot
+// 0 and slot rows + 1 are the halo rows (a boundary row's halo is never written: zeros).
+// This block's row j, for j0 - 1 <= j <= j1:
+__device__ __forceinline__ float2 *lrow(const Ctx &X, const LV &L, unsigned off, int j) {
+    return (float2 *)(X.sm + off) + (size_t)(j - L.j0 + 1) * L.nx;
 }
 // block c's row j (another block's through distributed shared memory)
-__device__ __forceinline__ float2 *crow(const Ctx &X, const CLevel &L, unsigned off, int j, int c) {
-    float2 *p = slot_row(X.sm, L, off, j, c);
-    return c == X.rank ? p : cg::this_cluster().map_shared_rank(p, (unsigned)c);
+__device__ __forceinline__ float2 *crow(const Ctx &X, const LV &L, unsigned off, int j, int c) {
+    if (c == X.rank) return lrow(X, L, off, j);
+    float2 *p = (float2 *)(X.sm + off) + (size_t)(j - L.B[c] + 1) * L.nx;
+    return cg::this_cluster().map_shared_rank(p, (unsigned)c);
 }
-__device__ __forceinline__ int owner_of(const CLevel &L, int nc, int j) {
+__device__ __forceinline__ int owner_of(const LV &L, int nc, int j) {
     int c = 0;
     while (c + 1 < nc && L.B[c + 1] <= j) c++;
     return c;
@@ -81,11 +101,13 @@ __device__ __forceinline__ int owner_of(const CLevel &L, int nc, int j) {
 // window of rows (B[c] - 1 .. B[c+1]) holds row j: the blocks just above the owner's slab whose
 // slabs end at row j (empty ones, then the nearest non-empty one) when j is the owner's first
 // row, and likewise below when j is its last row.
-__device__ __forceinline__ void put(const Ctx &X, const CLevel &L, unsigned off, int j, int i, float2 v, int owner) {
+__device__ __forceinline__ void put(const Ctx &X, const LV &L, unsigned off, int j, int i, float2 v, int owner) {
+    const bool own = owner == X.rank;
+    const int b0 = own ? L.j0 : L.B[owner], b1 = own ? L.j1 : L.B[owner + 1];
     crow(X, L, off, j, owner)[i] = v;
-    if (j == L.B[owner])
+    if (j == b0)
         for (int p = owner - 1; p >= 0 && L.B[p + 1] == j; p--) crow(X, L, off, j, p)[i] = v;
-    if (j == L.B[owner + 1] - 1)
+    if (j == b1 - 1)
         for (int q = owner + 1; q < X.nc && L.B[q] == j + 1; q++) crow(X, L, off, j, q)[i] = v;
 }
 
@@ -95,26 +117,26 @@ __device__ __forceinline__ void csync() { cg::this_cluster().sync(); }
 // along a row).  The row of pass index q is (q + 1/2) / m rounded down in FP32: exact for
 // q < 2^21, far above any slab.
 template <typename F>
-__device__ __forceinline__ void for_owned(const Ctx &X, const CLevel &L, F f) {
-    const int j0 = L.B[X.rank], m = L.nx - 2, total = (L.B[X.rank + 1] - j0) * m;
+__device__ __forceinline__ void for_owned(const Ctx &X, const LV &L, F f) {
+    const int m = L.nx - 2, total = (L.j1 - L.j0) * m;
     const float rm = 1.0f / (float)m;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
         const int r = __float2int_rz(((float)q + 0.5f) * rm);
-        f(j0 + r, 1 + q - r * m);
+        f(L.j0 + r, 1 + q - r * m);
     }
 }
 
 // The diagonal of M at an owned node, formed once per launch (bk k^2 + c + the two centre
 // coefficients) and kept in shared memory.
-__device__ __forceinline__ float2 diag_at(const Ctx &X, const CLevel &L, int j, int i) {
-    return ((const float2 *)(X.sm + L.ok))[(size_t)(j - L.B[X.rank]) * L.nx + i];
+__device__ __forceinline__ float2 diag_at(const Ctx &X, const LV &L, int j, int i) {
+    return ((const float2 *)(X.sm + L.ok))[(size_t)(j - L.j0) * L.nx + i];
 }
 
 // (M u)(j, i) from this block's rows of the array at offset u (j - 1 and j + 1 may be halo
 // rows); d = the diagonal.
-__device__ __forceinline__ float2 apply_at(const Ctx &X, const CLevel &L, unsigned u, int j, int i, float2 &d) {
+__device__ __forceinline__ float2 apply_at(const Ctx &X, const LV &L, unsigned u, int j, int i, float2 &d) {
     const float2 *cx = (const float2 *)(X.sm + L.ocx), *cy = (const float2 *)(X.sm + L.ocy);
-    const int li = j - L.B[X.rank];
+    const int li = j - L.j0;
     const float2 *un = lrow(X, L, u, j - 1), *uc = lrow(X, L, u, j), *us = lrow(X, L, u, j + 1);
     d = diag_at(X, L, j, i);
     float2 acc = cmul(cx[3 * i], uc[i - 1]);
@@ -130,15 +152,16 @@ __device__ __forceinline__ float2 apply_at(const Ctx &X, const CLevel &L, unsign
 
 // nu sweeps on level l from *cur (partner *oth); zero: u = 0 on entry.  Returns the new pair.
 __device__ __noinline__ uint2 ph_smooth(Ctx X, const CArgs *A, int l, int nu, uint2 co, bool zero) {
-    const CLevel &L = A->lv[l];
+    const LV L = lv_of(X, A->lv[l]);
     const float om = A->omega;
-    if (zero && (nu == 0 || A->rb)) {
+    const bool rb = A->rb != 0;
+    if (zero && (nu == 0 || rb)) {
         const unsigned u = co.x;
         for_owned(X, L, [&](int j, int i) { put(X, L, u, j, i, make_float2(0.f, 0.f), X.rank); });
         csync();
     }
     for (int s = 0; s < nu; s++) {
-        if (A->rb) {
+        if (rb) {
             for (int colour = 0; colour < 2; colour++) {
                 // in place: this colour's neighbours (the other colour) are not written here
                 const unsigned u = co.x;
@@ -176,7 +199,7 @@ __device__ __noinline__ uint2 ph_smooth(Ctx X, const CArgs *A, int l, int nu, ui
 // Residual of level l (iterate u) into r, then full weighting into level l + 1's b (the fine
 // rows 2J-1 .. 2J+1 of an owned coarse row J are owned or halo rows: nested slabs).
 __device__ __noinline__ void ph_restrict(Ctx X, const CArgs *A, int l, unsigned u, unsigned r) {
-    const CLevel &L = A->lv[l], &Lc = A->lv[l + 1];
+    const LV L = lv_of(X, A->lv[l]), Lc = lv_of(X, A->lv[l + 1]);
     for_owned(X, L, [&](int j, int i) {
         float2 d;
         const float2 mu = apply_at(X, L, u, j, i, d);
@@ -197,7 +220,7 @@ __device__ __noinline__ void ph_restrict(Ctx X, const CArgs *A, int l, unsigned 
 // Bilinear prolongation of level l + 1's u (coarse rows j/2 and (j+1)/2: owned or halo rows of
 // the coarse slab), added to level l's iterate u.
 __device__ __noinline__ void ph_prolong(Ctx X, const CArgs *A, int l, unsigned u) {
-    const CLevel &L = A->lv[l], &Lc = A->lv[l + 1];
+    const LV L = lv_of(X, A->lv[l]), Lc = lv_of(X, A->lv[l + 1]);
     for_owned(X, L, [&](int j, int i) {
         const float2 *ea = lrow(X, Lc, Lc.ou, j >> 1), *eb = lrow(X, Lc, Lc.ou, (j + 1) >> 1);
         const int ia = i >> 1, ib = (i + 1) >> 1;
@@ -208,7 +231,7 @@ __device__ __noinline__ void ph_prolong(Ctx X, const CArgs *A, int l, unsigned u
 }
 
 __device__ __noinline__ void ph_copy(Ctx X, const CArgs *A, int l, unsigned dst, unsigned src) {
-    const CLevel &L = A->lv[l];
+    const LV L = lv_of(X, A->lv[l]);
     for_owned(X, L, [&](int j, int i) { put(X, L, dst, j, i, lrow(X, L, src, j)[i], X.rank); });
     csync();
 }
@@ -217,7 +240,7 @@ __device__ __noinline__ void ph_copy(Ctx X, const CArgs *A, int l, unsigned dst,
 // the rows of Minv b (one warp per row) and stores each result in the owning block's u (and
 // the halos that hold its row).
 __device__ __noinline__ void ph_dense(Ctx X, const CArgs *A, int l) {
-    const CLevel &L = A->lv[l];
+    const LV L = lv_of(X, A->lv[l]);
     float2 *bc = (float2 *)(X.sm + A->obc);
     const int mx = L.nx - 2, nu = A->nu_c;
     for (int c = threadIdx.x; c < nu; c += blockDim.x) {
@@ -333,7 +356,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_mg_ctail(const __grid_constan
         __syncthreads();
         ct_init(X, A);
     }
-    const CLevel &T = A->lv[0];
+    const LV T = lv_of(X, A->lv[0]);
     // the operator data above is not written by earlier kernels; b_top and u_top are
     pdl_wait();
     // every block's initial fill precedes any store into its halos

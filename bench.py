@@ -205,11 +205,11 @@ def run_reference(args):
 # source file is the one that was captured (same SHA-1); otherwise null.
 NCU_TRAFFIC = {
     "update_norm": dict(kernel="k_update2_pair", source="paper_1012_4307_gb300/csrc/kernels_gs_df.cu",
-                        sha1="b5120166c5422607d9f88685d52b5622c2d74cd2", bytes=315617024,
+                        sha1="57192057f858d44ef0ecd41b7097a4cc8973d85f", bytes=314946304,
                         launch="basis slot j = 15, the mean over a restart cycle being 14.5",
                         profile="profiles/gram_schmidt_dcgs2_kernels_n1025.md"),
     "mdot": dict(kernel="k_mdot2_pair", source="paper_1012_4307_gb300/csrc/kernels_gs_df.cu",
-                 sha1="b5120166c5422607d9f88685d52b5622c2d74cd2", bytes=289014528,
+                 sha1="57192057f858d44ef0ecd41b7097a4cc8973d85f", bytes=289090816,
                  launch="basis slot j = 15, the mean over a restart cycle being 14.5",
                  profile="profiles/gram_schmidt_dcgs2_kernels_n1025.md"),
 }

@@ -73,11 +73,12 @@ def test_paper_model_problem(helm, table):
 
 def test_preconditioner_solution_as_starting_guess(helm):
     """Experiment 1's remark (Section 6): with the QD preconditioner, the paper started
-    Bi-CGSTAB from the preconditioner's own solution M x0 = f, computed by stand-alone multigrid
-    to 1e-2, and saw 50 fewer iterations.  Here both starts must converge to the tolerance; the
-    iteration counts are printed.  Measured on GB300: 167 from zero, 249 from the preconditioner
-    solution (not reproduced; the paper does not give its shadow residual, which Bi-CGSTAB takes
-    from the starting residual)."""
+    Bi-CGSTAB from the preconditioner's solution, computed by stand-alone multigrid to 1e-2, and
+    saw 50 fewer iterations.  QD in its table form is (1-i) I + Z / |Re lambda0|, so its solution
+    approximates |Re lambda0| Z^-1 f: started as it is, Bi-CGSTAB needs more iterations than from
+    zero (the start's residual is about 2e4 ||f||); divided by |Re lambda0| it is a start with a
+    residual of about 0.3 ||f||.  All three solves must converge; the counts are printed (the
+    oracle's: 172 from zero, 247 and 165 from the two starts)."""
     spec = GOLDEN["T1"]
     c = spec["qd"]
     P = BUILDERS[spec["problem"]](**spec["args"])
@@ -86,9 +87,10 @@ def test_preconditioner_solution_as_starting_guess(helm):
                    gamma=(1, c["gamma_c"]), re_lambda0=c["re_lambda0"])
     _, st0 = helm.krylov_solve(h, f, tol=P.tol, method="bicgstab", maxit=5000)
     x0, cycles, _ = helm.helm_mg_conv(h, f, tol=1e-2, maxcyc=100)
-    _, st1 = helm.krylov_solve(h, f, x0, tol=P.tol, method="bicgstab", maxit=5000)
+    _, st1 = helm.krylov_solve(h, f, x0.clone(), tol=P.tol, method="bicgstab", maxit=5000)
+    _, st2 = helm.krylov_solve(h, f, x0 / abs(c["re_lambda0"]), tol=P.tol, method="bicgstab", maxit=5000)
     h.close()
-    print("\nfrom zero: %d iterations; from the 1e-2 preconditioner solution (%d cycles): %d iterations"
-          % (st0.iterations, cycles, st1.iterations))
-    assert st0.status == helm.HELM_OK and st1.status == helm.HELM_OK
-    assert st0.rel_res <= P.tol and st1.rel_res <= P.tol
+    print("\nfrom zero: %d iterations; from the 1e-2 preconditioner solution (%d cycles): %d; "
+          "the same divided by |Re lambda0|: %d" % (st0.iterations, cycles, st1.iterations, st2.iterations))
+    for st in (st0, st1, st2):
+        assert st.status == helm.HELM_OK and st.rel_res <= P.tol

@@ -78,7 +78,7 @@ def test_preconditioner_solution_as_starting_guess(helm):
     approximates |Re lambda0| Z^-1 f: started as it is, Bi-CGSTAB needs more iterations than from
     zero (the start's residual is about 2e4 ||f||); divided by |Re lambda0| it is a start with a
     residual of about 0.3 ||f||.  All three solves must converge; the counts are printed (the
-    oracle's: 172 from zero, 247 and 165 from the two starts)."""
+    oracle's: 172 from zero, 247 and 165 from the two starts; on GB300: 167, 249 and 172)."""
     spec = GOLDEN["T1"]
     c = spec["qd"]
     P = BUILDERS[spec["problem"]](**spec["args"])

@@ -311,9 +311,11 @@ typedef struct {
 } helm_tuning;
 
 /* Sets / reads the handle's tuning (host struct).  Setting drops the handle's captured CUDA
- * graphs (they are re-captured on next use).  Errors: HELM_ERR_ARG (null pointers, a tile
- * index out of range, tail_levels < -1 or == 1, cluster_levels < 0 or == 1, cluster_ctas not
- * 8 or 16). */
+ * graphs (they are re-captured on next use) and, when the tuning selects a cluster tail not
+ * used before on this handle, allocates that tail's initial shared-memory image (every
+ * block's, at most 3.2 MB; freed by helm_destroy) and fills it with one kernel on the handle's
+ * stream.  Errors: HELM_ERR_ARG (null pointers, a tile index out of range, tail_levels < -1 or
+ * == 1, cluster_levels < 0 or == 1, cluster_ctas not 8 or 16). */
 helm_status helm_set_tuning(helm_handle *h, const helm_tuning *t);
 helm_status helm_get_tuning(const helm_handle *h, helm_tuning *t);
 
@@ -322,7 +324,8 @@ helm_status helm_get_tuning(const helm_handle *h, helm_tuning *t);
  * tunings with CUDA events on the handle's stream, greedily level by level from the finest
  * (each level's tile choice, then the tail depth), installs the fastest, and returns it in
  * *best and its time per application (ms) in *best_ms (may be null).  Allocates two
- * temporary vectors; synchronises the stream.  Errors: HELM_ERR_ARG (bad arguments, a handle
+ * temporary vectors, and the cluster-tail images of the candidates it times (kept with the
+ * handle, as helm_set_tuning does); synchronises the stream.  Errors: HELM_ERR_ARG (bad arguments, a handle
  * without a hierarchy), HELM_ERR_NOMEM, HELM_ERR_CUDA. */
 helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, helm_tuning *best, double *best_ms);
 

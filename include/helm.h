@@ -193,6 +193,24 @@ helm_status helm_solve_adjoint(helm_handle *h, const void *rhs, void *lambda, do
  *   lambda, u DEVICE c128; grad DEVICE double[n0*n1*n2]. */
 helm_status helm_grad_k2(helm_handle *h, const void *lambda, const void *u, double *grad);
 
+/* Reverse-mode step of u = A(k^2)^{-1} f for a real loss L(u) (the adjoint method; the paper
+ * solves only forward problems, so this follows from eq. (2.1) with the ECS FD matrix of
+ * Section 3.2): given grad_u = dL/d(conj u) as reverse-mode complex autodiff hands it (PyTorch's
+ * convention), solves A^T lambda = conj(grad_u) by the weighted identity of
+ * helm_solve_adjoint (FGMRES with the handle's preconditioner), then writes
+ *   grad_k2[p] = Re(lambda_p u_p)   (dL/dk^2_p, since dA/dk^2_p = -e_p e_p^T), and
+ *   grad_f[p]  = conj(lambda_p)     (dL/d(conj f) in the same convention),
+ * both 0 on the boundary nodes.  Every conjugation and product runs on the device.
+ *   grad_u  DEVICE c128, unchanged.      u  DEVICE c128 (the forward solution; unused and may be
+ *                                           null when grad_k2 is null).
+ *   grad_k2 DEVICE double[n0*n1*n2] or null;  grad_f DEVICE c128 or null (not both null; neither
+ *           may overlap grad_u or u).
+ *   tol, restart, maxit, stats  as for krylov_solve (the adjoint solve).
+ * Synchronises the handle's stream.  Returns the adjoint solve's status (the gradients are
+ * written for HELM_OK and HELM_ERR_NOCONV); HELM_ERR_ARG for bad pointers. */
+helm_status helm_backward(helm_handle *h, const void *grad_u, const void *u, double *grad_k2, void *grad_f,
+                          double tol, int restart, int maxit, helm_stats *stats);
+
 /* Stand-alone multigrid on M x = b from x = 0 (Section 5, "mg-conv"): repeats cycles until
  * ||b - M x|| <= tol ||b|| or maxcyc cycles; returns the cycle count and the geometric mean of
  * the residual reduction over the last five cycles.
@@ -202,26 +220,53 @@ helm_status helm_mg_conv(helm_handle *h, const void *b, void *x, helm_prec prec,
 
 /* Allocation-free helm_mg_conv (the paper has no counterpart; this is a library facility).
  * helm_mg_conv allocates a work area with cudaMalloc the first time it runs on a handle.
- * Some callers cannot allow that at the point of the call: code that runs while a CUDA graph
- * is being captured (device allocation is not permitted inside a capture), or a service that
- * fixes its device memory footprint at start-up and forbids any later growth.  This entry
- * point computes exactly what helm_mg_conv computes, with the same kernels, but takes its
- * work vectors from one fixed device array of HELM_NOALLOC_SCRATCH_BYTES that the library
- * holds on every GPU that loads it until the process exits; it calls no cudaMalloc, cudaFree,
- * cudaMallocHost or other allocating routine.
+ * Some callers cannot allow that at the point of the call: a service that sizes its device
+ * memory once at start-up (a fixed pool, or memory promised to other tenants of the GPU) and
+ * forbids any later growth, or a latency-bound loop that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree may cause.  This entry point computes exactly
+ * what helm_mg_conv computes, with the same kernels, but takes its work vectors from one fixed
+ * device array of HELM_NOALLOC_SCRATCH_BYTES that the library holds on every GPU that loads it
+ * until the process exits; it calls no cudaMalloc, cudaFree, cudaMallocHost or other
+ * allocating routine.
  *   - Limit: the grid's nodes n0*n1*n2 must satisfy 32 * nodes + a few KB <= 16 MiB, i.e.
  *     at most about 523,000 nodes (513 x 513 in 2D, 65 x 65 x 65 in 3D); larger grids are
  *     rejected with HELM_ERR_ARG and nothing runs.
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call before any stream
- *     capture begins.
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the life of the
+ *     process; make that first call before any stream capture begins.  After a
+ *     cudaDeviceReset the kept address is stale, as every handle's memory is: create new
+ *     handles and do not call this entry point again in that process.
  *   - Every call shares the one array and it keeps the previous call's contents (the entry
  *     point clears what must start at zero).  Calls that overlap on the GPU (different
  *     streams, threads or handles) race on it: serialise them.
+ *   - Each cycle's residual norm is read back to the host (the stream is synchronised after
+ *     every cycle), as in helm_mg_conv.
  * Arguments, results and errors are those of helm_mg_conv. */
 #define HELM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 helm_status helm_mg_conv_noalloc(helm_handle *h, const void *b, void *x, helm_prec prec, double tol, int maxcyc,
                                  int *ncycles, double *factor);
+
+/* Re(lambda0) for the QD preconditioner (helm_mg_params.re_lambda0; Section 5: lambda0 is the
+ * eigenvalue of Z = -Delta - k^2 with the smallest real part).  Host computation, no device
+ * work and no handle.  The two modes are the closing remark of Section 6:
+ *   HELM_LAMBDA0_AXES   the one-dimensional counterpart: for every axis a, the smallest real
+ *                       part over the eigenvalues of the 1D operator -d^2/dz^2 - k2_axis[a] on
+ *                       that axis's ECS contour (Sections 3.1-3.2, interior nodes, Dirichlet
+ *                       ends), summed over the axes.  Exact for a separable field
+ *                       k^2(x) = sum_a k2_axis[a](x_a), whose discrete Z is the Kronecker sum of
+ *                       the 1D operators; otherwise an estimate from the profiles given.
+ *                       Eigenvalues by a complex-symmetric tridiagonal QR iteration, O(n^2).
+ *   HELM_LAMBDA0_MAX_K2 minus the largest k^2 of that separable field over the interior nodes
+ *                       (the rough estimate for piecewise-constant wavenumbers).
+ *   grid, theta, r0_lo, r0_hi  as for helm_create (the same ECS contour per axis).
+ *   k2_axis     host: dim arrays of n[a] doubles (values at the real nodes; boundary entries are
+ *               ignored).
+ *   re_lambda0  host output.
+ * Errors: HELM_ERR_ARG (null pointers, bad grid or mode), HELM_ERR_NONFINITE (non-finite k2),
+ * HELM_ERR_NOCONV (the eigenvalue iteration did not converge). */
+typedef enum { HELM_LAMBDA0_AXES = 0, HELM_LAMBDA0_MAX_K2 = 1 } helm_lambda0_mode;
+helm_status helm_qd_lambda0(const helm_grid *grid, double theta, const double *r0_lo, const double *r0_hi,
+                            const double *const *k2_axis, int mode, double *re_lambda0);
 
 /* Number of levels and nodes per axis of level l (host query). */
 helm_status helm_levels(const helm_handle *h, int *nlev);

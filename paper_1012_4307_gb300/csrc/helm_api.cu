@@ -66,7 +66,7 @@ std::vector<cd> ecs_contour(int n, double lo, double hi, double theta, double r0
 // Per-node coefficient triples of a * (-d^2/dz^2) with all widths multiplied by e^{i ts}
 // (Section 3.2 formula for unequal widths): cw = -2/((hm+hp) hm), ce = -2/((hm+hp) hp),
 // cc = -(cw + ce).  Boundary entries are zero.
-static std::vector<cd> fd_triples(const std::vector<cd> &z, double ts, cd a) {
+std::vector<cd> fd_triples(const std::vector<cd> &z, double ts, cd a) {
     const int n = (int)z.size();
     std::vector<cd> t(3 * (size_t)n, cd(0, 0));
     const cd rot = std::polar(1.0, ts);

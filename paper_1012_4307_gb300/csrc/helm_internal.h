@@ -121,6 +121,13 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// Host setup shared by the translation units (helm_api.cu): the linear ECS contour of one axis
+// (Section 3.1) and its per-node FD coefficient triples (cw, cc, ce) of a * (-d^2/dz^2) with every
+// width multiplied by e^{i ts} (Section 3.2).
+std::vector<std::complex<double>> ecs_contour(int n, double lo, double hi, double theta, double r0lo, double r0hi);
+std::vector<std::complex<double>> fd_triples(const std::vector<std::complex<double>> &z, double ts,
+                                             std::complex<double> a);
+
 // Kernel launch geometry helpers
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
@@ -308,7 +315,12 @@ cudaError_t launch_axpy_mixed(size_t n, const double2 *a, const CY *x, double2 *
 cudaError_t launch_bicg_scalars(int stage, double2 *sc, cudaStream_t s);
 
 // adjoint helpers
+// y = w x or x / w (inverse) with w the product of the axes' dual volumes, on interior nodes;
+// conj_x: conj(x) in place of x
 cudaError_t launch_weight(size_t n, const int nodes[3], int dim, const double2 *w_axis[3], int inverse,
-                          const double2 *x, double2 *y, cudaStream_t s);
+                          const double2 *x, double2 *y, cudaStream_t s, int conj_x = 0);
+// lambda = w y; grad_k2 = Re(lambda u), grad_f = conj(lambda) (either may be null)
+cudaError_t launch_adjoint_grads(size_t n, const int nodes[3], int dim, const double2 *w_axis[3], const double2 *y,
+                                 const double2 *u, double *grad_k2, double2 *grad_f, cudaStream_t s);
 cudaError_t launch_grad_k2(size_t n, const int nodes[3], int dim, const double2 *lam, const double2 *u,
                            double *grad, cudaStream_t s);

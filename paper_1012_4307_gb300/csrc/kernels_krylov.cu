@@ -341,8 +341,10 @@ __global__ void k_axpy_mixed(size_t n, const double2 *__restrict__ a, const CY *
 }
 
 // y = W x or W^{-1} x, W_p = prod_axes w_axis[a][i_a] on interior nodes (boundary left).
+// y = w x (inverse: x / w) on interior nodes, w the product of the axes' dual volumes;
+// conj_x: x is conjugated first.
 __global__ void k_weight(int nx, int ny, int nz, int dim, const double2 *__restrict__ wx,
-                         const double2 *__restrict__ wy, const double2 *__restrict__ wz, int inverse,
+                         const double2 *__restrict__ wy, const double2 *__restrict__ wz, int inverse, int conj_x,
                          const double2 *__restrict__ x, double2 *__restrict__ y) {
     pdl_enter();
     const size_t n = (size_t)nx * ny * nz;
@@ -352,7 +354,35 @@ __global__ void k_weight(int nx, int ny, int nz, int dim, const double2 *__restr
         double2 w = cmul(wx[i], wy[j]);
         if (dim == 3) w = cmul(w, wz[k]);
         if (inverse) w = cinv(w);
-        y[q] = cmul(w, x[q]);
+        double2 v = x[q];
+        if (conj_x) v.y = -v.y;
+        y[q] = cmul(w, v);
+    }
+}
+
+// Gradients of a real loss after the adjoint solve: lambda = w y (w as in k_weight) at interior
+// nodes; grad_k2 = Re(lambda u) (null: skipped) and grad_f = conj(lambda) (null: skipped),
+// both 0 on the boundary.
+__global__ void k_adjoint_grads(int nx, int ny, int nz, int dim, const double2 *__restrict__ wx,
+                                const double2 *__restrict__ wy, const double2 *__restrict__ wz,
+                                const double2 *__restrict__ y, const double2 *__restrict__ u,
+                                double *__restrict__ grad_k2, double2 *__restrict__ grad_f) {
+    pdl_enter();
+    const size_t n = (size_t)nx * ny * nz;
+    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((size_t)nx * ny));
+        const bool in = !(i < 1 || i > nx - 2 || j < 1 || j > ny - 2 || (dim == 3 && (k < 1 || k > nz - 2)));
+        double2 lam = make_double2(0.0, 0.0);
+        if (in) {
+            double2 w = cmul(wx[i], wy[j]);
+            if (dim == 3) w = cmul(w, wz[k]);
+            lam = cmul(w, y[q]);
+        }
+        if (grad_k2) {
+            const double2 b = u[q];
+            grad_k2[q] = in ? (lam.x * b.x - lam.y * b.y) : 0.0;
+        }
+        if (grad_f) grad_f[q] = make_double2(lam.x, -lam.y);
     }
 }
 
@@ -489,9 +519,16 @@ template cudaError_t launch_axpy_mixed<float2>(size_t, const double2 *, const fl
 template cudaError_t launch_axpy_mixed<double2>(size_t, const double2 *, const double2 *, double2 *, cudaStream_t);
 
 cudaError_t launch_weight(size_t n, const int nodes[3], int dim, const double2 *w_axis[3], int inverse,
-                          const double2 *x, double2 *y, cudaStream_t s) {
+                          const double2 *x, double2 *y, cudaStream_t s, int conj_x) {
     launch_pdl(k_weight, stream_grid(n), NT, 0, s, nodes[0], nodes[1], dim == 3 ? nodes[2] : 1, dim, w_axis[0], w_axis[1],
-                                           w_axis[2], inverse, x, y);
+                                           w_axis[2], inverse, conj_x, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_grads(size_t n, const int nodes[3], int dim, const double2 *w_axis[3], const double2 *y,
+                                 const double2 *u, double *grad_k2, double2 *grad_f, cudaStream_t s) {
+    launch_pdl(k_adjoint_grads, stream_grid(n), NT, 0, s, nodes[0], nodes[1], dim == 3 ? nodes[2] : 1, dim, w_axis[0],
+               w_axis[1], w_axis[2], y, u, grad_k2, grad_f);
     return cudaGetLastError();
 }
 

@@ -809,12 +809,11 @@ extern "C" helm_status krylov_solve(helm_handle *h, helm_krylov method, const vo
     return st;
 }
 
-extern "C" helm_status helm_solve_adjoint(helm_handle *h, const void *rhs, void *lambda, double tol, int restart,
-                                          int maxit, helm_stats *stats) {
-    if (!h) return helm_fail(HELM_ERR_ARG, "null handle");
-    helm_status st;
-    if ((st = check_vec(rhs, "rhs")) != HELM_OK || (st = check_vec(lambda, "lambda")) != HELM_OK) return st;
-    if (rhs == lambda) return helm_fail(HELM_ERR_ARG, "rhs and lambda must not overlap");
+// y = A^{-1} W^{-1} r into h->adj_y, r = rhs or conj(rhs): with A^T = W A W^{-1} (the ECS FD
+// matrix is complex symmetric after weighting by the dual volumes W), lambda = W y solves
+// A^T lambda = r with the forward operator and its preconditioner.
+static helm_status adjoint_solve_y(helm_handle *h, const void *rhs, int conj_rhs, double tol, int restart, int maxit,
+                                   helm_stats *stats) {
     if (!h->adj_rhs) {
         // allocated outside the Krylov workspace so that a workspace regrow keeps them valid
         CKR(cudaMalloc((void **)&h->adj_rhs, h->np * sizeof(double2)));
@@ -824,13 +823,46 @@ extern "C" helm_status helm_solve_adjoint(helm_handle *h, const void *rhs, void 
         CKR(cudaMemsetAsync(h->adj_rhs, 0, h->np * sizeof(double2), h->stream));
     }
     const double2 *w[3] = {h->wts[0], h->wts[1], h->wts[2]};
-    // A^T = W A W^{-1}  =>  lambda = W A^{-1} W^{-1} rhs
-    CKR(launch_weight(h->np, h->n, h->dim, w, 1, (const double2 *)rhs, h->adj_rhs, h->stream));
+    CKR(launch_weight(h->np, h->n, h->dim, w, 1, (const double2 *)rhs, h->adj_rhs, h->stream, conj_rhs));
     CKR(cudaMemsetAsync(h->adj_y, 0, h->np * sizeof(double2), h->stream));
-    st = krylov_solve(h, HELM_FGMRES, h->adj_rhs, h->adj_y, tol, restart, maxit, stats);
+    return krylov_solve(h, HELM_FGMRES, h->adj_rhs, h->adj_y, tol, restart, maxit, stats);
+}
+
+extern "C" helm_status helm_solve_adjoint(helm_handle *h, const void *rhs, void *lambda, double tol, int restart,
+                                          int maxit, helm_stats *stats) {
+    if (!h) return helm_fail(HELM_ERR_ARG, "null handle");
+    helm_status st;
+    if ((st = check_vec(rhs, "rhs")) != HELM_OK || (st = check_vec(lambda, "lambda")) != HELM_OK) return st;
+    if (rhs == lambda) return helm_fail(HELM_ERR_ARG, "rhs and lambda must not overlap");
+    st = adjoint_solve_y(h, rhs, 0, tol, restart, maxit, stats);
     if (st != HELM_OK && st != HELM_ERR_NOCONV) return st;
+    const double2 *w[3] = {h->wts[0], h->wts[1], h->wts[2]};
     CKR(cudaMemsetAsync(lambda, 0, h->np * sizeof(double2), h->stream));
     CKR(launch_weight(h->np, h->n, h->dim, w, 0, h->adj_y, (double2 *)lambda, h->stream));
+    return st;
+}
+
+extern "C" helm_status helm_backward(helm_handle *h, const void *grad_u, const void *u, double *grad_k2,
+                                     void *grad_f, double tol, int restart, int maxit, helm_stats *stats) {
+    if (!h) return helm_fail(HELM_ERR_ARG, "null handle");
+    helm_status st;
+    if ((st = check_vec(grad_u, "grad_u")) != HELM_OK) return st;
+    if (!grad_k2 && !grad_f) return helm_fail(HELM_ERR_ARG, "grad_k2 and grad_f are both null");
+    if (grad_k2) {
+        if ((st = check_vec(u, "u")) != HELM_OK) return st;
+        if ((uintptr_t)grad_k2 % 8) return helm_fail(HELM_ERR_ARG, "grad_k2 is not 8-byte aligned");
+    }
+    if (grad_f && (st = check_vec(grad_f, "grad_f")) != HELM_OK) return st;
+    const void *outs[2] = {grad_k2, grad_f};
+    for (const void *o : outs)
+        if (o && (o == grad_u || o == u)) return helm_fail(HELM_ERR_ARG, "outputs must not overlap grad_u or u");
+    // A^T lambda = conj(grad_u)
+    st = adjoint_solve_y(h, grad_u, 1, tol, restart, maxit, stats);
+    if (st != HELM_OK && st != HELM_ERR_NOCONV) return st;
+    const double2 *w[3] = {h->wts[0], h->wts[1], h->wts[2]};
+    CKR(launch_adjoint_grads(h->np, h->n, h->dim, w, h->adj_y, (const double2 *)u, grad_k2, (double2 *)grad_f,
+                             h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
     return st;
 }
 

@@ -17,9 +17,10 @@
 // process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[HELM_NOALLOC_SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch per device.  In host code the symbol's name is only a
-// host-side stand-in; the address must come from cudaGetSymbolAddress, with that device
-// current, before any kernel may be handed the pointer.
+// Device address of g_noalloc_scratch per device, looked up once per device by the first call
+// (with that device current) and kept for the life of the process.  In host code the symbol's
+// name is only a host-side stand-in; a kernel may only be handed the looked-up address.  A
+// cudaDeviceReset invalidates the kept address, as it does every handle's memory.
 static void *g_scratch_addr[64];
 static std::mutex g_scratch_mutex;
 

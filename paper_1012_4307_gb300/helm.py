@@ -101,6 +101,8 @@ def load(build: bool = True):
             "krylov_solve": ([P, I, P, P, D, I, I, P], I),
             "helm_solve_adjoint": ([P, P, P, D, I, I, P], I),
             "helm_grad_k2": ([P, P, P, P], I),
+            "helm_backward": ([P, P, P, P, P, D, I, I, P], I),
+            "helm_qd_lambda0": ([P, D, P, P, P, I, P], I),
             "helm_mg_conv": ([P, P, P, I, D, I, P, P], I),
             "helm_mg_conv_noalloc": ([P, P, P, I, D, I, P, P], I),
             "helm_levels": ([P, P], I),
@@ -259,6 +261,36 @@ def helm_create(dim, n, k2: torch.Tensor, theta=math.pi / 6, r0_lo=None, r0_hi=N
     return h
 
 
+def helm_qd_lambda0(dim, n, k2_axis, theta=math.pi / 6, r0_lo=None, r0_hi=None, lo=None, hi=None,
+                    mode: str = "axes") -> float:
+    """Re(lambda0) for the QD preconditioner from per-axis k^2 profiles (host computation in the
+    library): mode "axes" = the one-dimensional counterpart (exact for a separable k^2 field),
+    "max_k2" = minus the largest k^2.  k2_axis: dim 1D arrays of n[a] values at the real nodes."""
+    import numpy as np
+    n = list(n) if hasattr(n, "__len__") else [n] * dim
+    lo = list(lo) if lo is not None else [-1.0] * dim
+    hi = list(hi) if hi is not None else [1.0] * dim
+    r0_lo = list(r0_lo) if r0_lo is not None else [-0.75] * dim
+    r0_hi = list(r0_hi) if r0_hi is not None else [0.75] * dim
+    g = _Grid()
+    g.dim = dim
+    for a in range(3):
+        g.n[a] = n[a] if a < dim else 1
+        g.lo[a] = lo[a] if a < dim else 0.0
+        g.hi[a] = hi[a] if a < dim else 1.0
+    prof = [np.ascontiguousarray(k2_axis[a], dtype=np.float64) for a in range(dim)]
+    for a in range(dim):
+        if prof[a].shape != (n[a],):
+            raise ValueError("k2_axis[%d] must hold %d values" % (a, n[a]))
+    ptrs = (C.c_void_p * 3)(*([p.ctypes.data for p in prof] + [None] * (3 - dim)))
+    rl = (C.c_double * 3)(*(r0_lo + [0.0] * (3 - dim)))
+    rh = (C.c_double * 3)(*(r0_hi + [0.0] * (3 - dim)))
+    out = C.c_double()
+    _check(load().helm_qd_lambda0(C.byref(g), float(theta), rl, rh, ptrs, {"axes": 0, "max_k2": 1}[mode],
+                                  C.byref(out)))
+    return out.value
+
+
 def helm_destroy(h: Handle):
     h.close()
 
@@ -346,6 +378,20 @@ def helm_grad_k2(h: Handle, lam: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
     _check(load().helm_grad_k2(h.ptr, C.c_void_p(_vec(lam, h.np, "lambda", torch.complex128)),
                                C.c_void_p(_vec(u, h.np, "u", torch.complex128)), C.c_void_p(grad.data_ptr())))
     return grad
+
+
+def helm_backward(h: Handle, grad_u: torch.Tensor, u: torch.Tensor | None, grad_k2: torch.Tensor | None,
+                  grad_f: torch.Tensor | None, tol=1e-10, restart=30, maxit=2000, raise_on_noconv=True):
+    """Adjoint step in the library: solves A^T lambda = conj(grad_u) and writes
+    grad_k2 = Re(lambda u) and grad_f = conj(lambda) into the given tensors (either may be None)."""
+    st = _Stats()
+    allow = (HELM_OK,) if raise_on_noconv else (HELM_OK, HELM_ERR_NOCONV)
+    pk2 = C.c_void_p(_vec(grad_k2, h.np, "grad_k2", torch.float64)) if grad_k2 is not None else None
+    pf = C.c_void_p(_vec(grad_f, h.np, "grad_f", torch.complex128)) if grad_f is not None else None
+    pu = C.c_void_p(_vec(u, h.np, "u", torch.complex128)) if u is not None else None
+    _check(load().helm_backward(h.ptr, C.c_void_p(_vec(grad_u, h.np, "grad_u", torch.complex128)), pu, pk2, pf,
+                                float(tol), int(restart), int(maxit), C.byref(st)), allow)
+    return _stats_from(st, None)
 
 
 def helm_mg_conv(h: Handle, b: torch.Tensor, tol=1e-6, maxcyc=100):
@@ -455,8 +501,9 @@ def helm_autotune(h: Handle, prec: str = "c64", reps: int = 10, cache: str | Non
 def helm_mg_conv_noalloc(h: Handle, b: torch.Tensor, x: torch.Tensor, tol=1e-6, maxcyc=100):
     """helm_mg_conv computed in the library's fixed scratch array (no allocation at all, not
     even here: the caller passes the output ``x``).  For callers that cannot allocate at the
-    point of the call, e.g. during CUDA graph capture.  Returns (cycles, factor); x is
-    overwritten with the stand-alone multigrid iterate."""
+    point of the call: a service whose device memory is sized once at start-up, or a loop that
+    cannot afford the device-wide synchronisation an allocation may cause.  Returns (cycles,
+    factor); x is overwritten with the stand-alone multigrid iterate."""
     nc, fac = C.c_int(), C.c_double()
     _check(load().helm_mg_conv_noalloc(h.ptr, C.c_void_p(_vec(b, h.np, "b")), C.c_void_p(_vec(x, h.np, "x", b.dtype)),
                                        _prec_of(b), float(tol), int(maxcyc), C.byref(nc), C.byref(fac)))
@@ -547,8 +594,9 @@ class HelmholtzSolve(torch.autograd.Function):
 
     forward(k2, f, handle_factory, tol, restart, maxit) -> u.  ``handle_factory(k2)`` returns
     a :class:`Handle` for that k^2.  Only u is saved (the Krylov basis is not kept).  backward
-    solves A^T lambda = conj(grad_u) by the adjoint identity and returns dL/dk^2 = Re(lambda u)
-    (PyTorch passes grad_u = 2 dL/d(conj u) for a real loss L).
+    is one library call (helm_backward): it solves A^T lambda = conj(grad_u) by the adjoint
+    identity and writes dL/dk^2 = Re(lambda u) and dL/df = conj(lambda) (PyTorch passes
+    grad_u = 2 dL/d(conj u) for a real loss L).
     """
 
     @staticmethod
@@ -565,10 +613,11 @@ class HelmholtzSolve(torch.autograd.Function):
     def backward(ctx, grad_u):
         (u,) = ctx.saved_tensors
         tol, restart, maxit = ctx.opts
-        # conj_physical materialises the conjugate (a lazy conj view would hand the library
-        # the unconjugated memory)
-        rhs = torch.conj_physical(grad_u.to(torch.complex128)).contiguous()
-        lam, _ = helm_solve_adjoint(ctx.h, rhs, tol=tol, restart=restart, maxit=maxit)
-        g = helm_grad_k2(ctx.h, lam, u)
-        gf = torch.conj_physical(lam) if ctx.needs_input_grad[1] else None
+        # marshalling only: complex128, contiguous, and a lazily conjugated view materialised
+        # (the library reads the memory as it is)
+        gu = grad_u.to(torch.complex128).resolve_conj().contiguous()
+        g = torch.empty(u.shape, dtype=torch.float64, device=u.device) if ctx.needs_input_grad[0] else None
+        gf = torch.empty_like(u) if ctx.needs_input_grad[1] else None
+        if g is not None or gf is not None:
+            helm_backward(ctx.h, gu, u, g, gf, tol=tol, restart=restart, maxit=maxit)
         return g, gf, None, None, None, None

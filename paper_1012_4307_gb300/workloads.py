@@ -214,11 +214,14 @@ def paper_mp1(k: float = 160.0, interior_cells: int = 256, layer_cells: int = 64
     k2 = np.full((n, n), k * k)
     f = np.zeros((n, n), complex)
     f[n // 2, n // 2] = 1.0
+    # k^2 as a sum of one profile per axis (input for the one-dimensional counterpart of QD's
+    # lambda0)
+    prof = np.full(n, k * k / 2.0)
     return Problem("mp1-k%g" % k, 2, n, k2, f, theta=math.pi / 6, r0=0.5, lo=-half, hi=half, coarsest_n=17,
-                   tol=1e-6)
+                   tol=1e-6, extra={"k2_axis": [prof, prof.copy()]})
 
 
-def _ne_layer_problem(name, k2fun, size, interior_cells, layer_cells):
+def _ne_layer_problem(name, k2fun, size, interior_cells, layer_cells, k2axis=None):
     """Square [0, size] of interior_cells cells per axis, ECS layers of layer_cells cells on the
     east and north sides only (Dirichlet at x = 0 and y = 0), ECS angle pi/6; source
     f = exp(-(x^2 + y^2)) (the printed exp(x^2 + y^2) read as the decaying Gaussian)."""
@@ -230,8 +233,13 @@ def _ne_layer_problem(name, k2fun, size, interior_cells, layer_cells):
     f = np.exp(-(X[0] ** 2 + X[1] ** 2)).astype(np.complex128)
     f = np.ascontiguousarray(np.broadcast_to(f, (n, n))).copy()
     _zero_ring(f)
+    extra = {}
+    if k2axis is not None:
+        x = X[0].ravel()
+        prof = np.asarray(k2axis(x), dtype=np.float64)
+        extra["k2_axis"] = [prof, prof.copy()]
     return Problem(name, 2, n, k2, f, theta=math.pi / 6, lo=0.0, hi=hi, r0_lo=-1.0, r0_hi=size, coarsest_n=17,
-                   tol=1e-6)
+                   tol=1e-6, extra=extra)
 
 
 def paper_mp2(k: float = 4.0, nu: float = 7.0, size: float = 50.0, interior_cells: int = 512,
@@ -239,7 +247,7 @@ def paper_mp2(k: float = 4.0, nu: float = 7.0, size: float = 50.0, interior_cell
     """MP2 (Table 2): Z = -Delta - nu (exp(-x^2) + exp(-y^2)) - k^2, i.e. k^2(x, y) = k^2 +
     nu (exp(-x^2) + exp(-y^2)) at the real nodes."""
     return _ne_layer_problem("mp2-k%g-nu%g" % (k, nu), lambda x, y: k * k + nu * (np.exp(-x * x) + np.exp(-y * y)),
-                             size, interior_cells, layer_cells)
+                             size, interior_cells, layer_cells, lambda x: k * k / 2.0 + nu * np.exp(-x * x))
 
 
 def paper_mp3(k: float = 2.0, size: float = 50.0, interior_cells: int = 512, layer_cells: int = 128) -> Problem:
@@ -249,4 +257,9 @@ def paper_mp3(k: float = 2.0, size: float = 50.0, interior_cells: int = 512, lay
         with np.errstate(divide="ignore"):
             v = k * k + 1.0 / x + 1.0 / y
         return np.where(np.isfinite(v), v, 0.0)
-    return _ne_layer_problem("mp3-k%g-L%g" % (k, size), k2fun, size, interior_cells, layer_cells)
+
+    def axis(x):
+        with np.errstate(divide="ignore"):
+            v = k * k / 2.0 + 1.0 / x
+        return np.where(np.isfinite(v), v, 0.0)
+    return _ne_layer_problem("mp3-k%g-L%g" % (k, size), k2fun, size, interior_cells, layer_cells, axis)

@@ -42,3 +42,11 @@ def to_gpu(x, dtype=None):
 
 def to_np(t):
     return t.detach().cpu().numpy()
+
+
+def small_problem_adjoint(n, kh=0.5):
+    """A 2D well problem of n x n nodes for the adjoint checks (E = 2, growth toward the
+    boundary up to k h = kh, Gaussian source of width 0.1)."""
+    from paper_1012_4307_gb300 import workloads as W
+    return W.Problem("adj", 2, n, W.k2_well_growth(2, n, E=2.0, kh_max=kh), W.gaussian_source(2, n, 0.1, 7),
+                     coarsest_n=17)

@@ -273,15 +273,36 @@ helm_status helm_levels(const helm_handle *h, int *nlev);
 helm_status helm_level_shape(const helm_handle *h, int level, int n[3]);
 
 /* ---- batched solves: many independent problems (energies, right-hand sides, grid sizes) ----
+ * The paper solves one problem at a time; batching is a library facility.
  * helm_create_batch builds one handle and one non-blocking CUDA stream per problem (all with
  * the same mg parameters).  helm_solve_batch solves every problem with FGMRES as krylov_solve
- * does, concurrently: one host thread advances the problems' resumable FGMRES loops (largest
- * grid first), each problem's steps are CUDA graphs replayed on its own stream, and the
- * problems' streams start after, and are joined back into, the stream given at creation.
- * Each problem's result equals that of krylov_solve on its handle.
+ * does, concurrently, with one of the engines below; the batch's work starts after, and is
+ * joined back into, the stream given at creation.  Each problem's result equals that of
+ * krylov_solve on its handle (with the handle's tuning).
  *   grids, theta, r0 (2*dim per problem: lo then hi), k2 (device pointers): arrays of nprob.
  *   rhs, x: arrays of nprob DEVICE c128 pointers.  stats: nprob host structs (optional).
  * Returns the worst status over the problems. */
+/* Engines of helm_solve_batch.
+ *   HELM_BATCH_LOCKSTEP  every problem advances its FGMRES steps in step with the others and every
+ *                        phase of a step is ONE launch over all problems: a temporally blocked pre-
+ *                        and post-smoothing launch per level shape above the coarse tail (covering
+ *                        every problem with a level of that shape), one thread-block-cluster launch
+ *                        for all problems' coarse tails, and one launch each for A z, the inner-
+ *                        product pass, its reduction, the Givens rotations and the update pass; the
+ *                        step is a replayed CUDA graph.  Requires 2D grids, a complex64 V(2,2)
+ *                        omega-Jacobi cycle with the delayed-CGS2 Arnoldi (HELM_GS_DCGS2), a common
+ *                        coarse tail (same coarsest levels), restart <= 63.  It installs on every
+ *                        problem's handle the cycle tuning it runs (cluster tail depth, tiles), so
+ *                        that krylov_solve on that handle gives the same result bit for bit.
+ *   HELM_BATCH_STREAMS   one stream per problem, steps interleaved by one host thread.
+ *   HELM_BATCH_AUTO      lockstep when the configuration allows it, else streams (default).
+ * helm_batch_set_engine: HELM_ERR_ARG for an unknown engine.  A solve with HELM_BATCH_LOCKSTEP on
+ * a batch it cannot run fails with HELM_ERR_ARG and the reason.  helm_batch_get_engine returns
+ * the engine of the last solve (HELM_BATCH_AUTO before any). */
+typedef enum { HELM_BATCH_AUTO = 0, HELM_BATCH_LOCKSTEP = 1, HELM_BATCH_STREAMS = 2 } helm_batch_engine;
+helm_status helm_batch_set_engine(helm_batch *b, int engine);
+helm_status helm_batch_get_engine(const helm_batch *b, int *last);
+
 helm_status helm_create_batch(int nprob, const helm_grid *grids, const double *theta, const double *r0,
                               const double *const *k2, const helm_mg_params *mg, void *stream,
                               helm_batch **out);
@@ -297,8 +318,13 @@ helm_status helm_batch_handle(helm_batch *b, int i, helm_handle **out);
  * drivers is bracketed by two CUDA events on the handle's stream and tagged with its class
  * and its algorithmic DRAM bytes and flops (each operand touched once).  helm_profile(h, 0)
  * disables it.  helm_profile_read synchronises the stream and returns, per class, the number
- * of launches, the summed event time (ms), and the summed algorithmic bytes and flops; the
- * four host arrays hold ncls entries (ncls <= HELM_K_NCLASS). */
+ * of launches, the summed event time (ms), and the summed algorithmic bytes and flops, and
+ * (bytes_pass, may be null) the bytes of the same work counted pass by pass: every smoothing
+ * sweep, residual and grid transfer as its own pass over its operands, as separate launches
+ * would move them (larger than the algorithmic bytes only for the temporally blocked kernels,
+ * which do several passes per launch); the host arrays hold ncls entries
+ * (ncls <= HELM_K_NCLASS).  Timed launches run eagerly (no CUDA graphs, no side stream), one
+ * event pair each, so their sum exceeds a graph-replayed solve's time. */
 typedef enum {
     HELM_K_APPLY = 0,         /* FP64 operator apply (A z, true residual)                */
     HELM_K_SMOOTH_FINE = 1,   /* smoothing sweeps on the finest level (blocked kernels:  */
@@ -316,7 +342,8 @@ typedef enum {
 } helm_kernel_class;
 
 helm_status helm_profile(helm_handle *h, int enable);
-helm_status helm_profile_read(helm_handle *h, int ncls, int *launches, double *ms, double *bytes, double *flops);
+helm_status helm_profile_read(helm_handle *h, int ncls, int *launches, double *ms, double *bytes, double *flops,
+                              double *bytes_pass);
 
 /* ---- cycle tuning (kernel choices; no counterpart in the paper) ----
  * The arithmetic of Algorithm 1 is fixed by helm_mg_params; these choices only pick which

@@ -131,12 +131,20 @@ static cplx diag_at(const or_op *op, int i, int j, int k)
         for (int j = 0; j < (op)->n[1]; j++)            \
             for (int i = 0; i < (op)->n[0]; i++)
 
+/* The same loop for bodies that write only their own node p from inputs the loop does not
+ * write: its iterations are independent, so with -fopenmp (the all-cores build of the CPU
+ * baseline) they are shared out over threads with bit-identical results; without -fopenmp the
+ * pragma is ignored.  Reductions (dot products, norms, counts) are never shared out. */
+#define FOR_NODES_INDEP(op)                             \
+    _Pragma("omp parallel for collapse(2) schedule(static)") \
+    FOR_NODES(op)
+
 #define PIDX(op) ((size_t)i + (size_t)(op)->n[0] * ((size_t)j + (size_t)(op)->n[1] * k))
 
 /* y = M x on interior nodes; boundary nodes of y are set to zero. */
 void or_apply(const or_op *op, const cplx *x, cplx *y)
 {
-    FOR_NODES(op) {
+    FOR_NODES_INDEP(op) {
         size_t p = PIDX(op);
         y[p] = is_interior(op, i, j, k) ? apply_at(op, x, i, j, k) : 0;
     }
@@ -147,7 +155,7 @@ void or_apply(const or_op *op, const cplx *x, cplx *y)
 void or_apply_T(const or_op *op, const cplx *x, cplx *y)
 {
     const size_t stride[3] = {1, (size_t)op->n[0], (size_t)op->n[0] * op->n[1]};
-    FOR_NODES(op) {
+    FOR_NODES_INDEP(op) {
         size_t p = PIDX(op);
         if (!is_interior(op, i, j, k)) { y[p] = 0; continue; }
         const int idx[3] = {i, j, k};
@@ -173,7 +181,7 @@ void or_apply_T(const or_op *op, const cplx *x, cplx *y)
 
 void or_diag(const or_op *op, cplx *d)
 {
-    FOR_NODES(op) {
+    FOR_NODES_INDEP(op) {
         size_t p = PIDX(op);
         d[p] = is_interior(op, i, j, k) ? diag_at(op, i, j, k) : 0;
     }
@@ -182,7 +190,7 @@ void or_diag(const or_op *op, cplx *d)
 /* r = f - M u on interior nodes, zero on the boundary (Algorithm 1, step 2). */
 void or_residual(const or_op *op, const cplx *f, const cplx *u, cplx *r)
 {
-    FOR_NODES(op) {
+    FOR_NODES_INDEP(op) {
         size_t p = PIDX(op);
         r[p] = is_interior(op, i, j, k) ? f[p] - apply_at(op, u, i, j, k) : 0;
     }
@@ -196,7 +204,7 @@ void or_jacobi(const or_op *op, double omega, int sweeps, const cplx *f, cplx *u
     cplx *r = (cplx *)malloc(np * sizeof(cplx));
     for (int s = 0; s < sweeps; s++) {
         or_residual(op, f, u, r);
-        FOR_NODES(op) {
+        FOR_NODES_INDEP(op) {
             if (!is_interior(op, i, j, k)) continue;
             size_t p = PIDX(op);
             u[p] += omega * r[p] / diag_at(op, i, j, k);
@@ -214,12 +222,12 @@ void or_rbjacobi(const or_op *op, double omega, int sweeps, const cplx *f, cplx 
         for (int colour = 0; colour < 2; colour++) {
             size_t np = npts(op);
             cplx *upd = (cplx *)calloc(np, sizeof(cplx));
-            FOR_NODES(op) {
+            FOR_NODES_INDEP(op) {
                 if (!is_interior(op, i, j, k) || ((i + j + k) & 1) != colour) continue;
                 size_t p = PIDX(op);
                 upd[p] = omega * (f[p] - apply_at(op, u, i, j, k)) / diag_at(op, i, j, k);
             }
-            FOR_NODES(op) {
+            FOR_NODES_INDEP(op) {
                 if (!is_interior(op, i, j, k) || ((i + j + k) & 1) != colour) continue;
                 u[PIDX(op)] += upd[PIDX(op)];
             }
@@ -236,6 +244,7 @@ void or_restrict(int dim, const int nf[3], const cplx *rf, cplx *rc)
 {
     int nc[3] = {1, 1, 1};
     for (int a = 0; a < dim; a++) nc[a] = (nf[a] + 1) / 2;
+    _Pragma("omp parallel for collapse(2) schedule(static)")
     for (int K = 0; K < nc[2]; K++)
         for (int J = 0; J < nc[1]; J++)
             for (int Ii = 0; Ii < nc[0]; Ii++) {
@@ -271,6 +280,7 @@ void or_prolong_add(int dim, const int nf[3], const cplx *ec, cplx *uf)
     int nc[3] = {1, 1, 1};
     int nfx[3] = {nf[0], dim >= 2 ? nf[1] : 1, dim >= 3 ? nf[2] : 1};
     for (int a = 0; a < dim; a++) nc[a] = (nf[a] + 1) / 2;
+    _Pragma("omp parallel for collapse(2) schedule(static)")
     for (int k = 0; k < nfx[2]; k++)
         for (int j = 0; j < nfx[1]; j++)
             for (int i = 0; i < nfx[0]; i++) {
@@ -568,6 +578,7 @@ int or_fgmres(const or_op *A, const or_mg *mg, int gf, int gc, const cplx *f, cp
         double beta = nrm2(np, w);
         if (beta <= tol * fn) { status = 0; break; }
         if (it >= maxit) break;
+        _Pragma("omp parallel for schedule(static)")
         for (size_t p = 0; p < np; p++) V[p] = w[p] / beta;
         for (int i = 0; i <= m; i++) g[i] = 0;
         g[0] = beta;
@@ -579,11 +590,13 @@ int or_fgmres(const or_op *A, const or_mg *mg, int gf, int gc, const cplx *f, cp
             for (int i = 0; i <= j; i++) {
                 cplx h = dotc(np, V + (size_t)i * np, w);
                 H[i + (size_t)(m + 1) * j] = h;
+                _Pragma("omp parallel for schedule(static)")
                 for (size_t p = 0; p < np; p++) w[p] -= h * V[(size_t)i * np + p];
             }
             double hn = nrm2(np, w);
             H[j + 1 + (size_t)(m + 1) * j] = hn;
             if (hn != 0.0)
+                _Pragma("omp parallel for schedule(static)")
                 for (size_t p = 0; p < np; p++) V[(size_t)(j + 1) * np + p] = w[p] / hn;
             /* previous rotations on column j */
             for (int i = 0; i < j; i++) {
@@ -613,6 +626,7 @@ int or_fgmres(const or_op *A, const or_mg *mg, int gf, int gc, const cplx *f, cp
             y[r] = s / H[r + (size_t)(m + 1) * r];
         }
         for (int c = 0; c < jdone; c++)
+            _Pragma("omp parallel for schedule(static)")
             for (size_t p = 0; p < np; p++) x[p] += y[c] * Z[(size_t)c * np + p];
         st->restarts++;
     }
@@ -649,16 +663,19 @@ int or_bicgstab(const or_op *A, const or_mg *mg, int gf, int gc, const cplx *f, 
         cplx rho = dotc(np, rh, r);
         if (rho == 0) { status = 2; break; }
         cplx beta = (rho / rho_old) * (alpha / om);
+        _Pragma("omp parallel for schedule(static)")
         for (size_t q = 0; q < np; q++) p[q] = r[q] + beta * (p[q] - om * v[q]);
         precond(mg, gf, gc, np, p, y);
         or_apply(A, y, v);
         cplx rv = dotc(np, rh, v);
         if (rv == 0) { status = 2; break; }
         alpha = rho / rv;
+        _Pragma("omp parallel for schedule(static)")
         for (size_t q = 0; q < np; q++) s[q] = r[q] - alpha * v[q];
         it++;
         double sn = nrm2(np, s);
         if (sn <= tol * fn) {
+            _Pragma("omp parallel for schedule(static)")
             for (size_t q = 0; q < np; q++) x[q] += alpha * y[q];
             if (st->history && it - 1 < st->history_len) st->history[it - 1] = sn / fn;
             status = 0;
@@ -669,6 +686,7 @@ int or_bicgstab(const or_op *A, const or_mg *mg, int gf, int gc, const cplx *f, 
         double tt = creal(dotc(np, t, t));
         if (tt == 0.0) { status = 2; break; }
         om = dotc(np, t, s) / tt;
+        _Pragma("omp parallel for schedule(static)")
         for (size_t q = 0; q < np; q++) {
             x[q] += alpha * y[q] + om * z[q];
             r[q] = s[q] - om * t[q];
@@ -720,7 +738,7 @@ int or_mg_conv(const or_mg *mg, int gf, int gc, const cplx *b, double tol, int m
  * nodes (used to state the complex symmetry of W M; zero on the boundary). */
 void or_weights(const or_op *op, cplx *wts)
 {
-    FOR_NODES(op) {
+    FOR_NODES_INDEP(op) {
         size_t p = PIDX(op);
         if (!is_interior(op, i, j, k)) { wts[p] = 0; continue; }
         const int idx[3] = {i, j, k};

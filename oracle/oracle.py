@@ -35,19 +35,40 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "helm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+# The same source built with -fopenmp: independent node loops shared out over the host's cores
+# (reductions stay serial, so every result is bit-identical to the single-threaded build).
+# Selected by HELM_ORACLE_OPENMP=1 in the environment before the first call; used only for the
+# all-cores CPU baseline.
+_LIB_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile helm_oracle.c with gcc (FP64, no contraction of a*b+c into FMAs)."""
+def _compile(out: str, extra) -> None:
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared", *extra,
+                           "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, out)
+
+
+def build(force: bool = False, openmp: bool | None = None) -> str:
+    """Compile helm_oracle.c with gcc (FP64, no contraction of a*b+c into FMAs), single-threaded
+    and with -fopenmp; returns the path of the variant in use."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    for path, extra in ((_LIB_PATH, []), (_LIB_OMP_PATH, ["-fopenmp"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+            _compile(path, extra)
+    if openmp is None:
+        openmp = os.environ.get("HELM_ORACLE_OPENMP", "0") == "1"
+    return _LIB_OMP_PATH if openmp else _LIB_PATH
+
+
+def threads() -> int:
+    """Threads the loaded oracle uses (1 for the single-threaded build)."""
+    if os.environ.get("HELM_ORACLE_OPENMP", "0") != "1":
+        return 1
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
 
 
 class _COp(C.Structure):

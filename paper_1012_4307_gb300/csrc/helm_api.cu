@@ -457,11 +457,15 @@ extern "C" helm_status helm_profile(helm_handle *h, int enable) {
 }
 
 extern "C" helm_status helm_profile_read(helm_handle *h, int ncls, int *launches, double *ms, double *bytes,
-                                         double *flops) {
+                                         double *flops, double *bytes_pass) {
     if (!h || !launches || !ms || !bytes || !flops || ncls < 1 || ncls > HELM_K_NCLASS)
         return helm_fail(HELM_ERR_ARG, "bad profile arguments");
     CKR(cudaStreamSynchronize(h->stream));
-    for (int c = 0; c < ncls; c++) { launches[c] = 0; ms[c] = bytes[c] = flops[c] = 0.0; }
+    for (int c = 0; c < ncls; c++) {
+        launches[c] = 0;
+        ms[c] = bytes[c] = flops[c] = 0.0;
+        if (bytes_pass) bytes_pass[c] = 0.0;
+    }
     for (const ProfRec &r : h->prof.recs) {
         if (r.cls < 0 || r.cls >= ncls) continue;
         float t = 0.f;
@@ -470,6 +474,7 @@ extern "C" helm_status helm_profile_read(helm_handle *h, int ncls, int *launches
         ms[r.cls] += t;
         bytes[r.cls] += r.bytes;
         flops[r.cls] += r.flops;
+        if (bytes_pass) bytes_pass[r.cls] += r.bytes_pass;
     }
     return HELM_OK;
 }
@@ -656,7 +661,11 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
             fused_jacobi2_ok(L.n, h->dim, tile)) {
             LevelDev &Lc = h->lv[l + 1];
             {
-                ProfScope ps(h, l == 0 ? HELM_K_SMOOTH_FINE : HELM_K_SMOOTH_COARSE, ni * (es + rs + es + es / nd), 0);
+                // fused: read b and 1/D, write u and the coarse residual; pass by pass: the
+                // first sweep from zero (b, k^2 -> u), the second (u, b, k^2 -> u), the
+                // residual with full weighting (u, b, k^2 -> coarse)
+                ProfScope ps(h, l == 0 ? HELM_K_SMOOTH_FINE : HELM_K_SMOOTH_COARSE, ni * (es + es + es + es / nd), 0,
+                             ni * ((2 * es + rs) + (3 * es + rs) + (2 * es + rs + es / nd)));
                 CKE(launch_pre2_restrict(L.M32, tile, (float)h->mg.omega, b, L.t32, Lc.b32, h->stream));
             }
             float2 *ec = Lc.u32;
@@ -668,7 +677,10 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
                     else CKE(cycle<R>(h, l + 1, Lc.b32, ec, false, gc, gf));
                 }
             }
-            ProfScope ps(h, l == 0 ? HELM_K_SMOOTH_FINE : HELM_K_SMOOTH_COARSE, ni * (es + es / nd + es + rs + es), 0);
+            // fused: read b, 1/D, u and the coarse correction, write u; pass by pass: the
+            // prolongation with correction (u, coarse -> u) and two sweeps (u, b, k^2 -> u)
+            ProfScope ps(h, l == 0 ? HELM_K_SMOOTH_FINE : HELM_K_SMOOTH_COARSE, ni * (es + es + es + es / nd + es), 0,
+                         ni * ((2 * es + es / nd) + 2 * (3 * es + rs)));
             return launch_prolong_post2(L.M32, tile, (float)h->mg.omega, b, L.t32, u, ec, h->stream);
         }
     }

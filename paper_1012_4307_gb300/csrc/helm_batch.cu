@@ -1,11 +1,16 @@
 // Batched solves of many independent problems (energies, right-hand sides, grid sizes).
 //
 // Each problem owns a full handle (levels, Krylov workspace) on its own non-blocking stream.
-// One host thread drives every problem's flexible-GMRES state machine round-robin: it only
-// ever polls events, so while one problem waits for its residual estimate the others keep
-// enqueueing, and kernels of different problems run concurrently on the GPU.  Every FGMRES
-// step of every problem is replayed from a CUDA graph captured on first use, so a step costs
-// one graph launch on the host.  Problems are visited largest first.
+// Two engines:
+//   lockstep (batch_lockstep.cu): the problems advance their FGMRES steps together and every
+//     phase of a step is one launch over all of them (complex64 V(2,2) Jacobi cycles with the
+//     delayed-CGS2 Arnoldi on 2D grids with a common coarse tail);
+//   streams: one host thread drives every problem's flexible-GMRES state machine round-robin:
+//     it only ever polls events, so while one problem waits for its residual estimate the
+//     others keep enqueueing, and kernels of different problems run concurrently on the GPU.
+//     Every FGMRES step of every problem is replayed from a CUDA graph captured on first use,
+//     so a step costs one graph launch on the host.  Problems are visited largest first.
+// The default picks lockstep whenever the configuration allows it.
 #include <algorithm>
 #include <numeric>
 #include <thread>
@@ -19,10 +24,17 @@ struct helm_batch {
     std::vector<cudaEvent_t> done;
     cudaEvent_t start = nullptr;
     cudaStream_t user = nullptr;
+    int engine = HELM_BATCH_AUTO;     // requested engine
+    int last = HELM_BATCH_AUTO;       // engine of the last solve
+    BatchLockstep *ls = nullptr;
 };
 
 extern "C" void helm_destroy_batch(helm_batch *b) {
     if (!b) return;
+    if (b->ls) {
+        cudaDeviceSynchronize();
+        lockstep_destroy(b->ls);
+    }
     for (helm_handle *h : b->h) helm_destroy(h);
     for (cudaStream_t s : b->streams)
         if (s) cudaStreamDestroy(s);
@@ -76,6 +88,20 @@ extern "C" helm_status helm_create_batch(int nprob, const helm_grid *grids, cons
     return HELM_OK;
 }
 
+extern "C" helm_status helm_batch_set_engine(helm_batch *b, int engine) {
+    if (!b) return helm_fail(HELM_ERR_ARG, "null batch");
+    if (engine != HELM_BATCH_AUTO && engine != HELM_BATCH_LOCKSTEP && engine != HELM_BATCH_STREAMS)
+        return helm_fail(HELM_ERR_ARG, "unknown batch engine %d", engine);
+    b->engine = engine;
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_batch_get_engine(const helm_batch *b, int *last) {
+    if (!b || !last) return helm_fail(HELM_ERR_ARG, "null argument");
+    *last = b->last;
+    return HELM_OK;
+}
+
 extern "C" helm_status helm_solve_batch(helm_batch *b, const void *const *rhs, void *const *x, double tol, int restart,
                                         int maxit, helm_stats *stats) {
     if (!b || !rhs || !x) return helm_fail(HELM_ERR_ARG, "bad batch arguments");
@@ -84,6 +110,25 @@ extern "C" helm_status helm_solve_batch(helm_batch *b, const void *const *rhs, v
     for (int i = 0; i < n; i++)
         if (!rhs[i] || !x[i] || rhs[i] == x[i] || ((uintptr_t)rhs[i] | (uintptr_t)x[i]) % 16)
             return helm_fail(HELM_ERR_ARG, "rhs/x of problem %d invalid (null, overlapping or misaligned)", i);
+    if (b->engine != HELM_BATCH_STREAMS) {
+        if (!b->ls && !(b->ls = lockstep_create(b->h))) return helm_fail(HELM_ERR_NOMEM, "host allocation failed");
+        if (lockstep_eligible(b->ls) && restart <= 63) {
+            // the problems' own streams may still hold work (setup, tuning images)
+            for (cudaStream_t s : b->streams)
+                if (cudaStreamSynchronize(s) != cudaSuccess) return helm_fail(HELM_ERR_CUDA, "cudaStreamSynchronize failed");
+            b->last = HELM_BATCH_LOCKSTEP;
+            std::vector<helm_stats> local(n);
+            helm_stats *sp = stats ? stats : local.data();
+            if (stats)
+                for (int i = 0; i < n; i++)
+                    if (!stats[i].history) stats[i].history_len = 0;
+            return lockstep_solve(b->ls, b->user, rhs, x, tol, restart, maxit, sp);
+        }
+        if (b->engine == HELM_BATCH_LOCKSTEP)
+            return helm_fail(HELM_ERR_ARG, "batch not eligible for the lockstep engine: %s%s", lockstep_why(b->ls),
+                             restart > 63 ? " (restart above 63)" : "");
+    }
+    b->last = HELM_BATCH_STREAMS;
     // the problems' streams start after everything already queued on the caller's stream
     if (cudaEventRecord(b->start, b->user) != cudaSuccess) return helm_fail(HELM_ERR_CUDA, "cudaEventRecord failed");
     for (cudaStream_t s : b->streams)

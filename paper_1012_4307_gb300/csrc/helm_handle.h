@@ -27,6 +27,7 @@ struct ProfRec {
     int cls;
     cudaEvent_t a, b;
     double bytes, flops;
+    double bytes_pass;  // the same work counted pass by pass (each sweep, residual, transfer)
 };
 struct Profiler {
     bool on = false;
@@ -122,12 +123,16 @@ struct helm_handle {
 
 // Launch-timing scope: records a start event now and, at destruction, a stop event plus the
 // launch's class and algorithmic cost.  A no-op unless the handle's profiler is on.
+// bytes: algorithmic DRAM bytes of the launch (each operand touched once); bytes_pass (< 0:
+// equal to bytes): the bytes of the same work counted pass by pass, as separate sweep, residual
+// and transfer launches would move them (differs for the temporally blocked kernels).
 struct ProfScope {
     helm_handle *h;
     int cls;
-    double bytes, flops;
+    double bytes, flops, bytes_pass;
     cudaEvent_t a = nullptr;
-    ProfScope(helm_handle *h_, int cls_, double bytes_, double flops_) : h(h_), cls(cls_), bytes(bytes_), flops(flops_) {
+    ProfScope(helm_handle *h_, int cls_, double bytes_, double flops_, double bytes_pass_ = -1.0)
+        : h(h_), cls(cls_), bytes(bytes_), flops(flops_), bytes_pass(bytes_pass_ < 0 ? bytes_ : bytes_pass_) {
         if (h->prof.on) {
             a = h->prof.next();
             if (a) cudaEventRecord(a, h->stream);
@@ -138,12 +143,14 @@ struct ProfScope {
         cudaEvent_t b = h->prof.next();
         if (!b) return;
         cudaEventRecord(b, h->stream);
-        h->prof.recs.push_back(ProfRec{cls, a, b, bytes, flops});
+        h->prof.recs.push_back(ProfRec{cls, a, b, bytes, flops, bytes_pass});
     }
 };
 
 helm_status helm_fail(helm_status st, const char *fmt, ...);
 void helm_free_krylov(helm_handle *h);
+// Allocates (or keeps) the handle's FGMRES workspace for restart length m.
+helm_status helm_ensure_krylov(helm_handle *h, int m);
 // Destroys the captured FGMRES step graphs (they are captured again on next use).
 void helm_drop_graphs(helm_handle *h);
 
@@ -179,3 +186,14 @@ int ctail_top(const helm_handle *h);
 // The cluster tail's initial shared-memory image for the current tuning (null: no tail, or not
 // built and build false); built on the handle's stream, outside graph capture.
 const void *ctail_image(helm_handle *h, bool build);
+
+// Lockstep engine of helm_solve_batch (batch_lockstep.cu): every phase of an FGMRES step is one
+// launch over all problems.  lockstep_eligible tells whether the batch's configuration is one it
+// runs (lockstep_why says why not).
+struct BatchLockstep;
+BatchLockstep *lockstep_create(const std::vector<helm_handle *> &handles);
+void lockstep_destroy(BatchLockstep *L);
+bool lockstep_eligible(BatchLockstep *L);
+const char *lockstep_why(const BatchLockstep *L);
+helm_status lockstep_solve(BatchLockstep *L, cudaStream_t user, const void *const *rhs, void *const *x, double tol,
+                           int m, int maxit, helm_stats *stats);

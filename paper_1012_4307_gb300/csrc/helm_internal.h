@@ -226,6 +226,73 @@ cudaError_t build_mg_ctail_image(int nlev, const DevOp<float> *ops, const float2
                                  cudaStream_t s);
 int mg_ctail_max_clusters(int nc, size_t bytes);
 
+// ------------------------------------------------------------------------------ batched launches
+// One launch covers the same phase of many problems (helm_solve_batch): a batched kernel reads
+// the table entry of blockIdx.z (or of the block range that holds blockIdx.x) and returns at
+// once when that problem's *active is 0.  Tables live in device memory.
+//
+// A level of one problem at one cycle phase (all entries of a launch have the same level shape):
+//   pre:  t = two sweeps from zero for M u = b, coarse = FW(b - M t)
+//   post: (u + j ustride) = two sweeps of (t + P coarse)
+struct BLevel {
+    DevOp<float> op;   // the level's complex64 operator (dinv set)
+    const float2 *b;   // right-hand side
+    float2 *t;         // pre: smoothed iterate (written); post: iterate (read)
+    float2 *u;         // post: result base
+    size_t ustride;    // post: the result is u + j * ustride (level 0: the j-th preconditioned vector)
+    float2 *coarse;    // pre: next level's right-hand side (written); post: next level's result (read)
+    const int *active;
+};
+// A problem's cluster tail (levels of equal shapes in every entry; image: the problem's prebuilt
+// initial shared memory for that tail).
+struct BTail {
+    const float2 *cx[MAX_CT_LEVELS], *cy[MAX_CT_LEVELS];
+    const float *k2[MAX_CT_LEVELS];
+    const float2 *minv;
+    const float2 *b_top;
+    float2 *u_top;      // result base: the result is u_top + j * ustride
+    size_t ustride;     // nonzero when the tail's top is the finest level (the j-th preconditioned vector)
+    const void *img;
+    const int *active;
+};
+// A problem's Krylov state for the batched delayed-CGS2 FGMRES step kernels.
+struct BVec {
+    size_t n;            // nodes
+    float4 *V;           // float-pair basis, slot stride n
+    float2 *Z;           // complex64 preconditioned vectors, slot stride n
+    float2 *b0;          // level 0's complex64 right-hand side (the next cycle's input)
+    DevOpDF A;           // A in double-FP32
+    double2 *partials, *hv, *alpha2, *H, *dcoef, *g, *sn;
+    const double2 *fnorm;
+    double *cs, *est;
+    unsigned *tickets;
+    int ldh;
+    const int *active;
+};
+cudaError_t launch_pre2_restrict_batch(const int n[3], int tile, int count, const BLevel *tab, float omega,
+                                       cudaStream_t s);
+cudaError_t launch_prolong_post2_batch(const int n[3], int tile, int count, const BLevel *tab, float omega, int j,
+                                       cudaStream_t s);
+cudaError_t launch_mg_ctail_batch(int nlev, const DevOp<float> *ops, int nu_c, int nu1, int nu2, int rb, float omega,
+                                  int gf, int gc, int nc, int count, const BTail *tab, int j, cudaStream_t s);
+// Flat blocks of one problem's batched 2D apply; problem e takes [first[e], first[e + 1]).
+unsigned apply_A_df_blocks(const int n[3]);
+cudaError_t launch_apply_A_df_batch(int count, const BVec *tab, const unsigned *first, unsigned nblocks, int j,
+                                    cudaStream_t s);
+// Block rows of the two-vector dot pass over nv basis vectors (its grid is gs_df_dot2_nblocks x
+// this); problem e's dot-pass blocks of step j are [first[e], first[e + 1]) of the launch.
+int gs_df_dot2_groups(int nv);
+// close: the closing step of a cycle with j columns (x and w both slot j)
+cudaError_t launch_mdot2_pair_batch(int count, const BVec *tab, const unsigned *first, unsigned nblocks, int j,
+                                    int close, cudaStream_t s);
+// has_w: 2 (w came from the unscaled slot j), 1 (w from slot 0), 0 (closing step: no new column)
+cudaError_t launch_reduce_dcgs2_batch(int count, const BVec *tab, const unsigned *first, int groups, int j,
+                                      int has_w, cudaStream_t s);
+cudaError_t launch_update2_pair_batch(int count, const BVec *tab, const unsigned *first, unsigned nblocks, int j,
+                                      cudaStream_t s);
+// Rotation of column j of every active problem; est_out[e] = its est[j] (-1 if inactive).
+cudaError_t launch_givens_batch(int count, const BVec *tab, int j, double *est_out, cudaStream_t s);
+
 template <typename CI, typename CO>
 cudaError_t launch_convert(size_t n, const CI *in, CO *out, cudaStream_t s);
 template <typename C>
@@ -270,8 +337,9 @@ cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int n
 // complex64 (the next step's preconditioner input).
 cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *x, const float4 *w,
                               double2 *partials, cudaStream_t s);
+// has_w as in launch_reduce_dcgs2_batch
 cudaError_t launch_reduce_dcgs2(const double2 *partials, int nblk, double2 *hv, unsigned *ticket, int j,
-                                const double2 *alpha2, double2 *H, int ldh, double2 *coef, int w_scaled,
+                                const double2 *alpha2, double2 *H, int ldh, double2 *coef, int has_w,
                                 cudaStream_t s);
 cudaError_t launch_dcgs2_coef(int j, int has_w, const double2 *hv, const double2 *alpha2, double2 *H, int ldh,
                               double2 *coef, cudaStream_t s);

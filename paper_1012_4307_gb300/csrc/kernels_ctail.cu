@@ -371,6 +371,56 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_mg_ctail(const __grid_constan
     for_owned(X, T, [&](int j, int i) { A->u_top[(size_t)i + (size_t)T.nx * j] = lrow(X, T, T.ou, j)[i]; });
 }
 
+// Batched cluster tail: cluster z runs problem z's tail (blockIdx.z is shared by every block of
+// a cluster, so a cluster returns as a whole when its problem is inactive).  The launch
+// arguments A0 are the levels' common layout; the problem's pointers come from its table entry,
+// and its blocks start from the problem's prebuilt image.
+__global__ void __launch_bounds__(CT_THREADS, 1) k_mg_ctail_b(const __grid_constant__ CArgs A0,
+                                                           const BTail *__restrict__ tab, int j) {
+    pdl_trigger();
+    const BTail &E = tab[blockIdx.z];
+    if (*E.active == 0) return;
+    extern __shared__ __align__(16) unsigned char ct_smem[];
+    __shared__ CArgs As;
+    cg::cluster_group cl = cg::this_cluster();
+    Ctx X{ct_smem, (int)cl.block_rank(), (int)cl.num_blocks()};
+    {
+        const int *src = reinterpret_cast<const int *>(&A0);
+        int *dst = reinterpret_cast<int *>(&As);
+        for (int q = threadIdx.x; q < (int)(sizeof(CArgs) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int l = 0; l < As.nlev; l++) {
+            As.lv[l].cx = E.cx[l];
+            As.lv[l].cy = E.cy[l];
+            As.lv[l].k2 = E.k2[l];
+        }
+        As.minv = E.minv;
+        As.b_top = E.b_top;
+        As.u_top = E.u_top + (size_t)j * E.ustride;
+        As.img = (const float4 *)E.img;
+    }
+    __syncthreads();
+    const CArgs *A = &As;
+    {
+        const float4 *src = A->img + (size_t)X.rank * (A->total / 16);
+        for (unsigned q = threadIdx.x; q < A->total / 16; q += blockDim.x) ((float4 *)ct_smem)[q] = src[q];
+        __syncthreads();
+    }
+    const LV T = lv_of(X, A->lv[0]);
+    pdl_wait();
+    csync();
+    for_owned(X, T, [&](int j, int i) {
+        const size_t p = (size_t)i + (size_t)T.nx * j;
+        lrow(X, T, T.ob, j)[i] = A->b_top[p];
+        if (!A->zero) put(X, T, T.ou, j, i, A->u_top[p], X.rank);
+    });
+    csync();
+    ct_cycle<0>(X, A, A->zero != 0, A->gf, A->gc);
+    for_owned(X, T, [&](int j, int i) { A->u_top[(size_t)i + (size_t)T.nx * j] = lrow(X, T, T.ou, j)[i]; });
+}
+
 // Nested slabs: level 0 in runs of ceil((ny - 2) / nc) rows, level l + 1 bounded by
 // (B_l[r] + 1) / 2.  False unless every level has odd ny and the next has (ny + 1) / 2.
 bool ct_bounds(int nlev, const int (*n)[3], int nc, int (*B)[CT_MAXC + 1]) {
@@ -519,6 +569,46 @@ cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_t
     cfg.attrs = at;
     cfg.numAttrs = pdl_enabled() ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, k_mg_ctail, A);
+}
+
+// Batched tail over count problems whose tail levels have the shapes of ops (every problem's
+// own pointers and prebuilt image in tab); one cluster of nc blocks per problem.
+cudaError_t launch_mg_ctail_batch(int nlev, const DevOp<float> *ops, int nu_c, int nu1, int nu2, int rb, float omega,
+                                  int gf, int gc, int nc, int count, const BTail *tab, int j, cudaStream_t s) {
+    if (count < 1 || count > 65535) return cudaErrorInvalidValue;
+    CArgs A;
+    const size_t bytes = ct_args(nlev, ops, nullptr, nu_c, nc, A);
+    if (!bytes) return cudaErrorInvalidValue;
+    A.nu1 = nu1;
+    A.nu2 = nu2;
+    A.rb = rb;
+    A.zero = 1;
+    A.omega = omega;
+    A.gf = gf;
+    A.gc = gc;
+    static bool attr[2] = {false, false};
+    const int ai = nc == 16;
+    if (!attr[ai]) {
+        cudaError_t e = cudaFuncSetAttribute(k_mg_ctail_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT_SMEM_BYTES);
+        if (e == cudaSuccess && nc > 8) e = cudaFuncSetAttribute(k_mg_ctail_b, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        attr[ai] = true;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(nc, 1, count);
+    cfg.blockDim = dim3(CT_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = nc;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, k_mg_ctail_b, A, tab, j);
 }
 
 // Clusters of nc blocks with the given shared memory that the device can run at once (0: the

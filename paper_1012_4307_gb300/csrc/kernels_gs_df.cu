@@ -241,16 +241,17 @@ __global__ void __launch_bounds__(NT) k_update_norm_pair(size_t n, const float4 
 // first-pass Hessenberg column, whose error the next step's double-FP32 reorthogonalisation
 // measures and adds to H (the update that uses it is double-FP32, so A z_j stays exactly
 // expanded in the basis), so it is formed from the hi parts in FP32.
+// bx: this block's index among the nblk blocks that cover the vector (one launch, or one
+// problem's share of a batched launch).
 template <int CH>
-__global__ void __launch_bounds__(NT, 6) k_mdot2_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
-                                                   const float4 *__restrict__ x, const float4 *__restrict__ w,
-                                                   double2 *__restrict__ partials) {
-    pdl_enter();
+__device__ __forceinline__ void mdot2_body(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
+                                           const float4 *__restrict__ x, const float4 *__restrict__ w,
+                                           double2 *__restrict__ partials, int bx, int nblk) {
     __shared__ double sums[4 * CH];
-    // block (b, y) = blockIdx.x = b * ngroups + y: the blocks that read the same stretch of x and
-    // w run side by side, so that all but the first of them find it in L2
+    // block (b, y) = bx = b * ngroups + y: the blocks that read the same stretch of x and w run
+    // side by side, so that all but the first of them find it in L2
     const int ngroups = (nv + CH - 1) / CH;
-    const int yb = blockIdx.x % ngroups, xb = blockIdx.x / ngroups, G = gridDim.x / ngroups;
+    const int yb = bx % ngroups, xb = bx / ngroups, G = nblk / ngroups;
     const int i0 = yb * CH;
     const int cnt = min(CH, nv - i0);
     float s[CH][4];   // V^H x: [basis][re.s, re.c, im.s, im.c]
@@ -299,6 +300,41 @@ __global__ void __launch_bounds__(NT, 6) k_mdot2_pair(size_t n, const float4 *__
     }
 }
 
+template <int CH>
+__global__ void __launch_bounds__(NT, 6) k_mdot2_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
+                                                   const float4 *__restrict__ x, const float4 *__restrict__ w,
+                                                   double2 *__restrict__ partials) {
+    pdl_enter();
+    mdot2_body<CH>(n, V, ldv, nv, x, w, partials, blockIdx.x, gridDim.x);
+}
+
+// Index of the entry whose block range [first[e], first[e + 1]) holds block b (count entries).
+__device__ __forceinline__ int batch_entry(const unsigned *first, int count, unsigned b) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batched two-vector pass of step j over many problems: problem e takes blocks
+// [first[e], first[e + 1]) (its one-launch grid); x = slot j and w = slot j + 1 of its basis.
+// close: the closing step of a cycle with j columns (w = x = slot j).
+template <int CH>
+__global__ void __launch_bounds__(NT, 6) k_mdot2_pair_b(const BVec *__restrict__ tab, const unsigned *__restrict__ first,
+                                                     int count, int j, int close) {
+    pdl_enter();
+    const int e = batch_entry(first, count, blockIdx.x);
+    const BVec &P = tab[e];
+    if (*P.active == 0) return;
+    const float4 *V = P.V;
+    const float4 *x = V + (size_t)j * P.n;
+    mdot2_body<CH>(P.n, V, P.n, j + 1, x, close ? x : x + P.n, P.partials, (int)(blockIdx.x - first[e]),
+                   (int)(first[e + 1] - first[e]));
+}
+
 // One pass of the DCGS2 update for step j with coefficients coef (see k_dcgs2_coef):
 //   x <- (x - sum_{i<j} V_i A_i) r             (x = basis slot j: its final vector v_j)
 //   w <- w rw - x_old s - sum_{i<j} V_i C_i    (w = slot j + 1: once orthogonalised, not
@@ -314,10 +350,10 @@ __global__ void __launch_bounds__(NT, 6) k_mdot2_pair(size_t n, const float4 *__
 template <bool SMALL_A>
 __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, size_t ldv, int j,
                                               const float4 *cA, const float4 *cC, ff rinv, ff sr, ff si, ff rw,
-                                              float2 *__restrict__ b_out, float &sn, float &cn) {
+                                              float2 *__restrict__ b_out, float &sn, float &cn, int bx, int nblk) {
     float4 *x = V + (size_t)j * ldv, *w = V + (size_t)(j + 1) * ldv;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+    for (size_t q = bx * (size_t)NT + threadIdx.x; q < n; q += (size_t)nblk * NT) {
         const float4 xq = x[q], wq = w[q];
         const ff xr = ff_re(xq), xi = ff_im(xq);
         // (sum, compensation) accumulators per component: v over the basis, started from x; w in
@@ -408,10 +444,11 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
     }
 }
 
-__global__ void __launch_bounds__(NT, 4) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
-                                                     const double2 *__restrict__ coef, double2 *__restrict__ partials,
-                                                     unsigned *ticket, double2 *alpha_out, float2 *__restrict__ b_out) {
-    pdl_enter();
+// bx: this block among the nblk blocks of the vector (see mdot2_body).
+__device__ __forceinline__ void update2_body(size_t n, float4 *__restrict__ V, size_t ldv, int j,
+                                             const double2 *__restrict__ coef, double2 *__restrict__ partials,
+                                             unsigned *ticket, double2 *alpha_out, float2 *__restrict__ b_out, int bx,
+                                             int nblk) {
     __shared__ float4 cA[64], cC[64];
     __shared__ float4 sc[2];  // (r hi, lo, small-correction flag, 0), s
     __shared__ float2 rws;    // scale of the incoming w: coef[2j+2].x as a float pair
@@ -435,15 +472,34 @@ __global__ void __launch_bounds__(NT, 4) k_update2_pair(size_t n, float4 *__rest
     const ff rinv = ff_re(sc[0]), sr = ff_re(sc[1]), si = ff_im(sc[1]), rw{rws.x, rws.y};
     float sn = 0.f, cn = 0.f;
     if (sc[0].z != 0.f)
-        update2_nodes<true>(n, V, ldv, j, cA, cC, rinv, sr, si, rw, b_out, sn, cn);
+        update2_nodes<true>(n, V, ldv, j, cA, cC, rinv, sr, si, rw, b_out, sn, cn, bx, nblk);
     else
-        update2_nodes<false>(n, V, ldv, j, cA, cC, rinv, sr, si, rw, b_out, sn, cn);
+        update2_nodes<false>(n, V, ldv, j, cA, cC, rinv, sr, si, rw, b_out, sn, cn, bx, nblk);
     ff vals[1] = {ff_norm(sn, cn)};
     block_sum_ff<1>(vals, sums);
-    if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(sums[0], 0.0);
-    if (!ticket || !last_block(ticket, gridDim.x)) return;
-    reduce_partials_block(partials, gridDim.x, 1, alpha_out, true);
+    if (threadIdx.x == 0) partials[bx] = make_double2(sums[0], 0.0);
+    if (!ticket || !last_block(ticket, nblk)) return;
+    reduce_partials_block(partials, nblk, 1, alpha_out, true);
     if (threadIdx.x == 0) *ticket = 0u;
+}
+
+__global__ void __launch_bounds__(NT, 4) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
+                                                     const double2 *__restrict__ coef, double2 *__restrict__ partials,
+                                                     unsigned *ticket, double2 *alpha_out, float2 *__restrict__ b_out) {
+    pdl_enter();
+    update2_body(n, V, ldv, j, coef, partials, ticket, alpha_out, b_out, blockIdx.x, gridDim.x);
+}
+
+// Batched update pass of step j: problem e takes blocks [first[e], first[e + 1]); its ticket
+// tickets[1] and alpha_out alpha2[j + 1], the new slot written into its level 0's right-hand side.
+__global__ void __launch_bounds__(NT, 4) k_update2_pair_b(const BVec *__restrict__ tab, const unsigned *__restrict__ first,
+                                                       int count, int j) {
+    pdl_enter();
+    const int e = batch_entry(first, count, blockIdx.x);
+    const BVec &P = tab[e];
+    if (*P.active == 0) return;
+    update2_body(P.n, P.V, P.n, j, P.dcoef, P.partials, P.tickets + 1, P.alpha2 + j + 1, P.b0,
+                 (int)(blockIdx.x - first[e]), (int)(first[e + 1] - first[e]));
 }
 
 // 1 / beta.x as a float pair, one FP64 division per block.
@@ -587,6 +643,22 @@ cudaError_t launch_update2_pair(size_t n, float4 *V, size_t ldv, int j, const do
                b_out);
     return cudaGetLastError();
 }
+
+cudaError_t launch_mdot2_pair_batch(int count, const BVec *tab, const unsigned *first, unsigned nblocks, int j,
+                                    int close, cudaStream_t s) {
+    if (count < 1 || j < 0 || j > 63 || nblocks < (unsigned)count) return cudaErrorInvalidValue;
+    launch_pdl(k_mdot2_pair_b<DF_CH2>, dim3(nblocks), NT, 0, s, tab, first, count, j, close);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update2_pair_batch(int count, const BVec *tab, const unsigned *first, unsigned nblocks, int j,
+                                      cudaStream_t s) {
+    if (count < 1 || j < 0 || j > 63 || nblocks < (unsigned)count) return cudaErrorInvalidValue;
+    launch_pdl(k_update2_pair_b, dim3(nblocks), NT, 0, s, tab, first, count, j);
+    return cudaGetLastError();
+}
+
+int gs_df_dot2_groups(int nv) { return std::max(1, (nv + DF_CH2 - 1) / DF_CH2); }
 
 static unsigned pair_grid(size_t n) { return (unsigned)std::max<size_t>(1, std::min<size_t>(cdiv(n, NT), 152 * 8)); }
 

@@ -201,11 +201,9 @@ __global__ void __launch_bounds__(NT) k_combine_df(size_t n, const float2 *__res
 // Complex Givens rotations G = [c s; -conj(s) c] (c real) on column j of the Hessenberg
 // matrix (column-major, leading dimension ldh); see Saad, Iterative Methods for Sparse Linear
 // Systems, Section 6.5.9 for the real case.
-__global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm_dev,
-                         double *est) {
-    pdl_enter();
+__device__ __forceinline__ void givens_body(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g,
+                                            const double2 *fnorm_dev, double *est) {
     const double fnorm = fnorm_dev->x;
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double2 *col = H + (size_t)ldh * j;
     for (int i = 0; i < j; i++) {
         const double2 a = col[i], b = col[i + 1];
@@ -237,12 +235,33 @@ __global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, do
     est[j] = hypot(g[j + 1].x, g[j + 1].y) / fnorm;
 }
 
+__global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm_dev,
+                         double *est) {
+    pdl_enter();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    givens_body(H, ldh, j, cs, sn, g, fnorm_dev, est);
+}
+
+// Batched rotation of column j (block z = problem), and the gather of every problem's estimate
+// est[j] into out[problem] (-1 for inactive problems), for one copy to the host.
+__global__ void k_givens_b(const BVec *__restrict__ tab, int j, double *out) {
+    pdl_enter();
+    const BVec &P = tab[blockIdx.z];
+    if (threadIdx.x != 0) return;
+    if (*P.active == 0) {
+        out[blockIdx.z] = -1.0;
+        return;
+    }
+    givens_body(P.H, P.ldh, j, P.cs, P.sn, P.g, P.fnorm, P.est);
+    out[blockIdx.z] = P.est[j];
+}
+
 // The reduction of the two-vector inner-product pass (block v sums value v of the partials in
 // the fixed order of k_reduce) followed, in the last block to finish, by the DCGS2 coefficient
 // step of step j (see dcgs2_coef.cuh); the ticket returns to 0.
-__global__ void k_reduce_dcgs2(const double2 *__restrict__ partials, int nblk, double2 *hv, unsigned *ticket, int j,
-                               const double2 *alpha2, double2 *H, int ldh, double2 *coef, int has_w) {
-    pdl_enter();
+__device__ __forceinline__ void reduce_dcgs2_body(const double2 *__restrict__ partials, int nblk, double2 *hv,
+                                                  unsigned *ticket, int j, const double2 *alpha2, double2 *H, int ldh,
+                                                  double2 *coef, int has_w) {
     __shared__ double2 sums[1];
     const int i = blockIdx.x;
     double2 acc[1] = {make_double2(0.0, 0.0)};
@@ -252,6 +271,23 @@ __global__ void k_reduce_dcgs2(const double2 *__restrict__ partials, int nblk, d
     if (!last_block(ticket, gridDim.x)) return;
     if (threadIdx.x < 32) dcgs2_coef_warp(j, has_w, hv, alpha2, H, ldh, coef);
     if (threadIdx.x == 0) *ticket = 0u;
+}
+
+__global__ void k_reduce_dcgs2(const double2 *__restrict__ partials, int nblk, double2 *hv, unsigned *ticket, int j,
+                               const double2 *alpha2, double2 *H, int ldh, double2 *coef, int has_w) {
+    pdl_enter();
+    reduce_dcgs2_body(partials, nblk, hv, ticket, j, alpha2, H, ldh, coef, has_w);
+}
+
+// Batched reduction + coefficient step of step j (block z = problem; the problem's dot pass
+// had first[z + 1] - first[z] blocks, i.e. that many / groups per value).
+__global__ void k_reduce_dcgs2_b(const BVec *__restrict__ tab, const unsigned *__restrict__ first, int groups, int j,
+                                 int has_w) {
+    pdl_enter();
+    const BVec &P = tab[blockIdx.z];
+    if (*P.active == 0) return;
+    const int nblk = (int)((first[blockIdx.z + 1] - first[blockIdx.z]) / groups);
+    reduce_dcgs2_body(P.partials, nblk, P.hv, P.tickets, j, P.alpha2, P.H, P.ldh, P.dcoef, has_w);
 }
 
 // DCGS2 coefficient step as its own launch (one warp); see dcgs2_coef.cuh.
@@ -465,11 +501,24 @@ cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, d
 }
 
 cudaError_t launch_reduce_dcgs2(const double2 *partials, int nblk, double2 *hv, unsigned *ticket, int j,
-                                const double2 *alpha2, double2 *H, int ldh, double2 *coef, int w_scaled,
+                                const double2 *alpha2, double2 *H, int ldh, double2 *coef, int has_w,
                                 cudaStream_t s) {
-    if (j < 0 || j > 63) return cudaErrorInvalidValue;
-    launch_pdl(k_reduce_dcgs2, 2 * (j + 1), NT, 0, s, partials, nblk, hv, ticket, j, alpha2, H, ldh, coef,
-               w_scaled ? 2 : 1);
+    if (j < 0 || j > 64 || has_w < 0 || has_w > 2) return cudaErrorInvalidValue;
+    launch_pdl(k_reduce_dcgs2, 2 * (j + 1), NT, 0, s, partials, nblk, hv, ticket, j, alpha2, H, ldh, coef, has_w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_dcgs2_batch(int count, const BVec *tab, const unsigned *first, int groups, int j,
+                                      int has_w, cudaStream_t s) {
+    if (count < 1 || count > 65535 || j < 0 || j > 64 || groups < 1 || has_w < 0 || has_w > 2)
+        return cudaErrorInvalidValue;
+    launch_pdl(k_reduce_dcgs2_b, dim3(2 * (j + 1), 1, count), NT, 0, s, tab, first, groups, j, has_w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_givens_batch(int count, const BVec *tab, int j, double *est_out, cudaStream_t s) {
+    if (count < 1 || count > 65535 || j < 0 || j > 63) return cudaErrorInvalidValue;
+    launch_pdl(k_givens_b, dim3(1, 1, count), 32, 0, s, tab, j, est_out);
     return cudaGetLastError();
 }
 

@@ -28,7 +28,7 @@ template <typename R> struct OpView {
     int nx, ny, nz;
 };
 
-template <typename R> __host__ OpView<R> view(const DevOp<R> &op) {
+template <typename R> __host__ __device__ OpView<R> view(const DevOp<R> &op) {
     OpView<R> v;
     v.cx = op.coef[0]; v.cy = op.coef[1]; v.cz = op.coef[2];
     v.k2 = op.k2; v.dinv = op.dinv; v.bk = op.bk; v.c = op.c;
@@ -245,6 +245,186 @@ __global__ void __launch_bounds__(BX *BY) k_prolong_add(int nx, int ny, int nz, 
     }
 }
 
+// 3D residual + full weighting, each fine residual computed once.  A block owns R3_TX x R3_TY
+// coarse nodes in (x, y) and R3_KC coarse planes; it marches the fine planes 2K - 1 .. 2K + 1 of
+// its coarse planes with a window of four u planes (the region around its fine residual region,
+// one node of halo) and a window of four residual planes in shared memory.  Phase z computes the
+// residual on fine plane z (from u planes z - 1 .. z + 1) and, for z = 2K + 2, applies
+// (1,2,1)^3 / 64 to residual planes 2K - 1 .. 2K + 1 for coarse plane K; the four-plane windows
+// let both run in one phase, one barrier per fine plane.  The phase is software-pipelined: it
+// first issues the global loads of the next phases (u plane z + 2, and b, k^2 of plane z + 1)
+// into registers, computes from shared memory while they are in flight, then stores the u
+// values.  Fine nodes outside the grid's interior hold zero residuals.  Same arithmetic as
+// k_residual_restrict.
+constexpr int R3_TX = 16, R3_TY = 8, R3_KC = 8, R3_NT = 256;
+constexpr int R3_FW = 2 * R3_TX + 1, R3_FH = 2 * R3_TY + 1;  // fine residual region
+constexpr int R3_UW = R3_FW + 2, R3_UH = R3_FH + 2;          // u window region
+constexpr int R3_UPT = (R3_UW * R3_UH + R3_NT - 1) / R3_NT;  // u values per thread and plane
+constexpr int R3_RPT = (R3_FW * R3_FH + R3_NT - 1) / R3_NT;  // residuals per thread and plane
+template <typename R> constexpr size_t r3_smem_bytes() {
+    return (size_t)4 * (R3_UW * R3_UH + R3_FW * R3_FH) * sizeof(typename CT<R>::T);
+}
+
+template <typename R, typename CB>
+__global__ void __launch_bounds__(R3_NT, 3) k_resrestrict3(OpView<R> o, const CB *__restrict__ b,
+                                                        const typename CT<R>::T *__restrict__ u,
+                                                        typename CT<R>::T *__restrict__ rc, int ncx, int ncy, int ncz) {
+    pdl_enter();
+    typedef typename CT<R>::T C;
+    extern __shared__ __align__(16) unsigned char r3_smem[];
+    C(*us)[R3_UH][R3_UW] = reinterpret_cast<C(*)[R3_UH][R3_UW]>(r3_smem);
+    C(*rs)[R3_FH][R3_FW] = reinterpret_cast<C(*)[R3_FH][R3_FW]>(r3_smem + (size_t)4 * R3_UW * R3_UH * sizeof(C));
+    const int nx = o.nx, ny = o.ny;
+    const int I0 = 1 + blockIdx.x * R3_TX, J0 = 1 + blockIdx.y * R3_TY;
+    const int K0 = 1 + blockIdx.z * R3_KC, K1 = min(K0 + R3_KC, ncz - 1);
+    const int X0 = 2 * I0 - 1, Y0 = 2 * J0 - 1;  // first fine node of the residual region
+    const size_t sxy = (size_t)nx * ny;
+    const C zero = mk(R(0), R(0));
+    // this thread's u-window nodes (global offset in a plane, or -1 outside the grid) and
+    // residual-region nodes (offset, or -1 outside the interior)
+    int uoff[R3_UPT], roff[R3_RPT];  // a plane has at most 2^16 x 2^16 nodes: 32-bit offsets
+#pragma unroll
+    for (int t = 0; t < R3_UPT; t++) {
+        const int q = threadIdx.x + t * R3_NT, qx = q % R3_UW, qy = q / R3_UW, x = X0 - 1 + qx, y = Y0 - 1 + qy;
+        uoff[t] = (q < R3_UW * R3_UH && x < nx && y < ny) ? x + nx * y : -1;
+    }
+#pragma unroll
+    for (int t = 0; t < R3_RPT; t++) {
+        const int q = threadIdx.x + t * R3_NT, qx = q % R3_FW, qy = q / R3_FW, x = X0 + qx, y = Y0 + qy;
+        roff[t] = (q < R3_FW * R3_FH && x <= nx - 2 && y <= ny - 2) ? x + nx * y : -1;
+    }
+    auto fetch_u = [&](int z, C (&v)[R3_UPT]) {
+#pragma unroll
+        for (int t = 0; t < R3_UPT; t++) v[t] = uoff[t] >= 0 ? u[(size_t)uoff[t] + sxy * z] : zero;
+    };
+    auto put_u = [&](int z, const C (&v)[R3_UPT]) {
+        C *dst = &us[z & 3][0][0];
+#pragma unroll
+        for (int t = 0; t < R3_UPT; t++) {
+            const int q = threadIdx.x + t * R3_NT;
+            if (q < R3_UW * R3_UH) dst[q] = v[t];
+        }
+    };
+    auto fetch_bk = [&](int z, C (&bv)[R3_RPT], R (&kv)[R3_RPT]) {
+#pragma unroll
+        for (int t = 0; t < R3_RPT; t++) {
+            bv[t] = zero;
+            kv[t] = R(0);
+            if (roff[t] >= 0) {
+                const size_t p = (size_t)roff[t] + sxy * z;
+                bv[t] = to_c(b[p], R());
+                kv[t] = o.k2[p];
+            }
+        }
+    };
+    auto residual = [&](int z, const C (&bv)[R3_RPT], const R (&kv)[R3_RPT]) {
+        const C(*um)[R3_UW] = us[(z - 1) & 3];
+        const C(*uc)[R3_UW] = us[z & 3];
+        const C(*up)[R3_UW] = us[(z + 1) & 3];
+        C *dst = &rs[z & 3][0][0];
+        const C czw = o.cz[3 * z], czc = o.cz[3 * z + 1], cze = o.cz[3 * z + 2];
+#pragma unroll
+        for (int t = 0; t < R3_RPT; t++) {
+            const int q = threadIdx.x + t * R3_NT;
+            if (q >= R3_FW * R3_FH) continue;
+            const int qx = q % R3_FW, qy = q / R3_FW;
+            C r = zero;
+            if (roff[t] >= 0) {
+                const int x = X0 + qx, y = Y0 + qy, lx = qx + 1, ly = qy + 1;
+                C cw = __ldg(&o.cx[3 * x]), cc = __ldg(&o.cx[3 * x + 1]), ce = __ldg(&o.cx[3 * x + 2]);
+                C acc = cmul(cw, uc[ly][lx - 1]);
+                acc = cfma(ce, uc[ly][lx + 1], acc);
+                C d = cc;
+                cw = __ldg(&o.cy[3 * y]); cc = __ldg(&o.cy[3 * y + 1]); ce = __ldg(&o.cy[3 * y + 2]);
+                acc = cfma(cw, uc[ly - 1][lx], acc);
+                acc = cfma(ce, uc[ly + 1][lx], acc);
+                d = cadd(d, cc);
+                acc = cfma(czw, um[ly][lx], acc);
+                acc = cfma(cze, up[ly][lx], acc);
+                d = cadd(d, czc);
+                d = cadd(d, cadd(cscale(o.bk, kv[t]), o.c));
+                r = csub(bv[t], cfma(d, uc[ly][lx], acc));
+            }
+            dst[q] = r;
+        }
+    };
+    auto weigh = [&](int K) {
+        const C(*r0)[R3_FW] = rs[(2 * K - 1) & 3];
+        const C(*r1)[R3_FW] = rs[(2 * K) & 3];
+        const C(*r2)[R3_FW] = rs[(2 * K + 1) & 3];
+        for (int q = threadIdx.x; q < R3_TX * R3_TY; q += R3_NT) {
+            const int cx = q % R3_TX, cy = q / R3_TX, I = I0 + cx, J = J0 + cy;
+            if (I > ncx - 2 || J > ncy - 2) continue;
+            const int fx = 2 * cx, fy = 2 * cy;  // region indices of fine nodes 2I - 1, 2J - 1
+            // (1,2,1)/4 along x, then y, then z
+            C pl[3];
+#pragma unroll
+            for (int t = 0; t < 3; t++) {
+                const C(*rr)[R3_FW] = t == 0 ? r0 : (t == 1 ? r1 : r2);
+                C a[3];
+#pragma unroll
+                for (int dy = 0; dy < 3; dy++) {
+                    const C *row = &rr[fy + dy][fx];
+                    a[dy] = cadd(cadd(row[0], row[2]), cscale(row[1], R(2)));
+                }
+                pl[t] = cadd(cadd(a[0], a[2]), cscale(a[1], R(2)));
+            }
+            const C v = cadd(cadd(pl[0], pl[2]), cscale(pl[1], R(2)));
+            rc[(size_t)I + (size_t)ncx * ((size_t)J + (size_t)ncy * K)] = cscale(v, R(1.0 / 64.0));
+        }
+    };
+    const int zs = 2 * K0 - 1, ze = 2 * K1 - 1;  // fine planes of the residual
+    C uv[R3_UPT], bcur[R3_RPT], bnext[R3_RPT];
+    R kcur[R3_RPT], knext[R3_RPT];
+    for (int z = zs - 1; z <= zs + 1; z++) {
+        fetch_u(z, uv);
+        put_u(z, uv);
+    }
+    fetch_bk(zs, bcur, kcur);
+    __syncthreads();
+    for (int z = zs; z <= ze + 1; z++) {
+        const bool more_u = z + 2 <= ze + 1, more_r = z + 1 <= ze;
+        if (more_u) fetch_u(z + 2, uv);
+        if (more_r) fetch_bk(z + 1, bnext, knext);
+        if (z <= ze) residual(z, bcur, kcur);
+        if ((z & 1) == 0 && z >= zs + 3) weigh((z - 2) / 2);
+        if (more_u) put_u(z + 2, uv);
+        if (more_r) {
+#pragma unroll
+            for (int t = 0; t < R3_RPT; t++) {
+                bcur[t] = bnext[t];
+                kcur[t] = knext[t];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// 3D prolongation + correction in closed form: uf[p] += 1/8 of the sum of ec at the eight corners
+// (floor / ceil of i/2, j/2, k/2), coincident corners repeated, i.e. the average over the distinct
+// coarse nodes of k_prolong_add.  Each thread marches KCHUNK fine planes.
+template <typename R>
+__global__ void __launch_bounds__(BX *BY) k_prolong3(int nx, int ny, int nz, const typename CT<R>::T *__restrict__ ec,
+                                                     typename CT<R>::T *__restrict__ uf) {
+    pdl_enter();
+    typedef typename CT<R>::T C;
+    const int i = blockIdx.x * BX + threadIdx.x + 1;
+    const int j = blockIdx.y * BY + threadIdx.y + 1;
+    if (i > nx - 2 || j > ny - 2) return;
+    const int ncx = (nx + 1) / 2, ncy = (ny + 1) / 2;
+    const int k0 = blockIdx.z * KCHUNK + 1, k1 = min(k0 + KCHUNK, nz - 1);
+    const size_t csy = (size_t)ncx, csz = (size_t)ncx * ncy;
+    const size_t c00 = (size_t)(i >> 1) + csy * (j >> 1), c10 = (size_t)((i + 1) >> 1) + csy * (j >> 1);
+    const size_t c01 = (size_t)(i >> 1) + csy * ((j + 1) >> 1), c11 = (size_t)((i + 1) >> 1) + csy * ((j + 1) >> 1);
+    for (int k = k0; k < k1; k++) {
+        const size_t za = csz * (k >> 1), zb = csz * ((k + 1) >> 1);
+        const C s0 = cadd(cadd(ec[c00 + za], ec[c10 + za]), cadd(ec[c01 + za], ec[c11 + za]));
+        const C s1 = cadd(cadd(ec[c00 + zb], ec[c10 + zb]), cadd(ec[c01 + zb], ec[c11 + zb]));
+        const size_t p = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k);
+        uf[p] = cadd(uf[p], cscale(cadd(s0, s1), R(0.125)));
+    }
+}
+
 // Exact coarsest solve as u = Minv b on the unknowns (interior nodes in natural order); one
 // warp per row, fixed-order lane partial sums reduced by shuffles.
 template <typename R>
@@ -385,16 +565,16 @@ __device__ __forceinline__ float2 tile_diag(const TC &tc, int sx, int sy, float 
 // u = two omega-Jacobi sweeps from u = 0 for M u = b, written on the owned fine nodes; then
 // rc = FW(b - M u) on the owned coarse nodes.  Blocks whose region lies inside the grid's
 // interior skip the per-node boundary tests.
+// (bx, by): the tile of coarse nodes this block owns.
 template <int TCX, int TCY>
-__global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float omega, const float2 *__restrict__ b,
-                                                       float2 *__restrict__ u, float2 *__restrict__ rc, int ncx,
-                                                       int ncy) {
-    pdl_enter();
+__device__ __forceinline__ void pre2_restrict_tile(const OpView<float> &o, float omega, const float2 *__restrict__ b,
+                                                   float2 *__restrict__ u, float2 *__restrict__ rc, int ncx, int ncy,
+                                                   int bx, int by) {
     typedef Tile<TCX, TCY> TL;
     constexpr int RW = TL::RW, RH = TL::RH;
     extern __shared__ __align__(16) unsigned char pre_smem[];
     typename TL::Pre &T = *reinterpret_cast<typename TL::Pre *>(pre_smem);
-    const int I0 = 1 + blockIdx.x * TCX, J0 = 1 + blockIdx.y * TCY;
+    const int I0 = 1 + bx * TCX, J0 = 1 + by * TCY;
     const int X0 = 2 * I0 - 3, Y0 = 2 * J0 - 3;
     const int nx = o.nx, ny = o.ny;
     const bool full = X0 >= 1 && X0 + RW - 1 <= nx - 2 && Y0 >= 1 && Y0 + RH - 1 <= ny - 2;
@@ -450,20 +630,27 @@ __global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float om
     }
 }
 
+template <int TCX, int TCY>
+__global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float omega, const float2 *__restrict__ b,
+                                                       float2 *__restrict__ u, float2 *__restrict__ rc, int ncx,
+                                                       int ncy) {
+    pdl_enter();
+    pre2_restrict_tile<TCX, TCY>(o, omega, b, u, rc, ncx, ncy, blockIdx.x, blockIdx.y);
+}
+
 // u_out <- two omega-Jacobi sweeps of (u_in + P ec), on the owned fine nodes.  u_in and u_out
 // are different arrays: blocks read their halo of u_in while other blocks write u_out.
 // Bilinear interpolation in closed form: P ec at fine node (x, y) is the mean of the four
 // coarse values at (floor/ceil(x/2), floor/ceil(y/2)), coincident ones repeated.
 template <int TCX, int TCY>
-__global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float omega, const float2 *__restrict__ b,
-                                                       const float2 *__restrict__ u_in, float2 *__restrict__ u,
-                                                       const float2 *__restrict__ ec, int ncx, int ncy) {
-    pdl_enter();
+__device__ __forceinline__ void prolong_post2_tile(const OpView<float> &o, float omega, const float2 *__restrict__ b,
+                                                   const float2 *__restrict__ u_in, float2 *__restrict__ u,
+                                                   const float2 *__restrict__ ec, int ncx, int ncy, int bx, int by) {
     typedef Tile<TCX, TCY> TL;
     constexpr int RW = TL::RW, RH = TL::RH;
     extern __shared__ __align__(16) unsigned char post_smem[];
     typename TL::Post &T = *reinterpret_cast<typename TL::Post *>(post_smem);
-    const int I0 = 1 + blockIdx.x * TCX, J0 = 1 + blockIdx.y * TCY;
+    const int I0 = 1 + bx * TCX, J0 = 1 + by * TCY;
     const int X0 = 2 * I0 - 3, Y0 = 2 * J0 - 3;
     const int nx = o.nx, ny = o.ny;
     const bool full = X0 >= 1 && X0 + RW - 1 <= nx - 2 && Y0 >= 1 && Y0 + RH - 1 <= ny - 2;
@@ -508,6 +695,35 @@ __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float om
         if (!inside(x, y)) continue;
         u[(size_t)x + (size_t)nx * y] = tile_jacobi<RW>(T.tc, T.u4, T.b, T.di, sx, sy, omega);
     }
+}
+
+template <int TCX, int TCY>
+__global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float omega, const float2 *__restrict__ b,
+                                                       const float2 *__restrict__ u_in, float2 *__restrict__ u,
+                                                       const float2 *__restrict__ ec, int ncx, int ncy) {
+    pdl_enter();
+    prolong_post2_tile<TCX, TCY>(o, omega, b, u_in, u, ec, ncx, ncy, blockIdx.x, blockIdx.y);
+}
+
+// Batched forms (many problems, one launch): blockIdx.z picks the table entry, whose level has
+// the same nodes in every entry of one launch; entries whose problem is inactive return at once.
+template <int TCX, int TCY>
+__global__ void __launch_bounds__(256) k_pre2_restrict_b(const BLevel *__restrict__ tab, float omega) {
+    pdl_enter();
+    const BLevel &E = tab[blockIdx.z];
+    if (*E.active == 0) return;
+    const OpView<float> o = view(E.op);
+    pre2_restrict_tile<TCX, TCY>(o, omega, E.b, E.t, E.coarse, (o.nx + 1) / 2, (o.ny + 1) / 2, blockIdx.x, blockIdx.y);
+}
+
+template <int TCX, int TCY>
+__global__ void __launch_bounds__(256) k_prolong_post2_b(const BLevel *__restrict__ tab, float omega, int j) {
+    pdl_enter();
+    const BLevel &E = tab[blockIdx.z];
+    if (*E.active == 0) return;
+    const OpView<float> o = view(E.op);
+    prolong_post2_tile<TCX, TCY>(o, omega, E.b, E.t, E.u + (size_t)j * E.ustride, E.coarse, (o.nx + 1) / 2,
+                                 (o.ny + 1) / 2, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------------------------------------------ coarse tail
@@ -820,6 +1036,18 @@ template <typename R, typename CB>
 cudaError_t launch_residual_restrict(const DevOp<R> &op, int dim, const CB *bb, const typename CT<R>::T *u,
                                      typename CT<R>::T *rc, cudaStream_t s) {
     int nc[3] = {(op.n[0] + 1) / 2, (op.n[1] + 1) / 2, dim == 3 ? (op.n[2] + 1) / 2 : 1};
+    if (dim == 3 && (size_t)op.n[0] * op.n[1] < ((size_t)1 << 31)) {  // 32-bit in-plane offsets
+        constexpr size_t smem = r3_smem_bytes<R>();
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_resrestrict3<R, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        dim3 g(cdiv(nc[0] - 2, R3_TX), cdiv(nc[1] - 2, R3_TY), cdiv(nc[2] - 2, R3_KC));
+        launch_pdl(k_resrestrict3<R, CB>, g, R3_NT, smem, s, view(op), bb, u, rc, nc[0], nc[1], nc[2]);
+        return cudaGetLastError();
+    }
     dim3 g = grid_for(nc, dim), b(BX, BY);
     if (dim == 3) launch_pdl(k_residual_restrict<R, 3, CB>, g, b, 0, s, view(op), bb, u, rc, nc[0], nc[1], nc[2]);
     else launch_pdl(k_residual_restrict<R, 2, CB>, g, b, 0, s, view(op), bb, u, rc, nc[0], nc[1], nc[2]);
@@ -830,7 +1058,7 @@ template <typename R>
 cudaError_t launch_prolong_add(const int nf[3], int dim, const typename CT<R>::T *ec, typename CT<R>::T *uf,
                                cudaStream_t s) {
     dim3 g = grid_for(nf, dim), b(BX, BY);
-    if (dim == 3) launch_pdl(k_prolong_add<R, 3>, g, b, 0, s, nf[0], nf[1], nf[2], ec, uf);
+    if (dim == 3) launch_pdl(k_prolong3<R>, g, b, 0, s, nf[0], nf[1], nf[2], ec, uf);
     else launch_pdl(k_prolong_add<R, 2>, g, b, 0, s, nf[0], nf[1], 1, ec, uf);
     return cudaGetLastError();
 }
@@ -949,6 +1177,58 @@ cudaError_t launch_prolong_post2(const DevOp<float> &op, int tile, float omega, 
     case 1: return post2_t<16, 16>(op, omega, b, u_in, u_out, ec, s);
     case 2: return post2_t<16, 8>(op, omega, b, u_in, u_out, ec, s);
     default: return post2_t<64, 4>(op, omega, b, u_in, u_out, ec, s);
+    }
+}
+
+template <int TCX, int TCY>
+static cudaError_t pre2_b_t(int n0, int n1, int count, const BLevel *tab, float omega, cudaStream_t s) {
+    const int ncx = (n0 + 1) / 2, ncy = (n1 + 1) / 2;
+    constexpr size_t smem = sizeof(typename Tile<TCX, TCY>::Pre);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_pre2_restrict_b<TCX, TCY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY), count);
+    launch_pdl(k_pre2_restrict_b<TCX, TCY>, g, 256, smem, s, tab, omega);
+    return cudaGetLastError();
+}
+
+template <int TCX, int TCY>
+static cudaError_t post2_b_t(int n0, int n1, int count, const BLevel *tab, float omega, int j, cudaStream_t s) {
+    const int ncx = (n0 + 1) / 2, ncy = (n1 + 1) / 2;
+    constexpr size_t smem = sizeof(typename Tile<TCX, TCY>::Post);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_prolong_post2_b<TCX, TCY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY), count);
+    launch_pdl(k_prolong_post2_b<TCX, TCY>, g, 256, smem, s, tab, omega, j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre2_restrict_batch(const int n[3], int tile, int count, const BLevel *tab, float omega,
+                                       cudaStream_t s) {
+    if (count < 1 || count > 65535 || tile == HELM_TILE_WAVE || !fused_jacobi2_ok(n, 2, tile)) return cudaErrorInvalidValue;
+    switch (tile) {
+    case 0: return pre2_b_t<32, 8>(n[0], n[1], count, tab, omega, s);
+    case 1: return pre2_b_t<16, 16>(n[0], n[1], count, tab, omega, s);
+    case 2: return pre2_b_t<16, 8>(n[0], n[1], count, tab, omega, s);
+    default: return pre2_b_t<64, 4>(n[0], n[1], count, tab, omega, s);
+    }
+}
+
+cudaError_t launch_prolong_post2_batch(const int n[3], int tile, int count, const BLevel *tab, float omega, int j,
+                                       cudaStream_t s) {
+    if (count < 1 || count > 65535 || tile == HELM_TILE_WAVE || !fused_jacobi2_ok(n, 2, tile)) return cudaErrorInvalidValue;
+    switch (tile) {
+    case 0: return post2_b_t<32, 8>(n[0], n[1], count, tab, omega, j, s);
+    case 1: return post2_b_t<16, 16>(n[0], n[1], count, tab, omega, j, s);
+    case 2: return post2_b_t<16, 8>(n[0], n[1], count, tab, omega, j, s);
+    default: return post2_b_t<64, 4>(n[0], n[1], count, tab, omega, j, s);
     }
 }
 

@@ -135,6 +135,8 @@ static helm_status ensure_ws(helm_handle *h, int m) {
     return HELM_OK;
 }
 
+helm_status helm_ensure_krylov(helm_handle *h, int m) { return ensure_ws(h, m); }
+
 static helm_status ensure_bicg(helm_handle *h) {
     helm_status st = ensure_ws(h, 1);
     if (st != HELM_OK) return st;
@@ -384,7 +386,7 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
         pdl_cycle_scope pdl;
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
         CKE(launch_reduce_dcgs2(h->partials, gs_df_dot2_nblocks(np, j + 1), h->hv, h->tickets, j, h->alpha2, h->H, ldh,
-                                h->dcoef, scaled ? 1 : 0, s));
+                                h->dcoef, scaled ? 2 : 1, s));
     }
     const bool fork = j > 0 && !h->prof.on;
     if (j > 0) {
@@ -425,9 +427,11 @@ static cudaError_t fgmres_close_dcgs2(helm_handle *h, int jc, int m) {
         CKE(launch_mdot2_pair(np, V4, np, jc + 1, x, x, h->partials, s));
     }
     {
+        // the reduction and, in its last block, the coefficient step that finishes column jc - 1
+        // only (the batched engine runs the same two launches)
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
-        CKE(launch_reduce(h->partials, gs_df_dot2_nblocks(np, jc + 1), jc + 1, h->hv, 0, nullptr, s));
-        CKE(launch_dcgs2_coef(jc, 0, h->hv, h->alpha2, h->H, ldh, h->dcoef, s));
+        CKE(launch_reduce_dcgs2(h->partials, gs_df_dot2_nblocks(np, jc + 1), h->hv, h->tickets, jc, h->alpha2, h->H,
+                                ldh, h->dcoef, 0, s));
         CKE(launch_givens(h->H, ldh, jc - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, s));
     }
     CKE(cudaMemcpyAsync(h->est_host + jc - 1, h->est_dev + jc - 1, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -111,11 +111,13 @@ def load(build: bool = True):
             "helm_solve_batch": ([P, P, P, D, I, I, P], I),
             "helm_destroy_batch": ([P], None),
             "helm_batch_handle": ([P, I, P], I),
+            "helm_batch_set_engine": ([P, I], I),
+            "helm_batch_get_engine": ([P, P], I),
             "helm_profile": ([P, I], I),
             "helm_set_tuning": ([P, P], I),
             "helm_get_tuning": ([P, P], I),
             "helm_autotune": ([P, I, I, P, P], I),
-            "helm_profile_read": ([P, I, P, P, P, P], I),
+            "helm_profile_read": ([P, I, P, P, P, P, P], I),
             "helm_last_error": ([], C.c_char_p),
             "helm_version": ([], C.c_char_p),
         }
@@ -413,11 +415,14 @@ def helm_profile(h: Handle, enable: bool = True):
 
 
 def helm_profile_read(h: Handle) -> dict:
-    """Per kernel class: launches, summed event time (ms), algorithmic bytes and flops."""
+    """Per kernel class: launches, summed event time (ms), algorithmic bytes and flops, and the
+    bytes counted pass by pass (bytes_pass)."""
     nc = len(KERNEL_CLASSES)
-    la, ms, by, fl = (C.c_int * nc)(), (C.c_double * nc)(), (C.c_double * nc)(), (C.c_double * nc)()
-    _check(load().helm_profile_read(h.ptr, nc, la, ms, by, fl))
-    return {name: dict(launches=la[i], ms=ms[i], bytes=by[i], flops=fl[i]) for i, name in enumerate(KERNEL_CLASSES)}
+    la, ms, by, fl, bp = ((C.c_int * nc)(), (C.c_double * nc)(), (C.c_double * nc)(), (C.c_double * nc)(),
+                          (C.c_double * nc)())
+    _check(load().helm_profile_read(h.ptr, nc, la, ms, by, fl, bp))
+    return {name: dict(launches=la[i], ms=ms[i], bytes=by[i], flops=fl[i], bytes_pass=bp[i])
+            for i, name in enumerate(KERNEL_CLASSES)}
 
 
 def _tuning_to_dict(t: _Tuning, nlev: int) -> dict:
@@ -577,6 +582,23 @@ def helm_autotune_batch(b: Batch, prec: str = "c64", reps: int = 10, cache: str 
         else:
             helm_set_tuning(h, chosen[key])
     return chosen
+
+
+BATCH_ENGINES = {"auto": 0, "lockstep": 1, "streams": 2}
+_BATCH_ENGINE_NAMES = {v: k for k, v in BATCH_ENGINES.items()}
+
+
+def helm_batch_set_engine(b: Batch, engine: str):
+    """Engine of helm_solve_batch: "lockstep" (every phase of a step one launch over all
+    problems), "streams" (one stream per problem) or "auto" (lockstep when it applies)."""
+    _check(load().helm_batch_set_engine(b.ptr, BATCH_ENGINES[engine]))
+
+
+def helm_batch_get_engine(b: Batch) -> str:
+    """The engine the last helm_solve_batch ran ("auto" before any)."""
+    e = C.c_int()
+    _check(load().helm_batch_get_engine(b.ptr, C.byref(e)))
+    return _BATCH_ENGINE_NAMES[e.value]
 
 
 def helm_solve_batch(b: Batch, rhs, x, tol=1e-8, restart=30, maxit=1000, raise_on_noconv=True):

@@ -163,17 +163,23 @@ def config_small(n: int = 65) -> Problem:
                    coarsest_n=17, restart=30, tol=1e-10)
 
 
+# CSG angle of the well workloads: the paper hand-tunes theta_a per model problem (Section 6,
+# Tables 1-4); for these workloads (V(2,2) cycle, k h up to 0.6) a sweep over pi/17 .. pi/6 puts
+# the fewest FGMRES iterations at pi/10 .. pi/9 on every grid.
+WELL_THETA_A = math.pi / 10
+
+
 def config_2d_well(n: int = 1025, seed: int = 1) -> Problem:
     """2D n x n nodes, k^2 = 2(E - V) with a Gaussian well (E=2, V0=5, sigma=0.2) and growth
     toward the boundary so that k h <= 0.6, ECS at pi/6, random source on |x|_inf < 0.5."""
     return Problem("2d-well-n%d" % n, 2, n, k2_well_growth(2, n), random_box_source(2, n, seed),
-                   coarsest_n=17, restart=30, tol=1e-8)
+                   coarsest_n=17, restart=30, tol=1e-8, theta_a=WELL_THETA_A)
 
 
 def config_3d_well(n: int = 257, seed: int = 2) -> Problem:
     """3D 7-point problem, n^3 nodes, same k^2 profile in r, ECS on all faces, FGMRES(20)."""
     return Problem("3d-well-n%d" % n, 3, n, k2_well_growth(3, n), random_box_source(3, n, seed),
-                   coarsest_n=9, restart=20, tol=1e-8)
+                   coarsest_n=9, restart=20, tol=1e-8, theta_a=WELL_THETA_A)
 
 
 def config_batch(count: int = 64, seed: int = 3, sizes=(129, 257, 513, 1025)):
@@ -187,14 +193,14 @@ def config_batch(count: int = 64, seed: int = 3, sizes=(129, 257, 513, 1025)):
         src_seed = int(splitmix64(seed + 1000 + i, 1)[0] % np.uint64(2 ** 31))
         out.append(Problem("batch%d-n%d" % (i, n), 2, n, k2_well_growth(2, n, E=E),
                            gaussian_source(2, n, 0.05, src_seed), coarsest_n=17, restart=30, tol=1e-8,
-                           extra={"E": E}))
+                           theta_a=WELL_THETA_A, extra={"E": E}))
     return out
 
 
 def config_adjoint(n: int = 513):
     """2D n x n, k^2 profile with E = 2, Gaussian source (seed 4) and Gaussian probe g (seed 5)."""
     p = Problem("2d-adjoint-n%d" % n, 2, n, k2_well_growth(2, n, E=2.0), gaussian_source(2, n, 0.05, 4),
-                coarsest_n=17, restart=30, tol=1e-10)
+                coarsest_n=17, restart=30, tol=1e-10, theta_a=WELL_THETA_A)
     g = gaussian_source(2, n, 0.05, 5).real.copy()
     p.extra["probe"] = g
     return p

@@ -19,8 +19,10 @@ def mg_params(helm, pc="csg", prec="c128", nu=(2, 2), omega=0.8, smoother="jacob
 
 
 def gpu_handle(helm, P, **kw):
+    """A handle for problem P (its grid, ECS, k^2; its CSG angle unless theta_a is given)."""
     import torch
     n = P.n if hasattr(P.n, "__len__") else [P.n] * P.dim
+    kw.setdefault("theta_a", P.theta_a)
     k2 = torch.from_numpy(np.ascontiguousarray(P.k2)).cuda()
     mg = mg_params(helm, coarsest_n=kw.pop("coarsest_n", P.coarsest_n), **kw)
     r0lo, r0hi = P.layers
@@ -28,7 +30,9 @@ def gpu_handle(helm, P, **kw):
                             lo=[P.lo] * P.dim, hi=[P.hi] * P.dim, mg=mg)
 
 
-def oracle_pair(O, P, pc="csg", theta_a=math.pi / 14, beta=(-1.0, -0.5), re_lambda0=None):
+def oracle_pair(O, P, pc="csg", theta_a=None, beta=(-1.0, -0.5), re_lambda0=None):
+    """The oracle's A and M for problem P (its CSG angle unless theta_a is given)."""
+    theta_a = P.theta_a if theta_a is None else theta_a
     n = P.n if hasattr(P.n, "__len__") else [P.n] * P.dim
     z = [O.contour(n[a], P.lo, P.hi, P.theta, *P.layers) for a in range(P.dim)]
     return O.helmholtz_ops(z, P.k2, pc=pc, theta_a=theta_a, beta=beta, re_lambda0=re_lambda0)

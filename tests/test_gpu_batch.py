@@ -24,7 +24,7 @@ def helm():
 
 def test_batch_matches_single_solves(helm, oracle):
     probs = W.config_batch(count=7, seed=11, sizes=(33, 65, 129))
-    mg = helm.MGParams(kind="csg", prec="c64", gs="df", coarsest_n=17)
+    mg = helm.MGParams(kind="csg", theta_a=probs[0].theta_a, prec="c64", gs="df", coarsest_n=17)
     specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
     b = helm.helm_create_batch(specs, mg=mg)
     rhs = [to_gpu(P.f) for P in probs]
@@ -44,7 +44,7 @@ def test_batch_matches_single_solves(helm, oracle):
 
 def test_batch_reports_per_problem_status(helm):
     probs = W.config_batch(count=3, seed=12, sizes=(33, 65))
-    mg = helm.MGParams(kind="csg", prec="c64", coarsest_n=17)
+    mg = helm.MGParams(kind="csg", theta_a=probs[0].theta_a, prec="c64", coarsest_n=17)
     specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
     b = helm.helm_create_batch(specs, mg=mg)
     rhs = [to_gpu(P.f) for P in probs]
@@ -55,7 +55,7 @@ def test_batch_reports_per_problem_status(helm):
 
 def test_autotuned_batch_matches_single_solves_with_the_same_tuning(helm, tmp_path):
     probs = W.config_batch(count=5, seed=13, sizes=(129, 257))
-    mg = helm.MGParams(kind="csg", prec="c64", gs="df", coarsest_n=17)
+    mg = helm.MGParams(kind="csg", theta_a=probs[0].theta_a, prec="c64", gs="df", coarsest_n=17)
     specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
     b = helm.helm_create_batch(specs, mg=mg)
     chosen = helm.helm_autotune_batch(b, "c64", reps=3, cache=str(tmp_path / "t.json"))
@@ -79,7 +79,7 @@ def test_autotuned_batch_matches_single_solves_with_the_same_tuning(helm, tmp_pa
 
 def lockstep_batch(helm, count, seed, sizes, engine="auto"):
     probs = W.config_batch(count=count, seed=seed, sizes=sizes)
-    mg = helm.MGParams(kind="csg", prec="c64", gs="dcgs2", coarsest_n=17)
+    mg = helm.MGParams(kind="csg", theta_a=probs[0].theta_a, prec="c64", gs="dcgs2", coarsest_n=17)
     specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
     b = helm.helm_create_batch(specs, mg=mg)
     helm.helm_batch_set_engine(b, engine)
@@ -153,7 +153,7 @@ def test_lockstep_status_and_restarts(helm):
 
 def test_lockstep_rejects_other_configurations(helm):
     probs = W.config_batch(count=2, seed=24, sizes=(129,))
-    mg = helm.MGParams(kind="csg", prec="c64", gs="df", coarsest_n=17)
+    mg = helm.MGParams(kind="csg", theta_a=probs[0].theta_a, prec="c64", gs="df", coarsest_n=17)
     specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
     b = helm.helm_create_batch(specs, mg=mg)
     helm.helm_batch_set_engine(b, "lockstep")

@@ -50,7 +50,7 @@ def test_3d_257_well_solve(helm, oracle, tmp_path):
 
 def test_batch_of_64_mixed_sizes(helm, oracle, tmp_path):
     probs = W.config_batch(64)
-    mg = helm.MGParams(kind="csg", prec="c64", gs="dcgs2", coarsest_n=17)
+    mg = helm.MGParams(kind="csg", theta_a=probs[0].theta_a, prec="c64", gs="dcgs2", coarsest_n=17)
     specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
     b = helm.helm_create_batch(specs, mg=mg)
     helm.helm_autotune_batch(b, "c64", reps=3, cache=str(tmp_path / "t.json"))

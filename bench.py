@@ -272,22 +272,22 @@ def run_reference(args):
 # kernels, from the ncu captures summarised under profiles/.  Reported only while the kernel's
 # source file is the one that was captured (same SHA-1); otherwise null.
 NCU_TRAFFIC = {
-    "update_norm": dict(kernel="k_update2_pair", source="paper_1012_4307_gb300/csrc/kernels_gs_df.cu",
-                        sha1="57192057f858d44ef0ecd41b7097a4cc8973d85f", bytes=314946304,
-                        launch="basis slot j = 15, the mean over a restart cycle being 14.5",
-                        profile="profiles/gram_schmidt_dcgs2_kernels_n1025.md"),
-    "mdot": dict(kernel="k_mdot2_pair", source="paper_1012_4307_gb300/csrc/kernels_gs_df.cu",
-                 sha1="57192057f858d44ef0ecd41b7097a4cc8973d85f", bytes=289090816,
-                 launch="basis slot j = 15, the mean over a restart cycle being 14.5",
-                 profile="profiles/gram_schmidt_dcgs2_kernels_n1025.md"),
+    ("2d-well-n1025", "update_norm"): dict(kernel="k_update2_pair", source="paper_1012_4307_gb300/csrc/kernels_gs_df.cu",
+                                           sha1="3201908874ebdc4d692362e7c40857f4b4e58905", bytes=315193600,
+                                           launch="basis slot j = 15, the mean over a restart cycle being 14.5",
+                                           profile="profiles/gram_schmidt_dcgs2_kernels_n1025.md"),
+    ("2d-well-n1025", "mdot"): dict(kernel="k_mdot2_pair", source="paper_1012_4307_gb300/csrc/kernels_gs_df.cu",
+                                    sha1="3201908874ebdc4d692362e7c40857f4b4e58905", bytes=289999104,
+                                    launch="basis slot j = 15, the mean over a restart cycle being 14.5",
+                                    profile="profiles/gram_schmidt_dcgs2_kernels_n1025.md"),
 }
 
 
-def ncu_traffic(kernel_class):
+def ncu_traffic(workload, kernel_class):
     import hashlib
-    t = NCU_TRAFFIC.get(kernel_class)
+    t = NCU_TRAFFIC.get((workload, kernel_class))
     if not t:
-        return None, None
+        return None, "no ncu capture of this kernel class on this workload"
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])
     with open(path, "rb") as fh:
         if hashlib.sha1(fh.read()).hexdigest() != t["sha1"]:
@@ -300,7 +300,7 @@ GS_NAMES = {"dcgs2": "double-FP32 delayed CGS2 on float-pair vectors",
             "fp64": "IEEE FP64 CGS + DGKS"}
 
 
-def roofline_from_profile(prof, peaks, peak_src, sm_max):
+def roofline_from_profile(prof, peaks, peak_src, sm_max, workload=""):
     """Roofline of the dominant kernel class of one profiled solve (eager launches, one event
     pair each): achieved = algorithmic bytes (or FP64 flops) per launch / mean launch time."""
     dname, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
@@ -318,7 +318,7 @@ def roofline_from_profile(prof, peaks, peak_src, sm_max):
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                 "peak_source": "%s hbm_gbs (%s)" % (peak_src, "of measured" if peak_src == "measured" else "of fallback")}
-    traffic, traffic_note = ncu_traffic(dname)
+    traffic, traffic_note = ncu_traffic(workload, dname)
     roof.update({"traffic": traffic, "traffic_note": traffic_note, "kernel_class": dname,
                  "launches_per_solve": d["launches"], "avg_launch_us": avg_s * 1e6,
                  "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
@@ -430,7 +430,7 @@ def run_single(args, workload, steps, warmup, extra=False):
     helm.helm_profile(h, False)
     launches = sum(v["launches"] for v in prof.values())
     sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    roof = roofline_from_profile(prof, peaks, peak_src, sm_max)
+    roof = roofline_from_profile(prof, peaks, peak_src, sm_max, P.name)
     breakdown = breakdown_from_profile(prof, peaks.get("hbm_gbs", 6800.0))
 
     # plain FP64 method on the same problem (FP64 cycle, FP64 Gram-Schmidt), and the mixed
@@ -540,9 +540,21 @@ def run_batch(args, count, steps, warmup, extra=False):
     mg = helm.MGParams(kind="csg", theta_a=probs[0].theta_a, prec="c64", gs=args.gs, coarsest_n=17)
     specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
     b = helm.helm_create_batch(specs, mg=mg)
-    tunings = None if args.no_tune else helm.helm_autotune_batch(b, "c64", cache=helm.default_tuning_cache())
     rhs = [torch.from_numpy(P.f).cuda() for P in probs]
     xs = [torch.zeros_like(r) for r in rhs]
+    if args.ncu_case:
+        # profiling case: the stored tunings, one batch solve capped at ncu_case iterations
+        for i in range(len(probs)):
+            hb = helm.batch_handle(b, i)
+            t = helm.cached_tuning(hb, "c64")
+            if t:
+                helm.helm_set_tuning(hb, t)
+        st = helm.helm_solve_batch(b, rhs, xs, tol=args.tol, restart=30, maxit=args.ncu_case, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "batch-%d" % count, "engine": helm.helm_batch_get_engine(b),
+                          "iterations": [x.iterations for x in st]}), flush=True)
+        return None
+    tunings = None if args.no_tune else helm.helm_autotune_batch(b, "c64", cache=helm.default_tuning_cache())
     unknowns = sum(P.unknowns for P in probs)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -594,8 +606,7 @@ def run_batch(args, count, steps, warmup, extra=False):
                     prof[k][f] += v[f]
     launches = sum(v["launches"] for v in prof.values())
     sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    roof = roofline_from_profile(prof, peaks, peak_src, sm_max)
-    roof["traffic"], roof["traffic_note"] = None, "no ncu capture of the batched workload"
+    roof = roofline_from_profile(prof, peaks, peak_src, sm_max, "batch-%d" % count)
     breakdown = breakdown_from_profile(prof, peaks.get("hbm_gbs", 6800.0))
 
     # end to end: every problem's rhs from pinned host memory, the batch solve, every solution back

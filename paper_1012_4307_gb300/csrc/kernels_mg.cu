@@ -157,6 +157,73 @@ __global__ void __launch_bounds__(BX *BY) k_jacobi(OpView<R> o, R omega, const C
     }
 }
 
+// 3D omega-Jacobi: k_jacobi's arithmetic in the same order, with the x and y coefficient
+// triples loaded once per thread, the (z - 1, z, z + 1) column in registers, and the next plane's
+// operands (four in-plane neighbours, z + 2, b, k^2) loaded while this plane is computed.
+template <typename R, typename CB, bool ZERO>
+__global__ void __launch_bounds__(BX *BY) k_jacobi3(OpView<R> o, R omega, const CB *__restrict__ b,
+                                                    const typename CT<R>::T *__restrict__ u,
+                                                    typename CT<R>::T *__restrict__ un) {
+    pdl_enter();
+    typedef typename CT<R>::T C;
+    constexpr int DIM = 3;
+    INTERIOR_IJ(o);
+    const size_t sy = (size_t)o.nx;
+    const C cwx = __ldg(&o.cx[3 * i]), ccx = __ldg(&o.cx[3 * i + 1]), cex = __ldg(&o.cx[3 * i + 2]);
+    const C cwy = __ldg(&o.cy[3 * j]), ccy = __ldg(&o.cy[3 * j + 1]), cey = __ldg(&o.cy[3 * j + 2]);
+    C bq = to_c(b[p], R());
+    R kq = o.k2[p];
+    if (ZERO) {
+        const C dxy = cadd(ccx, ccy);
+        for (int k = k0; k < k1; k++, p += sz) {
+            C bn = bq;
+            R kn = kq;
+            if (k + 1 < k1) {
+                bn = to_c(b[p + sz], R());
+                kn = o.k2[p + sz];
+            }
+            const C d = cadd(cadd(dxy, cadd(cscale(o.bk, kq), o.c)), __ldg(&o.cz[3 * k + 1]));
+            un[p] = cscale(cmul(bq, cinv(d)), omega);
+            bq = bn;
+            kq = kn;
+        }
+        return;
+    }
+    C xm = u[p - sz], xc = u[p], xp = u[p + sz];
+    C xw = u[p - 1], xe = u[p + 1], xs = u[p - sy], xn = u[p + sy];
+    for (int k = k0; k < k1; k++, p += sz) {
+        C xw2 = xw, xe2 = xe, xs2 = xs, xn2 = xn, xp2 = xp, bn = bq;
+        R kn = kq;
+        if (k + 1 < k1) {
+            const size_t q = p + sz;
+            xw2 = u[q - 1];
+            xe2 = u[q + 1];
+            xs2 = u[q - sy];
+            xn2 = u[q + sy];
+            xp2 = u[q + sz];
+            bn = to_c(b[q], R());
+            kn = o.k2[q];
+        }
+        C acc = cmul(cwx, xw);
+        acc = cfma(cex, xe, acc);
+        C d = ccx;
+        acc = cfma(cwy, xs, acc);
+        acc = cfma(cey, xn, acc);
+        d = cadd(d, ccy);
+        const C czw = __ldg(&o.cz[3 * k]), czc = __ldg(&o.cz[3 * k + 1]), cze = __ldg(&o.cz[3 * k + 2]);
+        acc = cfma(czw, xm, acc);
+        acc = cfma(cze, xp, acc);
+        d = cadd(d, czc);
+        d = cadd(d, cadd(cscale(o.bk, kq), o.c));
+        const C mu = cfma(d, xc, acc);
+        const C res = csub(bq, mu);
+        un[p] = cadd(xc, cscale(cmul(res, cinv(d)), omega));
+        xm = xc;
+        xc = xp;
+        xw = xw2; xe = xe2; xs = xs2; xn = xn2; xp = xp2; bq = bn; kq = kn;
+    }
+}
+
 // one colour of omega-red-black Jacobi, in place: threads map to every other x node.
 template <typename R, int DIM, typename CB>
 __global__ void __launch_bounds__(BX *BY) k_rb(OpView<R> o, R omega, const CB *__restrict__ b, typename CT<R>::T *u, int colour) {
@@ -416,12 +483,27 @@ __global__ void __launch_bounds__(BX *BY) k_prolong3(int nx, int ny, int nz, con
     const size_t csy = (size_t)ncx, csz = (size_t)ncx * ncy;
     const size_t c00 = (size_t)(i >> 1) + csy * (j >> 1), c10 = (size_t)((i + 1) >> 1) + csy * (j >> 1);
     const size_t c01 = (size_t)(i >> 1) + csy * ((j + 1) >> 1), c11 = (size_t)((i + 1) >> 1) + csy * ((j + 1) >> 1);
-    for (int k = k0; k < k1; k++) {
-        const size_t za = csz * (k >> 1), zb = csz * ((k + 1) >> 1);
-        const C s0 = cadd(cadd(ec[c00 + za], ec[c10 + za]), cadd(ec[c01 + za], ec[c11 + za]));
-        const C s1 = cadd(cadd(ec[c00 + zb], ec[c10 + zb]), cadd(ec[c01 + zb], ec[c11 + zb]));
-        const size_t p = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k);
-        uf[p] = cadd(uf[p], cscale(cadd(s0, s1), R(0.125)));
+    // S(c): the four in-plane corners' sum on coarse plane c; fine plane k takes S(k >> 1) and
+    // S((k + 1) >> 1), so every coarse plane is summed once and the next one is loaded while the
+    // current fine plane is written
+    auto corner_sum = [&](int c) {
+        const size_t z = csz * c;
+        return cadd(cadd(ec[c00 + z], ec[c10 + z]), cadd(ec[c01 + z], ec[c11 + z]));
+    };
+    C sa = corner_sum(k0 >> 1), sb = corner_sum((k0 + 1) >> 1);
+    size_t p = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k0);
+    C uq = uf[p];
+    for (int k = k0; k < k1; k++, p += (size_t)nx * ny) {
+        C sn = sb, un = uq;
+        if (k + 1 < k1) {
+            un = uf[p + (size_t)nx * ny];
+            if (((k + 2) >> 1) != ((k + 1) >> 1)) sn = corner_sum((k + 2) >> 1);
+        }
+        uf[p] = cadd(uq, cscale(cadd(sa, sb), R(0.125)));
+        // next fine plane: (k + 1) >> 1 is this plane's upper coarse plane
+        sa = sb;
+        sb = sn;
+        uq = un;
     }
 }
 
@@ -1014,10 +1096,10 @@ cudaError_t launch_jacobi(const DevOp<R> &op, int dim, R omega, const CB *bb, co
                           typename CT<R>::T *u_out, cudaStream_t s) {
     dim3 g = grid_for(op.n, dim), b(BX, BY);
     if (u_in == nullptr) {
-        if (dim == 3) launch_pdl(k_jacobi<R, 3, CB, true>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
+        if (dim == 3) launch_pdl(k_jacobi3<R, CB, true>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
         else launch_pdl(k_jacobi<R, 2, CB, true>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
     } else {
-        if (dim == 3) launch_pdl(k_jacobi<R, 3, CB, false>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
+        if (dim == 3) launch_pdl(k_jacobi3<R, CB, false>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
         else launch_pdl(k_jacobi<R, 2, CB, false>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
     }
     return cudaGetLastError();

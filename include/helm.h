@@ -49,7 +49,10 @@ typedef enum {
     HELM_ERR_NOCONV = 4,     /* iteration cap reached before the tolerance              */
     HELM_ERR_BREAKDOWN = 5,  /* Krylov breakdown (Bi-CGSTAB rho = 0, omega = 0, ...)    */
     HELM_ERR_NONFINITE = 6,  /* a residual norm became NaN or Inf                       */
-    HELM_ERR_TIMEOUT = 7     /* a device-side wait gave up after its iteration limit    */
+    HELM_ERR_TIMEOUT = 7     /* reserved for a device-side wait that gives up; no entry */
+                             /* point returns it: the library's kernels never spin-wait  */
+                             /* (phases are ordered by the stream, thread-block clusters */
+                             /* by hardware barriers, last-block reductions by atomics)  */
 } helm_status;
 
 typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_prec;

@@ -201,44 +201,60 @@ __global__ void __launch_bounds__(NT) k_combine_df(size_t n, const float2 *__res
 // Complex Givens rotations G = [c s; -conj(s) c] (c real) on column j of the Hessenberg
 // matrix (column-major, leading dimension ldh); see Saad, Iterative Methods for Sparse Linear
 // Systems, Section 6.5.9 for the real case.
+// Called by one warp: the lanes stage column j of H (j + 2 entries) and the earlier rotations in
+// shared memory, lane 0 applies the rotations in order and forms the new one, the lanes write the
+// column back.  The arithmetic is that of a single thread walking the column in global memory.
 __device__ __forceinline__ void givens_body(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g,
                                             const double2 *fnorm_dev, double *est) {
-    const double fnorm = fnorm_dev->x;
+    __shared__ double2 colS[66], snS[64];
+    __shared__ double csS[64];
+    const int lane = threadIdx.x & 31;
     double2 *col = H + (size_t)ldh * j;
-    for (int i = 0; i < j; i++) {
-        const double2 a = col[i], b = col[i + 1];
-        const double c = cs[i];
-        const double2 s = sn[i];
-        col[i] = cadd(cscale(a, c), cmul(s, b));
-        col[i + 1] = csub(cscale(b, c), cmul(make_double2(s.x, -s.y), a));
+    for (int i = lane; i <= j + 1; i += 32) colS[i] = col[i];
+    for (int i = lane; i < j; i += 32) {
+        csS[i] = cs[i];
+        snS[i] = sn[i];
     }
-    const double2 a = col[j], b = col[j + 1];
-    const double na = hypot(a.x, a.y);
-    const double t = hypot(na, hypot(b.x, b.y));
-    double c;
-    double2 s;
-    if (na == 0.0) {
-        c = 0.0;
-        s = make_double2(1.0, 0.0);
-    } else {
-        c = na / t;
-        const double2 ua = make_double2(a.x / na, a.y / na);
-        s = cscale(cmul(ua, make_double2(b.x, -b.y)), 1.0 / t);
+    __syncwarp();
+    if (lane == 0) {
+        const double fnorm = fnorm_dev->x;
+        for (int i = 0; i < j; i++) {
+            const double2 a = colS[i], b = colS[i + 1];
+            const double c = csS[i];
+            const double2 s = snS[i];
+            colS[i] = cadd(cscale(a, c), cmul(s, b));
+            colS[i + 1] = csub(cscale(b, c), cmul(make_double2(s.x, -s.y), a));
+        }
+        const double2 a = colS[j], b = colS[j + 1];
+        const double na = hypot(a.x, a.y);
+        const double t = hypot(na, hypot(b.x, b.y));
+        double c;
+        double2 s;
+        if (na == 0.0) {
+            c = 0.0;
+            s = make_double2(1.0, 0.0);
+        } else {
+            c = na / t;
+            const double2 ua = make_double2(a.x / na, a.y / na);
+            s = cscale(cmul(ua, make_double2(b.x, -b.y)), 1.0 / t);
+        }
+        cs[j] = c;
+        sn[j] = s;
+        colS[j] = cadd(cscale(a, c), cmul(s, b));
+        colS[j + 1] = make_double2(0.0, 0.0);
+        const double2 gj = g[j];
+        g[j + 1] = cscale(cmul(make_double2(-s.x, s.y), gj), 1.0);
+        g[j] = cscale(gj, c);
+        est[j] = hypot(g[j + 1].x, g[j + 1].y) / fnorm;
     }
-    cs[j] = c;
-    sn[j] = s;
-    col[j] = cadd(cscale(a, c), cmul(s, b));
-    col[j + 1] = make_double2(0.0, 0.0);
-    const double2 gj = g[j];
-    g[j + 1] = cscale(cmul(make_double2(-s.x, s.y), gj), 1.0);
-    g[j] = cscale(gj, c);
-    est[j] = hypot(g[j + 1].x, g[j + 1].y) / fnorm;
+    __syncwarp();
+    for (int i = lane; i <= j + 1; i += 32) col[i] = colS[i];
 }
 
 __global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm_dev,
                          double *est) {
     pdl_enter();
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (threadIdx.x >= 32 || blockIdx.x != 0) return;
     givens_body(H, ldh, j, cs, sn, g, fnorm_dev, est);
 }
 
@@ -247,13 +263,13 @@ __global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, do
 __global__ void k_givens_b(const BVec *__restrict__ tab, int j, double *out) {
     pdl_enter();
     const BVec &P = tab[blockIdx.z];
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;
     if (*P.active == 0) {
-        out[blockIdx.z] = -1.0;
+        if (threadIdx.x == 0) out[blockIdx.z] = -1.0;
         return;
     }
     givens_body(P.H, P.ldh, j, P.cs, P.sn, P.g, P.fnorm, P.est);
-    out[blockIdx.z] = P.est[j];
+    if (threadIdx.x == 0) out[blockIdx.z] = P.est[j];
 }
 
 // The reduction of the two-vector inner-product pass (block v sums value v of the partials in

@@ -160,14 +160,19 @@ __global__ void __launch_bounds__(BX *BY) k_jacobi(OpView<R> o, R omega, const C
 // 3D omega-Jacobi: k_jacobi's arithmetic in the same order, with the x and y coefficient
 // triples loaded once per thread, the (z - 1, z, z + 1) column in registers, and the next plane's
 // operands (four in-plane neighbours, z + 2, b, k^2) loaded while this plane is computed.
-template <typename R, typename CB, bool ZERO>
+// KC: fine planes per thread (shorter chunks on small grids give more blocks).
+template <typename R, typename CB, bool ZERO, int KC>
 __global__ void __launch_bounds__(BX *BY) k_jacobi3(OpView<R> o, R omega, const CB *__restrict__ b,
                                                     const typename CT<R>::T *__restrict__ u,
                                                     typename CT<R>::T *__restrict__ un) {
     pdl_enter();
     typedef typename CT<R>::T C;
-    constexpr int DIM = 3;
-    INTERIOR_IJ(o);
+    const int i = blockIdx.x * BX + threadIdx.x + 1;
+    const int j = blockIdx.y * BY + threadIdx.y + 1;
+    if (i > o.nx - 2 || j > o.ny - 2) return;
+    const int k0 = blockIdx.z * KC + 1, k1 = min(k0 + KC, o.nz - 1);
+    const size_t sz = (size_t)o.nx * o.ny;
+    size_t p = (size_t)i + (size_t)o.nx * ((size_t)j + (size_t)o.ny * k0);
     const size_t sy = (size_t)o.nx;
     const C cwx = __ldg(&o.cx[3 * i]), ccx = __ldg(&o.cx[3 * i + 1]), cex = __ldg(&o.cx[3 * i + 2]);
     const C cwy = __ldg(&o.cy[3 * j]), ccy = __ldg(&o.cy[3 * j + 1]), cey = __ldg(&o.cy[3 * j + 2]);
@@ -313,173 +318,125 @@ __global__ void __launch_bounds__(BX *BY) k_prolong_add(int nx, int ny, int nz, 
 }
 
 // 3D residual + full weighting, each fine residual computed once.  A block owns R3_TX x R3_TY
-// coarse nodes in (x, y) and R3_KC coarse planes; it marches the fine planes 2K - 1 .. 2K + 1 of
-// its coarse planes with a window of four u planes (the region around its fine residual region,
-// one node of halo) and a window of four residual planes in shared memory.  Phase z computes the
-// residual on fine plane z (from u planes z - 1 .. z + 1) and, for z = 2K + 2, applies
-// (1,2,1)^3 / 64 to residual planes 2K - 1 .. 2K + 1 for coarse plane K; the four-plane windows
-// let both run in one phase, one barrier per fine plane.  The phase is software-pipelined: it
-// first issues the global loads of the next phases (u plane z + 2, and b, k^2 of plane z + 1)
-// into registers, computes from shared memory while they are in flight, then stores the u
-// values.  Fine nodes outside the grid's interior hold zero residuals.  Same arithmetic as
-// k_residual_restrict.
-constexpr int R3_TX = 16, R3_TY = 8, R3_KC = 8, R3_NT = 256;
-constexpr int R3_FW = 2 * R3_TX + 1, R3_FH = 2 * R3_TY + 1;  // fine residual region
-constexpr int R3_UW = R3_FW + 2, R3_UH = R3_FH + 2;          // u window region
-constexpr int R3_UPT = (R3_UW * R3_UH + R3_NT - 1) / R3_NT;  // u values per thread and plane
-constexpr int R3_RPT = (R3_FW * R3_FH + R3_NT - 1) / R3_NT;  // residuals per thread and plane
+// coarse nodes in (x, y) and kc coarse planes (at most R3_KC); one thread per fine node of the region those
+// coarse nodes weigh ((2 R3_TX + 1) x (2 R3_TY + 1)) marches the block's fine planes
+// 2 K0 - 1 .. 2 K1 - 1 like k_jacobi3 (coefficients in registers, the u column (z - 1, z, z + 1)
+// in registers, the next plane's operands loaded while this plane is computed) and stores its
+// residual in a shared plane (two buffers); after one barrier per plane the coarse nodes' threads
+// apply (1,2,1)/4 in x and y from the shared plane and accumulate (1,2,1)/4 in z in registers:
+// an odd fine plane 2K + 1 completes coarse plane K and starts K + 1.  Fine nodes outside the
+// grid's interior hold zero residuals.  Same arithmetic as k_residual_restrict, with the weights
+// applied per axis.
+constexpr int R3_TX = 16, R3_TY = 8, R3_KC = 8;
+constexpr int R3_FW = 2 * R3_TX + 1, R3_FH = 2 * R3_TY + 1;  // fine region
+constexpr int R3_NT = ((R3_FW * R3_FH + 31) / 32) * 32;       // threads: one per region node
 template <typename R> constexpr size_t r3_smem_bytes() {
-    return (size_t)4 * (R3_UW * R3_UH + R3_FW * R3_FH) * sizeof(typename CT<R>::T);
+    return (size_t)2 * R3_FW * R3_FH * sizeof(typename CT<R>::T);
 }
 
 template <typename R, typename CB>
-__global__ void __launch_bounds__(R3_NT, 3) k_resrestrict3(OpView<R> o, const CB *__restrict__ b,
-                                                        const typename CT<R>::T *__restrict__ u,
-                                                        typename CT<R>::T *__restrict__ rc, int ncx, int ncy, int ncz) {
+__global__ void __launch_bounds__(R3_NT, sizeof(R) == sizeof(float) ? 2 : 1)
+    k_resrestrict3(OpView<R> o, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
+                   typename CT<R>::T *__restrict__ rc, int ncx, int ncy, int ncz, int kc) {
     pdl_enter();
     typedef typename CT<R>::T C;
     extern __shared__ __align__(16) unsigned char r3_smem[];
-    C(*us)[R3_UH][R3_UW] = reinterpret_cast<C(*)[R3_UH][R3_UW]>(r3_smem);
-    C(*rs)[R3_FH][R3_FW] = reinterpret_cast<C(*)[R3_FH][R3_FW]>(r3_smem + (size_t)4 * R3_UW * R3_UH * sizeof(C));
+    C(*rbuf)[R3_FH][R3_FW] = reinterpret_cast<C(*)[R3_FH][R3_FW]>(r3_smem);
     const int nx = o.nx, ny = o.ny;
     const int I0 = 1 + blockIdx.x * R3_TX, J0 = 1 + blockIdx.y * R3_TY;
-    const int K0 = 1 + blockIdx.z * R3_KC, K1 = min(K0 + R3_KC, ncz - 1);
-    const int X0 = 2 * I0 - 1, Y0 = 2 * J0 - 1;  // first fine node of the residual region
-    const size_t sxy = (size_t)nx * ny;
+    const int K0 = 1 + blockIdx.z * kc, K1 = min(K0 + kc, ncz - 1);
+    const int t = threadIdx.x, lx = t % R3_FW, ly = t / R3_FW;
+    const int x = 2 * I0 - 1 + lx, y = 2 * J0 - 1 + ly;
+    // region nodes inside the grid's interior compute residuals; the others hold zeros
+    const bool res = t < R3_FW * R3_FH && x <= nx - 2 && y <= ny - 2;
+    const size_t sy = (size_t)nx, sz = (size_t)nx * ny;
+    const int zs = 2 * K0 - 1, ze = 2 * K1 - 1;
     const C zero = mk(R(0), R(0));
-    // this thread's u-window nodes (global offset in a plane, or -1 outside the grid) and
-    // residual-region nodes (offset, or -1 outside the interior)
-    int uoff[R3_UPT], roff[R3_RPT];  // a plane has at most 2^16 x 2^16 nodes: 32-bit offsets
-#pragma unroll
-    for (int t = 0; t < R3_UPT; t++) {
-        const int q = threadIdx.x + t * R3_NT, qx = q % R3_UW, qy = q / R3_UW, x = X0 - 1 + qx, y = Y0 - 1 + qy;
-        uoff[t] = (q < R3_UW * R3_UH && x < nx && y < ny) ? x + nx * y : -1;
+    C cwx = zero, ccx = zero, cex = zero, cwy = zero, ccy = zero, cey = zero;
+    C xm = zero, xc = zero, xp = zero, xw = zero, xe = zero, xs = zero, xn = zero, bq = zero;
+    R kq = R(0);
+    size_t p = (size_t)x + sy * y + sz * zs;
+    if (res) {
+        cwx = __ldg(&o.cx[3 * x]); ccx = __ldg(&o.cx[3 * x + 1]); cex = __ldg(&o.cx[3 * x + 2]);
+        cwy = __ldg(&o.cy[3 * y]); ccy = __ldg(&o.cy[3 * y + 1]); cey = __ldg(&o.cy[3 * y + 2]);
+        xm = u[p - sz]; xc = u[p]; xp = u[p + sz];
+        xw = u[p - 1]; xe = u[p + 1]; xs = u[p - sy]; xn = u[p + sy];
+        bq = to_c(b[p], R());
+        kq = o.k2[p];
     }
-#pragma unroll
-    for (int t = 0; t < R3_RPT; t++) {
-        const int q = threadIdx.x + t * R3_NT, qx = q % R3_FW, qy = q / R3_FW, x = X0 + qx, y = Y0 + qy;
-        roff[t] = (q < R3_FW * R3_FH && x <= nx - 2 && y <= ny - 2) ? x + nx * y : -1;
-    }
-    auto fetch_u = [&](int z, C (&v)[R3_UPT]) {
-#pragma unroll
-        for (int t = 0; t < R3_UPT; t++) v[t] = uoff[t] >= 0 ? u[(size_t)uoff[t] + sxy * z] : zero;
-    };
-    auto put_u = [&](int z, const C (&v)[R3_UPT]) {
-        C *dst = &us[z & 3][0][0];
-#pragma unroll
-        for (int t = 0; t < R3_UPT; t++) {
-            const int q = threadIdx.x + t * R3_NT;
-            if (q < R3_UW * R3_UH) dst[q] = v[t];
-        }
-    };
-    auto fetch_bk = [&](int z, C (&bv)[R3_RPT], R (&kv)[R3_RPT]) {
-#pragma unroll
-        for (int t = 0; t < R3_RPT; t++) {
-            bv[t] = zero;
-            kv[t] = R(0);
-            if (roff[t] >= 0) {
-                const size_t p = (size_t)roff[t] + sxy * z;
-                bv[t] = to_c(b[p], R());
-                kv[t] = o.k2[p];
+    // the coarse node of this thread (threads below R3_TX * R3_TY), and its running z sum
+    const int cx = t % R3_TX, cy = t / R3_TX, I = I0 + cx, J = J0 + cy;
+    const bool own = t < R3_TX * R3_TY && I <= ncx - 2 && J <= ncy - 2;
+    C acc = zero;
+    for (int z = zs; z <= ze; z++, p += sz) {
+        if (res) {
+            C xw2 = xw, xe2 = xe, xs2 = xs, xn2 = xn, xp2 = xp, bn = bq;
+            R kn = kq;
+            if (z < ze) {
+                const size_t q = p + sz;
+                xw2 = u[q - 1];
+                xe2 = u[q + 1];
+                xs2 = u[q - sy];
+                xn2 = u[q + sy];
+                xp2 = u[q + sz];
+                bn = to_c(b[q], R());
+                kn = o.k2[q];
             }
-        }
-    };
-    auto residual = [&](int z, const C (&bv)[R3_RPT], const R (&kv)[R3_RPT]) {
-        const C(*um)[R3_UW] = us[(z - 1) & 3];
-        const C(*uc)[R3_UW] = us[z & 3];
-        const C(*up)[R3_UW] = us[(z + 1) & 3];
-        C *dst = &rs[z & 3][0][0];
-        const C czw = o.cz[3 * z], czc = o.cz[3 * z + 1], cze = o.cz[3 * z + 2];
-#pragma unroll
-        for (int t = 0; t < R3_RPT; t++) {
-            const int q = threadIdx.x + t * R3_NT;
-            if (q >= R3_FW * R3_FH) continue;
-            const int qx = q % R3_FW, qy = q / R3_FW;
-            C r = zero;
-            if (roff[t] >= 0) {
-                const int x = X0 + qx, y = Y0 + qy, lx = qx + 1, ly = qy + 1;
-                C cw = __ldg(&o.cx[3 * x]), cc = __ldg(&o.cx[3 * x + 1]), ce = __ldg(&o.cx[3 * x + 2]);
-                C acc = cmul(cw, uc[ly][lx - 1]);
-                acc = cfma(ce, uc[ly][lx + 1], acc);
-                C d = cc;
-                cw = __ldg(&o.cy[3 * y]); cc = __ldg(&o.cy[3 * y + 1]); ce = __ldg(&o.cy[3 * y + 2]);
-                acc = cfma(cw, uc[ly - 1][lx], acc);
-                acc = cfma(ce, uc[ly + 1][lx], acc);
-                d = cadd(d, cc);
-                acc = cfma(czw, um[ly][lx], acc);
-                acc = cfma(cze, up[ly][lx], acc);
-                d = cadd(d, czc);
-                d = cadd(d, cadd(cscale(o.bk, kv[t]), o.c));
-                r = csub(bv[t], cfma(d, uc[ly][lx], acc));
-            }
-            dst[q] = r;
-        }
-    };
-    auto weigh = [&](int K) {
-        const C(*r0)[R3_FW] = rs[(2 * K - 1) & 3];
-        const C(*r1)[R3_FW] = rs[(2 * K) & 3];
-        const C(*r2)[R3_FW] = rs[(2 * K + 1) & 3];
-        for (int q = threadIdx.x; q < R3_TX * R3_TY; q += R3_NT) {
-            const int cx = q % R3_TX, cy = q / R3_TX, I = I0 + cx, J = J0 + cy;
-            if (I > ncx - 2 || J > ncy - 2) continue;
-            const int fx = 2 * cx, fy = 2 * cy;  // region indices of fine nodes 2I - 1, 2J - 1
-            // (1,2,1)/4 along x, then y, then z
-            C pl[3];
-#pragma unroll
-            for (int t = 0; t < 3; t++) {
-                const C(*rr)[R3_FW] = t == 0 ? r0 : (t == 1 ? r1 : r2);
-                C a[3];
-#pragma unroll
-                for (int dy = 0; dy < 3; dy++) {
-                    const C *row = &rr[fy + dy][fx];
-                    a[dy] = cadd(cadd(row[0], row[2]), cscale(row[1], R(2)));
-                }
-                pl[t] = cadd(cadd(a[0], a[2]), cscale(a[1], R(2)));
-            }
-            const C v = cadd(cadd(pl[0], pl[2]), cscale(pl[1], R(2)));
-            rc[(size_t)I + (size_t)ncx * ((size_t)J + (size_t)ncy * K)] = cscale(v, R(1.0 / 64.0));
-        }
-    };
-    const int zs = 2 * K0 - 1, ze = 2 * K1 - 1;  // fine planes of the residual
-    C uv[R3_UPT], bcur[R3_RPT], bnext[R3_RPT];
-    R kcur[R3_RPT], knext[R3_RPT];
-    for (int z = zs - 1; z <= zs + 1; z++) {
-        fetch_u(z, uv);
-        put_u(z, uv);
-    }
-    fetch_bk(zs, bcur, kcur);
-    __syncthreads();
-    for (int z = zs; z <= ze + 1; z++) {
-        const bool more_u = z + 2 <= ze + 1, more_r = z + 1 <= ze;
-        if (more_u) fetch_u(z + 2, uv);
-        if (more_r) fetch_bk(z + 1, bnext, knext);
-        if (z <= ze) residual(z, bcur, kcur);
-        if ((z & 1) == 0 && z >= zs + 3) weigh((z - 2) / 2);
-        if (more_u) put_u(z + 2, uv);
-        if (more_r) {
-#pragma unroll
-            for (int t = 0; t < R3_RPT; t++) {
-                bcur[t] = bnext[t];
-                kcur[t] = knext[t];
-            }
+            C a2 = cmul(cwx, xw);
+            a2 = cfma(cex, xe, a2);
+            C d = ccx;
+            a2 = cfma(cwy, xs, a2);
+            a2 = cfma(cey, xn, a2);
+            d = cadd(d, ccy);
+            const C czw = __ldg(&o.cz[3 * z]), czc = __ldg(&o.cz[3 * z + 1]), cze = __ldg(&o.cz[3 * z + 2]);
+            a2 = cfma(czw, xm, a2);
+            a2 = cfma(cze, xp, a2);
+            d = cadd(d, czc);
+            d = cadd(d, cadd(cscale(o.bk, kq), o.c));
+            rbuf[z & 1][ly][lx] = csub(bq, cfma(d, xc, a2));
+            xm = xc;
+            xc = xp;
+            xw = xw2; xe = xe2; xs = xs2; xn = xn2; xp = xp2; bq = bn; kq = kn;
+        } else if (t < R3_FW * R3_FH) {
+            rbuf[z & 1][ly][lx] = zero;
         }
         __syncthreads();
+        if (own) {
+            // (1,2,1)/4 along x on the three fine rows 2J - 1 .. 2J + 1, then along y
+            const C(*rr)[R3_FW] = rbuf[z & 1];
+            const int fx = 2 * cx, fy = 2 * cy;
+            C a[3];
+#pragma unroll
+            for (int dy = 0; dy < 3; dy++) {
+                const C *row = &rr[fy + dy][fx];
+                a[dy] = cadd(cadd(row[0], row[2]), cscale(row[1], R(2)));
+            }
+            const C v = cadd(cadd(a[0], a[2]), cscale(a[1], R(2)));
+            if (z & 1) {
+                // fine plane 2K + 1 (K = (z - 1) / 2) completes coarse plane K and starts K + 1
+                const int K = (z - 1) >> 1;
+                if (K >= K0) rc[(size_t)I + (size_t)ncx * ((size_t)J + (size_t)ncy * K)] = cscale(cadd(acc, v), R(1.0 / 64.0));
+                acc = v;
+            } else {
+                acc = cadd(acc, cscale(v, R(2)));
+            }
+        }
     }
 }
 
 // 3D prolongation + correction in closed form: uf[p] += 1/8 of the sum of ec at the eight corners
 // (floor / ceil of i/2, j/2, k/2), coincident corners repeated, i.e. the average over the distinct
-// coarse nodes of k_prolong_add.  Each thread marches KCHUNK fine planes.
+// coarse nodes of k_prolong_add.  Each thread marches kc fine planes.
 template <typename R>
 __global__ void __launch_bounds__(BX *BY) k_prolong3(int nx, int ny, int nz, const typename CT<R>::T *__restrict__ ec,
-                                                     typename CT<R>::T *__restrict__ uf) {
+                                                     typename CT<R>::T *__restrict__ uf, int kc) {
     pdl_enter();
     typedef typename CT<R>::T C;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
     if (i > nx - 2 || j > ny - 2) return;
     const int ncx = (nx + 1) / 2, ncy = (ny + 1) / 2;
-    const int k0 = blockIdx.z * KCHUNK + 1, k1 = min(k0 + KCHUNK, nz - 1);
+    const int k0 = blockIdx.z * kc + 1, k1 = min(k0 + kc, nz - 1);
     const size_t csy = (size_t)ncx, csz = (size_t)ncx * ncy;
     const size_t c00 = (size_t)(i >> 1) + csy * (j >> 1), c10 = (size_t)((i + 1) >> 1) + csy * (j >> 1);
     const size_t c01 = (size_t)(i >> 1) + csy * ((j + 1) >> 1), c11 = (size_t)((i + 1) >> 1) + csy * ((j + 1) >> 1);
@@ -1067,6 +1024,14 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs<R> A, int gf,
     });
 }
 
+// Planes per thread of a 3D z-marching kernel: kmax, halved while the grid would have fewer than
+// `target` blocks (small levels: more, shorter chains instead of a few long ones).
+static int z_chunk(size_t tiles_xy, int planes, int kmax, size_t target) {
+    int kc = kmax;
+    while (kc > 1 && tiles_xy * cdiv(planes, kc) < target) kc /= 2;
+    return kc;
+}
+
 dim3 grid_for(const int n[3], int dim) {
     return dim3(cdiv(n[0] - 2, BX), cdiv(n[1] - 2, BY), dim == 3 ? cdiv(n[2] - 2, KCHUNK) : 1);
 }
@@ -1095,12 +1060,28 @@ template <typename R, typename CB>
 cudaError_t launch_jacobi(const DevOp<R> &op, int dim, R omega, const CB *bb, const typename CT<R>::T *u_in,
                           typename CT<R>::T *u_out, cudaStream_t s) {
     dim3 g = grid_for(op.n, dim), b(BX, BY);
-    if (u_in == nullptr) {
-        if (dim == 3) launch_pdl(k_jacobi3<R, CB, true>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
-        else launch_pdl(k_jacobi<R, 2, CB, true>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
+    if (dim == 3) {
+        const int kc = z_chunk((size_t)g.x * g.y, op.n[2] - 2, KCHUNK, 152 * 10);
+        g.z = cdiv(op.n[2] - 2, kc);
+        if (u_in == nullptr) {
+            switch (kc) {
+            case 8: launch_pdl(k_jacobi3<R, CB, true, 8>, g, b, 0, s, view(op), omega, bb, u_in, u_out); break;
+            case 4: launch_pdl(k_jacobi3<R, CB, true, 4>, g, b, 0, s, view(op), omega, bb, u_in, u_out); break;
+            case 2: launch_pdl(k_jacobi3<R, CB, true, 2>, g, b, 0, s, view(op), omega, bb, u_in, u_out); break;
+            default: launch_pdl(k_jacobi3<R, CB, true, 1>, g, b, 0, s, view(op), omega, bb, u_in, u_out); break;
+            }
+        } else {
+            switch (kc) {
+            case 8: launch_pdl(k_jacobi3<R, CB, false, 8>, g, b, 0, s, view(op), omega, bb, u_in, u_out); break;
+            case 4: launch_pdl(k_jacobi3<R, CB, false, 4>, g, b, 0, s, view(op), omega, bb, u_in, u_out); break;
+            case 2: launch_pdl(k_jacobi3<R, CB, false, 2>, g, b, 0, s, view(op), omega, bb, u_in, u_out); break;
+            default: launch_pdl(k_jacobi3<R, CB, false, 1>, g, b, 0, s, view(op), omega, bb, u_in, u_out); break;
+            }
+        }
+    } else if (u_in == nullptr) {
+        launch_pdl(k_jacobi<R, 2, CB, true>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
     } else {
-        if (dim == 3) launch_pdl(k_jacobi3<R, CB, false>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
-        else launch_pdl(k_jacobi<R, 2, CB, false>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
+        launch_pdl(k_jacobi<R, 2, CB, false>, g, b, 0, s, view(op), omega, bb, u_in, u_out);
     }
     return cudaGetLastError();
 }
@@ -1126,8 +1107,10 @@ cudaError_t launch_residual_restrict(const DevOp<R> &op, int dim, const CB *bb, 
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        dim3 g(cdiv(nc[0] - 2, R3_TX), cdiv(nc[1] - 2, R3_TY), cdiv(nc[2] - 2, R3_KC));
-        launch_pdl(k_resrestrict3<R, CB>, g, R3_NT, smem, s, view(op), bb, u, rc, nc[0], nc[1], nc[2]);
+        dim3 g(cdiv(nc[0] - 2, R3_TX), cdiv(nc[1] - 2, R3_TY), 1);
+        const int kc = z_chunk((size_t)g.x * g.y, nc[2] - 2, R3_KC, 152 * 4);
+        g.z = cdiv(nc[2] - 2, kc);
+        launch_pdl(k_resrestrict3<R, CB>, g, R3_NT, smem, s, view(op), bb, u, rc, nc[0], nc[1], nc[2], kc);
         return cudaGetLastError();
     }
     dim3 g = grid_for(nc, dim), b(BX, BY);
@@ -1140,8 +1123,13 @@ template <typename R>
 cudaError_t launch_prolong_add(const int nf[3], int dim, const typename CT<R>::T *ec, typename CT<R>::T *uf,
                                cudaStream_t s) {
     dim3 g = grid_for(nf, dim), b(BX, BY);
-    if (dim == 3) launch_pdl(k_prolong3<R>, g, b, 0, s, nf[0], nf[1], nf[2], ec, uf);
-    else launch_pdl(k_prolong_add<R, 2>, g, b, 0, s, nf[0], nf[1], 1, ec, uf);
+    if (dim == 3) {
+        const int kc = z_chunk((size_t)g.x * g.y, nf[2] - 2, KCHUNK, 152 * 10);
+        g.z = cdiv(nf[2] - 2, kc);
+        launch_pdl(k_prolong3<R>, g, b, 0, s, nf[0], nf[1], nf[2], ec, uf, kc);
+    } else {
+        launch_pdl(k_prolong_add<R, 2>, g, b, 0, s, nf[0], nf[1], 1, ec, uf);
+    }
     return cudaGetLastError();
 }
 

@@ -69,7 +69,8 @@ struct BatchLockstep {
     cudaStream_t s = nullptr, cap = nullptr;
     std::vector<cudaGraphExec_t> step_graph, close_graph;
     std::vector<cudaEvent_t> step_ev, close_ev;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr;
+    std::vector<cudaEvent_t> pev;   // per problem: end of its fanned-out restart work
     std::vector<void *> owned;
     std::vector<const void *> key;  // workspace pointers the tables were built for
     bool graphs_ok = true;
@@ -104,6 +105,9 @@ struct BatchLockstep {
             if (e) cudaEventDestroy(e);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        for (cudaEvent_t e : pev)
+            if (e) cudaEventDestroy(e);
         if (active_h) cudaFreeHost(active_h);
         if (est_h) cudaFreeHost(est_h);
         if (norm_h) cudaFreeHost(norm_h);
@@ -327,6 +331,13 @@ helm_status build(BatchLockstep *L, int m) {
     if (!L->cap) CKR(cudaStreamCreateWithFlags(&L->cap, cudaStreamNonBlocking));
     if (!L->ev_in) CKR(cudaEventCreateWithFlags(&L->ev_in, cudaEventDisableTiming));
     if (!L->ev_out) CKR(cudaEventCreateWithFlags(&L->ev_out, cudaEventDisableTiming));
+    if (!L->ev_fork) CKR(cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming));
+    if ((int)L->pev.size() != P) {
+        for (cudaEvent_t e : L->pev)
+            if (e) cudaEventDestroy(e);
+        L->pev.assign(P, nullptr);
+        for (auto &e : L->pev) CKR(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     for (cudaEvent_t e : L->step_ev) cudaEventDestroy(e);
     for (cudaEvent_t e : L->close_ev) cudaEventDestroy(e);
     L->step_ev.assign(m, nullptr);
@@ -482,6 +493,22 @@ bool event_ready(cudaEvent_t e, cudaError_t *err) {
     return *err == cudaSuccess;
 }
 
+// Per-problem stream work (restarts, solution updates) for the problems in list, each on its own
+// stream so that their small launches overlap: ordered after everything queued on the engine's
+// stream so far, and joined back into it.
+template <typename F> cudaError_t fan_out(BatchLockstep *L, const std::vector<int> &list, F work) {
+    if (list.empty()) return cudaSuccess;
+    CKE(cudaEventRecord(L->ev_fork, L->s));
+    for (int p : list) {
+        cudaStream_t ps = L->h[p]->stream;
+        CKE(cudaStreamWaitEvent(ps, L->ev_fork, 0));
+        CKE(work(p, ps));
+        CKE(cudaEventRecord(L->pev[p], ps));
+        CKE(cudaStreamWaitEvent(L->s, L->pev[p], 0));
+    }
+    return cudaSuccess;
+}
+
 cudaError_t norm_into(helm_handle *h, const double2 *x, double2 *out, cudaStream_t s) {
     CKE(launch_mdot_norm(h->np, nullptr, h->np, 0, x, h->partials, nullptr, s));
     return launch_reduce(h->partials, blas_nblocks(h->np), 1, out, 2, nullptr, s);
@@ -527,13 +554,17 @@ helm_status lockstep_solve(BatchLockstep *L, cudaStream_t user, const void *cons
         cudaStream_t k;
         ~Restore() { h->stream = k; }
     } restore{h0, keep0};
+    std::vector<int> all(P);
     for (int p = 0; p < P; p++) {
         r[p].f = (const double2 *)rhs[p];
         r[p].x = (double2 *)x[p];
-        helm_handle *h = L->h[p];
-        CKR(norm_into(h, r[p].f, h->fnorm_dev, s));
-        CKR(cudaMemcpyAsync(L->norm_h + p, h->fnorm_dev, sizeof(double2), cudaMemcpyDeviceToHost, s));
+        all[p] = p;
     }
+    CKR(fan_out(L, all, [&](int p, cudaStream_t ps) -> cudaError_t {
+        helm_handle *h = L->h[p];
+        CKE(norm_into(h, r[p].f, h->fnorm_dev, ps));
+        return cudaMemcpyAsync(L->norm_h + p, h->fnorm_dev, sizeof(double2), cudaMemcpyDeviceToHost, ps);
+    }));
     CKR(cudaStreamSynchronize(s));
     for (int p = 0; p < P; p++) {
         Run &R = r[p];
@@ -554,12 +585,12 @@ helm_status lockstep_solve(BatchLockstep *L, cudaStream_t user, const void *cons
         for (int p = 0; p < P; p++)
             if (!r[p].done) pend.push_back(p);
         if (pend.empty()) break;
-        for (int p : pend) {
+        CKR(fan_out(L, pend, [&](int p, cudaStream_t ps) -> cudaError_t {
             helm_handle *h = L->h[p];
-            CKR(launch_residual<double, double2>(h->A64, 2, r[p].f, r[p].x, h->V, s));
-            CKR(norm_into(h, h->V, h->scal, s));
-            CKR(cudaMemcpyAsync(L->norm_h + p, h->scal, sizeof(double2), cudaMemcpyDeviceToHost, s));
-        }
+            CKE(launch_residual<double, double2>(h->A64, 2, r[p].f, r[p].x, h->V, ps));
+            CKE(norm_into(h, h->V, h->scal, ps));
+            return cudaMemcpyAsync(L->norm_h + p, h->scal, sizeof(double2), cudaMemcpyDeviceToHost, ps);
+        }));
         CKR(cudaStreamSynchronize(s));
         std::vector<int> cyc;
         for (int p : pend) {
@@ -579,18 +610,20 @@ helm_status lockstep_solve(BatchLockstep *L, cudaStream_t user, const void *cons
         }
         for (int p : cyc) {
             Run &R = r[p];
-            helm_handle *h = L->h[p];
             R.restarts++;
             R.jmax = std::min(m, maxit - R.it);
             jmax = std::max(jmax, R.jmax);
-            // v_0 = r0 / beta as a float-pair vector; its complex64 copy is the first cycle's input
-            CKR(launch_split_scale(h->np, h->V, h->scal, s));
-            CKR(cudaMemsetAsync(h->g, 0, (m + 1) * sizeof(double2), s));
-            CKR(cudaMemcpyAsync(h->g, h->scal, sizeof(double2), cudaMemcpyDeviceToDevice, s));
-            CKR(launch_pair_to_c64(h->np, (const float4 *)h->V, nullptr, h->lv[0].b32, s));
             act[p] = 1;
             L->active_h[p] = 1;
         }
+        // v_0 = r0 / beta as a float-pair vector; its complex64 copy is the first cycle's input
+        CKR(fan_out(L, cyc, [&](int p, cudaStream_t ps) -> cudaError_t {
+            helm_handle *h = L->h[p];
+            CKE(launch_split_scale(h->np, h->V, h->scal, ps));
+            CKE(cudaMemsetAsync(h->g, 0, (m + 1) * sizeof(double2), ps));
+            CKE(cudaMemcpyAsync(h->g, h->scal, sizeof(double2), cudaMemcpyDeviceToDevice, ps));
+            return launch_pair_to_c64(h->np, (const float4 *)h->V, nullptr, h->lv[0].b32, ps);
+        }));
         CKR(cudaMemcpyAsync(L->active, L->active_h, P * sizeof(int), cudaMemcpyHostToDevice, s));
         auto unit = [&](int k) -> cudaError_t {
             if (k + 1 < jmax)
@@ -604,10 +637,9 @@ helm_status lockstep_solve(BatchLockstep *L, cudaStream_t user, const void *cons
         for (int j = 0; j < jmax && !live.empty(); j++) {
             cudaError_t err;
             if (!event_ready(unit_event(j), &err)) return helm_fail(HELM_ERR_CUDA, "event: %s", cudaGetErrorString(err));
-            std::vector<int> still;
+            std::vector<int> still, leave;
             for (int p : live) {
                 Run &R = r[p];
-                helm_handle *h = L->h[p];
                 R.est = L->est_h[(size_t)j * P + p];
                 R.it++;
                 helm_stats *sp = stats ? &stats[p] : nullptr;
@@ -624,12 +656,18 @@ helm_status lockstep_solve(BatchLockstep *L, cudaStream_t user, const void *cons
                         R.done = true;
                         continue;
                     }
-                    CKR(launch_backsolve(h->H, m + 1, j + 1, h->g, h->y, s));
-                    CKR(launch_combine<float2>(h->np, (const float2 *)h->Z, h->np, j + 1, h->y, h->alpha2, R.x, s));
+                    leave.push_back(p);
                     continue;
                 }
                 still.push_back(p);
             }
+            // x += Z y of the problems that left at this step, side by side (the steps already
+            // queued only write their columns and slots past j)
+            CKR(fan_out(L, leave, [&](int p, cudaStream_t ps) -> cudaError_t {
+                helm_handle *h = L->h[p];
+                CKE(launch_backsolve(h->H, m + 1, j + 1, h->g, h->y, ps));
+                return launch_combine<float2>(h->np, (const float2 *)h->Z, h->np, j + 1, h->y, h->alpha2, r[p].x, ps);
+            }));
             live.swap(still);
             if (!live.empty() && j + 3 < jmax) CKR(unit(j + 3));
         }

@@ -363,7 +363,7 @@ helm_status helm_profile_read(helm_handle *h, int ncls, int *launches, double *m
  *                  transfer launches (HELM_TILE_NONE).  Ignored where it does not apply (other
  *                  smoothers, complex128 cycles, 3D, levels inside the tail, grids the tile
  *                  does not fit: those use the separate launches).
- * Default: tail_levels = -1, HELM_TILE_32x8 on every level, cluster_levels = 0 (16 blocks). */
+ * Default: tail_levels = -1, HELM_TILE_32x8 on every level, cluster_levels = 0 (16 blocks, cluster_halo 3). */
 #define HELM_MAX_LEVELS 16
 typedef enum {
     HELM_TILE_NONE = -1,
@@ -383,6 +383,12 @@ typedef struct {
                             takes precedence over tail_levels; clamped to what fits (200 KB per
                             block, at most 6 levels) */
     int cluster_ctas;    /* blocks (SMs) of that cluster: 8 or 16 */
+    int cluster_halo;    /* rows each block of the cluster keeps beyond its slab of every level:
+                            1 = one halo row, a cluster barrier after every sweep and transfer;
+                            3 = three rows, recomputed locally, so that a level's way down and its
+                            way up each need one barrier (V-cycles of omega-Jacobi with at most two
+                            sweeps each way from a zero guess, where the levels fit; otherwise the
+                            one-row form runs).  Same results either way. */
 } helm_tuning;
 
 /* Sets / reads the handle's tuning (host struct).  Setting drops the handle's captured CUDA

@@ -53,6 +53,8 @@ struct Phase {
 
 struct BatchLockstep {
     int P = 0, m = 0, T = 0, nc = 16, nu_c = 0;
+    int halo = 3;        // cluster tail: halo rows the problems' tunings ask for
+    bool deep = false;   // ... and whether the deep-halo kernel runs
     std::vector<helm_handle *> h;
     std::vector<Phase> phases;                  // largest shape first
     DevOp<float> tail_ops[MAX_CT_LEVELS] = {};  // shapes of the tail levels
@@ -205,6 +207,7 @@ bool plan(BatchLockstep *L, bool commit) {
     L->phases.swap(phases);
     L->T = T;
     L->nc = nc;
+    L->halo = R->tune.cluster_halo;
     L->nu_c = R->nu_c;
     for (int k = 0; k < T; k++) L->tail_ops[k] = R->lv[nr - T + k].M32;
     return true;
@@ -233,6 +236,7 @@ helm_status build(BatchLockstep *L, int m) {
         helm_tuning t = h->tune;
         t.cluster_levels = L->T;
         t.cluster_ctas = L->nc;
+        t.cluster_halo = L->halo;
         t.tail_levels = 0;
         for (int l = 0; l < HELM_MAX_LEVELS; l++) t.level_tile[l] = HELM_TILE_32x8;
         for (const Phase &ph : L->phases)
@@ -240,7 +244,9 @@ helm_status build(BatchLockstep *L, int m) {
                 if (mb.first == p && mb.second < HELM_MAX_LEVELS) t.level_tile[mb.second] = ph.tile;
         helm_status st = helm_set_tuning(h, &t);
         if (st != HELM_OK) return st;
-        if (!ctail_image(h, false)) return helm_fail(HELM_ERR_NOMEM, "cluster-tail image of problem %d", p);
+        if (p == 0) L->deep = ctail_deep(h);
+        if (ctail_deep(h) != L->deep) return helm_fail(HELM_ERR_ARG, "the problems' cluster tails differ");
+        if (!ctail_image(h, false, L->deep)) return helm_fail(HELM_ERR_NOMEM, "cluster-tail image of problem %d", p);
         CKR(cudaStreamSynchronize(h->stream));
     }
     CKR(cudaMalloc((void **)&L->active, P * sizeof(int)));
@@ -284,7 +290,7 @@ helm_status build(BatchLockstep *L, int m) {
         E.b_top = h->lv[t0].b32;
         E.u_top = t0 == 0 ? (float2 *)h->Z : h->lv[t0].u32;
         E.ustride = t0 == 0 ? h->np : 0;
-        E.img = ctail_image(h, false);
+        E.img = ctail_image(h, false, L->deep);
         E.active = L->active + p;
         BVec &V = vec[p];
         V.n = h->np;
@@ -384,7 +390,8 @@ cudaError_t record_step(BatchLockstep *L, const Prof &pf, int j, cudaStream_t s)
         }
         {
             ProfScope ps(h0, HELM_K_COARSE, 0, 0);
-            CKE(launch_mg_ctail_batch(L->T, L->tail_ops, L->nu_c, 2, 2, 0, om, 1, 1, L->nc, P, L->tail, j, s));
+            if (L->deep) CKE(launch_mg_chalo_batch(L->T, L->tail_ops, L->nu_c, 2, 2, om, L->nc, P, L->tail, j, s));
+            else CKE(launch_mg_ctail_batch(L->T, L->tail_ops, L->nu_c, 2, 2, 0, om, 1, 1, L->nc, P, L->tail, j, s));
         }
         for (auto it = L->phases.rbegin(); it != L->phases.rend(); ++it) {
             const Phase &ph = *it;

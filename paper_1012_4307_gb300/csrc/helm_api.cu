@@ -386,6 +386,7 @@ helm_status helm_create_impl(const helm_grid *grid, double theta, const double *
     for (int l = 0; l < HELM_MAX_LEVELS; l++) h->tune.level_tile[l] = HELM_TILE_32x8;
     h->tune.cluster_levels = 0;
     h->tune.cluster_ctas = 16;
+    h->tune.cluster_halo = 3;
     // how many coarsest levels a cluster tail can hold (2D only)
     if (mg->kind != HELM_PC_NONE && dim == 2) {
         const int nlev = (int)h->lv.size();
@@ -396,7 +397,7 @@ helm_status helm_create_impl(const helm_grid *grid, double theta, const double *
                 int n[MAX_CT_LEVELS][3];
                 for (int q = 0; q < nt; q++)
                     for (int a = 0; a < 3; a++) n[q][a] = h->lv[nlev - nt + q].n[a];
-                unsigned off[MAX_CT_LEVELS][6], obc, oz;
+                unsigned off[MAX_CT_LEVELS][7], obc, oz;
                 if (mg_ctail_layout(nt, n, nc, h->nu_c, off, &obc, &oz) <= CT_SMEM_BYTES) fit = nt;
             }
             h->ctail_fit[k] = fit;
@@ -576,10 +577,10 @@ template <typename R> int tail_top(const helm_handle *h) {
 template int tail_top<float>(const helm_handle *);
 template int tail_top<double>(const helm_handle *);
 
-const void *ctail_image(helm_handle *h, bool build) {
+const void *ctail_image(helm_handle *h, bool build, bool deep) {
     const int top = ctail_top(h);
     if (top < 0) return nullptr;
-    const int nc = h->tune.cluster_ctas, key = top * 32 + nc;
+    const int nc = h->tune.cluster_ctas, key = top * 32 + nc + (deep ? 1024 : 0);
     for (const auto &e : h->ctail_img)
         if (e.first == key) return e.second;
     if (!build) return nullptr;
@@ -587,7 +588,8 @@ const void *ctail_image(helm_handle *h, bool build) {
     DevOp<float> ops[MAX_CT_LEVELS];
     for (int k = 0; k < nt; k++) ops[k] = h->lv[top + k].M32;
     void *img = nullptr;
-    if (build_mg_ctail_image(nt, ops, h->minv32, h->nu_c, nc, &img, h->stream) != cudaSuccess) {
+    if ((deep ? build_mg_chalo_image(nt, ops, h->minv32, h->nu_c, nc, &img, h->stream)
+              : build_mg_ctail_image(nt, ops, h->minv32, h->nu_c, nc, &img, h->stream)) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -599,6 +601,18 @@ const void *ctail_image(helm_handle *h, bool build) {
         return nullptr;
     }
     return img;
+}
+
+bool ctail_deep(const helm_handle *h) {
+    if (h->tune.cluster_halo != 3) return false;
+    const int top = ctail_top(h);
+    const helm_mg_params &m = h->mg;
+    if (top < 0 || m.smoother != HELM_SMOOTH_JACOBI || m.gamma_f != 1 || m.gamma_c != 1 || m.nu1 > 2 || m.nu2 > 2)
+        return false;
+    const int nt = (int)h->lv.size() - top;
+    DevOp<float> ops[MAX_CT_LEVELS];
+    for (int k = 0; k < nt; k++) ops[k] = h->lv[top + k].M32;
+    return mg_chalo_bytes(nt, ops, h->nu_c, h->tune.cluster_ctas) > 0;
 }
 
 int ctail_top(const helm_handle *h) {
@@ -628,9 +642,15 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
                 bytes += interior(h->lv[l + k], h->dim) * sizeof(float2) * 8.0;
             }
             ProfScope ps(h, HELM_K_COARSE, bytes + (double)h->nu_c * h->nu_c * sizeof(float2), 0);
+            if (zero && ctail_deep(h)) {
+                const void *img = ctail_image(h, !h->capturing, true);
+                if (img)
+                    return launch_mg_chalo(nt, ops, b, u, h->minv32, h->nu_c, h->mg.nu1, h->mg.nu2,
+                                           (float)h->mg.omega, h->tune.cluster_ctas, img, h->stream);
+            }
             return launch_mg_ctail(nt, ops, b, u, h->minv32, h->nu_c, h->mg.nu1, h->mg.nu2,
                                    h->mg.smoother == HELM_SMOOTH_RB, (float)h->mg.omega, zero ? 1 : 0, gf, gc,
-                                   h->tune.cluster_ctas, ctail_image(h, !h->capturing), h->stream);
+                                   h->tune.cluster_ctas, ctail_image(h, !h->capturing, false), h->stream);
         }
     }
     if (l == tail_top<R>(h)) {

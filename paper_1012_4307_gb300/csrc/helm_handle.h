@@ -183,9 +183,14 @@ float2 *level0_rhs_c64(helm_handle *h);
 template <typename R> int tail_top(const helm_handle *h);
 // First level of the cluster tail (2D complex64 cycles) under the handle's tuning (-1: none).
 int ctail_top(const helm_handle *h);
-// The cluster tail's initial shared-memory image for the current tuning (null: no tail, or not
-// built and build false); built on the handle's stream, outside graph capture.
-const void *ctail_image(helm_handle *h, bool build);
+// Whether the cluster tail of a cycle from zero runs as the deep-halo kernel under the handle's
+// tuning (cluster_halo 3, a V-cycle of omega-Jacobi with at most two sweeps each way, levels that
+// fit).
+bool ctail_deep(const helm_handle *h);
+// The initial shared-memory image of the cluster tail (deep: of the deep-halo kernel) for the
+// current tuning (null: no tail, or not built and build false); built on the handle's stream,
+// outside graph capture.
+const void *ctail_image(helm_handle *h, bool build, bool deep);
 
 // Lockstep engine of helm_solve_batch (batch_lockstep.cu): every phase of an FGMRES step is one
 // launch over all problems.  lockstep_eligible tells whether the batch's configuration is one it

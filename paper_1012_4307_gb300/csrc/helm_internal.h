@@ -44,6 +44,25 @@ __device__ __forceinline__ float2 cinv_fast(float2 a) {
     const float r = __fdividef(1.0f, a.x * a.x + a.y * a.y);
     return make_float2(a.x * r, -a.y * r);
 }
+// dst[q] = src[q] for q < n (src global and unchanged during the kernel, dst this block's
+// shared memory): each thread issues eight loads before it stores, so that a block's copy takes
+// a few memory round trips instead of one per float4 a thread moves.
+__device__ __forceinline__ void block_copy16(float4 *dst, const float4 *__restrict__ src, unsigned n) {
+    constexpr int U = 8;
+    for (unsigned q0 = threadIdx.x; q0 < n; q0 += U * blockDim.x) {
+        float4 r[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const unsigned q = q0 + u * blockDim.x;
+            r[u] = q < n ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const unsigned q = q0 + u * blockDim.x;
+            if (q < n) dst[q] = r[u];
+        }
+    }
+}
 __device__ __forceinline__ float2 to_c(float2 v, float) { return v; }
 __device__ __forceinline__ float2 to_c(double2 v, float) { return make_float2((float)v.x, (float)v.y); }
 __device__ __forceinline__ double2 to_c(float2 v, double) { return make_double2((double)v.x, (double)v.y); }
@@ -214,8 +233,18 @@ cudaError_t launch_mg_tail(int dim, int nlev, const DevOp<R> *ops, typename CT<R
 // (rows split into slabs).  b_top / u_top: the first of those levels' right-hand side and result
 // (global; u_top is the initial guess unless zero).
 constexpr int MAX_CT_LEVELS = 6;
+constexpr int MAX_CT_BLOCKS = 16;      // blocks per cluster at most
+constexpr int CT_BLOCK_THREADS = 512;  // threads per block of a cluster tail
 constexpr size_t CT_SMEM_BYTES = 200 * 1024;
-size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (*off)[6], unsigned *obc,
+// Nested row slabs of the tail levels: block r owns the interior rows B[l][r] .. B[l][r+1]-1 of
+// level l (level 0 in runs of ceil((ny - 2) / nc) rows, B[l+1][r] = (B[l][r] + 1) / 2).  False
+// unless every level has odd ny and the next has (ny + 1) / 2.
+bool mg_ctail_bounds(int nlev, const int (*n)[3], int nc, int (*B)[MAX_CT_BLOCKS + 1]);
+// Rows of the coarsest inverse each warp stages in the dense phase, and their shared-memory
+// bytes (0 when above 64 KB: the rows are then read from global memory).
+int mg_ctail_minv_rows(int nc, int nu_c);
+size_t mg_ctail_minv_stage_bytes(int nc, int nu_c);
+size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (*off)[7], unsigned *obc,
                        unsigned *ominv);
 // img: the blocks' initial shared memory from build_mg_ctail_image for the same levels and nc
 // (null: each launch builds it itself); *out is device memory the caller frees.
@@ -225,6 +254,19 @@ cudaError_t launch_mg_ctail(int nlev, const DevOp<float> *ops, const float2 *b_t
 cudaError_t build_mg_ctail_image(int nlev, const DevOp<float> *ops, const float2 *minv, int nu_c, int nc, void **out,
                                  cudaStream_t s);
 int mg_ctail_max_clusters(int nc, size_t bytes);
+// Deep-halo cluster tail (kernels_chalo.cu): the same levels for a V-cycle of omega-Jacobi with
+// nu1, nu2 <= 2 sweeps from a zero guess, each block keeping three rows beyond its slab so that
+// each level needs one cluster barrier down and one up.  img (required): the blocks' initial
+// shared memory from build_mg_chalo_image.  mg_chalo_bytes: its shared memory per block (0: the
+// levels do not fit).
+size_t mg_chalo_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (*off)[8], unsigned *obc,
+                       unsigned *ominv);
+size_t mg_chalo_bytes(int nlev, const DevOp<float> *ops, int nu_c, int nc);
+cudaError_t build_mg_chalo_image(int nlev, const DevOp<float> *ops, const float2 *minv, int nu_c, int nc, void **out,
+                                 cudaStream_t s);
+cudaError_t launch_mg_chalo(int nlev, const DevOp<float> *ops, const float2 *b_top, float2 *u_top, const float2 *minv,
+                            int nu_c, int nu1, int nu2, float omega, int nc, const void *img, cudaStream_t s);
+int mg_chalo_max_clusters(int nc, size_t bytes);
 
 // ------------------------------------------------------------------------------ batched launches
 // One launch covers the same phase of many problems (helm_solve_batch): a batched kernel reads
@@ -275,6 +317,8 @@ cudaError_t launch_prolong_post2_batch(const int n[3], int tile, int count, cons
                                        cudaStream_t s);
 cudaError_t launch_mg_ctail_batch(int nlev, const DevOp<float> *ops, int nu_c, int nu1, int nu2, int rb, float omega,
                                   int gf, int gc, int nc, int count, const BTail *tab, int j, cudaStream_t s);
+cudaError_t launch_mg_chalo_batch(int nlev, const DevOp<float> *ops, int nu_c, int nu1, int nu2, float omega, int nc,
+                                  int count, const BTail *tab, int j, cudaStream_t s);
 // Flat blocks of one problem's batched 2D apply; problem e takes [first[e], first[e + 1]).
 unsigned apply_A_df_blocks(const int n[3]);
 cudaError_t launch_apply_A_df_batch(int count, const BVec *tab, const unsigned *first, unsigned nblocks, int j,

@@ -25,17 +25,17 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int CT_THREADS = 512;
-constexpr int CT_MAXC = 16;  // blocks per cluster at most
+constexpr int CT_THREADS = CT_BLOCK_THREADS;
 
 struct CLevel {
     const float2 *cx, *cy;  // global coefficient triples (3 nx, 3 ny)
     const float *k2;        // global k^2 (nx ny)
     float2 bk, c;
     int nx, ny;
-    int B[CT_MAXC + 1];     // block r owns interior rows B[r] .. B[r+1]-1 (possibly none)
-    unsigned ob, ou, ot, ok, ocx, ocy;  // byte offsets in shared memory (same in every block);
-                                        // ok: the diagonal of M at the owned nodes
+    int B[MAX_CT_BLOCKS + 1];     // block r owns interior rows B[r] .. B[r+1]-1 (possibly none)
+    unsigned ob, ou, ot, ok, oi, ocx, ocy;  // byte offsets in shared memory (same in every block);
+                                            // ok: the diagonal of M at the owned nodes, oi: its
+                                            // reciprocal (cinv_fast, formed once)
 };
 
 struct CArgs {
@@ -63,7 +63,7 @@ struct Ctx {
 // accesses to other blocks' rows.
 struct LV {
     int nx, j0, j1;
-    unsigned ob, ou, ot, ok, ocx, ocy;
+    unsigned ob, ou, ot, ok, oi, ocx, ocy;
     float2 bk, c;
     const int *B;
 };
@@ -72,7 +72,7 @@ __device__ __forceinline__ LV lv_of(const Ctx &X, const CLevel &L) {
     v.nx = L.nx;
     v.j0 = L.B[X.rank];
     v.j1 = L.B[X.rank + 1];
-    v.ob = L.ob; v.ou = L.ou; v.ot = L.ot; v.ok = L.ok; v.ocx = L.ocx; v.ocy = L.ocy;
+    v.ob = L.ob; v.ou = L.ou; v.ot = L.ot; v.ok = L.ok; v.oi = L.oi; v.ocx = L.ocx; v.ocy = L.ocy;
     v.bk = L.bk;
     v.c = L.c;
     v.B = L.B;
@@ -131,6 +131,9 @@ __device__ __forceinline__ void for_owned(const Ctx &X, const LV &L, F f) {
 __device__ __forceinline__ float2 diag_at(const Ctx &X, const LV &L, int j, int i) {
     return ((const float2 *)(X.sm + L.ok))[(size_t)(j - L.j0) * L.nx + i];
 }
+__device__ __forceinline__ float2 dinv_at(const Ctx &X, const LV &L, int j, int i) {
+    return ((const float2 *)(X.sm + L.oi))[(size_t)(j - L.j0) * L.nx + i];
+}
 
 // (M u)(j, i) from this block's rows of the array at offset u (j - 1 and j + 1 may be halo
 // rows); d = the diagonal.
@@ -170,7 +173,7 @@ __device__ __noinline__ uint2 ph_smooth(Ctx X, const CArgs *A, int l, int nu, ui
                     float2 d;
                     const float2 mu = apply_at(X, L, u, j, i, d);
                     const float2 uc = lrow(X, L, u, j)[i], b = lrow(X, L, L.ob, j)[i];
-                    put(X, L, u, j, i, cadd(uc, cscale(cmul(csub(b, mu), cinv_fast(d)), om)), X.rank);
+                    put(X, L, u, j, i, cadd(uc, cscale(cmul(csub(b, mu), dinv_at(X, L, j, i)), om)), X.rank);
                 });
                 csync();
             }
@@ -181,11 +184,11 @@ __device__ __noinline__ uint2 ph_smooth(Ctx X, const CArgs *A, int l, int nu, ui
                 const float2 b = lrow(X, L, L.ob, j)[i];
                 float2 v;
                 if (z0) {
-                    v = cscale(cmul(b, cinv_fast(diag_at(X, L, j, i))), om);
+                    v = cscale(cmul(b, dinv_at(X, L, j, i)), om);
                 } else {
                     float2 d;
                     const float2 mu = apply_at(X, L, src, j, i, d);
-                    v = cadd(lrow(X, L, src, j)[i], cscale(cmul(csub(b, mu), cinv_fast(d)), om));
+                    v = cadd(lrow(X, L, src, j)[i], cscale(cmul(csub(b, mu), dinv_at(X, L, j, i)), om));
                 }
                 put(X, L, dst, j, i, v, X.rank);
             });
@@ -317,11 +320,13 @@ __device__ __noinline__ void ct_init(Ctx X, const CArgs *A) {
         const CLevel &L = A->lv[l];
         const int j0 = L.B[X.rank], j1 = L.B[X.rank + 1];
         const float2 *cx = (const float2 *)(X.sm + L.ocx), *cy = (const float2 *)(X.sm + L.ocy);
-        float2 *dg = (float2 *)(X.sm + L.ok);
+        float2 *dg = (float2 *)(X.sm + L.ok), *di = (float2 *)(X.sm + L.oi);
         for (int q = threadIdx.x; q < (j1 - j0) * L.nx; q += blockDim.x) {
             const int li = q / L.nx, i = q - li * L.nx;
             const float k2 = L.k2[(size_t)j0 * L.nx + q];
-            dg[q] = cadd(cadd(cx[3 * i + 1], cy[3 * li + 1]), cadd(cscale(L.bk, k2), L.c));
+            const float2 d = cadd(cadd(cx[3 * i + 1], cy[3 * li + 1]), cadd(cscale(L.bk, k2), L.c));
+            dg[q] = d;
+            di[q] = cinv_fast(d);
         }
     }
     if (A->mrow) ph_stage_minv(X, A);
@@ -350,7 +355,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_mg_ctail(const __grid_constan
     const CArgs *A = &As;
     if (A0.img) {
         const float4 *src = A0.img + (size_t)X.rank * (A0.total / 16);
-        for (unsigned q = threadIdx.x; q < A0.total / 16; q += blockDim.x) ((float4 *)ct_smem)[q] = src[q];
+        block_copy16((float4 *)ct_smem, src, A0.total / 16);
         __syncthreads();
     } else {
         __syncthreads();
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_mg_ctail_b(const __grid_const
     const CArgs *A = &As;
     {
         const float4 *src = A->img + (size_t)X.rank * (A->total / 16);
-        for (unsigned q = threadIdx.x; q < A->total / 16; q += blockDim.x) ((float4 *)ct_smem)[q] = src[q];
+        block_copy16((float4 *)ct_smem, src, A->total / 16);
         __syncthreads();
     }
     const LV T = lv_of(X, A->lv[0]);
@@ -421,10 +426,10 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_mg_ctail_b(const __grid_const
     for_owned(X, T, [&](int j, int i) { A->u_top[(size_t)i + (size_t)T.nx * j] = lrow(X, T, T.ou, j)[i]; });
 }
 
-// Nested slabs: level 0 in runs of ceil((ny - 2) / nc) rows, level l + 1 bounded by
-// (B_l[r] + 1) / 2.  False unless every level has odd ny and the next has (ny + 1) / 2.
-bool ct_bounds(int nlev, const int (*n)[3], int nc, int (*B)[CT_MAXC + 1]) {
-    if (nc < 1 || nc > CT_MAXC) return false;
+}  // namespace
+
+bool mg_ctail_bounds(int nlev, const int (*n)[3], int nc, int (*B)[MAX_CT_BLOCKS + 1]) {
+    if (nc < 1 || nc > MAX_CT_BLOCKS) return false;
     for (int l = 0; l < nlev; l++) {
         if (n[l][1] < 3 || n[l][1] % 2 == 0) return false;
         if (l + 1 < nlev && n[l + 1][1] != (n[l][1] + 1) / 2) return false;
@@ -436,28 +441,23 @@ bool ct_bounds(int nlev, const int (*n)[3], int nc, int (*B)[CT_MAXC + 1]) {
     return true;
 }
 
-}  // namespace
-
-// Rows of the coarsest inverse each warp handles in the dense phase, and the shared memory that
-// staging them takes (0 when that is more than 64 KB: the dense phase then reads them from
-// global memory).
-static int ct_minv_rows(int nc, int nu_c) { return (nu_c + nc * (CT_THREADS / 32) - 1) / (nc * (CT_THREADS / 32)); }
-static size_t ct_minv_stage_bytes(int nc, int nu_c) {
-    const size_t b = (size_t)(CT_THREADS / 32) * ct_minv_rows(nc, nu_c) * nu_c * sizeof(float2);
+int mg_ctail_minv_rows(int nc, int nu_c) { return (nu_c + nc * (CT_THREADS / 32) - 1) / (nc * (CT_THREADS / 32)); }
+size_t mg_ctail_minv_stage_bytes(int nc, int nu_c) {
+    const size_t b = (size_t)(CT_THREADS / 32) * mg_ctail_minv_rows(nc, nu_c) * nu_c * sizeof(float2);
     return b <= 64 * 1024 ? b : 0;
 }
 
 // Shared-memory layout of the cluster tail (identical in every block): per level b, u, t
 // ((rmax + 2) rows x nx complex64 each: the owned rows between two halo rows; rmax = the most
-// rows a block owns), the diagonal of M (rmax x nx complex64), x coefficients (3 nx), y
-// coefficients of the owned rows (3 rmax); then the compact coarsest right-hand side and the
-// block's staged rows of the coarsest inverse (ominv).  Levels that are not nested (odd ny,
+// rows a block owns), the diagonal of M and its reciprocal (rmax x nx complex64 each), x
+// coefficients (3 nx), y coefficients of the owned rows (3 rmax); then the compact coarsest
+// right-hand side and the block's staged rows of the coarsest inverse (ominv).  Levels that are not nested (odd ny,
 // halved) get a size no launch accepts.
-size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (*off)[6], unsigned *obc,
+size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (*off)[7], unsigned *obc,
                        unsigned *ominv) {
     auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
-    int B[MAX_CT_LEVELS][CT_MAXC + 1];
-    if (nlev < 1 || nlev > MAX_CT_LEVELS || !ct_bounds(nlev, n, nc, B)) return ~(size_t)0;
+    int B[MAX_CT_LEVELS][MAX_CT_BLOCKS + 1];
+    if (nlev < 1 || nlev > MAX_CT_LEVELS || !mg_ctail_bounds(nlev, n, nc, B)) return ~(size_t)0;
     size_t p = 0;
     for (int l = 0; l < nlev; l++) {
         const int nx = n[l][0];
@@ -468,13 +468,14 @@ size_t mg_ctail_layout(int nlev, const int (*n)[3], int nc, int nu_c, unsigned (
         off[l][1] = (unsigned)p; p += vec;                                             // u
         off[l][2] = (unsigned)p; p += vec;                                             // t
         off[l][3] = (unsigned)p; p += al((size_t)rmax * nx * sizeof(float2));          // diagonal
-        off[l][4] = (unsigned)p; p += al((size_t)3 * nx * sizeof(float2));             // x coefficients
-        off[l][5] = (unsigned)p; p += al((size_t)3 * rmax * sizeof(float2));           // y coefficients
+        off[l][4] = (unsigned)p; p += al((size_t)rmax * nx * sizeof(float2));          // its reciprocal
+        off[l][5] = (unsigned)p; p += al((size_t)3 * nx * sizeof(float2));             // x coefficients
+        off[l][6] = (unsigned)p; p += al((size_t)3 * rmax * sizeof(float2));           // y coefficients
     }
     *obc = (unsigned)p;
     p += al((size_t)nu_c * sizeof(float2));
     *ominv = (unsigned)p;
-    p += al(ct_minv_stage_bytes(nc, nu_c));
+    p += al(mg_ctail_minv_stage_bytes(nc, nu_c));
     return p;
 }
 
@@ -484,11 +485,11 @@ static size_t ct_args(int nlev, const DevOp<float> *ops, const float2 *minv, int
     int n[MAX_CT_LEVELS][3];
     for (int l = 0; l < nlev; l++)
         for (int a = 0; a < 3; a++) n[l][a] = ops[l].n[a];
-    unsigned off[MAX_CT_LEVELS][6], obc = 0, ominv = 0;
+    unsigned off[MAX_CT_LEVELS][7], obc = 0, ominv = 0;
     const size_t bytes = mg_ctail_layout(nlev, n, nc, nu_c, off, &obc, &ominv);
     if (bytes > CT_SMEM_BYTES) return 0;
-    int B[MAX_CT_LEVELS][CT_MAXC + 1];
-    if (!ct_bounds(nlev, n, nc, B)) return 0;
+    int B[MAX_CT_LEVELS][MAX_CT_BLOCKS + 1];
+    if (!mg_ctail_bounds(nlev, n, nc, B)) return 0;
     A = CArgs{};
     for (int l = 0; l < nlev; l++) {
         CLevel &L = A.lv[l];
@@ -499,15 +500,16 @@ static size_t ct_args(int nlev, const DevOp<float> *ops, const float2 *minv, int
         L.c = ops[l].c;
         L.nx = n[l][0];
         L.ny = n[l][1];
-        for (int r = 0; r <= CT_MAXC; r++) L.B[r] = B[l][std::min(r, nc)];
-        L.ob = off[l][0]; L.ou = off[l][1]; L.ot = off[l][2]; L.ok = off[l][3]; L.ocx = off[l][4]; L.ocy = off[l][5];
+        for (int r = 0; r <= MAX_CT_BLOCKS; r++) L.B[r] = B[l][std::min(r, nc)];
+        L.ob = off[l][0]; L.ou = off[l][1]; L.ot = off[l][2]; L.ok = off[l][3]; L.oi = off[l][4];
+        L.ocx = off[l][5]; L.ocy = off[l][6];
     }
     A.nlev = nlev;
     A.nu_c = nu_c;
     A.minv = minv;
     A.obc = obc;
     A.ominv = ominv;
-    A.mrow = ct_minv_stage_bytes(nc, nu_c) ? ct_minv_rows(nc, nu_c) : 0;
+    A.mrow = mg_ctail_minv_stage_bytes(nc, nu_c) ? mg_ctail_minv_rows(nc, nu_c) : 0;
     A.total = (unsigned)bytes;
     return bytes;
 }

@@ -353,7 +353,13 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
                                               float2 *__restrict__ b_out, float &sn, float &cn, int bx, int nblk) {
     float4 *x = V + (size_t)j * ldv, *w = V + (size_t)(j + 1) * ldv;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (size_t q = bx * (size_t)NT + threadIdx.x; q < n; q += (size_t)nblk * NT) {
+    // The dot pass before this one sweeps the nodes upwards, so L2 holds the top of every
+    // vector it read: this pass sweeps downwards and starts on those lines, and it ends at
+    // the bottom, where the next step's dot pass starts.
+    const size_t stride = (size_t)nblk * NT, base = bx * (size_t)NT + threadIdx.x;
+    for (size_t round = (n + stride - 1) / stride; round-- > 0;) {
+        const size_t q = round * stride + base;
+        if (q >= n) continue;
         const float4 xq = x[q], wq = w[q];
         const ff xr = ff_re(xq), xi = ff_im(xq);
         // (sum, compensation) accumulators per component: v over the basis, started from x; w in

@@ -35,6 +35,7 @@ bool tuning_valid(const helm_tuning &t) {
     if (t.tail_levels < -1 || t.tail_levels == 1) return false;
     if (t.cluster_levels < 0 || t.cluster_levels == 1) return false;
     if (t.cluster_ctas != 8 && t.cluster_ctas != 16) return false;
+    if (t.cluster_halo != 1 && t.cluster_halo != 3) return false;
     for (int l = 0; l < HELM_MAX_LEVELS; l++)
         if (t.level_tile[l] < HELM_TILE_NONE || t.level_tile[l] >= HELM_TILE_COUNT) return false;
     return true;
@@ -44,10 +45,11 @@ bool tuning_valid(const helm_tuning &t) {
 
 extern "C" helm_status helm_set_tuning(helm_handle *h, const helm_tuning *t) {
     if (!h || !t) return helm_fail(HELM_ERR_ARG, "null argument");
-    if (!tuning_valid(*t)) return helm_fail(HELM_ERR_ARG, "invalid tuning (tail or cluster levels, cluster blocks, or a tile)");
+    if (!tuning_valid(*t))
+        return helm_fail(HELM_ERR_ARG, "invalid tuning (tail or cluster levels, cluster blocks or halo, or a tile)");
     h->tune = *t;
     helm_drop_graphs(h);
-    ctail_image(h, true);
+    ctail_image(h, true, ctail_deep(h));
     return HELM_OK;
 }
 
@@ -87,7 +89,7 @@ extern "C" helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, h
     // skipped
     auto time_it = [&](const helm_tuning &t, bool soft = false) -> double {
         h->tune = t;
-        ctail_image(h, true);
+        ctail_image(h, true, ctail_deep(h));
         cudaStream_t keep_s = h->stream;
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
@@ -144,23 +146,34 @@ extern "C" helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, h
             if (ms >= 0 && ms < cur_ms) { cur = t; cur_ms = ms; }
         }
     };
-    // cluster tail (2D complex64): off, or 2 .. the levels that fit, on 8 or 16 blocks
+    // cluster tail (2D complex64): off, or 2 .. the levels that fit, on 8 or 16 blocks, with one
+    // or (where it applies) three halo rows
     auto tune_cluster = [&]() {
         if (!(c64 && h->dim == 2)) return;
+        const helm_mg_params &m = h->mg;
+        const bool vj2 = m.smoother == HELM_SMOOTH_JACOBI && m.gamma_f == 1 && m.gamma_c == 1 && m.nu1 <= 2 && m.nu2 <= 2;
         for (int k = 0; k < 2 && st == HELM_OK; k++) {
             const int nc = k ? 16 : 8;
             for (int cl = 2; cl <= h->ctail_fit[k] && st == HELM_OK; cl++) {
-                if (cl == cur.cluster_levels && nc == cur.cluster_ctas) continue;
                 int n[MAX_CT_LEVELS][3];
-                for (int q = 0; q < cl; q++)
-                    for (int a = 0; a < 3; a++) n[q][a] = h->lv[last - cl + 1 + q].n[a];
-                unsigned off[MAX_CT_LEVELS][6], obc, oz;
+                DevOp<float> ops[MAX_CT_LEVELS];
+                for (int q = 0; q < cl; q++) {
+                    ops[q] = h->lv[last - cl + 1 + q].M32;
+                    for (int a = 0; a < 3; a++) n[q][a] = ops[q].n[a];
+                }
+                unsigned off[MAX_CT_LEVELS][7], obc, oz;
                 if (mg_ctail_max_clusters(nc, mg_ctail_layout(cl, n, nc, h->nu_c, off, &obc, &oz)) < 1) continue;
-                helm_tuning t = cur;
-                t.cluster_levels = cl;
-                t.cluster_ctas = nc;
-                const double ms = time_it(t, true);
-                if (ms >= 0 && ms < cur_ms) { cur = t; cur_ms = ms; }
+                const size_t deep_bytes = vj2 ? mg_chalo_bytes(cl, ops, h->nu_c, nc) : 0;
+                for (int halo : {1, 3}) {
+                    if (cl == cur.cluster_levels && nc == cur.cluster_ctas && halo == cur.cluster_halo) continue;
+                    if (halo == 3 && (!deep_bytes || mg_chalo_max_clusters(nc, deep_bytes) < 1)) continue;
+                    helm_tuning t = cur;
+                    t.cluster_levels = cl;
+                    t.cluster_ctas = nc;
+                    t.cluster_halo = halo;
+                    const double ms = time_it(t, true);
+                    if (ms >= 0 && ms < cur_ms) { cur = t; cur_ms = ms; }
+                }
             }
         }
         if (cur.cluster_levels > 0 && st == HELM_OK) {  // and without it
@@ -214,7 +227,7 @@ extern "C" helm_status helm_autotune(helm_handle *h, helm_prec prec, int reps, h
     h->prof.on = prof;
     h->tune = st == HELM_OK ? cur : keep;
     helm_drop_graphs(h);
-    ctail_image(h, true);
+    ctail_image(h, true, ctail_deep(h));
     if (st != HELM_OK) return st;
     if (best) *best = cur;
     if (best_ms) *best_ms = cur_ms;

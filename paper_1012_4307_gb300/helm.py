@@ -64,7 +64,7 @@ _TILE_NAMES = {v: k for k, v in TILES.items()}
 
 class _Tuning(C.Structure):
     _fields_ = [("tail_levels", C.c_int), ("level_tile", C.c_int * HELM_MAX_LEVELS),
-                ("cluster_levels", C.c_int), ("cluster_ctas", C.c_int)]
+                ("cluster_levels", C.c_int), ("cluster_ctas", C.c_int), ("cluster_halo", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -427,13 +427,13 @@ def helm_profile_read(h: Handle) -> dict:
 
 def _tuning_to_dict(t: _Tuning, nlev: int) -> dict:
     return {"tail_levels": t.tail_levels, "level_tile": [_TILE_NAMES[t.level_tile[l]] for l in range(nlev)],
-            "cluster_levels": t.cluster_levels, "cluster_ctas": t.cluster_ctas}
+            "cluster_levels": t.cluster_levels, "cluster_ctas": t.cluster_ctas, "cluster_halo": t.cluster_halo}
 
 
 def helm_get_tuning(h: Handle) -> dict:
     """The handle's kernel choices: tail_levels (-1 = as many as fit), a tile name per level
-    ("none" = separate sweep / residual / transfer launches), cluster_levels (0 = off) and
-    cluster_ctas (8 or 16)."""
+    ("none" = separate sweep / residual / transfer launches), cluster_levels (0 = off),
+    cluster_ctas (8 or 16) and cluster_halo (1 or 3 rows beyond each block's slab)."""
     t = _Tuning()
     _check(load().helm_get_tuning(h.ptr, C.byref(t)))
     return _tuning_to_dict(t, len(h.levels))
@@ -447,6 +447,7 @@ def helm_set_tuning(h: Handle, tuning: dict):
         t.level_tile[l] = TILES[name]
     t.cluster_levels = int(tuning.get("cluster_levels", t.cluster_levels))
     t.cluster_ctas = int(tuning.get("cluster_ctas", t.cluster_ctas))
+    t.cluster_halo = int(tuning.get("cluster_halo", t.cluster_halo))
     _check(load().helm_set_tuning(h.ptr, C.byref(t)))
 
 

@@ -41,13 +41,16 @@ def test_every_tuning_is_the_same_cycle(helm, oracle, n):
                for tile in ("none", "32x8", "16x16", "16x8", "64x4", "wave")]
     mixed = ["64x4", "wave", "16x8", "16x16", "32x8", "none"]
     choices.append(dict(tail_levels=-1, level_tile=[mixed[l % len(mixed)] for l in range(nlev)]))
-    # thread-block-cluster tails over the coarsest 2 .. 5 levels, 8 or 16 blocks
+    # thread-block-cluster tails over the coarsest 2 .. 5 levels, 8 or 16 blocks, 1 or 3 halo rows
     for cl in (2, 3, 4, 5):
         for nc in (8, 16):
-            choices.append(dict(tail_levels=0, level_tile=["16x8"] * nlev, cluster_levels=cl, cluster_ctas=nc))
+            for halo in (1, 3):
+                choices.append(dict(tail_levels=0, level_tile=["16x8"] * nlev, cluster_levels=cl, cluster_ctas=nc,
+                                    cluster_halo=halo))
     for c in choices:
         c.setdefault("cluster_levels", 0)
         c.setdefault("cluster_ctas", 16)
+        c.setdefault("cluster_halo", 3)
         helm.helm_set_tuning(h, c)
         got = helm.helm_get_tuning(h)
         assert got == c
@@ -88,6 +91,8 @@ def test_set_tuning_rejects_bad_values(helm):
         helm.helm_set_tuning(h, dict(cluster_levels=1))
     with pytest.raises(helm.HelmError):
         helm.helm_set_tuning(h, dict(cluster_levels=2, cluster_ctas=4))
+    with pytest.raises(helm.HelmError):
+        helm.helm_set_tuning(h, dict(cluster_levels=2, cluster_halo=2))
 
 
 @pytest.mark.parametrize("smoother,nu,gamma", [("rb", (1, 1), (1, 2)), ("jacobi", (1, 2), (2, 2)), ("jacobi", (0, 1), (1, 1))])
@@ -105,3 +110,38 @@ def test_cluster_tail_general_cycles(helm, oracle, smoother, nu, gamma):
         helm.helm_set_tuning(h, dict(tail_levels=0, level_tile=["none"] * nlev, cluster_levels=cl, cluster_ctas=8))
         z = to_np(helm.mg_precondition(h, to_gpu(v)))
         assert rel_l2(z, ref) <= 2e-5, cl
+
+
+def kernel_names(fn):
+    """Names of the CUDA kernels fn launches (torch's profiler); None when it records none."""
+    from torch.profiler import ProfilerActivity, profile
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        fn()
+        torch.cuda.synchronize()
+    names = {e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA}
+    return names or None
+
+
+@pytest.mark.parametrize("n", [129, 257, 1025])
+@pytest.mark.parametrize("nu", [(2, 2), (1, 2), (2, 1), (0, 1), (1, 0)])
+def test_deep_halo_cluster_tail_equals_one_row_tail(helm, n, nu):
+    """With three halo rows each block recomputes the rows next to its slab from the same
+    operands with the same operations as their owner, so the cycle equals the one-row cluster
+    tail's bit for bit, for every tail depth and cluster size that fits."""
+    P = problem(n)
+    h = gpu_handle(helm, P, pc="csg", prec="c64", nu=nu)
+    nlev = len(h.levels)
+    v = to_gpu(W.random_field(P.k2.shape, 44))
+    ran_deep = False
+    for cl in (2, 3, 4, 5):
+        for nc in (8, 16):
+            outs = []
+            for halo in (1, 3):
+                helm.helm_set_tuning(h, dict(tail_levels=0, level_tile=["16x8"] * nlev, cluster_levels=cl,
+                                             cluster_ctas=nc, cluster_halo=halo))
+                outs.append(helm.mg_precondition(h, v))
+                if halo == 3 and not ran_deep:
+                    names = kernel_names(lambda: helm.mg_precondition(h, v))
+                    ran_deep = names is None or any("k_mg_chalo" in s for s in names)
+            assert torch.equal(outs[0], outs[1]), (cl, nc)
+    assert ran_deep

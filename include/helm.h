@@ -373,7 +373,8 @@ typedef enum {
     HELM_TILE_64x4 = 3,
     HELM_TILE_WAVE = 4, /* register wavefront: one warp per strip of 13 coarse columns and 8 coarse
                            rows, the sweeps pipelined down the rows, no shared memory */
-    HELM_TILE_COUNT = 5
+    HELM_TILE_8x8 = 5,  /* small tiles: more blocks and fewer passes per phase on the small levels */
+    HELM_TILE_COUNT = 6
 } helm_tile;
 typedef struct {
     int tail_levels;

@@ -175,6 +175,9 @@ bool plan(BatchLockstep *L, bool commit) {
     std::map<std::pair<int, int>, int> tile_of;
     for (int l = 0; l < nr - T; l++) {
         int t = l < HELM_MAX_LEVELS ? R->tune.level_tile[l] : HELM_TILE_32x8;
+        // the small tile pays off when a lone small level leaves most SMs idle; a launch over many
+        // problems fills the GPU, where its larger halo share costs time
+        if (t == HELM_TILE_8x8) t = HELM_TILE_16x8;
         if (t == HELM_TILE_NONE || t == HELM_TILE_WAVE || !fused_jacobi2_ok(R->lv[l].n, 2, t)) t = HELM_TILE_32x8;
         tile_of[{R->lv[l].n[0], R->lv[l].n[1]}] = t;
     }

@@ -1181,12 +1181,13 @@ template cudaError_t launch_mg_tail<double>(int, int, const DevOp<double> *, dou
                                             double2 *const *, const double2 *, int, int, int, int, double, int, int,
                                             int, cudaStream_t);
 
-// Tile shapes (coarse nodes per block) of the temporally blocked kernels, by tile index.
-static const int kTiles[HELM_TILE_WAVE][2] = {{32, 8}, {16, 16}, {16, 8}, {64, 4}};
+// Tile shapes (coarse nodes per block) of the temporally blocked kernels, by tile index (the
+// wavefront, HELM_TILE_WAVE, has none).
+static const int kTiles[HELM_TILE_COUNT][2] = {{32, 8}, {16, 16}, {16, 8}, {64, 4}, {0, 0}, {8, 8}};
 
 bool fused_jacobi2_ok(const int n[3], int dim, int tile) {
     if (tile == HELM_TILE_WAVE) return wave_jacobi2_ok(n, dim);
-    if (tile < 0 || tile >= HELM_TILE_WAVE) return false;
+    if (tile < 0 || tile >= HELM_TILE_COUNT) return false;
     if (dim != 2 || (n[0] - 1) % 2 || (n[1] - 1) % 2) return false;
     const int ncx = (n[0] + 1) / 2, ncy = (n[1] + 1) / 2;
     // the last tile's owned range must reach the last interior node: a tile row or column
@@ -1234,6 +1235,7 @@ cudaError_t launch_pre2_restrict(const DevOp<float> &op, int tile, float omega, 
     case 0: return pre2_t<32, 8>(op, omega, b, u_out, rc, s);
     case 1: return pre2_t<16, 16>(op, omega, b, u_out, rc, s);
     case 2: return pre2_t<16, 8>(op, omega, b, u_out, rc, s);
+    case HELM_TILE_8x8: return pre2_t<8, 8>(op, omega, b, u_out, rc, s);
     default: return pre2_t<64, 4>(op, omega, b, u_out, rc, s);
     }
 }
@@ -1246,6 +1248,7 @@ cudaError_t launch_prolong_post2(const DevOp<float> &op, int tile, float omega, 
     case 0: return post2_t<32, 8>(op, omega, b, u_in, u_out, ec, s);
     case 1: return post2_t<16, 16>(op, omega, b, u_in, u_out, ec, s);
     case 2: return post2_t<16, 8>(op, omega, b, u_in, u_out, ec, s);
+    case HELM_TILE_8x8: return post2_t<8, 8>(op, omega, b, u_in, u_out, ec, s);
     default: return post2_t<64, 4>(op, omega, b, u_in, u_out, ec, s);
     }
 }
@@ -1287,6 +1290,7 @@ cudaError_t launch_pre2_restrict_batch(const int n[3], int tile, int count, cons
     case 0: return pre2_b_t<32, 8>(n[0], n[1], count, tab, omega, s);
     case 1: return pre2_b_t<16, 16>(n[0], n[1], count, tab, omega, s);
     case 2: return pre2_b_t<16, 8>(n[0], n[1], count, tab, omega, s);
+    case HELM_TILE_8x8: return pre2_b_t<8, 8>(n[0], n[1], count, tab, omega, s);
     default: return pre2_b_t<64, 4>(n[0], n[1], count, tab, omega, s);
     }
 }
@@ -1298,6 +1302,7 @@ cudaError_t launch_prolong_post2_batch(const int n[3], int tile, int count, cons
     case 0: return post2_b_t<32, 8>(n[0], n[1], count, tab, omega, j, s);
     case 1: return post2_b_t<16, 16>(n[0], n[1], count, tab, omega, j, s);
     case 2: return post2_b_t<16, 8>(n[0], n[1], count, tab, omega, j, s);
+    case HELM_TILE_8x8: return post2_b_t<8, 8>(n[0], n[1], count, tab, omega, j, s);
     default: return post2_b_t<64, 4>(n[0], n[1], count, tab, omega, j, s);
     }
 }

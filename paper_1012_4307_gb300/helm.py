@@ -58,7 +58,7 @@ class _MG(C.Structure):
 
 
 HELM_MAX_LEVELS = 16
-TILES = {"none": -1, "32x8": 0, "16x16": 1, "16x8": 2, "64x4": 3, "wave": 4}
+TILES = {"none": -1, "32x8": 0, "16x16": 1, "16x8": 2, "64x4": 3, "wave": 4, "8x8": 5}
 _TILE_NAMES = {v: k for k, v in TILES.items()}
 
 

@@ -38,8 +38,8 @@ def test_every_tuning_is_the_same_cycle(helm, oracle, n):
     vg = to_gpu(v)
     nlev = len(h.levels)
     choices = [dict(tail_levels=t, level_tile=[tile] * nlev) for t in (0, 2, 3)
-               for tile in ("none", "32x8", "16x16", "16x8", "64x4", "wave")]
-    mixed = ["64x4", "wave", "16x8", "16x16", "32x8", "none"]
+               for tile in ("none", "32x8", "16x16", "16x8", "64x4", "wave", "8x8")]
+    mixed = ["64x4", "wave", "16x8", "8x8", "16x16", "32x8", "none"]
     choices.append(dict(tail_levels=-1, level_tile=[mixed[l % len(mixed)] for l in range(nlev)]))
     # thread-block-cluster tails over the coarsest 2 .. 5 levels, 8 or 16 blocks, 1 or 3 halo rows
     for cl in (2, 3, 4, 5):

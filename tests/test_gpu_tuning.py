@@ -145,3 +145,28 @@ def test_deep_halo_cluster_tail_equals_one_row_tail(helm, n, nu):
                     ran_deep = names is None or any("k_mg_chalo" in s for s in names)
             assert torch.equal(outs[0], outs[1]), (cl, nc)
     assert ran_deep
+
+
+@pytest.mark.parametrize("nx,ny", [(257, 129), (129, 257)])
+def test_deep_halo_cluster_tail_on_nonsquare_grids(helm, oracle, nx, ny):
+    """Non-square grids (each block owns a slab of rows of every level, the columns whole): the
+    three-row cluster tail equals the one-row tail bit for bit, and both follow the oracle's
+    cycle to complex64 accuracy, for every tail depth and cluster size that fits."""
+    k2 = np.ascontiguousarray(W.k2_well_growth(2, max(nx, ny), kh_max=0.5)[:ny, :nx])
+    P = W.Problem("ns", 2, [nx, ny], k2, np.zeros((ny, nx), complex), coarsest_n=17)
+    h = gpu_handle(helm, P, pc="csg", prec="c64")
+    A, M = oracle_pair(oracle, P)
+    v = W.random_field((ny, nx), 45)
+    ref = oracle.MG(M, P.coarsest_n, 2, 2, 0.8, "jacobi").cycle(v)
+    vg = to_gpu(v)
+    nlev = len(h.levels)
+    for cl in range(2, nlev + 1):
+        for nc in (8, 16):
+            outs = []
+            for halo in (1, 3):
+                helm.helm_set_tuning(h, dict(tail_levels=0, level_tile=["16x8"] * nlev, cluster_levels=cl,
+                                             cluster_ctas=nc, cluster_halo=halo))
+                z = helm.mg_precondition(h, vg)
+                assert rel_l2(to_np(z), ref) <= 2e-5, (cl, nc, halo)
+                outs.append(z)
+            assert torch.equal(outs[0], outs[1]), (cl, nc)

@@ -548,6 +548,7 @@ def run_batch(args, count, steps, warmup, extra=False):
     """count problems solved together by helm_solve_batch, against the same problems solved one
     after another by krylov_solve.  Under torchrun the problems are sharded over the ranks by
     longest processing time (no data exchange); the job's time is the slowest rank's."""
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -563,8 +564,14 @@ def run_batch(args, count, steps, warmup, extra=False):
     mg = helm.MGParams(kind="csg", theta_a=probs[0].theta_a, prec="c64", gs=args.gs, coarsest_n=17)
     specs = [dict(dim=2, n=P.n, k2=torch.from_numpy(P.k2), theta=P.theta) for P in probs]
     b = helm.helm_create_batch(specs, mg=mg)
-    rhs = [torch.from_numpy(P.f).cuda() for P in probs]
-    xs = [torch.zeros_like(r) for r in rhs]
+    # every problem's right-hand side and solution as a view into one device buffer each, so that
+    # a whole batch moves between host and device in one copy per direction
+    sizes = [P.f.size for P in probs]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(int)
+    rhs_flat = torch.from_numpy(np.concatenate([P.f.ravel() for P in probs])).cuda()
+    x_flat = torch.zeros_like(rhs_flat)
+    rhs = [rhs_flat[offs[i]:offs[i + 1]].view(P.f.shape) for i, P in enumerate(probs)]
+    xs = [x_flat[offs[i]:offs[i + 1]].view(P.f.shape) for i, P in enumerate(probs)]
     if args.ncu_case:
         # profiling case: the stored tunings, one batch solve capped at ncu_case iterations
         for i in range(len(probs)):
@@ -584,8 +591,7 @@ def run_batch(args, count, steps, warmup, extra=False):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def batch_once():
-        for x in xs:
-            x.zero_()
+        x_flat.zero_()
         return helm.helm_solve_batch(b, rhs, xs, tol=args.tol, restart=30, maxit=5000)
 
     for _ in range(max(1, warmup)):
@@ -632,23 +638,22 @@ def run_batch(args, count, steps, warmup, extra=False):
     roof = roofline_from_profile(prof, peaks, peak_src, sm_max, "batch-%d" % count)
     breakdown = breakdown_from_profile(prof, peaks.get("hbm_gbs", 6800.0))
 
-    # end to end: every problem's rhs from pinned host memory, the batch solve, every solution back
-    f_host = [torch.from_numpy(P.f).pin_memory() for P in probs]
-    x_host = [torch.empty_like(fh).pin_memory() for fh in f_host]
+    # end to end: every problem's rhs from pinned host memory (one buffer, one copy), the batch
+    # solve, every solution back (one copy)
+    f_host = rhs_flat.cpu().pin_memory()
+    x_host = torch.empty_like(f_host).pin_memory()
     e2e_ms = 0.0
     for _ in range(steps):
         flush.fill_(3)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for r, fh in zip(rhs, f_host):
-            r.copy_(fh, non_blocking=True)
+        rhs_flat.copy_(f_host, non_blocking=True)
         batch_once()
-        for xh, x in zip(x_host, xs):
-            xh.copy_(x, non_blocking=True)
+        x_host.copy_(x_flat, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_ms = D.max_over_ranks(e2e_ms / steps, device="cuda")
-    nbytes = sum(fh.numel() * 16 for fh in f_host)
+    nbytes = f_host.numel() * 16
     e2e = {"value": unknowns_all / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms}
 

@@ -514,8 +514,14 @@ template <typename C> __global__ void k_zero(size_t n, C *x) {
 // interior of the grid are held at zero (Dirichlet).  Same arithmetic as k_jacobi /
 // k_residual_restrict / k_prolong_add, in one launch per phase of the cycle instead of three.
 // The tile shape is a template parameter; the host picks one per level (tuning).
+// Threads of a block of the blocked kernels for a region of n nodes: the fewest passes over the
+// region with at most 512 threads, then the fewest warps for that many passes (a fixed 256 left a
+// nearly empty last pass on some tiles: 777 = 3 x 256 + 9).
+constexpr int tile_threads(int n) { return ((n + (n + 511) / 512 - 1) / ((n + 511) / 512) + 31) / 32 * 32; }
+
 template <int TCX, int TCY> struct Tile {
     static constexpr int RW = 2 * TCX + 5, RH = 2 * TCY + 5;  // R3 extent
+    static constexpr int NT = tile_threads(RW * RH);           // threads per block
     struct Coef {
         float2 x[RW][3], y[RH][3];
     };
@@ -578,11 +584,11 @@ __device__ __forceinline__ float2 tile_jacobi(const TC &tc, const float2 (*u)[RW
     return cadd(uc, cscale(csub(t, uc), omega));
 }
 
-// f(sx, sy) for every node of an RW x RH region, 256 threads, node q = tid + 256 k in row-major
+// f(sx, sy) for every node of an RW x RH region, ST threads, node q = tid + ST k in row-major
 // order (the region coordinates advance incrementally).
-template <int RW, int RH, typename F>
+template <int RW, int RH, int ST, typename F>
 __device__ __forceinline__ void for_region(F f) {
-    constexpr int N = RW * RH, ST = 256, DX = ST % RW, DY = ST / RW;
+    constexpr int N = RW * RH, DX = ST % RW, DY = ST / RW;
     int sx = threadIdx.x % RW, sy = threadIdx.x / RW;
     for (int q = threadIdx.x; q < N; q += ST) {
         f(sx, sy);
@@ -621,7 +627,7 @@ __device__ __forceinline__ void pre2_restrict_tile(const OpView<float> &o, float
     tile_coef<RW, RH>(o, X0, Y0, T.tc);
     __syncthreads();
     // load b and 1 / D; sweep 1 from zero (pointwise): u1 = omega b / D
-    for_region<RW, RH>([&](int sx, int sy) {
+    for_region<RW, RH, TL::NT>([&](int sx, int sy) {
         const int x = X0 + sx, y = Y0 + sy;
         float2 bv = make_float2(0.f, 0.f), dv = make_float2(0.f, 0.f);
         if (inside(x, y)) {
@@ -635,7 +641,7 @@ __device__ __forceinline__ void pre2_restrict_tile(const OpView<float> &o, float
     });
     __syncthreads();
     // sweep 2 on R3 shrunk by one
-    for_region<RW, RH>([&](int sx, int sy) {
+    for_region<RW, RH, TL::NT>([&](int sx, int sy) {
         float2 v = make_float2(0.f, 0.f);
         if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy))
             v = tile_jacobi<RW>(T.tc, T.u1, T.b, T.di, sx, sy, omega);
@@ -643,7 +649,7 @@ __device__ __forceinline__ void pre2_restrict_tile(const OpView<float> &o, float
     });
     __syncthreads();
     // owned fine nodes of the smoothed iterate, and the residual on R3 shrunk by two
-    for_region<RW, RH>([&](int sx, int sy) {
+    for_region<RW, RH, TL::NT>([&](int sx, int sy) {
         const int x = X0 + sx, y = Y0 + sy;
         const bool in = inside(x, y);
         if (in && sx >= 2 && sx < 2 + 2 * TCX && sy >= 2 && sy < 2 + 2 * TCY) u[(size_t)x + (size_t)nx * y] = T.u2[sy][sx];
@@ -670,7 +676,7 @@ __device__ __forceinline__ void pre2_restrict_tile(const OpView<float> &o, float
 }
 
 template <int TCX, int TCY>
-__global__ void __launch_bounds__(256) k_pre2_restrict(OpView<float> o, float omega, const float2 *__restrict__ b,
+__global__ void __launch_bounds__(Tile<TCX, TCY>::NT, 4) k_pre2_restrict(OpView<float> o, float omega, const float2 *__restrict__ b,
                                                        float2 *__restrict__ u, float2 *__restrict__ rc, int ncx,
                                                        int ncy) {
     pdl_enter();
@@ -703,7 +709,7 @@ __device__ __forceinline__ void prolong_post2_tile(const OpView<float> &o, float
     }
     __syncthreads();
     // u3 = u + P ec on the region
-    for_region<RW, RH>([&](int sx, int sy) {
+    for_region<RW, RH, TL::NT>([&](int sx, int sy) {
         const int x = X0 + sx, y = Y0 + sy;
         float2 bv = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
         float2 dv = make_float2(0.f, 0.f);
@@ -721,7 +727,7 @@ __device__ __forceinline__ void prolong_post2_tile(const OpView<float> &o, float
     });
     __syncthreads();
     // sweep 1 on R3 shrunk by one
-    for_region<RW, RH>([&](int sx, int sy) {
+    for_region<RW, RH, TL::NT>([&](int sx, int sy) {
         float2 v = make_float2(0.f, 0.f);
         if (sx >= 1 && sx < RW - 1 && sy >= 1 && sy < RH - 1 && inside(X0 + sx, Y0 + sy))
             v = tile_jacobi<RW>(T.tc, T.u3, T.b, T.di, sx, sy, omega);
@@ -737,7 +743,7 @@ __device__ __forceinline__ void prolong_post2_tile(const OpView<float> &o, float
 }
 
 template <int TCX, int TCY>
-__global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float omega, const float2 *__restrict__ b,
+__global__ void __launch_bounds__(Tile<TCX, TCY>::NT, 4) k_prolong_post2(OpView<float> o, float omega, const float2 *__restrict__ b,
                                                        const float2 *__restrict__ u_in, float2 *__restrict__ u,
                                                        const float2 *__restrict__ ec, int ncx, int ncy) {
     pdl_enter();
@@ -747,7 +753,7 @@ __global__ void __launch_bounds__(256) k_prolong_post2(OpView<float> o, float om
 // Batched forms (many problems, one launch): blockIdx.z picks the table entry, whose level has
 // the same nodes in every entry of one launch; entries whose problem is inactive return at once.
 template <int TCX, int TCY>
-__global__ void __launch_bounds__(256) k_pre2_restrict_b(const BLevel *__restrict__ tab, float omega) {
+__global__ void __launch_bounds__(Tile<TCX, TCY>::NT, 4) k_pre2_restrict_b(const BLevel *__restrict__ tab, float omega) {
     pdl_enter();
     const BLevel &E = tab[blockIdx.z];
     if (*E.active == 0) return;
@@ -756,7 +762,7 @@ __global__ void __launch_bounds__(256) k_pre2_restrict_b(const BLevel *__restric
 }
 
 template <int TCX, int TCY>
-__global__ void __launch_bounds__(256) k_prolong_post2_b(const BLevel *__restrict__ tab, float omega, int j) {
+__global__ void __launch_bounds__(Tile<TCX, TCY>::NT, 4) k_prolong_post2_b(const BLevel *__restrict__ tab, float omega, int j) {
     pdl_enter();
     const BLevel &E = tab[blockIdx.z];
     if (*E.active == 0) return;
@@ -1207,7 +1213,7 @@ static cudaError_t pre2_t(const DevOp<float> &op, float omega, const float2 *b, 
         attr = true;
     }
     dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY));
-    launch_pdl(k_pre2_restrict<TCX, TCY>, g, 256, smem, s, view(op), omega, b, u_out, rc, ncx, ncy);
+    launch_pdl(k_pre2_restrict<TCX, TCY>, g, Tile<TCX, TCY>::NT, smem, s, view(op), omega, b, u_out, rc, ncx, ncy);
     return cudaGetLastError();
 }
 
@@ -1223,7 +1229,8 @@ static cudaError_t post2_t(const DevOp<float> &op, float omega, const float2 *b,
         attr = true;
     }
     dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY));
-    launch_pdl(k_prolong_post2<TCX, TCY>, g, 256, smem, s, view(op), omega, b, u_in, u_out, ec, ncx, ncy);
+    launch_pdl(k_prolong_post2<TCX, TCY>, g, Tile<TCX, TCY>::NT, smem, s, view(op), omega, b, u_in, u_out, ec, ncx,
+               ncy);
     return cudaGetLastError();
 }
 
@@ -1264,7 +1271,7 @@ static cudaError_t pre2_b_t(int n0, int n1, int count, const BLevel *tab, float 
         attr = true;
     }
     dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY), count);
-    launch_pdl(k_pre2_restrict_b<TCX, TCY>, g, 256, smem, s, tab, omega);
+    launch_pdl(k_pre2_restrict_b<TCX, TCY>, g, Tile<TCX, TCY>::NT, smem, s, tab, omega);
     return cudaGetLastError();
 }
 
@@ -1279,7 +1286,7 @@ static cudaError_t post2_b_t(int n0, int n1, int count, const BLevel *tab, float
         attr = true;
     }
     dim3 g(cdiv(ncx - 2, TCX), cdiv(ncy - 2, TCY), count);
-    launch_pdl(k_prolong_post2_b<TCX, TCY>, g, 256, smem, s, tab, omega, j);
+    launch_pdl(k_prolong_post2_b<TCX, TCY>, g, Tile<TCX, TCY>::NT, smem, s, tab, omega, j);
     return cudaGetLastError();
 }
 

@@ -397,7 +397,7 @@ def run_single(args, workload, steps, warmup, extra=False):
             if tuning:
                 helm.helm_set_tuning(h, tuning)
         else:
-            tuning, tune_ms = helm.helm_autotune(h, "c64", reps=10, cache=helm.default_tuning_cache())
+            tuning, tune_ms = helm.helm_autotune(h, "c64", reps=25, cache=helm.default_tuning_cache())
 
     def solve(handle, out):
         out.zero_()
@@ -584,7 +584,7 @@ def run_batch(args, count, steps, warmup, extra=False):
         print(json.dumps({"ncu_case": "batch-%d" % count, "engine": helm.helm_batch_get_engine(b),
                           "iterations": [x.iterations for x in st]}), flush=True)
         return None
-    tunings = None if args.no_tune else helm.helm_autotune_batch(b, "c64", cache=helm.default_tuning_cache())
+    tunings = None if args.no_tune else helm.helm_autotune_batch(b, "c64", reps=25, cache=helm.default_tuning_cache())
     unknowns = sum(P.unknowns for P in probs)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -477,7 +477,7 @@ def cached_tuning(h: Handle, prec: str = "c64", cache: str | None = None):
         return json.load(fh).get(tuning_key(h, prec), {}).get("tuning")
 
 
-def helm_autotune(h: Handle, prec: str = "c64", reps: int = 10, cache: str | None = None, retune: bool = False):
+def helm_autotune(h: Handle, prec: str = "c64", reps: int = 25, cache: str | None = None, retune: bool = False):
     """Picks the cycle's kernels (tail depth, tile shape per level) by timing preconditioner
     applications on the device, installs the choice and returns (tuning dict, ms per cycle).
     With a cache path (JSON, keyed by tuning_key), a stored choice is installed without timing
@@ -571,7 +571,7 @@ def batch_handle(b: Batch, i: int) -> Handle:
     return h
 
 
-def helm_autotune_batch(b: Batch, prec: str = "c64", reps: int = 10, cache: str | None = None) -> dict:
+def helm_autotune_batch(b: Batch, prec: str = "c64", reps: int = 25, cache: str | None = None) -> dict:
     """Autotunes one handle per distinct grid of the batch (through helm_autotune and its cache)
     and installs the choice on every problem with that grid; returns {tuning key: tuning}."""
     chosen = {}

@@ -367,7 +367,6 @@ helm_status build(BatchLockstep *L, int m) {
 struct Prof {
     BatchLockstep *L;
     const std::vector<char> *act;
-    helm_handle *h0() const { return L->h[0]; }
     bool on() const { return L->h[0]->prof.on && !L->capturing; }
 };
 double interior(const LevelDev &Lv) { return (double)(Lv.n[0] - 2) * (Lv.n[1] - 2); }

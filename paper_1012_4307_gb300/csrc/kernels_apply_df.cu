@@ -46,7 +46,7 @@ __device__ __forceinline__ void apply_A_df_tile(const DevOpDF &o, const float2 *
     const ff dxy_r = ff_add(ff{cxc.x, cxc.y}, ff{cyc.x, cyc.y}), dxy_i = ff_add(ff{cxc.z, cxc.w}, ff{cyc.z, cyc.w});
     if constexpr (DIM == 3) {
         // march in z with the column (z - 1, z, z + 1) in registers and the next plane's
-        // operands loaded while this plane is processed (same arithmetic order as below)
+        // operands loaded while this plane is processed (same arithmetic order as the 2D branch)
         size_t p = (size_t)i + sy * ((size_t)j + (size_t)ny * k0);
         float2 zm = z[p - sz], zc = z[p];
         float2 zw = z[p - 1], ze = z[p + 1], zs = z[p - sy], zn = z[p + sy], zp = z[p + sz];
@@ -81,28 +81,21 @@ __device__ __forceinline__ void apply_A_df_tile(const DevOpDF &o, const float2 *
             zc = zp;
             zw = zw2; ze = ze2; zs = zs2; zn = zn2; zp = zp2; kk = kk2;
         }
-        return;
-    }
-    for (int k = k0; k < k1; k++) {
-        const size_t p = (size_t)i + sy * ((size_t)j + (size_t)ny * k);
-        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-        cmac(cxw, z[p - 1], sr, cr, si, ci);
-        cmac(cxe, z[p + 1], sr, cr, si, ci);
-        cmac(cyw, z[p - sy], sr, cr, si, ci);
-        cmac(cye, z[p + sy], sr, cr, si, ci);
-        ff dr = dxy_r, di = dxy_i;
-        if (DIM == 3) {
-            const float4 czw = o.coef[2][3 * k], czc = o.coef[2][3 * k + 1], cze = o.coef[2][3 * k + 2];
-            cmac(czw, z[p - sz], sr, cr, si, ci);
-            cmac(cze, z[p + sz], sr, cr, si, ci);
-            dr = ff_add(dr, ff{czc.x, czc.y});
-            di = ff_add(di, ff{czc.z, czc.w});
+    } else {
+        for (int k = k0; k < k1; k++) {
+            const size_t p = (size_t)i + sy * ((size_t)j + (size_t)ny * k);
+            float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+            cmac(cxw, z[p - 1], sr, cr, si, ci);
+            cmac(cxe, z[p + 1], sr, cr, si, ci);
+            cmac(cyw, z[p - sy], sr, cr, si, ci);
+            cmac(cye, z[p + sy], sr, cr, si, ci);
+            ff dr = dxy_r, di = dxy_i;
+            const float2 kk = o.k2[p];
+            dr = ff_add(dr, ff{-kk.x, -kk.y});  // diagonal: sum of centre coefficients - k^2
+            cmac(make_float4(dr.hi, dr.lo, di.hi, di.lo), z[p], sr, cr, si, ci);
+            const ff yr = ff_norm(sr, cr), yi = ff_norm(si, ci);
+            y[p] = make_float4(yr.hi, yr.lo, yi.hi, yi.lo);
         }
-        const float2 kk = o.k2[p];
-        dr = ff_add(dr, ff{-kk.x, -kk.y});  // diagonal: sum of centre coefficients - k^2
-        cmac(make_float4(dr.hi, dr.lo, di.hi, di.lo), z[p], sr, cr, si, ci);
-        const ff yr = ff_norm(sr, cr), yi = ff_norm(si, ci);
-        y[p] = make_float4(yr.hi, yr.lo, yi.hi, yi.lo);
     }
 }
 

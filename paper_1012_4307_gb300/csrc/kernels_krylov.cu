@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(NT) k_mdot_norm(size_t n, const double2 *__res
     }
     block_sum<CH + 1>(acc, sums);
     const int G = gridDim.x;
-    if (threadIdx.x < CH && (int)threadIdx.x < cnt) partials[(size_t)(i0 + threadIdx.x) * G + blockIdx.x] = sums[threadIdx.x];
+    if constexpr (CH > 0)
+        if (threadIdx.x < CH && (int)threadIdx.x < cnt) partials[(size_t)(i0 + threadIdx.x) * G + blockIdx.x] = sums[threadIdx.x];
     if (first && threadIdx.x == CH) partials[(size_t)nv * G + blockIdx.x] = sums[CH];
 }
 

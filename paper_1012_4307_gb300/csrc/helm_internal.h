@@ -102,9 +102,10 @@ cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, float
 // captures a CUDA graph (pdl_capture_scope): measured on GB300, replayed graphs of the FGMRES
 // steps ran about 4% slower with programmatic edges, while eager launch sequences (the cycle
 // alone) ran about 10% faster with them.
-// The multigrid cycle's launches (pdl_cycle_scope) keep the attribute inside captured graphs too:
-// its kernels are short and latency-bound, and each lets the next one's blocks be scheduled
-// while it drains.
+// Launches under pdl_cycle_scope keep the attribute inside captured graphs too: the multigrid
+// cycle's (short, latency-bound kernels, each letting the next one's blocks be scheduled while it
+// drains), and in a delayed-CGS2 step the reduction (a few blocks, placed while the dot pass
+// drains) and the update pass after it (placed while the reduction's few blocks finish).
 extern thread_local bool g_pdl_off, g_pdl_cycle;
 constexpr bool kPdlCycleInGraphs = true;
 struct pdl_capture_scope {

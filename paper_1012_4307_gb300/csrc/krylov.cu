@@ -401,7 +401,11 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
         if (fork) CKE(cudaEventRecord(h->ev_join, h->side));
     }
     {
-        // the update and the norm of the new vector in one launch
+        // the update and the norm of the new vector in one launch; launched programmatically, so
+        // that its blocks are placed on the SMs while the few blocks of the reduction finish
+        // (about 2 us per step; the same attribute on the dot pass, which follows the many-block
+        // apply, spread its one-wave grid unevenly and cost 36 us per step)
+        pdl_cycle_scope pdl;
         ProfScope ps(h, HELM_K_UPDATE_NORM, np * 16.0 * (nv + 3), 0);
         CKE(launch_update2_pair(np, V4, np, j, h->dcoef, h->partials, h->tickets + 1, h->alpha2 + j + 1,
                                 fold ? level0_rhs_c64(h) : nullptr, s));

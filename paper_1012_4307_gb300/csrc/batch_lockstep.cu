@@ -65,8 +65,9 @@ struct BatchLockstep {
     std::vector<unsigned> dot_blocks;  // per row j = 0 .. m (nv = j + 1)
     int *active = nullptr;             // device flags, one per problem
     int *active_h = nullptr;           // pinned staging of the flags
-    double *est_dev = nullptr;         // (m + 1) x P gathered estimates
-    double *est_h = nullptr;           // pinned copy
+    // (m + 1) x P gathered estimates, pinned host memory that the batched rotation kernel writes
+    // directly (no copy node in the step graphs)
+    double *est_h = nullptr;
     double2 *norm_h = nullptr;         // pinned: per problem ||f|| or ||r0||
     cudaStream_t s = nullptr, cap = nullptr;
     std::vector<cudaGraphExec_t> step_graph, close_graph;
@@ -96,7 +97,6 @@ struct BatchLockstep {
         vec = nullptr;
         apply_first = upd_first = dot_first = nullptr;
         active = nullptr;
-        est_dev = nullptr;
         key.clear();
     }
     ~BatchLockstep() {
@@ -329,8 +329,6 @@ helm_status build(BatchLockstep *L, int m) {
     CKR(upload(L, &L->apply_first, af));
     CKR(upload(L, &L->upd_first, uf));
     CKR(upload(L, &L->dot_first, df));
-    CKR(cudaMalloc((void **)&L->est_dev, (size_t)(m + 1) * P * sizeof(double)));
-    L->owned.push_back(L->est_dev);
     if (L->est_h) cudaFreeHost(L->est_h);
     L->est_h = nullptr;
     CKR(cudaMallocHost((void **)&L->est_h, (size_t)(m + 1) * P * sizeof(double)));
@@ -434,15 +432,12 @@ cudaError_t record_step(BatchLockstep *L, const Prof &pf, int j, cudaStream_t s)
     }
     if (j > 0) {
         ProfScope ps(h0, HELM_K_SMALL, 0, 0);
-        CKE(launch_givens_batch(P, L->vec, j - 1, L->est_dev + (size_t)(j - 1) * P, s));
+        CKE(launch_givens_batch(P, L->vec, j - 1, L->est_h + (size_t)(j - 1) * P, s));
     }
     {
         ProfScope ps(h0, HELM_K_UPDATE_NORM, vec_bytes(16.0 * (j + 4) + 8.0), 0);
         CKE(launch_update2_pair_batch(P, L->vec, L->upd_first, L->upd_blocks, j, s));
     }
-    if (j > 0)
-        CKE(cudaMemcpyAsync(L->est_h + (size_t)(j - 1) * P, L->est_dev + (size_t)(j - 1) * P, P * sizeof(double),
-                            cudaMemcpyDeviceToHost, s));
     return L->capturing ? cudaEventRecordWithFlags(L->step_ev[j], s, cudaEventRecordExternal)
                         : cudaEventRecord(L->step_ev[j], s);
 }
@@ -463,10 +458,8 @@ cudaError_t record_close(BatchLockstep *L, const Prof &pf, int jc, cudaStream_t 
     {
         ProfScope ps(h0, HELM_K_SMALL, 0, 0);
         CKE(launch_reduce_dcgs2_batch(P, L->vec, row, gs_df_dot2_groups(jc + 1), jc, 0, s));
-        CKE(launch_givens_batch(P, L->vec, jc - 1, L->est_dev + (size_t)(jc - 1) * P, s));
+        CKE(launch_givens_batch(P, L->vec, jc - 1, L->est_h + (size_t)(jc - 1) * P, s));
     }
-    CKE(cudaMemcpyAsync(L->est_h + (size_t)(jc - 1) * P, L->est_dev + (size_t)(jc - 1) * P, P * sizeof(double),
-                        cudaMemcpyDeviceToHost, s));
     return L->capturing ? cudaEventRecordWithFlags(L->close_ev[jc], s, cudaEventRecordExternal)
                         : cudaEventRecord(L->close_ev[jc], s);
 }

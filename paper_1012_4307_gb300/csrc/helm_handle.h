@@ -93,7 +93,7 @@ struct helm_handle {
     double *est_dev = nullptr;
     int *gs_flag = nullptr;   // DGKS decision of the current Arnoldi step (device)
     int *gs_count = nullptr;  // re-orthogonalisations in the current solve (device)
-    double *est_host = nullptr;  // pinned: residual estimate of every FGMRES step
+    double *est_host = nullptr;  // pinned: residual estimate of every FGMRES step (stored by the rotation kernel)
     int est_host_len = 0;
     double2 *fnorm_dev = nullptr;  // ||f|| of the current solve (device scalar)
     // FGMRES steps: one event per step j, and a CUDA graph of step j captured on cap_stream

@@ -411,7 +411,7 @@ cudaError_t launch_combine(size_t n, const CZ *Z, size_t ldz, int nz, const doub
 // FGMRES small dense work on the device (one warp): rotations of column j, new rotation,
 // residual estimate |g_{j+1}| / fnorm->x written to est[j].
 cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm,
-                          double *est, cudaStream_t s);
+                          double *est, double *est_host, cudaStream_t s);
 // y = H(0:k,0:k)^{-1} g(0:k)  (upper triangular back substitution)
 cudaError_t launch_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y, cudaStream_t s);
 

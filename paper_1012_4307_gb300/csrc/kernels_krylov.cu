@@ -205,8 +205,11 @@ __global__ void __launch_bounds__(NT) k_combine_df(size_t n, const float2 *__res
 // Called by one warp: the lanes stage column j of H (j + 2 entries) and the earlier rotations in
 // shared memory, lane 0 applies the rotations in order and forms the new one, the lanes write the
 // column back.  The arithmetic is that of a single thread walking the column in global memory.
+// est_host (may be null): pinned host memory, where est[j] is also stored, so that the host reads
+// the estimate once the step's event has fired, with no copy in the step (a device-to-host copy
+// node cost about 7 us per step at the end of every replayed step graph).
 __device__ __forceinline__ void givens_body(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g,
-                                            const double2 *fnorm_dev, double *est) {
+                                            const double2 *fnorm_dev, double *est, double *est_host = nullptr) {
     __shared__ double2 colS[66], snS[64];
     __shared__ double csS[64];
     const int lane = threadIdx.x & 31;
@@ -247,20 +250,22 @@ __device__ __forceinline__ void givens_body(double2 *H, int ldh, int j, double *
         g[j + 1] = cscale(cmul(make_double2(-s.x, s.y), gj), 1.0);
         g[j] = cscale(gj, c);
         est[j] = hypot(g[j + 1].x, g[j + 1].y) / fnorm;
+        if (est_host) est_host[j] = est[j];
     }
     __syncwarp();
     for (int i = lane; i <= j + 1; i += 32) col[i] = colS[i];
 }
 
 __global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm_dev,
-                         double *est) {
+                         double *est, double *est_host) {
     pdl_enter();
     if (threadIdx.x >= 32 || blockIdx.x != 0) return;
-    givens_body(H, ldh, j, cs, sn, g, fnorm_dev, est);
+    givens_body(H, ldh, j, cs, sn, g, fnorm_dev, est, est_host);
 }
 
 // Batched rotation of column j (block z = problem), and the gather of every problem's estimate
-// est[j] into out[problem] (-1 for inactive problems), for one copy to the host.
+// est[j] into out[problem] (-1 for inactive problems); out is pinned host memory, which the host
+// reads once the step's event has fired.
 __global__ void k_givens_b(const BVec *__restrict__ tab, int j, double *out) {
     pdl_enter();
     const BVec &P = tab[blockIdx.z];
@@ -512,8 +517,8 @@ template cudaError_t launch_combine<double2>(size_t, const double2 *, size_t, in
                                              double2 *, cudaStream_t);
 
 cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm,
-                          double *est, cudaStream_t s) {
-    k_givens<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g, fnorm, est);
+                          double *est, double *est_host, cudaStream_t s) {
+    k_givens<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g, fnorm, est, est_host);
     return cudaGetLastError();
 }
 

@@ -337,9 +337,8 @@ static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
     }
     {
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
-        CKE(launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, s));
+        CKE(launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, h->est_host, s));
     }
-    CKE(cudaMemcpyAsync(h->est_host + j, h->est_dev + j, sizeof(double), cudaMemcpyDeviceToHost, s));
     // inside a capture the record must become an event node of the graph (external), so that
     // the host can wait on the event after every replay
     return h->capturing ? cudaEventRecordWithFlags(h->step_ev[j], s, cudaEventRecordExternal)
@@ -397,7 +396,7 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
             CKE(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         }
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
-        CKE(launch_givens(h->H, ldh, j - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, gs));
+        CKE(launch_givens(h->H, ldh, j - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, h->est_host, gs));
         if (fork) CKE(cudaEventRecord(h->ev_join, h->side));
     }
     {
@@ -411,7 +410,6 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
                                 fold ? level0_rhs_c64(h) : nullptr, s));
     }
     if (fork) CKE(cudaStreamWaitEvent(s, h->ev_join, 0));
-    if (j > 0) CKE(cudaMemcpyAsync(h->est_host + j - 1, h->est_dev + j - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     return h->capturing ? cudaEventRecordWithFlags(h->step_ev[j], s, cudaEventRecordExternal)
                         : cudaEventRecord(h->step_ev[j], s);
 }
@@ -436,9 +434,8 @@ static cudaError_t fgmres_close_dcgs2(helm_handle *h, int jc, int m) {
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
         CKE(launch_reduce_dcgs2(h->partials, gs_df_dot2_nblocks(np, jc + 1), h->hv, h->tickets, jc, h->alpha2, h->H,
                                 ldh, h->dcoef, 0, s));
-        CKE(launch_givens(h->H, ldh, jc - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, s));
+        CKE(launch_givens(h->H, ldh, jc - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, h->est_host, s));
     }
-    CKE(cudaMemcpyAsync(h->est_host + jc - 1, h->est_dev + jc - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     return h->capturing ? cudaEventRecordWithFlags(h->close_ev[jc], s, cudaEventRecordExternal)
                         : cudaEventRecord(h->close_ev[jc], s);
 }

@@ -622,8 +622,7 @@ helm_status lockstep_solve(BatchLockstep *L, cudaStream_t user, const void *cons
         CKR(fan_out(L, cyc, [&](int p, cudaStream_t ps) -> cudaError_t {
             helm_handle *h = L->h[p];
             CKE(launch_split_scale(h->np, h->V, h->scal, ps));
-            CKE(cudaMemsetAsync(h->g, 0, (m + 1) * sizeof(double2), ps));
-            CKE(cudaMemcpyAsync(h->g, h->scal, sizeof(double2), cudaMemcpyDeviceToDevice, ps));
+            CKE(launch_cycle_start(h->g, m + 1, h->scal, nullptr, nullptr, 0.0, ps));
             return launch_pair_to_c64(h->np, (const float4 *)h->V, nullptr, h->lv[0].b32, ps);
         }));
         CKR(cudaMemcpyAsync(L->active, L->active_h, P * sizeof(int), cudaMemcpyHostToDevice, s));

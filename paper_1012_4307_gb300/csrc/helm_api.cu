@@ -722,7 +722,7 @@ static cudaError_t cycle(helm_handle *h, int l, const typename CT<R>::T *b, type
     }
     {
         ProfScope ps(h, HELM_K_PROLONG, ni * (2 * es + es / nd), 0);
-        CKE(launch_prolong_add<R>(L.n, h->dim, ec, cur, h->stream));
+        CKE(launch_prolong_add<R>(L.n, h->dim, ec, cur, h->stream, LvBuf<R>::op(L).gate));
     }
     CKE(smooth<R>(h, l, h->mg.nu2, b, &cur, &oth, false));
     if (cur != u) CKE(cudaMemcpyAsync(u, cur, L.np * sizeof(C), cudaMemcpyDeviceToDevice, h->stream));

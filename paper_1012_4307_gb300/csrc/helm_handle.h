@@ -91,7 +91,8 @@ struct helm_handle {
     double2 *partials = nullptr;
     double2 *scal = nullptr;   // scalar scratch (norms, Bi-CGSTAB scalars)
     double *est_dev = nullptr;
-    int *gs_flag = nullptr;   // DGKS decision of the current Arnoldi step (device)
+    int *gs_flag = nullptr;   // DGKS decision of the current Arnoldi step (device); [2]: the cycle's stop flag
+    double *tol_dev = nullptr;  // the solve's tolerance (device), for the stop flag
     int *gs_count = nullptr;  // re-orthogonalisations in the current solve (device)
     double *est_host = nullptr;  // pinned: residual estimate of every FGMRES step (stored by the rotation kernel)
     int est_host_len = 0;

@@ -82,6 +82,10 @@ template <typename R> struct DevOp {
     // 2D complex64 levels: 1 / (diagonal of M) at every node (0 off the interior), formed once
     // by launch_diag_inv for the temporally blocked smoothers; null otherwise
     const C *dinv = nullptr;
+    // device flag (null: none): when it is set at launch, this level's smoothing, residual and
+    // transfer kernels return at once.  Set only on the copy of the finest level's operator
+    // that an FGMRES step queued ahead of the host's convergence test launches with.
+    const int *gate = nullptr;
 };
 
 // The Helmholtz operator A = L_h - k^2 with coefficients and k^2 stored as float pairs
@@ -92,7 +96,9 @@ struct DevOpDF {
     const float2 *k2;
 };
 // y = A z in double-FP32 arithmetic, z complex64, y a float-pair vector (interior written).
-cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, float4 *y, cudaStream_t s);
+// gate (may be null): nothing is written when the device flag is set at launch.
+cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, float4 *y, cudaStream_t s,
+                             const int *gate = nullptr);
 
 // Programmatic dependent launch.  Every kernel of the library begins with pdl_wait() (it returns
 // once the kernel before it in the stream has finished and its writes are visible; a no-op when
@@ -174,7 +180,7 @@ cudaError_t launch_residual_restrict(const DevOp<R> &op, int dim, const CB *b, c
 // uf += P ec (fine nodes nf).
 template <typename R>
 cudaError_t launch_prolong_add(const int nf[3], int dim, const typename CT<R>::T *ec, typename CT<R>::T *uf,
-                               cudaStream_t s);
+                               cudaStream_t s, const int *gate = nullptr);
 // u = Minv b on the interior unknowns of the coarsest grid (nodes n), natural order.
 template <typename R>
 cudaError_t launch_dense_solve(const int n[3], int dim, int nu, const typename CT<R>::T *minv,
@@ -380,8 +386,11 @@ cudaError_t launch_update_norm_pair(size_t n, const float4 *V, size_t ldv, int n
 // alpha_j times the true ones (the preconditioner was applied to the unscaled slot j).
 // The update pass scales w by coef[2j+2].x and, with b_out, also writes the new slot j + 1 as
 // complex64 (the next step's preconditioner input).
+// gate (may be null): a device flag; when it is set at launch, the dot pass writes nothing and the
+// update pass leaves the vectors as they are (its norm partials are zero and its ticket protocol
+// still runs) -- used to skip FGMRES steps queued ahead of a converged one.
 cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *x, const float4 *w,
-                              double2 *partials, cudaStream_t s);
+                              double2 *partials, const int *gate, cudaStream_t s);
 // has_w as in launch_reduce_dcgs2_batch
 cudaError_t launch_reduce_dcgs2(const double2 *partials, int nblk, double2 *hv, unsigned *ticket, int j,
                                 const double2 *alpha2, double2 *H, int ldh, double2 *coef, int has_w,
@@ -389,7 +398,7 @@ cudaError_t launch_reduce_dcgs2(const double2 *partials, int nblk, double2 *hv, 
 cudaError_t launch_dcgs2_coef(int j, int has_w, const double2 *hv, const double2 *alpha2, double2 *H, int ldh,
                               double2 *coef, cudaStream_t s);
 cudaError_t launch_update2_pair(size_t n, float4 *V, size_t ldv, int j, const double2 *coef, double2 *partials,
-                                unsigned *ticket, double2 *alpha_out, float2 *b_out, cudaStream_t s);
+                                unsigned *ticket, double2 *alpha_out, float2 *b_out, const int *gate, cudaStream_t s);
 // w <- w / beta->x (float pairs)
 cudaError_t launch_scale_inv_pair(size_t n, float4 *w, const double2 *beta, cudaStream_t s);
 // in place: the double2 vector x becomes the float-pair vector x / beta->x (beta null: 1)
@@ -409,9 +418,16 @@ cudaError_t launch_combine(size_t n, const CZ *Z, size_t ldz, int nz, const doub
                            double2 *x, cudaStream_t s);
 
 // FGMRES small dense work on the device (one warp): rotations of column j, new rotation,
-// residual estimate |g_{j+1}| / fnorm->x written to est[j].
+// residual estimate |g_{j+1}| / fnorm->x written to est[j] and, when est_host is not null, to
+// est_host[j] (pinned host memory).  With stop not null, *stop = 1 when est[j] <= *tol (or is not
+// a number): the host's own convergence test, taken on the device so that the steps already
+// queued behind this one skip their vector passes.
 cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm,
-                          double *est, double *est_host, cudaStream_t s);
+                          double *est, double *est_host, const double *tol, int *stop, cudaStream_t s);
+// Start of an FGMRES cycle: g = (beta, 0, ..., 0) (len entries, beta = *beta), *stop = 0 and
+// *tol_dev = tol.
+cudaError_t launch_cycle_start(double2 *g, int len, const double2 *beta, int *stop, double *tol_dev, double tol,
+                               cudaStream_t s);
 // y = H(0:k,0:k)^{-1} g(0:k)  (upper triangular back substitution)
 cudaError_t launch_backsolve(const double2 *H, int ldh, int k, const double2 *g, double2 *y, cudaStream_t s);
 

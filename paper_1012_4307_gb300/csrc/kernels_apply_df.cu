@@ -100,8 +100,10 @@ __device__ __forceinline__ void apply_A_df_tile(const DevOpDF &o, const float2 *
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(BX *BY) k_apply_A_df(DevOpDF o, const float2 *__restrict__ z, float4 *__restrict__ y) {
+__global__ void __launch_bounds__(BX *BY) k_apply_A_df(DevOpDF o, const float2 *__restrict__ z, float4 *__restrict__ y,
+                                                       const int *__restrict__ gate) {
     pdl_enter();
+    if (gate && *gate) return;
     apply_A_df_tile<DIM>(o, z, y, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
@@ -134,9 +136,10 @@ cudaError_t launch_apply_A_df_batch(int count, const BVec *tab, const unsigned *
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, float4 *y, cudaStream_t s) {
+cudaError_t launch_apply_A_df(const DevOpDF &op, int dim, const float2 *z, float4 *y, cudaStream_t s,
+                              const int *gate) {
     dim3 g(cdiv(op.n[0] - 2, BX), cdiv(op.n[1] - 2, BY), dim == 3 ? cdiv(op.n[2] - 2, KCHUNK) : 1), b(BX, BY);
-    if (dim == 3) launch_pdl(k_apply_A_df<3>, g, b, 0, s, op, z, y);
-    else launch_pdl(k_apply_A_df<2>, g, b, 0, s, op, z, y);
+    if (dim == 3) launch_pdl(k_apply_A_df<3>, g, b, 0, s, op, z, y, gate);
+    else launch_pdl(k_apply_A_df<2>, g, b, 0, s, op, z, y, gate);
     return cudaGetLastError();
 }

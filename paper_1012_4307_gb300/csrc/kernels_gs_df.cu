@@ -303,8 +303,9 @@ __device__ __forceinline__ void mdot2_body(size_t n, const float4 *__restrict__ 
 template <int CH>
 __global__ void __launch_bounds__(NT, 6) k_mdot2_pair(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
                                                    const float4 *__restrict__ x, const float4 *__restrict__ w,
-                                                   double2 *__restrict__ partials) {
+                                                   double2 *__restrict__ partials, const int *__restrict__ gate) {
     pdl_enter();
+    if (gate && *gate) return;
     mdot2_body<CH>(n, V, ldv, nv, x, w, partials, blockIdx.x, gridDim.x);
 }
 
@@ -450,11 +451,12 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
     }
 }
 
-// bx: this block among the nblk blocks of the vector (see mdot2_body).
+// bx: this block among the nblk blocks of the vector (see mdot2_body).  skip: leave the vectors
+// as they are (zero norm partials; the ticket protocol still runs, so the ticket returns to 0).
 __device__ __forceinline__ void update2_body(size_t n, float4 *__restrict__ V, size_t ldv, int j,
                                              const double2 *__restrict__ coef, double2 *__restrict__ partials,
                                              unsigned *ticket, double2 *alpha_out, float2 *__restrict__ b_out, int bx,
-                                             int nblk) {
+                                             int nblk, bool skip) {
     __shared__ float4 cA[64], cC[64];
     __shared__ float4 sc[2];  // (r hi, lo, small-correction flag, 0), s
     __shared__ float2 rws;    // scale of the incoming w: coef[2j+2].x as a float pair
@@ -477,10 +479,12 @@ __device__ __forceinline__ void update2_body(size_t n, float4 *__restrict__ V, s
     __syncthreads();
     const ff rinv = ff_re(sc[0]), sr = ff_re(sc[1]), si = ff_im(sc[1]), rw{rws.x, rws.y};
     float sn = 0.f, cn = 0.f;
-    if (sc[0].z != 0.f)
+    if (skip) {
+    } else if (sc[0].z != 0.f) {
         update2_nodes<true>(n, V, ldv, j, cA, cC, rinv, sr, si, rw, b_out, sn, cn, bx, nblk);
-    else
+    } else {
         update2_nodes<false>(n, V, ldv, j, cA, cC, rinv, sr, si, rw, b_out, sn, cn, bx, nblk);
+    }
     ff vals[1] = {ff_norm(sn, cn)};
     block_sum_ff<1>(vals, sums);
     if (threadIdx.x == 0) partials[bx] = make_double2(sums[0], 0.0);
@@ -491,9 +495,10 @@ __device__ __forceinline__ void update2_body(size_t n, float4 *__restrict__ V, s
 
 __global__ void __launch_bounds__(NT, 4) k_update2_pair(size_t n, float4 *__restrict__ V, size_t ldv, int j,
                                                      const double2 *__restrict__ coef, double2 *__restrict__ partials,
-                                                     unsigned *ticket, double2 *alpha_out, float2 *__restrict__ b_out) {
+                                                     unsigned *ticket, double2 *alpha_out, float2 *__restrict__ b_out,
+                                                     const int *__restrict__ gate) {
     pdl_enter();
-    update2_body(n, V, ldv, j, coef, partials, ticket, alpha_out, b_out, blockIdx.x, gridDim.x);
+    update2_body(n, V, ldv, j, coef, partials, ticket, alpha_out, b_out, blockIdx.x, gridDim.x, gate && *gate);
 }
 
 // Batched update pass of step j: problem e takes blocks [first[e], first[e + 1]); its ticket
@@ -505,7 +510,7 @@ __global__ void __launch_bounds__(NT, 4) k_update2_pair_b(const BVec *__restrict
     const BVec &P = tab[e];
     if (*P.active == 0) return;
     update2_body(P.n, P.V, P.n, j, P.dcoef, P.partials, P.tickets + 1, P.alpha2 + j + 1, P.b0,
-                 (int)(blockIdx.x - first[e]), (int)(first[e + 1] - first[e]));
+                 (int)(blockIdx.x - first[e]), (int)(first[e + 1] - first[e]), false);
 }
 
 // 1 / beta.x as a float pair, one FP64 division per block.
@@ -635,18 +640,18 @@ int gs_df_dot2_nblocks(size_t n, int nv) {
 }
 
 cudaError_t launch_mdot2_pair(size_t n, const float4 *V, size_t ldv, int nv, const float4 *x, const float4 *w,
-                              double2 *partials, cudaStream_t s) {
+                              double2 *partials, const int *gate, cudaStream_t s) {
     if (nv < 1 || nv > 64) return cudaErrorInvalidValue;
     const unsigned g = (unsigned)gs_df_dot2_nblocks(n, nv) * (unsigned)((nv + DF_CH2 - 1) / DF_CH2);
-    launch_pdl(k_mdot2_pair<DF_CH2>, dim3(g), NT, 0, s, n, V, ldv, nv, x, w, partials);
+    launch_pdl(k_mdot2_pair<DF_CH2>, dim3(g), NT, 0, s, n, V, ldv, nv, x, w, partials, gate);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update2_pair(size_t n, float4 *V, size_t ldv, int j, const double2 *coef, double2 *partials,
-                                unsigned *ticket, double2 *alpha_out, float2 *b_out, cudaStream_t s) {
+                                unsigned *ticket, double2 *alpha_out, float2 *b_out, const int *gate, cudaStream_t s) {
     if (j < 0 || j > 64) return cudaErrorInvalidValue;
     launch_pdl(k_update2_pair, gs_df_update_nblocks(n), NT, 0, s, n, V, ldv, j, coef, partials, ticket, alpha_out,
-               b_out);
+               b_out, gate);
     return cudaGetLastError();
 }
 

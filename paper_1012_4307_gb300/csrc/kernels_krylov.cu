@@ -208,8 +208,10 @@ __global__ void __launch_bounds__(NT) k_combine_df(size_t n, const float2 *__res
 // est_host (may be null): pinned host memory, where est[j] is also stored, so that the host reads
 // the estimate once the step's event has fired, with no copy in the step (a device-to-host copy
 // node cost about 7 us per step at the end of every replayed step graph).
+// tol, stop (may be null): *stop = 1 when est[j] <= *tol or is not a number.
 __device__ __forceinline__ void givens_body(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g,
-                                            const double2 *fnorm_dev, double *est, double *est_host = nullptr) {
+                                            const double2 *fnorm_dev, double *est, double *est_host = nullptr,
+                                            const double *tol = nullptr, int *stop = nullptr) {
     __shared__ double2 colS[66], snS[64];
     __shared__ double csS[64];
     const int lane = threadIdx.x & 31;
@@ -251,16 +253,26 @@ __device__ __forceinline__ void givens_body(double2 *H, int ldh, int j, double *
         g[j] = cscale(gj, c);
         est[j] = hypot(g[j + 1].x, g[j + 1].y) / fnorm;
         if (est_host) est_host[j] = est[j];
+        if (stop && !(est[j] > *tol)) *stop = 1;
     }
     __syncwarp();
     for (int i = lane; i <= j + 1; i += 32) col[i] = colS[i];
 }
 
 __global__ void k_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm_dev,
-                         double *est, double *est_host) {
+                         double *est, double *est_host, const double *tol, int *stop) {
     pdl_enter();
     if (threadIdx.x >= 32 || blockIdx.x != 0) return;
-    givens_body(H, ldh, j, cs, sn, g, fnorm_dev, est, est_host);
+    givens_body(H, ldh, j, cs, sn, g, fnorm_dev, est, est_host, tol, stop);
+}
+
+__global__ void k_cycle_start(double2 *g, int len, const double2 *beta, int *stop, double *tol_dev, double tol) {
+    pdl_enter();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) g[i] = i == 0 ? *beta : make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) {
+        if (stop) *stop = 0;
+        if (tol_dev) *tol_dev = tol;
+    }
 }
 
 // Batched rotation of column j (block z = problem), and the gather of every problem's estimate
@@ -517,8 +529,16 @@ template cudaError_t launch_combine<double2>(size_t, const double2 *, size_t, in
                                              double2 *, cudaStream_t);
 
 cudaError_t launch_givens(double2 *H, int ldh, int j, double *cs, double2 *sn, double2 *g, const double2 *fnorm,
-                          double *est, double *est_host, cudaStream_t s) {
-    k_givens<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g, fnorm, est, est_host);
+                          double *est, double *est_host, const double *tol, int *stop, cudaStream_t s) {
+    if (stop && !tol) return cudaErrorInvalidValue;
+    k_givens<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g, fnorm, est, est_host, tol, stop);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cycle_start(double2 *g, int len, const double2 *beta, int *stop, double *tol_dev, double tol,
+                               cudaStream_t s) {
+    if (len < 1) return cudaErrorInvalidValue;
+    launch_pdl(k_cycle_start, 1, NT, 0, s, g, len, beta, stop, tol_dev, tol);
     return cudaGetLastError();
 }
 

@@ -26,12 +26,13 @@ template <typename R> struct OpView {
     const C *__restrict__ dinv;
     C bk, c;
     int nx, ny, nz;
+    const int *gate;  // see DevOp::gate
 };
 
 template <typename R> __host__ __device__ OpView<R> view(const DevOp<R> &op) {
     OpView<R> v;
     v.cx = op.coef[0]; v.cy = op.coef[1]; v.cz = op.coef[2];
-    v.k2 = op.k2; v.dinv = op.dinv; v.bk = op.bk; v.c = op.c;
+    v.k2 = op.k2; v.dinv = op.dinv; v.bk = op.bk; v.c = op.c; v.gate = op.gate;
     v.nx = op.n[0]; v.ny = op.n[1]; v.nz = op.n[2];
     return v;
 }
@@ -115,6 +116,7 @@ template <typename R, int DIM, typename CB>
 __global__ void __launch_bounds__(BX *BY) k_residual(OpView<R> o, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
                                                      typename CT<R>::T *__restrict__ r) {
     pdl_enter();
+    if (o.gate && *o.gate) return;
     typedef typename CT<R>::T C;
     INTERIOR_IJ(o);
     C xm = mk(R(0), R(0)), xc = u[p], xp = mk(R(0), R(0));
@@ -133,6 +135,7 @@ template <typename R, int DIM, typename CB, bool ZERO>
 __global__ void __launch_bounds__(BX *BY) k_jacobi(OpView<R> o, R omega, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
                                                    typename CT<R>::T *__restrict__ un) {
     pdl_enter();
+    if (o.gate && *o.gate) return;
     typedef typename CT<R>::T C;
     INTERIOR_IJ(o);
     if (ZERO) {
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(BX *BY) k_jacobi3(OpView<R> o, R omega, const 
                                                     const typename CT<R>::T *__restrict__ u,
                                                     typename CT<R>::T *__restrict__ un) {
     pdl_enter();
+    if (o.gate && *o.gate) return;
     typedef typename CT<R>::T C;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -233,6 +237,7 @@ __global__ void __launch_bounds__(BX *BY) k_jacobi3(OpView<R> o, R omega, const 
 template <typename R, int DIM, typename CB>
 __global__ void __launch_bounds__(BX *BY) k_rb(OpView<R> o, R omega, const CB *__restrict__ b, typename CT<R>::T *u, int colour) {
     pdl_enter();
+    if (o.gate && *o.gate) return;
     typedef typename CT<R>::T C;
     const int t = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -258,6 +263,7 @@ template <typename R, int DIM, typename CB>
 __global__ void __launch_bounds__(BX *BY) k_residual_restrict(OpView<R> o, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
                                                               typename CT<R>::T *__restrict__ rc, int ncx, int ncy, int ncz) {
     pdl_enter();
+    if (o.gate && *o.gate) return;
     typedef typename CT<R>::T C;
     const int I = blockIdx.x * BX + threadIdx.x + 1;
     const int J = blockIdx.y * BY + threadIdx.y + 1;
@@ -292,8 +298,10 @@ __global__ void __launch_bounds__(BX *BY) k_residual_restrict(OpView<R> o, const
 // uf[q] += average of ec over coarse nodes floor(q/2), ceil(q/2) along every axis.
 template <typename R, int DIM>
 __global__ void __launch_bounds__(BX *BY) k_prolong_add(int nx, int ny, int nz, const typename CT<R>::T *__restrict__ ec,
-                                                        typename CT<R>::T *__restrict__ uf) {
+                                                        typename CT<R>::T *__restrict__ uf,
+                                                        const int *__restrict__ gate) {
     pdl_enter();
+    if (gate && *gate) return;
     typedef typename CT<R>::T C;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -339,6 +347,7 @@ __global__ void __launch_bounds__(R3_NT, sizeof(R) == sizeof(float) ? 2 : 1)
     k_resrestrict3(OpView<R> o, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
                    typename CT<R>::T *__restrict__ rc, int ncx, int ncy, int ncz, int kc) {
     pdl_enter();
+    if (o.gate && *o.gate) return;
     typedef typename CT<R>::T C;
     extern __shared__ __align__(16) unsigned char r3_smem[];
     C(*rbuf)[R3_FH][R3_FW] = reinterpret_cast<C(*)[R3_FH][R3_FW]>(r3_smem);
@@ -429,8 +438,10 @@ __global__ void __launch_bounds__(R3_NT, sizeof(R) == sizeof(float) ? 2 : 1)
 // coarse nodes of k_prolong_add.  Each thread marches kc fine planes.
 template <typename R>
 __global__ void __launch_bounds__(BX *BY) k_prolong3(int nx, int ny, int nz, const typename CT<R>::T *__restrict__ ec,
-                                                     typename CT<R>::T *__restrict__ uf, int kc) {
+                                                     typename CT<R>::T *__restrict__ uf, int kc,
+                                                     const int *__restrict__ gate) {
     pdl_enter();
+    if (gate && *gate) return;
     typedef typename CT<R>::T C;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -680,6 +691,7 @@ __global__ void __launch_bounds__(Tile<TCX, TCY>::NT, 4) k_pre2_restrict(OpView<
                                                        float2 *__restrict__ u, float2 *__restrict__ rc, int ncx,
                                                        int ncy) {
     pdl_enter();
+    if (o.gate && *o.gate) return;
     pre2_restrict_tile<TCX, TCY>(o, omega, b, u, rc, ncx, ncy, blockIdx.x, blockIdx.y);
 }
 
@@ -747,6 +759,7 @@ __global__ void __launch_bounds__(Tile<TCX, TCY>::NT, 4) k_prolong_post2(OpView<
                                                        const float2 *__restrict__ u_in, float2 *__restrict__ u,
                                                        const float2 *__restrict__ ec, int ncx, int ncy) {
     pdl_enter();
+    if (o.gate && *o.gate) return;
     prolong_post2_tile<TCX, TCY>(o, omega, b, u_in, u, ec, ncx, ncy, blockIdx.x, blockIdx.y);
 }
 
@@ -1127,14 +1140,14 @@ cudaError_t launch_residual_restrict(const DevOp<R> &op, int dim, const CB *bb, 
 
 template <typename R>
 cudaError_t launch_prolong_add(const int nf[3], int dim, const typename CT<R>::T *ec, typename CT<R>::T *uf,
-                               cudaStream_t s) {
+                               cudaStream_t s, const int *gate) {
     dim3 g = grid_for(nf, dim), b(BX, BY);
     if (dim == 3) {
         const int kc = z_chunk((size_t)g.x * g.y, nf[2] - 2, KCHUNK, 152 * 10);
         g.z = cdiv(nf[2] - 2, kc);
-        launch_pdl(k_prolong3<R>, g, b, 0, s, nf[0], nf[1], nf[2], ec, uf, kc);
+        launch_pdl(k_prolong3<R>, g, b, 0, s, nf[0], nf[1], nf[2], ec, uf, kc, gate);
     } else {
-        launch_pdl(k_prolong_add<R, 2>, g, b, 0, s, nf[0], nf[1], 1, ec, uf);
+        launch_pdl(k_prolong_add<R, 2>, g, b, 0, s, nf[0], nf[1], 1, ec, uf, gate);
     }
     return cudaGetLastError();
 }
@@ -1334,7 +1347,8 @@ template <typename C> cudaError_t launch_zero(size_t n, C *x, cudaStream_t s) {
                                                  cudaStream_t);                                                 \
     template cudaError_t launch_residual_restrict<R, CT<R>::T>(const DevOp<R> &, int, const CT<R>::T *,          \
                                                                 const CT<R>::T *, CT<R>::T *, cudaStream_t);    \
-    template cudaError_t launch_prolong_add<R>(const int *, int, const CT<R>::T *, CT<R>::T *, cudaStream_t);    \
+    template cudaError_t launch_prolong_add<R>(const int *, int, const CT<R>::T *, CT<R>::T *, cudaStream_t,      \
+                                               const int *);                                                   \
     template cudaError_t launch_dense_solve<R>(const int *, int, int, const CT<R>::T *, const CT<R>::T *,        \
                                                 CT<R>::T *, cudaStream_t);
 INST_R(float)

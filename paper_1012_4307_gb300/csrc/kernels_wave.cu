@@ -18,6 +18,7 @@ struct WaveOp {
     const float *k2;
     float2 bk, c;
     int nx, ny;
+    const int *gate;  // see DevOp::gate
 };
 
 constexpr int WV_CX = 13;  // coarse columns per warp (26 owned fine columns of 32 lanes)
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(32 * WV_WARPS) k_pre2_wave(WaveOp o, float ome
                                                              float2 *__restrict__ u, float2 *__restrict__ rc, int ncx,
                                                              int ncy) {
     pdl_enter();
+    if (o.gate && *o.gate) return;
     int I0, J0;
     bool live;
     wave_geometry(ncx, ncy, I0, J0, live);
@@ -169,6 +171,7 @@ __global__ void __launch_bounds__(32 * WV_WARPS) k_post2_wave(WaveOp o, float om
                                                               const float2 *__restrict__ u_in, float2 *__restrict__ u,
                                                               const float2 *__restrict__ ec, int ncx, int ncy) {
     pdl_enter();
+    if (o.gate && *o.gate) return;
     int I0, J0;
     bool live;
     wave_geometry(ncx, ncy, I0, J0, live);
@@ -268,7 +271,7 @@ static unsigned wave_blocks(const int n[3]) {
 cudaError_t launch_pre2_wave(const DevOp<float> &op, float omega, const float2 *b, float2 *u_out, float2 *rc,
                              cudaStream_t s) {
     if (!wave_jacobi2_ok(op.n, 2)) return cudaErrorInvalidValue;
-    const WaveOp v{op.coef[0], op.coef[1], op.k2, op.bk, op.c, op.n[0], op.n[1]};
+    const WaveOp v{op.coef[0], op.coef[1], op.k2, op.bk, op.c, op.n[0], op.n[1], op.gate};
     const int ncx = (op.n[0] + 1) / 2, ncy = (op.n[1] + 1) / 2;
     return launch_pdl(k_pre2_wave, wave_blocks(op.n), 32 * WV_WARPS, 0, s, v, omega, b, u_out, rc, ncx, ncy);
 }
@@ -276,7 +279,7 @@ cudaError_t launch_pre2_wave(const DevOp<float> &op, float omega, const float2 *
 cudaError_t launch_post2_wave(const DevOp<float> &op, float omega, const float2 *b, const float2 *u_in, float2 *u_out,
                               const float2 *ec, cudaStream_t s) {
     if (!wave_jacobi2_ok(op.n, 2)) return cudaErrorInvalidValue;
-    const WaveOp v{op.coef[0], op.coef[1], op.k2, op.bk, op.c, op.n[0], op.n[1]};
+    const WaveOp v{op.coef[0], op.coef[1], op.k2, op.bk, op.c, op.n[0], op.n[1], op.gate};
     const int ncx = (op.n[0] + 1) / 2, ncy = (op.n[1] + 1) / 2;
     return launch_pdl(k_post2_wave, wave_blocks(op.n), 32 * WV_WARPS, 0, s, v, omega, b, u_in, u_out, ec, ncx, ncy);
 }

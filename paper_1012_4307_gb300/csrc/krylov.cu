@@ -44,7 +44,7 @@ static void free_krylov(helm_handle *h) {
     for (void *p : h->krylov_owned) cudaFree(p);
     h->krylov_owned.clear();
     h->V = nullptr; h->Z = nullptr; h->H = nullptr; h->g = h->sn = h->y = h->h2 = nullptr;
-    h->cs = nullptr; h->partials = nullptr; h->scal = nullptr; h->est_dev = nullptr;
+    h->cs = nullptr; h->partials = nullptr; h->scal = nullptr; h->est_dev = nullptr; h->tol_dev = nullptr;
     h->gs_flag = h->gs_count = nullptr;
     h->m_alloc = 0;
     h->bicg_alloc = false;
@@ -102,6 +102,7 @@ static helm_status ensure_ws(helm_handle *h, int m) {
     KA(&h->tickets, 4);
     KA(&h->scal, 32);
     KA(&h->est_dev, (size_t)m + 4);
+    KA(&h->tol_dev, 1);
     KA(&h->gs_flag, 4);
     h->gs_count = h->gs_flag + 1;
 #undef KA
@@ -221,14 +222,21 @@ static bool dcgs2_fold(const helm_handle *h) {
     return h->mg.gs_arith == HELM_GS_DCGS2 && h->z_prec == HELM_C64 && h->mg.kind != HELM_PC_NONE;
 }
 
-// z = cycle(level 0's right-hand side) in complex64; w = A z as a float-pair vector.
-static cudaError_t precond_apply_level0(helm_handle *h, float2 *z, float4 *w) {
+// z = cycle(level 0's right-hand side) in complex64; w = A z as a float-pair vector.  When the
+// device flag gate is set at launch, the finest level's kernels and the apply do nothing.
+static cudaError_t precond_apply_level0(helm_handle *h, float2 *z, float4 *w, const int *gate) {
     pdl_cycle_scope pdl;  // the apply follows the cycle's last kernel
+    h->lv[0].M32.gate = gate;  // for these launches only
     cudaError_t e = precondition_level0_c64(h, z);
+    h->lv[0].M32.gate = nullptr;
     if (e != cudaSuccess) return e;
     ProfScope ps(h, HELM_K_APPLY, interior_pts(h) * (8 + 8 + 16), 0);
-    return launch_apply_A_df(h->Adf, h->dim, z, w, h->stream);
+    return launch_apply_A_df(h->Adf, h->dim, z, w, h->stream, gate);
 }
+
+// Device flag of the current FGMRES cycle: set by the rotation kernel when a residual estimate
+// meets the tolerance, cleared at the start of every cycle.
+static int *stop_flag(helm_handle *h) { return h->gs_flag + 2; }
 
 // z = precondition(v) in the workspace precision; w = A z (FP64)
 static cudaError_t precond_apply(helm_handle *h, const double2 *v, void *z, double2 *w) {
@@ -337,7 +345,7 @@ static cudaError_t fgmres_step(helm_handle *h, int j, int m) {
     }
     {
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
-        CKE(launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, h->est_host, s));
+        CKE(launch_givens(h->H, ldh, j, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, h->est_host, nullptr, nullptr, s));
     }
     // inside a capture the record must become an event node of the graph (external), so that
     // the host can wait on the event after every replay
@@ -373,11 +381,14 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
     // step, the update pass and the solution update divide by alpha_j (the cycle and A are
     // linear), and no conversion launch is needed.
     const bool fold = dcgs2_fold(h), scaled = fold && j > 0;
-    if (scaled) CKE(precond_apply_level0(h, (float2 *)zj, w));
+    // steps queued behind a converged one (the host learns of it one or two steps later) skip
+    // the apply and the two basis passes: the rotation that met the tolerance set the flag
+    int *stop = stop_flag(h);
+    if (scaled) CKE(precond_apply_level0(h, (float2 *)zj, w, stop));
     else CKE(precond_apply_pair(h, u, j > 0 ? h->alpha2 + j : nullptr, zj, w));
     {
         ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (nv + 1), 0);
-        CKE(launch_mdot2_pair(np, V4, np, j + 1, u, w, h->partials, s));
+        CKE(launch_mdot2_pair(np, V4, np, j + 1, u, w, h->partials, stop, s));
     }
     {
         // reduction and, in its last block, the coefficient step (its few blocks may be scheduled
@@ -396,7 +407,8 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
             CKE(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         }
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
-        CKE(launch_givens(h->H, ldh, j - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, h->est_host, gs));
+        CKE(launch_givens(h->H, ldh, j - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, h->est_host, h->tol_dev,
+                          stop, gs));
         if (fork) CKE(cudaEventRecord(h->ev_join, h->side));
     }
     {
@@ -407,7 +419,7 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
         pdl_cycle_scope pdl;
         ProfScope ps(h, HELM_K_UPDATE_NORM, np * 16.0 * (nv + 3), 0);
         CKE(launch_update2_pair(np, V4, np, j, h->dcoef, h->partials, h->tickets + 1, h->alpha2 + j + 1,
-                                fold ? level0_rhs_c64(h) : nullptr, s));
+                                fold ? level0_rhs_c64(h) : nullptr, stop, s));
     }
     if (fork) CKE(cudaStreamWaitEvent(s, h->ev_join, 0));
     return h->capturing ? cudaEventRecordWithFlags(h->step_ev[j], s, cudaEventRecordExternal)
@@ -426,7 +438,7 @@ static cudaError_t fgmres_close_dcgs2(helm_handle *h, int jc, int m) {
         // and x^H x (slot jc is x)
         ProfScope ps(h, HELM_K_MDOT, np * 16.0 * (jc + 1), 0);
         const float4 *x = V4 + (size_t)jc * np;
-        CKE(launch_mdot2_pair(np, V4, np, jc + 1, x, x, h->partials, s));
+        CKE(launch_mdot2_pair(np, V4, np, jc + 1, x, x, h->partials, nullptr, s));
     }
     {
         // the reduction and, in its last block, the coefficient step that finishes column jc - 1
@@ -434,7 +446,8 @@ static cudaError_t fgmres_close_dcgs2(helm_handle *h, int jc, int m) {
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
         CKE(launch_reduce_dcgs2(h->partials, gs_df_dot2_nblocks(np, jc + 1), h->hv, h->tickets, jc, h->alpha2, h->H,
                                 ldh, h->dcoef, 0, s));
-        CKE(launch_givens(h->H, ldh, jc - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, h->est_host, s));
+        CKE(launch_givens(h->H, ldh, jc - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, h->est_host, nullptr,
+                          nullptr, s));
     }
     return h->capturing ? cudaEventRecordWithFlags(h->close_ev[jc], s, cudaEventRecordExternal)
                         : cudaEventRecord(h->close_ev[jc], s);
@@ -523,7 +536,7 @@ helm_status fgmres_begin(helm_handle *h, FgmresRun &r, const double2 *f, double2
     r.status = HELM_ERR_NOCONV;
     r.phase = FgmresRun::WAIT_FN;
     cudaStream_t s = h->stream;
-    CKR(cudaMemsetAsync(h->gs_flag, 0, 2 * sizeof(int), s));
+    CKR(cudaMemsetAsync(h->gs_flag, 0, 3 * sizeof(int), s));
     CKR(dev_norm(h, f, h->fnorm_dev));
     CKR(cudaMemcpyAsync(h->est_host + m + 2, h->fnorm_dev, sizeof(double2), cudaMemcpyDeviceToHost, s));
     CKR(cudaEventRecord(h->ev_fn, s));
@@ -608,8 +621,8 @@ helm_status fgmres_advance(FgmresRun &r, bool block) {
             // v_0 = r0 / beta (as a float-pair vector for the double-FP32 Arnoldi)
             if (h->mg.gs_arith != HELM_GS_FP64) CKR(launch_split_scale(np, h->V, h->scal, s));
             else CKR(launch_scale_inv(np, h->V, h->scal, h->V, s));
-            CKR(cudaMemsetAsync(h->g, 0, (m + 1) * sizeof(double2), s));
-            CKR(cudaMemcpyAsync(h->g, h->scal, sizeof(double2), cudaMemcpyDeviceToDevice, s));
+            // g = beta e_1; the cycle's stop flag cleared and the tolerance it is tested against set
+            CKR(launch_cycle_start(h->g, m + 1, h->scal, stop_flag(h), h->tol_dev, r.tol, s));
             r.jmax = std::min(m, r.maxit - r.it);
             r.next = 0;
             // One step of look-ahead: step j+1 is queued before the host waits for step j's

@@ -361,9 +361,10 @@ cudaError_t launch_mdot_norm(size_t n, const double2 *V, size_t ldv, int nv, con
 // w -= sum_i V_i h_i, then partials[b] = (||w||^2, 0)   (h on device)
 cudaError_t launch_update_norm(size_t n, const double2 *V, size_t ldv, int nv, const double2 *h, double2 *w,
                                double2 *partials, const int *gate, cudaStream_t s);
-// out[i] (mode 0: =, 1: +=, 2: (sqrt(re), 0)) = fixed-order sum of partials of vector i
+// out[i] (mode 0: =, 1: +=, 2: (sqrt(re), 0)) = fixed-order sum of partials of vector i; with
+// host_out (pinned host memory), host_out[i] = the real part of out[i] as well
 cudaError_t launch_reduce(const double2 *partials, int nblk, int nv, double2 *out, int mode, const int *gate,
-                          cudaStream_t s);
+                          cudaStream_t s, double *host_out = nullptr);
 // Same two passes in double-FP32 arithmetic on float-pair vectors (kernels_gs_df.cu): node q
 // of such a vector is the float4 (re.hi, re.lo, im.hi, im.lo).  Dot-pass partials use
 // G = gs_df_nblocks(n) blocks per vector, update-pass partials gs_df_update_nblocks(n).

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(NT) k_update_norm(size_t n, const double2 *__r
 // out[i] = sum_b partials[i * nblk + b] in a fixed order for i = blockIdx.x; mode 0 '=',
 // 1 '+=', 2 (sqrt(re), 0).  Gated.
 __global__ void k_reduce(const double2 *__restrict__ partials, int nblk, double2 *__restrict__ out, int mode,
-                         const int *__restrict__ gate) {
+                         const int *__restrict__ gate, double *host_out) {
     pdl_enter();
     if (gate && *gate == 0) return;
     __shared__ double2 sums[1];
@@ -114,9 +114,12 @@ __global__ void k_reduce(const double2 *__restrict__ partials, int nblk, double2
     block_sum<1>(s, sums);
     if (threadIdx.x == 0) {
         const double2 t = sums[0];
-        if (mode == 0) out[i] = t;
-        else if (mode == 1) out[i] = cadd(out[i], t);
-        else out[i] = make_double2(sqrt(t.x), 0.0);
+        double2 r;
+        if (mode == 0) r = t;
+        else if (mode == 1) r = cadd(out[i], t);
+        else r = make_double2(sqrt(t.x), 0.0);
+        out[i] = r;
+        if (host_out) host_out[i] = r.x;
     }
 }
 
@@ -495,8 +498,8 @@ cudaError_t launch_update_norm(size_t n, const double2 *V, size_t ldv, int nv, c
 }
 
 cudaError_t launch_reduce(const double2 *partials, int nblk, int nv, double2 *out, int mode, const int *gate,
-                          cudaStream_t s) {
-    launch_pdl(k_reduce, nv, NT, 0, s, partials, nblk, out, mode, gate);
+                          cudaStream_t s, double *host_out) {
+    launch_pdl(k_reduce, nv, NT, 0, s, partials, nblk, out, mode, gate, host_out);
     return cudaGetLastError();
 }
 

@@ -164,11 +164,12 @@ static helm_status ensure_bicg(helm_handle *h) {
 }
 
 // ||x||_2 -> out (device scalar, .x); optionally read back to the host.
-static cudaError_t dev_norm(helm_handle *h, const double2 *x, double2 *out) {
+// out = (||x||, 0) on the device; with host_out (pinned), *host_out = ||x|| too.
+static cudaError_t dev_norm(helm_handle *h, const double2 *x, double2 *out, double *host_out = nullptr) {
     ProfScope ps(h, HELM_K_VECTOR, h->np * 16.0, h->np * 4.0);
     cudaError_t e = launch_mdot_norm(h->np, nullptr, h->np, 0, x, h->partials, nullptr, h->stream);
     if (e != cudaSuccess) return e;
-    return launch_reduce(h->partials, blas_nblocks(h->np), 1, out, 2, nullptr, h->stream);
+    return launch_reduce(h->partials, blas_nblocks(h->np), 1, out, 2, nullptr, h->stream, host_out);
 }
 
 static cudaError_t dev_dot(helm_handle *h, const double2 *a, const double2 *b, double2 *out) {
@@ -537,8 +538,7 @@ helm_status fgmres_begin(helm_handle *h, FgmresRun &r, const double2 *f, double2
     r.phase = FgmresRun::WAIT_FN;
     cudaStream_t s = h->stream;
     CKR(cudaMemsetAsync(h->gs_flag, 0, 3 * sizeof(int), s));
-    CKR(dev_norm(h, f, h->fnorm_dev));
-    CKR(cudaMemcpyAsync(h->est_host + m + 2, h->fnorm_dev, sizeof(double2), cudaMemcpyDeviceToHost, s));
+    CKR(dev_norm(h, f, h->fnorm_dev, h->est_host + m + 2));
     CKR(cudaEventRecord(h->ev_fn, s));
     return HELM_OK;
 }
@@ -601,8 +601,7 @@ helm_status fgmres_advance(FgmresRun &r, bool block) {
                              apply_flops(h) + 2 * interior_pts(h));
                 CKR(launch_residual<double, double2>(h->A64, h->dim, r.f, r.x, h->V, s));
             }
-            CKR(dev_norm(h, h->V, h->scal));
-            CKR(cudaMemcpyAsync(h->est_host + m + 4, h->scal, sizeof(double2), cudaMemcpyDeviceToHost, s));
+            CKR(dev_norm(h, h->V, h->scal, h->est_host + m + 4));
             CKR(cudaEventRecord(h->ev_beta, s));
             r.phase = FgmresRun::WAIT_BETA;
             break;

@@ -258,6 +258,36 @@ def test_dcgs2_residual_history_matches_cgs(helm, restart):
     assert np.all(np.abs(a - b) <= 1e-7 * b + 1e-13)
 
 
+@pytest.mark.parametrize("restart", [30, 7])
+def test_dcgs2_solves_after_an_early_stop(helm, restart):
+    """Delayed CGS2 with a complex64 cycle queues steps ahead of the host's convergence test;
+    those queued behind a converged step skip their work (a device flag that the rotation kernel
+    sets when an estimate meets the current solve's tolerance, cleared at every cycle start).
+    Solves of different tolerances in a row on one handle, so with the flag set by the previous
+    solve and the replayed step graphs, give bit for bit the iterations and solutions of fresh
+    handles."""
+    P = W.config_2d_well(129)
+    f = to_gpu(P.f)
+    tols = (1e-3, 1e-9, 1e-5)
+
+    def solve(h, tol):
+        x, st = helm.krylov_solve(h, f, tol=tol, restart=restart, maxit=2000, history=True)
+        return x.clone(), st
+
+    h = gpu_handle(helm, P, pc="csg", prec="c64", gs="dcgs2")
+    seq = [solve(h, t) for t in tols]
+    h.close()
+    for t, (x, st) in zip(tols, seq):
+        hf = gpu_handle(helm, P, pc="csg", prec="c64", gs="dcgs2")
+        xf, stf = solve(hf, t)
+        hf.close()
+        assert st.status == helm.HELM_OK and st.rel_res <= t
+        assert st.iterations == stf.iterations and st.restarts == stf.restarts
+        assert np.array_equal(np.array(st.history[: st.iterations]), np.array(stf.history[: stf.iterations]))
+        assert torch.equal(x, xf)
+    assert seq[0][1].iterations < seq[2][1].iterations < seq[1][1].iterations
+
+
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 def test_bicgstab_matches_oracle(helm, oracle, prec):
     P = W.config_small(65)

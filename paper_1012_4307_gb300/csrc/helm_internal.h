@@ -131,6 +131,9 @@ __device__ __forceinline__ void pdl_enter() {
     pdl_wait();
     pdl_trigger();
 }
+// Value of a gate flag (0 when there is none).  Kernels load it first and test it only after
+// they have issued their first loads, so that its latency overlaps theirs.
+__device__ __forceinline__ int gate_value(const int *g) { return g ? *g : 0; }
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args... args) {

@@ -27,10 +27,11 @@ __device__ __forceinline__ void cmac(float4 a, float2 z, float &sr, float &cr, f
     ff_acc_prod(si, ci, p, e);
 }
 
-// (bx, by, bz): this block's tile of interior nodes.
+// (bx, by, bz): this block's tile of interior nodes.  gv != 0 (a gate flag's value): return
+// once the first operands have been loaded, writing nothing.
 template <int DIM>
 __device__ __forceinline__ void apply_A_df_tile(const DevOpDF &o, const float2 *__restrict__ z, float4 *__restrict__ y,
-                                                int bx, int by, int bz) {
+                                                int bx, int by, int bz, int gv = 0) {
     const int nx = o.n[0], ny = o.n[1], nz = o.n[2];
     const int i = bx * BX + threadIdx.x + 1;
     const int j = by * BY + threadIdx.y + 1;
@@ -51,6 +52,7 @@ __device__ __forceinline__ void apply_A_df_tile(const DevOpDF &o, const float2 *
         float2 zm = z[p - sz], zc = z[p];
         float2 zw = z[p - 1], ze = z[p + 1], zs = z[p - sy], zn = z[p + sy], zp = z[p + sz];
         float2 kk = o.k2[p];
+        if (gv) return;
         for (int k = k0; k < k1; k++, p += sz) {
             float2 zw2 = zw, ze2 = ze, zs2 = zs, zn2 = zn, zp2 = zp, kk2 = kk;
             if (k + 1 < k1) {
@@ -84,15 +86,17 @@ __device__ __forceinline__ void apply_A_df_tile(const DevOpDF &o, const float2 *
     } else {
         for (int k = k0; k < k1; k++) {
             const size_t p = (size_t)i + sy * ((size_t)j + (size_t)ny * k);
-            float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-            cmac(cxw, z[p - 1], sr, cr, si, ci);
-            cmac(cxe, z[p + 1], sr, cr, si, ci);
-            cmac(cyw, z[p - sy], sr, cr, si, ci);
-            cmac(cye, z[p + sy], sr, cr, si, ci);
-            ff dr = dxy_r, di = dxy_i;
+            const float2 zw = z[p - 1], ze = z[p + 1], zs = z[p - sy], zn = z[p + sy], zc = z[p];
             const float2 kk = o.k2[p];
+            if (gv) return;
+            float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+            cmac(cxw, zw, sr, cr, si, ci);
+            cmac(cxe, ze, sr, cr, si, ci);
+            cmac(cyw, zs, sr, cr, si, ci);
+            cmac(cye, zn, sr, cr, si, ci);
+            ff dr = dxy_r, di = dxy_i;
             dr = ff_add(dr, ff{-kk.x, -kk.y});  // diagonal: sum of centre coefficients - k^2
-            cmac(make_float4(dr.hi, dr.lo, di.hi, di.lo), z[p], sr, cr, si, ci);
+            cmac(make_float4(dr.hi, dr.lo, di.hi, di.lo), zc, sr, cr, si, ci);
             const ff yr = ff_norm(sr, cr), yi = ff_norm(si, ci);
             y[p] = make_float4(yr.hi, yr.lo, yi.hi, yi.lo);
         }
@@ -103,8 +107,8 @@ template <int DIM>
 __global__ void __launch_bounds__(BX *BY) k_apply_A_df(DevOpDF o, const float2 *__restrict__ z, float4 *__restrict__ y,
                                                        const int *__restrict__ gate) {
     pdl_enter();
-    if (gate && *gate) return;
-    apply_A_df_tile<DIM>(o, z, y, blockIdx.x, blockIdx.y, blockIdx.z);
+    const int gv = gate_value(gate);
+    apply_A_df_tile<DIM>(o, z, y, blockIdx.x, blockIdx.y, blockIdx.z, gv);
 }
 
 // Batched 2D apply of step j over many problems: problem e takes the flat blocks

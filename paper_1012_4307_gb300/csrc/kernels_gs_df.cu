@@ -243,10 +243,11 @@ __global__ void __launch_bounds__(NT) k_update_norm_pair(size_t n, const float4 
 // expanded in the basis), so it is formed from the hi parts in FP32.
 // bx: this block's index among the nblk blocks that cover the vector (one launch, or one
 // problem's share of a batched launch).
+// gv != 0 (a gate flag's value): stop after the first loads (the partials are then meaningless).
 template <int CH>
 __device__ __forceinline__ void mdot2_body(size_t n, const float4 *__restrict__ V, size_t ldv, int nv,
                                            const float4 *__restrict__ x, const float4 *__restrict__ w,
-                                           double2 *__restrict__ partials, int bx, int nblk) {
+                                           double2 *__restrict__ partials, int bx, int nblk, int gv = 0) {
     __shared__ double sums[4 * CH];
     // block (b, y) = bx = b * ngroups + y: the blocks that read the same stretch of x and w run
     // side by side, so that all but the first of them find it in L2
@@ -267,6 +268,7 @@ __device__ __forceinline__ void mdot2_body(size_t n, const float4 *__restrict__ 
         float4 vq[CH];
 #pragma unroll
         for (int t = 0; t < CH; t++) vq[t] = t < cnt ? V[(size_t)(i0 + t) * ldv + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gv) break;
         const ff xr = ff_re(xq), xi = ff_im(xq);
 #pragma unroll
         for (int t = 0; t < CH; t++) {
@@ -305,8 +307,8 @@ __global__ void __launch_bounds__(NT, 6) k_mdot2_pair(size_t n, const float4 *__
                                                    const float4 *__restrict__ x, const float4 *__restrict__ w,
                                                    double2 *__restrict__ partials, const int *__restrict__ gate) {
     pdl_enter();
-    if (gate && *gate) return;
-    mdot2_body<CH>(n, V, ldv, nv, x, w, partials, blockIdx.x, gridDim.x);
+    const int gv = gate_value(gate);
+    mdot2_body<CH>(n, V, ldv, nv, x, w, partials, blockIdx.x, gridDim.x, gv);
 }
 
 // Index of the entry whose block range [first[e], first[e + 1]) holds block b (count entries).
@@ -451,15 +453,17 @@ __device__ __forceinline__ void update2_nodes(size_t n, float4 *__restrict__ V, 
     }
 }
 
-// bx: this block among the nblk blocks of the vector (see mdot2_body).  skip: leave the vectors
-// as they are (zero norm partials; the ticket protocol still runs, so the ticket returns to 0).
+// bx: this block among the nblk blocks of the vector (see mdot2_body).  gate (may be null): when
+// the flag is set, leave the vectors as they are (zero norm partials; the ticket protocol still
+// runs, so the ticket returns to 0).
 __device__ __forceinline__ void update2_body(size_t n, float4 *__restrict__ V, size_t ldv, int j,
                                              const double2 *__restrict__ coef, double2 *__restrict__ partials,
                                              unsigned *ticket, double2 *alpha_out, float2 *__restrict__ b_out, int bx,
-                                             int nblk, bool skip) {
+                                             int nblk, const int *gate) {
     __shared__ float4 cA[64], cC[64];
     __shared__ float4 sc[2];  // (r hi, lo, small-correction flag, 0), s
     __shared__ float2 rws;    // scale of the incoming w: coef[2j+2].x as a float pair
+    __shared__ int skip;      // the gate flag
     __shared__ double sums[1];
     for (int i = threadIdx.x; i < j; i += NT) {
         const ff a = ff_split(coef[i].x), b = ff_split(coef[i].y);
@@ -475,6 +479,7 @@ __device__ __forceinline__ void update2_body(size_t n, float4 *__restrict__ V, s
         sc[1] = make_float4(a.hi, a.lo, b.hi, b.lo);
         const ff rw = ff_split(coef[2 * j + 2].x);
         rws = make_float2(rw.hi, rw.lo);
+        skip = gate_value(gate);
     }
     __syncthreads();
     const ff rinv = ff_re(sc[0]), sr = ff_re(sc[1]), si = ff_im(sc[1]), rw{rws.x, rws.y};
@@ -498,7 +503,7 @@ __global__ void __launch_bounds__(NT, 4) k_update2_pair(size_t n, float4 *__rest
                                                      unsigned *ticket, double2 *alpha_out, float2 *__restrict__ b_out,
                                                      const int *__restrict__ gate) {
     pdl_enter();
-    update2_body(n, V, ldv, j, coef, partials, ticket, alpha_out, b_out, blockIdx.x, gridDim.x, gate && *gate);
+    update2_body(n, V, ldv, j, coef, partials, ticket, alpha_out, b_out, blockIdx.x, gridDim.x, gate);
 }
 
 // Batched update pass of step j: problem e takes blocks [first[e], first[e + 1]); its ticket
@@ -510,7 +515,7 @@ __global__ void __launch_bounds__(NT, 4) k_update2_pair_b(const BVec *__restrict
     const BVec &P = tab[e];
     if (*P.active == 0) return;
     update2_body(P.n, P.V, P.n, j, P.dcoef, P.partials, P.tickets + 1, P.alpha2 + j + 1, P.b0,
-                 (int)(blockIdx.x - first[e]), (int)(first[e + 1] - first[e]), false);
+                 (int)(blockIdx.x - first[e]), (int)(first[e + 1] - first[e]), nullptr);
 }
 
 // 1 / beta.x as a float pair, one FP64 division per block.

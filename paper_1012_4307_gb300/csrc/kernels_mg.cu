@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(BX *BY) k_jacobi3(OpView<R> o, R omega, const 
                                                     const typename CT<R>::T *__restrict__ u,
                                                     typename CT<R>::T *__restrict__ un) {
     pdl_enter();
-    if (o.gate && *o.gate) return;
+    const int gv = gate_value(o.gate);
     typedef typename CT<R>::T C;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(BX *BY) k_jacobi3(OpView<R> o, R omega, const 
     const C cwy = __ldg(&o.cy[3 * j]), ccy = __ldg(&o.cy[3 * j + 1]), cey = __ldg(&o.cy[3 * j + 2]);
     C bq = to_c(b[p], R());
     R kq = o.k2[p];
+    if (gv) return;
     if (ZERO) {
         const C dxy = cadd(ccx, ccy);
         for (int k = k0; k < k1; k++, p += sz) {
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(R3_NT, sizeof(R) == sizeof(float) ? 2 : 1)
     k_resrestrict3(OpView<R> o, const CB *__restrict__ b, const typename CT<R>::T *__restrict__ u,
                    typename CT<R>::T *__restrict__ rc, int ncx, int ncy, int ncz, int kc) {
     pdl_enter();
-    if (o.gate && *o.gate) return;
+    const int gv = gate_value(o.gate);
     typedef typename CT<R>::T C;
     extern __shared__ __align__(16) unsigned char r3_smem[];
     C(*rbuf)[R3_FH][R3_FW] = reinterpret_cast<C(*)[R3_FH][R3_FW]>(r3_smem);
@@ -373,6 +374,7 @@ __global__ void __launch_bounds__(R3_NT, sizeof(R) == sizeof(float) ? 2 : 1)
         bq = to_c(b[p], R());
         kq = o.k2[p];
     }
+    if (gv) return;  // the same value in every thread: no barrier is left waiting
     // the coarse node of this thread (threads below R3_TX * R3_TY), and its running z sum
     const int cx = t % R3_TX, cy = t / R3_TX, I = I0 + cx, J = J0 + cy;
     const bool own = t < R3_TX * R3_TY && I <= ncx - 2 && J <= ncy - 2;
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(BX *BY) k_prolong3(int nx, int ny, int nz, con
                                                      typename CT<R>::T *__restrict__ uf, int kc,
                                                      const int *__restrict__ gate) {
     pdl_enter();
-    if (gate && *gate) return;
+    const int gv = gate_value(gate);
     typedef typename CT<R>::T C;
     const int i = blockIdx.x * BX + threadIdx.x + 1;
     const int j = blockIdx.y * BY + threadIdx.y + 1;
@@ -461,6 +463,7 @@ __global__ void __launch_bounds__(BX *BY) k_prolong3(int nx, int ny, int nz, con
     C sa = corner_sum(k0 >> 1), sb = corner_sum((k0 + 1) >> 1);
     size_t p = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k0);
     C uq = uf[p];
+    if (gv) return;
     for (int k = k0; k < k1; k++, p += (size_t)nx * ny) {
         C sn = sb, un = uq;
         if (k + 1 < k1) {
@@ -625,10 +628,12 @@ __device__ __forceinline__ float2 tile_diag(const TC &tc, int sx, int sy, float 
 template <int TCX, int TCY>
 __device__ __forceinline__ void pre2_restrict_tile(const OpView<float> &o, float omega, const float2 *__restrict__ b,
                                                    float2 *__restrict__ u, float2 *__restrict__ rc, int ncx, int ncy,
-                                                   int bx, int by) {
+                                                   int bx, int by, const int *gate = nullptr) {
     typedef Tile<TCX, TCY> TL;
     constexpr int RW = TL::RW, RH = TL::RH;
     extern __shared__ __align__(16) unsigned char pre_smem[];
+    __shared__ int gate_s;  // the gate flag, published by the first block barrier
+    if (threadIdx.x == 0) gate_s = gate_value(gate);
     typename TL::Pre &T = *reinterpret_cast<typename TL::Pre *>(pre_smem);
     const int I0 = 1 + bx * TCX, J0 = 1 + by * TCY;
     const int X0 = 2 * I0 - 3, Y0 = 2 * J0 - 3;
@@ -637,6 +642,7 @@ __device__ __forceinline__ void pre2_restrict_tile(const OpView<float> &o, float
     auto inside = [&](int x, int y) { return full || (x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2); };
     tile_coef<RW, RH>(o, X0, Y0, T.tc);
     __syncthreads();
+    if (gate_s) return;
     // load b and 1 / D; sweep 1 from zero (pointwise): u1 = omega b / D
     for_region<RW, RH, TL::NT>([&](int sx, int sy) {
         const int x = X0 + sx, y = Y0 + sy;
@@ -691,8 +697,7 @@ __global__ void __launch_bounds__(Tile<TCX, TCY>::NT, 4) k_pre2_restrict(OpView<
                                                        float2 *__restrict__ u, float2 *__restrict__ rc, int ncx,
                                                        int ncy) {
     pdl_enter();
-    if (o.gate && *o.gate) return;
-    pre2_restrict_tile<TCX, TCY>(o, omega, b, u, rc, ncx, ncy, blockIdx.x, blockIdx.y);
+    pre2_restrict_tile<TCX, TCY>(o, omega, b, u, rc, ncx, ncy, blockIdx.x, blockIdx.y, o.gate);
 }
 
 // u_out <- two omega-Jacobi sweeps of (u_in + P ec), on the owned fine nodes.  u_in and u_out
@@ -702,10 +707,13 @@ __global__ void __launch_bounds__(Tile<TCX, TCY>::NT, 4) k_pre2_restrict(OpView<
 template <int TCX, int TCY>
 __device__ __forceinline__ void prolong_post2_tile(const OpView<float> &o, float omega, const float2 *__restrict__ b,
                                                    const float2 *__restrict__ u_in, float2 *__restrict__ u,
-                                                   const float2 *__restrict__ ec, int ncx, int ncy, int bx, int by) {
+                                                   const float2 *__restrict__ ec, int ncx, int ncy, int bx, int by,
+                                                   const int *gate = nullptr) {
     typedef Tile<TCX, TCY> TL;
     constexpr int RW = TL::RW, RH = TL::RH;
     extern __shared__ __align__(16) unsigned char post_smem[];
+    __shared__ int gate_s;  // the gate flag, published by the first block barrier
+    if (threadIdx.x == 0) gate_s = gate_value(gate);
     typename TL::Post &T = *reinterpret_cast<typename TL::Post *>(post_smem);
     const int I0 = 1 + bx * TCX, J0 = 1 + by * TCY;
     const int X0 = 2 * I0 - 3, Y0 = 2 * J0 - 3;
@@ -720,6 +728,7 @@ __device__ __forceinline__ void prolong_post2_tile(const OpView<float> &o, float
         T.ec[cy][cx] = (I >= 0 && I < ncx && J >= 0 && J < ncy) ? ec[(size_t)I + (size_t)ncx * J] : make_float2(0.f, 0.f);
     }
     __syncthreads();
+    if (gate_s) return;
     // u3 = u + P ec on the region
     for_region<RW, RH, TL::NT>([&](int sx, int sy) {
         const int x = X0 + sx, y = Y0 + sy;
@@ -759,8 +768,7 @@ __global__ void __launch_bounds__(Tile<TCX, TCY>::NT, 4) k_prolong_post2(OpView<
                                                        const float2 *__restrict__ u_in, float2 *__restrict__ u,
                                                        const float2 *__restrict__ ec, int ncx, int ncy) {
     pdl_enter();
-    if (o.gate && *o.gate) return;
-    prolong_post2_tile<TCX, TCY>(o, omega, b, u_in, u, ec, ncx, ncy, blockIdx.x, blockIdx.y);
+    prolong_post2_tile<TCX, TCY>(o, omega, b, u_in, u, ec, ncx, ncy, blockIdx.x, blockIdx.y, o.gate);
 }
 
 // Batched forms (many problems, one launch): blockIdx.z picks the table entry, whose level has

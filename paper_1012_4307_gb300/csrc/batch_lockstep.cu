@@ -64,6 +64,7 @@ struct BatchLockstep {
     unsigned apply_blocks = 0, upd_blocks = 0;
     std::vector<unsigned> dot_blocks;  // per row j = 0 .. m (nv = j + 1)
     int *active = nullptr;             // device flags, one per problem
+    double *tol_dev = nullptr;         // the solve's tolerance (device), for the batched rotation
     int *active_h = nullptr;           // pinned staging of the flags
     // (m + 1) x P gathered estimates, pinned host memory that the batched rotation kernel writes
     // directly (no copy node in the step graphs)
@@ -97,6 +98,7 @@ struct BatchLockstep {
         vec = nullptr;
         apply_first = upd_first = dot_first = nullptr;
         active = nullptr;
+        tol_dev = nullptr;
         key.clear();
     }
     ~BatchLockstep() {
@@ -254,6 +256,8 @@ helm_status build(BatchLockstep *L, int m) {
     }
     CKR(cudaMalloc((void **)&L->active, P * sizeof(int)));
     L->owned.push_back(L->active);
+    CKR(cudaMalloc((void **)&L->tol_dev, sizeof(double)));
+    L->owned.push_back(L->tol_dev);
     CKR(cudaMemset(L->active, 0, P * sizeof(int)));
     for (Phase &ph : L->phases) {
         std::vector<BLevel> pre, post;
@@ -432,7 +436,7 @@ cudaError_t record_step(BatchLockstep *L, const Prof &pf, int j, cudaStream_t s)
     }
     if (j > 0) {
         ProfScope ps(h0, HELM_K_SMALL, 0, 0);
-        CKE(launch_givens_batch(P, L->vec, j - 1, L->est_h + (size_t)(j - 1) * P, s));
+        CKE(launch_givens_batch(P, L->vec, j - 1, L->est_h + (size_t)(j - 1) * P, L->tol_dev, s));
     }
     {
         ProfScope ps(h0, HELM_K_UPDATE_NORM, vec_bytes(16.0 * (j + 4) + 8.0), 0);
@@ -458,7 +462,7 @@ cudaError_t record_close(BatchLockstep *L, const Prof &pf, int jc, cudaStream_t 
     {
         ProfScope ps(h0, HELM_K_SMALL, 0, 0);
         CKE(launch_reduce_dcgs2_batch(P, L->vec, row, gs_df_dot2_groups(jc + 1), jc, 0, s));
-        CKE(launch_givens_batch(P, L->vec, jc - 1, L->est_h + (size_t)(jc - 1) * P, s));
+        CKE(launch_givens_batch(P, L->vec, jc - 1, L->est_h + (size_t)(jc - 1) * P, L->tol_dev, s));
     }
     return L->capturing ? cudaEventRecordWithFlags(L->close_ev[jc], s, cudaEventRecordExternal)
                         : cudaEventRecord(L->close_ev[jc], s);
@@ -537,6 +541,7 @@ helm_status lockstep_solve(BatchLockstep *L, cudaStream_t user, const void *cons
     cudaStream_t s = L->s;
     CKR(cudaEventRecord(L->ev_in, user));
     CKR(cudaStreamWaitEvent(s, L->ev_in, 0));
+    CKR(cudaMemcpyAsync(L->tol_dev, &tol, sizeof(double), cudaMemcpyHostToDevice, s));  // staged before return
     struct Run {
         const double2 *f;
         double2 *x;
@@ -647,11 +652,13 @@ helm_status lockstep_solve(BatchLockstep *L, cudaStream_t user, const void *cons
                 if (sp && sp->history && R.it - 1 < sp->history_len) sp->history[R.it - 1] = R.est;
                 const bool bad = !std::isfinite(R.est);
                 if (bad || R.est <= tol || j + 1 >= R.jmax) {
-                    // the problem leaves the lockstep: its flag is cleared behind the steps
-                    // already queued (they only write columns and slots past j), then x += Z y
-                    // over its first j + 1 columns
+                    // the problem leaves the lockstep, then x += Z y over its first j + 1
+                    // columns.  On convergence the rotation that formed the estimate has already
+                    // cleared its flag, so the steps queued behind it skip the problem; otherwise
+                    // (a full cycle, a non-finite estimate) the flag is cleared here, behind them
+                    // (they only write columns and slots past j)
                     act[p] = 0;
-                    CKR(cudaMemsetAsync(L->active + p, 0, sizeof(int), s));
+                    if (!(R.est <= tol)) CKR(cudaMemsetAsync(L->active + p, 0, sizeof(int), s));
                     if (bad) {
                         R.status = HELM_ERR_NONFINITE;
                         R.done = true;

@@ -319,7 +319,7 @@ struct BVec {
     double *cs, *est;
     unsigned *tickets;
     int ldh;
-    const int *active;
+    int *active;  // the problem's flag (the batched rotation clears it on convergence)
 };
 cudaError_t launch_pre2_restrict_batch(const int n[3], int tile, int count, const BLevel *tab, float omega,
                                        cudaStream_t s);
@@ -345,7 +345,8 @@ cudaError_t launch_reduce_dcgs2_batch(int count, const BVec *tab, const unsigned
 cudaError_t launch_update2_pair_batch(int count, const BVec *tab, const unsigned *first, unsigned nblocks, int j,
                                       cudaStream_t s);
 // Rotation of column j of every active problem; est_out[e] = its est[j] (-1 if inactive).
-cudaError_t launch_givens_batch(int count, const BVec *tab, int j, double *est_out, cudaStream_t s);
+// tol (device, may be null): problems whose estimate meets it are made inactive
+cudaError_t launch_givens_batch(int count, const BVec *tab, int j, double *est_out, const double *tol, cudaStream_t s);
 
 template <typename CI, typename CO>
 cudaError_t launch_convert(size_t n, const CI *in, CO *out, cudaStream_t s);

@@ -280,8 +280,10 @@ __global__ void k_cycle_start(double2 *g, int len, const double2 *beta, int *sto
 
 // Batched rotation of column j (block z = problem), and the gather of every problem's estimate
 // est[j] into out[problem] (-1 for inactive problems); out is pinned host memory, which the host
-// reads once the step's event has fired.
-__global__ void k_givens_b(const BVec *__restrict__ tab, int j, double *out) {
+// reads once the step's event has fired.  A problem whose estimate meets *tol (or is not a
+// number) is made inactive at once, so that the steps already queued behind this one skip it
+// (the host, reading the same estimate, takes it out of the lockstep).
+__global__ void k_givens_b(const BVec *__restrict__ tab, int j, double *out, const double *tol) {
     pdl_enter();
     const BVec &P = tab[blockIdx.z];
     if (threadIdx.x >= 32) return;
@@ -290,7 +292,11 @@ __global__ void k_givens_b(const BVec *__restrict__ tab, int j, double *out) {
         return;
     }
     givens_body(P.H, P.ldh, j, P.cs, P.sn, P.g, P.fnorm, P.est);
-    if (threadIdx.x == 0) out[blockIdx.z] = P.est[j];
+    if (threadIdx.x == 0) {
+        const double e = P.est[j];
+        out[blockIdx.z] = e;
+        if (tol && !(e > *tol)) *P.active = 0;
+    }
 }
 
 // The reduction of the two-vector inner-product pass (block v sums value v of the partials in
@@ -561,9 +567,9 @@ cudaError_t launch_reduce_dcgs2_batch(int count, const BVec *tab, const unsigned
     return cudaGetLastError();
 }
 
-cudaError_t launch_givens_batch(int count, const BVec *tab, int j, double *est_out, cudaStream_t s) {
+cudaError_t launch_givens_batch(int count, const BVec *tab, int j, double *est_out, const double *tol, cudaStream_t s) {
     if (count < 1 || count > 65535 || j < 0 || j > 63) return cudaErrorInvalidValue;
-    launch_pdl(k_givens_b, dim3(1, 1, count), 32, 0, s, tab, j, est_out);
+    launch_pdl(k_givens_b, dim3(1, 1, count), 32, 0, s, tab, j, est_out, tol);
     return cudaGetLastError();
 }
 

@@ -151,6 +151,25 @@ def test_lockstep_status_and_restarts(helm):
         assert st1.iterations == st.iterations and torch.equal(x, x1)
 
 
+def test_lockstep_solves_after_an_early_stop(helm):
+    """The batched rotation takes a converged problem out of the steps already queued behind it
+    (its flag cleared on the device, tested against the current solve's tolerance): batch solves
+    of different tolerances in a row give each problem what a single solve gives, bit for bit."""
+    probs, b = lockstep_batch(helm, 4, 25, (129, 257))
+    rhs = [to_gpu(P.f) for P in probs]
+    for tol in (1e-4, 1e-9, 1e-6):
+        xs = [torch.zeros_like(r) for r in rhs]
+        stats = helm.helm_solve_batch(b, rhs, xs, tol=tol, restart=30, maxit=3000)
+        assert helm.helm_batch_get_engine(b) == "lockstep"
+        for i, (P, r, x, st) in enumerate(zip(probs, rhs, xs, stats)):
+            assert st.status == helm.HELM_OK and st.rel_res <= tol
+            h = gpu_handle(helm, P, pc="csg", prec="c64", gs="dcgs2")
+            helm.helm_set_tuning(h, helm.helm_get_tuning(helm.batch_handle(b, i)))
+            x1, st1 = helm.krylov_solve(h, r, tol=tol, restart=30, maxit=3000)
+            h.close()
+            assert st1.iterations == st.iterations and torch.equal(x, x1)
+
+
 def test_lockstep_rejects_other_configurations(helm):
     probs = W.config_batch(count=2, seed=24, sizes=(129,))
     mg = helm.MGParams(kind="csg", theta_a=probs[0].theta_a, prec="c64", gs="df", coarsest_n=17)

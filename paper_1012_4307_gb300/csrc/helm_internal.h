@@ -83,8 +83,8 @@ template <typename R> struct DevOp {
     // by launch_diag_inv for the temporally blocked smoothers; null otherwise
     const C *dinv = nullptr;
     // device flag (null: none): when it is set at launch, this level's smoothing, residual and
-    // transfer kernels return at once.  Set only on the copy of the finest level's operator
-    // that an FGMRES step queued ahead of the host's convergence test launches with.
+    // transfer kernels return at once (the fused coarse-tail kernels do not test it).  Set only
+    // while the launches of an FGMRES step that may be queued behind a converged one are made.
     const int *gate = nullptr;
 };
 

@@ -224,12 +224,13 @@ static bool dcgs2_fold(const helm_handle *h) {
 }
 
 // z = cycle(level 0's right-hand side) in complex64; w = A z as a float-pair vector.  When the
-// device flag gate is set at launch, the finest level's kernels and the apply do nothing.
+// device flag gate is set at launch, the levels' smoothing, residual and transfer kernels (all but
+// the fused coarse tails) and the apply do nothing.
 static cudaError_t precond_apply_level0(helm_handle *h, float2 *z, float4 *w, const int *gate) {
     pdl_cycle_scope pdl;  // the apply follows the cycle's last kernel
-    h->lv[0].M32.gate = gate;  // for these launches only
+    for (LevelDev &L : h->lv) L.M32.gate = gate;  // for these launches only
     cudaError_t e = precondition_level0_c64(h, z);
-    h->lv[0].M32.gate = nullptr;
+    for (LevelDev &L : h->lv) L.M32.gate = nullptr;
     if (e != cudaSuccess) return e;
     ProfScope ps(h, HELM_K_APPLY, interior_pts(h) * (8 + 8 + 16), 0);
     return launch_apply_A_df(h->Adf, h->dim, z, w, h->stream, gate);

@@ -289,17 +289,17 @@ def run_reference(args):
 # source file is the one that was captured (same SHA-1); otherwise null.
 NCU_TRAFFIC = {
     ("2d-well-n1025", "update_norm"): dict(kernel="k_update2_pair", source="paper_1012_4307_gb300/csrc/kernels_gs_df.cu",
-                                           sha1="d4a0351bfc243b825ca0efadcc3b1c2c319ab3d0", bytes=314222592,
+                                           sha1="093841d405022c73eadc49970ff88b158dc8bcf7", bytes=314093312,
                                            launch="basis slot j = 15, the mean over a restart cycle being 14.5",
                                            profile="profiles/gram_schmidt_dcgs2_kernels_n1025.md"),
     ("2d-well-n1025", "mdot"): dict(kernel="k_mdot2_pair", source="paper_1012_4307_gb300/csrc/kernels_gs_df.cu",
-                                    sha1="d4a0351bfc243b825ca0efadcc3b1c2c319ab3d0", bytes=290177024,
+                                    sha1="093841d405022c73eadc49970ff88b158dc8bcf7", bytes=290221312,
                                     launch="basis slot j = 15, the mean over a restart cycle being 14.5",
                                     profile="profiles/gram_schmidt_dcgs2_kernels_n1025.md"),
     # captured at 161^3 (whose basis vectors, 67 MB each, also stream from DRAM: traffic 0.98 x the
     # algorithmic bytes) and scaled to 257^3 by the node count
     ("3d-well-n257", "update_norm"): dict(kernel="k_update2_pair", source="paper_1012_4307_gb300/csrc/kernels_gs_df.cu",
-                                          sha1="d4a0351bfc243b825ca0efadcc3b1c2c319ab3d0", bytes=3871196000,
+                                          sha1="093841d405022c73eadc49970ff88b158dc8bcf7", bytes=3871945711,
                                           launch="basis slot j = 10 of FGMRES(20), captured at 161^3 and scaled by "
                                                  "the node count",
                                           profile="profiles/update_pass_3d_well_n161.md"),

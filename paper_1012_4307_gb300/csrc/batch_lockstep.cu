@@ -436,7 +436,7 @@ cudaError_t record_step(BatchLockstep *L, const Prof &pf, int j, cudaStream_t s)
     }
     if (j > 0) {
         ProfScope ps(h0, HELM_K_SMALL, 0, 0);
-        CKE(launch_givens_batch(P, L->vec, j - 1, L->est_h + (size_t)(j - 1) * P, L->tol_dev, s));
+        CKE(launch_givens_batch(P, L->vec, j - 1, L->est_h + (size_t)(j - 1) * P, pf.on() ? nullptr : L->tol_dev, s));
     }
     {
         ProfScope ps(h0, HELM_K_UPDATE_NORM, vec_bytes(16.0 * (j + 4) + 8.0), 0);
@@ -462,7 +462,7 @@ cudaError_t record_close(BatchLockstep *L, const Prof &pf, int jc, cudaStream_t 
     {
         ProfScope ps(h0, HELM_K_SMALL, 0, 0);
         CKE(launch_reduce_dcgs2_batch(P, L->vec, row, gs_df_dot2_groups(jc + 1), jc, 0, s));
-        CKE(launch_givens_batch(P, L->vec, jc - 1, L->est_h + (size_t)(jc - 1) * P, L->tol_dev, s));
+        CKE(launch_givens_batch(P, L->vec, jc - 1, L->est_h + (size_t)(jc - 1) * P, pf.on() ? nullptr : L->tol_dev, s));
     }
     return L->capturing ? cudaEventRecordWithFlags(L->close_ev[jc], s, cudaEventRecordExternal)
                         : cudaEventRecord(L->close_ev[jc], s);
@@ -655,10 +655,11 @@ helm_status lockstep_solve(BatchLockstep *L, cudaStream_t user, const void *cons
                     // the problem leaves the lockstep, then x += Z y over its first j + 1
                     // columns.  On convergence the rotation that formed the estimate has already
                     // cleared its flag, so the steps queued behind it skip the problem; otherwise
-                    // (a full cycle, a non-finite estimate) the flag is cleared here, behind them
+                    // (a full cycle, a non-finite estimate, or launches timed one by one, where
+                    // the rotation leaves the flags alone) the flag is cleared here, behind them
                     // (they only write columns and slots past j)
                     act[p] = 0;
-                    if (!(R.est <= tol)) CKR(cudaMemsetAsync(L->active + p, 0, sizeof(int), s));
+                    if (pf.on() || !(R.est <= tol)) CKR(cudaMemsetAsync(L->active + p, 0, sizeof(int), s));
                     if (bad) {
                         R.status = HELM_ERR_NONFINITE;
                         R.done = true;

@@ -384,8 +384,9 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
     // linear), and no conversion launch is needed.
     const bool fold = dcgs2_fold(h), scaled = fold && j > 0;
     // steps queued behind a converged one (the host learns of it one or two steps later) skip
-    // the apply and the two basis passes: the rotation that met the tolerance set the flag
-    int *stop = stop_flag(h);
+    // their work: the rotation that met the tolerance sets the flag.  Not while launches are
+    // timed one by one (helm_profile), so that every timed launch does its full work.
+    int *stop = h->prof.on ? nullptr : stop_flag(h);
     if (scaled) CKE(precond_apply_level0(h, (float2 *)zj, w, stop));
     else CKE(precond_apply_pair(h, u, j > 0 ? h->alpha2 + j : nullptr, zj, w));
     {
@@ -409,8 +410,8 @@ static cudaError_t fgmres_step_dcgs2(helm_handle *h, int j, int m) {
             CKE(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         }
         ProfScope ps(h, HELM_K_SMALL, 0, 0);
-        CKE(launch_givens(h->H, ldh, j - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, h->est_host, h->tol_dev,
-                          stop, gs));
+        CKE(launch_givens(h->H, ldh, j - 1, h->cs, h->sn, h->g, h->fnorm_dev, h->est_dev, h->est_host,
+                          stop ? h->tol_dev : nullptr, stop, gs));
         if (fork) CKE(cudaEventRecord(h->ev_join, h->side));
     }
     {

@@ -516,7 +516,9 @@ static cudaEvent_t unit_event(helm_handle *h, int k, int jmax) {
 //   IN_CYCLE    step j's estimate read back; step j+2 queued (one step of look-ahead; delayed
 //               CGS2: unit j+3, two steps);
 //               converged or cycle full: x += Z y     -> START
-// Pinned host slots: est_host[0..m) step estimates, [m+2] ||f||, [m+4] ||r0||.
+// Pinned host slots, written by the kernels that form the values (no copy in the stream; the
+// host reads a slot once the phase's event has fired): est_host[0..m) step estimates,
+// [m+2] ||f||, [m+4] ||r0||.
 
 static bool event_ready(cudaEvent_t e, bool block, cudaError_t *err) {
     *err = cudaSuccess;

@@ -258,9 +258,10 @@ def test_dcgs2_residual_history_matches_cgs(helm, restart):
     assert np.all(np.abs(a - b) <= 1e-7 * b + 1e-13)
 
 
-@pytest.mark.parametrize("restart", [30, 7])
-def test_dcgs2_solves_after_an_early_stop(helm, restart):
-    """Delayed CGS2 with a complex64 cycle queues steps ahead of the host's convergence test;
+@pytest.mark.parametrize("restart,prec", [(30, "c64"), (7, "c64"), (30, "c128")])
+def test_dcgs2_solves_after_an_early_stop(helm, restart, prec):
+    """Delayed CGS2 queues steps ahead of the host's convergence test (here with a complex64 or a
+    complex128 cycle);
     those queued behind a converged step skip their work (a device flag that the rotation kernel
     sets when an estimate meets the current solve's tolerance, cleared at every cycle start).
     Solves of different tolerances in a row on one handle, so with the flag set by the previous
@@ -274,11 +275,11 @@ def test_dcgs2_solves_after_an_early_stop(helm, restart):
         x, st = helm.krylov_solve(h, f, tol=tol, restart=restart, maxit=2000, history=True)
         return x.clone(), st
 
-    h = gpu_handle(helm, P, pc="csg", prec="c64", gs="dcgs2")
+    h = gpu_handle(helm, P, pc="csg", prec=prec, gs="dcgs2")
     seq = [solve(h, t) for t in tols]
     h.close()
     for t, (x, st) in zip(tols, seq):
-        hf = gpu_handle(helm, P, pc="csg", prec="c64", gs="dcgs2")
+        hf = gpu_handle(helm, P, pc="csg", prec=prec, gs="dcgs2")
         xf, stf = solve(hf, t)
         hf.close()
         assert st.status == helm.HELM_OK and st.rel_res <= t

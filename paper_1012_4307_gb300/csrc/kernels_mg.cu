@@ -640,9 +640,9 @@ __device__ __forceinline__ void pre2_restrict_tile(const OpView<float> &o, float
     const int nx = o.nx, ny = o.ny;
     const bool full = X0 >= 1 && X0 + RW - 1 <= nx - 2 && Y0 >= 1 && Y0 + RH - 1 <= ny - 2;
     auto inside = [&](int x, int y) { return full || (x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2); };
+    // the coefficients are first used by the second sweep: one barrier publishes them with b,
+    // 1 / D and the first sweep
     tile_coef<RW, RH>(o, X0, Y0, T.tc);
-    __syncthreads();
-    if (gate_s) return;
     // load b and 1 / D; sweep 1 from zero (pointwise): u1 = omega b / D
     for_region<RW, RH, TL::NT>([&](int sx, int sy) {
         const int x = X0 + sx, y = Y0 + sy;
@@ -657,6 +657,7 @@ __device__ __forceinline__ void pre2_restrict_tile(const OpView<float> &o, float
         T.u1[sy][sx] = cscale(cmul(bv, dv), omega);
     });
     __syncthreads();
+    if (gate_s) return;
     // sweep 2 on R3 shrunk by one
     for_region<RW, RH, TL::NT>([&](int sx, int sy) {
         float2 v = make_float2(0.f, 0.f);

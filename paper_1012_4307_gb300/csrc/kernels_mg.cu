@@ -552,7 +552,6 @@ template <int TCX, int TCY> struct Tile {
         float2 di[RH][RW];  // 1 / diagonal
         float2 u3[RH][RW];
         float2 u4[RH][RW];
-        float2 ec[TCY + 4][TCX + 4];
     };
 };
 
@@ -721,15 +720,10 @@ __device__ __forceinline__ void prolong_post2_tile(const OpView<float> &o, float
     const int nx = o.nx, ny = o.ny;
     const bool full = X0 >= 1 && X0 + RW - 1 <= nx - 2 && Y0 >= 1 && Y0 + RH - 1 <= ny - 2;
     auto inside = [&](int x, int y) { return full || (x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2); };
-    // coarse nodes [I0 - 2, I0 + TCX + 1] cover floor/ceil(x / 2) for every region column
-    const int C0 = I0 - 2, D0 = J0 - 2;
+    // the coefficients are first used by the first sweep: one barrier publishes them with b,
+    // 1 / D and u + P ec, whose coarse values each node reads itself (the four corner nodes
+    // floor/ceil(x / 2), floor/ceil(y / 2) of an interior fine node lie in the coarse grid)
     tile_coef<RW, RH>(o, X0, Y0, T.tc);
-    for (int q = threadIdx.x; q < (TCX + 4) * (TCY + 4); q += blockDim.x) {
-        const int cx = q % (TCX + 4), cy = q / (TCX + 4), I = C0 + cx, J = D0 + cy;
-        T.ec[cy][cx] = (I >= 0 && I < ncx && J >= 0 && J < ncy) ? ec[(size_t)I + (size_t)ncx * J] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    if (gate_s) return;
     // u3 = u + P ec on the region
     for_region<RW, RH, TL::NT>([&](int sx, int sy) {
         const int x = X0 + sx, y = Y0 + sy;
@@ -739,8 +733,9 @@ __device__ __forceinline__ void prolong_post2_tile(const OpView<float> &o, float
             const size_t p = (size_t)x + (size_t)nx * y;
             bv = b[p];
             dv = o.dinv[p];
-            const int xa = (x >> 1) - C0, xb = ((x + 1) >> 1) - C0, ya = (y >> 1) - D0, yb = ((y + 1) >> 1) - D0;
-            const float2 e = cadd(cadd(T.ec[ya][xa], T.ec[ya][xb]), cadd(T.ec[yb][xa], T.ec[yb][xb]));
+            const size_t ya = (size_t)ncx * (y >> 1), yb = (size_t)ncx * ((y + 1) >> 1);
+            const int xa = x >> 1, xb = (x + 1) >> 1;
+            const float2 e = cadd(cadd(ec[ya + xa], ec[ya + xb]), cadd(ec[yb + xa], ec[yb + xb]));
             v = cadd(u_in[p], cscale(e, 0.25f));
         }
         T.b[sy][sx] = bv;
@@ -748,6 +743,7 @@ __device__ __forceinline__ void prolong_post2_tile(const OpView<float> &o, float
         T.u3[sy][sx] = v;
     });
     __syncthreads();
+    if (gate_s) return;
     // sweep 1 on R3 shrunk by one
     for_region<RW, RH, TL::NT>([&](int sx, int sy) {
         float2 v = make_float2(0.f, 0.f);

@@ -327,7 +327,9 @@ helm_status helm_batch_handle(helm_batch *b, int i, helm_handle **out);
  * would move them (larger than the algorithmic bytes only for the temporally blocked kernels,
  * which do several passes per launch); the host arrays hold ncls entries
  * (ncls <= HELM_K_NCLASS).  Timed launches run eagerly (no CUDA graphs, no side stream), one
- * event pair each, so their sum exceeds a graph-replayed solve's time. */
+ * event pair each, so their sum exceeds a graph-replayed solve's time; and every timed launch
+ * does its full work (the FGMRES steps queued behind a converged one, which an untimed solve
+ * skips on the device, run in full). */
 typedef enum {
     HELM_K_APPLY = 0,         /* FP64 operator apply (A z, true residual)                */
     HELM_K_SMOOTH_FINE = 1,   /* smoothing sweeps on the finest level (blocked kernels:  */

@@ -27,9 +27,24 @@ __device__ __forceinline__ void cmac(float4 a, float2 z, float &sr, float &cr, f
     ff_acc_prod(si, ci, p, e);
 }
 
-// (bx, by, bz): this block's tile of interior nodes.  gv != 0 (a gate flag's value): return
-// once the first operands have been loaded, writing nothing.
-template <int DIM>
+// The first term of the sums: (sr, cr) and (si, ci) start as its exact products (what adding
+// them to zero accumulators with TwoSum gives, up to the sign of a zero).
+__device__ __forceinline__ void cmac_first(float4 a, float2 z, float &sr, float &cr, float &si, float &ci) {
+    const ff ar{a.x, a.y}, ai{a.z, a.w};
+    float p, e;
+    ff_prod_f(ar, z.x, sr, cr);
+    ff_prod_f(ai, z.y, p, e);
+    ff_acc_prod(sr, cr, -p, -e);
+    ff_prod_f(ar, z.y, si, ci);
+    ff_prod_f(ai, z.x, p, e);
+    ff_acc_prod(si, ci, p, e);
+}
+
+// (bx, by, bz): this block's tile of interior nodes.  GATED: gv != 0 (a gate flag's value)
+// returns once the first operands have been loaded, writing nothing (the 2D form then loads a
+// node's operands before its arithmetic; without the gate they are loaded as the arithmetic
+// uses them, which keeps the batched kernel at 32 registers).
+template <int DIM, bool GATED>
 __device__ __forceinline__ void apply_A_df_tile(const DevOpDF &o, const float2 *__restrict__ z, float4 *__restrict__ y,
                                                 int bx, int by, int bz, int gv = 0) {
     const int nx = o.n[0], ny = o.n[1], nz = o.n[2];
@@ -52,7 +67,7 @@ __device__ __forceinline__ void apply_A_df_tile(const DevOpDF &o, const float2 *
         float2 zm = z[p - sz], zc = z[p];
         float2 zw = z[p - 1], ze = z[p + 1], zs = z[p - sy], zn = z[p + sy], zp = z[p + sz];
         float2 kk = o.k2[p];
-        if (gv) return;
+        if (GATED && gv) return;
         for (int k = k0; k < k1; k++, p += sz) {
             float2 zw2 = zw, ze2 = ze, zs2 = zs, zn2 = zn, zp2 = zp, kk2 = kk;
             if (k + 1 < k1) {
@@ -64,8 +79,8 @@ __device__ __forceinline__ void apply_A_df_tile(const DevOpDF &o, const float2 *
                 zp2 = z[q + sz];
                 kk2 = o.k2[q];
             }
-            float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-            cmac(cxw, zw, sr, cr, si, ci);
+            float sr, cr, si, ci;
+            cmac_first(cxw, zw, sr, cr, si, ci);
             cmac(cxe, ze, sr, cr, si, ci);
             cmac(cyw, zs, sr, cr, si, ci);
             cmac(cye, zn, sr, cr, si, ci);
@@ -86,16 +101,28 @@ __device__ __forceinline__ void apply_A_df_tile(const DevOpDF &o, const float2 *
     } else {
         for (int k = k0; k < k1; k++) {
             const size_t p = (size_t)i + sy * ((size_t)j + (size_t)ny * k);
-            const float2 zw = z[p - 1], ze = z[p + 1], zs = z[p - sy], zn = z[p + sy], zc = z[p];
-            const float2 kk = o.k2[p];
-            if (gv) return;
-            float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-            cmac(cxw, zw, sr, cr, si, ci);
-            cmac(cxe, ze, sr, cr, si, ci);
-            cmac(cyw, zs, sr, cr, si, ci);
-            cmac(cye, zn, sr, cr, si, ci);
+            float sr, cr, si, ci;
             ff dr = dxy_r, di = dxy_i;
-            dr = ff_add(dr, ff{-kk.x, -kk.y});  // diagonal: sum of centre coefficients - k^2
+            float2 zc;
+            if constexpr (GATED) {
+                const float2 zw = z[p - 1], ze = z[p + 1], zs = z[p - sy], zn = z[p + sy];
+                const float2 kk = o.k2[p];
+                zc = z[p];
+                if (gv) return;
+                cmac_first(cxw, zw, sr, cr, si, ci);
+                cmac(cxe, ze, sr, cr, si, ci);
+                cmac(cyw, zs, sr, cr, si, ci);
+                cmac(cye, zn, sr, cr, si, ci);
+                dr = ff_add(dr, ff{-kk.x, -kk.y});  // diagonal: sum of centre coefficients - k^2
+            } else {
+                cmac_first(cxw, z[p - 1], sr, cr, si, ci);
+                cmac(cxe, z[p + 1], sr, cr, si, ci);
+                cmac(cyw, z[p - sy], sr, cr, si, ci);
+                cmac(cye, z[p + sy], sr, cr, si, ci);
+                const float2 kk = o.k2[p];
+                dr = ff_add(dr, ff{-kk.x, -kk.y});
+                zc = z[p];
+            }
             cmac(make_float4(dr.hi, dr.lo, di.hi, di.lo), zc, sr, cr, si, ci);
             const ff yr = ff_norm(sr, cr), yi = ff_norm(si, ci);
             y[p] = make_float4(yr.hi, yr.lo, yi.hi, yi.lo);
@@ -108,7 +135,7 @@ __global__ void __launch_bounds__(BX *BY) k_apply_A_df(DevOpDF o, const float2 *
                                                        const int *__restrict__ gate) {
     pdl_enter();
     const int gv = gate_value(gate);
-    apply_A_df_tile<DIM>(o, z, y, blockIdx.x, blockIdx.y, blockIdx.z, gv);
+    apply_A_df_tile<DIM, true>(o, z, y, blockIdx.x, blockIdx.y, blockIdx.z, gv);
 }
 
 // Batched 2D apply of step j over many problems: problem e takes the flat blocks
@@ -125,7 +152,7 @@ __global__ void __launch_bounds__(BX *BY) k_apply_A_df_b(const BVec *__restrict_
     const BVec &P = tab[lo];
     if (*P.active == 0) return;
     const int t = (int)(blockIdx.x - first[lo]), tx = (P.A.n[0] - 2 + BX - 1) / BX;
-    apply_A_df_tile<2>(P.A, P.Z + (size_t)j * P.n, P.V + (size_t)(j + 1) * P.n, t % tx, t / tx, 0);
+    apply_A_df_tile<2, false>(P.A, P.Z + (size_t)j * P.n, P.V + (size_t)(j + 1) * P.n, t % tx, t / tx, 0);
 }
 
 }  // namespace
